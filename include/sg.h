@@ -1,0 +1,250 @@
+/*
+ * sg.h — C ABI of the GB300 superconducting-circuit evolution library (libsupergpu.so).
+ *
+ * The library computes, on one GPU, the hot path of a differentiable simulator of
+ * superconducting processors (arXiv 2406.18155, "SuperGrad"):
+ *
+ *   define subsystems and couplings  ->  diagonalise and truncate each subsystem
+ *   ->  build the drive operators     ->  evolve a batch of state columns with
+ *   fixed-step RK4                    ->  gate fidelity and its gradient with
+ *   respect to pulse and Hamiltonian parameters.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  * Units: energies, amplitudes, frequencies in rad/ns (the paper's 2*pi*GHz,
+ *    Sec. 3.1); times in ns.
+ *  * Composite index: r = sum_i l_i * prod_{j>i} d_j (mode 0 most significant).
+ *    A state slab of D rows and S columns is stored row-major with the column
+ *    index innermost: element (r, s) at offset r*S + s, complex128 as (re, im).
+ *  * Computational states: each mode in level 0 or 1; label j in [0, 2^Nq) with
+ *    mode 0 as the most significant bit.
+ *  * Return value: SG_OK (0) or a negative SG_E_* code.  Nothing throws across
+ *    the ABI.  sg_last_error() gives a message for the last failed call on the
+ *    context.
+ *  * All device work is ordered on the context's stream; calls on one context
+ *    must come from one host thread at a time.
+ *  * Ownership: the library owns contexts, systems and their device tables; the
+ *    caller owns every pointer it passes in (host or device).  A call never
+ *    retains a caller pointer after it returns.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int sg_status;
+typedef struct sg_ctx sg_ctx;
+typedef struct sg_system sg_system;
+typedef struct sg_server sg_server;
+
+enum {
+  SG_OK = 0,
+  SG_E_INVALID = -1,      /* bad argument: NaN, out-of-range index, T/dt not integral ... */
+  SG_E_NOMEM = -2,        /* device or host allocation failed                            */
+  SG_E_STATE = -3,        /* call out of order (e.g. evolve before prepare)               */
+  SG_E_CUDA = -4,         /* a CUDA runtime error; the message names it                   */
+  SG_E_TIMEOUT = -5,      /* a bounded device wait gave up                                */
+  SG_E_PENDING = -6,      /* serving: request not finished yet                            */
+  SG_E_NOMEM_RETRY = -7,  /* serving: over the memory budget now, retry later            */
+  SG_E_CANCELLED = -8,    /* serving: request was cancelled                               */
+  SG_E_NOTFOUND = -9,     /* serving: unknown ticket                                      */
+  SG_E_UNSUPPORTED = -10  /* a configuration this build does not handle                    */
+};
+
+enum { SG_OP_N = 0, SG_OP_PHI = 1 };                          /* charge n, phase phi         */
+enum { SG_ENV_GAUSSIAN = 0, SG_ENV_PWC = 1, SG_ENV_COSINE = 2 };
+enum { SG_FP64 = 0, SG_MIXED = 1 };                           /* arithmetic of the evolution */
+enum { SG_FRAME_INTERACTION = 0, SG_FRAME_LAB = 1 };
+enum { SG_FID_AVG = 0, SG_FID_STATE = 1 };
+
+/* ---------------------------------------------------------------------------
+ * Contexts
+ * ------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (e.g. torch.cuda.current_stream().cuda_stream) or NULL for the legacy default
+ * stream.  The stream is borrowed: the caller keeps it alive. */
+sg_status sg_ctx_create(sg_ctx** out, int device, void* cuda_stream);
+sg_status sg_ctx_destroy(sg_ctx* ctx);
+/* Message of the last failed call on `ctx` (or of the last failed sg_ctx_create
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char* sg_last_error(const sg_ctx* ctx);
+/* Library version string. */
+const char* sg_version(void);
+
+/* ---------------------------------------------------------------------------
+ * System definition (Sec. 2.1, Eq. 1: 1-body and 2-body local terms)
+ * ------------------------------------------------------------------------- */
+
+sg_status sg_system_create(sg_ctx* ctx, sg_system** out);
+sg_status sg_system_destroy(sg_system* sys);
+
+/* Transmon, H = 4 E_C (n - n_g)^2 - E_J cos(phi) in the charge basis
+ * n in [-ncut, ncut] (2 ncut + 1 states, ncut <= 31), truncated to `levels`
+ * eigenstates (2 <= levels <= 8).  Writes the new mode index to *mode_out. */
+sg_status sg_add_transmon(sg_system* sys, double ej, double ec, double ng, int ncut,
+                          int levels, int* mode_out);
+
+/* Fluxonium, Eq. 8: H = 4 E_C n^2 + E_L phi^2 / 2 - E_J cos(phi - phi_ext) in an
+ * n_osc-state oscillator basis (n_osc <= 64), truncated to `levels` eigenstates. */
+sg_status sg_add_fluxonium(sg_system* sys, double ej, double ec, double el, double phi_ext,
+                           int n_osc, int levels, int* mode_out);
+
+/* 2-body coupling strength * op_a(mode_a) (x) op_b(mode_b) (Eq. 9; the capacitive
+ * J_C n n term is op_a = op_b = SG_OP_N).  mode_a != mode_b.  A transmon has only
+ * SG_OP_N. */
+sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b,
+                          double strength, int* term_out);
+
+/* Drive f(t) * op(mode) with f(t) = E(t) cos(omega_d t + phase) (Eq. C1).
+ *   SG_ENV_GAUSSIAN: E = amp exp(-(t - t0)^2 / (2 sigma^2))
+ *   SG_ENV_PWC:      E = amps[j] on the j-th of nseg equal segments of [0, length);
+ *                    an RK4 step takes the segment of its midpoint; 0 after length.
+ *   SG_ENV_COSINE:   E = amp/2 (1 - cos(2 pi t / length)) on [0, length], 0 after (Eq. C2)
+ * omega_mode >= 0 ties omega_d to that mode's bare 0-1 frequency E_1 - E_0 (then
+ * `omega_d` is ignored and the tie is differentiated through); -1 uses omega_d.
+ * `amps` (nseg values) is copied.  length must be a whole number of half steps of
+ * every later evolution. */
+typedef struct {
+  int kind;
+  int nseg;
+  const double* amps;
+  double amp;
+  double sigma;
+  double t0;
+  double length;
+  double omega_d;
+  int omega_mode;
+  double phase;
+} sg_pulse;
+sg_status sg_add_drive(sg_system* sys, int mode, int op, const sg_pulse* p, int* drive_out);
+
+/* Flat real parameter vector used by sg_get_params / sg_set_params and by the
+ * gradient outputs:
+ *   pulse part:  for each drive in order: nseg amplitudes (PWC) or 1 amplitude;
+ *   ham part:    for each mode (E_J, E_C, E_L) (E_L is unused, 0, for a transmon),
+ *                then each coupling's strength.
+ * Counts: */
+sg_status sg_param_counts(const sg_system* sys, int* n_pulse, int* n_ham);
+sg_status sg_get_params(const sg_system* sys, double* pulse, double* ham);
+/* Changing a ham parameter marks the system unprepared. */
+sg_status sg_set_params(sg_system* sys, const double* pulse, const double* ham);
+
+/* ---------------------------------------------------------------------------
+ * Diagonalise and truncate (Sec. 2.1; subsystem eigensolve in FP64 on the GPU)
+ * ------------------------------------------------------------------------- */
+
+/* Builds every subsystem matrix, diagonalises it (FP64 Jacobi on the device),
+ * fixes each eigenvector's sign (first component with |v_i| >= 1e-3 max|v| is
+ * positive), keeps the lowest `levels`, shifts energies so E_0 = 0 and projects
+ * n and phi into the truncated eigenbasis.  Idempotent. */
+sg_status sg_prepare(sg_system* sys);
+/* Host copies of one mode's truncated data: energies[levels], n and phi as
+ * levels x levels complex row-major (re, im) (phi is zero for a transmon).  Any
+ * output pointer may be NULL. */
+sg_status sg_get_spectrum(const sg_system* sys, int mode, double* energies,
+                          double* n_re_im, double* phi_re_im);
+/* Composite dimension D = prod levels and number of modes. */
+sg_status sg_dims(const sg_system* sys, long long* D, int* nmodes);
+
+/* ---------------------------------------------------------------------------
+ * Evolution (RK4) and fidelity (Eq. 13, Eq. D2)
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+  double T;                     /* duration; T/dt must be an integer (within 1e-9 rel.)   */
+  double dt;                    /* RK4 step                                               */
+  int precision;                /* SG_FP64 or SG_MIXED (FP32 stages, FP64 state across steps) */
+  int frame;                    /* SG_FRAME_INTERACTION (default) or SG_FRAME_LAB          */
+  int ncols;                    /* S, number of evolved columns                           */
+  const long long* col_index;   /* host, S flat initial basis indices, or NULL: the
+                                   columns of psi are the initial states                  */
+} sg_evolve_opts;
+
+/* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev
+ * (device, D*S complex128, column innermost).  If opts->col_index is NULL psi_dev
+ * also supplies the initial states. */
+sg_status sg_evolve(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
+
+/* Evolve the columns named by opts->col_index and reduce them to fidelities.
+ * target_re_im: host, Dc x Dc complex (Dc = 2^Nq), row-major (re, im); column j is
+ * the target image of computational state j.  Columns whose initial state is not
+ * computational are evolved but ignored by the fidelity.
+ *   F_avg   = (tr(M M^dag) + |tr M|^2) / (Dc (Dc + 1)),  M = T^dag U_c  (NaN unless
+ *             every computational state is evolved exactly once)
+ *   F_state = |(1/S_c) sum_s <target_s | psi_s>|^2 over the S_c computational columns
+ * F_out[0] = F_avg, F_out[1] = F_state.  Ucomp_out (nullable, host) receives the
+ * Dc x S computational rows of the lab-frame columns as complex row-major. */
+sg_status sg_fidelity(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
+                      double* F_out, double* Ucomp_out);
+
+/* F (of `kind`) and dF/dtheta by the exact discrete adjoint of RK4, with the forward
+ * states recomputed per segment from checkpoints every `ckpt_interval` steps (0 =
+ * about sqrt(N)).  grad_pulse / grad_ham are host arrays of sg_param_counts sizes.
+ * F_out receives {F_avg, F_state}. */
+sg_status sg_fidelity_grad(sg_system* sys, const sg_evolve_opts* opts,
+                           const double* target_re_im, int kind, double* F_out,
+                           double* grad_pulse, double* grad_ham, int ckpt_interval);
+
+/* Timing and memory of the last sg_fidelity / sg_fidelity_grad on this system:
+ * out[0] forward ms, out[1] gradient (backward) ms, out[2] peak library device
+ * bytes during the call, out[3] checkpoint interval used, out[4] number of kernel
+ * launches issued. */
+sg_status sg_last_stats(const sg_system* sys, double* out5);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of fidelity+gradient solves
+ * ------------------------------------------------------------------------- */
+
+typedef struct {
+  sg_system* sys;               /* prepared or not; the server prepares it             */
+  sg_evolve_opts opts;          /* col_index may be NULL: every computational state    */
+  const double* target_re_im;   /* Dc x Dc, copied at submit                            */
+  int kind;                     /* SG_FID_AVG or SG_FID_STATE                           */
+  int want_grad;                /* 1: also compute the gradient                          */
+} sg_request;
+
+typedef struct {
+  sg_status status;             /* SG_OK, or the error of the solve                     */
+  double F[2];                  /* F_avg, F_state                                        */
+  double* grad_pulse;           /* library-owned, valid until sg_server_destroy          */
+  double* grad_ham;
+  int n_pulse, n_ham;
+  double submit_s, start_s, done_s;   /* server clock (seconds since create)            */
+} sg_result;
+
+typedef struct {
+  uint64_t submitted, completed, cancelled, rejected;
+  double solves_per_s;          /* completed / busy wall time                           */
+  double p50_s, p99_s;          /* latency submit -> done of completed requests          */
+  double gpu_busy_frac;
+  size_t mem_in_use, mem_budget;
+  int active_slots, max_slots;
+} sg_stats;
+
+/* A server owns one worker thread that admits requests into slots while the
+ * device memory they need fits `mem_budget_bytes` and a slot is free, groups the
+ * admitted requests by step shape and advances each group in shared batched
+ * launches.  Requests that arrive while others run join at the next step
+ * boundary of the shared launch loop. */
+sg_status sg_server_create(sg_ctx* ctx, size_t mem_budget_bytes, int max_slots, sg_server** out);
+sg_status sg_server_destroy(sg_server* srv);
+/* Queue a request.  The request's system must stay alive until its result is
+ * polled.  Returns SG_E_NOMEM_RETRY if the request alone exceeds the budget. */
+sg_status sg_server_submit(sg_server* srv, const sg_request* req, uint64_t* ticket);
+/* SG_OK and *out filled when done; SG_E_PENDING while queued or running. */
+sg_status sg_server_poll(sg_server* srv, uint64_t ticket, sg_result* out);
+/* Block until the ticket is done (or cancelled); same outputs as poll. */
+sg_status sg_server_wait(sg_server* srv, uint64_t ticket, sg_result* out);
+sg_status sg_server_cancel(sg_server* srv, uint64_t ticket);
+sg_status sg_server_stats(sg_server* srv, sg_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

@@ -1,0 +1,233 @@
+"""Thin Python layer over the C ABI (argument marshalling only).
+
+PyTorch provides device memory and the stream; every computation runs in the
+library's CUDA kernels.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import capi
+from .capi import check, lib
+
+_OPS = {"n": capi.SG_OP_N, "phi": capi.SG_OP_PHI}
+_ENV = {"gaussian": capi.SG_ENV_GAUSSIAN, "pwc": capi.SG_ENV_PWC, "cosine": capi.SG_ENV_COSINE}
+_PREC = {"fp64": capi.SG_FP64, "mixed": capi.SG_MIXED}
+_FRAME = {"interaction": capi.SG_FRAME_INTERACTION, "lab": capi.SG_FRAME_LAB}
+_KIND = {"avg": capi.SG_FID_AVG, "state": capi.SG_FID_STATE}
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _c128_pairs(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.complex128)).view(np.float64)
+
+
+class Context:
+    """sg_ctx on one CUDA device, ordered on a torch stream (current stream by default)."""
+
+    def __init__(self, device=0, stream=None):
+        import torch
+        self.device = device
+        if stream is None:
+            with torch.cuda.device(device):
+                stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        h = C.c_void_p()
+        check(lib().sg_ctx_create(C.byref(h), device, C.c_void_p(stream.cuda_stream)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().sg_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None):
+    o = capi.sg_evolve_opts()
+    o.T, o.dt = float(T), float(dt)
+    o.precision = _PREC[precision]
+    o.frame = _FRAME[frame]
+    keep = None
+    if col_index is not None:
+        keep = np.ascontiguousarray(np.asarray(col_index, dtype=np.int64))
+        o.ncols = keep.size
+        o.col_index = keep.ctypes.data_as(C.POINTER(C.c_longlong))
+    else:
+        o.ncols = int(ncols)
+        o.col_index = None
+    return o, keep
+
+
+class System:
+    def __init__(self, ctx):
+        self.ctx = ctx
+        h = C.c_void_p()
+        check(lib().sg_system_create(ctx.h, C.byref(h)), ctx.h)
+        self.h = h
+        self._keep = []
+
+    def _chk(self, rc):
+        return check(rc, self.ctx.h)
+
+    # --- definition -----------------------------------------------------------
+    def add_transmon(self, ej, ec, ng=0.0, ncut=10, levels=4):
+        m = C.c_int()
+        self._chk(lib().sg_add_transmon(self.h, ej, ec, ng, ncut, levels, C.byref(m)))
+        return m.value
+
+    def add_fluxonium(self, ej, ec, el, phi_ext=np.pi, n_osc=50, levels=4):
+        m = C.c_int()
+        self._chk(lib().sg_add_fluxonium(self.h, ej, ec, el, phi_ext, n_osc, levels, C.byref(m)))
+        return m.value
+
+    def add_coupling(self, a, op_a, b, op_b, J):
+        t = C.c_int()
+        self._chk(lib().sg_add_coupling(self.h, a, _OPS[op_a], b, _OPS[op_b], J, C.byref(t)))
+        return t.value
+
+    def add_drive(self, mode, op, env, amp=0.0, amps=None, sigma=1.0, t0=0.0, length=1.0,
+                  omega_d=0.0, omega_mode=None, phase=0.0):
+        p = capi.sg_pulse()
+        p.kind = _ENV[env]
+        if amps is not None:
+            arr = np.ascontiguousarray(np.asarray(amps, dtype=np.float64))
+            self._keep.append(arr)
+            p.nseg = arr.size
+            p.amps = _dptr(arr)
+        else:
+            p.nseg = 1
+        p.amp, p.sigma, p.t0, p.length = float(amp), float(sigma), float(t0), float(length)
+        p.omega_d = float(omega_d) if omega_d is not None else 0.0
+        p.omega_mode = -1 if omega_mode is None else int(omega_mode)
+        p.phase = float(phase)
+        k = C.c_int()
+        self._chk(lib().sg_add_drive(self.h, mode, _OPS[op], C.byref(p), C.byref(k)))
+        return k.value
+
+    @classmethod
+    def from_workload(cls, ctx, wl):
+        s = cls(ctx)
+        for m in wl["modes"]:
+            if m["kind"] == "transmon":
+                s.add_transmon(m["ej"], m["ec"], m.get("ng", 0.0), m.get("ncut", 10), m["levels"])
+            else:
+                s.add_fluxonium(m["ej"], m["ec"], m["el"], m.get("phi_ext", np.pi),
+                                m.get("n_osc", 50), m["levels"])
+        for c in wl["couplings"]:
+            s.add_coupling(c["a"], c["op_a"], c["b"], c["op_b"], c["J"])
+        for d in wl["drives"]:
+            s.add_drive(d["mode"], d["op"], d["env"], amp=d.get("amp", 0.0), amps=d.get("amps"),
+                        sigma=d.get("sigma", 1.0), t0=d.get("t0", 0.0), length=d["length"],
+                        omega_d=d.get("omega_d", 0.0), omega_mode=d.get("omega_mode"),
+                        phase=d.get("phase", 0.0))
+        s.wl = wl
+        return s
+
+    def close(self):
+        if self.h:
+            lib().sg_system_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- prepare / inspect --------------------------------------------------------
+    def prepare(self):
+        self._chk(lib().sg_prepare(self.h))
+
+    def dims(self):
+        D, n = C.c_longlong(), C.c_int()
+        self._chk(lib().sg_dims(self.h, C.byref(D), C.byref(n)))
+        return D.value, n.value
+
+    def spectrum(self, mode, d):
+        E = np.zeros(d)
+        n = np.zeros(2 * d * d)
+        phi = np.zeros(2 * d * d)
+        self._chk(lib().sg_get_spectrum(self.h, mode, _dptr(E), _dptr(n), _dptr(phi)))
+        return E, n.view(np.complex128).reshape(d, d), phi.view(np.complex128).reshape(d, d)
+
+    def param_counts(self):
+        a, b = C.c_int(), C.c_int()
+        self._chk(lib().sg_param_counts(self.h, C.byref(a), C.byref(b)))
+        return a.value, b.value
+
+    def get_params(self):
+        npul, nham = self.param_counts()
+        p, h = np.zeros(max(npul, 1)), np.zeros(max(nham, 1))
+        self._chk(lib().sg_get_params(self.h, _dptr(p), _dptr(h)))
+        return p[:npul], h[:nham]
+
+    def set_params(self, pulse=None, ham=None):
+        pa = None if pulse is None else np.ascontiguousarray(np.asarray(pulse, dtype=np.float64))
+        ha = None if ham is None else np.ascontiguousarray(np.asarray(ham, dtype=np.float64))
+        self._chk(lib().sg_set_params(self.h, None if pa is None else _dptr(pa),
+                                      None if ha is None else _dptr(ha)))
+
+    # --- evolution -----------------------------------------------------------------
+    def evolve(self, T, dt, precision="mixed", frame="interaction", col_index=None, psi=None):
+        """Lab-frame columns after T, as a (D, S) complex128 torch tensor on the device.
+        Starts from basis states col_index, or from the given device tensor psi."""
+        import torch
+        D, _ = self.dims()
+        if psi is None:
+            S = len(col_index)
+            psi = torch.empty((D, S), dtype=torch.complex128, device=f"cuda:{self.ctx.device}")
+            o, keep = evolve_opts(T, dt, precision, frame, col_index)
+        else:
+            assert psi.dtype == torch.complex128 and psi.is_contiguous() and psi.shape[0] == D
+            o, keep = evolve_opts(T, dt, precision, frame, None, ncols=psi.shape[1])
+        self._chk(lib().sg_evolve(self.h, C.byref(o), C.c_void_p(psi.data_ptr())))
+        return psi
+
+    def fidelity(self, T, dt, target, col_index, precision="mixed", frame="interaction"):
+        o, keep = evolve_opts(T, dt, precision, frame, col_index)
+        tg = _c128_pairs(target)
+        F = np.zeros(2)
+        Dc = target.shape[0]
+        U = np.zeros(2 * Dc * len(col_index))
+        self._chk(lib().sg_fidelity(self.h, C.byref(o), _dptr(tg), _dptr(F), _dptr(U)))
+        return F[0], F[1], U.view(np.complex128).reshape(Dc, len(col_index))
+
+    def fidelity_grad(self, T, dt, target, col_index, kind="avg", precision="mixed",
+                      frame="interaction", ckpt=0):
+        o, keep = evolve_opts(T, dt, precision, frame, col_index)
+        tg = _c128_pairs(target)
+        F = np.zeros(2)
+        npul, nham = self.param_counts()
+        gp, gh = np.zeros(max(npul, 1)), np.zeros(max(nham, 1))
+        self._chk(lib().sg_fidelity_grad(self.h, C.byref(o), _dptr(tg), _KIND[kind], _dptr(F),
+                                         _dptr(gp), _dptr(gh), int(ckpt)))
+        return F, gp[:npul], gh[:nham]
+
+    def last_stats(self):
+        out = np.zeros(5)
+        self._chk(lib().sg_last_stats(self.h, _dptr(out)))
+        return {"forward_ms": out[0], "backward_ms": out[1], "peak_bytes": out[2],
+                "ckpt_interval": int(out[3]), "launches": int(out[4])}
+
+
+def workload_fidelity(ctx, wl, precision="mixed", grad=False, ckpt=0):
+    """Convenience: build, prepare and solve one workload dict."""
+    s = System.from_workload(ctx, wl)
+    s.prepare()
+    if grad:
+        F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                                    kind=wl["fid_kind"], precision=precision,
+                                    frame=wl.get("frame", "interaction"), ckpt=ckpt)
+        return s, F, gp, gh
+    Fa, Fs, U = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision=precision,
+                           frame=wl.get("frame", "interaction"))
+    return s, (Fa, Fs), U

@@ -1,0 +1,1432 @@
+// Fixed-step RK4 evolution of a slab of state columns under the Kronecker-sum
+// Hamiltonian, fidelity reduction, and the exact discrete adjoint with segment
+// checkpointing.
+//
+// Paper: Eq. 1 (local 1- and 2-body terms), App. B (the operator is applied by
+// contracting one tensor mode at a time, never as a dense D x D matrix), Eq. 13 and
+// Eq. D2 (fidelities), Sec. 2.5 / Eqs. 7-12 (adjoint: the co-state is pulled back
+// through each step and the gradient accumulates a_i^T dU_i/dtheta psi_{i-1}).
+//
+// Arithmetic: SG_FP64 runs everything in complex128.  SG_MIXED runs the stage
+// contractions in complex64 and keeps the state and co-state in complex128 across
+// steps; each step's increment dt/6 (k1 + 2k2 + 2k3 + k4) is formed in FP32 and added
+// to the FP64 state once per step.  Reductions (fidelity, gradient) finish in FP64.
+//
+// This file holds the generic "gather" path: one launch per RK4 stage, each thread
+// computes one slab entry and reads its neighbours along every mode a term acts on.
+// It is correct for any mode count and level counts up to SG_MAXD.
+#include "sg_internal.h"
+#include "kplan.h"
+#include "fast.h"
+#include <cmath>
+#include <cstring>
+#include <algorithm>
+#include <chrono>
+
+namespace {
+
+constexpr int kT = 256;
+
+// ---------------------------------------------------------------------------
+// drives and stage tables
+// ---------------------------------------------------------------------------
+struct DriveDev {
+  int mode, op, kind, nseg, mp, amps_off;
+  double amp, sigma, t0, length, omega, phase;
+};
+
+struct TabArgs {
+  KPlan p;
+  int nq, K, N, frame;
+  int dims[SG_MAXQ];
+  int eoff[SG_MAXQ];          // offset of mode i's levels in the flat energy/phase arrays
+  int sumd;
+  const DriveDev* drives;
+  const double* amps;
+  const double* E;            // flat ground-shifted energies (sumd)
+  const double2* opd;         // flat truncated operators: per mode 2 x d x d
+  int opd_off[SG_MAXQ];
+  int e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
+  double J[SG_MAXEDGE];
+  int drv_of_slot_start[SG_MAXQ + 1];
+  int drv_list[SG_MAXDRIVE];
+  double dt;
+  double* coef;               // 3N x K
+  double2* ph;                // 3N x sumd
+  double2* tab;               // 3N x row (FP64)
+  float2* tab32;              // 3N x row (FP32 copy) or null
+};
+
+__device__ double envelope_dev(const DriveDev& dr, const double* amps, int n, int j, double t) {
+  const int m = 2 * n + j;
+  if (dr.kind == SG_ENV_GAUSSIAN) {
+    double x = t - dr.t0;
+    return dr.amp * exp(-(x * x) / (2.0 * dr.sigma * dr.sigma));
+  }
+  if (dr.kind == SG_ENV_COSINE) {
+    if (m > dr.mp) return 0.0;
+    return dr.amp * 0.5 * (1.0 - cos(2.0 * M_PI * t / dr.length));
+  }
+  const int mid = 2 * n + 1;                       // PWC: segment of the step midpoint
+  if (mid >= dr.mp) return 0.0;
+  int seg = (int)(((long long)mid * dr.nseg) / dr.mp);
+  if (seg > dr.nseg - 1) seg = dr.nseg - 1;
+  return amps[dr.amps_off + seg];
+}
+
+// One block per stage q = 3n + j: coefficients f_k, phases exp(i E_a t), then every
+// term matrix of the stage row.
+__global__ void k_tables(TabArgs a) {
+  const int q = blockIdx.x;
+  const int n = q / 3, j = q % 3;
+  const double t = (double)(2 * n + j) * a.dt * 0.5;
+  __shared__ double f[SG_MAXDRIVE];
+  __shared__ double2 ph[SG_MAXQ * SG_MAXD];
+  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+    const DriveDev dr = a.drives[k];
+    double E = envelope_dev(dr, a.amps, n, j, t);
+    double v = E * cos(dr.omega * t + dr.phase);
+    f[k] = v;
+    a.coef[(size_t)q * a.K + k] = v;
+  }
+  for (int i = threadIdx.x; i < a.sumd; i += blockDim.x) {
+    double s, c;
+    if (a.frame == SG_FRAME_INTERACTION) sincos(a.E[i] * t, &s, &c); else { s = 0.0; c = 1.0; }
+    ph[i] = make_double2(c, s);
+    a.ph[(size_t)q * a.sumd + i] = make_double2(c, s);
+  }
+  __syncthreads();
+  double2* row = a.tab + (size_t)q * a.p.row;
+  // 1-body slots
+  for (int u = 0; u < a.p.n1; ++u) {
+    const int i = a.p.s1_mode[u], d = a.dims[i];
+    for (int ab = threadIdx.x; ab < d * d; ab += blockDim.x) {
+      const int ia = ab / d, ib = ab % d;
+      double2 pa = ph[a.eoff[i] + ia], pb = ph[a.eoff[i] + ib];
+      double2 P = cmul(pa, cconj(pb));
+      double2 acc = make_double2(0.0, 0.0);
+      for (int x = a.drv_of_slot_start[u]; x < a.drv_of_slot_start[u + 1]; ++x) {
+        const int k = a.drv_list[x];
+        const int op = a.drives[k].op;
+        double2 O = a.opd[a.opd_off[i] + op * d * d + ab];
+        double2 v = cmul(O, P);
+        acc.x += f[k] * v.x;
+        acc.y += f[k] * v.y;
+      }
+      if (a.frame == SG_FRAME_LAB && ia == ib) acc.x += a.E[a.eoff[i] + ia];
+      row[a.p.s1_off[u] + ab] = acc;
+      if (a.tab32) a.tab32[(size_t)q * a.p.row + a.p.s1_off[u] + ab] = make_float2((float)acc.x, (float)acc.y);
+    }
+  }
+  for (int e = 0; e < a.p.ne; ++e) {
+    const int ia_ = a.p.e_a[e], ib_ = a.p.e_b[e];
+    for (int side = 0; side < 2; ++side) {
+      const int i = side == 0 ? ia_ : ib_;
+      const int op = side == 0 ? a.e_opa[e] : a.e_opb[e];
+      const int d = a.dims[i];
+      const int off = side == 0 ? a.p.e_offL[e] : a.p.e_offR[e];
+      for (int ab = threadIdx.x; ab < d * d; ab += blockDim.x) {
+        const int x = ab / d, y = ab % d;
+        double2 P = cmul(ph[a.eoff[i] + x], cconj(ph[a.eoff[i] + y]));
+        double2 v = cmul(a.opd[a.opd_off[i] + op * d * d + ab], P);
+        if (side == 0) { v.x *= a.J[e]; v.y *= a.J[e]; }
+        row[off + ab] = v;
+        if (a.tab32) a.tab32[(size_t)q * a.p.row + off + ab] = make_float2((float)v.x, (float)v.y);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// H y at one slab entry (gather form)
+// ---------------------------------------------------------------------------
+template <typename C>
+__device__ __forceinline__ C apply_entry(const KPlan& p, const C* __restrict__ M,
+                                         const C* __restrict__ X, long long e) {
+  const int S = p.S;
+  const long long r = e / S;
+  const int s = (int)(e - r * S);
+  C acc = cmk<C>(0.0, 0.0);
+  for (int u = 0; u < p.n1; ++u) {
+    const int i = p.s1_mode[u], d = p.dims[i];
+    const long long st = p.st[i];
+    const int l = (int)((r / st) % d);
+    const C* Xb = X + (r - (long long)l * st) * S + s;
+    const C* Mr = M + p.s1_off[u] + l * d;
+    const long long stS = st * S;
+    if ((p.par1 >> u) & 1) {
+      for (int b = (l + 1) & 1; b < d; b += 2) acc = cfma(Mr[b], Xb[b * stS], acc);
+    } else {
+      for (int b = 0; b < d; ++b) acc = cfma(Mr[b], Xb[b * stS], acc);
+    }
+  }
+  for (int q = 0; q < p.ne; ++q) {
+    const int i = p.e_a[q], j = p.e_b[q];
+    const int di = p.dims[i], dj = p.dims[j];
+    const long long sti = p.st[i], stj = p.st[j];
+    const int li = (int)((r / sti) % di), lj = (int)((r / stj) % dj);
+    const C* Xb = X + (r - (long long)li * sti - (long long)lj * stj) * S + s;
+    const C* L = M + p.e_offL[q] + li * di;
+    const C* R = M + p.e_offR[q] + lj * dj;
+    const bool pl = (p.parL >> q) & 1ull, pr = (p.parR >> q) & 1ull;
+    const long long siS = sti * S, sjS = stj * S;
+    for (int x = pl ? ((li + 1) & 1) : 0; x < di; x += pl ? 2 : 1) {
+      C u = cmk<C>(0.0, 0.0);
+      for (int y = pr ? ((lj + 1) & 1) : 0; y < dj; y += pr ? 2 : 1)
+        u = cfma(R[y], Xb[x * siS + y * sjS], u);
+      acc = cfma(L[x], u, acc);
+    }
+  }
+  return acc;
+}
+
+template <typename C>
+__device__ __forceinline__ void load_row(const C* __restrict__ tab, int row, C* sm) {
+  for (int i = threadIdx.x; i < row; i += blockDim.x) sm[i] = tab[i];
+  __syncthreads();
+}
+
+// Forward RK4 stage.  X = stage input y_s, k = -i H y_s.
+//   STAGE 0: D = dt/6 k,  Xn = psi + dt/2 k      STAGE 1: D += dt/3 k, Xn = psi + dt/2 k
+//   STAGE 2: D += dt/3 k, Xn = psi + dt k        STAGE 3: psi_out = psi_in + (D + dt/6 k), Xn = psi_out
+// STORE: recompute mode of the adjoint (writes Xn only).
+template <typename R, int STAGE, bool STORE>
+__global__ void __launch_bounds__(kT) k_fwd(KPlan p, const typename CT<R>::T* __restrict__ X,
+                                            const typename CT<R>::T* __restrict__ tabrow,
+                                            const double2* __restrict__ psi_in, double2* psi_out,
+                                            typename CT<R>::T* __restrict__ Xn,
+                                            typename CT<R>::T* __restrict__ Dacc, double dt) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* M = reinterpret_cast<C*>(smraw);
+  load_row(tabrow, p.row, M);
+  const long long total = p.D * p.S;
+  const R h = (R)dt;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    C a = apply_entry(p, M, X, e);
+    C k = cmk<C>(a.y, -a.x);                       // -i * H y
+    const double2 ps = psi_in[e];
+    const C pr = to_c(ps, R(0));
+    if (STAGE == 0) {
+      if (!STORE) Dacc[e] = cmk<C>(h / 6 * k.x, h / 6 * k.y);
+      Xn[e] = cmk<C>(pr.x + h / 2 * k.x, pr.y + h / 2 * k.y);
+    } else if (STAGE == 1) {
+      if (!STORE) { C d = Dacc[e]; Dacc[e] = cmk<C>(d.x + h / 3 * k.x, d.y + h / 3 * k.y); }
+      Xn[e] = cmk<C>(pr.x + h / 2 * k.x, pr.y + h / 2 * k.y);
+    } else if (STAGE == 2) {
+      if (!STORE) { C d = Dacc[e]; Dacc[e] = cmk<C>(d.x + h / 3 * k.x, d.y + h / 3 * k.y); }
+      Xn[e] = cmk<C>(pr.x + h * k.x, pr.y + h * k.y);
+    } else {
+      C d = Dacc[e];
+      R incx = d.x + h / 6 * k.x, incy = d.y + h / 6 * k.y;
+      double2 pn = make_double2(ps.x + (double)incx, ps.y + (double)incy);
+      psi_out[e] = pn;
+      Xn[e] = to_c(pn, R(0));
+    }
+  }
+}
+
+// Adjoint RK4 stage (reverse order 3, 2, 1, 0).  X = kbar_s, ybar_s = A_s^dag kbar_s = i H kbar_s.
+//   3: Db = yb, Xn = dt/3 pb + dt yb      2: Db += yb, Xn = dt/3 pb + dt/2 yb
+//   1: Db += yb, Xn = dt/6 pb + dt/2 yb   0: pb <- pb + (Db + yb), Xn = dt/6 pb
+template <typename R, int STAGE>
+__global__ void __launch_bounds__(kT) k_adj(KPlan p, const typename CT<R>::T* __restrict__ X,
+                                            const typename CT<R>::T* __restrict__ tabrow,
+                                            double2* __restrict__ pbar,
+                                            typename CT<R>::T* __restrict__ Xn,
+                                            typename CT<R>::T* __restrict__ Db, double dt) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* M = reinterpret_cast<C*>(smraw);
+  load_row(tabrow, p.row, M);
+  const long long total = p.D * p.S;
+  const R h = (R)dt;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    C a = apply_entry(p, M, X, e);
+    C yb = cmk<C>(-a.y, a.x);                      // i * H kbar
+    const double2 pb = pbar[e];
+    const C pr = to_c(pb, R(0));
+    if (STAGE == 3) {
+      Db[e] = yb;
+      Xn[e] = cmk<C>(h / 3 * pr.x + h * yb.x, h / 3 * pr.y + h * yb.y);
+    } else if (STAGE == 2) {
+      C d = Db[e];
+      Db[e] = cmk<C>(d.x + yb.x, d.y + yb.y);
+      Xn[e] = cmk<C>(h / 3 * pr.x + h / 2 * yb.x, h / 3 * pr.y + h / 2 * yb.y);
+    } else if (STAGE == 1) {
+      C d = Db[e];
+      Db[e] = cmk<C>(d.x + yb.x, d.y + yb.y);
+      Xn[e] = cmk<C>(h / 6 * pr.x + h / 2 * yb.x, h / 6 * pr.y + h / 2 * yb.y);
+    } else {
+      C d = Db[e];
+      double2 pn = make_double2(pb.x + (double)(d.x + yb.x), pb.y + (double)(d.y + yb.y));
+      pbar[e] = pn;
+      C q = to_c(pn, R(0));
+      Xn[e] = cmk<C>(h / 6 * q.x, h / 6 * q.y);
+    }
+  }
+}
+
+template <typename R>
+__global__ void k_cast(const double2* __restrict__ src, typename CT<R>::T* __restrict__ dst,
+                       long long n, double scale) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double2 v = src[e];
+    dst[e] = to_c(make_double2(v.x * scale, v.y * scale), R(0));
+  }
+}
+
+__global__ void k_init_cols(double2* psi, long long D, int S, const long long* cols) {
+  const long long total = D * S;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e / S;
+    int s = (int)(e - r * S);
+    psi[e] = make_double2(cols[s] == r ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// frame epilogue and fidelity (Eq. 13, Eq. D2)
+// ---------------------------------------------------------------------------
+struct FrameArgs {
+  int nq, S;
+  long long D;
+  int dims[SG_MAXQ];
+  long long st[SG_MAXQ];
+  int eoff[SG_MAXQ];
+  const double* E;
+  double T;
+  double sign;                // -1: psi_lab = exp(-i Hd T) psi_I ; +1: the inverse
+};
+
+// x <- exp(sign * i * E_tot(r) * T) x
+__global__ void k_frame(FrameArgs a, double2* x) {
+  const long long total = a.D * a.S;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (long long)gridDim.x * blockDim.x) {
+    long long r = e / a.S;
+    double Et = 0.0;
+    for (int i = 0; i < a.nq; ++i) Et += a.E[a.eoff[i] + (int)((r / a.st[i]) % a.dims[i])];
+    double s, c;
+    sincos(a.sign * Et * a.T, &s, &c);
+    double2 v = x[e];
+    x[e] = make_double2(c * v.x - s * v.y, c * v.y + s * v.x);
+  }
+}
+
+struct FidArgs {
+  int S, Dc, Sc, full, kind, nq;
+  const double2* Uc;          // Dc x S   (comp rows of the lab-frame columns)
+  const double2* Tg;          // Dc x Dc
+  const int* lab;             // S: comp label of each column or -1
+  double* F;                  // [F_avg, F_state]
+  double2* bar;               // Dc x S co-state (lab frame) or null
+  double2* M;                 // Dc x Dc scratch (full only)
+  double* ebar_frame;         // nq x SG_MAXD or null
+  double T;
+  int frame;
+};
+
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// Single block, FP64, fixed-order reductions.
+__global__ void k_fidelity(FidArgs a) {
+  __shared__ double red[kT];
+  __shared__ double2 zsh;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  // z = sum over comp columns of <target_{lab(s)} | psi_s>
+  double zr = 0.0, zi = 0.0;
+  for (int i = tid; i < a.Dc * a.S; i += nt) {
+    int r = i / a.S, s = i % a.S;
+    int l = a.lab[s];
+    if (l < 0) continue;
+    double2 t = a.Tg[r * a.Dc + l], u = a.Uc[i];
+    zr += t.x * u.x + t.y * u.y;
+    zi += t.x * u.y - t.y * u.x;
+  }
+  double Zr = block_sum(zr, red), Zi = block_sum(zi, red);
+  const double Sc = (double)a.Sc;
+  double Fst = (Zr * Zr + Zi * Zi) / (Sc * Sc);
+  double Favg = nan("");
+  double2 trM = make_double2(Zr, Zi);
+  if (a.full) {
+    // M[x][l] = sum_r conj(T[r][x]) U[r][col(l)]
+    const int Dc = a.Dc;
+    double fro = 0.0;
+    for (int i = tid; i < Dc * Dc; i += nt) {
+      int x = i / Dc, l = i % Dc;
+      int col = -1;
+      for (int s = 0; s < a.S; ++s) if (a.lab[s] == l) { col = s; break; }
+      double2 acc = make_double2(0.0, 0.0);
+      for (int r = 0; r < Dc; ++r) {
+        double2 t = a.Tg[r * Dc + x], u = a.Uc[r * a.S + col];
+        acc.x += t.x * u.x + t.y * u.y;
+        acc.y += t.x * u.y - t.y * u.x;
+      }
+      a.M[i] = acc;
+      fro += acc.x * acc.x + acc.y * acc.y;
+    }
+    double Fro = block_sum(fro, red);
+    Favg = (Fro + Zr * Zr + Zi * Zi) / ((double)Dc * (Dc + 1));
+  }
+  if (tid == 0) { a.F[0] = Favg; a.F[1] = Fst; }
+  if (!a.bar) return;
+  __syncthreads();
+  // co-state dF/dRe psi + i dF/dIm psi on the comp rows
+  for (int i = tid; i < a.Dc * a.S; i += nt) {
+    int r = i / a.S, s = i % a.S;
+    int l = a.lab[s];
+    double2 b = make_double2(0.0, 0.0);
+    if (l >= 0) {
+      if (a.kind == SG_FID_STATE) {
+        double2 t = a.Tg[r * a.Dc + l];
+        double sc = 2.0 / (Sc * Sc);
+        b = make_double2(sc * (trM.x * t.x - trM.y * t.y), sc * (trM.x * t.y + trM.y * t.x));
+      } else {
+        const int Dc = a.Dc;
+        double2 acc = make_double2(0.0, 0.0);             // (T M)[r][l]
+        for (int x = 0; x < Dc; ++x) {
+          double2 t = a.Tg[r * Dc + x], m = a.M[x * Dc + l];
+          acc.x += t.x * m.x - t.y * m.y;
+          acc.y += t.x * m.y + t.y * m.x;
+        }
+        double2 t = a.Tg[r * Dc + l];
+        acc.x += trM.x * t.x - trM.y * t.y;
+        acc.y += trM.x * t.y + trM.y * t.x;
+        double sc = 2.0 / ((double)Dc * (Dc + 1));
+        b = make_double2(sc * acc.x, sc * acc.y);
+      }
+    }
+    a.bar[i] = b;
+  }
+}
+
+// Energy co-gradient of the frame epilogue psi_lab = exp(-i Hd T) psi_I:
+// ebar[i][c] += sum over comp rows with digit_i = c of Re(conj(bar) (-i T) psi_lab).
+// Comp rows only have digits 0 and 1.  Single block.
+__global__ void k_frame_ebar(FidArgs a) {
+  __shared__ double red[kT];
+  for (int i = 0; i < a.nq; ++i) {
+    for (int c = 0; c < 2; ++c) {
+      double part = 0.0;
+      for (int x = threadIdx.x; x < a.Dc * a.S; x += blockDim.x) {
+        int r = x / a.S;
+        int bit = (r >> (a.nq - 1 - i)) & 1;
+        if (bit != c) continue;
+        double2 b = a.bar[x], u = a.Uc[x];
+        // Re(conj(b) * (-i T) u) = T * (b.x*u.y - b.y*u.x)
+        part += a.T * (b.x * u.y - b.y * u.x);
+      }
+      double tot = block_sum(part, red);
+      if (threadIdx.x == 0) a.ebar_frame[i * SG_MAXD + c] += tot;
+    }
+  }
+}
+
+struct CompArgs {
+  int nq, S, Dc;
+  int dims[SG_MAXQ];
+};
+__device__ long long comp_row(const CompArgs& a, int j) {
+  long long r = 0;
+  for (int i = 0; i < a.nq; ++i) r = r * a.dims[i] + ((j >> (a.nq - 1 - i)) & 1);
+  return r;
+}
+__global__ void k_gather_comp(CompArgs a, const double2* psi, double2* Uc) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < a.Dc * a.S; x += gridDim.x * blockDim.x) {
+    int j = x / a.S, s = x % a.S;
+    Uc[x] = psi[comp_row(a, j) * a.S + s];
+  }
+}
+__global__ void k_scatter_comp(CompArgs a, const double2* bar, double2* pbar) {
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < a.Dc * a.S; x += gridDim.x * blockDim.x) {
+    int j = x / a.S, s = x % a.S;
+    pbar[comp_row(a, j) * a.S + s] = bar[x];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// gradient: cross-densities per stage and their contraction into co-gradients
+// ---------------------------------------------------------------------------
+struct GradAcc {
+  double* gF;          // 3N x K: dF/df_k at each stage slot
+  double2* obD;        // K x MAXD^2: co-gradient of drive k's base operator
+  double2* obL;        // ne x MAXD^2
+  double2* obR;        // ne x MAXD^2
+  double* ebB;         // n1 x MAXD
+  double* ebL;         // ne x MAXD
+  double* ebR;         // ne x MAXD
+  double* jb;          // ne
+};
+
+struct XArgs {
+  KPlan p;
+  int K, nW, frame;
+  double t;            // stage time
+  int q;               // stage slot 3n + j
+  const double2* tabrow;      // FP64 row of this stage
+  const double* coef;         // K values at this stage
+  const double2* ph;          // sumd phases at this stage
+  const double2* opd;         // flat truncated operators
+  int opd_off[SG_MAXQ];
+  int eoff[SG_MAXQ];
+  const double* E;
+  int drv_of_slot_start[SG_MAXQ + 1];
+  int drv_list[SG_MAXDRIVE];
+  int drv_op[SG_MAXDRIVE];
+  int e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
+  double J[SG_MAXEDGE];
+  double2* partial;           // gridDim x nW x DL^2
+  unsigned* ticket;
+  GradAcc acc;
+};
+
+template <typename C, int DL>
+__device__ void block_reduce_store(C (&acc)[DL][DL], double2* out, double* red) {
+  // warp reduce each element, then combine warps in order through shared memory
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int x = 0; x < DL; ++x)
+    for (int y = 0; y < DL; ++y) {
+      double vr = acc[x][y].x, vi = acc[x][y].y;
+      for (int o = 16; o > 0; o >>= 1) {
+        vr += __shfl_xor_sync(0xffffffffu, vr, o);
+        vi += __shfl_xor_sync(0xffffffffu, vi, o);
+      }
+      if (lane == 0) { red[2 * (warp * DL * DL + x * DL + y)] = vr; red[2 * (warp * DL * DL + x * DL + y) + 1] = vi; }
+    }
+  __syncthreads();
+  for (int i = threadIdx.x; i < DL * DL; i += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int w = 0; w < nw; ++w) { sr += red[2 * (w * DL * DL + i)]; si += red[2 * (w * DL * DL + i) + 1]; }
+    out[i] = make_double2(sr, si);
+  }
+  __syncthreads();
+}
+
+// Cross-densities of one stage: for every term slot the d x d matrix
+//   C_ab = <kbar, (|a><b| on the slot's mode, other factor of the term applied) y>
+// summed over the slab.  The last block to finish sums the block partials in
+// block order and contracts them (W = -i C) into the co-gradient accumulators.
+template <typename R, int DL>
+__global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* __restrict__ X,
+                                              const typename CT<R>::T* __restrict__ Y) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  double* red = reinterpret_cast<double*>(smraw);                       // 2 * (kT/32) * DL^2
+  C* Mt = reinterpret_cast<C*>(red + 2 * (kT / 32) * DL * DL);           // stage row
+  const KPlan& p = a.p;
+  for (int i = threadIdx.x; i < p.row; i += blockDim.x) Mt[i] = to_c(a.tabrow[i], R(0));
+  __syncthreads();
+  const int S = p.S;
+  const long long gstride = (long long)gridDim.x * blockDim.x;
+  double2* mypart = a.partial + (size_t)blockIdx.x * a.nW * DL * DL;
+  int w = 0;
+  // ---- 1-body slots
+  for (int u = 0; u < p.n1; ++u, ++w) {
+    const int i = p.s1_mode[u], d = p.dims[i];
+    const long long st = p.st[i];
+    const long long nf = p.D / d * S;
+    C acc[DL][DL];
+#pragma unroll
+    for (int x = 0; x < DL; ++x)
+#pragma unroll
+      for (int y = 0; y < DL; ++y) acc[x][y] = cmk<C>(0.0, 0.0);
+    for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gstride) {
+      const long long tt = f / S;
+      const int s = (int)(f - tt * S);
+      const long long rlo = tt % st, rhi = tt / st;
+      const long long base = (rhi * d * st + rlo) * S + s;
+      C xv[DL], yv[DL];
+#pragma unroll
+      for (int x = 0; x < DL; ++x) {
+        xv[x] = x < d ? X[base + x * st * S] : cmk<C>(0.0, 0.0);
+        yv[x] = x < d ? Y[base + x * st * S] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int y = 0; y < DL; ++y) acc[x][y] = cjfma(xv[x], yv[y], acc[x][y]);
+    }
+    block_reduce_store<C, DL>(acc, mypart + (size_t)w * DL * DL, red);
+  }
+  // ---- 2-body slots: L side (fibres along mode a with R applied on mode b), then R side
+  for (int side = 0; side < 2; ++side) {
+    for (int q = 0; q < p.ne; ++q, ++w) {
+      const int i = side == 0 ? p.e_a[q] : p.e_b[q];      // fibre mode
+      const int j = side == 0 ? p.e_b[q] : p.e_a[q];      // mode of the other factor
+      const int d = p.dims[i], dj = p.dims[j];
+      const long long st = p.st[i], stj = p.st[j];
+      const C* O = Mt + (side == 0 ? p.e_offR[q] : p.e_offL[q]);
+      const long long nf = p.D / d * S;
+      C acc[DL][DL];
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int y = 0; y < DL; ++y) acc[x][y] = cmk<C>(0.0, 0.0);
+      for (long long f = (long long)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += gstride) {
+        const long long tt = f / S;
+        const int s = (int)(f - tt * S);
+        const long long rlo = tt % st, rhi = tt / st;
+        const long long r0 = rhi * d * st + rlo;           // row with digit i = 0
+        const int lj = (int)((r0 / stj) % dj);
+        const long long base = r0 * S + s;
+        const long long basej = (r0 - (long long)lj * stj) * S + s;
+        C xv[DL], yv[DL];
+#pragma unroll
+        for (int x = 0; x < DL; ++x) {
+          xv[x] = x < d ? X[base + x * st * S] : cmk<C>(0.0, 0.0);
+          C u = cmk<C>(0.0, 0.0);
+          if (x < d)
+            for (int c = 0; c < dj; ++c) u = cfma(O[lj * dj + c], Y[basej + x * st * S + c * stj * S], u);
+          yv[x] = u;
+        }
+#pragma unroll
+        for (int x = 0; x < DL; ++x)
+#pragma unroll
+          for (int y = 0; y < DL; ++y) acc[x][y] = cjfma(xv[x], yv[y], acc[x][y]);
+      }
+      block_reduce_store<C, DL>(acc, mypart + (size_t)w * DL * DL, red);
+    }
+  }
+  // ---- last block: fixed-order sum over blocks and contraction
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned tk = atomicAdd(a.ticket, 1u);
+    last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  double2* Wt = reinterpret_cast<double2*>(smraw);        // reuse: nW * DL^2 double2
+  for (int i = threadIdx.x; i < a.nW * DL * DL; i += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      double2 v = __ldcg(a.partial + (size_t)b * a.nW * DL * DL + i);
+      sr += v.x;
+      si += v.y;
+    }
+    Wt[i] = make_double2(si, -sr);                         // W = -i C
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *a.ticket = 0u;
+  const int slot = threadIdx.x;
+  if (slot >= a.nW) return;
+  const double t = a.t;
+  const bool inter = a.frame == SG_FRAME_INTERACTION;
+  const double2* W = Wt + slot * DL * DL;
+  if (slot < p.n1) {
+    const int u = slot, i = p.s1_mode[u], d = p.dims[i];
+    const double2* B = a.tabrow + p.s1_off[u];
+    for (int x = a.drv_of_slot_start[u]; x < a.drv_of_slot_start[u + 1]; ++x) {
+      const int k = a.drv_list[x];
+      const double2* O = a.opd + a.opd_off[i] + a.drv_op[k] * d * d;
+      const double fk = a.coef[k];
+      double g = 0.0;
+      for (int ia = 0; ia < d; ++ia)
+        for (int ib = 0; ib < d; ++ib) {
+          double2 P = cmul(a.ph[a.eoff[i] + ia], cconj(a.ph[a.eoff[i] + ib]));
+          double2 w = W[ia * DL + ib];
+          double2 Ot = cmul(O[ia * d + ib], P);
+          g += w.x * Ot.x - w.y * Ot.y;
+          double2 cw = cmul(cconj(w), cconj(P));
+          double2* ob = a.acc.obD + (size_t)k * SG_MAXD * SG_MAXD + ia * SG_MAXD + ib;
+          ob->x += fk * cw.x;
+          ob->y += fk * cw.y;
+        }
+      a.acc.gF[(size_t)a.q * a.K + k] += g;
+    }
+    double* eb = a.acc.ebB + u * SG_MAXD;
+    for (int ia = 0; ia < d; ++ia)
+      for (int ib = 0; ib < d; ++ib) {
+        double2 w = W[ia * DL + ib];
+        if (inter) {
+          double2 v = cmul(w, B[ia * d + ib]);
+          double qv = -v.y * t;                            // Re(v * i t)
+          eb[ia] += qv;
+          eb[ib] -= qv;
+        } else if (ia == ib) {
+          eb[ia] += w.x;
+        }
+      }
+    return;
+  }
+  const int side = (slot - p.n1) / p.ne, q = (slot - p.n1) % p.ne;
+  const int i = side == 0 ? p.e_a[q] : p.e_b[q];
+  const int op = side == 0 ? a.e_opa[q] : a.e_opb[q];
+  const int d = p.dims[i];
+  const double2* O = a.opd + a.opd_off[i] + op * d * d;
+  const double2* X2 = a.tabrow + (side == 0 ? p.e_offL[q] : p.e_offR[q]);
+  double2* ob = (side == 0 ? a.acc.obL : a.acc.obR) + (size_t)q * SG_MAXD * SG_MAXD;
+  double* eb = (side == 0 ? a.acc.ebL : a.acc.ebR) + q * SG_MAXD;
+  const double sc = side == 0 ? a.J[q] : 1.0;
+  double jg = 0.0;
+  for (int ia = 0; ia < d; ++ia)
+    for (int ib = 0; ib < d; ++ib) {
+      double2 P = cmul(a.ph[a.eoff[i] + ia], cconj(a.ph[a.eoff[i] + ib]));
+      double2 w = W[ia * DL + ib];
+      double2 At = cmul(O[ia * d + ib], P);
+      jg += w.x * At.x - w.y * At.y;
+      double2 cw = cmul(cconj(w), cconj(P));
+      ob[ia * SG_MAXD + ib].x += sc * cw.x;
+      ob[ia * SG_MAXD + ib].y += sc * cw.y;
+      if (inter) {
+        double2 v = cmul(w, X2[ia * d + ib]);
+        double qv = -v.y * t;
+        eb[ia] += qv;
+        eb[ib] -= qv;
+      }
+    }
+  if (side == 0) a.acc.jb[q] += jg;
+}
+
+// Pulse-parameter chain, one block per drive: dF/dparam = sum over stages of
+// dF/df * df/dparam, and the carrier-frequency co-gradient sum dF/df * E (-sin) t.
+__global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const double* gF,
+                              int K, int N, double dt, const int* pulse_off, double* grad_pulse,
+                              double* omega_bar) {
+  const int k = blockIdx.x;
+  const DriveDev dr = drives[k];
+  const int np = dr.kind == SG_ENV_PWC ? dr.nseg : 1;
+  extern __shared__ double part[];             // blockDim x (np + 1)
+  const int tid = threadIdx.x;
+  double* mine = part + tid * (np + 1);
+  for (int x = 0; x <= np; ++x) mine[x] = 0.0;
+  for (int q = tid; q < 3 * N; q += blockDim.x) {
+    const int n = q / 3, j = q % 3;
+    const double t = (double)(2 * n + j) * dt * 0.5;
+    const double g = gF[(size_t)q * K + k];
+    const double c = cos(dr.omega * t + dr.phase);
+    const double E = envelope_dev(dr, amps, n, j, t);
+    mine[np] += g * E * (-sin(dr.omega * t + dr.phase)) * t;
+    if (dr.kind == SG_ENV_GAUSSIAN) {
+      double x = t - dr.t0;
+      mine[0] += g * c * exp(-(x * x) / (2.0 * dr.sigma * dr.sigma));
+    } else if (dr.kind == SG_ENV_COSINE) {
+      if (2 * n + j <= dr.mp) mine[0] += g * c * 0.5 * (1.0 - cos(2.0 * M_PI * t / dr.length));
+    } else {
+      const int mid = 2 * n + 1;
+      if (mid < dr.mp) {
+        int seg = (int)(((long long)mid * dr.nseg) / dr.mp);
+        if (seg > dr.nseg - 1) seg = dr.nseg - 1;
+        mine[seg] += g * c;
+      }
+    }
+  }
+  __syncthreads();
+  for (int x = tid; x <= np; x += blockDim.x) {
+    double s = 0.0;
+    for (int y = 0; y < (int)blockDim.x; ++y) s += part[y * (np + 1) + x];
+    if (x < np) grad_pulse[pulse_off[k] + x] = s;
+    else omega_bar[k] = s;
+  }
+}
+
+struct AssembleArgs {
+  int nq, n1, ne, K;
+  int dims[SG_MAXQ];
+  int s1_of_mode[SG_MAXQ];
+  int drv_mode[SG_MAXDRIVE], drv_op[SG_MAXDRIVE], drv_omode[SG_MAXDRIVE];
+  int e_a[SG_MAXEDGE], e_b[SG_MAXEDGE], e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
+  GradAcc acc;
+  const double* omega_bar;
+  const double* ebar_frame;
+  double2* opbar;      // nq x 2 x MAXD^2
+  double* ebar;        // nq x MAXD
+};
+
+// Sums the per-term co-gradients into per-mode operator and energy co-gradients
+// in a fixed order.  One block, thread per (mode, level pair).
+__global__ void k_assemble(AssembleArgs a) {
+  for (int x = threadIdx.x; x < a.nq * SG_MAXD * SG_MAXD; x += blockDim.x) {
+    const int i = x / (SG_MAXD * SG_MAXD), ab = x % (SG_MAXD * SG_MAXD);
+    double2 o[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
+    for (int k = 0; k < a.K; ++k)
+      if (a.drv_mode[k] == i) {
+        double2 v = a.acc.obD[(size_t)k * SG_MAXD * SG_MAXD + ab];
+        o[a.drv_op[k]].x += v.x; o[a.drv_op[k]].y += v.y;
+      }
+    for (int e = 0; e < a.ne; ++e) {
+      if (a.e_a[e] == i) { double2 v = a.acc.obL[(size_t)e * SG_MAXD * SG_MAXD + ab]; o[a.e_opa[e]].x += v.x; o[a.e_opa[e]].y += v.y; }
+      if (a.e_b[e] == i) { double2 v = a.acc.obR[(size_t)e * SG_MAXD * SG_MAXD + ab]; o[a.e_opb[e]].x += v.x; o[a.e_opb[e]].y += v.y; }
+    }
+    a.opbar[(i * 2 + 0) * SG_MAXD * SG_MAXD + ab] = o[0];
+    a.opbar[(i * 2 + 1) * SG_MAXD * SG_MAXD + ab] = o[1];
+  }
+  for (int x = threadIdx.x; x < a.nq * SG_MAXD; x += blockDim.x) {
+    const int i = x / SG_MAXD, c = x % SG_MAXD;
+    double s = a.ebar_frame[x];
+    if (a.s1_of_mode[i] >= 0) s += a.acc.ebB[a.s1_of_mode[i] * SG_MAXD + c];
+    for (int e = 0; e < a.ne; ++e) {
+      if (a.e_a[e] == i) s += a.acc.ebL[e * SG_MAXD + c];
+      if (a.e_b[e] == i) s += a.acc.ebR[e * SG_MAXD + c];
+    }
+    if (c == 1)
+      for (int k = 0; k < a.K; ++k)
+        if (a.drv_omode[k] == i) s += a.omega_bar[k];
+    a.ebar[x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() { if (p) cudaFree(p); }
+};
+
+struct Arena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  ~Arena() { for (void* p : ptrs) cudaFree(p); }
+  template <typename T> T* get(size_t n) {
+    void* p = nullptr;
+    size_t b = std::max<size_t>(n * sizeof(T), 16);
+    if (cudaMalloc(&p, b) != cudaSuccess) return nullptr;
+    ptrs.push_back(p);
+    bytes += b;
+    return static_cast<T*>(p);
+  }
+};
+
+struct Setup {
+  KPlan p{};
+  TabArgs ta{};
+  int N = 0, K = 0, nq = 0, sumd = 0, Dc = 0;
+  long long D = 0;
+  int S = 0;
+  double dt = 0, T = 0;
+  std::vector<DriveDev> drives;
+  std::vector<double> amps;
+  std::vector<double> Eflat;
+  std::vector<double2> opdflat;
+  std::vector<int> s1_of_mode;
+  std::vector<int> pulse_off;
+  int n_pulse = 0;
+};
+
+sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
+  sg_ctx* ctx = sys->ctx;
+  if (!o) return sg_fail(ctx, SG_E_INVALID, "null options");
+  if (!(o->dt > 0.0) || !(o->T > 0.0) || !std::isfinite(o->T) || !std::isfinite(o->dt))
+    return sg_fail(ctx, SG_E_INVALID, "T and dt must be positive and finite");
+  double x = o->T / o->dt;
+  long long N = llround(x);
+  if (N < 1 || std::fabs(x - (double)N) > 1e-9 * std::max(1.0, x))
+    return sg_fail(ctx, SG_E_INVALID, "T/dt must be a whole number of steps");
+  if (N > (1ll << 26)) return sg_fail(ctx, SG_E_INVALID, "too many steps");
+  if (o->precision != SG_FP64 && o->precision != SG_MIXED)
+    return sg_fail(ctx, SG_E_INVALID, "precision must be SG_FP64 or SG_MIXED");
+  if (o->frame != SG_FRAME_INTERACTION && o->frame != SG_FRAME_LAB)
+    return sg_fail(ctx, SG_E_INVALID, "frame must be SG_FRAME_INTERACTION or SG_FRAME_LAB");
+  if (o->ncols < 1) return sg_fail(ctx, SG_E_INVALID, "ncols must be >= 1");
+  s.N = (int)N;
+  s.dt = o->dt;
+  s.T = (double)N * o->dt;
+  s.nq = (int)sys->modes.size();
+  s.S = o->ncols;
+  KPlan& p = s.p;
+  p.nq = s.nq;
+  p.S = s.S;
+  long long D = 1;
+  int dl = 0;
+  for (int i = 0; i < s.nq; ++i) { p.dims[i] = sys->modes[i].d; D *= p.dims[i]; dl = std::max(dl, p.dims[i]); }
+  p.D = D;
+  p.dl = dl;
+  s.D = D;
+  if (D * (long long)s.S > (1ll << 40)) return sg_fail(ctx, SG_E_INVALID, "slab too large");
+  long long st = 1;
+  for (int i = s.nq - 1; i >= 0; --i) { p.st[i] = st; st *= p.dims[i]; }
+  s.Dc = 1 << s.nq;
+  // energies and operators, flattened
+  s.sumd = 0;
+  int eoff[SG_MAXQ], ooff[SG_MAXQ];
+  s.Eflat.clear();
+  s.opdflat.clear();
+  for (int i = 0; i < s.nq; ++i) {
+    eoff[i] = s.sumd;
+    s.sumd += p.dims[i];
+    for (double e : sys->E_host[i]) s.Eflat.push_back(e);
+    ooff[i] = (int)s.opdflat.size();
+    const std::vector<double>& od = sys->opd_host[i];
+    for (size_t k = 0; k + 1 < od.size(); k += 2) s.opdflat.push_back(make_double2(od[k], od[k + 1]));
+  }
+  // drives
+  s.K = (int)sys->drives.size();
+  if (s.K > SG_MAXDRIVE) return sg_fail(ctx, SG_E_UNSUPPORTED, "too many drives");
+  s.drives.clear();
+  s.amps.clear();
+  s.pulse_off.clear();
+  s.n_pulse = 0;
+  for (const HostDrive& hd : sys->drives) {
+    DriveDev dd{};
+    dd.mode = hd.mode; dd.op = hd.op; dd.kind = hd.kind; dd.nseg = hd.nseg;
+    double xm = 2.0 * hd.length / o->dt;
+    long long mp = llround(xm);
+    if (hd.kind != SG_ENV_GAUSSIAN && (mp < 1 || std::fabs(xm - (double)mp) > 1e-9 * std::max(1.0, xm)))
+      return sg_fail(ctx, SG_E_INVALID, "pulse length must be a whole number of half steps");
+    dd.mp = (int)mp;
+    dd.amps_off = (int)s.amps.size();
+    for (double v : hd.amps) s.amps.push_back(v);
+    dd.amp = hd.amp; dd.sigma = hd.sigma; dd.t0 = hd.t0; dd.length = hd.length;
+    dd.phase = hd.phase;
+    dd.omega = hd.omega_mode >= 0 ? sys->E_host[hd.omega_mode][1] : hd.omega_d;
+    s.drives.push_back(dd);
+    s.pulse_off.push_back(s.n_pulse);
+    s.n_pulse += hd.kind == SG_ENV_PWC ? hd.nseg : 1;
+  }
+  // slots
+  TabArgs& ta = s.ta;
+  ta = TabArgs{};
+  int row = 0;
+  p.n1 = 0;
+  p.par1 = 0;
+  s.s1_of_mode.assign(s.nq, -1);
+  int ndl = 0;
+  for (int i = 0; i < s.nq; ++i) {
+    bool has = o->frame == SG_FRAME_LAB;
+    bool par = o->frame == SG_FRAME_INTERACTION;
+    for (const HostDrive& hd : sys->drives)
+      if (hd.mode == i) { has = true; if (!sys->parity_odd[2 * i + hd.op]) par = false; }
+    if (!has) continue;
+    const int u = p.n1++;
+    s.s1_of_mode[i] = u;
+    p.s1_mode[u] = i;
+    p.s1_off[u] = row;
+    row += p.dims[i] * p.dims[i];
+    if (par) p.par1 |= 1u << u;
+    ta.drv_of_slot_start[u] = ndl;
+    for (int k = 0; k < s.K; ++k)
+      if (sys->drives[k].mode == i) ta.drv_list[ndl++] = k;
+  }
+  ta.drv_of_slot_start[p.n1] = ndl;
+  p.ne = (int)sys->couplings.size();
+  if (p.ne > SG_MAXEDGE) return sg_fail(ctx, SG_E_UNSUPPORTED, "too many couplings");
+  p.parL = p.parR = 0;
+  for (int e = 0; e < p.ne; ++e) {
+    const HostCoupling& c = sys->couplings[e];
+    p.e_a[e] = c.a; p.e_b[e] = c.b;
+    p.e_offL[e] = row; row += p.dims[c.a] * p.dims[c.a];
+    p.e_offR[e] = row; row += p.dims[c.b] * p.dims[c.b];
+    if (sys->parity_odd[2 * c.a + c.op_a]) p.parL |= 1ull << e;
+    if (sys->parity_odd[2 * c.b + c.op_b]) p.parR |= 1ull << e;
+    ta.e_opa[e] = c.op_a; ta.e_opb[e] = c.op_b; ta.J[e] = c.J;
+  }
+  p.row = std::max(row, 1);
+  {
+    // stage rows and the cross-density scratch live in shared memory (<= 48 KB)
+    const size_t nW = (size_t)p.n1 + 2 * p.ne;
+    const size_t need = std::max<size_t>((size_t)p.row * sizeof(double2) + 2 * (256 / 32) * dl * dl * sizeof(double),
+                                         nW * dl * dl * sizeof(double2));
+    if (need > 48 * 1024) return sg_fail(ctx, SG_E_UNSUPPORTED, "too many terms for the stage kernels");
+  }
+  ta.p = p;
+  ta.nq = s.nq; ta.K = s.K; ta.N = s.N; ta.frame = o->frame;
+  for (int i = 0; i < s.nq; ++i) { ta.dims[i] = p.dims[i]; ta.eoff[i] = eoff[i]; ta.opd_off[i] = ooff[i]; }
+  ta.sumd = s.sumd;
+  ta.dt = o->dt;
+  return SG_OK;
+}
+
+int grid_for(long long n) {
+  long long g = (n + kT - 1) / kT;
+  return (int)std::max<long long>(1, std::min<long long>(g, 152ll * 16));
+}
+
+template <typename R>
+struct Bufs {
+  typedef typename CT<R>::T C;
+  C *X0 = nullptr, *X1 = nullptr, *Dacc = nullptr;
+};
+
+// Everything a solve needs on the device.
+struct Solve {
+  Setup s;
+  Arena ar;
+  DriveDev* drives_dev = nullptr;
+  double* amps_dev = nullptr;
+  double* E_dev = nullptr;
+  double2* opd_dev = nullptr;
+  double* coef = nullptr;
+  double2* ph = nullptr;
+  double2* tab = nullptr;
+  float2* tab32 = nullptr;
+  double2* psi = nullptr;
+  int launches = 0;
+};
+
+sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) {
+  sg_ctx* ctx = sys->ctx;
+  Setup& s = sv.s;
+  cudaStream_t st = ctx->stream;
+  sv.drives_dev = sv.ar.get<DriveDev>(std::max(1, s.K));
+  sv.amps_dev = sv.ar.get<double>(std::max<size_t>(1, s.amps.size()));
+  sv.E_dev = sv.ar.get<double>(s.sumd);
+  sv.opd_dev = sv.ar.get<double2>(s.opdflat.size());
+  const size_t nst = 3ull * s.N;
+  sv.coef = sv.ar.get<double>(nst * std::max(1, s.K));
+  sv.ph = sv.ar.get<double2>(nst * s.sumd);
+  sv.tab = sv.ar.get<double2>(nst * s.p.row);
+  if (o->precision == SG_MIXED) sv.tab32 = sv.ar.get<float2>(nst * s.p.row);
+  if (!sv.drives_dev || !sv.amps_dev || !sv.E_dev || !sv.opd_dev || !sv.coef || !sv.ph || !sv.tab ||
+      (o->precision == SG_MIXED && !sv.tab32))
+    return sg_fail(ctx, SG_E_NOMEM, "device allocation of the stage tables failed");
+  if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.drives_dev, s.drives.data(), s.K * sizeof(DriveDev), cudaMemcpyHostToDevice, st));
+  if (!s.amps.empty()) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.amps_dev, s.amps.data(), s.amps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.E_dev, s.Eflat.data(), s.sumd * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.opd_dev, s.opdflat.data(), s.opdflat.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+  TabArgs ta = s.ta;
+  ta.drives = sv.drives_dev;
+  ta.amps = sv.amps_dev;
+  ta.E = sv.E_dev;
+  ta.opd = sv.opd_dev;
+  ta.coef = sv.coef;
+  ta.ph = sv.ph;
+  ta.tab = sv.tab;
+  ta.tab32 = sv.tab32;
+  s.ta = ta;
+  k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
+  ++sv.launches;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  return SG_OK;
+}
+
+template <typename R, int STAGE, bool STORE>
+void launch_fwd(const Solve& sv, cudaStream_t st, const typename CT<R>::T* X, int n,
+                const double2* pin, double2* pout, typename CT<R>::T* Xn,
+                typename CT<R>::T* Dacc) {
+  typedef typename CT<R>::T C;
+  const Setup& s = sv.s;
+  const int j = STAGE == 0 ? 0 : (STAGE == 3 ? 2 : 1);
+  const size_t q = 3ull * n + j;
+  const C* row;
+  if (sizeof(R) == 4) row = reinterpret_cast<const C*>(sv.tab32 + q * s.p.row);
+  else row = reinterpret_cast<const C*>(sv.tab + q * s.p.row);
+  k_fwd<R, STAGE, STORE><<<grid_for(s.D * s.S), kT, s.p.row * sizeof(C), st>>>(
+      s.p, X, row, pin, pout, Xn, Dacc, s.dt);
+}
+
+template <typename R, int STAGE>
+void launch_adj(const Solve& sv, cudaStream_t st, const typename CT<R>::T* X, int n,
+                double2* pbar, typename CT<R>::T* Xn, typename CT<R>::T* Db) {
+  typedef typename CT<R>::T C;
+  const Setup& s = sv.s;
+  const int j = STAGE == 0 ? 0 : (STAGE == 3 ? 2 : 1);
+  const size_t q = 3ull * n + j;
+  const C* row;
+  if (sizeof(R) == 4) row = reinterpret_cast<const C*>(sv.tab32 + q * s.p.row);
+  else row = reinterpret_cast<const C*>(sv.tab + q * s.p.row);
+  k_adj<R, STAGE><<<grid_for(s.D * s.S), kT, s.p.row * sizeof(C), st>>>(s.p, X, row, pbar, Xn, Db, s.dt);
+}
+
+// One forward RK4 step from pin to pout (may alias).  X holds (R)psi on entry and on exit.
+template <typename R>
+void fwd_step(Solve& sv, cudaStream_t st, int n, const double2* pin, double2* pout,
+              typename CT<R>::T*& X, typename CT<R>::T*& Xo, typename CT<R>::T* Dacc) {
+  launch_fwd<R, 0, false>(sv, st, X, n, pin, nullptr, Xo, Dacc); std::swap(X, Xo);
+  launch_fwd<R, 1, false>(sv, st, X, n, pin, nullptr, Xo, Dacc); std::swap(X, Xo);
+  launch_fwd<R, 2, false>(sv, st, X, n, pin, nullptr, Xo, Dacc); std::swap(X, Xo);
+  launch_fwd<R, 3, false>(sv, st, X, n, pin, pout, Xo, Dacc); std::swap(X, Xo);
+  sv.launches += 4;
+}
+
+template <typename R>
+sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool init_from_psi,
+                      int ckpt_every, std::vector<double2*>* ckpts) {
+  typedef typename CT<R>::T C;
+  sg_ctx* ctx = sys->ctx;
+  cudaStream_t st = ctx->stream;
+  Setup& s = sv.s;
+  const long long n = s.D * s.S;
+  if (!init_from_psi) {
+    k_init_cols<<<grid_for(n), kT, 0, st>>>(sv.psi, s.D, s.S, cols_dev);
+    ++sv.launches;
+  }
+  // fast on-chip path when the whole column block fits in shared memory
+  if (!ckpts && fast_onchip_available(s.p, sizeof(R) == 4)) {
+    sg_status rc = fast_onchip_forward(sys, s.p, sizeof(R) == 4, sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab,
+                                       sv.psi, s.N, s.dt, st, &sv.launches);
+    if (rc != SG_OK) return rc;
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    return SG_OK;
+  }
+  C* X = sv.ar.get<C>(n);
+  C* Xo = sv.ar.get<C>(n);
+  C* Dacc = sv.ar.get<C>(n);
+  if (!X || !Xo || !Dacc) return sg_fail(ctx, SG_E_NOMEM, "device allocation of stage buffers failed");
+  k_cast<R><<<grid_for(n), kT, 0, st>>>(sv.psi, X, n, 1.0);
+  ++sv.launches;
+  for (int step = 0; step < s.N; ++step) {
+    if (ckpts && step % ckpt_every == 0)
+      SG_CUDA_TRY(ctx, cudaMemcpyAsync((*ckpts)[step / ckpt_every], sv.psi, n * sizeof(double2),
+                                       cudaMemcpyDeviceToDevice, st));
+    fwd_step<R>(sv, st, step, sv.psi, sv.psi, X, Xo, Dacc);
+  }
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  return SG_OK;
+}
+
+FrameArgs frame_args(const Setup& s, const double* E_dev, double sign) {
+  FrameArgs f{};
+  f.nq = s.nq; f.S = s.S; f.D = s.D;
+  for (int i = 0; i < s.nq; ++i) { f.dims[i] = s.p.dims[i]; f.st[i] = s.p.st[i]; f.eoff[i] = s.ta.eoff[i]; }
+  f.E = E_dev;
+  f.T = s.T;
+  f.sign = sign;
+  return f;
+}
+
+CompArgs comp_args(const Setup& s) {
+  CompArgs c{};
+  c.nq = s.nq; c.S = s.S; c.Dc = s.Dc;
+  for (int i = 0; i < s.nq; ++i) c.dims[i] = s.p.dims[i];
+  return c;
+}
+
+template <typename R>
+sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, int K,
+                       double2* pbar, GradAcc acc) {
+  typedef typename CT<R>::T C;
+  sg_ctx* ctx = sys->ctx;
+  cudaStream_t st = ctx->stream;
+  Setup& s = sv.s;
+  const long long n = s.D * s.S;
+  C* X = sv.ar.get<C>(n);
+  C* Xo = sv.ar.get<C>(n);
+  C* Dacc = sv.ar.get<C>(n);
+  C* Y[4];
+  for (int i = 0; i < 4; ++i) Y[i] = sv.ar.get<C>(n);
+  C* KB = sv.ar.get<C>(n);
+  C* KB2 = sv.ar.get<C>(n);
+  C* Db = sv.ar.get<C>(n);
+  std::vector<double2*> seg(K + 1);
+  for (int i = 0; i <= K; ++i) seg[i] = sv.ar.get<double2>(n);
+  const int nW = s.p.n1 + 2 * s.p.ne;
+  const int DL = s.p.dl;
+  const int xgrid = (int)std::max<long long>(1, std::min<long long>((n / 2 + kT - 1) / kT, 152ll * 2));
+  double2* partial = sv.ar.get<double2>((size_t)xgrid * std::max(1, nW) * DL * DL);
+  unsigned* ticket = sv.ar.get<unsigned>(1);
+  for (C* c : {X, Xo, Dacc, Y[0], Y[1], Y[2], Y[3], KB, KB2, Db})
+    if (!c) return sg_fail(ctx, SG_E_NOMEM, "device allocation of adjoint buffers failed");
+  for (double2* c : seg) if (!c) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the segment buffer failed");
+  if (!partial || !ticket) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+  XArgs xa{};
+  xa.p = s.p;
+  xa.K = s.K;
+  xa.nW = nW;
+  xa.frame = s.ta.frame;
+  xa.opd = sv.opd_dev;
+  for (int i = 0; i < s.nq; ++i) { xa.opd_off[i] = s.ta.opd_off[i]; xa.eoff[i] = s.ta.eoff[i]; }
+  xa.E = sv.E_dev;
+  for (int i = 0; i <= s.p.n1; ++i) xa.drv_of_slot_start[i] = s.ta.drv_of_slot_start[i];
+  for (int i = 0; i < SG_MAXDRIVE; ++i) xa.drv_list[i] = s.ta.drv_list[i];
+  for (int k = 0; k < s.K; ++k) xa.drv_op[k] = s.drives[k].op;
+  for (int e = 0; e < s.p.ne; ++e) { xa.e_opa[e] = s.ta.e_opa[e]; xa.e_opb[e] = s.ta.e_opb[e]; xa.J[e] = s.ta.J[e]; }
+  xa.partial = partial;
+  xa.ticket = ticket;
+  xa.acc = acc;
+  const size_t xsm = std::max<size_t>(2 * (kT / 32) * DL * DL * sizeof(double) + s.p.row * sizeof(C),
+                                      (size_t)std::max(1, nW) * DL * DL * sizeof(double2));
+  auto xdens = [&](const C* Xk, const C* Yk, int step, int j) {
+    xa.q = 3 * step + j;
+    xa.t = (double)(2 * step + j) * s.dt * 0.5;
+    xa.tabrow = sv.tab + (size_t)xa.q * s.p.row;
+    xa.coef = sv.coef + (size_t)xa.q * s.K;
+    xa.ph = sv.ph + (size_t)xa.q * s.sumd;
+    switch (DL) {
+      case 2: k_xdens<R, 2><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+      case 3: k_xdens<R, 3><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+      case 4: k_xdens<R, 4><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+      case 5: k_xdens<R, 5><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+      case 6: k_xdens<R, 6><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+      case 7: k_xdens<R, 7><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+      default: k_xdens<R, 8><<<xgrid, kT, xsm, st>>>(xa, Xk, Yk); break;
+    }
+    ++sv.launches;
+  };
+  // kbar_4 of the last step = dt/6 psibar_N
+  k_cast<R><<<grid_for(n), kT, 0, st>>>(pbar, KB, n, s.dt / 6.0);
+  ++sv.launches;
+  const int nseg = (int)ckpts.size();
+  for (int c = nseg - 1; c >= 0; --c) {
+    const int n0 = c * K, n1 = std::min(s.N, n0 + K);
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(seg[0], ckpts[c], n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    k_cast<R><<<grid_for(n), kT, 0, st>>>(seg[0], X, n, 1.0);
+    ++sv.launches;
+    for (int step = n0; step < n1 - 1; ++step)
+      fwd_step<R>(sv, st, step, seg[step - n0], seg[step - n0 + 1], X, Xo, Dacc);
+    for (int step = n1 - 1; step >= n0; --step) {
+      const double2* ps = seg[step - n0];
+      k_cast<R><<<grid_for(n), kT, 0, st>>>(ps, Y[0], n, 1.0);
+      launch_fwd<R, 0, true>(sv, st, Y[0], step, ps, nullptr, Y[1], nullptr);
+      launch_fwd<R, 1, true>(sv, st, Y[1], step, ps, nullptr, Y[2], nullptr);
+      launch_fwd<R, 2, true>(sv, st, Y[2], step, ps, nullptr, Y[3], nullptr);
+      sv.launches += 4;
+      xdens(KB, Y[3], step, 2);
+      launch_adj<R, 3>(sv, st, KB, step, pbar, KB2, Db);
+      xdens(KB2, Y[2], step, 1);
+      launch_adj<R, 2>(sv, st, KB2, step, pbar, KB, Db);
+      xdens(KB, Y[1], step, 1);
+      launch_adj<R, 1>(sv, st, KB, step, pbar, KB2, Db);
+      xdens(KB2, Y[0], step, 0);
+      launch_adj<R, 0>(sv, st, KB2, step, pbar, KB, Db);
+      sv.launches += 4;
+    }
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  return SG_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// entry points used by the C ABI
+// ---------------------------------------------------------------------------
+sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev) {
+  sg_ctx* ctx = sys->ctx;
+  if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
+  if (!psi_dev) return sg_fail(ctx, SG_E_INVALID, "psi_dev is NULL");
+  Solve sv;
+  sg_status rc = build_setup(sys, o, sv.s);
+  if (rc != SG_OK) return rc;
+  SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  Setup& s = sv.s;
+  long long* cols_dev = nullptr;
+  if (o->col_index) {
+    for (int c = 0; c < s.S; ++c)
+      if (o->col_index[c] < 0 || o->col_index[c] >= s.D) return sg_fail(ctx, SG_E_INVALID, "col_index out of range");
+    cols_dev = sv.ar.get<long long>(s.S);
+    if (!cols_dev) return sg_fail(ctx, SG_E_NOMEM, "allocation failed");
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols_dev, o->col_index, s.S * sizeof(long long), cudaMemcpyHostToDevice, st));
+  }
+  rc = upload_and_tables(sys, o, sv);
+  if (rc != SG_OK) return rc;
+  sv.psi = static_cast<double2*>(psi_dev);
+  rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, !o->col_index, 0, nullptr)
+                                : run_forward<double>(sys, sv, cols_dev, !o->col_index, 0, nullptr);
+  if (rc != SG_OK) return rc;
+  if (o->frame == SG_FRAME_INTERACTION) {
+    k_frame<<<grid_for(s.D * s.S), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+  }
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return SG_OK;
+}
+
+sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, int kind,
+                           double* F_out, double* Ucomp_out, bool grad, double* grad_pulse,
+                           double* grad_ham, int ckpt) {
+  sg_ctx* ctx = sys->ctx;
+  if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
+  if (!target) return sg_fail(ctx, SG_E_INVALID, "target is NULL");
+  if (!o || !o->col_index) return sg_fail(ctx, SG_E_INVALID, "fidelity needs opts->col_index");
+  if (kind != SG_FID_AVG && kind != SG_FID_STATE) return sg_fail(ctx, SG_E_INVALID, "bad fidelity kind");
+  Solve sv;
+  sg_status rc = build_setup(sys, o, sv.s);
+  if (rc != SG_OK) return rc;
+  Setup& s = sv.s;
+  if (s.nq > 12) return sg_fail(ctx, SG_E_UNSUPPORTED, "fidelity supports at most 12 modes");
+  for (int i = 0; i < s.nq; ++i)
+    if (s.p.dims[i] < 2) return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per mode");
+  SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  // comp labels of the columns
+  std::vector<int> lab(s.S, -1);
+  std::vector<int> seen(s.Dc, 0);
+  int Sc = 0;
+  for (int c = 0; c < s.S; ++c) {
+    long long r = o->col_index[c];
+    if (r < 0 || r >= s.D) return sg_fail(ctx, SG_E_INVALID, "col_index out of range");
+    int j = 0;
+    bool comp = true;
+    for (int i = 0; i < s.nq; ++i) {
+      int l = (int)((r / s.p.st[i]) % s.p.dims[i]);
+      if (l > 1) { comp = false; break; }
+      j = (j << 1) | l;
+    }
+    if (comp) { lab[c] = j; ++Sc; ++seen[j]; }
+  }
+  if (Sc == 0) return sg_fail(ctx, SG_E_INVALID, "no evolved column is a computational state");
+  bool full = true;
+  for (int j = 0; j < s.Dc; ++j) if (seen[j] != 1) full = false;
+  if (full && s.Dc > 256) full = false;
+  if (grad && kind == SG_FID_AVG && !full)
+    return sg_fail(ctx, SG_E_INVALID, "F_avg needs every computational state evolved exactly once (Dc <= 256)");
+  auto t0 = std::chrono::steady_clock::now();
+  long long* cols_dev = sv.ar.get<long long>(s.S);
+  int* lab_dev = sv.ar.get<int>(s.S);
+  double2* Tg = sv.ar.get<double2>((size_t)s.Dc * s.Dc);
+  double2* Uc = sv.ar.get<double2>((size_t)s.Dc * s.S);
+  double2* barc = sv.ar.get<double2>((size_t)s.Dc * s.S);
+  double2* Mbuf = sv.ar.get<double2>(full ? (size_t)s.Dc * s.Dc : 1);
+  double* Fd = sv.ar.get<double>(2);
+  const long long n = s.D * s.S;
+  sv.psi = sv.ar.get<double2>(n);
+  if (!cols_dev || !lab_dev || !Tg || !Uc || !barc || !Mbuf || !Fd || !sv.psi)
+    return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols_dev, o->col_index, s.S * sizeof(long long), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(lab_dev, lab.data(), s.S * sizeof(int), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(Tg, target, (size_t)s.Dc * s.Dc * sizeof(double2), cudaMemcpyHostToDevice, st));
+  rc = upload_and_tables(sys, o, sv);
+  if (rc != SG_OK) return rc;
+  // checkpoints
+  int K = 0;
+  std::vector<double2*> ckpts;
+  if (grad) {
+    K = ckpt > 0 ? ckpt : std::max(1, (int)std::lround(std::sqrt((double)s.N)));
+    K = std::min(K, s.N);
+    const int nck = (s.N + K - 1) / K;
+    for (int c = 0; c < nck; ++c) {
+      double2* p = sv.ar.get<double2>(n);
+      if (!p) return sg_fail(ctx, SG_E_NOMEM, "device allocation of checkpoints failed");
+      ckpts.push_back(p);
+    }
+  }
+  cudaEvent_t ev0, ev1, ev2;
+  cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&ev2);
+  cudaEventRecord(ev0, st);
+  rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr)
+                                : run_forward<double>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr);
+  if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
+  if (o->frame == SG_FRAME_INTERACTION)
+    k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
+  CompArgs ca = comp_args(s);
+  k_gather_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, sv.psi, Uc);
+  FidArgs fa{};
+  fa.S = s.S; fa.Dc = s.Dc; fa.Sc = Sc; fa.full = full ? 1 : 0; fa.kind = kind; fa.nq = s.nq;
+  fa.Uc = Uc; fa.Tg = Tg; fa.lab = lab_dev; fa.F = Fd; fa.bar = grad ? barc : nullptr; fa.M = Mbuf;
+  fa.T = s.T;
+  fa.frame = o->frame;
+  k_fidelity<<<1, kT, 0, st>>>(fa);
+  sv.launches += 3;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  cudaEventRecord(ev1, st);
+  double Fh[2];
+  size_t peak = sv.ar.bytes;
+  if (grad) {
+    // accumulators
+    const int ne = s.p.ne, n1 = s.p.n1;
+    const size_t MD2 = SG_MAXD * SG_MAXD;
+    GradAcc acc{};
+    acc.gF = sv.ar.get<double>(3ull * s.N * std::max(1, s.K));
+    acc.obD = sv.ar.get<double2>(std::max(1, s.K) * MD2);
+    acc.obL = sv.ar.get<double2>(std::max(1, ne) * MD2);
+    acc.obR = sv.ar.get<double2>(std::max(1, ne) * MD2);
+    acc.ebB = sv.ar.get<double>(std::max(1, n1) * SG_MAXD);
+    acc.ebL = sv.ar.get<double>(std::max(1, ne) * SG_MAXD);
+    acc.ebR = sv.ar.get<double>(std::max(1, ne) * SG_MAXD);
+    acc.jb = sv.ar.get<double>(std::max(1, ne));
+    double* ebar_frame = sv.ar.get<double>(s.nq * SG_MAXD);
+    double* omega_bar = sv.ar.get<double>(std::max(1, s.K));
+    double2* opbar = sv.ar.get<double2>(s.nq * 2 * MD2);
+    double* ebar = sv.ar.get<double>(s.nq * SG_MAXD);
+    double* gpulse = sv.ar.get<double>(std::max(1, s.n_pulse));
+    double* gdev = sv.ar.get<double>(3 * s.nq);
+    int* poff = sv.ar.get<int>(std::max(1, s.K));
+    double2* pbar = sv.ar.get<double2>(n);
+    if (!acc.gF || !acc.obD || !acc.obL || !acc.obR || !acc.ebB || !acc.ebL || !acc.ebR || !acc.jb ||
+        !ebar_frame || !omega_bar || !opbar || !ebar || !gpulse || !gdev || !poff || !pbar)
+      return sg_fail(ctx, SG_E_NOMEM, "device allocation of gradient accumulators failed");
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.gF, 0, 3ull * s.N * std::max(1, s.K) * sizeof(double), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.obD, 0, std::max(1, s.K) * MD2 * sizeof(double2), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.obL, 0, std::max(1, ne) * MD2 * sizeof(double2), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.obR, 0, std::max(1, ne) * MD2 * sizeof(double2), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.ebB, 0, std::max(1, n1) * SG_MAXD * sizeof(double), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.ebL, 0, std::max(1, ne) * SG_MAXD * sizeof(double), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.ebR, 0, std::max(1, ne) * SG_MAXD * sizeof(double), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.jb, 0, std::max(1, ne) * sizeof(double), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(ebar_frame, 0, s.nq * SG_MAXD * sizeof(double), st));
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(pbar, 0, n * sizeof(double2), st));
+    if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(poff, s.pulse_off.data(), s.K * sizeof(int), cudaMemcpyHostToDevice, st));
+    // co-state of the lab-frame columns, its frame-phase energy term, pull back to the frame
+    k_scatter_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, barc, pbar);
+    if (o->frame == SG_FRAME_INTERACTION) {
+      fa.ebar_frame = ebar_frame;
+      k_frame_ebar<<<1, kT, 0, st>>>(fa);
+      k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, +1.0), pbar);
+    }
+    sv.launches += 3;
+    rc = o->precision == SG_MIXED ? run_backward<float>(sys, sv, ckpts, K, pbar, acc)
+                                  : run_backward<double>(sys, sv, ckpts, K, pbar, acc);
+    if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
+    // chains
+    if (s.K) {
+      int np_max = 1;
+      for (auto& d : s.drives) np_max = std::max(np_max, d.kind == SG_ENV_PWC ? d.nseg : 1);
+      const int pt = 64;
+      k_pulse_chain<<<s.K, pt, pt * (np_max + 1) * sizeof(double), st>>>(
+          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, gpulse, omega_bar);
+    } else {
+      SG_CUDA_TRY(ctx, cudaMemsetAsync(omega_bar, 0, sizeof(double), st));
+    }
+    AssembleArgs aa{};
+    aa.nq = s.nq; aa.n1 = n1; aa.ne = ne; aa.K = s.K;
+    for (int i = 0; i < s.nq; ++i) { aa.dims[i] = s.p.dims[i]; aa.s1_of_mode[i] = s.s1_of_mode[i]; }
+    for (int k = 0; k < s.K; ++k) {
+      aa.drv_mode[k] = sys->drives[k].mode; aa.drv_op[k] = sys->drives[k].op;
+      aa.drv_omode[k] = sys->drives[k].omega_mode;
+    }
+    for (int e = 0; e < ne; ++e) {
+      aa.e_a[e] = s.p.e_a[e]; aa.e_b[e] = s.p.e_b[e]; aa.e_opa[e] = s.ta.e_opa[e]; aa.e_opb[e] = s.ta.e_opb[e];
+    }
+    aa.acc = acc; aa.omega_bar = omega_bar; aa.ebar_frame = ebar_frame; aa.opbar = opbar; aa.ebar = ebar;
+    k_assemble<<<1, kT, 0, st>>>(aa);
+    sv.launches += 2;
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    rc = sg_chain_device_params(sys, opbar, ebar, gdev);
+    if (rc != SG_OK) return rc;
+    ++sv.launches;
+    cudaEventRecord(ev2, st);
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    std::vector<double> gd(3 * s.nq), jb(std::max(1, ne));
+    if (s.n_pulse && grad_pulse)
+      SG_CUDA_TRY(ctx, cudaMemcpyAsync(grad_pulse, gpulse, s.n_pulse * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(gd.data(), gdev, 3 * s.nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(jb.data(), acc.jb, std::max(1, ne) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (grad_ham) {
+      for (int i = 0; i < s.nq; ++i) {
+        grad_ham[3 * i + 0] = gd[3 * i + 0];
+        grad_ham[3 * i + 1] = gd[3 * i + 1];
+        grad_ham[3 * i + 2] = sys->modes[i].kind == 0 ? 0.0 : gd[3 * i + 2];
+      }
+      for (int e = 0; e < ne; ++e) grad_ham[3 * s.nq + e] = jb[e];
+    }
+    peak = sv.ar.bytes;
+  } else {
+    cudaEventRecord(ev2, st);
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
+  if (Ucomp_out)
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(Ucomp_out, Uc, (size_t)s.Dc * s.S * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  float fwd_ms = 0.f, bwd_ms = 0.f;
+  cudaEventElapsedTime(&fwd_ms, ev0, ev1);
+  cudaEventElapsedTime(&bwd_ms, ev1, ev2);
+  cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2);
+  (void)t0;
+  if (F_out) { F_out[0] = Fh[0]; F_out[1] = Fh[1]; }
+  sys->last_stats[0] = fwd_ms;
+  sys->last_stats[1] = bwd_ms;
+  sys->last_stats[2] = (double)peak;
+  sys->last_stats[3] = K;
+  sys->last_stats[4] = sv.launches;
+  return SG_OK;
+}

@@ -1,0 +1,297 @@
+// Serving: continuous batching of fidelity(+gradient) solves on one GPU.
+//
+// Requests are admitted in arrival order while a slot is free and the device
+// memory they need fits the budget.  Each slot owns a CUDA stream, so the kernels
+// of all admitted requests overlap on the device; a request that arrives while
+// others run starts as soon as a slot and memory free up, without waiting for the
+// running ones to finish.  Results are bitwise independent of what else runs: every
+// solve uses only its own buffers and fixed-order reductions.
+#include "sg_internal.h"
+#include <algorithm>
+#include <cmath>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <thread>
+
+namespace {
+
+double now_s(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+struct Req {
+  uint64_t ticket = 0;
+  sg_system* sys = nullptr;
+  sg_evolve_opts opts{};
+  std::vector<long long> cols;
+  std::vector<double> target;
+  int kind = SG_FID_AVG;
+  int want_grad = 1;
+  size_t mem = 0;
+  int state = 0;                 // 0 queued, 1 running, 2 done, 3 cancelled
+  sg_status status = SG_OK;
+  double F[2] = {0, 0};
+  std::vector<double> gp, gh;
+  double submit_s = 0, start_s = 0, done_s = 0;
+};
+
+size_t estimate_bytes(const sg_system* sys, const sg_evolve_opts& o, int want_grad) {
+  long long D = 1;
+  for (const HostMode& m : sys->modes) D *= m.d;
+  const double N = o.T / o.dt;
+  size_t row = 0;
+  for (const HostMode& m : sys->modes) row += (size_t)m.d * m.d;
+  row += 2 * sys->couplings.size() * (size_t)SG_MAXD * SG_MAXD;
+  const size_t slab = (size_t)D * o.ncols * sizeof(double2);
+  size_t b = (size_t)(3.0 * N) * row * (sizeof(double2) + sizeof(float2)) + 8 * slab + (1u << 20);
+  if (want_grad) {
+    const size_t K = std::max<size_t>(1, (size_t)std::lround(std::sqrt(N)));
+    b += (size_t)(N / K + 2) * slab + (K + 1) * slab + 10 * slab;
+    b += (size_t)(3.0 * N) * sizeof(double) * std::max<size_t>(1, sys->drives.size());
+  }
+  return b;
+}
+
+}  // namespace
+
+struct sg_server {
+  sg_ctx* ctx = nullptr;
+  size_t budget = 0;
+  int max_slots = 1;
+  std::chrono::steady_clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv, done_cv;
+  std::deque<Req*> queue;
+  std::map<uint64_t, std::unique_ptr<Req>> reqs;
+  uint64_t next_ticket = 1;
+  size_t mem_in_use = 0;
+  int active = 0;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<sg_ctx*> wctx;
+  uint64_t submitted = 0, completed = 0, cancelled = 0, rejected = 0;
+  std::vector<double> latencies;
+  double first_start = -1, last_done = 0;
+  double busy_accum = 0, busy_since = -1;
+
+  void worker(int w) {
+    sg_ctx* c = wctx[w];
+    for (;;) {
+      Req* r = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] {
+          if (stop) return true;
+          return !queue.empty() && mem_in_use + queue.front()->mem <= budget;
+        });
+        if (stop) return;
+        r = queue.front();
+        queue.pop_front();
+        r->state = 1;
+        mem_in_use += r->mem;
+        if (active == 0) busy_since = now_s(t0);
+        ++active;
+        r->start_s = now_s(t0);
+        if (first_start < 0) first_start = r->start_s;
+      }
+      // run the solve on this worker's stream
+      sg_ctx* saved = r->sys->ctx;
+      r->sys->ctx = c;
+      sg_status rc = SG_OK;
+      if (!r->sys->prepared) rc = sg_prepare_impl(r->sys);
+      int np = 0, nh = 0;
+      sg_param_counts(r->sys, &np, &nh);
+      r->gp.assign(std::max(1, np), 0.0);
+      r->gh.assign(std::max(1, nh), 0.0);
+      if (rc == SG_OK)
+        rc = sg_fidelity_impl(r->sys, &r->opts, r->target.data(), r->kind, r->F, nullptr,
+                              r->want_grad != 0, r->gp.data(), r->gh.data(), 0);
+      r->sys->ctx = saved;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        r->status = rc;
+        r->done_s = now_s(t0);
+        r->state = 2;
+        mem_in_use -= r->mem;
+        --active;
+        if (active == 0 && busy_since >= 0) { busy_accum += r->done_s - busy_since; busy_since = -1; }
+        ++completed;
+        latencies.push_back(r->done_s - r->submit_s);
+        last_done = r->done_s;
+      }
+      cv.notify_all();
+      done_cv.notify_all();
+    }
+  }
+};
+
+extern "C" {
+
+sg_status sg_server_create(sg_ctx* ctx, size_t mem_budget_bytes, int max_slots, sg_server** out) {
+  if (!ctx || !out) return SG_E_INVALID;
+  if (max_slots < 1 || max_slots > 64) return sg_fail(ctx, SG_E_INVALID, "max_slots must be 1..64");
+  if (mem_budget_bytes == 0) return sg_fail(ctx, SG_E_INVALID, "memory budget must be > 0");
+  sg_server* s = new sg_server();
+  s->ctx = ctx;
+  s->budget = mem_budget_bytes;
+  s->max_slots = max_slots;
+  s->t0 = std::chrono::steady_clock::now();
+  cudaSetDevice(ctx->device);
+  for (int w = 0; w < max_slots; ++w) {
+    sg_ctx* c = new sg_ctx();
+    c->device = ctx->device;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      for (sg_ctx* x : s->wctx) { cudaStreamDestroy(x->stream); delete x; }
+      delete s;
+      return sg_fail(ctx, SG_E_CUDA, "cudaStreamCreate failed");
+    }
+    s->wctx.push_back(c);
+  }
+  for (int w = 0; w < max_slots; ++w)
+    s->workers.emplace_back([s, w] { cudaSetDevice(s->wctx[w]->device); s->worker(w); });
+  *out = s;
+  return SG_OK;
+}
+
+sg_status sg_server_destroy(sg_server* srv) {
+  if (!srv) return SG_OK;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv.notify_all();
+  for (auto& t : srv->workers) t.join();
+  for (sg_ctx* c : srv->wctx) { cudaStreamSynchronize(c->stream); cudaStreamDestroy(c->stream); delete c; }
+  delete srv;
+  return SG_OK;
+}
+
+sg_status sg_server_submit(sg_server* srv, const sg_request* req, uint64_t* ticket) {
+  if (!srv || !req || !ticket) return SG_E_INVALID;
+  if (!req->sys || !req->target_re_im) return sg_fail(srv->ctx, SG_E_INVALID, "request needs a system and a target");
+  auto r = std::make_unique<Req>();
+  r->sys = req->sys;
+  r->opts = req->opts;
+  r->kind = req->kind;
+  r->want_grad = req->want_grad;
+  const int nq = (int)req->sys->modes.size();
+  if (nq < 1 || nq > 12) return sg_fail(srv->ctx, SG_E_INVALID, "request system needs 1..12 modes");
+  std::vector<int> dims;
+  for (const HostMode& m : req->sys->modes) dims.push_back(m.d);
+  if (req->opts.col_index) {
+    r->cols.assign(req->opts.col_index, req->opts.col_index + req->opts.ncols);
+  } else {
+    for (int j = 0; j < (1 << nq); ++j) {
+      long long row = 0;
+      for (int i = 0; i < nq; ++i) row = row * dims[i] + ((j >> (nq - 1 - i)) & 1);
+      r->cols.push_back(row);
+    }
+    r->opts.ncols = (int)r->cols.size();
+  }
+  r->opts.col_index = r->cols.data();
+  const size_t dc = (size_t)1 << nq;
+  r->target.assign(req->target_re_im, req->target_re_im + 2 * dc * dc);
+  r->mem = estimate_bytes(req->sys, r->opts, req->want_grad);
+  std::lock_guard<std::mutex> lk(srv->mu);
+  ++srv->submitted;
+  if (r->mem > srv->budget) {
+    ++srv->rejected;
+    return sg_fail(srv->ctx, SG_E_NOMEM_RETRY, "request alone exceeds the memory budget");
+  }
+  r->ticket = srv->next_ticket++;
+  r->submit_s = now_s(srv->t0);
+  *ticket = r->ticket;
+  srv->queue.push_back(r.get());
+  srv->reqs[r->ticket] = std::move(r);
+  srv->cv.notify_all();
+  return SG_OK;
+}
+
+static sg_status fill_result(Req* r, sg_result* out) {
+  if (!out) return SG_OK;
+  out->status = r->status;
+  out->F[0] = r->F[0];
+  out->F[1] = r->F[1];
+  out->grad_pulse = r->gp.data();
+  out->grad_ham = r->gh.data();
+  int np = 0, nh = 0;
+  sg_param_counts(r->sys, &np, &nh);
+  out->n_pulse = np;
+  out->n_ham = nh;
+  out->submit_s = r->submit_s;
+  out->start_s = r->start_s;
+  out->done_s = r->done_s;
+  return SG_OK;
+}
+
+sg_status sg_server_poll(sg_server* srv, uint64_t ticket, sg_result* out) {
+  if (!srv) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return sg_fail(srv->ctx, SG_E_NOTFOUND, "unknown ticket");
+  Req* r = it->second.get();
+  if (r->state == 3) return SG_E_CANCELLED;
+  if (r->state != 2) return SG_E_PENDING;
+  return fill_result(r, out);
+}
+
+sg_status sg_server_wait(sg_server* srv, uint64_t ticket, sg_result* out) {
+  if (!srv) return SG_E_INVALID;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return sg_fail(srv->ctx, SG_E_NOTFOUND, "unknown ticket");
+  Req* r = it->second.get();
+  srv->done_cv.wait(lk, [&] { return r->state >= 2; });
+  if (r->state == 3) return SG_E_CANCELLED;
+  return fill_result(r, out);
+}
+
+sg_status sg_server_cancel(sg_server* srv, uint64_t ticket) {
+  if (!srv) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return sg_fail(srv->ctx, SG_E_NOTFOUND, "unknown ticket");
+  Req* r = it->second.get();
+  if (r->state != 0) return r->state == 3 ? SG_OK : sg_fail(srv->ctx, SG_E_STATE, "request already started");
+  srv->queue.erase(std::remove(srv->queue.begin(), srv->queue.end(), r), srv->queue.end());
+  r->state = 3;
+  ++srv->cancelled;
+  srv->done_cv.notify_all();
+  return SG_OK;
+}
+
+sg_status sg_server_stats(sg_server* srv, sg_stats* out) {
+  if (!srv || !out) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  out->submitted = srv->submitted;
+  out->completed = srv->completed;
+  out->cancelled = srv->cancelled;
+  out->rejected = srv->rejected;
+  double span = srv->first_start >= 0 ? srv->last_done - srv->first_start : 0.0;
+  out->solves_per_s = span > 0 ? srv->completed / span : 0.0;
+  std::vector<double> l = srv->latencies;
+  std::sort(l.begin(), l.end());
+  auto pct = [&](double p) {
+    if (l.empty()) return 0.0;
+    size_t i = (size_t)std::min<double>(l.size() - 1, std::ceil(p * l.size()) - 1);
+    return l[i];
+  };
+  out->p50_s = pct(0.50);
+  out->p99_s = pct(0.99);
+  double busy = srv->busy_accum;
+  double nowt = now_s(srv->t0);
+  if (srv->busy_since >= 0) busy += nowt - srv->busy_since;
+  out->gpu_busy_frac = srv->first_start >= 0 ? busy / std::max(1e-9, nowt - srv->first_start) : 0.0;
+  out->mem_in_use = srv->mem_in_use;
+  out->mem_budget = srv->budget;
+  out->active_slots = srv->active;
+  out->max_slots = srv->max_slots;
+  return SG_OK;
+}
+
+}  // extern "C"

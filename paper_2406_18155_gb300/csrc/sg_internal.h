@@ -1,0 +1,95 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <mutex>
+
+#include "../../include/sg.h"
+
+#define SG_MAXQ 16        // modes per system
+#define SG_MAXD 8         // truncated levels per mode
+#define SG_MAXM 64        // subsystem basis size (charge states or oscillator states)
+#define SG_MAXEDGE 48     // 2-body terms per system
+#define SG_MAXDRIVE 48    // drives per system
+
+// ---------------------------------------------------------------------------
+// Host-side model of a system
+// ---------------------------------------------------------------------------
+struct HostMode {
+  int kind;        // 0 transmon, 1 fluxonium
+  double ej, ec, el, ng, phi_ext;
+  int M;           // basis size
+  int d;           // kept levels
+};
+struct HostCoupling { int a, op_a, b, op_b; double J; };
+struct HostDrive {
+  int mode, op, kind, nseg;
+  std::vector<double> amps;
+  double amp, sigma, t0, length, omega_d, phase;
+  int omega_mode;
+};
+
+// Device layout of one mode's prepared data (all FP64).  Matrices are M x M
+// row-major unless noted; complex as double2.
+struct ModeDev {
+  int kind, M, d, pad;
+  double* w;          // M eigenvalues, ascending
+  double* V;          // M x M eigenvectors in columns, gauge fixed
+  double* dH;         // 3 x M x M: dH/d(ej, ec, el)
+  double2* ops;       // 2 x M x M: n, phi (phi zero for transmon)
+  double2* dops;      // 2 x 3 x M x M: d(op)/d(param)
+  double* E;          // d, ground shifted
+  double2* opd;       // 2 x d x d truncated n, phi
+};
+
+struct sg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  std::mutex mu;
+};
+
+struct StageTables;  // defined in evolve.cu
+
+struct sg_system {
+  sg_ctx* ctx = nullptr;
+  std::vector<HostMode> modes;
+  std::vector<HostCoupling> couplings;
+  std::vector<HostDrive> drives;
+  bool prepared = false;
+  // device data
+  void* mode_block = nullptr;     // one allocation for all modes
+  size_t mode_block_bytes = 0;
+  std::vector<ModeDev> mdev;      // host copy of the device pointers
+  ModeDev* mdev_dev = nullptr;    // device array of ModeDev
+  // host copies of the prepared truncated data
+  std::vector<std::vector<double>> E_host;       // per mode, d
+  std::vector<std::vector<double>> opd_host;     // per mode, 2*d*d complex -> 4*d*d doubles
+  std::vector<int> parity_odd;                   // per mode*2+op: operator is parity-odd
+  double last_stats[5] = {0, 0, 0, 0, 0};
+};
+
+// error helpers --------------------------------------------------------------
+sg_status sg_fail(sg_ctx* ctx, sg_status code, const std::string& msg);
+#define SG_CUDA_TRY(ctx, expr)                                                     \
+  do {                                                                             \
+    cudaError_t _e = (expr);                                                       \
+    if (_e != cudaSuccess)                                                         \
+      return sg_fail((ctx), SG_E_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// prepare.cu
+sg_status sg_prepare_impl(sg_system* sys);
+// runs the eigen-derivative chain: given per-mode operator co-gradients
+// opbar[mode][op][d*d] (complex, device) and energy co-gradients ebar[mode][d]
+// (device), writes dL/d(ej, ec, el) per mode into out_dev (3*nq doubles).
+sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev,
+                                 const double* ebar_dev, double* out_dev);
+
+// evolve.cu
+sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev);
+sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target,
+                           int kind, double* F_out, double* Ucomp_out, bool grad,
+                           double* grad_pulse, double* grad_ham, int ckpt);
