@@ -18,6 +18,9 @@
 #include "sg_internal.h"
 #include "kplan.h"
 #include "fast.h"
+#include "grad.cuh"
+#include "slab.h"
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <algorithm>
@@ -462,39 +465,6 @@ __global__ void k_scatter_comp(CompArgs a, const double2* bar, double2* pbar) {
 // ---------------------------------------------------------------------------
 // gradient: cross-densities per stage and their contraction into co-gradients
 // ---------------------------------------------------------------------------
-struct GradAcc {
-  double* gF;          // 3N x K: dF/df_k at each stage slot
-  double2* obD;        // K x MAXD^2: co-gradient of drive k's base operator
-  double2* obL;        // ne x MAXD^2
-  double2* obR;        // ne x MAXD^2
-  double* ebB;         // n1 x MAXD
-  double* ebL;         // ne x MAXD
-  double* ebR;         // ne x MAXD
-  double* jb;          // ne
-};
-
-struct XArgs {
-  KPlan p;
-  int K, nW, frame;
-  double t;            // stage time
-  int q;               // stage slot 3n + j
-  const double2* tabrow;      // FP64 row of this stage
-  const double* coef;         // K values at this stage
-  const double2* ph;          // sumd phases at this stage
-  const double2* opd;         // flat truncated operators
-  int opd_off[SG_MAXQ];
-  int eoff[SG_MAXQ];
-  const double* E;
-  int drv_of_slot_start[SG_MAXQ + 1];
-  int drv_list[SG_MAXDRIVE];
-  int drv_op[SG_MAXDRIVE];
-  int e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
-  double J[SG_MAXEDGE];
-  double2* partial;           // gridDim x nW x DL^2
-  unsigned* ticket;
-  GradAcc acc;
-};
-
 template <typename C, int DL>
 __device__ void block_reduce_store(C (&acc)[DL][DL], double2* out, double* red) {
   // warp reduce each element, then combine warps in order through shared memory
@@ -625,73 +595,7 @@ __global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* 
   __syncthreads();
   if (threadIdx.x == 0) *a.ticket = 0u;
   const int slot = threadIdx.x;
-  if (slot >= a.nW) return;
-  const double t = a.t;
-  const bool inter = a.frame == SG_FRAME_INTERACTION;
-  const double2* W = Wt + slot * DL * DL;
-  if (slot < p.n1) {
-    const int u = slot, i = p.s1_mode[u], d = p.dims[i];
-    const double2* B = a.tabrow + p.s1_off[u];
-    for (int x = a.drv_of_slot_start[u]; x < a.drv_of_slot_start[u + 1]; ++x) {
-      const int k = a.drv_list[x];
-      const double2* O = a.opd + a.opd_off[i] + a.drv_op[k] * d * d;
-      const double fk = a.coef[k];
-      double g = 0.0;
-      for (int ia = 0; ia < d; ++ia)
-        for (int ib = 0; ib < d; ++ib) {
-          double2 P = cmul(a.ph[a.eoff[i] + ia], cconj(a.ph[a.eoff[i] + ib]));
-          double2 w = W[ia * DL + ib];
-          double2 Ot = cmul(O[ia * d + ib], P);
-          g += w.x * Ot.x - w.y * Ot.y;
-          double2 cw = cmul(cconj(w), cconj(P));
-          double2* ob = a.acc.obD + (size_t)k * SG_MAXD * SG_MAXD + ia * SG_MAXD + ib;
-          ob->x += fk * cw.x;
-          ob->y += fk * cw.y;
-        }
-      a.acc.gF[(size_t)a.q * a.K + k] += g;
-    }
-    double* eb = a.acc.ebB + u * SG_MAXD;
-    for (int ia = 0; ia < d; ++ia)
-      for (int ib = 0; ib < d; ++ib) {
-        double2 w = W[ia * DL + ib];
-        if (inter) {
-          double2 v = cmul(w, B[ia * d + ib]);
-          double qv = -v.y * t;                            // Re(v * i t)
-          eb[ia] += qv;
-          eb[ib] -= qv;
-        } else if (ia == ib) {
-          eb[ia] += w.x;
-        }
-      }
-    return;
-  }
-  const int side = (slot - p.n1) / p.ne, q = (slot - p.n1) % p.ne;
-  const int i = side == 0 ? p.e_a[q] : p.e_b[q];
-  const int op = side == 0 ? a.e_opa[q] : a.e_opb[q];
-  const int d = p.dims[i];
-  const double2* O = a.opd + a.opd_off[i] + op * d * d;
-  const double2* X2 = a.tabrow + (side == 0 ? p.e_offL[q] : p.e_offR[q]);
-  double2* ob = (side == 0 ? a.acc.obL : a.acc.obR) + (size_t)q * SG_MAXD * SG_MAXD;
-  double* eb = (side == 0 ? a.acc.ebL : a.acc.ebR) + q * SG_MAXD;
-  const double sc = side == 0 ? a.J[q] : 1.0;
-  double jg = 0.0;
-  for (int ia = 0; ia < d; ++ia)
-    for (int ib = 0; ib < d; ++ib) {
-      double2 P = cmul(a.ph[a.eoff[i] + ia], cconj(a.ph[a.eoff[i] + ib]));
-      double2 w = W[ia * DL + ib];
-      double2 At = cmul(O[ia * d + ib], P);
-      jg += w.x * At.x - w.y * At.y;
-      double2 cw = cmul(cconj(w), cconj(P));
-      ob[ia * SG_MAXD + ib].x += sc * cw.x;
-      ob[ia * SG_MAXD + ib].y += sc * cw.y;
-      if (inter) {
-        double2 v = cmul(w, X2[ia * d + ib]);
-        double qv = -v.y * t;
-        eb[ia] += qv;
-        eb[ib] -= qv;
-      }
-    }
-  if (side == 0) a.acc.jb[q] += jg;
+  if (slot < a.nW) contract_slot(a, slot, Wt + slot * DL * DL, DL);
 }
 
 // Pulse-parameter chain, one block per drive: dF/dparam = sum over stages of
@@ -968,7 +872,17 @@ struct Solve {
   float2* tab32 = nullptr;
   double2* psi = nullptr;
   int launches = 0;
+  bool mixed = false;
+  SlabPlanHost* slab = nullptr;
+  ~Solve() { slab_plan_destroy(slab); }
 };
+
+// Kernel family: SG_PATH=gather forces the generic gather kernels (a test knob);
+// otherwise the tiled slab kernels run whenever they handle the plan.
+bool use_slab_path() {
+  const char* e = std::getenv("SG_PATH");
+  return !(e && std::string(e) == "gather");
+}
 
 sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) {
   sg_ctx* ctx = sys->ctx;
@@ -1002,6 +916,9 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) 
   s.ta = ta;
   k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
   ++sv.launches;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  sv.mixed = o->precision == SG_MIXED;
+  if (use_slab_path()) sv.slab = slab_plan_create(s.p, sv.mixed, st);
   SG_CUDA_TRY(ctx, cudaGetLastError());
   return SG_OK;
 }
@@ -1069,6 +986,27 @@ sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool
   C* Xo = sv.ar.get<C>(n);
   C* Dacc = sv.ar.get<C>(n);
   if (!X || !Xo || !Dacc) return sg_fail(ctx, SG_E_NOMEM, "device allocation of stage buffers failed");
+  if (sv.slab) {
+    C* kA = sv.ar.get<C>(slab_passes(sv.slab) > 1 ? n : 1);
+    double2* pint = sv.ar.get<double2>(n);
+    if (!kA || !pint) return sg_fail(ctx, SG_E_NOMEM, "device allocation of stage buffers failed");
+    slab_to_internal(sv.slab, sv.psi, pint, st);
+    k_cast<R><<<grid_for(n), kT, 0, st>>>(pint, X, n, 1.0);
+    sv.launches += 2;
+    const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
+    void* Xv = X;
+    void* Xov = Xo;
+    for (int step = 0; step < s.N; ++step) {
+      if (ckpts && step % ckpt_every == 0)
+        SG_CUDA_TRY(ctx, cudaMemcpyAsync((*ckpts)[step / ckpt_every], pint, n * sizeof(double2),
+                                         cudaMemcpyDeviceToDevice, st));
+      sv.launches += slab_fwd_step(sv.slab, sv.mixed, tab, step, pint, pint, Xv, Xov, Dacc, kA, s.dt, st);
+    }
+    slab_from_internal(sv.slab, pint, sv.psi, st);
+    ++sv.launches;
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    return SG_OK;
+  }
   k_cast<R><<<grid_for(n), kT, 0, st>>>(sv.psi, X, n, 1.0);
   ++sv.launches;
   for (int step = 0; step < s.N; ++step) {
@@ -1160,6 +1098,43 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
     }
     ++sv.launches;
   };
+  if (sv.slab) {
+    C* kA = sv.ar.get<C>(slab_passes(sv.slab) > 1 ? n : 1);
+    C* yA = sv.ar.get<C>(slab_passes(sv.slab) > 1 ? n : 1);
+    double2* pint = sv.ar.get<double2>(n);
+    double2* spart = sv.ar.get<double2>(slab_partial_elems(sv.slab));
+    if (!kA || !yA || !pint || !spart) return sg_fail(ctx, SG_E_NOMEM, "device allocation of adjoint buffers failed");
+    xa.partial = spart;
+    slab_to_internal(sv.slab, pbar, pint, st);
+    k_cast<R><<<grid_for(n), kT, 0, st>>>(pint, KB, n, s.dt / 6.0);
+    sv.launches += 2;
+    const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
+    void* Yv[4] = {Y[0], Y[1], Y[2], Y[3]};
+    void* KBv = KB;
+    void* KB2v = KB2;
+    const int nseg = (int)ckpts.size();
+    for (int c = nseg - 1; c >= 0; --c) {
+      const int n0 = c * K, n1 = std::min(s.N, n0 + K);
+      SG_CUDA_TRY(ctx, cudaMemcpyAsync(seg[0], ckpts[c], n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      k_cast<R><<<grid_for(n), kT, 0, st>>>(seg[0], X, n, 1.0);
+      ++sv.launches;
+      void* Xv = X;
+      void* Xov = Xo;
+      for (int step = n0; step < n1 - 1; ++step)
+        sv.launches += slab_fwd_step(sv.slab, sv.mixed, tab, step, seg[step - n0], seg[step - n0 + 1], Xv, Xov,
+                                     Dacc, kA, s.dt, st);
+      for (int step = n1 - 1; step >= n0; --step) {
+        const double2* ps = seg[step - n0];
+        k_cast<R><<<grid_for(n), kT, 0, st>>>(ps, Y[0], n, 1.0);
+        ++sv.launches;
+        sv.launches += slab_fwd_store(sv.slab, sv.mixed, tab, step, ps, Yv, kA, s.dt, st);
+        sv.launches += slab_adj_step(sv.slab, sv.mixed, tab, step, Yv, pint, KBv, KB2v, Db, yA, s.dt, xa,
+                                     sv.tab, sv.coef, sv.ph, s.sumd, s.K, st);
+      }
+      SG_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return SG_OK;
+  }
   // kbar_4 of the last step = dt/6 psibar_N
   k_cast<R><<<grid_for(n), kT, 0, st>>>(pbar, KB, n, s.dt / 6.0);
   ++sv.launches;

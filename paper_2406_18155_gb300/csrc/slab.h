@@ -1,0 +1,41 @@
+// Tiled ("slab") RK4 kernels for state slabs that live in HBM.
+//
+// The Kronecker-sum Hamiltonian is applied one mode group at a time (App. B: local
+// operators contracted into the state tensor, never a dense matrix).  A pass loads
+// tiles that hold the full extent of a group of modes for one column into shared
+// memory and applies every term whose support lies in the group.  Terms are split
+// over at most four passes; a stage is one launch per pass.
+#pragma once
+#include "grad.cuh"
+
+struct SlabPlanHost;   // opaque
+
+// Returns nullptr when the plan is not handled by the slab kernels (non-uniform
+// level counts, more than 4 passes, too many terms per pass); the caller then
+// uses the gather kernels.
+SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st);
+void slab_plan_destroy(SlabPlanHost* sp);
+int slab_passes(const SlabPlanHost* sp);
+
+// Internal slab layout: column-major [S][D] with a permuted digit order.
+void slab_to_internal(const SlabPlanHost* sp, const double2* api, double2* internal, cudaStream_t st);
+void slab_from_internal(const SlabPlanHost* sp, const double2* internal, double2* api, cudaStream_t st);
+
+// One forward RK4 step pin -> pout (may alias) on internal buffers.  X holds the
+// stage input (R)psi on entry and on exit; Xo, Dacc, kA are scratch slabs of the
+// stage precision.  tab: stage rows of the stage precision.  Returns launches.
+int slab_fwd_step(const SlabPlanHost* sp, bool mixed, const void* tab, int step, const double2* pin,
+                  double2* pout, void*& X, void*& Xo, void* Dacc, void* kA, double dt,
+                  cudaStream_t st);
+// Recompute y2, y3, y4 of one step from y1 = (R)psi_n (STORE mode).  Returns launches.
+int slab_fwd_store(const SlabPlanHost* sp, bool mixed, const void* tab, int step, const double2* psi,
+                   void* const Y[4], void* kA, double dt, cudaStream_t st);
+// One adjoint step: KB holds kbar_4 on entry and kbar_4 of the previous step on
+// exit; pbar (complex128) is updated in place; the cross-densities of every
+// stage are contracted into the accumulators of xa.  Returns launches.
+int slab_adj_step(const SlabPlanHost* sp, bool mixed, const void* tab, int step, void* const Y[4],
+                  double2* pbar, void*& KB, void*& KB2, void* Db, void* yA, double dt, XArgs xa,
+                  const double2* tab64, const double* coef, const double2* ph, int sumd, int K,
+                  cudaStream_t st);
+// Size of the per-block partial buffer (double2 elements) slab_adj_step needs.
+size_t slab_partial_elems(const SlabPlanHost* sp);

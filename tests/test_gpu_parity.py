@@ -12,6 +12,13 @@ from paper_2406_18155_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
+
+@pytest.fixture(params=["slab", "gather"])
+def path(request, monkeypatch):
+    """Kernel family: the tiled slab kernels (default) or the generic gather kernels."""
+    monkeypatch.setenv("SG_PATH", request.param)
+    return request.param
+
 GHZ = 2 * np.pi
 
 
@@ -68,7 +75,7 @@ def test_spectrum_matches_oracle(sgctx, mode_spec):
 
 @pytest.mark.parametrize("case", sorted(CASES))
 @pytest.mark.parametrize("frame", ["interaction", "lab"])
-def test_fp64_evolution_matches_oracle(sgctx, case, frame):
+def test_fp64_evolution_matches_oracle(sgctx, case, frame, path):
     wl = CASES[case]()
     wl["frame"] = frame
     if frame == "lab":
@@ -83,7 +90,7 @@ def test_fp64_evolution_matches_oracle(sgctx, case, frame):
 
 
 @pytest.mark.parametrize("case", sorted(CASES))
-def test_fidelity_fp64_and_mixed(sgctx, case):
+def test_fidelity_fp64_and_mixed(sgctx, case, path):
     wl = CASES[case]()
     s = _system(sgctx, wl)
     sysr = OracleSystem(wl)
@@ -114,7 +121,7 @@ def test_evolve_from_arbitrary_states(sgctx):
 
 
 @pytest.mark.parametrize("case", ["fluxonium_pair_cr_T1", "transmon_pair_T2", "ring3_mixed_dims"])
-def test_gradient_fp64_matches_oracle_adjoint(sgctx, case):
+def test_gradient_fp64_matches_oracle_adjoint(sgctx, case, path):
     wl = CASES[case]()
     if case == "transmon_pair_T2":
         wl["T"] = 0.5
@@ -134,7 +141,7 @@ def test_gradient_fp64_matches_oracle_adjoint(sgctx, case):
     assert np.max(np.abs(g - gr)) <= 1e-8 * scale, (g, gr)
 
 
-def test_gradient_mixed_matches_oracle(sgctx):
+def test_gradient_mixed_matches_oracle(sgctx, path):
     wl = CASES["fluxonium_pair_cr_T1"]()
     s = _system(sgctx, wl)
     F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
@@ -162,3 +169,46 @@ def test_invalid_inputs_are_rejected(sgctx):
     assert e.value.code == SG_E_INVALID
     with pytest.raises(SGError):
         s.add_coupling(0, "phi", 1, "n", 0.1)         # transmon has no phi
+
+
+@pytest.mark.parametrize("tmax,nq,levels,ring", [(9, 4, 3, False), (27, 4, 3, True), (4, 5, 2, True)])
+def test_multipass_slab_matches_oracle(sgctx, monkeypatch, tmax, nq, levels, ring):
+    # a small tile budget splits the terms over several mode-group passes
+    monkeypatch.setenv("SG_PATH", "slab")
+    monkeypatch.setenv("SG_SLAB_TMAX", str(tmax))
+    wl = W.fluxonium_chain(seed=tmax, nq=nq, levels=levels, T=0.3, dt=0.01, nseg=3, ring=ring)
+    s = _system(sgctx, wl)
+    psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"]).cpu().numpy()
+    assert np.max(np.abs(psi - _oracle_psi(wl))) < 1e-10
+    F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                precision="fp64", ckpt=5)
+    Fr, gr, _ = adjoint_gradient(wl)
+    assert abs(F[1] - Fr) < 1e-10
+    assert np.max(np.abs(np.concatenate([gp, gh]) - gr)) <= 1e-8 * np.max(np.abs(gr))
+    F32, gp32, gh32 = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                                      kind="state", precision="mixed", ckpt=5)
+    assert abs(F32[1] - Fr) < 1e-5
+    assert np.max(np.abs(np.concatenate([gp32, gh32]) - gr)) <= 1e-3 * np.max(np.abs(gr))
+
+
+def test_two_pass_ring7_against_matrix_free_oracle(sgctx, monkeypatch):
+    # D = 4^7 = 16384 > one tile: the ring splits into two overlapping mode groups
+    from oracle.evolve import rk4_evolve_matrix_free
+    monkeypatch.setenv("SG_PATH", "slab")
+    wl = W.fluxonium_chain(seed=9, nq=7, levels=4, T=0.1, dt=0.01, nseg=2, ring=True, ncols=3)
+    s = _system(sgctx, wl)
+    psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"]).cpu().numpy()
+    so = OracleSystem(wl)
+    ref = frame_epilogue(so, rk4_evolve_matrix_free(so, initial_columns(so, wl["col_index"])))
+    assert np.max(np.abs(psi - ref)) < 1e-10
+    psi32 = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"]).cpu().numpy()
+    assert np.max(np.abs(psi32 - ref)) < 1e-5
+    # gradient: the slab kernels against the independent gather kernels
+    g = {}
+    for pth in ("slab", "gather"):
+        monkeypatch.setenv("SG_PATH", pth)
+        F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                                    kind="state", precision="fp64", ckpt=3)
+        g[pth] = (F, np.concatenate([gp, gh]))
+    assert abs(g["slab"][0][1] - g["gather"][0][1]) < 1e-12
+    assert np.max(np.abs(g["slab"][1] - g["gather"][1])) <= 1e-10 * np.max(np.abs(g["gather"][1]))
