@@ -197,6 +197,14 @@ sg_status sg_fidelity_grad(sg_system* sys, const sg_evolve_opts* opts,
  * launches issued. */
 sg_status sg_last_stats(const sg_system* sys, double* out5);
 
+/* Device time per kernel family of the last sg_evolve / sg_fidelity /
+ * sg_fidelity_grad on this system.  When the environment variable SG_KTIMING=1 is
+ * set at the call, CUDA events on the context stream bracket the launches of every
+ * 16th step; out[3k] = bracketed ms, out[3k+1] = bracketed launches, out[3k+2] =
+ * all launches of family k, for k = 0 forward stage passes, 1 adjoint stage passes,
+ * 2 forward recompute (store) passes.  n is the capacity of out (>= 9). */
+sg_status sg_kernel_times(const sg_system* sys, double* out, int n);
+
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of fidelity+gradient solves
  * ------------------------------------------------------------------------- */

@@ -82,6 +82,7 @@ SIGNATURES = {
     "sg_fidelity": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _PD, _PD]),
     "sg_fidelity_grad": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I]),
     "sg_last_stats": (_I, [_P, _PD]),
+    "sg_kernel_times": (_I, [_P, _PD, _I]),
     "sg_server_create": (_I, [_P, C.c_size_t, _I, C.POINTER(_P)]),
     "sg_server_destroy": (_I, [_P]),
     "sg_server_submit": (_I, [_P, C.POINTER(sg_request), C.POINTER(C.c_uint64)]),

@@ -257,4 +257,10 @@ sg_status sg_last_stats(const sg_system* sys, double* out5) {
   return SG_OK;
 }
 
+sg_status sg_kernel_times(const sg_system* sys, double* out, int n) {
+  if (!sys || !out || n < 9) return SG_E_INVALID;
+  for (int i = 0; i < 9; ++i) out[i] = sys->ktimes[i];
+  return SG_OK;
+}
+
 }  // extern "C"

@@ -859,7 +859,54 @@ struct Bufs {
 };
 
 // Everything a solve needs on the device.
+// CUDA-event brackets around the launches of every 16th step, per kernel family
+// (0 forward stage passes, 1 adjoint passes, 2 recompute passes), enabled by
+// SG_KTIMING=1.
+struct KTimer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> ev[3];
+  std::vector<int> nl[3];
+  long long total[3] = {0, 0, 0};
+  template <typename F> void run(int k, int step, F&& f) {
+    if (on && step % 16 == 0) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, st);
+      int n = f();
+      cudaEventRecord(b, st);
+      ev[k].push_back(a);
+      ev[k].push_back(b);
+      nl[k].push_back(n);
+      total[k] += n;
+    } else {
+      total[k] += f();
+    }
+  }
+  void finish(double* out) {
+    for (int k = 0; k < 3; ++k) {
+      double ms = 0.0, nb = 0.0;
+      for (size_t i = 0; i + 1 < ev[k].size(); i += 2) {
+        float x = 0.f;
+        cudaEventSynchronize(ev[k][i + 1]);
+        cudaEventElapsedTime(&x, ev[k][i], ev[k][i + 1]);
+        ms += x;
+        nb += nl[k][i / 2];
+        cudaEventDestroy(ev[k][i]);
+        cudaEventDestroy(ev[k][i + 1]);
+      }
+      ev[k].clear();
+      nl[k].clear();
+      out[3 * k] = ms;
+      out[3 * k + 1] = nb;
+      out[3 * k + 2] = (double)total[k];
+    }
+  }
+};
+
 struct Solve {
+  KTimer kt;
   Setup s;
   Arena ar;
   DriveDev* drives_dev = nullptr;
@@ -919,6 +966,11 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) 
   SG_CUDA_TRY(ctx, cudaGetLastError());
   sv.mixed = o->precision == SG_MIXED;
   if (use_slab_path()) sv.slab = slab_plan_create(s.p, sv.mixed, st);
+  {
+    const char* e = std::getenv("SG_KTIMING");
+    sv.kt.on = e && e[0] == '1';
+    sv.kt.st = st;
+  }
   SG_CUDA_TRY(ctx, cudaGetLastError());
   return SG_OK;
 }
@@ -1000,7 +1052,7 @@ sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool
       if (ckpts && step % ckpt_every == 0)
         SG_CUDA_TRY(ctx, cudaMemcpyAsync((*ckpts)[step / ckpt_every], pint, n * sizeof(double2),
                                          cudaMemcpyDeviceToDevice, st));
-      sv.launches += slab_fwd_step(sv.slab, sv.mixed, tab, step, pint, pint, Xv, Xov, Dacc, kA, s.dt, st);
+      sv.kt.run(0, step, [&] { return slab_fwd_step(sv.slab, sv.mixed, tab, step, pint, pint, Xv, Xov, Dacc, kA, s.dt, st); });
     }
     slab_from_internal(sv.slab, pint, sv.psi, st);
     ++sv.launches;
@@ -1121,15 +1173,18 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
       void* Xv = X;
       void* Xov = Xo;
       for (int step = n0; step < n1 - 1; ++step)
-        sv.launches += slab_fwd_step(sv.slab, sv.mixed, tab, step, seg[step - n0], seg[step - n0 + 1], Xv, Xov,
-                                     Dacc, kA, s.dt, st);
+        sv.kt.run(0, step, [&] {
+          return slab_fwd_step(sv.slab, sv.mixed, tab, step, seg[step - n0], seg[step - n0 + 1], Xv, Xov, Dacc, kA, s.dt, st);
+        });
       for (int step = n1 - 1; step >= n0; --step) {
         const double2* ps = seg[step - n0];
         k_cast<R><<<grid_for(n), kT, 0, st>>>(ps, Y[0], n, 1.0);
         ++sv.launches;
-        sv.launches += slab_fwd_store(sv.slab, sv.mixed, tab, step, ps, Yv, kA, s.dt, st);
-        sv.launches += slab_adj_step(sv.slab, sv.mixed, tab, step, Yv, pint, KBv, KB2v, Db, yA, s.dt, xa,
-                                     sv.tab, sv.coef, sv.ph, s.sumd, s.K, st);
+        sv.kt.run(2, step, [&] { return slab_fwd_store(sv.slab, sv.mixed, tab, step, ps, Yv, kA, s.dt, st); });
+        sv.kt.run(1, step, [&] {
+          return slab_adj_step(sv.slab, sv.mixed, tab, step, Yv, pint, KBv, KB2v, Db, yA, s.dt, xa, sv.tab,
+                               sv.coef, sv.ph, s.sumd, s.K, st);
+        });
       }
       SG_CUDA_TRY(ctx, cudaGetLastError());
     }
@@ -1202,6 +1257,9 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
     SG_CUDA_TRY(ctx, cudaGetLastError());
   }
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  sv.kt.finish(sys->ktimes);
+  sv.launches += (int)(sv.kt.total[0] + sv.kt.total[1] + sv.kt.total[2]);
+  sys->last_stats[4] = sv.launches;
   return SG_OK;
 }
 
@@ -1402,6 +1460,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   sys->last_stats[1] = bwd_ms;
   sys->last_stats[2] = (double)peak;
   sys->last_stats[3] = K;
-  sys->last_stats[4] = sv.launches;
+  sv.kt.finish(sys->ktimes);
+  sys->last_stats[4] = sv.launches + (double)(sv.kt.total[0] + sv.kt.total[1] + sv.kt.total[2]);
   return SG_OK;
 }

@@ -69,6 +69,7 @@ struct sg_system {
   std::vector<std::vector<double>> opd_host;     // per mode, 2*d*d complex -> 4*d*d doubles
   std::vector<int> parity_odd;                   // per mode*2+op: operator is parity-odd
   double last_stats[5] = {0, 0, 0, 0, 0};
+  double ktimes[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // error helpers --------------------------------------------------------------

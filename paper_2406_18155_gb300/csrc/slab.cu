@@ -342,6 +342,7 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
   const int DL = p.dims[0];
   for (int i = 0; i < nq; ++i) if (p.dims[i] != DL) return nullptr;
   if (DL < 2 || DL > 5) return nullptr;
+  if (p.D >= (1ll << 31)) return nullptr;
   // SG_SLAB_TMAX lowers the tile budget so small systems exercise multi-pass plans (tests)
   long long tmax = kTmax;
   if (const char* e = std::getenv("SG_SLAB_TMAX")) tmax = std::max(1ll, std::min<long long>(kTmax, atoll(e)));
