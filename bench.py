@@ -1,0 +1,412 @@
+#!/usr/bin/env python
+"""Benchmark of the fidelity + adjoint-gradient solve on one GB300 (or N, as
+independent replicas with their own seeds: the columns of one solve are a
+partition of the path, so N GPUs run weak-scaled copies and need no collective).
+
+One bench step = one pass of the whole hot path on the workload: subsystem build
+and eigensolve, stage tables, forward RK4 of every column with checkpoints,
+fidelity, co-state, checkpointed discrete adjoint with fused cross-density
+reductions, and the parameter chain.  Metric: state-column RK steps per second of
+that solve (S columns x N steps per solve).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...     # the FP64 CPU oracle as it stands
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2406_18155_gb300 import workloads as W
+
+METRIC = "state-column RK steps/s (fidelity + adjoint-gradient solve)"
+UNIT = "col-steps/s"
+
+WORKLOADS = {
+    "fluxonium_ring10": ("10-fluxonium ring, 4 levels (D=1,048,576), 16 computational columns, "
+                         "10 drives x 10 PWC segments, T=40 ns, dt=0.01 ns (N=4000)",
+                         lambda seed: W.fluxonium_ring10(seed=seed)),
+    "fluxonium_chain6": ("6-fluxonium chain, 4 levels (D=4096), 64 columns, 6 drives x 10 PWC "
+                         "segments, T=60 ns, dt=0.01 ns (N=6000)",
+                         lambda seed: W.fluxonium_chain6(seed=seed)),
+    "fluxonium_pair_cr": ("2 fluxoniums, 5 levels (D=25), 4 columns, CR drive 20 PWC segments, "
+                          "T=100 ns, dt=0.01 ns (N=10000)",
+                          lambda seed: W.fluxonium_pair_cr(seed=seed)),
+    "transmon_pair": ("2 transmons, 4 levels (D=16), 16 columns, Gaussian drive, T=50 ns, "
+                      "dt=0.005 ns (N=10000)", lambda seed: W.transmon_pair(seed=seed)),
+}
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# algorithmic bytes per entry of each kernel family
+# ----------------------------------------------------------------------------
+def fwd_bytes_per_entry_step(c, npass):
+    """Forward RK4 step, bytes per slab entry: c = bytes of a stage value (8 mixed,
+    16 FP64); the state psi is complex128 (16)."""
+    p = 16
+    if npass == 1:
+        return (c + p + c + c) + 2 * (c + p + 2 * c + c) + (c + c + 2 * p + c)
+    partial_first = 2 * c                      # read y, write kA
+    partial_mid = 3 * c                        # read y, kA; write kA
+    last_extra = c                             # read kA
+    last = (c + p + c + c) + 2 * (c + p + 2 * c + c) + (c + c + 2 * p + c) + 4 * last_extra
+    return 4 * (partial_first + (npass - 2) * partial_mid) + last
+
+
+def adj_bytes_per_entry_step(c, npass):
+    """Adjoint step (4 stage passes each reading kbar and y_s), bytes per entry."""
+    p = 16
+    reads = 2 * c                              # kbar tile, y_s tile per pass
+    partial = [reads + c] + [reads + 2 * c] * max(0, npass - 2)
+    last_extra = c if npass > 1 else 0
+    st3 = reads + last_extra + p + c + c       # read pbar, write Db, Xn
+    st21 = reads + last_extra + p + 2 * c + c  # Db read+write
+    st0 = reads + last_extra + 2 * p + c + c   # pbar r+w, Db read, Xn
+    part = sum(partial) if npass > 1 else 0
+    return 4 * part + st3 + 2 * st21 + st0
+
+
+def store_bytes_per_entry_step(c, npass):
+    """Recompute of y2..y4 (3 stage passes, writes only the next stage input)."""
+    p = 16
+    if npass == 1:
+        return 3 * (c + p + c)
+    return 3 * (2 * c + (npass - 2) * 3 * c + (c + c + p + c))
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        from paper_2406_18155_gb300 import build as B
+        B.build()
+    from paper_2406_18155_gb300.api import Context, System, evolve_opts
+    desc, make = WORKLOADS[args.workload]
+    wl = make(1000 + rank)
+    ctx = Context(local)
+    sysm = System.from_workload(ctx, wl)
+    sysm.prepare()
+    S = len(wl["col_index"])
+    N = int(round(wl["T"] / wl["dt"]))
+    D = int(np.prod([m["levels"] for m in wl["modes"]]))
+    prec = args.precision
+    stream = torch.cuda.current_stream(local)
+
+    def one_step():
+        sysm.prepare()
+        return sysm.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                                  kind=wl["fid_kind"], precision=prec, ckpt=args.ckpt)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time with CUDA events on the library's stream
+    os.environ["SG_KTIMING"] = "1"
+    clk = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    launches = 0
+    fam = np.zeros(9)
+    fwd_ms, bwd_ms, peak = [], [], 0
+    for _ in range(args.steps):
+        F, gp, gh = one_step()
+        st = sysm.last_stats()
+        launches += st["launches"]
+        fwd_ms.append(st["forward_ms"])
+        bwd_ms.append(st["backward_ms"])
+        peak = max(peak, st["peak_bytes"])
+        kt = np.zeros(9)
+        from paper_2406_18155_gb300.capi import lib
+        import ctypes
+        lib().sg_kernel_times(sysm.h, kt.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 9)
+        fam += kt
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop()
+    os.environ["SG_KTIMING"] = "0"
+    t_s = ev0.elapsed_time(ev1) / 1e3
+    if dist:
+        tt = torch.tensor([t_s], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_s = float(tt.item())
+    units = S * N * args.steps * world
+    value = units / t_s
+
+    # ---- end to end through the public call: host target in, host gradients out
+    h2d = wl["target"].size * 16 + S * 8 + 8 * sum(len(d.get("amps", [0])) for d in wl["drives"])
+    npul, nham = sysm.param_counts()
+    d2h = 16 + 8 * (npul + nham)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(max(1, args.e2e_steps)):
+        one_step()
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = S * N * max(1, args.e2e_steps) * world / t_e2e
+
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "warmup": args.warmup,
+               "ms_per_step": t_s / args.steps * 1e3, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None,
+               "dtype": "c64 stages, c128 state/co-state, f64 reductions" if prec == "mixed" else "c128",
+               "data": "synthetic (seeded, shapes and value ranges of the paper's fluxonium workloads)",
+               "config": {"workload": f"{args.workload}: {desc}", "columns": S, "rk4_steps": N,
+                          "composite_dim": D, "precision": prec,
+                          "l2": "inputs larger than L2 (slab 128 MiB c64 / 256 MiB c128)"
+                          if D * S * 8 > 129e6 else "L2-resident working set; no flush",
+                          "parallelism": f"{world} independent replica(s), one per GPU"},
+               "forward_ms": statistics.mean(fwd_ms), "gradient_ms": statistics.mean(bwd_ms),
+               "O_t": (statistics.mean(fwd_ms) + statistics.mean(bwd_ms)) / statistics.mean(fwd_ms),
+               "peak_library_bytes": peak, "F": [float(F[0]), float(F[1])],
+               "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(d2h)},
+               "gpu_launches": int(launches), "clocks": clocks}
+        # ---- roofline of the dominant kernel family
+        out["roofline"], out["kernel_families"] = roofline(fam, D, S, N, prec, sysm, args)
+        # ---- the plain FP64 GPU path on a bounded number of steps
+        if args.fp64_steps > 0:
+            out["fp64_vs_mixed"] = fp64_comparison(sysm, wl, args.fp64_steps, stream)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def slab_passes(D):
+    # plans used by the tiled kernels: one pass while a column fits one tile
+    # (4096 entries), two overlapping mode groups for the ring beyond that
+    return 1 if D <= 4096 else 2
+
+
+def roofline(fam, D, S, N, prec, sysm, args):
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    c = 8 if prec == "mixed" else 16
+    npass = slab_passes(D)
+    E = D * S
+    per_step = {"forward_stage_pass": fwd_bytes_per_entry_step(c, npass),
+                "adjoint_stage_pass": adj_bytes_per_entry_step(c, npass),
+                "recompute_stage_pass": store_bytes_per_entry_step(c, npass)}
+    launches_per_step = {"forward_stage_pass": 4 * npass, "adjoint_stage_pass": 4 * npass,
+                         "recompute_stage_pass": 3 * npass}
+    fams = {}
+    for k, name in enumerate(["forward_stage_pass", "adjoint_stage_pass", "recompute_stage_pass"]):
+        ms, nl, tot = fam[3 * k], fam[3 * k + 1], fam[3 * k + 2]
+        if nl <= 0:
+            continue
+        avg_ms = ms / nl
+        bytes_per_launch = per_step[name] * E / launches_per_step[name]
+        fams[name] = {"avg_launch_ms": avg_ms, "launches": int(tot),
+                      "est_total_ms": avg_ms * tot,
+                      "algorithmic_bytes_per_launch": bytes_per_launch,
+                      "achieved_gbs": bytes_per_launch / (avg_ms * 1e-3) / 1e9}
+    if not fams:
+        return None, fams
+    dom = max(fams, key=lambda k: fams[k]["est_total_ms"])
+    f = fams[dom]
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tf):
+        with open(tf) as fh:
+            t = json.load(fh)
+        key = f"{args.workload}:{prec}:{dom}"
+        if key in t:
+            traffic = t[key]
+    return ({"bound": "hbm", "kernel": dom, "achieved": f["achieved_gbs"], "peak": hbm,
+             "unit": "GB/s", "frac": f["achieved_gbs"] / hbm, "peak_source": src,
+             "traffic": traffic}, fams)
+
+
+def fp64_comparison(sysm, wl, nsteps, stream):
+    """The plain FP64 GPU path against the mixed one, forward RK4 over the first
+    nsteps steps of the same workload (same columns), device time."""
+    import torch
+    T = nsteps * wl["dt"]
+    out = {"steps": nsteps}
+    for prec in ("fp64", "mixed"):
+        sysm.evolve(T, wl["dt"], precision=prec, col_index=wl["col_index"])   # warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysm.evolve(T, wl["dt"], precision=prec, col_index=wl["col_index"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        out[f"{prec}_forward_col_steps_per_s"] = len(wl["col_index"]) * nsteps / t
+    out["mixed_over_fp64"] = out["mixed_forward_col_steps_per_s"] / out["fp64_forward_col_steps_per_s"]
+    return out
+
+
+def cpu_baseline(wl, nsteps):
+    """The FP64 oracle as it stands on this host: matrix-free RK4 (per-mode tensor
+    contraction) of one column for nsteps steps.  numpy.einsum without path
+    optimisation runs on one thread."""
+    import oracle
+    from oracle.evolve import initial_columns, rk4_evolve_matrix_free
+    from oracle.system import OracleSystem
+    s = OracleSystem(wl)
+    psi0 = initial_columns(s, wl["col_index"][:1])
+    t0 = time.perf_counter()
+    rk4_evolve_matrix_free(s, psi0, nsteps=nsteps)
+    t = time.perf_counter() - t0
+    return {"value": nsteps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"matrix-free FP64 forward RK4, 1 of {len(wl['col_index'])} columns, "
+                      f"{nsteps} steps ({t:.1f} s); the oracle's adjoint forms dense D x D "
+                      "matrices and cannot run at this D, so the sample covers the forward "
+                      "part of the step"}
+
+
+# ----------------------------------------------------------------------------
+# reference arm: the oracle as it stands, on the host cores
+# ----------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    desc, make = WORKLOADS[args.workload]
+    wl = make(1000)
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(wl, args.cpu_sample_steps)
+        if i >= args.warmup:
+            vals.append(r["value"])
+    v = statistics.mean(vals)
+    N = int(round(wl["T"] / wl["dt"]))
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": args.cpu_sample_steps / v * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+           "config": {"workload": f"{args.workload}: {desc}", "columns": len(wl["col_index"]),
+                      "rk4_steps": N, "precision": "fp64"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": r["sample"]},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fluxonium_ring10", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--ckpt", type=int, default=0)
+    ap.add_argument("--fp64-steps", type=int, default=32)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -23,6 +23,21 @@ constexpr int kTmax = 4096;       // entries per tile
 constexpr int kMaxPass = 4;
 constexpr int kSPW = 2;           // cross-density slots per warp
 constexpr int kMaxX = kSPW * (kST / 32);
+constexpr int kMaxPhase = 12;
+
+// One phase of a pass: every thread owns d x d blocks over two tile digits
+// (ka, kb) and applies the terms living on them in registers: the edge
+// L(ka) (x) R(kb) and up to two 1-body matrices on ka and kb.
+struct Phase {
+  int ka, kb;
+  int offL, offR, offA, offB;   // stage-row offsets (-1: absent)
+  int ge, gA, gB;               // global edge index, global 1-body slots of A and B
+  unsigned par;                 // bit 0 L, 1 R, 2 A, 3 B parity-odd
+  int no;                       // other digits, in thread-mapping order
+  int ost[SG_MAXQ];             // their tile strides
+  int allpar;                   // every present term is parity-odd
+  int po[SG_MAXD * SG_MAXD];    // shared-memory offset of block entry (x, z) from the block base
+};
 
 struct SlabPass {
   int ng, T, ntpc, row;
@@ -39,15 +54,208 @@ struct SlabPass {
   int ne;
   int e_ka[SG_MAXEDGE], e_kb[SG_MAXEDGE], e_offL[SG_MAXEDGE], e_offR[SG_MAXEDGE];
   unsigned long long parL, parR;
-  int nx;                         // cross-density slots
-  int x_k[kMaxX], x_k2[kMaxX], x_off2[kMaxX], x_gslot[kMaxX];
+  int nx;                         // cross-density slots: phase, kind (0 A, 1 B, 2 L, 3 R), global id
+  int x_ph[kMaxX], x_type[kMaxX], x_gslot[kMaxX];
+  int nph;                        // register-blocked phases
+  Phase ph[kMaxPhase];
   const int* off;                 // device tile offsets [T]
 };
 
+// Padded shared-memory position of tile entry t: one pad element per 16 and per
+// 256 entries, so that a half-warp whose threads vary over one even-stride and
+// one odd-stride base-4 digit touches 16 distinct 8-byte bank pairs.
+// For power-of-two level counts the digits of a block base and of an in-block
+// offset occupy disjoint bits, so spos(base + o) = spos(base) + spos(o).
 template <int DL>
-__device__ __forceinline__ int digit(const SlabPass& sp, int t, int k) {
-  if (DL == 2 || DL == 4 || DL == 8) return (t >> sp.tlg[k]) & (DL - 1);
-  return (t / sp.tsh[k]) % DL;
+__host__ __device__ __forceinline__ int spos(int t) {
+  return (DL == 2 || DL == 4 || DL == 8) ? t + (t >> 4) + (t >> 8) : t;
+}
+__host__ __device__ constexpr int spad(int T) { return T + (T >> 4) + (T >> 8) + 1; }
+
+// Global -> shared tile copy with NB independent loads in flight per thread.
+template <int DL, int NB, typename C>
+__device__ __forceinline__ void load_tile(const SlabPass& sp, const C* __restrict__ X, long long base,
+                                          const int* __restrict__ off, C* __restrict__ ys) {
+  for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * NB) {
+    C v[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int t = t0 + j * kST;
+      v[j] = t < sp.T ? X[base + __ldg(off + t)] : cmk<C>(0.0, 0.0);
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) {
+      const int t = t0 + j * kST;
+      if (t < sp.T) ys[spos<DL>(t)] = v[j];
+    }
+  }
+}
+
+// u[x][z] = sum_c R[z][c] y[x][c]      (apply along the block's second digit)
+template <int DL, bool PAR, typename C>
+__device__ __forceinline__ void blk_right(const C* __restrict__ Rm, const C (&y)[DL][DL], C (&u)[DL][DL]) {
+#pragma unroll
+  for (int z = 0; z < DL; ++z) {
+    C r[DL];
+#pragma unroll
+    for (int c = 0; c < DL; ++c) r[c] = (!PAR || ((z + c) & 1)) ? Rm[z * DL + c] : cmk<C>(0.0, 0.0);
+#pragma unroll
+    for (int x = 0; x < DL; ++x) {
+      C a = cmk<C>(0.0, 0.0);
+#pragma unroll
+      for (int c = 0; c < DL; ++c)
+        if (!PAR || ((z + c) & 1)) a = cfma(r[c], y[x][c], a);
+      u[x][z] = a;
+    }
+  }
+}
+// out[x][z] += sum_a L[x][a] u[a][z]    (apply along the block's first digit)
+template <int DL, bool PAR, typename C>
+__device__ __forceinline__ void blk_left_acc(const C* __restrict__ Lm, const C (&u)[DL][DL], C (&out)[DL][DL]) {
+#pragma unroll
+  for (int x = 0; x < DL; ++x) {
+    C l[DL];
+#pragma unroll
+    for (int a = 0; a < DL; ++a) l[a] = (!PAR || ((x + a) & 1)) ? Lm[x * DL + a] : cmk<C>(0.0, 0.0);
+#pragma unroll
+    for (int z = 0; z < DL; ++z) {
+      C acc = out[x][z];
+#pragma unroll
+      for (int a = 0; a < DL; ++a)
+        if (!PAR || ((x + a) & 1)) acc = cfma(l[a], u[a][z], acc);
+      out[x][z] = acc;
+    }
+  }
+}
+// out[x][z] += sum_c B[z][c] y[x][c]
+template <int DL, bool PAR, typename C>
+__device__ __forceinline__ void blk_right_acc(const C* __restrict__ Bm, const C (&y)[DL][DL], C (&out)[DL][DL]) {
+#pragma unroll
+  for (int z = 0; z < DL; ++z) {
+    C r[DL];
+#pragma unroll
+    for (int c = 0; c < DL; ++c) r[c] = (!PAR || ((z + c) & 1)) ? Bm[z * DL + c] : cmk<C>(0.0, 0.0);
+#pragma unroll
+    for (int x = 0; x < DL; ++x) {
+      C a = out[x][z];
+#pragma unroll
+      for (int c = 0; c < DL; ++c)
+        if (!PAR || ((z + c) & 1)) a = cfma(r[c], y[x][c], a);
+      out[x][z] = a;
+    }
+  }
+}
+
+// H (restricted to the phase's terms) applied to one d x d block in registers.
+template <int DL, typename C>
+__device__ __forceinline__ void blk_apply(const Phase& P, const C* __restrict__ M, const C (&y)[DL][DL],
+                                          C (&out)[DL][DL]) {
+#pragma unroll
+  for (int x = 0; x < DL; ++x)
+#pragma unroll
+    for (int z = 0; z < DL; ++z) out[x][z] = cmk<C>(0.0, 0.0);
+  if (P.offL >= 0) {
+    C u[DL][DL];
+    if (P.par & 2u) blk_right<DL, true>(M + P.offR, y, u);
+    else blk_right<DL, false>(M + P.offR, y, u);
+    if (P.par & 1u) blk_left_acc<DL, true>(M + P.offL, u, out);
+    else blk_left_acc<DL, false>(M + P.offL, u, out);
+  }
+  if (P.offA >= 0) {
+    if (P.par & 4u) blk_left_acc<DL, true>(M + P.offA, y, out);
+    else blk_left_acc<DL, false>(M + P.offA, y, out);
+  }
+  if (P.offB >= 0) {
+    if (P.par & 8u) blk_right_acc<DL, true>(M + P.offB, y, out);
+    else blk_right_acc<DL, false>(M + P.offB, y, out);
+  }
+}
+
+template <int DL>
+__device__ __forceinline__ int blk_base(const Phase& P, int b) {
+  int tb = 0;
+  for (int j = 0; j < P.no; ++j) {
+    tb += (b % DL) * P.ost[j];
+    b /= DL;
+  }
+  return tb;
+}
+
+// One block of one phase, one output column z at a time (keeps registers low):
+//   out[x][z] = sum_a L[x][a] sum_c R[z][c] y[a][c] + sum_a A[x][a] y[a][z] + sum_c B[z][c] y[x][c]
+// PAR: every present term is parity-odd, so only index pairs of odd sum are visited.
+template <int DL, bool PAR, typename C>
+__device__ __forceinline__ void phase_block(const Phase& P, const C* __restrict__ M, const C* __restrict__ ys,
+                                            C* __restrict__ ks, int pb, const bool FIRST) {
+  C y[DL][DL];
+#pragma unroll
+  for (int x = 0; x < DL; ++x)
+#pragma unroll
+    for (int z = 0; z < DL; ++z) y[x][z] = ys[pb + P.po[x * DL + z]];
+  const C* Lm = M + P.offL;
+  const C* Rm = M + P.offR;
+  const C* Am = M + P.offA;
+  const C* Bm = M + P.offB;
+  const bool hasE = P.offL >= 0, hasA = P.offA >= 0, hasB = P.offB >= 0;
+#pragma unroll
+  for (int z = 0; z < DL; ++z) {
+    C o[DL];
+#pragma unroll
+    for (int x = 0; x < DL; ++x) o[x] = cmk<C>(0.0, 0.0);
+    if (hasE) {
+      C u[DL];
+#pragma unroll
+      for (int a = 0; a < DL; ++a) {
+        C acc = cmk<C>(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < DL; ++c)
+          if (!PAR || ((z + c) & 1)) acc = cfma(Rm[z * DL + c], y[a][c], acc);
+        u[a] = acc;
+      }
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int a = 0; a < DL; ++a)
+          if (!PAR || ((x + a) & 1)) o[x] = cfma(Lm[x * DL + a], u[a], o[x]);
+    }
+    if (hasA) {
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int a = 0; a < DL; ++a)
+          if (!PAR || ((x + a) & 1)) o[x] = cfma(Am[x * DL + a], y[a][z], o[x]);
+    }
+    if (hasB) {
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int c = 0; c < DL; ++c)
+          if (!PAR || ((z + c) & 1)) o[x] = cfma(Bm[z * DL + c], y[x][c], o[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < DL; ++x) {
+      const int ps = pb + P.po[x * DL + z];
+      if (FIRST) ks[ps] = o[x];
+      else { C q = ks[ps]; ks[ps] = cmk<C>(q.x + o[x].x, q.y + o[x].y); }
+    }
+  }
+}
+
+// Applies every phase of the pass to the tile in ys, leaving H y (restricted to
+// the pass's terms) in ks.  Ends with a barrier.
+template <int DL, typename C>
+__device__ __forceinline__ void pass_apply(const SlabPass& sp, const C* __restrict__ M,
+                                           const C* __restrict__ ys, C* __restrict__ ks) {
+  const int nb = sp.T / (DL * DL);
+  for (int q = 0; q < sp.nph; ++q) {
+    const Phase& P = sp.ph[q];
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+      const int pb = spos<DL>(blk_base<DL>(P, b));
+      if (P.allpar) phase_block<DL, true>(P, M, ys, ks, pb, q == 0);
+      else phase_block<DL, false>(P, M, ys, ks, pb, q == 0);
+    }
+    __syncthreads();
+  }
 }
 
 __device__ __forceinline__ long long tile_base(const SlabPass& sp, long long tile) {
@@ -62,127 +270,159 @@ __device__ __forceinline__ long long tile_base(const SlabPass& sp, long long til
   return b;
 }
 
-// H y at tile entry t, from the tile in shared memory.
-template <int DL, typename C>
-__device__ __forceinline__ C apply_tile(const SlabPass& sp, const C* __restrict__ M,
-                                        const C* __restrict__ y, int t) {
-  C acc = cmk<C>(0.0, 0.0);
-  for (int u = 0; u < sp.n1; ++u) {
-    const int k = sp.s1_k[u], sh = sp.tsh[k];
-    const int l = digit<DL>(sp, t, k);
-    const C* yb = y + (t - l * sh);
-    const C* Mr = M + sp.s1_off[u] + l * DL;
-    if ((sp.par1 >> u) & 1u) {
-#pragma unroll
-      for (int b = 0; b < DL; ++b)
-        if (((b + l) & 1) == 1) acc = cfma(Mr[b], yb[b * sh], acc);
-    } else {
-#pragma unroll
-      for (int b = 0; b < DL; ++b) acc = cfma(Mr[b], yb[b * sh], acc);
-    }
-  }
-  for (int e = 0; e < sp.ne; ++e) {
-    const int ka = sp.e_ka[e], kb = sp.e_kb[e];
-    const int sa = sp.tsh[ka], sb = sp.tsh[kb];
-    const int la = digit<DL>(sp, t, ka), lb = digit<DL>(sp, t, kb);
-    const C* yb = y + (t - la * sa - lb * sb);
-    const C* L = M + sp.e_offL[e] + la * DL;
-    const C* R = M + sp.e_offR[e] + lb * DL;
-    const bool pl = (sp.parL >> e) & 1ull, pr = (sp.parR >> e) & 1ull;
-#pragma unroll
-    for (int x = 0; x < DL; ++x) {
-      if (pl && ((x + la) & 1) == 0) continue;
-      C u = cmk<C>(0.0, 0.0);
-#pragma unroll
-      for (int z = 0; z < DL; ++z) {
-        if (pr && ((z + lb) & 1) == 0) continue;
-        u = cfma(R[z], yb[x * sa + z * sb], u);
-      }
-      acc = cfma(L[x], u, acc);
-    }
-  }
-  return acc;
-}
-
 template <typename C>
-__device__ __forceinline__ void load_common(const SlabPass& sp, const C* __restrict__ tabrow, C* M,
-                                            int* off) {
+__device__ __forceinline__ void load_common(const SlabPass& sp, const C* __restrict__ tabrow, C* M) {
   for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = tabrow[i];
-  for (int i = threadIdx.x; i < sp.T; i += blockDim.x) off[i] = sp.off[i];
   __syncthreads();
 }
 
 // KIND: 0 first partial pass (kA = k), 1 middle partial (kA += k), 2 last pass after
 // partials (k += kA then the RK4 epilogue), 3 single pass (epilogue).
-template <typename R, int DL, int STAGE, bool STORE, int KIND>
-__global__ void __launch_bounds__(kST) k_slab_fwd(SlabPass sp, const typename CT<R>::T* __restrict__ X,
-                                                  const typename CT<R>::T* __restrict__ tabrow,
-                                                  const double2* __restrict__ psi_in, double2* psi_out,
-                                                  typename CT<R>::T* __restrict__ Xn,
-                                                  typename CT<R>::T* __restrict__ Dacc,
-                                                  typename CT<R>::T* __restrict__ kA, double dt) {
+template <typename R, int DL>
+__global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 3 : 1) k_slab_fwd(SlabPass sp, const typename CT<R>::T* __restrict__ X,
+                                                     const typename CT<R>::T* __restrict__ tabrow,
+                                                     const double2* __restrict__ psi_in, double2* psi_out,
+                                                     typename CT<R>::T* __restrict__ Xn,
+                                                     typename CT<R>::T* __restrict__ Dacc,
+                                                     typename CT<R>::T* __restrict__ kA, double dt,
+                                                     const int STAGE, const bool STORE, const int KIND) {
   typedef typename CT<R>::T C;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* yt = reinterpret_cast<C*>(smraw);
-  C* M = yt + sp.T;
-  int* off = reinterpret_cast<int*>(M + sp.row);
-  load_common(sp, tabrow, M, off);
+  C* ys = reinterpret_cast<C*>(smraw);
+  C* ks = ys + spad(sp.T);
+  C* M = ks + spad(sp.T);
+  const int* __restrict__ off = sp.off;
+  load_common(sp, tabrow, M);
   const long long ntiles = (long long)sp.S * sp.ntpc;
   const R h = (R)dt;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long base = tile_base(sp, tile);
-    for (int t = threadIdx.x; t < sp.T; t += kST) yt[t] = X[base + off[t]];
+    load_tile<DL, 8>(sp, X, base, off, ys);
     __syncthreads();
-    for (int t = threadIdx.x; t < sp.T; t += kST) {
-      const C a = apply_tile<DL>(sp, M, yt, t);
-      C k = cmk<C>(a.y, -a.x);                     // -i H y
-      const long long g = base + off[t];
-      if (KIND == 0) { kA[g] = k; continue; }
-      if (KIND == 1) { C p = kA[g]; kA[g] = cmk<C>(p.x + k.x, p.y + k.y); continue; }
-      if (KIND == 2) { C p = kA[g]; k = cmk<C>(p.x + k.x, p.y + k.y); }
-      const double2 ps = psi_in[g];
-      const C pr = to_c(ps, R(0));
-      if (STAGE == 0) {
-        if (!STORE) Dacc[g] = cmk<C>(h / 6 * k.x, h / 6 * k.y);
-        Xn[g] = cmk<C>(pr.x + h / 2 * k.x, pr.y + h / 2 * k.y);
-      } else if (STAGE == 1) {
-        if (!STORE) { C d = Dacc[g]; Dacc[g] = cmk<C>(d.x + h / 3 * k.x, d.y + h / 3 * k.y); }
-        Xn[g] = cmk<C>(pr.x + h / 2 * k.x, pr.y + h / 2 * k.y);
-      } else if (STAGE == 2) {
-        if (!STORE) { C d = Dacc[g]; Dacc[g] = cmk<C>(d.x + h / 3 * k.x, d.y + h / 3 * k.y); }
-        Xn[g] = cmk<C>(pr.x + h * k.x, pr.y + h * k.y);
-      } else {
-        C d = Dacc[g];
-        R incx = d.x + h / 6 * k.x, incy = d.y + h / 6 * k.y;
-        double2 pn = make_double2(ps.x + (double)incx, ps.y + (double)incy);
-        psi_out[g] = pn;
-        Xn[g] = to_c(pn, R(0));
+    pass_apply<DL>(sp, M, ys, ks);
+    // epilogue, four entries per thread at a time so their loads are in flight together
+    constexpr int EB = 4;
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * EB) {
+      long long g[EB];
+      C k[EB], pa[EB], dd[EB];
+      double2 ps[EB];
+      bool ok[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int t = t0 + j * kST;
+        ok[j] = t < sp.T;
+        g[j] = ok[j] ? base + __ldg(off + t) : base;
+        const C a = ok[j] ? ks[spos<DL>(t)] : cmk<C>(0.0, 0.0);
+        k[j] = cmk<C>(a.y, -a.x);                   // -i H y
+        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? kA[g[j]] : cmk<C>(0.0, 0.0);
+        ps[j] = (KIND >= 2) && ok[j] ? psi_in[g[j]] : make_double2(0.0, 0.0);
+        dd[j] = (KIND >= 2) && ok[j] && !STORE && STAGE > 0 ? Dacc[g[j]] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        if (!ok[j]) continue;
+        C kk = k[j];
+        if (KIND == 0) { kA[g[j]] = kk; continue; }
+        if (KIND == 1) { kA[g[j]] = cmk<C>(pa[j].x + kk.x, pa[j].y + kk.y); continue; }
+        if (KIND == 2) kk = cmk<C>(pa[j].x + kk.x, pa[j].y + kk.y);
+        const C pr = to_c(ps[j], R(0));
+        const C d = dd[j];
+        if (STAGE == 0) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(h / 6 * kk.x, h / 6 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+        } else if (STAGE == 1) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(d.x + h / 3 * kk.x, d.y + h / 3 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+        } else if (STAGE == 2) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(d.x + h / 3 * kk.x, d.y + h / 3 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h * kk.x, pr.y + h * kk.y);
+        } else {
+          R incx = d.x + h / 6 * kk.x, incy = d.y + h / 6 * kk.y;
+          double2 pn = make_double2(ps[j].x + (double)incx, ps[j].y + (double)incy);
+          psi_out[g[j]] = pn;
+          Xn[g[j]] = to_c(pn, R(0));
+        }
       }
     }
     __syncthreads();
   }
 }
 
+// Cross-density of one slot over one d x d block (x = kbar block, y = y_s block):
+//   A (1-body on ka):  C[a][b] += sum_z conj(x[a][z]) y[b][z]
+//   B (1-body on kb):  C[c][d] += sum_x conj(x[x][c]) y[x][d]
+//   L (edge, ka):      C[a][b] += sum_z conj(x[a][z]) (y R^T)[b][z]
+//   R (edge, kb):      C[c][d] += sum_x conj(x[x][c]) (L y)[x][d]
+// With a parity-odd operator only entries with a + b odd are accumulated (the
+// others multiply zeros in the contraction).
+template <int DL, bool PAR, typename C>
+__device__ __forceinline__ void xd_first(const C (&x)[DL][DL], const C (&y)[DL][DL], C (&acc)[DL][DL]) {
+#pragma unroll
+  for (int a = 0; a < DL; ++a)
+#pragma unroll
+    for (int b = 0; b < DL; ++b) {
+      if (PAR && !((a + b) & 1)) continue;
+      C s = acc[a][b];
+#pragma unroll
+      for (int z = 0; z < DL; ++z) s = cjfma(x[a][z], y[b][z], s);
+      acc[a][b] = s;
+    }
+}
+template <int DL, bool PAR, typename C>
+__device__ __forceinline__ void xd_second(const C (&x)[DL][DL], const C (&y)[DL][DL], C (&acc)[DL][DL]) {
+#pragma unroll
+  for (int c = 0; c < DL; ++c)
+#pragma unroll
+    for (int d = 0; d < DL; ++d) {
+      if (PAR && !((c + d) & 1)) continue;
+      C s = acc[c][d];
+#pragma unroll
+      for (int z = 0; z < DL; ++z) s = cjfma(x[z][c], y[z][d], s);
+      acc[c][d] = s;
+    }
+}
+
+template <int DL, typename C>
+__device__ __forceinline__ void xd_block(const Phase& P, int type, const C* __restrict__ M,
+                                         const C (&x)[DL][DL], const C (&y)[DL][DL], C (&acc)[DL][DL]) {
+  if (type == 0) {
+    if (P.par & 4u) xd_first<DL, true>(x, y, acc); else xd_first<DL, false>(x, y, acc);
+  } else if (type == 1) {
+    if (P.par & 8u) xd_second<DL, true>(x, y, acc); else xd_second<DL, false>(x, y, acc);
+  } else if (type == 2) {
+    C u[DL][DL];
+    if (P.par & 2u) blk_right<DL, true>(M + P.offR, y, u); else blk_right<DL, false>(M + P.offR, y, u);
+    if (P.par & 1u) xd_first<DL, true>(x, u, acc); else xd_first<DL, false>(x, u, acc);
+  } else {
+    C v[DL][DL];
+#pragma unroll
+    for (int a = 0; a < DL; ++a)
+#pragma unroll
+      for (int b = 0; b < DL; ++b) v[a][b] = cmk<C>(0.0, 0.0);
+    if (P.par & 1u) blk_left_acc<DL, true>(M + P.offL, y, v); else blk_left_acc<DL, false>(M + P.offL, y, v);
+    if (P.par & 2u) xd_second<DL, true>(x, v, acc); else xd_second<DL, false>(x, v, acc);
+  }
+}
+
 // Adjoint pass: X = kbar_s tile, Y = y_s tile.  Applies A_s^dag = i H to kbar
-// (partial or with the adjoint epilogue) and accumulates the cross-densities of
-// this pass's slots, one warp per slot (kSPW slots per warp), persisting across
-// tiles; one fixed-order reduction at the end.
-template <typename R, int DL, int STAGE, int KIND>
-__global__ void __launch_bounds__(kST) k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X,
-                                                  const typename CT<R>::T* __restrict__ Y,
-                                                  const typename CT<R>::T* __restrict__ tabrow,
-                                                  double2* __restrict__ pbar,
-                                                  typename CT<R>::T* __restrict__ Xn,
-                                                  typename CT<R>::T* __restrict__ Db,
-                                                  typename CT<R>::T* __restrict__ yA, double dt,
-                                                  XArgs xa) {
+// (partial, or with the adjoint epilogue) with the register-blocked phases, and
+// accumulates the cross-densities of this pass's slots: warp w owns slots w and
+// w + 8, its lanes walk the blocks of the slot's phase, and the d x d partial sums
+// stay in registers across all tiles; one fixed-order reduction at the end.
+template <typename R, int DL>
+__global__ void __launch_bounds__(kST, 1)
+k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename CT<R>::T* __restrict__ Y,
+           const typename CT<R>::T* __restrict__ tabrow, double2* __restrict__ pbar,
+           typename CT<R>::T* __restrict__ Xn, typename CT<R>::T* __restrict__ Db,
+           typename CT<R>::T* __restrict__ yA, double dt, XArgs xa, const int STAGE, const int KIND) {
   typedef typename CT<R>::T C;
   extern __shared__ __align__(16) unsigned char smraw[];
-  C* xt = reinterpret_cast<C*>(smraw);
-  C* yt = xt + sp.T;
-  C* M = yt + sp.T;
-  int* off = reinterpret_cast<int*>(M + sp.row);
-  load_common(sp, tabrow, M, off);
+  C* xs = reinterpret_cast<C*>(smraw);
+  C* ys = xs + spad(sp.T);
+  C* ks = ys + spad(sp.T);
+  C* M = ks + spad(sp.T);
+  const int* __restrict__ off = sp.off;
+  load_common(sp, tabrow, M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   C acc[kSPW][DL][DL];
 #pragma unroll
@@ -193,74 +433,75 @@ __global__ void __launch_bounds__(kST) k_slab_adj(SlabPass sp, const typename CT
       for (int b = 0; b < DL; ++b) acc[s][a][b] = cmk<C>(0.0, 0.0);
   const long long ntiles = (long long)sp.S * sp.ntpc;
   const R h = (R)dt;
-  const int nf = sp.T / DL;
+  const int nb = sp.T / (DL * DL);
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long base = tile_base(sp, tile);
-    for (int t = threadIdx.x; t < sp.T; t += kST) {
-      const long long g = base + off[t];
-      xt[t] = X[g];
-      yt[t] = Y[g];
-    }
+    load_tile<DL, 8>(sp, X, base, off, xs);
+    load_tile<DL, 8>(sp, Y, base, off, ys);
     __syncthreads();
-    for (int t = threadIdx.x; t < sp.T; t += kST) {
-      const C a = apply_tile<DL>(sp, M, xt, t);
-      C yb = cmk<C>(-a.y, a.x);                     // i H kbar
-      const long long g = base + off[t];
-      if (KIND == 0) { yA[g] = yb; continue; }
-      if (KIND == 1) { C p = yA[g]; yA[g] = cmk<C>(p.x + yb.x, p.y + yb.y); continue; }
-      if (KIND == 2) { C p = yA[g]; yb = cmk<C>(p.x + yb.x, p.y + yb.y); }
-      const double2 pb = pbar[g];
-      const C pr = to_c(pb, R(0));
-      if (STAGE == 3) {
-        Db[g] = yb;
-        Xn[g] = cmk<C>(h / 3 * pr.x + h * yb.x, h / 3 * pr.y + h * yb.y);
-      } else if (STAGE == 2) {
-        C d = Db[g];
-        Db[g] = cmk<C>(d.x + yb.x, d.y + yb.y);
-        Xn[g] = cmk<C>(h / 3 * pr.x + h / 2 * yb.x, h / 3 * pr.y + h / 2 * yb.y);
-      } else if (STAGE == 1) {
-        C d = Db[g];
-        Db[g] = cmk<C>(d.x + yb.x, d.y + yb.y);
-        Xn[g] = cmk<C>(h / 6 * pr.x + h / 2 * yb.x, h / 6 * pr.y + h / 2 * yb.y);
-      } else {
-        C d = Db[g];
-        double2 pn = make_double2(pb.x + (double)(d.x + yb.x), pb.y + (double)(d.y + yb.y));
-        pbar[g] = pn;
-        C q = to_c(pn, R(0));
-        Xn[g] = cmk<C>(h / 6 * q.x, h / 6 * q.y);
+    pass_apply<DL>(sp, M, xs, ks);
+    constexpr int EB = 4;
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * EB) {
+      long long g[EB];
+      C yb[EB], pa[EB], dd[EB];
+      double2 pbv[EB];
+      bool ok[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int t = t0 + j * kST;
+        ok[j] = t < sp.T;
+        g[j] = ok[j] ? base + __ldg(off + t) : base;
+        const C a = ok[j] ? ks[spos<DL>(t)] : cmk<C>(0.0, 0.0);
+        yb[j] = cmk<C>(-a.y, a.x);                  // i H kbar
+        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? yA[g[j]] : cmk<C>(0.0, 0.0);
+        pbv[j] = (KIND >= 2) && ok[j] ? pbar[g[j]] : make_double2(0.0, 0.0);
+        dd[j] = (KIND >= 2) && ok[j] && STAGE < 3 ? Db[g[j]] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        if (!ok[j]) continue;
+        C y = yb[j];
+        if (KIND == 0) { yA[g[j]] = y; continue; }
+        if (KIND == 1) { yA[g[j]] = cmk<C>(pa[j].x + y.x, pa[j].y + y.y); continue; }
+        if (KIND == 2) y = cmk<C>(pa[j].x + y.x, pa[j].y + y.y);
+        const C pr = to_c(pbv[j], R(0));
+        const C d = dd[j];
+        if (STAGE == 3) {
+          Db[g[j]] = y;
+          Xn[g[j]] = cmk<C>(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
+        } else if (STAGE == 2) {
+          Db[g[j]] = cmk<C>(d.x + y.x, d.y + y.y);
+          Xn[g[j]] = cmk<C>(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
+        } else if (STAGE == 1) {
+          Db[g[j]] = cmk<C>(d.x + y.x, d.y + y.y);
+          Xn[g[j]] = cmk<C>(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
+        } else {
+          double2 pn = make_double2(pbv[j].x + (double)(d.x + y.x), pbv[j].y + (double)(d.y + y.y));
+          pbar[g[j]] = pn;
+          C q = to_c(pn, R(0));
+          Xn[g[j]] = cmk<C>(h / 6 * q.x, h / 6 * q.y);
+        }
       }
     }
     // cross-densities of this warp's slots over the tile
 #pragma unroll
     for (int s = 0; s < kSPW; ++s) {
       const int slot = warp + s * (kST / 32);
-      if (slot >= sp.nx) continue;
-      const int k = sp.x_k[slot], sh = sp.tsh[k];
-      const int k2 = sp.x_k2[slot];
-      for (int f = lane; f < nf; f += 32) {
-        const int t0 = (f / sh) * (DL * sh) + (f % sh);
-        C xv[DL], yv[DL];
-        if (k2 < 0) {
+      if (slot >= sp.nx) continue;                  // warp-uniform
+      const Phase& P = sp.ph[sp.x_ph[slot]];
+      const int type = sp.x_type[slot];
+      for (int b = lane; b < nb; b += 32) {
+        const int pb = spos<DL>(blk_base<DL>(P, b));
+        C xv[DL][DL], yv[DL][DL];
 #pragma unroll
-          for (int a = 0; a < DL; ++a) { xv[a] = xt[t0 + a * sh]; yv[a] = yt[t0 + a * sh]; }
-        } else {
-          const int sh2 = sp.tsh[k2];
-          const int l2 = digit<DL>(sp, t0, k2);
-          const C* O2 = M + sp.x_off2[slot] + l2 * DL;
-          const C* yb = yt + (t0 - l2 * sh2);
+        for (int x = 0; x < DL; ++x)
 #pragma unroll
-          for (int a = 0; a < DL; ++a) {
-            xv[a] = xt[t0 + a * sh];
-            C u = cmk<C>(0.0, 0.0);
-#pragma unroll
-            for (int c = 0; c < DL; ++c) u = cfma(O2[c], yb[a * sh + c * sh2], u);
-            yv[a] = u;
+          for (int z = 0; z < DL; ++z) {
+            const int ps = pb + P.po[x * DL + z];
+            xv[x][z] = xs[ps];
+            yv[x][z] = ys[ps];
           }
-        }
-#pragma unroll
-        for (int a = 0; a < DL; ++a)
-#pragma unroll
-          for (int b = 0; b < DL; ++b) acc[s][a][b] = cjfma(xv[a], yv[b], acc[s][a][b]);
+        xd_block<DL>(P, type, M, xv, yv, acc[s]);
       }
     }
     __syncthreads();
@@ -461,15 +702,14 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
     sp.n1 = 0;
     sp.par1 = 0;
     sp.nx = 0;
+    int s1_global[SG_MAXQ], e_global[SG_MAXEDGE];
     for (int u = 0; u < p.n1; ++u) {
       if (slot_group[u] != g) continue;
       const int j = sp.n1++;
       sp.s1_k[j] = local[p.s1_mode[u]];
       sp.s1_off[j] = p.s1_off[u];
+      s1_global[j] = u;
       if ((p.par1 >> u) & 1u) sp.par1 |= 1u << j;
-      if (sp.nx >= kMaxX) { delete h; return nullptr; }
-      sp.x_k[sp.nx] = local[p.s1_mode[u]]; sp.x_k2[sp.nx] = -1; sp.x_off2[sp.nx] = 0; sp.x_gslot[sp.nx] = u;
-      ++sp.nx;
     }
     sp.ne = 0;
     sp.parL = sp.parR = 0;
@@ -482,13 +722,84 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
       sp.e_offR[j] = p.e_offR[e];
       if ((p.parL >> e) & 1ull) sp.parL |= 1ull << j;
       if ((p.parR >> e) & 1ull) sp.parR |= 1ull << j;
-      if (sp.nx + 2 > kMaxX) { delete h; return nullptr; }
-      sp.x_k[sp.nx] = local[p.e_a[e]]; sp.x_k2[sp.nx] = local[p.e_b[e]]; sp.x_off2[sp.nx] = p.e_offR[e];
-      sp.x_gslot[sp.nx] = p.n1 + e;
-      ++sp.nx;
-      sp.x_k[sp.nx] = local[p.e_b[e]]; sp.x_k2[sp.nx] = local[p.e_a[e]]; sp.x_off2[sp.nx] = p.e_offL[e];
-      sp.x_gslot[sp.nx] = p.n1 + p.ne + e;
-      ++sp.nx;
+      e_global[j] = e;
+    }
+    // register-blocked phases: one per edge, 1-body terms fused into the first
+    // phase holding their digit, or a phase of their own
+    if (sp.ng < 2) { delete h; return nullptr; }
+    sp.nph = 0;
+    auto new_phase = [&](int ka, int kb) -> Phase* {
+      if (sp.nph >= kMaxPhase) return nullptr;
+      Phase& P = sp.ph[sp.nph++];
+      P = Phase{};
+      P.ka = ka; P.kb = kb;
+      P.offL = P.offR = P.offA = P.offB = -1;
+      P.ge = P.gA = P.gB = -1;
+      P.par = 0;
+      // other digits: the lowest even-exponent, the lowest odd-exponent, then the rest
+      std::vector<int> others;
+      for (int k = sp.ng - 1; k >= 0; --k) if (k != ka && k != kb) others.push_back(k);
+      std::vector<int> ord;
+      auto expo = [&](int k) { return sp.ng - 1 - k; };
+      for (int k : others) if (expo(k) % 2 == 0) { ord.push_back(k); break; }
+      for (int k : others) if (expo(k) % 2 == 1) { ord.push_back(k); break; }
+      for (int k : others) if (std::find(ord.begin(), ord.end(), k) == ord.end()) ord.push_back(k);
+      P.no = (int)ord.size();
+      for (int j = 0; j < P.no; ++j) P.ost[j] = sp.tsh[ord[j]];
+      return &P;
+    };
+    for (int j = 0; j < sp.ne; ++j) {
+      Phase* P = new_phase(sp.e_ka[j], sp.e_kb[j]);
+      if (!P) { delete h; return nullptr; }
+      P->offL = sp.e_offL[j];
+      P->offR = sp.e_offR[j];
+      P->ge = e_global[j];
+      if ((sp.parL >> j) & 1ull) P->par |= 1u;
+      if ((sp.parR >> j) & 1ull) P->par |= 2u;
+    }
+    for (int j = 0; j < sp.n1; ++j) {
+      const int k = sp.s1_k[j];
+      const bool par = (sp.par1 >> j) & 1u;
+      bool done = false;
+      for (int q = 0; q < sp.nph && !done; ++q) {
+        Phase& P = sp.ph[q];
+        if (P.ka == k && P.offA < 0) { P.offA = sp.s1_off[j]; P.gA = s1_global[j]; if (par) P.par |= 4u; done = true; }
+        else if (P.kb == k && P.offB < 0) { P.offB = sp.s1_off[j]; P.gB = s1_global[j]; if (par) P.par |= 8u; done = true; }
+      }
+      if (!done) {
+        const int other = (k == sp.ng - 1) ? sp.ng - 2 : sp.ng - 1;
+        Phase* P = new_phase(k, other);
+        if (!P) { delete h; return nullptr; }
+        P->offA = sp.s1_off[j];
+        P->gA = s1_global[j];
+        if (par) P->par |= 4u;
+      }
+    }
+    for (int q = 0; q < sp.nph; ++q) {
+      Phase& P = sp.ph[q];
+      const int sa = sp.tsh[P.ka], sb = sp.tsh[P.kb];
+      const bool pw2 = DL == 2 || DL == 4;
+      for (int x = 0; x < DL; ++x)
+        for (int z = 0; z < DL; ++z) {
+          const int o = x * sa + z * sb;
+          P.po[x * DL + z] = pw2 ? o + (o >> 4) + (o >> 8) : o;
+        }
+      unsigned need = (P.offL >= 0 ? 3u : 0u) | (P.offA >= 0 ? 4u : 0u) | (P.offB >= 0 ? 8u : 0u);
+      P.allpar = (P.par & need) == need ? 1 : 0;
+    }
+    // cross-density slots, phase by phase
+    for (int q = 0; q < sp.nph; ++q) {
+      const Phase& P = sp.ph[q];
+      auto add = [&](int type, int gslot) {
+        if (sp.nx >= kMaxX) return false;
+        sp.x_ph[sp.nx] = q; sp.x_type[sp.nx] = type; sp.x_gslot[sp.nx] = gslot; ++sp.nx;
+        return true;
+      };
+      bool ok = true;
+      if (P.offL >= 0) { ok = ok && add(2, p.n1 + P.ge); ok = ok && add(3, p.n1 + p.ne + P.ge); }
+      if (P.offA >= 0) ok = ok && add(0, P.gA);
+      if (P.offB >= 0) ok = ok && add(1, P.gB);
+      if (!ok) { delete h; return nullptr; }
     }
     // offsets of the tile entries
     std::vector<int> off(sp.T);
@@ -500,14 +811,13 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
     if (cudaMalloc(&h->off_dev[g], sp.T * sizeof(int)) != cudaSuccess) { slab_plan_destroy(h); return nullptr; }
     cudaMemcpyAsync(h->off_dev[g], off.data(), sp.T * sizeof(int), cudaMemcpyHostToDevice, st);
     sp.off = h->off_dev[g];
-    h->sm_fwd[g] = sp.T * csz + p.row * csz + sp.T * sizeof(int);
-    h->sm_adj[g] = std::max(2 * sp.T * csz + p.row * csz + sp.T * sizeof(int),
-                            (size_t)kMaxX * DL * DL * sizeof(double2));
+    h->sm_fwd[g] = 2 * spad(sp.T) * csz + p.row * csz;
+    h->sm_adj[g] = std::max(3 * spad(sp.T) * csz + p.row * csz, (size_t)kMaxX * DL * DL * sizeof(double2));
     if (h->sm_adj[g] > 200 * 1024) { slab_plan_destroy(h); return nullptr; }
   }
   long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
-  h->grid_fwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 3 : 2));
-  h->grid_adj = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
+  h->grid_fwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 3 : 1));
+  h->grid_adj = (int)std::min<long long>(ntiles, 152ll);
   cudaStreamSynchronize(st);
   return h;
 }
@@ -538,50 +848,53 @@ void slab_from_internal(const SlabPlanHost* h, const double2* in, double2* api, 
 // ---------------------------------------------------------------------------
 namespace {
 
-template <typename R, int DL, int STAGE, bool STORE, int KIND>
+template <typename R, int DL>
 void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, const double2* pin,
-                double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st) {
+                double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st, int stage,
+                bool store, int kind) {
   typedef typename CT<R>::T C;
-  auto kern = k_slab_fwd<R, DL, STAGE, STORE, KIND>;
+  auto kern = k_slab_fwd<R, DL>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   kern<<<h->grid_fwd, kST, h->sm_fwd[g], st>>>(h->pass[g], (const C*)X, (const C*)row, pin, pout,
-                                                 (C*)Xn, (C*)Dacc, (C*)kA, dt);
+                                                 (C*)Xn, (C*)Dacc, (C*)kA, dt, stage, store, kind);
 }
 
-template <typename R, int DL, int STAGE, bool STORE>
-void fwd_stage(const SlabPlanHost* h, const void* X, const void* row, const double2* pin, double2* pout,
-               void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st) {
+// One RK4 stage: the partial passes accumulate into kA, the last one applies the epilogue.
+template <typename R, int DL>
+void fwd_stage(const SlabPlanHost* h, int stage, bool store, const void* X, const void* row,
+               const double2* pin, double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st) {
   if (h->np == 1) {
-    fwd_launch<R, DL, STAGE, STORE, 3>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st);
+    fwd_launch<R, DL>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 3);
     return;
   }
-  fwd_launch<R, DL, STAGE, STORE, 0>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st);
-  for (int g = 1; g < h->np - 1; ++g) fwd_launch<R, DL, STAGE, STORE, 1>(h, g, X, row, pin, pout, Xn, Dacc, kA, dt, st);
-  fwd_launch<R, DL, STAGE, STORE, 2>(h, h->np - 1, X, row, pin, pout, Xn, Dacc, kA, dt, st);
+  fwd_launch<R, DL>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 0);
+  for (int g = 1; g < h->np - 1; ++g) fwd_launch<R, DL>(h, g, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 1);
+  fwd_launch<R, DL>(h, h->np - 1, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 2);
 }
 
-template <typename R, int DL, int STAGE, int KIND>
+template <typename R, int DL>
 void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, const void* row,
-                double2* pbar, void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st) {
+                double2* pbar, void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st,
+                int stage, int kind) {
   typedef typename CT<R>::T C;
-  auto kern = k_slab_adj<R, DL, STAGE, KIND>;
+  auto kern = k_slab_adj<R, DL>;
   static bool attr = false;
   if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
   kern<<<h->grid_adj, kST, h->sm_adj[g], st>>>(h->pass[g], (const C*)X, (const C*)Y, (const C*)row, pbar,
-                                                 (C*)Xn, (C*)Db, (C*)yA, dt, xa);
+                                                 (C*)Xn, (C*)Db, (C*)yA, dt, xa, stage, kind);
 }
 
-template <typename R, int DL, int STAGE>
-void adj_stage(const SlabPlanHost* h, const void* X, const void* Y, const void* row, double2* pbar,
+template <typename R, int DL>
+void adj_stage(const SlabPlanHost* h, int stage, const void* X, const void* Y, const void* row, double2* pbar,
                void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st) {
   if (h->np == 1) {
-    adj_launch<R, DL, STAGE, 3>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st);
+    adj_launch<R, DL>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 3);
     return;
   }
-  adj_launch<R, DL, STAGE, 0>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st);
-  for (int g = 1; g < h->np - 1; ++g) adj_launch<R, DL, STAGE, 1>(h, g, X, Y, row, pbar, Xn, Db, yA, dt, xa, st);
-  adj_launch<R, DL, STAGE, 2>(h, h->np - 1, X, Y, row, pbar, Xn, Db, yA, dt, xa, st);
+  adj_launch<R, DL>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 0);
+  for (int g = 1; g < h->np - 1; ++g) adj_launch<R, DL>(h, g, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 1);
+  adj_launch<R, DL>(h, h->np - 1, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 2);
 }
 
 template <typename R>
@@ -594,10 +907,10 @@ template <typename R, int DL>
 int fwd_step_t(const SlabPlanHost* h, const void* tab, int step, const double2* pin, double2* pout,
                void*& X, void*& Xo, void* Dacc, void* kA, double dt, cudaStream_t st) {
   const int row = h->pass[0].row;
-  fwd_stage<R, DL, 0, false>(h, X, row_of<R>(tab, row, step, 0), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
-  fwd_stage<R, DL, 1, false>(h, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
-  fwd_stage<R, DL, 2, false>(h, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
-  fwd_stage<R, DL, 3, false>(h, X, row_of<R>(tab, row, step, 2), pin, pout, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 0, false, X, row_of<R>(tab, row, step, 0), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 1, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 2, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 3, false, X, row_of<R>(tab, row, step, 2), pin, pout, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
   return 4 * h->np;
 }
 
@@ -605,9 +918,9 @@ template <typename R, int DL>
 int fwd_store_t(const SlabPlanHost* h, const void* tab, int step, const double2* psi, void* const Y[4],
                 void* kA, double dt, cudaStream_t st) {
   const int row = h->pass[0].row;
-  fwd_stage<R, DL, 0, true>(h, Y[0], row_of<R>(tab, row, step, 0), psi, nullptr, Y[1], nullptr, kA, dt, st);
-  fwd_stage<R, DL, 1, true>(h, Y[1], row_of<R>(tab, row, step, 1), psi, nullptr, Y[2], nullptr, kA, dt, st);
-  fwd_stage<R, DL, 2, true>(h, Y[2], row_of<R>(tab, row, step, 1), psi, nullptr, Y[3], nullptr, kA, dt, st);
+  fwd_stage<R, DL>(h, 0, true, Y[0], row_of<R>(tab, row, step, 0), psi, nullptr, Y[1], nullptr, kA, dt, st);
+  fwd_stage<R, DL>(h, 1, true, Y[1], row_of<R>(tab, row, step, 1), psi, nullptr, Y[2], nullptr, kA, dt, st);
+  fwd_stage<R, DL>(h, 2, true, Y[2], row_of<R>(tab, row, step, 1), psi, nullptr, Y[3], nullptr, kA, dt, st);
   return 3 * h->np;
 }
 
@@ -624,12 +937,12 @@ int adj_step_t(const SlabPlanHost* h, const void* tab, int step, void* const Y[4
     xa.ph = ph + (size_t)xa.q * sumd;
   };
   set(2);
-  adj_stage<R, DL, 3>(h, KB, Y[3], row_of<R>(tab, row, step, 2), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  adj_stage<R, DL>(h, 3, KB, Y[3], row_of<R>(tab, row, step, 2), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
   set(1);
-  adj_stage<R, DL, 2>(h, KB, Y[2], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
-  adj_stage<R, DL, 1>(h, KB, Y[1], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  adj_stage<R, DL>(h, 2, KB, Y[2], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  adj_stage<R, DL>(h, 1, KB, Y[1], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
   set(0);
-  adj_stage<R, DL, 0>(h, KB, Y[0], row_of<R>(tab, row, step, 0), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  adj_stage<R, DL>(h, 0, KB, Y[0], row_of<R>(tab, row, step, 0), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
   return 4 * h->np;
 }
 
