@@ -171,6 +171,22 @@ typedef struct {
  * also supplies the initial states. */
 sg_status sg_evolve(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
 
+/* Same evolution as sg_evolve, for callers that cannot allocate device memory
+ * during the call: a program whose GPU memory belongs to another allocator (for
+ * example a framework's caching allocator that has reserved the device), or a
+ * latency-bound loop that cannot afford cudaMalloc's implicit synchronisation.
+ * The paper has no counterpart; this is an interface of this library only.
+ * Every per-call buffer lives in one array of 32 MiB compiled into the library,
+ * held on every GPU that loads the library until the process exits; the call
+ * makes no cudaMalloc or cudaFree (sg_prepare, which allocates the system's own
+ * tables, must have run before).  The first call on a device looks up the array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the one array and it keeps the last call's contents: calls that overlap
+ * on the GPU (on different streams or contexts) race.  Uses the generic gather
+ * kernels.  Returns SG_E_INVALID with the needed size when the evolution needs
+ * more than the 32 MiB (stage tables of 3 T/dt rows plus three D x S slabs). */
+sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
+
 /* Evolve the columns named by opts->col_index and reduce them to fidelities.
  * target_re_im: host, Dc x Dc complex (Dc = 2^Nq), row-major (re, im); column j is
  * the target image of computational state j.  Columns whose initial state is not

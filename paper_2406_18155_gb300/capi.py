@@ -79,6 +79,7 @@ SIGNATURES = {
     "sg_get_spectrum": (_I, [_P, _I, _PD, _PD, _PD]),
     "sg_dims": (_I, [_P, C.POINTER(C.c_longlong), _PI]),
     "sg_evolve": (_I, [_P, C.POINTER(sg_evolve_opts), _P]),
+    "sg_evolve_noalloc": (_I, [_P, C.POINTER(sg_evolve_opts), _P]),
     "sg_fidelity": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _PD, _PD]),
     "sg_fidelity_grad": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I]),
     "sg_last_stats": (_I, [_P, _PD]),

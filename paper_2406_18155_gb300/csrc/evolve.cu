@@ -25,6 +25,8 @@
 #include <cstring>
 #include <algorithm>
 #include <chrono>
+#include <cstdio>
+#include <mutex>
 
 namespace {
 
@@ -1463,4 +1465,133 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   sv.kt.finish(sys->ktimes);
   sys->last_stats[4] = sv.launches + (double)(sv.kt.total[0] + sv.kt.total[1] + sv.kt.total[2]);
   return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Evolution without allocation (sg_evolve_noalloc)
+// ---------------------------------------------------------------------------
+// Some callers cannot allocate device memory when they evolve: a host program
+// whose GPU memory is owned by another allocator (for example a framework's
+// caching allocator that has reserved the device), or a latency-bound control
+// loop that cannot afford cudaMalloc's implicit synchronisation.  For them this
+// entry point keeps every per-call buffer (drive data, stage tables, stage slabs)
+// in one fixed array compiled into the library.  Every GPU that loads the
+// library holds the array until the process exits.
+namespace {
+constexpr size_t kNoAllocScratchBytes = 32ull << 20;   // 32 MiB
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of the scratch array on the context's device.  The host-side
+// symbol is only a stand-in, so the address is looked up once per device (with
+// that device current) and cached.
+static sg_status noalloc_scratch(sg_ctx* ctx, unsigned char** out) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  const int dev = ctx->device;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return sg_fail(ctx, SG_E_UNSUPPORTED, "device index beyond 63");
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return sg_fail(ctx, SG_E_CUDA, std::string("cudaGetSymbolAddress of the scratch array: ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_ptr[dev]);
+  return SG_OK;
+}
+
+template <typename R>
+static sg_status noalloc_run(sg_system* sys, const sg_evolve_opts* o, double2* psi) {
+  typedef typename CT<R>::T C;
+  sg_ctx* ctx = sys->ctx;
+  Solve sv;
+  sg_status rc = build_setup(sys, o, sv.s);
+  if (rc != SG_OK) return rc;
+  Setup& s = sv.s;
+  if (o->col_index)
+    for (int c = 0; c < s.S; ++c)
+      if (o->col_index[c] < 0 || o->col_index[c] >= s.D) return sg_fail(ctx, SG_E_INVALID, "col_index out of range");
+  // layout of the scratch array
+  size_t used = 0;
+  auto carve = [&](size_t bytes) {
+    const size_t at = used;
+    used = (used + std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t nst = 3ull * s.N;
+  const long long n = s.D * s.S;
+  const size_t o_drv = carve(std::max(1, s.K) * sizeof(DriveDev));
+  const size_t o_amp = carve(std::max<size_t>(1, s.amps.size()) * sizeof(double));
+  const size_t o_E = carve(s.sumd * sizeof(double));
+  const size_t o_opd = carve(s.opdflat.size() * sizeof(double2));
+  const size_t o_coef = carve(nst * std::max(1, s.K) * sizeof(double));
+  const size_t o_ph = carve(nst * s.sumd * sizeof(double2));
+  const size_t o_tab = carve(nst * s.p.row * sizeof(double2));
+  const size_t o_tab32 = carve(sizeof(R) == 4 ? nst * s.p.row * sizeof(float2) : 1);
+  const size_t o_cols = carve(s.S * sizeof(long long));
+  const size_t o_X = carve(n * sizeof(C));
+  const size_t o_Xo = carve(n * sizeof(C));
+  const size_t o_D = carve(n * sizeof(C));
+  if (used > kNoAllocScratchBytes) {
+    char msg[200];
+    std::snprintf(msg, sizeof msg,
+                  "this evolution needs %.1f MiB of scratch; sg_evolve_noalloc has a fixed %zu MiB "
+                  "(use sg_evolve, or fewer steps, columns or levels)",
+                  used / 1048576.0, kNoAllocScratchBytes >> 20);
+    return sg_fail(ctx, SG_E_INVALID, msg);
+  }
+  SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  unsigned char* base = nullptr;
+  rc = noalloc_scratch(ctx, &base);
+  if (rc != SG_OK) return rc;
+  cudaStream_t st = ctx->stream;
+  sv.drives_dev = reinterpret_cast<DriveDev*>(base + o_drv);
+  sv.amps_dev = reinterpret_cast<double*>(base + o_amp);
+  sv.E_dev = reinterpret_cast<double*>(base + o_E);
+  sv.opd_dev = reinterpret_cast<double2*>(base + o_opd);
+  sv.coef = reinterpret_cast<double*>(base + o_coef);
+  sv.ph = reinterpret_cast<double2*>(base + o_ph);
+  sv.tab = reinterpret_cast<double2*>(base + o_tab);
+  sv.tab32 = sizeof(R) == 4 ? reinterpret_cast<float2*>(base + o_tab32) : nullptr;
+  long long* cols = reinterpret_cast<long long*>(base + o_cols);
+  C* X = reinterpret_cast<C*>(base + o_X);
+  C* Xo = reinterpret_cast<C*>(base + o_Xo);
+  C* Dacc = reinterpret_cast<C*>(base + o_D);
+  if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.drives_dev, s.drives.data(), s.K * sizeof(DriveDev), cudaMemcpyHostToDevice, st));
+  if (!s.amps.empty()) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.amps_dev, s.amps.data(), s.amps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.E_dev, s.Eflat.data(), s.sumd * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.opd_dev, s.opdflat.data(), s.opdflat.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+  if (o->col_index)
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols, o->col_index, s.S * sizeof(long long), cudaMemcpyHostToDevice, st));
+  TabArgs ta = s.ta;
+  ta.drives = sv.drives_dev; ta.amps = sv.amps_dev; ta.E = sv.E_dev; ta.opd = sv.opd_dev;
+  ta.coef = sv.coef; ta.ph = sv.ph; ta.tab = sv.tab; ta.tab32 = sv.tab32;
+  s.ta = ta;
+  // every scratch buffer below is fully written before it is read, so nothing is cleared
+  k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
+  if (o->col_index) k_init_cols<<<grid_for(n), kT, 0, st>>>(psi, s.D, s.S, cols);
+  sv.mixed = sizeof(R) == 4;
+  sv.psi = psi;
+  k_cast<R><<<grid_for(n), kT, 0, st>>>(psi, X, n, 1.0);
+  for (int step = 0; step < s.N; ++step) fwd_step<R>(sv, st, step, psi, psi, X, Xo, Dacc);
+  if (o->frame == SG_FRAME_INTERACTION)
+    k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), psi);
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  return SG_OK;
+}
+
+extern "C" sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev) {
+  if (!sys) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(sys->ctx->mu);
+  sg_ctx* ctx = sys->ctx;
+  if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
+  if (!psi_dev) return sg_fail(ctx, SG_E_INVALID, "psi_dev is NULL");
+  if (!opts) return sg_fail(ctx, SG_E_INVALID, "null options");
+  double2* psi = static_cast<double2*>(psi_dev);
+  return opts->precision == SG_MIXED ? noalloc_run<float>(sys, opts, psi) : noalloc_run<double>(sys, opts, psi);
 }
