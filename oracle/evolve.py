@@ -204,11 +204,18 @@ def adjoint_gradient(wl, kind=None, nsteps=None):
     sys = OracleSystem(wl)
     kind = kind or wl["fid_kind"]
     N = sys.N if nsteps is None else nsteps
-    dt = sys.dt
     psi0 = initial_columns(sys, wl["col_index"])
     psiT, hist = rk4_evolve(sys, psi0, N, store=True)
     psi_lab = frame_epilogue(sys, psiT, N)
     F, bar_lab = fidelity_and_costate(sys, psi_lab, kind)
+    grad, prms = adjoint_from_costate(sys, hist, psi_lab, bar_lab, N)
+    return F, grad, prms
+
+
+def adjoint_from_costate(sys, hist, psi_lab, bar_lab, N):
+    """Pull a lab-frame co-state back through the frame epilogue and N RK4 steps:
+    returns (sum over stages of Re <kbar_s, dA_s/dtheta y_s> + the frame term, params)."""
+    dt = sys.dt
     prms = sys.param_list()
     grad = np.zeros(len(prms))
     # frame epilogue: psi_lab = Phi psi_I, Phi = exp(-i Hd T)
@@ -250,7 +257,7 @@ def adjoint_gradient(wl, kind=None, nsteps=None):
             grad[p] += np.real(np.vdot(kb1, dA1 @ y1) + np.vdot(kb2, dA2 @ y2)
                                + np.vdot(kb3, dA2 @ y3) + np.vdot(kb4, dA4 @ y4))
         bar = bar + yb2 + yb3 + yb4 + A1.conj().T @ kb1
-    return F, grad, prms
+    return grad, prms
 
 
 # ----------------------------------------------------------------------------

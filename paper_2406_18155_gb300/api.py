@@ -62,7 +62,7 @@ def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, n
         o.ncols = keep.size
         o.col_index = keep.ctypes.data_as(C.POINTER(C.c_longlong))
     else:
-        o.ncols = int(ncols)
+        o.ncols = int(ncols or 0)
         o.col_index = None
     return o, keep
 
@@ -231,3 +231,70 @@ def workload_fidelity(ctx, wl, precision="mixed", grad=False, ckpt=0):
     Fa, Fs, U = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision=precision,
                            frame=wl.get("frame", "interaction"))
     return s, (Fa, Fs), U
+
+
+class Server:
+    """Continuous-batching server (sg_server_*): requests are admitted by device
+    memory and free slots, and run concurrently on the slots' streams."""
+
+    def __init__(self, ctx, mem_budget_bytes, max_slots):
+        self.ctx = ctx
+        h = C.c_void_p()
+        check(lib().sg_server_create(ctx.h, C.c_size_t(int(mem_budget_bytes)), int(max_slots),
+                                     C.byref(h)), ctx.h)
+        self.h = h
+        self._keep = {}
+
+    def submit(self, system, T, dt, target, col_index=None, kind="avg", precision="mixed",
+               want_grad=True):
+        r = capi.sg_request()
+        r.sys = system.h
+        o, keep = evolve_opts(T, dt, precision, "interaction", col_index, ncols=0)
+        r.opts = o
+        tg = _c128_pairs(target)
+        r.target_re_im = _dptr(tg)
+        r.kind = _KIND[kind]
+        r.want_grad = 1 if want_grad else 0
+        t = C.c_uint64()
+        check(lib().sg_server_submit(self.h, C.byref(r), C.byref(t)), self.ctx.h)
+        self._keep[t.value] = (system, keep, tg)
+        return t.value
+
+    def _result(self, res):
+        out = {"status": res.status, "F": (res.F[0], res.F[1]), "submit_s": res.submit_s,
+               "start_s": res.start_s, "done_s": res.done_s}
+        out["grad_pulse"] = np.array([res.grad_pulse[i] for i in range(res.n_pulse)])
+        out["grad_ham"] = np.array([res.grad_ham[i] for i in range(res.n_ham)])
+        return out
+
+    def poll(self, ticket):
+        res = capi.sg_result()
+        rc = lib().sg_server_poll(self.h, C.c_uint64(ticket), C.byref(res))
+        if rc == capi.SG_E_PENDING:
+            return None
+        check(rc, self.ctx.h)
+        return self._result(res)
+
+    def wait(self, ticket):
+        res = capi.sg_result()
+        check(lib().sg_server_wait(self.h, C.c_uint64(ticket), C.byref(res)), self.ctx.h)
+        return self._result(res)
+
+    def cancel(self, ticket):
+        return lib().sg_server_cancel(self.h, C.c_uint64(ticket))
+
+    def stats(self):
+        st = capi.sg_stats()
+        check(lib().sg_server_stats(self.h, C.byref(st)), self.ctx.h)
+        return {f: getattr(st, f) for f, _ in capi.sg_stats._fields_}
+
+    def close(self):
+        if self.h:
+            lib().sg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

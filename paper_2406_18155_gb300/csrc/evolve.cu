@@ -696,19 +696,37 @@ struct DevBuf {
   ~DevBuf() { if (p) cudaFree(p); }
 };
 
+// Per-solve device buffers, stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// solve's stream), so solves on different streams never synchronise the device
+// through allocation.  The device's default pool keeps freed memory for reuse.
 struct Arena {
   std::vector<void*> ptrs;
   size_t bytes = 0;
-  ~Arena() { for (void* p : ptrs) cudaFree(p); }
+  cudaStream_t st = nullptr;
+  ~Arena() { for (void* p : ptrs) cudaFreeAsync(p, st); }
   template <typename T> T* get(size_t n) {
     void* p = nullptr;
     size_t b = std::max<size_t>(n * sizeof(T), 16);
-    if (cudaMalloc(&p, b) != cudaSuccess) return nullptr;
+    if (cudaMallocAsync(&p, b, st) != cudaSuccess) { cudaGetLastError(); return nullptr; }
     ptrs.push_back(p);
     bytes += b;
     return static_cast<T*>(p);
   }
 };
+
+// Keep freed pool memory cached in the process (released at exit), once per device.
+void keep_pool_memory(int device) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  std::lock_guard<std::mutex> lk(mu);
+  if (device < 0 || device >= 64 || done[device]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[device] = true;
+}
 
 struct Setup {
   KPlan p{};
@@ -1098,25 +1116,32 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
   cudaStream_t st = ctx->stream;
   Setup& s = sv.s;
   const long long n = s.D * s.S;
-  C* X = sv.ar.get<C>(n);
-  C* Xo = sv.ar.get<C>(n);
+  const bool slab = sv.slab != nullptr;
+  // buffers of the gather path only (the slab path keeps a segment store instead)
+  C* X = slab ? nullptr : sv.ar.get<C>(n);
+  C* Xo = slab ? nullptr : sv.ar.get<C>(n);
   C* Dacc = sv.ar.get<C>(n);
-  C* Y[4];
-  for (int i = 0; i < 4; ++i) Y[i] = sv.ar.get<C>(n);
+  C* Y[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (!slab) for (int i = 0; i < 4; ++i) Y[i] = sv.ar.get<C>(n);
   C* KB = sv.ar.get<C>(n);
   C* KB2 = sv.ar.get<C>(n);
   C* Db = sv.ar.get<C>(n);
-  std::vector<double2*> seg(K + 1);
-  for (int i = 0; i <= K; ++i) seg[i] = sv.ar.get<double2>(n);
+  std::vector<double2*> seg(slab ? 0 : K + 1);
+  for (auto& b : seg) b = sv.ar.get<double2>(n);
   const int nW = s.p.n1 + 2 * s.p.ne;
   const int DL = s.p.dl;
   const int xgrid = (int)std::max<long long>(1, std::min<long long>((n / 2 + kT - 1) / kT, 152ll * 2));
-  double2* partial = sv.ar.get<double2>((size_t)xgrid * std::max(1, nW) * DL * DL);
+  double2* partial = slab ? nullptr : sv.ar.get<double2>((size_t)xgrid * std::max(1, nW) * DL * DL);
   unsigned* ticket = sv.ar.get<unsigned>(1);
-  for (C* c : {X, Xo, Dacc, Y[0], Y[1], Y[2], Y[3], KB, KB2, Db})
+  for (C* c : {Dacc, KB, KB2, Db})
     if (!c) return sg_fail(ctx, SG_E_NOMEM, "device allocation of adjoint buffers failed");
-  for (double2* c : seg) if (!c) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the segment buffer failed");
-  if (!partial || !ticket) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  if (!slab) {
+    for (C* c : {X, Xo, Y[0], Y[1], Y[2], Y[3]})
+      if (!c) return sg_fail(ctx, SG_E_NOMEM, "device allocation of adjoint buffers failed");
+    for (double2* c : seg) if (!c) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the segment buffer failed");
+    if (!partial) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  }
+  if (!ticket) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
   SG_CUDA_TRY(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
   XArgs xa{};
   xa.p = s.p;
@@ -1153,36 +1178,46 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
     ++sv.launches;
   };
   if (sv.slab) {
+    // segment store: every stage input y1..y4 of every step of one segment, so the
+    // adjoint needs no in-step recompute; one working psi
     C* kA = sv.ar.get<C>(slab_passes(sv.slab) > 1 ? n : 1);
     C* yA = sv.ar.get<C>(slab_passes(sv.slab) > 1 ? n : 1);
     double2* pint = sv.ar.get<double2>(n);
     double2* spart = sv.ar.get<double2>(slab_partial_elems(sv.slab));
-    if (!kA || !yA || !pint || !spart) return sg_fail(ctx, SG_E_NOMEM, "device allocation of adjoint buffers failed");
+    double2* pwork = sv.ar.get<double2>(n);
+    if (!kA || !yA || !pint || !spart || !pwork) return sg_fail(ctx, SG_E_NOMEM, "device allocation of adjoint buffers failed");
+    std::vector<C*> segY(4 * (size_t)K + 1);
+    for (auto& b : segY) {
+      b = sv.ar.get<C>(n);
+      if (!b) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the segment store failed");
+    }
     xa.partial = spart;
     slab_to_internal(sv.slab, pbar, pint, st);
     k_cast<R><<<grid_for(n), kT, 0, st>>>(pint, KB, n, s.dt / 6.0);
     sv.launches += 2;
     const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
-    void* Yv[4] = {Y[0], Y[1], Y[2], Y[3]};
     void* KBv = KB;
     void* KB2v = KB2;
     const int nseg = (int)ckpts.size();
     for (int c = nseg - 1; c >= 0; --c) {
       const int n0 = c * K, n1 = std::min(s.N, n0 + K);
-      SG_CUDA_TRY(ctx, cudaMemcpyAsync(seg[0], ckpts[c], n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-      k_cast<R><<<grid_for(n), kT, 0, st>>>(seg[0], X, n, 1.0);
+      SG_CUDA_TRY(ctx, cudaMemcpyAsync(pwork, ckpts[c], n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      k_cast<R><<<grid_for(n), kT, 0, st>>>(pwork, segY[0], n, 1.0);
       ++sv.launches;
-      void* Xv = X;
-      void* Xov = Xo;
-      for (int step = n0; step < n1 - 1; ++step)
-        sv.kt.run(0, step, [&] {
-          return slab_fwd_step(sv.slab, sv.mixed, tab, step, seg[step - n0], seg[step - n0 + 1], Xv, Xov, Dacc, kA, s.dt, st);
-        });
+      for (int step = n0; step < n1; ++step) {
+        void* Yk[4] = {segY[4 * (step - n0)], segY[4 * (step - n0) + 1], segY[4 * (step - n0) + 2],
+                       segY[4 * (step - n0) + 3]};
+        if (step < n1 - 1)
+          sv.kt.run(0, step, [&] {
+            return slab_fwd_step_keep(sv.slab, sv.mixed, tab, step, pwork, pwork, Yk, segY[4 * (step - n0 + 1)],
+                                      Dacc, kA, s.dt, st);
+          });
+        else
+          sv.kt.run(2, step, [&] { return slab_fwd_store(sv.slab, sv.mixed, tab, step, pwork, Yk, kA, s.dt, st); });
+      }
       for (int step = n1 - 1; step >= n0; --step) {
-        const double2* ps = seg[step - n0];
-        k_cast<R><<<grid_for(n), kT, 0, st>>>(ps, Y[0], n, 1.0);
-        ++sv.launches;
-        sv.kt.run(2, step, [&] { return slab_fwd_store(sv.slab, sv.mixed, tab, step, ps, Yv, kA, s.dt, st); });
+        void* Yv[4] = {segY[4 * (step - n0)], segY[4 * (step - n0) + 1], segY[4 * (step - n0) + 2],
+                       segY[4 * (step - n0) + 3]};
         sv.kt.run(1, step, [&] {
           return slab_adj_step(sv.slab, sv.mixed, tab, step, Yv, pint, KBv, KB2v, Db, yA, s.dt, xa, sv.tab,
                                sv.coef, sv.ph, s.sumd, s.K, st);
@@ -1235,9 +1270,11 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
   if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
   if (!psi_dev) return sg_fail(ctx, SG_E_INVALID, "psi_dev is NULL");
   Solve sv;
+  sv.ar.st = ctx->stream;
   sg_status rc = build_setup(sys, o, sv.s);
   if (rc != SG_OK) return rc;
   SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  keep_pool_memory(ctx->device);
   cudaStream_t st = ctx->stream;
   Setup& s = sv.s;
   long long* cols_dev = nullptr;
@@ -1274,6 +1311,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (!o || !o->col_index) return sg_fail(ctx, SG_E_INVALID, "fidelity needs opts->col_index");
   if (kind != SG_FID_AVG && kind != SG_FID_STATE) return sg_fail(ctx, SG_E_INVALID, "bad fidelity kind");
   Solve sv;
+  sv.ar.st = ctx->stream;
   sg_status rc = build_setup(sys, o, sv.s);
   if (rc != SG_OK) return rc;
   Setup& s = sv.s;
@@ -1281,6 +1319,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   for (int i = 0; i < s.nq; ++i)
     if (s.p.dims[i] < 2) return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per mode");
   SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  keep_pool_memory(ctx->device);
   cudaStream_t st = ctx->stream;
   // comp labels of the columns
   std::vector<int> lab(s.S, -1);

@@ -36,7 +36,8 @@ struct Phase {
   int no;                       // other digits, in thread-mapping order
   int ost[SG_MAXQ];             // their tile strides
   int allpar;                   // every present term is parity-odd
-  int po[SG_MAXD * SG_MAXD];    // shared-memory offset of block entry (x, z) from the block base
+  int psa, psb;                 // padded shared-memory strides of ka and kb
+  int pst[SG_MAXQ];             // padded strides of the other digits (mapping order)
 };
 
 struct SlabPass {
@@ -171,27 +172,38 @@ __device__ __forceinline__ void blk_apply(const Phase& P, const C* __restrict__ 
   }
 }
 
+// Padded shared-memory position of block b's (0, 0) entry: the other digits of b,
+// in mapping order, times their padded strides.  For power-of-two level counts
+// the padding is linear in each digit (spos(x s) = x spos(s) for a digit x of a
+// stride s), so block offsets are x psa + z psb.
 template <int DL>
-__device__ __forceinline__ int blk_base(const Phase& P, int b) {
-  int tb = 0;
+__device__ __forceinline__ int blk_pos(const Phase& P, int b) {
+  int pb = 0;
   for (int j = 0; j < P.no; ++j) {
-    tb += (b % DL) * P.ost[j];
+    pb += (b % DL) * P.pst[j];
     b /= DL;
   }
-  return tb;
+  return pb;
 }
 
-// One block of one phase, one output column z at a time (keeps registers low):
+// One block of one phase:
 //   out[x][z] = sum_a L[x][a] sum_c R[z][c] y[a][c] + sum_a A[x][a] y[a][z] + sum_c B[z][c] y[x][c]
-// PAR: every present term is parity-odd, so only index pairs of odd sum are visited.
+// computed one output column z at a time.  All loads (the y block and, after the
+// first phase, the running sum) come first so none waits behind a store to a
+// possibly aliasing address.  PAR: every present term is parity-odd, so only index
+// pairs of odd sum are visited.
 template <int DL, bool PAR, typename C>
 __device__ __forceinline__ void phase_block(const Phase& P, const C* __restrict__ M, const C* __restrict__ ys,
                                             C* __restrict__ ks, int pb, const bool FIRST) {
-  C y[DL][DL];
+  const int psa = P.psa, psb = P.psb;
+  C y[DL][DL], o[DL][DL];
 #pragma unroll
   for (int x = 0; x < DL; ++x)
 #pragma unroll
-    for (int z = 0; z < DL; ++z) y[x][z] = ys[pb + P.po[x * DL + z]];
+    for (int z = 0; z < DL; ++z) {
+      y[x][z] = ys[pb + x * psa + z * psb];
+      o[x][z] = FIRST ? cmk<C>(0.0, 0.0) : ks[pb + x * psa + z * psb];
+    }
   const C* Lm = M + P.offL;
   const C* Rm = M + P.offR;
   const C* Am = M + P.offA;
@@ -199,9 +211,6 @@ __device__ __forceinline__ void phase_block(const Phase& P, const C* __restrict_
   const bool hasE = P.offL >= 0, hasA = P.offA >= 0, hasB = P.offB >= 0;
 #pragma unroll
   for (int z = 0; z < DL; ++z) {
-    C o[DL];
-#pragma unroll
-    for (int x = 0; x < DL; ++x) o[x] = cmk<C>(0.0, 0.0);
     if (hasE) {
       C u[DL];
 #pragma unroll
@@ -216,29 +225,27 @@ __device__ __forceinline__ void phase_block(const Phase& P, const C* __restrict_
       for (int x = 0; x < DL; ++x)
 #pragma unroll
         for (int a = 0; a < DL; ++a)
-          if (!PAR || ((x + a) & 1)) o[x] = cfma(Lm[x * DL + a], u[a], o[x]);
+          if (!PAR || ((x + a) & 1)) o[x][z] = cfma(Lm[x * DL + a], u[a], o[x][z]);
     }
     if (hasA) {
 #pragma unroll
       for (int x = 0; x < DL; ++x)
 #pragma unroll
         for (int a = 0; a < DL; ++a)
-          if (!PAR || ((x + a) & 1)) o[x] = cfma(Am[x * DL + a], y[a][z], o[x]);
+          if (!PAR || ((x + a) & 1)) o[x][z] = cfma(Am[x * DL + a], y[a][z], o[x][z]);
     }
     if (hasB) {
 #pragma unroll
       for (int x = 0; x < DL; ++x)
 #pragma unroll
         for (int c = 0; c < DL; ++c)
-          if (!PAR || ((z + c) & 1)) o[x] = cfma(Bm[z * DL + c], y[x][c], o[x]);
-    }
-#pragma unroll
-    for (int x = 0; x < DL; ++x) {
-      const int ps = pb + P.po[x * DL + z];
-      if (FIRST) ks[ps] = o[x];
-      else { C q = ks[ps]; ks[ps] = cmk<C>(q.x + o[x].x, q.y + o[x].y); }
+          if (!PAR || ((z + c) & 1)) o[x][z] = cfma(Bm[z * DL + c], y[x][c], o[x][z]);
     }
   }
+#pragma unroll
+  for (int x = 0; x < DL; ++x)
+#pragma unroll
+    for (int z = 0; z < DL; ++z) ks[pb + x * psa + z * psb] = o[x][z];
 }
 
 // Applies every phase of the pass to the tile in ys, leaving H y (restricted to
@@ -250,7 +257,7 @@ __device__ __forceinline__ void pass_apply(const SlabPass& sp, const C* __restri
   for (int q = 0; q < sp.nph; ++q) {
     const Phase& P = sp.ph[q];
     for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-      const int pb = spos<DL>(blk_base<DL>(P, b));
+      const int pb = blk_pos<DL>(P, b);
       if (P.allpar) phase_block<DL, true>(P, M, ys, ks, pb, q == 0);
       else phase_block<DL, false>(P, M, ys, ks, pb, q == 0);
     }
@@ -348,59 +355,97 @@ __global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 3 : 1) k_slab_fwd(SlabPa
   }
 }
 
-// Cross-density of one slot over one d x d block (x = kbar block, y = y_s block):
+// Cross-density accumulators of one slot.  With PARX every operator of the plan is
+// parity-odd and only entries with a + b odd are kept (the others multiply zeros in
+// the contraction), packed in row-major order.
+template <int DL, bool PARX> __host__ __device__ constexpr int xd_n() { return PARX ? (DL * DL) / 2 : DL * DL; }
+template <int DL, bool PARX> __host__ __device__ constexpr int xd_i(int a, int b) {
+  if (!PARX) return a * DL + b;
+  int n = 0;
+  for (int i = 0; i < a * DL + b; ++i) n += ((i / DL) + (i % DL)) & 1;
+  return n;
+}
+
+// Cross-density of one slot over one d x d block (x = kbar block, y = y_s block),
+// streamed from shared memory a column or a row at a time:
 //   A (1-body on ka):  C[a][b] += sum_z conj(x[a][z]) y[b][z]
 //   B (1-body on kb):  C[c][d] += sum_x conj(x[x][c]) y[x][d]
-//   L (edge, ka):      C[a][b] += sum_z conj(x[a][z]) (y R^T)[b][z]
-//   R (edge, kb):      C[c][d] += sum_x conj(x[x][c]) (L y)[x][d]
-// With a parity-odd operator only entries with a + b odd are accumulated (the
-// others multiply zeros in the contraction).
-template <int DL, bool PAR, typename C>
-__device__ __forceinline__ void xd_first(const C (&x)[DL][DL], const C (&y)[DL][DL], C (&acc)[DL][DL]) {
+//   L (edge, ka):      C[a][b] += sum_z conj(x[a][z]) u[b][z],  u[b][z] = sum_c R[z][c] y[b][c]
+//   R (edge, kb):      C[c][d] += sum_x conj(x[x][c]) v[x][d],  v[x][d] = sum_a L[x][a] y[a][d]
+template <int DL, bool PARX, typename C>
+__device__ __forceinline__ void xd_slot(const Phase& P, int type, const C* __restrict__ M,
+                                        const C* __restrict__ xs, const C* __restrict__ ys, int pb,
+                                        C (&acc)[xd_n<DL, PARX>()]) {
+  const int psa = P.psa, psb = P.psb;
+  if (type == 0 || type == 1) {
+#pragma unroll
+    for (int z = 0; z < DL; ++z) {
+      C xc[DL], yc[DL];
+#pragma unroll
+      for (int a = 0; a < DL; ++a) {
+        const int o = type == 0 ? a * psa + z * psb : z * psa + a * psb;
+        xc[a] = xs[pb + o];
+        yc[a] = ys[pb + o];
+      }
+#pragma unroll
+      for (int a = 0; a < DL; ++a)
+#pragma unroll
+        for (int b = 0; b < DL; ++b) {
+          if (PARX && !((a + b) & 1)) continue;
+          acc[xd_i<DL, PARX>(a, b)] = cjfma(xc[a], yc[b], acc[xd_i<DL, PARX>(a, b)]);
+        }
+    }
+    return;
+  }
+  C y[DL][DL];
 #pragma unroll
   for (int a = 0; a < DL; ++a)
 #pragma unroll
-    for (int b = 0; b < DL; ++b) {
-      if (PAR && !((a + b) & 1)) continue;
-      C s = acc[a][b];
+    for (int b = 0; b < DL; ++b) y[a][b] = ys[pb + a * psa + b * psb];
+  if (type == 2) {
+    const C* Rm = M + P.offR;
 #pragma unroll
-      for (int z = 0; z < DL; ++z) s = cjfma(x[a][z], y[b][z], s);
-      acc[a][b] = s;
+    for (int z = 0; z < DL; ++z) {
+      C u[DL], xc[DL];
+#pragma unroll
+      for (int b = 0; b < DL; ++b) {
+        C t = cmk<C>(0.0, 0.0);
+#pragma unroll
+        for (int c = 0; c < DL; ++c)
+          if (!PARX || ((z + c) & 1)) t = cfma(Rm[z * DL + c], y[b][c], t);
+        u[b] = t;
+        xc[b] = xs[pb + b * psa + z * psb];
+      }
+#pragma unroll
+      for (int a = 0; a < DL; ++a)
+#pragma unroll
+        for (int b = 0; b < DL; ++b) {
+          if (PARX && !((a + b) & 1)) continue;
+          acc[xd_i<DL, PARX>(a, b)] = cjfma(xc[a], u[b], acc[xd_i<DL, PARX>(a, b)]);
+        }
     }
-}
-template <int DL, bool PAR, typename C>
-__device__ __forceinline__ void xd_second(const C (&x)[DL][DL], const C (&y)[DL][DL], C (&acc)[DL][DL]) {
-#pragma unroll
-  for (int c = 0; c < DL; ++c)
-#pragma unroll
-    for (int d = 0; d < DL; ++d) {
-      if (PAR && !((c + d) & 1)) continue;
-      C s = acc[c][d];
-#pragma unroll
-      for (int z = 0; z < DL; ++z) s = cjfma(x[z][c], y[z][d], s);
-      acc[c][d] = s;
-    }
-}
-
-template <int DL, typename C>
-__device__ __forceinline__ void xd_block(const Phase& P, int type, const C* __restrict__ M,
-                                         const C (&x)[DL][DL], const C (&y)[DL][DL], C (&acc)[DL][DL]) {
-  if (type == 0) {
-    if (P.par & 4u) xd_first<DL, true>(x, y, acc); else xd_first<DL, false>(x, y, acc);
-  } else if (type == 1) {
-    if (P.par & 8u) xd_second<DL, true>(x, y, acc); else xd_second<DL, false>(x, y, acc);
-  } else if (type == 2) {
-    C u[DL][DL];
-    if (P.par & 2u) blk_right<DL, true>(M + P.offR, y, u); else blk_right<DL, false>(M + P.offR, y, u);
-    if (P.par & 1u) xd_first<DL, true>(x, u, acc); else xd_first<DL, false>(x, u, acc);
   } else {
-    C v[DL][DL];
+    const C* Lm = M + P.offL;
 #pragma unroll
-    for (int a = 0; a < DL; ++a)
+    for (int x = 0; x < DL; ++x) {
+      C v[DL], xr[DL];
 #pragma unroll
-      for (int b = 0; b < DL; ++b) v[a][b] = cmk<C>(0.0, 0.0);
-    if (P.par & 1u) blk_left_acc<DL, true>(M + P.offL, y, v); else blk_left_acc<DL, false>(M + P.offL, y, v);
-    if (P.par & 2u) xd_second<DL, true>(x, v, acc); else xd_second<DL, false>(x, v, acc);
+      for (int d = 0; d < DL; ++d) {
+        C t = cmk<C>(0.0, 0.0);
+#pragma unroll
+        for (int a = 0; a < DL; ++a)
+          if (!PARX || ((x + a) & 1)) t = cfma(Lm[x * DL + a], y[a][d], t);
+        v[d] = t;
+        xr[d] = xs[pb + x * psa + d * psb];
+      }
+#pragma unroll
+      for (int c = 0; c < DL; ++c)
+#pragma unroll
+        for (int d = 0; d < DL; ++d) {
+          if (PARX && !((c + d) & 1)) continue;
+          acc[xd_i<DL, PARX>(c, d)] = cjfma(xr[c], v[d], acc[xd_i<DL, PARX>(c, d)]);
+        }
+    }
   }
 }
 
@@ -409,8 +454,8 @@ __device__ __forceinline__ void xd_block(const Phase& P, int type, const C* __re
 // accumulates the cross-densities of this pass's slots: warp w owns slots w and
 // w + 8, its lanes walk the blocks of the slot's phase, and the d x d partial sums
 // stay in registers across all tiles; one fixed-order reduction at the end.
-template <typename R, int DL>
-__global__ void __launch_bounds__(kST, 1)
+template <typename R, int DL, bool PARX>
+__global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 2 : 1)
 k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename CT<R>::T* __restrict__ Y,
            const typename CT<R>::T* __restrict__ tabrow, double2* __restrict__ pbar,
            typename CT<R>::T* __restrict__ Xn, typename CT<R>::T* __restrict__ Db,
@@ -424,13 +469,12 @@ k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename 
   const int* __restrict__ off = sp.off;
   load_common(sp, tabrow, M);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  C acc[kSPW][DL][DL];
+  constexpr int NA = xd_n<DL, PARX>();
+  C acc[kSPW][NA];
 #pragma unroll
   for (int s = 0; s < kSPW; ++s)
 #pragma unroll
-    for (int a = 0; a < DL; ++a)
-#pragma unroll
-      for (int b = 0; b < DL; ++b) acc[s][a][b] = cmk<C>(0.0, 0.0);
+    for (int a = 0; a < NA; ++a) acc[s][a] = cmk<C>(0.0, 0.0);
   const long long ntiles = (long long)sp.S * sp.ntpc;
   const R h = (R)dt;
   const int nb = sp.T / (DL * DL);
@@ -490,19 +534,8 @@ k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename 
       if (slot >= sp.nx) continue;                  // warp-uniform
       const Phase& P = sp.ph[sp.x_ph[slot]];
       const int type = sp.x_type[slot];
-      for (int b = lane; b < nb; b += 32) {
-        const int pb = spos<DL>(blk_base<DL>(P, b));
-        C xv[DL][DL], yv[DL][DL];
-#pragma unroll
-        for (int x = 0; x < DL; ++x)
-#pragma unroll
-          for (int z = 0; z < DL; ++z) {
-            const int ps = pb + P.po[x * DL + z];
-            xv[x][z] = xs[ps];
-            yv[x][z] = ys[ps];
-          }
-        xd_block<DL>(P, type, M, xv, yv, acc[s]);
-      }
+      for (int b = lane; b < nb; b += 32)
+        xd_slot<DL, PARX>(P, type, M, xs, ys, blk_pos<DL>(P, b), acc[s]);
     }
     __syncthreads();
   }
@@ -515,10 +548,14 @@ k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename 
     for (int a = 0; a < DL; ++a)
 #pragma unroll
       for (int b = 0; b < DL; ++b) {
-        double vr = acc[s][a][b].x, vi = acc[s][a][b].y;
-        for (int o = 16; o > 0; o >>= 1) {
-          vr += __shfl_xor_sync(0xffffffffu, vr, o);
-          vi += __shfl_xor_sync(0xffffffffu, vi, o);
+        double vr = 0.0, vi = 0.0;
+        if (!PARX || ((a + b) & 1)) {
+          vr = acc[s][xd_i<DL, PARX>(a, b)].x;
+          vi = acc[s][xd_i<DL, PARX>(a, b)].y;
+          for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, o);
+            vi += __shfl_xor_sync(0xffffffffu, vi, o);
+          }
         }
         if (lane == 0) xa.partial[((size_t)blockIdx.x * kMaxX + slot) * DL * DL + a * DL + b] = make_double2(vr, vi);
       }
@@ -570,6 +607,8 @@ __global__ void k_perm(PermArgs a, const double2* __restrict__ src, double2* __r
 
 struct SlabPlanHost {
   int DL = 0, np = 0;
+  bool allpar = false;             // every phase of every pass is parity-odd
+  cudaStream_t st = nullptr;       // stream the offset tables were allocated on
   bool mixed = false;
   SlabPass pass[kMaxPass];
   int* off_dev[kMaxPass] = {nullptr, nullptr, nullptr, nullptr};
@@ -665,6 +704,7 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
     for (int k = nq - 1; k >= 0; --k) { st_int[order[k]] = s; s *= p.dims[order[k]]; }
   }
   SlabPlanHost* h = new SlabPlanHost();
+  h->st = st;
   h->DL = DL;
   h->np = np;
   h->mixed = mixed;
@@ -777,13 +817,11 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
     }
     for (int q = 0; q < sp.nph; ++q) {
       Phase& P = sp.ph[q];
-      const int sa = sp.tsh[P.ka], sb = sp.tsh[P.kb];
       const bool pw2 = DL == 2 || DL == 4;
-      for (int x = 0; x < DL; ++x)
-        for (int z = 0; z < DL; ++z) {
-          const int o = x * sa + z * sb;
-          P.po[x * DL + z] = pw2 ? o + (o >> 4) + (o >> 8) : o;
-        }
+      auto pad = [&](int o) { return pw2 ? o + (o >> 4) + (o >> 8) : o; };
+      P.psa = pad(sp.tsh[P.ka]);
+      P.psb = pad(sp.tsh[P.kb]);
+      for (int j = 0; j < P.no; ++j) P.pst[j] = pad(P.ost[j]);
       unsigned need = (P.offL >= 0 ? 3u : 0u) | (P.offA >= 0 ? 4u : 0u) | (P.offB >= 0 ? 8u : 0u);
       P.allpar = (P.par & need) == need ? 1 : 0;
     }
@@ -808,23 +846,26 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
       for (int k = 0; k < sp.ng; ++k) o += (long long)((t / sp.tsh[k]) % p.dims[tm[k]]) * st_int[tm[k]];
       off[t] = (int)o;
     }
-    if (cudaMalloc(&h->off_dev[g], sp.T * sizeof(int)) != cudaSuccess) { slab_plan_destroy(h); return nullptr; }
+    if (cudaMallocAsync(&h->off_dev[g], sp.T * sizeof(int), st) != cudaSuccess) { slab_plan_destroy(h); return nullptr; }
     cudaMemcpyAsync(h->off_dev[g], off.data(), sp.T * sizeof(int), cudaMemcpyHostToDevice, st);
     sp.off = h->off_dev[g];
     h->sm_fwd[g] = 2 * spad(sp.T) * csz + p.row * csz;
     h->sm_adj[g] = std::max(3 * spad(sp.T) * csz + p.row * csz, (size_t)kMaxX * DL * DL * sizeof(double2));
     if (h->sm_adj[g] > 200 * 1024) { slab_plan_destroy(h); return nullptr; }
   }
+  h->allpar = true;
+  for (int g = 0; g < np; ++g)
+    for (int q = 0; q < h->pass[g].nph; ++q) h->allpar = h->allpar && h->pass[g].ph[q].allpar;
   long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   h->grid_fwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 3 : 1));
-  h->grid_adj = (int)std::min<long long>(ntiles, 152ll);
+  h->grid_adj = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
   cudaStreamSynchronize(st);
   return h;
 }
 
 void slab_plan_destroy(SlabPlanHost* h) {
   if (!h) return;
-  for (int g = 0; g < kMaxPass; ++g) if (h->off_dev[g]) cudaFree(h->off_dev[g]);
+  for (int g = 0; g < kMaxPass; ++g) if (h->off_dev[g]) cudaFreeAsync(h->off_dev[g], h->st);
   delete h;
 }
 
@@ -878,9 +919,13 @@ void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, cons
                 double2* pbar, void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st,
                 int stage, int kind) {
   typedef typename CT<R>::T C;
-  auto kern = k_slab_adj<R, DL>;
+  auto kern = h->allpar ? k_slab_adj<R, DL, true> : k_slab_adj<R, DL, false>;
   static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
+  if (!attr) {
+    cudaFuncSetAttribute(k_slab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_slab_adj<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    attr = true;
+  }
   kern<<<h->grid_adj, kST, h->sm_adj[g], st>>>(h->pass[g], (const C*)X, (const C*)Y, (const C*)row, pbar,
                                                  (C*)Xn, (C*)Db, (C*)yA, dt, xa, stage, kind);
 }
@@ -911,6 +956,19 @@ int fwd_step_t(const SlabPlanHost* h, const void* tab, int step, const double2* 
   fwd_stage<R, DL>(h, 1, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
   fwd_stage<R, DL>(h, 2, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
   fwd_stage<R, DL>(h, 3, false, X, row_of<R>(tab, row, step, 2), pin, pout, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
+  return 4 * h->np;
+}
+
+// Forward step that keeps every stage input: Yk[0..3] = y1..y4 of this step (Yk[0]
+// holds y1 on entry), Ynext0 = y1 of the next step.
+template <typename R, int DL>
+int fwd_step_keep_t(const SlabPlanHost* h, const void* tab, int step, const double2* pin, double2* pout,
+                    void* const Yk[4], void* Ynext0, void* Dacc, void* kA, double dt, cudaStream_t st) {
+  const int row = h->pass[0].row;
+  fwd_stage<R, DL>(h, 0, false, Yk[0], row_of<R>(tab, row, step, 0), pin, nullptr, Yk[1], Dacc, kA, dt, st);
+  fwd_stage<R, DL>(h, 1, false, Yk[1], row_of<R>(tab, row, step, 1), pin, nullptr, Yk[2], Dacc, kA, dt, st);
+  fwd_stage<R, DL>(h, 2, false, Yk[2], row_of<R>(tab, row, step, 1), pin, nullptr, Yk[3], Dacc, kA, dt, st);
+  fwd_stage<R, DL>(h, 3, false, Yk[3], row_of<R>(tab, row, step, 2), pin, pout, Ynext0, Dacc, kA, dt, st);
   return 4 * h->np;
 }
 
@@ -975,6 +1033,12 @@ int slab_fwd_step(const SlabPlanHost* h, bool mixed, const void* tab, int step, 
 int slab_fwd_store(const SlabPlanHost* h, bool mixed, const void* tab, int step, const double2* psi,
                    void* const Y[4], void* kA, double dt, cudaStream_t st) {
   SLAB_DISPATCH(fwd_store_t, h, tab, step, psi, Y, kA, dt, st);
+}
+
+int slab_fwd_step_keep(const SlabPlanHost* h, bool mixed, const void* tab, int step, const double2* pin,
+                       double2* pout, void* const Yk[4], void* Ynext0, void* Dacc, void* kA, double dt,
+                       cudaStream_t st) {
+  SLAB_DISPATCH(fwd_step_keep_t, h, tab, step, pin, pout, Yk, Ynext0, Dacc, kA, dt, st);
 }
 
 int slab_adj_step(const SlabPlanHost* h, bool mixed, const void* tab, int step, void* const Y[4],

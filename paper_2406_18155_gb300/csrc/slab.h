@@ -27,6 +27,11 @@ void slab_from_internal(const SlabPlanHost* sp, const double2* internal, double2
 int slab_fwd_step(const SlabPlanHost* sp, bool mixed, const void* tab, int step, const double2* pin,
                   double2* pout, void*& X, void*& Xo, void* Dacc, void* kA, double dt,
                   cudaStream_t st);
+// Forward step that keeps all four stage inputs: Yk[0] holds y1 = (R)psi on entry;
+// y2..y4 go to Yk[1..3] and the next step's y1 to Ynext0.  Returns launches.
+int slab_fwd_step_keep(const SlabPlanHost* sp, bool mixed, const void* tab, int step, const double2* pin,
+                       double2* pout, void* const Yk[4], void* Ynext0, void* Dacc, void* kA, double dt,
+                       cudaStream_t st);
 // Recompute y2, y3, y4 of one step from y1 = (R)psi_n (STORE mode).  Returns launches.
 int slab_fwd_store(const SlabPlanHost* sp, bool mixed, const void* tab, int step, const double2* psi,
                    void* const Y[4], void* kA, double dt, cudaStream_t st);
