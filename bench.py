@@ -262,11 +262,65 @@ def run_ours(args):
             out["fp64_vs_mixed"] = fp64_comparison(sysm, wl, args.fp64_steps, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
+    if rank == 0 and args.serving > 0:
+        out["serving"] = serving_bench(ctx, args.serving, args.serving_slots)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def serving_bench(ctx, n_requests, slots, seed=7):
+    """Config 4: requests of 2-5 coupled transmons or fluxoniums at 3-5 levels,
+    T ~ U[20, 200] ns, random 10-segment pulses, each a fidelity + gradient solve.
+    First all of n_requests/2 submitted at once (saturated throughput), then
+    n_requests with Poisson arrivals at 0.7 x that rate (latency under load)."""
+    from paper_2406_18155_gb300.api import Server, System
+    rng = np.random.Generator(np.random.PCG64(seed))
+
+    def make(nr):
+        out = []
+        for _ in range(nr):
+            wl = W.serving_request(rng)
+            s = System.from_workload(ctx, wl)
+            out.append((wl, s))
+        return out
+
+    srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
+    sat = make(max(1, n_requests // 2))
+    t0 = time.perf_counter()
+    tk = [srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg") for wl, s in sat]
+    for t in tk:
+        srv.wait(t)
+    sat_rate = len(sat) / (time.perf_counter() - t0)
+    srv.close()
+    srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
+    reqs = make(n_requests)
+    rate = 0.7 * sat_rate
+    gaps = rng.exponential(1.0 / rate, size=len(reqs))
+    t0 = time.perf_counter()
+    tk = []
+    next_t = 0.0
+    for (wl, s), g in zip(reqs, gaps):
+        next_t += g
+        dly = next_t - (time.perf_counter() - t0)
+        if dly > 0:
+            time.sleep(dly)
+        tk.append(srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg"))
+    res = [srv.wait(t) for t in tk]
+    wall = time.perf_counter() - t0
+    lat = np.array([r["done_s"] - r["submit_s"] for r in res])
+    st = srv.stats()
+    srv.close()
+    steps = np.array([int(round(wl["T"] / wl["dt"])) for wl, _ in reqs])
+    return {"requests": len(reqs), "saturated_solves_per_s": sat_rate, "arrival_rate_per_s": rate,
+            "solves_per_s": len(reqs) / wall, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "slots": slots,
+            "gpu_busy_frac": st["gpu_busy_frac"], "errors": int(sum(r["status"] != 0 for r in res)),
+            "mean_rk4_steps": float(steps.mean()),
+            "sample": f"{len(sat)} saturated + {len(reqs)} Poisson requests of the serving "
+                      "distribution (the full stream is 10k requests), fidelity + gradient each"}
 
 
 def slab_passes(D):
@@ -401,8 +455,19 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serving", type=int, default=24, help="requests of the serving sample (0: skip)")
+    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only_serving:
+        import torch
+        from paper_2406_18155_gb300 import build as B
+        B.build()
+        from paper_2406_18155_gb300.api import Context
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": serving_bench(Context(0), args.serving, args.serving_slots)}),
+              flush=True)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
