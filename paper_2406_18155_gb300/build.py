@@ -39,7 +39,7 @@ def _stale(obj, deps):
 def build(verbose=False, extra=()):
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(HERE, "..", "include", "sg.h"))
     jobs = []
     for f in sources():

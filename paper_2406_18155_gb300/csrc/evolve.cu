@@ -17,7 +17,7 @@
 // It is correct for any mode count and level counts up to SG_MAXD.
 #include "sg_internal.h"
 #include "kplan.h"
-#include "fast.h"
+#include "onchip.h"
 #include "grad.cuh"
 #include "slab.h"
 #include <cstdlib>
@@ -941,14 +941,23 @@ struct Solve {
   int launches = 0;
   bool mixed = false;
   SlabPlanHost* slab = nullptr;
-  ~Solve() { slab_plan_destroy(slab); }
+  OnchipPlan* oc = nullptr;
+  ~Solve() {
+    slab_plan_destroy(slab);
+    onchip_plan_destroy(oc);
+  }
+  // the on-chip kernels evolve this solve (gradient solves need the adjoint to fit too)
+  bool onchip(bool grad) const { return oc && (!grad || onchip_adjoint_ok(oc)); }
 };
 
-// Kernel family: SG_PATH=gather forces the generic gather kernels (a test knob);
-// otherwise the tiled slab kernels run whenever they handle the plan.
-bool use_slab_path() {
+// Kernel family, a test knob: SG_PATH=gather forces the generic gather kernels,
+// SG_PATH=slab the tiled HBM kernels; otherwise the on-chip kernels run whenever
+// the columns fit in shared memory, else the tiled kernels when they handle the
+// plan, else the gather kernels.
+int path_choice() {
   const char* e = std::getenv("SG_PATH");
-  return !(e && std::string(e) == "gather");
+  const std::string v = e ? e : "";
+  return v == "gather" ? 2 : (v == "slab" ? 1 : 0);
 }
 
 sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) {
@@ -985,7 +994,9 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) 
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
   sv.mixed = o->precision == SG_MIXED;
-  if (use_slab_path()) sv.slab = slab_plan_create(s.p, sv.mixed, st);
+  const int pc = path_choice();
+  if (pc == 0) sv.oc = onchip_plan_create(s.p, sv.mixed, s.K, s.sumd, st);
+  if (pc <= 1 && !(sv.oc && onchip_adjoint_ok(sv.oc))) sv.slab = slab_plan_create(s.p, sv.mixed, st);
   {
     const char* e = std::getenv("SG_KTIMING");
     sv.kt.on = e && e[0] == '1';
@@ -1046,11 +1057,12 @@ sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool
     k_init_cols<<<grid_for(n), kT, 0, st>>>(sv.psi, s.D, s.S, cols_dev);
     ++sv.launches;
   }
-  // fast on-chip path when the whole column block fits in shared memory
-  if (!ckpts && fast_onchip_available(s.p, sizeof(R) == 4)) {
-    sg_status rc = fast_onchip_forward(sys, s.p, sizeof(R) == 4, sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab,
-                                       sv.psi, s.N, s.dt, st, &sv.launches);
-    if (rc != SG_OK) return rc;
+  // on-chip: the whole evolution in one launch, checkpoints as state images
+  // (ckpts[c] = ckpts[0] + c * onchip_state_elems)
+  if (sv.onchip(ckpts != nullptr)) {
+    const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
+    sv.launches += onchip_forward(sv.oc, tab, sv.psi, nullptr, sv.psi, ckpts ? (*ckpts)[0] : nullptr,
+                                  ckpt_every, 0, s.N, s.dt, nullptr, st);
     SG_CUDA_TRY(ctx, cudaGetLastError());
     return SG_OK;
   }
@@ -1108,6 +1120,71 @@ CompArgs comp_args(const Setup& s) {
   return c;
 }
 
+// Constant part of the cross-density contraction arguments of a solve.
+XArgs make_xargs(const Solve& sv, GradAcc acc) {
+  const Setup& s = sv.s;
+  XArgs xa{};
+  xa.p = s.p;
+  xa.K = s.K;
+  xa.nW = s.p.n1 + 2 * s.p.ne;
+  xa.frame = s.ta.frame;
+  xa.opd = sv.opd_dev;
+  for (int i = 0; i < s.nq; ++i) { xa.opd_off[i] = s.ta.opd_off[i]; xa.eoff[i] = s.ta.eoff[i]; }
+  xa.E = sv.E_dev;
+  for (int i = 0; i <= s.p.n1; ++i) xa.drv_of_slot_start[i] = s.ta.drv_of_slot_start[i];
+  for (int i = 0; i < SG_MAXDRIVE; ++i) xa.drv_list[i] = s.ta.drv_list[i];
+  for (int k = 0; k < s.K; ++k) xa.drv_op[k] = s.drives[k].op;
+  for (int e = 0; e < s.p.ne; ++e) { xa.e_opa[e] = s.ta.e_opa[e]; xa.e_opb[e] = s.ta.e_opb[e]; xa.J[e] = s.ta.J[e]; }
+  xa.acc = acc;
+  return xa;
+}
+
+// Adjoint on the on-chip kernels: per checkpoint segment one recompute launch that
+// stores every stage input, one adjoint launch; per-CTA accumulators summed at the end.
+template <typename R>
+sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, int K,
+                              double2* pbar, GradAcc acc) {
+  typedef typename CT<R>::T C;
+  sg_ctx* ctx = sys->ctx;
+  cudaStream_t st = ctx->stream;
+  Setup& s = sv.s;
+  const OnchipPlan* oc = sv.oc;
+  const XArgs xa = make_xargs(sv, acc);
+  const long long ns = onchip_state_elems(oc);
+  const long long nstage = onchip_stage_elems(oc);
+  const int ncta = onchip_ctas(oc);
+  const long long nst = 3ll * s.N;
+  const int Kd = std::max(1, s.K);
+  double2* pimg = sv.ar.get<double2>(ns);
+  C* segY = sv.ar.get<C>((size_t)4 * K * nstage);
+  double* gFc = sv.ar.get<double>((size_t)ncta * nst * Kd);
+  double* accc = sv.ar.get<double>((size_t)ncta * onchip_acc_doubles(oc));
+  int* err = sv.ar.get<int>(1);
+  if (!pimg || !segY || !gFc || !accc || !err)
+    return sg_fail(ctx, SG_E_NOMEM, "device allocation of the on-chip adjoint buffers failed");
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(gFc, 0, (size_t)ncta * nst * Kd * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(accc, 0, (size_t)ncta * onchip_acc_doubles(oc) * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+  onchip_to_image(oc, pbar, pimg, st);
+  ++sv.launches;
+  const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
+  const int nseg = (int)ckpts.size();
+  for (int c = nseg - 1; c >= 0; --c) {
+    const int n0 = c * K, n1 = std::min(s.N, n0 + K);
+    sv.launches += onchip_forward(oc, tab, nullptr, ckpts[c], nullptr, nullptr, K, n0, n1, s.dt, segY, st);
+    sv.launches += onchip_adjoint(oc, tab, sv.tab, sv.coef, sv.ph, segY, pimg, n0, n1, s.dt, xa, (int)nst,
+                                  gFc, accc, err, st);
+  }
+  onchip_reduce(oc, gFc, accc, nst, s.K, s.p.n1, s.p.ne, acc, st);
+  ++sv.launches;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  int herr = 0;
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (herr) return sg_fail(ctx, SG_E_CUDA, "on-chip adjoint: a bulk copy of a stage input did not complete");
+  return SG_OK;
+}
+
 template <typename R>
 sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, int K,
                        double2* pbar, GradAcc acc) {
@@ -1116,6 +1193,7 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
   cudaStream_t st = ctx->stream;
   Setup& s = sv.s;
   const long long n = s.D * s.S;
+  if (sv.onchip(true)) return run_backward_onchip<R>(sys, sv, ckpts, K, pbar, acc);
   const bool slab = sv.slab != nullptr;
   // buffers of the gather path only (the slab path keeps a segment store instead)
   C* X = slab ? nullptr : sv.ar.get<C>(n);
@@ -1143,21 +1221,9 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
   }
   if (!ticket) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
   SG_CUDA_TRY(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
-  XArgs xa{};
-  xa.p = s.p;
-  xa.K = s.K;
-  xa.nW = nW;
-  xa.frame = s.ta.frame;
-  xa.opd = sv.opd_dev;
-  for (int i = 0; i < s.nq; ++i) { xa.opd_off[i] = s.ta.opd_off[i]; xa.eoff[i] = s.ta.eoff[i]; }
-  xa.E = sv.E_dev;
-  for (int i = 0; i <= s.p.n1; ++i) xa.drv_of_slot_start[i] = s.ta.drv_of_slot_start[i];
-  for (int i = 0; i < SG_MAXDRIVE; ++i) xa.drv_list[i] = s.ta.drv_list[i];
-  for (int k = 0; k < s.K; ++k) xa.drv_op[k] = s.drives[k].op;
-  for (int e = 0; e < s.p.ne; ++e) { xa.e_opa[e] = s.ta.e_opa[e]; xa.e_opb[e] = s.ta.e_opb[e]; xa.J[e] = s.ta.J[e]; }
+  XArgs xa = make_xargs(sv, acc);
   xa.partial = partial;
   xa.ticket = ticket;
-  xa.acc = acc;
   const size_t xsm = std::max<size_t>(2 * (kT / 32) * DL * DL * sizeof(double) + s.p.row * sizeof(C),
                                       (size_t)std::max(1, nW) * DL * DL * sizeof(double2));
   auto xdens = [&](const C* Xk, const C* Yk, int step, int j) {
@@ -1367,10 +1433,18 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     K = ckpt > 0 ? ckpt : std::max(1, (int)std::lround(std::sqrt((double)s.N)));
     K = std::min(K, s.N);
     const int nck = (s.N + K - 1) / K;
-    for (int c = 0; c < nck; ++c) {
-      double2* p = sv.ar.get<double2>(n);
+    if (sv.onchip(true)) {
+      // one block of state images, ckpts[c] = ckpts[0] + c * image size
+      const long long ns = onchip_state_elems(sv.oc);
+      double2* p = sv.ar.get<double2>((size_t)nck * ns);
       if (!p) return sg_fail(ctx, SG_E_NOMEM, "device allocation of checkpoints failed");
-      ckpts.push_back(p);
+      for (int c = 0; c < nck; ++c) ckpts.push_back(p + (size_t)c * ns);
+    } else {
+      for (int c = 0; c < nck; ++c) {
+        double2* p = sv.ar.get<double2>(n);
+        if (!p) return sg_fail(ctx, SG_E_NOMEM, "device allocation of checkpoints failed");
+        ckpts.push_back(p);
+      }
     }
   }
   cudaEvent_t ev0, ev1, ev2;

@@ -1,0 +1,53 @@
+// On-chip evolution for systems whose columns fit in one CTA's shared memory.
+//
+// One CTA owns a group of Sc state columns for the whole run: the state, the RK4
+// stage input and increment (forward) or the co-state, kbar and the stage inputs
+// (adjoint) stay in shared memory across steps, so a full forward evolution is one
+// launch and an adjoint checkpoint segment is two (recompute, then pull back).
+// Columns never exchange data during the evolution (Eq. 1's H(t) acts on each
+// column separately), so CTAs need no grid synchronisation; the cross-densities of
+// the gradient (Sec. 2.5) are contracted per CTA and stage into per-CTA
+// accumulators that one reduction sums in a fixed order.
+#pragma once
+#include "grad.cuh"
+
+struct OnchipPlan;   // opaque
+
+// nullptr unless the plan is a single tile (one pass of the tiled kernels), every
+// mode has the same level count (2..5) and at least the forward state fits in
+// shared memory.  K drives and sumd = sum of level counts size the adjoint's
+// per-stage buffers.
+OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cudaStream_t st);
+void onchip_plan_destroy(OnchipPlan* oc);
+// The adjoint kernel fits too (gradient solves may use the on-chip path).
+bool onchip_adjoint_ok(const OnchipPlan* oc);
+// complex128 entries of one state image (CTA-major, Sc columns of D entries per CTA).
+long long onchip_state_elems(const OnchipPlan* oc);
+// stage-precision entries of one stored stage-input image (all CTAs).
+long long onchip_stage_elems(const OnchipPlan* oc);
+int onchip_ctas(const OnchipPlan* oc);
+// doubles of one CTA's operator/energy/coupling accumulators (GradAcc layout minus gF).
+long long onchip_acc_doubles(const OnchipPlan* oc);
+
+// Forward RK4 steps n0 .. n1-1.  The start state is img_in (state image) when
+// non-null, else psi_api (D x S, column innermost).  Writes the state before step
+// n0 + c K to ck_out + c * state_elems when ck_out is non-null, the final state to
+// psi_out (API layout) when non-null, and every stage input of every step to
+// segY (stage images, slot 4 (step - n0) + stage) when non-null.  Returns launches.
+int onchip_forward(const OnchipPlan* oc, const void* tab, const double2* psi_api, const double2* img_in,
+                   double2* psi_out, double2* ck_out, int K, int n0, int n1, double dt, void* segY,
+                   cudaStream_t st);
+// API layout -> state image (columns past S are zero).
+void onchip_to_image(const OnchipPlan* oc, const double2* api, double2* img, cudaStream_t st);
+// Adjoint of steps n1-1 .. n0 from the stage inputs in segY: pbar_img (state image
+// of the co-state before the segment's last step) is pulled back in place; the
+// cross-densities of every stage are contracted into gF_cta (CTA-major, 3N x K
+// each, one store per stage slot) and acc_cta (CTA-major, onchip_acc_doubles
+// each, added to).  *err is set when a bounded wait on a bulk copy gives up.
+// Returns launches.
+int onchip_adjoint(const OnchipPlan* oc, const void* tab, const double2* tab64, const double* coef,
+                   const double2* ph, const void* segY, double2* pbar_img, int n0, int n1, double dt,
+                   const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err, cudaStream_t st);
+// acc += sum over CTAs (in CTA order) of the per-CTA accumulators.
+void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc_cta, long long nst, int K,
+                   int n1, int ne, GradAcc acc, cudaStream_t st);

@@ -13,9 +13,10 @@ from paper_2406_18155_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(params=["slab", "gather"])
+@pytest.fixture(params=["onchip", "slab", "gather"])
 def path(request, monkeypatch):
-    """Kernel family: the tiled slab kernels (default) or the generic gather kernels."""
+    """Kernel family: on-chip (the default where the columns fit in shared memory),
+    the tiled HBM slab kernels, or the generic gather kernels."""
     monkeypatch.setenv("SG_PATH", request.param)
     return request.param
 
