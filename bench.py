@@ -291,8 +291,7 @@ def serving_bench(ctx, n_requests, slots, seed=7):
     sat = make(max(1, n_requests // 2))
     t0 = time.perf_counter()
     tk = [srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg") for wl, s in sat]
-    for t in tk:
-        srv.wait(t)
+    sat_res = [srv.wait(t) for t in tk]
     sat_rate = len(sat) / (time.perf_counter() - t0)
     srv.close()
     srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
@@ -318,6 +317,10 @@ def serving_bench(ctx, n_requests, slots, seed=7):
             "solves_per_s": len(reqs) / wall, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "slots": slots,
             "gpu_busy_frac": st["gpu_busy_frac"], "errors": int(sum(r["status"] != 0 for r in res)),
+            "saturated_errors": int(sum(r["status"] != 0 for r in sat_res)),
+            "error_kinds": sorted({f'{wl["name"]}: {r["error"]}'
+                                   for (wl, _), r in list(zip(reqs, res)) + list(zip(sat, sat_res))
+                                   if r["status"] != 0}),
             "mean_rk4_steps": float(steps.mean()),
             "sample": f"{len(sat)} saturated + {len(reqs)} Poisson requests of the serving "
                       "distribution (the full stream is 10k requests), fidelity + gradient each"}
@@ -455,8 +458,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-sample-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serving", type=int, default=24, help="requests of the serving sample (0: skip)")
-    ap.add_argument("--serving-slots", type=int, default=8)
+    ap.add_argument("--serving", type=int, default=48, help="requests of the serving sample (0: skip)")
+    ap.add_argument("--serving-slots", type=int, default=16)
     ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
     args = ap.parse_args()
     if args.only_serving:

@@ -240,6 +240,7 @@ typedef struct {
   double* grad_ham;
   int n_pulse, n_ham;
   double submit_s, start_s, done_s;   /* server clock (seconds since create)            */
+  char error[192];              /* the solve's error message when status != SG_OK        */
 } sg_result;
 
 typedef struct {

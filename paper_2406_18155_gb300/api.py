@@ -262,7 +262,8 @@ class Server:
 
     def _result(self, res):
         out = {"status": res.status, "F": (res.F[0], res.F[1]), "submit_s": res.submit_s,
-               "start_s": res.start_s, "done_s": res.done_s}
+               "start_s": res.start_s, "done_s": res.done_s,
+               "error": res.error.decode(errors="replace")}
         out["grad_pulse"] = np.array([res.grad_pulse[i] for i in range(res.n_pulse)])
         out["grad_ham"] = np.array([res.grad_ham[i] for i in range(res.n_ham)])
         return out

@@ -43,7 +43,7 @@ class sg_result(C.Structure):
     _fields_ = [("status", C.c_int), ("F", C.c_double * 2),
                 ("grad_pulse", C.POINTER(C.c_double)), ("grad_ham", C.POINTER(C.c_double)),
                 ("n_pulse", C.c_int), ("n_ham", C.c_int), ("submit_s", C.c_double),
-                ("start_s", C.c_double), ("done_s", C.c_double)]
+                ("start_s", C.c_double), ("done_s", C.c_double), ("error", C.c_char * 192)]
 
 
 class sg_stats(C.Structure):

@@ -603,7 +603,7 @@ __global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* 
 // Pulse-parameter chain, one block per drive: dF/dparam = sum over stages of
 // dF/df * df/dparam, and the carrier-frequency co-gradient sum dF/df * E (-sin) t.
 __global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const double* gF,
-                              int K, int N, double dt, const int* pulse_off, double* grad_pulse,
+                              int K, int N, double dt, const int* pulse_off, int n_pulse, double* grad_pulse,
                               double* omega_bar) {
   const int k = blockIdx.x;
   const DriveDev dr = drives[k];
@@ -637,8 +637,12 @@ __global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const 
   for (int x = tid; x <= np; x += blockDim.x) {
     double s = 0.0;
     for (int y = 0; y < (int)blockDim.x; ++y) s += part[y * (np + 1) + x];
-    if (x < np) grad_pulse[pulse_off[k] + x] = s;
-    else omega_bar[k] = s;
+    if (x < np) {
+      const int o = pulse_off[k] + x;
+      if (o >= 0 && o < n_pulse) grad_pulse[o] = s;               // offsets come from the host plan
+    } else {
+      omega_bar[k] = s;
+    }
   }
 }
 
@@ -990,13 +994,15 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) 
   ta.tab = sv.tab;
   ta.tab32 = sv.tab32;
   s.ta = ta;
-  k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
-  ++sv.launches;
-  SG_CUDA_TRY(ctx, cudaGetLastError());
+  // plans first: they upload their offset tables, and every host-to-device copy of
+  // a solve goes before its first kernel (see dcopy)
   sv.mixed = o->precision == SG_MIXED;
   const int pc = path_choice();
   if (pc == 0) sv.oc = onchip_plan_create(s.p, sv.mixed, s.K, s.sumd, st);
   if (pc <= 1 && !(sv.oc && onchip_adjoint_ok(sv.oc))) sv.slab = slab_plan_create(s.p, sv.mixed, st);
+  k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
+  ++sv.launches;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
   {
     const char* e = std::getenv("SG_KTIMING");
     sv.kt.on = e && e[0] == '1';
@@ -1045,6 +1051,13 @@ void fwd_step(Solve& sv, cudaStream_t st, int n, const double2* pin, double2* po
   sv.launches += 4;
 }
 
+// Device-to-device copy as a kernel.  (A cudaMemcpyAsync waiting behind this
+// stream's kernels would sit in a copy-engine queue shared with other streams and
+// hold back their copies until those kernels end.)
+void dcopy(double2* dst, const double2* src, long long n, cudaStream_t st) {
+  k_cast<double><<<grid_for(n), kT, 0, st>>>(src, dst, n, 1.0);
+}
+
 template <typename R>
 sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool init_from_psi,
                       int ckpt_every, std::vector<double2*>* ckpts) {
@@ -1081,9 +1094,7 @@ sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool
     void* Xv = X;
     void* Xov = Xo;
     for (int step = 0; step < s.N; ++step) {
-      if (ckpts && step % ckpt_every == 0)
-        SG_CUDA_TRY(ctx, cudaMemcpyAsync((*ckpts)[step / ckpt_every], pint, n * sizeof(double2),
-                                         cudaMemcpyDeviceToDevice, st));
+      if (ckpts && step % ckpt_every == 0) dcopy((*ckpts)[step / ckpt_every], pint, n, st);
       sv.kt.run(0, step, [&] { return slab_fwd_step(sv.slab, sv.mixed, tab, step, pint, pint, Xv, Xov, Dacc, kA, s.dt, st); });
     }
     slab_from_internal(sv.slab, pint, sv.psi, st);
@@ -1094,9 +1105,7 @@ sg_status run_forward(sg_system* sys, Solve& sv, const long long* cols_dev, bool
   k_cast<R><<<grid_for(n), kT, 0, st>>>(sv.psi, X, n, 1.0);
   ++sv.launches;
   for (int step = 0; step < s.N; ++step) {
-    if (ckpts && step % ckpt_every == 0)
-      SG_CUDA_TRY(ctx, cudaMemcpyAsync((*ckpts)[step / ckpt_every], sv.psi, n * sizeof(double2),
-                                       cudaMemcpyDeviceToDevice, st));
+    if (ckpts && step % ckpt_every == 0) dcopy((*ckpts)[step / ckpt_every], sv.psi, n, st);
     fwd_step<R>(sv, st, step, sv.psi, sv.psi, X, Xo, Dacc);
   }
   SG_CUDA_TRY(ctx, cudaGetLastError());
@@ -1168,17 +1177,31 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
   onchip_to_image(oc, pbar, pimg, st);
   ++sv.launches;
   const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
+  OnchipTables tb{tab, sv.coef, sv.ph, sv.opd_dev};
+  if (sizeof(R) == 4) {
+    // stage-precision copies of the phase, coefficient and operator tables
+    const long long nph = 2 * nst * s.sumd, ncf = nst * s.K, nop = 2 * (long long)s.opdflat.size();
+    float* ph32 = sv.ar.get<float>(nph);
+    float* cf32 = sv.ar.get<float>(std::max(1ll, ncf));
+    float* op32 = sv.ar.get<float>(nop);
+    if (!ph32 || !cf32 || !op32) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the FP32 tables failed");
+    onchip_to_f32(reinterpret_cast<const double*>(sv.ph), ph32, nph, st);
+    if (ncf) onchip_to_f32(sv.coef, cf32, ncf, st);
+    onchip_to_f32(reinterpret_cast<const double*>(sv.opd_dev), op32, nop, st);
+    sv.launches += 3;
+    tb = OnchipTables{tab, cf32, ph32, op32};
+  }
   const int nseg = (int)ckpts.size();
   for (int c = nseg - 1; c >= 0; --c) {
     const int n0 = c * K, n1 = std::min(s.N, n0 + K);
     sv.launches += onchip_forward(oc, tab, nullptr, ckpts[c], nullptr, nullptr, K, n0, n1, s.dt, segY, st);
-    sv.launches += onchip_adjoint(oc, tab, sv.tab, sv.coef, sv.ph, segY, pimg, n0, n1, s.dt, xa, (int)nst,
-                                  gFc, accc, err, st);
+    sv.launches += onchip_adjoint(oc, tb, segY, pimg, n0, n1, s.dt, xa, (int)nst, gFc, accc, err, st);
   }
   onchip_reduce(oc, gFc, accc, nst, s.K, s.p.n1, s.p.ne, acc, st);
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
   int herr = 0;
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));     // reads only from an idle stream (see dcopy)
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
   if (herr) return sg_fail(ctx, SG_E_CUDA, "on-chip adjoint: a bulk copy of a stage input did not complete");
@@ -1267,7 +1290,7 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
     const int nseg = (int)ckpts.size();
     for (int c = nseg - 1; c >= 0; --c) {
       const int n0 = c * K, n1 = std::min(s.N, n0 + K);
-      SG_CUDA_TRY(ctx, cudaMemcpyAsync(pwork, ckpts[c], n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      dcopy(pwork, ckpts[c], n, st);
       k_cast<R><<<grid_for(n), kT, 0, st>>>(pwork, segY[0], n, 1.0);
       ++sv.launches;
       for (int step = n0; step < n1; ++step) {
@@ -1299,7 +1322,7 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
   const int nseg = (int)ckpts.size();
   for (int c = nseg - 1; c >= 0; --c) {
     const int n0 = c * K, n1 = std::min(s.N, n0 + K);
-    SG_CUDA_TRY(ctx, cudaMemcpyAsync(seg[0], ckpts[c], n * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    dcopy(seg[0], ckpts[c], n, st);
     k_cast<R><<<grid_for(n), kT, 0, st>>>(seg[0], X, n, 1.0);
     ++sv.launches;
     for (int step = n0; step < n1 - 1; ++step)
@@ -1424,6 +1447,12 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols_dev, o->col_index, s.S * sizeof(long long), cudaMemcpyHostToDevice, st));
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(lab_dev, lab.data(), s.S * sizeof(int), cudaMemcpyHostToDevice, st));
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(Tg, target, (size_t)s.Dc * s.Dc * sizeof(double2), cudaMemcpyHostToDevice, st));
+  int* poff = nullptr;
+  if (grad) {
+    poff = sv.ar.get<int>(std::max(1, s.K));
+    if (!poff) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+    if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(poff, s.pulse_off.data(), s.K * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
   rc = upload_and_tables(sys, o, sv);
   if (rc != SG_OK) return rc;
   // checkpoints
@@ -1487,7 +1516,6 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     double* ebar = sv.ar.get<double>(s.nq * SG_MAXD);
     double* gpulse = sv.ar.get<double>(std::max(1, s.n_pulse));
     double* gdev = sv.ar.get<double>(3 * s.nq);
-    int* poff = sv.ar.get<int>(std::max(1, s.K));
     double2* pbar = sv.ar.get<double2>(n);
     if (!acc.gF || !acc.obD || !acc.obL || !acc.obR || !acc.ebB || !acc.ebL || !acc.ebR || !acc.jb ||
         !ebar_frame || !omega_bar || !opbar || !ebar || !gpulse || !gdev || !poff || !pbar)
@@ -1502,7 +1530,6 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.jb, 0, std::max(1, ne) * sizeof(double), st));
     SG_CUDA_TRY(ctx, cudaMemsetAsync(ebar_frame, 0, s.nq * SG_MAXD * sizeof(double), st));
     SG_CUDA_TRY(ctx, cudaMemsetAsync(pbar, 0, n * sizeof(double2), st));
-    if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(poff, s.pulse_off.data(), s.K * sizeof(int), cudaMemcpyHostToDevice, st));
     // co-state of the lab-frame columns, its frame-phase energy term, pull back to the frame
     k_scatter_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, barc, pbar);
     if (o->frame == SG_FRAME_INTERACTION) {
@@ -1520,7 +1547,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
       for (auto& d : s.drives) np_max = std::max(np_max, d.kind == SG_ENV_PWC ? d.nseg : 1);
       const int pt = 64;
       k_pulse_chain<<<s.K, pt, pt * (np_max + 1) * sizeof(double), st>>>(
-          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, gpulse, omega_bar);
+          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar);
     } else {
       SG_CUDA_TRY(ctx, cudaMemsetAsync(omega_bar, 0, sizeof(double), st));
     }
@@ -1542,6 +1569,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     if (rc != SG_OK) return rc;
     ++sv.launches;
     cudaEventRecord(ev2, st);
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));   // reads only from an idle stream (see dcopy)
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     std::vector<double> gd(3 * s.nq), jb(std::max(1, ne));
     if (s.n_pulse && grad_pulse)
@@ -1560,6 +1588,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     peak = sv.ar.bytes;
   } else {
     cudaEventRecord(ev2, st);
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   }
   if (Ucomp_out)

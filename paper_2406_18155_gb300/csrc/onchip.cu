@@ -3,16 +3,28 @@
 // Shared-memory images: column c of a CTA's group starts at c * CS (CS = padded
 // column stride, even, so every column and image is 16-byte aligned) and entry t of
 // a column sits at spos(t), the bank-conflict-free padding of the tiled kernels.
-// The register-blocked phases of the tiled kernels (slab_dev.cuh) apply H; their
-// block index runs over all Sc columns.
+// H is applied phase by phase with the register-blocked phases of the tiled kernels
+// (slab_dev.cuh), one d x d block per thread.  (Splitting blocks into their d output
+// columns to occupy more threads on small systems measured slower at every size:
+// the extra loads and index arithmetic cost more than the added parallelism.)
 //
-// Adjoint stage (reverse order 3, 2, 1, 0 of one RK4 step), everything in shared
-// memory:  ks = H kbar_s (phases) -> epilogue: ybar = i ks, Db, pbar, next kbar (in
-// place in ks) -> cross-densities of this stage's term slots between kbar_s and the
-// stored stage input y_s, one warp per slot, reduced across the warp and contracted
-// by the warp's lanes (one lane per level pair) into shared-memory accumulators.
-// The stage input of the next stage arrives by a bulk copy (cp.async.bulk, completion
-// on an mbarrier) and the next table rows by cp.async while this stage computes.
+// Mixed precision keeps the state (forward) and the co-state (adjoint) as
+// float-float pairs (hi + lo, each FP32, renormalised after every addition), so the
+// hot loop has no FP64 arithmetic, which runs at a small fraction of the FP32 rate
+// on this part; the pair carries about 48 significant bits, more than the
+// per-step FP32 increments it accumulates can use.  FP64 mode keeps complex128.
+//
+// Adjoint stage (reverse order 3, 2, 1, 0 of one RK4 step), warp-specialised:
+//   phase warps:   ks = H kbar_s (phases, named barrier among them), then the
+//                  epilogue: ybar = i ks, Db, pbar, next kbar (in place in ks);
+//   density warps: the cross-densities of this stage's term slots between kbar_s
+//                  and the stored stage input y_s, one warp per slot at a time,
+//                  reduced across the warp and contracted by its lanes (one lane
+//                  per level pair) into shared-memory accumulators.
+// Both groups only read kbar_s, y_s and the stage row, so they run side by side;
+// one CTA barrier ends the stage.  The next stage input arrives by a bulk copy
+// (cp.async.bulk, completion on an mbarrier) and the next table rows by cp.async
+// while the stage computes.
 #include "sg_internal.h"
 #include "kplan.h"
 #include "grad.cuh"
@@ -21,15 +33,19 @@
 #include "onchip.h"
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 
 namespace {
 
 // ---------------------------------------------------------------------------
-// asynchronous copies
+// asynchronous copies and barriers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
-// cp.async of 8 or 16 bytes global -> shared (no registers, completes at cp_wait_all)
+// cp.async of 4, 8 or 16 bytes global -> shared (no registers, completes at cp_wait_all)
+__device__ __forceinline__ void cp4(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
+}
 __device__ __forceinline__ void cp8(void* s, const void* g) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
 }
@@ -37,10 +53,10 @@ __device__ __forceinline__ void cp16(void* s, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(s)), "l"(g) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
-template <typename C> __device__ __forceinline__ void cpc(C* s, const C* g);
-template <> __device__ __forceinline__ void cpc<float2>(float2* s, const float2* g) { cp8(s, g); }
-template <> __device__ __forceinline__ void cpc<double2>(double2* s, const double2* g) { cp16(s, g); }
-__device__ __forceinline__ void cpd(double* s, const double* g) { cp8(s, g); }
+__device__ __forceinline__ void cpv(float2* s, const float2* g) { cp8(s, g); }
+__device__ __forceinline__ void cpv(double2* s, const double2* g) { cp16(s, g); }
+__device__ __forceinline__ void cpv(float* s, const float* g) { cp4(s, g); }
+__device__ __forceinline__ void cpv(double* s, const double* g) { cp8(s, g); }
 
 __device__ __forceinline__ void mb_init(uint64_t* mb) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mb)) : "memory");
@@ -78,6 +94,58 @@ __device__ __forceinline__ void mb_wait(uint64_t* mb, unsigned parity, int* err)
   }
   atomicExch(err, 1);
 }
+// Barrier among the first n threads of the CTA (n a multiple of 32); id 0 is __syncthreads.
+__device__ __forceinline__ void bar_sub(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// state: complex128, or float-float pairs in mixed precision
+// ---------------------------------------------------------------------------
+// hi + lo <- hi + lo + x with hi = fl(hi + lo) afterwards (TwoSum, then a fast
+// renormalisation); exact up to the rounding of the low word.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float e = (hi - (s - bb)) + (x - bb);
+  const float l = lo + e;
+  const float h2 = s + l;
+  lo = l - (h2 - s);
+  hi = h2;
+}
+
+template <typename R> struct StateArr;
+template <> struct StateArr<double> {
+  double2* p;
+  __device__ void init(unsigned char* base, int n) { p = reinterpret_cast<double2*>(base); (void)n; }
+  __device__ void set(int e, double2 v) { p[e] = v; }
+  __device__ double2 get(int e) const { return p[e]; }
+  __device__ double2 hi(int e) const { return p[e]; }
+  __device__ void add(int e, double2 x) { p[e] = make_double2(p[e].x + x.x, p[e].y + x.y); }
+};
+template <> struct StateArr<float> {
+  float2 *h, *l;
+  __device__ void init(unsigned char* base, int n) {
+    h = reinterpret_cast<float2*>(base);
+    l = h + n;
+  }
+  __device__ void set(int e, double2 v) {
+    const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
+    h[e] = make_float2(hx, hy);
+    l[e] = make_float2(__double2float_rn(v.x - (double)hx), __double2float_rn(v.y - (double)hy));
+  }
+  __device__ double2 get(int e) const {
+    return make_double2((double)h[e].x + (double)l[e].x, (double)h[e].y + (double)l[e].y);
+  }
+  __device__ float2 hi(int e) const { return h[e]; }
+  __device__ void add(int e, float2 x) {
+    float2 a = h[e], b = l[e];
+    ff_add(a.x, b.x, x.x);
+    ff_add(a.y, b.y, x.y);
+    h[e] = a;
+    l[e] = b;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // plan arguments
@@ -85,43 +153,49 @@ __device__ __forceinline__ void mb_wait(uint64_t* mb, unsigned parity, int* err)
 struct OcArgs {
   int D, S, Sc, nbc, nbt, CS, CSP, ncta, row, K, sumd, n1, ne;
   int ent;               // Sc * D entries per CTA
+  int npw;               // adjoint: phase warps (the rest compute cross-densities)
   // forward shared-memory byte offsets
   int f_ys, f_ks, f_ps, f_dl, f_M;
   // adjoint shared-memory byte offsets
-  int a_xs, a_ks, a_ys, a_yn, a_db, a_pb, a_M, a_T, a_cf, a_ph, a_obD, a_obL, a_obR, a_ebB, a_ebL, a_ebR,
+  int a_xs, a_ks, a_ys, a_yn, a_db, a_pb, a_M, a_cf, a_ph, a_obD, a_obL, a_obR, a_ebB, a_ebL, a_ebR,
       a_jb, a_gs, a_sq;
-  int rowA, Kp;          // row and K rounded up to even counts
+  int rowA, Kp, sumdA;   // row, K and sumd rounded up to even counts
   long long accd;        // doubles per CTA accumulator block (global layout)
 };
 
 template <int DL>
-__device__ __forceinline__ int oc_pos(const OcArgs& oa, int e, int& c, int& t) {
-  c = e / oa.D;
-  t = e - c * oa.D;
+__device__ __forceinline__ int oc_pos(const OcArgs& oa, int e) {
+  const int c = e / oa.D;
+  const int t = e - c * oa.D;
   return c * oa.CS + spos<DL>(t);
 }
 
-// All phases of the single pass over the CTA's Sc columns: ks = H ys.  Ends with a barrier.
+// All phases over the CTA's Sc columns: ks = H ys, one d x d block per thread at a
+// time (phase_block of the tiled kernels), by threads [0, nthr) with barrier `bar`
+// among them after every phase.
 template <int DL, typename C>
 __device__ __forceinline__ void oc_apply(const SlabPass& sp, const OcArgs& oa, const C* __restrict__ M,
-                                         const C* __restrict__ ys, C* __restrict__ ks) {
+                                         const C* __restrict__ ys, C* __restrict__ ks, int nthr, int bar) {
   for (int q = 0; q < sp.nph; ++q) {
     const Phase& P = sp.ph[q];
-    for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
+    for (int b = threadIdx.x; b < oa.nbt; b += nthr) {
       const int c = b / oa.nbc;
       const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
       if (P.allpar) phase_block<DL, true>(P, M, ys, ks, pb, q == 0);
       else phase_block<DL, false>(P, M, ys, ks, pb, q == 0);
     }
-    __syncthreads();
+    if (bar == 0) __syncthreads();
+    else bar_sub(bar, nthr);
   }
 }
 
-template <typename C>
-__device__ __forceinline__ void issue_row(const C* __restrict__ tab, int row, int q, C* dst) {
-  const C* src = tab + (size_t)q * row;
-  for (int i = threadIdx.x; i < row; i += blockDim.x) cpc<C>(dst + i, src + i);
+template <typename V>
+__device__ __forceinline__ void issue_rows(const V* __restrict__ tab, int row, int q, V* dst, int tid, int nthr) {
+  const V* src = tab + (size_t)q * row;
+  for (int i = tid; i < row; i += nthr) cpv(dst + i, src + i);
 }
+
+__host__ __device__ __forceinline__ int stage_row(int s) { return s == 0 ? 0 : (s == 3 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
 // forward
@@ -135,51 +209,50 @@ k_oc_fwd(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   extern __shared__ __align__(16) unsigned char sm[];
   C* ys = reinterpret_cast<C*>(sm + oa.f_ys);
   C* ks = reinterpret_cast<C*>(sm + oa.f_ks);
-  double2* ps = reinterpret_cast<double2*>(sm + oa.f_ps);
+  StateArr<R> ps;
+  ps.init(sm + oa.f_ps, oa.ent);
   C* dl = reinterpret_cast<C*>(sm + oa.f_dl);
-  C* Mb[2] = {reinterpret_cast<C*>(sm + oa.f_M), reinterpret_cast<C*>(sm + oa.f_M) + oa.rowA};
+  C* const M0 = reinterpret_cast<C*>(sm + oa.f_M);
+  C* const M1 = M0 + oa.rowA;
   const int cta = blockIdx.x;
   const R h = (R)dt;
   for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
-    int c, t;
-    const int pos = oc_pos<DL>(oa, e, c, t);
+    const int c = e / oa.D, t = e - c * oa.D;
     const int col = cta * oa.Sc + c;
     double2 v = make_double2(0.0, 0.0);
     if (img_in) v = img_in[(size_t)cta * oa.ent + e];
     else if (col < oa.S) v = psi_api[(size_t)t * oa.S + col];
-    ps[e] = v;
-    ys[pos] = to_c(v, R(0));
+    ps.set(e, v);
+    ys[oc_pos<DL>(oa, e)] = ps.hi(e);
   }
-  if (n0 < n1) issue_row<C>(tab, oa.row, 3 * n0, Mb[0]);
+  if (n0 < n1) issue_rows<C>(tab, oa.row, 3 * n0, M0, threadIdx.x, blockDim.x);
   cp_wait_all();
   __syncthreads();
   int buf = 0;
   for (int step = n0; step < n1; ++step) {
     if (ck_out && (step - n0) % K == 0) {
       double2* ck = ck_out + ((size_t)((step - n0) / K) * oa.ncta + cta) * oa.ent;
-      for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) ck[e] = ps[e];
+      for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) ck[e] = ps.get(e);
     }
 #pragma unroll 1
     for (int s = 0; s < 4; ++s) {
+      C* const Mc = buf ? M1 : M0;
       // next stage's table row
       const int nstep = s < 3 ? step : step + 1, ns = s < 3 ? s + 1 : 0;
-      if (nstep < n1) issue_row<C>(tab, oa.row, 3 * nstep + (ns == 0 ? 0 : (ns == 3 ? 2 : 1)), Mb[buf ^ 1]);
+      if (nstep < n1) issue_rows<C>(tab, oa.row, 3 * nstep + stage_row(ns), buf ? M0 : M1, threadIdx.x, blockDim.x);
       if (segY) {
         C* g = segY + ((size_t)(4 * (step - n0) + s) * oa.ncta + cta) * oa.CSP;
         for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
-          int c, t;
-          const int pos = oc_pos<DL>(oa, e, c, t);
+          const int pos = oc_pos<DL>(oa, e);
           g[pos] = ys[pos];
         }
       }
-      oc_apply<DL>(sp, oa, Mb[buf], ys, ks);
+      oc_apply<DL>(sp, oa, Mc, ys, ks, blockDim.x, 0);
       for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
-        int c, t;
-        const int pos = oc_pos<DL>(oa, e, c, t);
+        const int pos = oc_pos<DL>(oa, e);
         const C a = ks[pos];
         const C kk = cmk<C>(a.y, -a.x);                 // -i H y
-        const double2 p = ps[e];
-        const C pr = to_c(p, R(0));
+        const C pr = ps.hi(e);
         if (s == 0) {
           dl[e] = cmk<C>(h / 6 * kk.x, h / 6 * kk.y);
           ys[pos] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
@@ -193,10 +266,8 @@ k_oc_fwd(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
           ys[pos] = cmk<C>(pr.x + h * kk.x, pr.y + h * kk.y);
         } else {
           const C d = dl[e];
-          const R incx = d.x + h / 6 * kk.x, incy = d.y + h / 6 * kk.y;
-          const double2 pn = make_double2(p.x + (double)incx, p.y + (double)incy);
-          ps[e] = pn;
-          ys[pos] = to_c(pn, R(0));
+          ps.add(e, cmk<C>(d.x + h / 6 * kk.x, d.y + h / 6 * kk.y));
+          ys[pos] = ps.hi(e);
         }
       }
       cp_wait_all();
@@ -208,7 +279,7 @@ k_oc_fwd(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
     for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
       const int c = e / oa.D, t = e - c * oa.D;
       const int col = cta * oa.Sc + c;
-      if (col < oa.S) psi_out[(size_t)t * oa.S + col] = ps[e];
+      if (col < oa.S) psi_out[(size_t)t * oa.S + col] = ps.get(e);
     }
   }
 }
@@ -222,25 +293,31 @@ __device__ __forceinline__ C shfl_xor_c(C v, int o) {
   v.y = __shfl_xor_sync(0xffffffffu, v.y, o);
   return v;
 }
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+template <typename C> __device__ __forceinline__ C cmulT(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C cconjT(C a) { return cmk<C>(a.x, -a.y); }
 
-// Shared-memory accumulators of one CTA (level-pair stride DL * DL, level stride DL).
+// Shared-memory accumulators of one CTA and segment (level-pair stride DL * DL, level stride DL).
+template <typename T>
 struct OcAcc {
-  double2 *obD, *obL, *obR;
-  double *ebB, *ebL, *ebR, *jb, *gs;
+  typedef typename CT<T>::T C;
+  C *obD, *obL, *obR;
+  T *ebB, *ebL, *ebR, *jb, *gs;
 };
 
-// Energy co-gradient of one slot from the lanes' qv(a, b) = -Im(W_ab X_ab) t:
-// eb[a] += sum_b qv(a, b) - sum_b qv(b, a).
-template <int DL>
-__device__ __forceinline__ void eb_rowcol(double qv, int lane, double* sq, double* eb) {
+// eb[a] += sum_b qv(a, b) - sum_b qv(b, a) from the lanes' qv (lane = a * DL + b).
+template <int DL, typename T>
+__device__ __forceinline__ void eb_rowcol(T qv, int lane, T* sq, T* eb) {
   sq[lane] = qv;
   __syncwarp();
   if (lane < DL) {
-    double s = 0.0;
+    T s = 0;
 #pragma unroll
     for (int b = 0; b < DL; ++b) s += sq[lane * DL + b] - sq[b * DL + lane];
     eb[lane] += s;
@@ -249,32 +326,35 @@ __device__ __forceinline__ void eb_rowcol(double qv, int lane, double* sq, doubl
 }
 
 // Contraction of one slot's W (lane = level pair a * DL + b, lanes >= DL^2 hold 0)
-// into the co-gradients: the same sums as contract_slot, spread over the warp.
-//   1-body slot, drive k:  gF[q][k] += Re sum W O_k(t),  obD[k] += f_k conj(W P)
-//   edge side:             jb += Re sum W A(t) (side a),  obL/obR += J conj(W P) / conj(W P)
+// into the co-gradients: the sums of contract_slot spread over the warp, in the
+// stage precision T.
+//   1-body slot, drive k:  gF[q][k] = Re sum W O_k(t),    obD[k] += f_k conj(W P)
+//   edge side:             jb += Re sum W A(t) (side a),  obL += J conj(W P), obR += conj(W P)
 //   interaction frame:     eb[a] += sum_b qv(a, b) - qv(b, a),  qv = -Im(W_ab X_ab(t)) t
 //   lab frame, 1-body:     eb[a] += Re W_aa
-template <int DL>
-__device__ __forceinline__ void oc_contract(const XArgs& xa, int slot, double2 w, int lane, const double2* tabrow,
-                                            const double* cf, const double2* phs, double t, int q, int s,
-                                            const OcAcc& A, double* sq, double* gFc) {
+// with P_ab = exp(i (E_a - E_b) t) and X the stage's term matrix (B, L or R).
+template <int DL, typename T>
+__device__ __forceinline__ void oc_contract(const XArgs& xa, const typename CT<T>::T* __restrict__ opd, int slot,
+                                            typename CT<T>::T w, int lane, const typename CT<T>::T* tabrow,
+                                            const T* cf, const typename CT<T>::T* phs, T t, int q, int s,
+                                            const OcAcc<T>& A, T* sq, double* gFc) {
+  typedef typename CT<T>::T C;
   const KPlan& p = xa.p;
   const bool inter = xa.frame == SG_FRAME_INTERACTION;
   const bool on = lane < DL * DL;
   const int ia = on ? lane / DL : 0, ib = on ? lane - ia * DL : 0;
   if (slot < p.n1) {
     const int u = slot, i = p.s1_mode[u];
-    const double2 P = on ? cmul(phs[xa.eoff[i] + ia], cconj(phs[xa.eoff[i] + ib])) : make_double2(0.0, 0.0);
+    const C P = on ? cmulT(phs[xa.eoff[i] + ia], cconjT(phs[xa.eoff[i] + ib])) : cmk<C>(0.0, 0.0);
     for (int x = xa.drv_of_slot_start[u]; x < xa.drv_of_slot_start[u + 1]; ++x) {
       const int k = xa.drv_list[x];
-      double g = 0.0;
+      T g = 0;
       if (on) {
-        const double2 O = __ldg(xa.opd + xa.opd_off[i] + xa.drv_op[k] * DL * DL + lane);
-        const double2 Ot = cmul(O, P);
+        const C Ot = cmulT(opd[xa.opd_off[i] + xa.drv_op[k] * DL * DL + lane], P);
         g = w.x * Ot.x - w.y * Ot.y;
-        const double2 cw = cmul(cconj(w), cconj(P));
-        const double fk = cf[k];
-        double2& ob = A.obD[k * DL * DL + lane];
+        const C cw = cmulT(cconjT(w), cconjT(P));
+        const T fk = cf[k];
+        C& ob = A.obD[k * DL * DL + lane];
         ob.x += fk * cw.x;
         ob.y += fk * cw.y;
       }
@@ -282,14 +362,14 @@ __device__ __forceinline__ void oc_contract(const XArgs& xa, int slot, double2 w
       if (lane == 0) {
         // stages 2 and 1 share the slot q = 3n + 1: hold stage 2's share, store once
         if (s == 2) A.gs[k] = g;
-        else gFc[(size_t)q * xa.K + k] = s == 1 ? A.gs[k] + g : g;
+        else gFc[(size_t)q * xa.K + k] = s == 1 ? (double)A.gs[k] + (double)g : (double)g;
       }
     }
-    double* eb = A.ebB + u * DL;
+    T* eb = A.ebB + u * DL;
     if (inter) {
-      double qv = 0.0;
+      T qv = 0;
       if (on) {
-        const double2 v = cmul(w, tabrow[p.s1_off[u] + lane]);
+        const C v = cmulT(w, tabrow[p.s1_off[u] + lane]);
         qv = -v.y * t;
       }
       eb_rowcol<DL>(qv, lane, sq, eb);
@@ -301,22 +381,21 @@ __device__ __forceinline__ void oc_contract(const XArgs& xa, int slot, double2 w
   const int side = (slot - p.n1) / p.ne, qe = (slot - p.n1) % p.ne;
   const int i = side == 0 ? p.e_a[qe] : p.e_b[qe];
   const int op = side == 0 ? xa.e_opa[qe] : xa.e_opb[qe];
-  const double sc = side == 0 ? xa.J[qe] : 1.0;
-  double jg = 0.0;
+  const T sc = side == 0 ? (T)xa.J[qe] : (T)1;
+  T jg = 0;
   if (on) {
-    const double2 P = cmul(phs[xa.eoff[i] + ia], cconj(phs[xa.eoff[i] + ib]));
-    const double2 O = __ldg(xa.opd + xa.opd_off[i] + op * DL * DL + lane);
-    const double2 At = cmul(O, P);
+    const C P = cmulT(phs[xa.eoff[i] + ia], cconjT(phs[xa.eoff[i] + ib]));
+    const C At = cmulT(opd[xa.opd_off[i] + op * DL * DL + lane], P);
     jg = w.x * At.x - w.y * At.y;
-    const double2 cw = cmul(cconj(w), cconj(P));
-    double2& ob = (side == 0 ? A.obL : A.obR)[qe * DL * DL + lane];
+    const C cw = cmulT(cconjT(w), cconjT(P));
+    C& ob = (side == 0 ? A.obL : A.obR)[qe * DL * DL + lane];
     ob.x += sc * cw.x;
     ob.y += sc * cw.y;
   }
   if (inter) {
-    double qv = 0.0;
+    T qv = 0;
     if (on) {
-      const double2 v = cmul(w, tabrow[(side == 0 ? p.e_offL[qe] : p.e_offR[qe]) + lane]);
+      const C v = cmulT(w, tabrow[(side == 0 ? p.e_offL[qe] : p.e_offR[qe]) + lane]);
       qv = -v.y * t;
     }
     eb_rowcol<DL>(qv, lane, sq, (side == 0 ? A.ebL : A.ebR) + qe * DL);
@@ -329,8 +408,8 @@ __device__ __forceinline__ void oc_contract(const XArgs& xa, int slot, double2 w
 
 template <typename R, int DL, bool PARX>
 __global__ void __launch_bounds__(kST, 1)
-k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, const double2* __restrict__ tab64,
-         const double* __restrict__ coef, const double2* __restrict__ ph,
+k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, const R* __restrict__ coef,
+         const typename CT<R>::T* __restrict__ ph, const typename CT<R>::T* __restrict__ opd,
          const typename CT<R>::T* __restrict__ segY, double2* __restrict__ pbar_img, int n0, int n1, double dt,
          XArgs xa, double* __restrict__ gF_cta, double* __restrict__ acc_cta, long long nstK,
          int* __restrict__ err) {
@@ -342,53 +421,54 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   C* ys = reinterpret_cast<C*>(sm + oa.a_ys);
   C* yn = reinterpret_cast<C*>(sm + oa.a_yn);
   C* db = reinterpret_cast<C*>(sm + oa.a_db);
-  double2* pb = reinterpret_cast<double2*>(sm + oa.a_pb);
-  C* Mb[2] = {reinterpret_cast<C*>(sm + oa.a_M), reinterpret_cast<C*>(sm + oa.a_M) + oa.rowA};
-  double2* Tb[2] = {reinterpret_cast<double2*>(sm + oa.a_T), reinterpret_cast<double2*>(sm + oa.a_T) + oa.row};
-  double* cf[2] = {reinterpret_cast<double*>(sm + oa.a_cf), reinterpret_cast<double*>(sm + oa.a_cf) + oa.Kp};
-  double2* phb[2] = {reinterpret_cast<double2*>(sm + oa.a_ph), reinterpret_cast<double2*>(sm + oa.a_ph) + oa.sumd};
-  OcAcc A;
-  A.obD = reinterpret_cast<double2*>(sm + oa.a_obD);
-  A.obL = reinterpret_cast<double2*>(sm + oa.a_obL);
-  A.obR = reinterpret_cast<double2*>(sm + oa.a_obR);
-  A.ebB = reinterpret_cast<double*>(sm + oa.a_ebB);
-  A.ebL = reinterpret_cast<double*>(sm + oa.a_ebL);
-  A.ebR = reinterpret_cast<double*>(sm + oa.a_ebR);
-  A.jb = reinterpret_cast<double*>(sm + oa.a_jb);
-  A.gs = reinterpret_cast<double*>(sm + oa.a_gs);
+  StateArr<R> pb;
+  pb.init(sm + oa.a_pb, oa.ent);
+  C* const M0 = reinterpret_cast<C*>(sm + oa.a_M);
+  C* const M1 = M0 + oa.rowA;
+  R* const cf0 = reinterpret_cast<R*>(sm + oa.a_cf);
+  R* const cf1 = cf0 + oa.Kp;
+  C* const ph0 = reinterpret_cast<C*>(sm + oa.a_ph);
+  C* const ph1 = ph0 + oa.sumdA;
+  OcAcc<R> A;
+  A.obD = reinterpret_cast<C*>(sm + oa.a_obD);
+  A.obL = reinterpret_cast<C*>(sm + oa.a_obL);
+  A.obR = reinterpret_cast<C*>(sm + oa.a_obR);
+  A.ebB = reinterpret_cast<R*>(sm + oa.a_ebB);
+  A.ebL = reinterpret_cast<R*>(sm + oa.a_ebL);
+  A.ebR = reinterpret_cast<R*>(sm + oa.a_ebR);
+  A.jb = reinterpret_cast<R*>(sm + oa.a_jb);
+  A.gs = reinterpret_cast<R*>(sm + oa.a_gs);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* sq = reinterpret_cast<double*>(sm + oa.a_sq) + warp * 32;
+  const int nphase = oa.npw * 32;                      // phase threads: [0, nphase)
+  const int nxw = kST / 32 - oa.npw;                   // density warps: [npw, 8)
+  R* sq = reinterpret_cast<R*>(sm + oa.a_sq) + warp * 32;
   const int cta = blockIdx.x;
   const R h = (R)dt;
   const int DD = DL * DL;
-  for (int i = threadIdx.x; i < oa.K * DD; i += blockDim.x) A.obD[i] = make_double2(0.0, 0.0);
-  for (int i = threadIdx.x; i < oa.ne * DD; i += blockDim.x) A.obL[i] = A.obR[i] = make_double2(0.0, 0.0);
-  for (int i = threadIdx.x; i < oa.n1 * DL; i += blockDim.x) A.ebB[i] = 0.0;
-  for (int i = threadIdx.x; i < oa.ne * DL; i += blockDim.x) A.ebL[i] = A.ebR[i] = 0.0;
-  for (int i = threadIdx.x; i < oa.ne; i += blockDim.x) A.jb[i] = 0.0;
-  for (int i = threadIdx.x; i < oa.K; i += blockDim.x) A.gs[i] = 0.0;
+  for (int i = threadIdx.x; i < oa.K * DD; i += blockDim.x) A.obD[i] = cmk<C>(0.0, 0.0);
+  for (int i = threadIdx.x; i < oa.ne * DD; i += blockDim.x) A.obL[i] = A.obR[i] = cmk<C>(0.0, 0.0);
+  for (int i = threadIdx.x; i < oa.n1 * DL; i += blockDim.x) A.ebB[i] = 0;
+  for (int i = threadIdx.x; i < oa.ne * DL; i += blockDim.x) A.ebL[i] = A.ebR[i] = 0;
+  for (int i = threadIdx.x; i < oa.ne; i += blockDim.x) A.jb[i] = 0;
+  for (int i = threadIdx.x; i < oa.K; i += blockDim.x) A.gs[i] = 0;
   if (threadIdx.x == 0) mb_init(&mbar);
-  // co-state, and kbar_4 = dt/6 pbar of the segment's last step
+  // co-state, and kbar_4 = dt/6 pbar of the segment's last step (the epilogue's formula)
   for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
-    int c, t;
-    const int pos = oc_pos<DL>(oa, e, c, t);
-    const double2 v = pbar_img[(size_t)cta * oa.ent + e];
-    pb[e] = v;
-    const C qv = to_c(v, R(0));
-    xs[pos] = cmk<C>(h / 6 * qv.x, h / 6 * qv.y);
+    pb.set(e, pbar_img[(size_t)cta * oa.ent + e]);
+    const C qv = pb.hi(e);
+    xs[oc_pos<DL>(oa, e)] = cmk<C>(h / 6 * qv.x, h / 6 * qv.y);
   }
   __syncthreads();
   const unsigned img_bytes = (unsigned)(oa.CSP * sizeof(C));
   double* gFc = gF_cta + (size_t)cta * nstK;
-  // prefetch of stage s of step n into (ydst, buffer b)
+  // prefetch of stage s of step n: its input into ydst, its rows into buffer b
   auto issue = [&](int n, int s, C* ydst, int b) {
     if (threadIdx.x == 0)
       bulk_load(ydst, segY + ((size_t)(4 * (n - n0) + s) * oa.ncta + cta) * oa.CSP, img_bytes, &mbar);
-    const int q = 3 * n + (s == 0 ? 0 : (s == 3 ? 2 : 1));
-    issue_row<C>(tab, oa.row, q, Mb[b]);
-    issue_row<double2>(tab64, oa.row, q, Tb[b]);
-    for (int i = threadIdx.x; i < oa.K; i += blockDim.x) cpd(cf[b] + i, coef + (size_t)q * oa.K + i);
-    for (int i = threadIdx.x; i < oa.sumd; i += blockDim.x) cpc<double2>(phb[b] + i, ph + (size_t)q * oa.sumd + i);
+    const int q = 3 * n + stage_row(s);
+    issue_rows<C>(tab, oa.row, q, b ? M1 : M0, threadIdx.x, blockDim.x);
+    issue_rows<R>(coef, oa.K, q, b ? cf1 : cf0, threadIdx.x, blockDim.x);
+    issue_rows<C>(ph, oa.sumd, q, b ? ph1 : ph0, threadIdx.x, blockDim.x);
   };
   unsigned parity = 0;
   if (n0 < n1) {
@@ -403,71 +483,71 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   for (int step = n1 - 1; step >= n0; --step) {
 #pragma unroll 1
     for (int s = 3; s >= 0; --s) {
-      const int j = s == 0 ? 0 : (s == 3 ? 2 : 1);
-      const int q = 3 * step + j;
-      const double tq = (double)(2 * step + j) * dt * 0.5;
+      const int q = 3 * step + stage_row(s);
+      const R tq = (R)((double)(2 * step + stage_row(s)) * dt * 0.5);
       const int pn = s > 0 ? step : step - 1, psn = s > 0 ? s - 1 : 3;
       const bool more = pn >= n0;
+      const C* Mc = buf ? M1 : M0;
       if (more) issue(pn, psn, yn, buf ^ 1);
-      oc_apply<DL>(sp, oa, Mb[buf], xs, ks);
-      // epilogue: ybar = i H kbar; next kbar written over ks
-      for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
-        int c, t;
-        const int pos = oc_pos<DL>(oa, e, c, t);
-        const C a = ks[pos];
-        const C y = cmk<C>(-a.y, a.x);
-        const double2 pv = pb[e];
-        const C pr = to_c(pv, R(0));
-        if (s == 3) {
-          db[e] = y;
-          ks[pos] = cmk<C>(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
-        } else if (s == 2) {
-          const C d = db[e];
-          db[e] = cmk<C>(d.x + y.x, d.y + y.y);
-          ks[pos] = cmk<C>(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
-        } else if (s == 1) {
-          const C d = db[e];
-          db[e] = cmk<C>(d.x + y.x, d.y + y.y);
-          ks[pos] = cmk<C>(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
-        } else {
-          const C d = db[e];
-          const double2 pnv = make_double2(pv.x + (double)(d.x + y.x), pv.y + (double)(d.y + y.y));
-          pb[e] = pnv;
-          const C qq = to_c(pnv, R(0));
-          ks[pos] = cmk<C>(h / 6 * qq.x, h / 6 * qq.y);
-        }
-      }
-      // cross-densities of this stage (kbar_s in xs, y_s in ys), one warp per slot
-#pragma unroll 1
-      for (int sl = 0; sl < kSPW; ++sl) {
-        const int slot = warp + sl * (kST / 32);
-        if (slot >= sp.nx) continue;                // warp-uniform
-        const Phase& P = sp.ph[sp.x_ph[slot]];
-        const int type = sp.x_type[slot];
-        C acc[NA];
-#pragma unroll
-        for (int a = 0; a < NA; ++a) acc[a] = cmk<C>(0.0, 0.0);
-        for (int b = lane; b < oa.nbt; b += 32) {
-          const int c = b / oa.nbc;
-          xd_slot<DL, PARX>(P, type, Mb[buf], xs, ys, blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS, acc);
-        }
-#pragma unroll
-        for (int a = 0; a < NA; ++a)
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const C v = shfl_xor_c(acc[a], o);
-            acc[a].x += v.x;
-            acc[a].y += v.y;
+      if (warp < oa.npw) {
+        // phase warps: ks = H kbar_s, then the adjoint epilogue
+        oc_apply<DL>(sp, oa, Mc, xs, ks, nphase, 1);
+        for (int e = threadIdx.x; e < oa.ent; e += nphase) {
+          const int pos = oc_pos<DL>(oa, e);
+          const C a = ks[pos];
+          const C y = cmk<C>(-a.y, a.x);                 // ybar = i H kbar
+          const C pr = pb.hi(e);
+          if (s == 3) {
+            db[e] = y;
+            ks[pos] = cmk<C>(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
+          } else if (s == 2) {
+            const C d = db[e];
+            db[e] = cmk<C>(d.x + y.x, d.y + y.y);
+            ks[pos] = cmk<C>(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
+          } else if (s == 1) {
+            const C d = db[e];
+            db[e] = cmk<C>(d.x + y.x, d.y + y.y);
+            ks[pos] = cmk<C>(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
+          } else {
+            const C d = db[e];
+            pb.add(e, cmk<C>(d.x + y.x, d.y + y.y));
+            const C qq = pb.hi(e);
+            ks[pos] = cmk<C>(h / 6 * qq.x, h / 6 * qq.y);
           }
-        // this lane's level pair
-        C mine = cmk<C>(0.0, 0.0);
+        }
+      } else {
+        // density warps: cross-densities of this stage, one slot per warp at a time
+        const C* phs = buf ? ph1 : ph0;
+        const R* cfs = buf ? cf1 : cf0;
+#pragma unroll 1
+        for (int slot = warp - oa.npw; slot < sp.nx; slot += nxw) {
+          const Phase& P = sp.ph[sp.x_ph[slot]];
+          const int type = sp.x_type[slot];
+          C acc[NA];
 #pragma unroll
-        for (int a = 0; a < DL; ++a)
+          for (int a = 0; a < NA; ++a) acc[a] = cmk<C>(0.0, 0.0);
+          for (int b = lane; b < oa.nbt; b += 32) {
+            const int c = b / oa.nbc;
+            xd_slot<DL, PARX>(P, type, Mc, xs, ys, blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS, acc);
+          }
 #pragma unroll
-          for (int b = 0; b < DL; ++b)
-            if ((!PARX || ((a + b) & 1)) && lane == a * DL + b) mine = acc[xd_i<DL, PARX>(a, b)];
-        const double2 w = make_double2((double)mine.y, -(double)mine.x);   // W = -i C
-        oc_contract<DL>(xa, sp.x_gslot[slot], w, lane, Tb[buf], cf[buf], phb[buf], tq, q, s, A, sq, gFc);
+          for (int a = 0; a < NA; ++a)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              const C v = shfl_xor_c(acc[a], o);
+              acc[a].x += v.x;
+              acc[a].y += v.y;
+            }
+          // this lane's level pair
+          C mine = cmk<C>(0.0, 0.0);
+#pragma unroll
+          for (int a = 0; a < DL; ++a)
+#pragma unroll
+            for (int b = 0; b < DL; ++b)
+              if ((!PARX || ((a + b) & 1)) && lane == a * DL + b) mine = acc[xd_i<DL, PARX>(a, b)];
+          const C w = cmk<C>(mine.y, -mine.x);             // W = -i C
+          oc_contract<DL, R>(xa, opd, sp.x_gslot[slot], w, lane, Mc, cfs, phs, tq, q, s, A, sq, gFc);
+        }
       }
       if (more) {
         cp_wait_all();
@@ -480,8 +560,8 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
       buf ^= 1;
     }
   }
-  for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) pbar_img[(size_t)cta * oa.ent + e] = pb[e];
-  // add the CTA's accumulators to its global block (GradAcc layout, SG_MAXD strides)
+  for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) pbar_img[(size_t)cta * oa.ent + e] = pb.get(e);
+  // add the segment's accumulators to the CTA's global block (GradAcc layout, SG_MAXD strides)
   double* G = acc_cta + (size_t)cta * oa.accd;
   const int MD2 = SG_MAXD * SG_MAXD;
   double* gD = G;
@@ -494,24 +574,24 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   for (int i = threadIdx.x; i < oa.K * DD; i += blockDim.x) {
     const int k = i / DD, ab = i - k * DD, a = ab / DL, b = ab - a * DL;
     double* g = gD + 2 * ((size_t)k * MD2 + a * SG_MAXD + b);
-    g[0] += A.obD[i].x;
-    g[1] += A.obD[i].y;
+    g[0] += (double)A.obD[i].x;
+    g[1] += (double)A.obD[i].y;
   }
   for (int i = threadIdx.x; i < oa.ne * DD; i += blockDim.x) {
     const int k = i / DD, ab = i - k * DD, a = ab / DL, b = ab - a * DL;
     double* g = gL + 2 * ((size_t)k * MD2 + a * SG_MAXD + b);
-    g[0] += A.obL[i].x;
-    g[1] += A.obL[i].y;
+    g[0] += (double)A.obL[i].x;
+    g[1] += (double)A.obL[i].y;
     g = gR + 2 * ((size_t)k * MD2 + a * SG_MAXD + b);
-    g[0] += A.obR[i].x;
-    g[1] += A.obR[i].y;
+    g[0] += (double)A.obR[i].x;
+    g[1] += (double)A.obR[i].y;
   }
-  for (int i = threadIdx.x; i < oa.n1 * DL; i += blockDim.x) geB[(i / DL) * SG_MAXD + i % DL] += A.ebB[i];
+  for (int i = threadIdx.x; i < oa.n1 * DL; i += blockDim.x) geB[(i / DL) * SG_MAXD + i % DL] += (double)A.ebB[i];
   for (int i = threadIdx.x; i < oa.ne * DL; i += blockDim.x) {
-    geL[(i / DL) * SG_MAXD + i % DL] += A.ebL[i];
-    geR[(i / DL) * SG_MAXD + i % DL] += A.ebR[i];
+    geL[(i / DL) * SG_MAXD + i % DL] += (double)A.ebL[i];
+    geR[(i / DL) * SG_MAXD + i % DL] += (double)A.ebR[i];
   }
-  for (int i = threadIdx.x; i < oa.ne; i += blockDim.x) gjb[i] += A.jb[i];
+  for (int i = threadIdx.x; i < oa.ne; i += blockDim.x) gjb[i] += (double)A.jb[i];
 }
 
 // API layout [D][S] -> state image [cta][Sc][D]
@@ -523,6 +603,12 @@ __global__ void k_oc_image(OcArgs oa, const double2* __restrict__ api, double2* 
     const int t = (int)(e - col * oa.D);
     img[e] = col < oa.S ? api[(size_t)t * oa.S + col] : make_double2(0.0, 0.0);
   }
+}
+
+// FP64 -> FP32 copy of the per-stage phase and coefficient tables and the operators.
+__global__ void k_oc_f32(const double* __restrict__ src, float* __restrict__ dst, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    dst[i] = __double2float_rn(src[i]);
 }
 
 // Fixed-order sum over CTAs of the per-CTA gradient blocks.
@@ -582,6 +668,7 @@ size_t al16(size_t x) { return (x + 15) & ~size_t(15); }
 // Shared-memory layout for Sc columns per CTA; returns the forward and adjoint bytes.
 void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   const bool pw2 = DL == 2 || DL == 4;
+  const size_t rs = cs / 2;                       // real of the stage precision
   a.CS = pw2 ? spad(a.D) : a.D;
   a.CS += a.CS & 1;
   a.CSP = a.Sc * a.CS;
@@ -589,6 +676,7 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   a.nbt = a.Sc * a.nbc;
   a.rowA = a.row + (a.row & 1);
   a.Kp = std::max(2, a.K + (a.K & 1));
+  a.sumdA = a.sumd + (a.sumd & 1);
   size_t o = 0;
   auto take = [&](size_t bytes) { size_t r = o; o = al16(o + bytes); return (int)r; };
   a.f_ys = take(a.CSP * cs);
@@ -605,19 +693,18 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   a.a_db = take((size_t)a.ent * cs);
   a.a_pb = take((size_t)a.ent * 16);
   a.a_M = take(2 * (size_t)a.rowA * cs);
-  a.a_T = take(2 * (size_t)a.row * 16);
-  a.a_cf = take(2 * (size_t)a.Kp * 8);
-  a.a_ph = take(2 * (size_t)a.sumd * 16);
+  a.a_cf = take(2 * (size_t)a.Kp * rs);
+  a.a_ph = take(2 * (size_t)a.sumdA * cs);
   const int DD = DL * DL;
-  a.a_obD = take((size_t)std::max(1, a.K) * DD * 16);
-  a.a_obL = take((size_t)std::max(1, a.ne) * DD * 16);
-  a.a_obR = take((size_t)std::max(1, a.ne) * DD * 16);
-  a.a_ebB = take((size_t)std::max(1, a.n1) * DL * 8);
-  a.a_ebL = take((size_t)std::max(1, a.ne) * DL * 8);
-  a.a_ebR = take((size_t)std::max(1, a.ne) * DL * 8);
-  a.a_jb = take((size_t)std::max(1, a.ne) * 8);
-  a.a_gs = take((size_t)std::max(1, a.K) * 8);
-  a.a_sq = take((size_t)(kST / 32) * 32 * 8);
+  a.a_obD = take((size_t)std::max(1, a.K) * DD * cs);
+  a.a_obL = take((size_t)std::max(1, a.ne) * DD * cs);
+  a.a_obR = take((size_t)std::max(1, a.ne) * DD * cs);
+  a.a_ebB = take((size_t)std::max(1, a.n1) * DL * rs);
+  a.a_ebL = take((size_t)std::max(1, a.ne) * DL * rs);
+  a.a_ebR = take((size_t)std::max(1, a.ne) * DL * rs);
+  a.a_jb = take((size_t)std::max(1, a.ne) * rs);
+  a.a_gs = take((size_t)std::max(1, a.K) * rs);
+  a.a_sq = take((size_t)(kST / 32) * 32 * rs);
   adj = o;
 }
 
@@ -653,8 +740,9 @@ OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cuda
   a.n1 = p.n1;
   a.ne = p.ne;
   const size_t cs = mixed ? sizeof(float2) : sizeof(double2);
-  // columns per CTA: enough blocks to give every thread one per phase, within shared memory
-  int sc0 = std::max(1, std::min(p.S, std::max(1, kST / std::max(1, a.nbc))));
+  // Columns per CTA: as many as give every thread one block per phase, within shared
+  // memory (fewer CTAs per solve amortise the per-stage barriers and contractions).
+  int sc0 = std::max(1, std::min(p.S, (kST + a.nbc - 1) / std::max(1, a.nbc)));
   size_t fwd = 0, adj = 0;
   int best_adj = 0, best_fwd = 0;
   for (int sc = sc0; sc >= 1; --sc) {
@@ -672,6 +760,24 @@ OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cuda
   oc->adj_ok = adj <= limit;
   oc->sm_fwd = fwd;
   oc->sm_adj = adj;
+  // Adjoint warp split from the complex multiply-adds per stage: a phase block costs
+  // 2 d^3 per edge and d^3 per 1-body term, a slot's cross-density d^3 (1-body) or
+  // 2 d^3 (edge side); parity-odd operators halve both.  SG_OC_PW overrides (1..7).
+  {
+    const SlabPass& sp0 = h->pass[0];
+    double wp = 0.0, wx = 0.0;
+    for (int q = 0; q < sp0.nph; ++q) {
+      const Phase& P = sp0.ph[q];
+      wp += (P.offL >= 0 ? 2.0 : 0.0) + (P.offA >= 0 ? 1.0 : 0.0) + (P.offB >= 0 ? 1.0 : 0.0);
+    }
+    for (int x = 0; x < sp0.nx; ++x) wx += sp0.x_type[x] >= 2 ? 2.0 : 1.0;
+    const int nw = kST / 32;
+    int npw = (int)std::lround(nw * wp / std::max(1e-9, wp + wx));
+    npw = std::min(npw, (a.nbt + 31) / 32);                 // no idle phase warps
+    npw = std::min(npw, nw - (sp0.nx + 3) / 4);             // at most 4 slots per density warp
+    a.npw = std::max(1, std::min(nw - 1, npw));
+    if (const char* e = std::getenv("SG_OC_PW")) a.npw = std::max(1, std::min(nw - 1, atoi(e)));
+  }
   const long long MD2 = SG_MAXD * SG_MAXD;
   a.accd = 2 * (long long)K * MD2 + 4 * (long long)p.ne * MD2 + (long long)p.n1 * SG_MAXD +
            2 * (long long)p.ne * SG_MAXD + p.ne;
@@ -685,6 +791,7 @@ void onchip_plan_destroy(OnchipPlan* oc) {
 }
 
 bool onchip_adjoint_ok(const OnchipPlan* oc) { return oc && oc->adj_ok; }
+bool onchip_mixed(const OnchipPlan* oc) { return oc->mixed; }
 long long onchip_state_elems(const OnchipPlan* oc) { return (long long)oc->oa.ncta * oc->oa.ent; }
 long long onchip_stage_elems(const OnchipPlan* oc) { return (long long)oc->oa.ncta * oc->oa.CSP; }
 int onchip_ctas(const OnchipPlan* oc) { return oc->oa.ncta; }
@@ -692,27 +799,44 @@ long long onchip_acc_doubles(const OnchipPlan* oc) { return oc->oa.accd; }
 
 namespace {
 
+// Raise a kernel's dynamic shared-memory limit to the device's opt-in maximum, once
+// per kernel (the template parameter is the kernel itself: kernels of one signature
+// share a type).  (Setting it per solve to the solve's own size races with concurrent
+// solves of other sizes that launch the same kernel: a smaller size set between
+// another solve's set and launch fails that launch.)
+template <auto kern>
+void smem_limit_once() {
+  static const bool done = [] {
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - 1024);
+    return true;
+  }();
+  (void)done;
+}
+
 template <typename R, int DL>
 int fwd_t(const OnchipPlan* oc, const void* tab, const double2* psi_api, const double2* img_in, double2* psi_out,
           double2* ck_out, int K, int n0, int n1, double dt, void* segY, cudaStream_t st) {
   typedef typename CT<R>::T C;
   auto kern = k_oc_fwd<R, DL>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oc->sm_fwd);
+  smem_limit_once<k_oc_fwd<R, DL>>();
   kern<<<oc->oa.ncta, kST, oc->sm_fwd, st>>>(oc->h->pass[0], oc->oa, (const C*)tab, psi_api, img_in, psi_out,
                                              ck_out, std::max(1, K), n0, n1, dt, (C*)segY);
   return 1;
 }
 
 template <typename R, int DL>
-int adj_t(const OnchipPlan* oc, const void* tab, const double2* tab64, const double* coef, const double2* ph,
-          const void* segY, double2* pbar_img, int n0, int n1, double dt, const XArgs& xa, int nst, double* gF_cta,
-          double* acc_cta, int* err, cudaStream_t st) {
+int adj_t(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0, int n1,
+          double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err, cudaStream_t st) {
   typedef typename CT<R>::T C;
   auto kern = oc->h->allpar ? k_oc_adj<R, DL, true> : k_oc_adj<R, DL, false>;
-  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oc->sm_adj);
-  kern<<<oc->oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oc->oa, (const C*)tab, tab64, coef, ph,
-                                             (const C*)segY, pbar_img, n0, n1, dt, xa, gF_cta, acc_cta,
-                                             (long long)nst * std::max(1, oc->oa.K), err);
+  smem_limit_once<k_oc_adj<R, DL, true>>();
+  smem_limit_once<k_oc_adj<R, DL, false>>();
+  kern<<<oc->oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oc->oa, (const C*)tb.tab, (const R*)tb.coef,
+                                             (const C*)tb.ph, (const C*)tb.opd, (const C*)segY, pbar_img, n0, n1,
+                                             dt, xa, gF_cta, acc_cta, (long long)nst * std::max(1, oc->oa.K), err);
   return 1;
 }
 
@@ -743,14 +867,18 @@ int onchip_forward(const OnchipPlan* oc, const void* tab, const double2* psi_api
   OC_DISPATCH(fwd_t, oc, tab, psi_api, img_in, psi_out, ck_out, K, n0, n1, dt, segY, st);
 }
 
-int onchip_adjoint(const OnchipPlan* oc, const void* tab, const double2* tab64, const double* coef,
-                   const double2* ph, const void* segY, double2* pbar_img, int n0, int n1, double dt,
-                   const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err, cudaStream_t st) {
-  OC_DISPATCH(adj_t, oc, tab, tab64, coef, ph, segY, pbar_img, n0, n1, dt, xa, nst, gF_cta, acc_cta, err, st);
+int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0,
+                   int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
+                   cudaStream_t st) {
+  OC_DISPATCH(adj_t, oc, tb, segY, pbar_img, n0, n1, dt, xa, nst, gF_cta, acc_cta, err, st);
 }
 
 void onchip_to_image(const OnchipPlan* oc, const double2* api, double2* img, cudaStream_t st) {
   k_oc_image<<<grid_of(onchip_state_elems(oc)), 256, 0, st>>>(oc->oa, api, img);
+}
+
+void onchip_to_f32(const double* src, float* dst, long long n, cudaStream_t st) {
+  k_oc_f32<<<grid_of(n), 256, 0, st>>>(src, dst, n);
 }
 
 void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc_cta, long long nst, int K,

@@ -39,15 +39,27 @@ int onchip_forward(const OnchipPlan* oc, const void* tab, const double2* psi_api
                    cudaStream_t st);
 // API layout -> state image (columns past S are zero).
 void onchip_to_image(const OnchipPlan* oc, const double2* api, double2* img, cudaStream_t st);
+// Per-stage tables the adjoint reads, in the stage precision (complex64 / float in
+// mixed precision, complex128 / double otherwise): term rows (3N x row), drive
+// coefficients (3N x K), frame phases (3N x sumd) and the flat truncated operators.
+struct OnchipTables {
+  const void* tab;
+  const void* coef;
+  const void* ph;
+  const void* opd;
+};
 // Adjoint of steps n1-1 .. n0 from the stage inputs in segY: pbar_img (state image
 // of the co-state before the segment's last step) is pulled back in place; the
 // cross-densities of every stage are contracted into gF_cta (CTA-major, 3N x K
 // each, one store per stage slot) and acc_cta (CTA-major, onchip_acc_doubles
 // each, added to).  *err is set when a bounded wait on a bulk copy gives up.
 // Returns launches.
-int onchip_adjoint(const OnchipPlan* oc, const void* tab, const double2* tab64, const double* coef,
-                   const double2* ph, const void* segY, double2* pbar_img, int n0, int n1, double dt,
-                   const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err, cudaStream_t st);
+int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0,
+                   int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
+                   cudaStream_t st);
+// Element-wise FP64 -> FP32 copy (tables for the mixed-precision adjoint).
+void onchip_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
+bool onchip_mixed(const OnchipPlan* oc);
 // acc += sum over CTAs (in CTA order) of the per-CTA accumulators.
 void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc_cta, long long nst, int K,
                    int n1, int ne, GradAcc acc, cudaStream_t st);

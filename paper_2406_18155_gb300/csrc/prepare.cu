@@ -400,8 +400,12 @@ sg_status sg_prepare_impl(sg_system* sys) {
   }
   args.scratch = reinterpret_cast<double*>(base + per_mode * nq);
   const size_t smem = (2 * MM + 2 * SG_MAXM) * sizeof(double) + 2 * SG_MAXM * sizeof(int);
-  SG_CUDA_TRY(ctx, cudaFuncSetAttribute(k_build_modes, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
+  // the limit for the largest basis, once (a per-call size would race with
+  // concurrent prepares of other basis sizes on other host threads)
+  static const cudaError_t attr = cudaFuncSetAttribute(
+      k_build_modes, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      (int)((2 * SG_MAXM * SG_MAXM + 2 * SG_MAXM) * sizeof(double) + 2 * SG_MAXM * sizeof(int)));
+  SG_CUDA_TRY(ctx, attr);
   k_build_modes<<<nq, kThreads, smem, ctx->stream>>>(args);
   SG_CUDA_TRY(ctx, cudaGetLastError());
   if (!sys->mdev_dev) SG_CUDA_TRY(ctx, cudaMalloc(&sys->mdev_dev, SG_MAXQ * sizeof(ModeDev)));

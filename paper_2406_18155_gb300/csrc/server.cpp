@@ -6,6 +6,7 @@
 // others run starts as soon as a slot and memory free up, without waiting for the
 // running ones to finish.  Results are bitwise independent of what else runs: every
 // solve uses only its own buffers and fixed-order reductions.
+#include <cstdio>
 #include "sg_internal.h"
 #include <algorithm>
 #include <cmath>
@@ -37,6 +38,7 @@ struct Req {
   double F[2] = {0, 0};
   std::vector<double> gp, gh;
   double submit_s = 0, start_s = 0, done_s = 0;
+  std::string error;
 };
 
 size_t estimate_bytes(const sg_system* sys, const sg_evolve_opts& o, int want_grad) {
@@ -114,6 +116,7 @@ struct sg_server {
       {
         std::lock_guard<std::mutex> lk(mu);
         r->status = rc;
+        if (rc != SG_OK) r->error = c->last_error;
         r->done_s = now_s(t0);
         r->state = 2;
         mem_in_use -= r->mem;
@@ -226,6 +229,7 @@ static sg_status fill_result(Req* r, sg_result* out) {
   out->submit_s = r->submit_s;
   out->start_s = r->start_s;
   out->done_s = r->done_s;
+  std::snprintf(out->error, sizeof out->error, "%s", r->error.c_str());
   return SG_OK;
 }
 

@@ -520,8 +520,10 @@ void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, co
                 bool store, int kind) {
   typedef typename CT<R>::T C;
   auto kern = k_slab_fwd<R, DL>;
-  static bool attr = false;
-  if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024); attr = true; }
+  // once per kernel, thread-safe (solves on several host threads launch the same kernels)
+  static const bool attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                           cudaSuccess;
+  (void)attr;
   kern<<<h->grid_fwd, kST, h->sm_fwd[g], st>>>(h->pass[g], (const C*)X, (const C*)row, pin, pout,
                                                  (C*)Xn, (C*)Dacc, (C*)kA, dt, stage, store, kind);
 }
@@ -545,12 +547,12 @@ void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, cons
                 int stage, int kind) {
   typedef typename CT<R>::T C;
   auto kern = h->allpar ? k_slab_adj<R, DL, true> : k_slab_adj<R, DL, false>;
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     cudaFuncSetAttribute(k_slab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     cudaFuncSetAttribute(k_slab_adj<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   kern<<<h->grid_adj, kST, h->sm_adj[g], st>>>(h->pass[g], (const C*)X, (const C*)Y, (const C*)row, pbar,
                                                  (C*)Xn, (C*)Db, (C*)yA, dt, xa, stage, kind);
 }

@@ -82,6 +82,39 @@ def test_server_results_alone_equal_results_in_the_mix(sgctx):
     srv.close()
 
 
+def test_server_concurrent_shapes_sharing_kernels(sgctx):
+    # every 3-level request (2..5 modes, both kinds) launches the same kernels with
+    # different shared-memory sizes; many run at once, none may fail or change
+    from paper_2406_18155_gb300.api import Server
+    wls = []
+    for seed in range(4000):
+        wl = W.serving_request(np.random.Generator(np.random.PCG64(seed)))
+        if wl["modes"][0]["levels"] != 3 or any(w["name"] == wl["name"] for w in wls):
+            continue
+        wl["T"] = 40 * wl["dt"]
+        for d in wl["drives"]:
+            d["length"] = wl["T"]
+        wls.append(wl)
+        if len(wls) == 8:
+            break
+    alone = {}
+    for wl in wls:
+        s = _system(sgctx, wl)
+        alone[wl["name"]] = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                                            kind="avg", precision="mixed")
+    srv = Server(sgctx, mem_budget_bytes=16 << 30, max_slots=16)
+    reqs = [(wl, _system(sgctx, wl)) for wl in wls for _ in range(4)]
+    tickets = [srv.submit(sy, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg")
+               for wl, sy in reqs]
+    res = [srv.wait(t) for t in tickets]
+    srv.close()
+    for (wl, _), r in zip(reqs, res):
+        assert r["status"] == 0, (wl["name"], r["error"])
+        F, gp, gh = alone[wl["name"]]
+        assert abs(r["F"][0] - F[0]) <= 1e-12
+        assert np.max(np.abs(r["grad_pulse"] - gp)) <= 1e-12 * max(1.0, np.max(np.abs(gp)))
+
+
 def test_server_admission_and_cancel(sgctx):
     from paper_2406_18155_gb300.api import Server
     from paper_2406_18155_gb300.capi import SGError, SG_E_NOMEM_RETRY
