@@ -15,6 +15,10 @@ that solve (S columns x N steps per solve).
 import argparse
 import json
 import os
+
+# one hardware work queue per concurrent stream (set before CUDA initialises; the
+# package sets the same default)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 import statistics
 import subprocess
 import sys

@@ -1,6 +1,7 @@
 // C ABI: argument checking, system bookkeeping and dispatch.  See include/sg.h.
 #include "sg_internal.h"
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 
@@ -21,6 +22,9 @@ const char* sg_version(void) { return "supergpu 0.1 (sm_103a)"; }
 sg_status sg_ctx_create(sg_ctx** out, int device, void* cuda_stream) {
   if (!out) return sg_fail(nullptr, SG_E_INVALID, "out is NULL");
   *out = nullptr;
+  // one hardware work queue per concurrent stream (the server's slots); honoured only
+  // when this call creates the process's CUDA context, and a value already set is kept
+  setenv("CUDA_DEVICE_MAX_CONNECTIONS", "32", 0);
   int n = 0;
   cudaError_t e = cudaGetDeviceCount(&n);
   if (e != cudaSuccess) return sg_fail(nullptr, SG_E_CUDA, std::string("cudaGetDeviceCount: ") + cudaGetErrorString(e));

@@ -142,6 +142,79 @@ __global__ void k_tables(TabArgs a) {
   }
 }
 
+// exp(i theta) for large |theta|: reduction to [-pi, pi] in FP64 with a two-term
+// 2 pi (Cody-Waite), then the FP32 sine and cosine.  The phase keeps an absolute
+// error of a few 1e-8 where an FP32 product E t alone would lose ~1e-4 rad at
+// E t ~ 1e4 rad.
+__device__ __forceinline__ float2 cis32(double theta) {
+  const double k = rint(theta * 0.15915494309189535);                // 1 / (2 pi)
+  const double r = fma(-k, 6.283185307179586, theta) - k * 2.4492935982947064e-16;
+  float sn, cs;
+  sincosf((float)r, &sn, &cs);
+  return make_float2(cs, sn);
+}
+
+// Stage tables in FP32 only (mixed precision on the on-chip kernels, which read
+// nothing else): the same coefficients, phases and term rows as k_tables, with the
+// FP64 work cut to the envelope and the argument reduction.
+__global__ void k_tables32(TabArgs a, float* __restrict__ coef32, float2* __restrict__ ph32) {
+  const int q = blockIdx.x;
+  const int n = q / 3, j = q % 3;
+  const double t = (double)(2 * n + j) * a.dt * 0.5;
+  __shared__ float f[SG_MAXDRIVE];
+  __shared__ float2 ph[SG_MAXQ * SG_MAXD];
+  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+    const DriveDev dr = a.drives[k];
+    const double E = envelope_dev(dr, a.amps, n, j, t);
+    const float v = (float)E * cis32(dr.omega * t + dr.phase).x;
+    f[k] = v;
+    coef32[(size_t)q * a.K + k] = v;
+  }
+  for (int i = threadIdx.x; i < a.sumd; i += blockDim.x) {
+    const float2 c = a.frame == SG_FRAME_INTERACTION ? cis32(a.E[i] * t) : make_float2(1.f, 0.f);
+    ph[i] = c;
+    ph32[(size_t)q * a.sumd + i] = c;
+  }
+  __syncthreads();
+  float2* row = a.tab32 + (size_t)q * a.p.row;
+  auto pmul = [&](int i, int x, int y) {          // exp(i (E_x - E_y) t)
+    const float2 px = ph[a.eoff[i] + x], py = ph[a.eoff[i] + y];
+    return make_float2(px.x * py.x + px.y * py.y, px.y * py.x - px.x * py.y);
+  };
+  for (int u = 0; u < a.p.n1; ++u) {
+    const int i = a.p.s1_mode[u], d = a.dims[i];
+    for (int ab = threadIdx.x; ab < d * d; ab += blockDim.x) {
+      const int ia = ab / d, ib = ab % d;
+      const float2 P = pmul(i, ia, ib);
+      float2 acc = make_float2(0.f, 0.f);
+      for (int x = a.drv_of_slot_start[u]; x < a.drv_of_slot_start[u + 1]; ++x) {
+        const int k = a.drv_list[x];
+        const double2 O = a.opd[a.opd_off[i] + a.drives[k].op * d * d + ab];
+        const float ox = (float)O.x, oy = (float)O.y;
+        acc.x += f[k] * (ox * P.x - oy * P.y);
+        acc.y += f[k] * (ox * P.y + oy * P.x);
+      }
+      if (a.frame == SG_FRAME_LAB && ia == ib) acc.x += (float)a.E[a.eoff[i] + ia];
+      row[a.p.s1_off[u] + ab] = acc;
+    }
+  }
+  for (int e = 0; e < a.p.ne; ++e) {
+    for (int side = 0; side < 2; ++side) {
+      const int i = side == 0 ? a.p.e_a[e] : a.p.e_b[e];
+      const int op = side == 0 ? a.e_opa[e] : a.e_opb[e];
+      const int d = a.dims[i];
+      const int off = side == 0 ? a.p.e_offL[e] : a.p.e_offR[e];
+      const float sc = side == 0 ? (float)a.J[e] : 1.f;
+      for (int ab = threadIdx.x; ab < d * d; ab += blockDim.x) {
+        const float2 P = pmul(i, ab / d, ab % d);
+        const double2 O = a.opd[a.opd_off[i] + op * d * d + ab];
+        const float ox = (float)O.x, oy = (float)O.y;
+        row[off + ab] = make_float2(sc * (ox * P.x - oy * P.y), sc * (ox * P.y + oy * P.x));
+      }
+    }
+  }
+}
+
 // ---------------------------------------------------------------------------
 // H y at one slab entry (gather form)
 // ---------------------------------------------------------------------------
@@ -941,6 +1014,8 @@ struct Solve {
   double2* ph = nullptr;
   double2* tab = nullptr;
   float2* tab32 = nullptr;
+  float* coef32 = nullptr;        // FP32-only tables (mixed on-chip solves): coef32, ph32, tab32
+  float2* ph32 = nullptr;
   double2* psi = nullptr;
   int launches = 0;
   bool mixed = false;
@@ -964,21 +1039,34 @@ int path_choice() {
   return v == "gather" ? 2 : (v == "slab" ? 1 : 0);
 }
 
-sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) {
+sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, bool grad) {
   sg_ctx* ctx = sys->ctx;
   Setup& s = sv.s;
   cudaStream_t st = ctx->stream;
+  // plans first: they upload their offset tables, and every host-to-device copy of
+  // a solve goes before its first kernel (see dcopy)
+  sv.mixed = o->precision == SG_MIXED;
+  const int pc = path_choice();
+  if (pc == 0) sv.oc = onchip_plan_create(s.p, sv.mixed, s.K, s.sumd, st);
+  if (pc <= 1 && !(sv.oc && onchip_adjoint_ok(sv.oc))) sv.slab = slab_plan_create(s.p, sv.mixed, st);
+  // mixed precision on the on-chip kernels reads only FP32 tables
+  const bool f32only = sv.mixed && sv.onchip(grad);
   sv.drives_dev = sv.ar.get<DriveDev>(std::max(1, s.K));
   sv.amps_dev = sv.ar.get<double>(std::max<size_t>(1, s.amps.size()));
   sv.E_dev = sv.ar.get<double>(s.sumd);
   sv.opd_dev = sv.ar.get<double2>(s.opdflat.size());
   const size_t nst = 3ull * s.N;
-  sv.coef = sv.ar.get<double>(nst * std::max(1, s.K));
-  sv.ph = sv.ar.get<double2>(nst * s.sumd);
-  sv.tab = sv.ar.get<double2>(nst * s.p.row);
-  if (o->precision == SG_MIXED) sv.tab32 = sv.ar.get<float2>(nst * s.p.row);
-  if (!sv.drives_dev || !sv.amps_dev || !sv.E_dev || !sv.opd_dev || !sv.coef || !sv.ph || !sv.tab ||
-      (o->precision == SG_MIXED && !sv.tab32))
+  if (f32only) {
+    sv.coef32 = sv.ar.get<float>(nst * std::max(1, s.K));
+    sv.ph32 = sv.ar.get<float2>(nst * s.sumd);
+  } else {
+    sv.coef = sv.ar.get<double>(nst * std::max(1, s.K));
+    sv.ph = sv.ar.get<double2>(nst * s.sumd);
+    sv.tab = sv.ar.get<double2>(nst * s.p.row);
+  }
+  if (sv.mixed) sv.tab32 = sv.ar.get<float2>(nst * s.p.row);
+  if (!sv.drives_dev || !sv.amps_dev || !sv.E_dev || !sv.opd_dev || (sv.mixed && !sv.tab32) ||
+      (f32only ? (!sv.coef32 || !sv.ph32) : (!sv.coef || !sv.ph || !sv.tab)))
     return sg_fail(ctx, SG_E_NOMEM, "device allocation of the stage tables failed");
   if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.drives_dev, s.drives.data(), s.K * sizeof(DriveDev), cudaMemcpyHostToDevice, st));
   if (!s.amps.empty()) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.amps_dev, s.amps.data(), s.amps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -994,13 +1082,8 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv) 
   ta.tab = sv.tab;
   ta.tab32 = sv.tab32;
   s.ta = ta;
-  // plans first: they upload their offset tables, and every host-to-device copy of
-  // a solve goes before its first kernel (see dcopy)
-  sv.mixed = o->precision == SG_MIXED;
-  const int pc = path_choice();
-  if (pc == 0) sv.oc = onchip_plan_create(s.p, sv.mixed, s.K, s.sumd, st);
-  if (pc <= 1 && !(sv.oc && onchip_adjoint_ok(sv.oc))) sv.slab = slab_plan_create(s.p, sv.mixed, st);
-  k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
+  if (f32only) k_tables32<<<(unsigned)nst, 64, 0, st>>>(ta, sv.coef32, sv.ph32);
+  else k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
   {
@@ -1179,17 +1262,13 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
   const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
   OnchipTables tb{tab, sv.coef, sv.ph, sv.opd_dev};
   if (sizeof(R) == 4) {
-    // stage-precision copies of the phase, coefficient and operator tables
-    const long long nph = 2 * nst * s.sumd, ncf = nst * s.K, nop = 2 * (long long)s.opdflat.size();
-    float* ph32 = sv.ar.get<float>(nph);
-    float* cf32 = sv.ar.get<float>(std::max(1ll, ncf));
+    // FP32 tables (k_tables32) and an FP32 copy of the operators
+    const long long nop = 2 * (long long)s.opdflat.size();
     float* op32 = sv.ar.get<float>(nop);
-    if (!ph32 || !cf32 || !op32) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the FP32 tables failed");
-    onchip_to_f32(reinterpret_cast<const double*>(sv.ph), ph32, nph, st);
-    if (ncf) onchip_to_f32(sv.coef, cf32, ncf, st);
+    if (!op32 || !sv.coef32 || !sv.ph32) return sg_fail(ctx, SG_E_NOMEM, "FP32 tables missing");
     onchip_to_f32(reinterpret_cast<const double*>(sv.opd_dev), op32, nop, st);
-    sv.launches += 3;
-    tb = OnchipTables{tab, cf32, ph32, op32};
+    ++sv.launches;
+    tb = OnchipTables{tab, sv.coef32, sv.ph32, op32};
   }
   const int nseg = (int)ckpts.size();
   for (int c = nseg - 1; c >= 0; --c) {
@@ -1374,7 +1453,7 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
     if (!cols_dev) return sg_fail(ctx, SG_E_NOMEM, "allocation failed");
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols_dev, o->col_index, s.S * sizeof(long long), cudaMemcpyHostToDevice, st));
   }
-  rc = upload_and_tables(sys, o, sv);
+  rc = upload_and_tables(sys, o, sv, false);
   if (rc != SG_OK) return rc;
   sv.psi = static_cast<double2*>(psi_dev);
   rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, !o->col_index, 0, nullptr)
@@ -1453,7 +1532,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     if (!poff) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
     if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(poff, s.pulse_off.data(), s.K * sizeof(int), cudaMemcpyHostToDevice, st));
   }
-  rc = upload_and_tables(sys, o, sv);
+  rc = upload_and_tables(sys, o, sv, grad);
   if (rc != SG_OK) return rc;
   // checkpoints
   int K = 0;
