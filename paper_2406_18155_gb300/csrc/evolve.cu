@@ -1252,7 +1252,8 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
   double* gFc = sv.ar.get<double>((size_t)ncta * nst * Kd);
   double* accc = sv.ar.get<double>((size_t)ncta * onchip_acc_doubles(oc));
   int* err = sv.ar.get<int>(1);
-  if (!pimg || !segY || !gFc || !accc || !err)
+  void* colow = onchip_colow_global(oc) ? (void*)sv.ar.get<float2>(ns) : nullptr;
+  if (!pimg || !segY || !gFc || !accc || !err || (onchip_colow_global(oc) && !colow))
     return sg_fail(ctx, SG_E_NOMEM, "device allocation of the on-chip adjoint buffers failed");
   SG_CUDA_TRY(ctx, cudaMemsetAsync(gFc, 0, (size_t)ncta * nst * Kd * sizeof(double), st));
   SG_CUDA_TRY(ctx, cudaMemsetAsync(accc, 0, (size_t)ncta * onchip_acc_doubles(oc) * sizeof(double), st));
@@ -1274,7 +1275,7 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
   for (int c = nseg - 1; c >= 0; --c) {
     const int n0 = c * K, n1 = std::min(s.N, n0 + K);
     sv.launches += onchip_forward(oc, tab, nullptr, ckpts[c], nullptr, nullptr, K, n0, n1, s.dt, segY, st);
-    sv.launches += onchip_adjoint(oc, tb, segY, pimg, n0, n1, s.dt, xa, (int)nst, gFc, accc, err, st);
+    sv.launches += onchip_adjoint(oc, tb, segY, pimg, n0, n1, s.dt, xa, (int)nst, gFc, accc, err, colow, st);
   }
   onchip_reduce(oc, gFc, accc, nst, s.K, s.p.n1, s.p.ne, acc, st);
   ++sv.launches;

@@ -129,6 +129,12 @@ template <> struct StateArr<float> {
     h = reinterpret_cast<float2*>(base);
     l = h + n;
   }
+  // high words in shared memory, low words elsewhere (global memory when shared
+  // memory is short: they are touched once per step)
+  __device__ void init_split(unsigned char* base, float2* lo) {
+    h = reinterpret_cast<float2*>(base);
+    l = lo;
+  }
   __device__ void set(int e, double2 v) {
     const float hx = __double2float_rn(v.x), hy = __double2float_rn(v.y);
     h[e] = make_float2(hx, hy);
@@ -154,6 +160,7 @@ struct OcArgs {
   int D, S, Sc, nbc, nbt, CS, CSP, ncta, row, K, sumd, n1, ne;
   int ent;               // Sc * D entries per CTA
   int npw;               // adjoint: phase warps (the rest compute cross-densities)
+  int pblo_g;            // adjoint, mixed: co-state low words in global memory (shared memory short)
   // forward shared-memory byte offsets
   int f_ys, f_ks, f_ps, f_dl, f_M;
   // adjoint shared-memory byte offsets
@@ -412,7 +419,7 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
          const typename CT<R>::T* __restrict__ ph, const typename CT<R>::T* __restrict__ opd,
          const typename CT<R>::T* __restrict__ segY, double2* __restrict__ pbar_img, int n0, int n1, double dt,
          XArgs xa, double* __restrict__ gF_cta, double* __restrict__ acc_cta, long long nstK,
-         int* __restrict__ err) {
+         int* __restrict__ err, float2* __restrict__ pblo) {
   typedef typename CT<R>::T C;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
@@ -422,7 +429,12 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   C* yn = reinterpret_cast<C*>(sm + oa.a_yn);
   C* db = reinterpret_cast<C*>(sm + oa.a_db);
   StateArr<R> pb;
-  pb.init(sm + oa.a_pb, oa.ent);
+  if constexpr (sizeof(R) == 4) {
+    if (oa.pblo_g) pb.init_split(sm + oa.a_pb, pblo + (size_t)blockIdx.x * oa.ent);
+    else pb.init(sm + oa.a_pb, oa.ent);
+  } else {
+    pb.init(sm + oa.a_pb, oa.ent);
+  }
   C* const M0 = reinterpret_cast<C*>(sm + oa.a_M);
   C* const M1 = M0 + oa.rowA;
   R* const cf0 = reinterpret_cast<R*>(sm + oa.a_cf);
@@ -691,7 +703,7 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   a.a_ys = take(a.CSP * cs);
   a.a_yn = take(a.CSP * cs);
   a.a_db = take((size_t)a.ent * cs);
-  a.a_pb = take((size_t)a.ent * 16);
+  a.a_pb = take((size_t)a.ent * (a.pblo_g ? 8 : 16));
   a.a_M = take(2 * (size_t)a.rowA * cs);
   a.a_cf = take(2 * (size_t)a.Kp * rs);
   a.a_ph = take(2 * (size_t)a.sumdA * cs);
@@ -745,12 +757,18 @@ OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cuda
   int sc0 = std::max(1, std::min(p.S, (kST + a.nbc - 1) / std::max(1, a.nbc)));
   size_t fwd = 0, adj = 0;
   int best_adj = 0, best_fwd = 0;
-  for (int sc = sc0; sc >= 1; --sc) {
-    a.Sc = sc;
-    layout(a, DL, cs, fwd, adj);
-    if (!best_fwd && fwd <= limit) best_fwd = sc;
-    if (!best_adj && adj <= limit) { best_adj = sc; break; }
+  // mixed precision: if the adjoint does not fit at one column per CTA, retry with the
+  // co-state's low words in global memory
+  for (a.pblo_g = 0; a.pblo_g <= (mixed ? 1 : 0) && !best_adj; ++a.pblo_g) {
+    for (int sc = sc0; sc >= 1; --sc) {
+      a.Sc = sc;
+      layout(a, DL, cs, fwd, adj);
+      if (!best_fwd && fwd <= limit) best_fwd = sc;
+      if (!best_adj && adj <= limit) { best_adj = sc; break; }
+    }
+    if (best_adj) break;
   }
+  if (!best_adj) a.pblo_g = 0;
   const int sc = best_adj ? best_adj : best_fwd;
   if (!sc) { onchip_plan_destroy(oc); return nullptr; }
   // balance the columns over the CTAs
@@ -791,6 +809,7 @@ void onchip_plan_destroy(OnchipPlan* oc) {
 }
 
 bool onchip_adjoint_ok(const OnchipPlan* oc) { return oc && oc->adj_ok; }
+bool onchip_colow_global(const OnchipPlan* oc) { return oc->oa.pblo_g != 0; }
 bool onchip_mixed(const OnchipPlan* oc) { return oc->mixed; }
 long long onchip_state_elems(const OnchipPlan* oc) { return (long long)oc->oa.ncta * oc->oa.ent; }
 long long onchip_stage_elems(const OnchipPlan* oc) { return (long long)oc->oa.ncta * oc->oa.CSP; }
@@ -829,14 +848,16 @@ int fwd_t(const OnchipPlan* oc, const void* tab, const double2* psi_api, const d
 
 template <typename R, int DL>
 int adj_t(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0, int n1,
-          double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err, cudaStream_t st) {
+          double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err, void* pblo,
+          cudaStream_t st) {
   typedef typename CT<R>::T C;
   auto kern = oc->h->allpar ? k_oc_adj<R, DL, true> : k_oc_adj<R, DL, false>;
   smem_limit_once<k_oc_adj<R, DL, true>>();
   smem_limit_once<k_oc_adj<R, DL, false>>();
   kern<<<oc->oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oc->oa, (const C*)tb.tab, (const R*)tb.coef,
                                              (const C*)tb.ph, (const C*)tb.opd, (const C*)segY, pbar_img, n0, n1,
-                                             dt, xa, gF_cta, acc_cta, (long long)nst * std::max(1, oc->oa.K), err);
+                                             dt, xa, gF_cta, acc_cta, (long long)nst * std::max(1, oc->oa.K), err,
+                                             (float2*)pblo);
   return 1;
 }
 
@@ -869,8 +890,8 @@ int onchip_forward(const OnchipPlan* oc, const void* tab, const double2* psi_api
 
 int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0,
                    int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
-                   cudaStream_t st) {
-  OC_DISPATCH(adj_t, oc, tb, segY, pbar_img, n0, n1, dt, xa, nst, gF_cta, acc_cta, err, st);
+                   void* colow, cudaStream_t st) {
+  OC_DISPATCH(adj_t, oc, tb, segY, pbar_img, n0, n1, dt, xa, nst, gF_cta, acc_cta, err, colow, st);
 }
 
 void onchip_to_image(const OnchipPlan* oc, const double2* api, double2* img, cudaStream_t st) {

@@ -54,9 +54,13 @@ struct OnchipTables {
 // each, one store per stage slot) and acc_cta (CTA-major, onchip_acc_doubles
 // each, added to).  *err is set when a bounded wait on a bulk copy gives up.
 // Returns launches.
+// colow: when onchip_colow_global(oc), a device buffer of onchip_state_elems complex64
+// entries that holds the low words of the float-float co-state across the segments
+// of one backward sweep (contents undefined before the first segment); else null.
 int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0,
                    int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
-                   cudaStream_t st);
+                   void* colow, cudaStream_t st);
+bool onchip_colow_global(const OnchipPlan* oc);
 // Element-wise FP64 -> FP32 copy (tables for the mixed-precision adjoint).
 void onchip_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 bool onchip_mixed(const OnchipPlan* oc);

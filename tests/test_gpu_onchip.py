@@ -134,3 +134,19 @@ def test_onchip_largest_tile_mixed(sgctx, onchip, monkeypatch):
     assert abs(F[0] - Fg[0]) < 1e-5
     g = np.concatenate([gpg, ghg])
     assert np.max(np.abs(np.concatenate([gp, gh]) - g)) <= 1e-3 * np.max(np.abs(g))
+
+
+def test_onchip_d4096_low_words_in_global(sgctx, monkeypatch):
+    # D = 4^6 = 4096: the mixed adjoint fits one column per CTA only with the
+    # co-state's low words in global memory; checked against the FP64 tiled kernels
+    wl = _chain(11, 6, 4, T=0.2, ncols=8)
+    s = _system(sgctx, wl)
+    monkeypatch.delenv("SG_PATH", raising=False)
+    F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                precision="mixed", ckpt=6)
+    monkeypatch.setenv("SG_PATH", "slab")
+    Fr, gpr, ghr = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                   precision="fp64", ckpt=6)
+    assert abs(F[1] - Fr[1]) < 1e-5
+    g, gr = np.concatenate([gp, gh]), np.concatenate([gpr, ghr])
+    assert np.max(np.abs(g - gr)) <= 1e-3 * np.max(np.abs(gr))
