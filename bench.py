@@ -165,6 +165,11 @@ def run_ours(args):
     from paper_2406_18155_gb300.api import Context, System, evolve_opts
     desc, make = WORKLOADS[args.workload]
     wl = make(1000 + rank)
+    if args.t_ns > 0:                     # shortened run (profiling captures)
+        wl["T"] = round(args.t_ns / wl["dt"]) * wl["dt"]
+        for d in wl["drives"]:
+            d["length"] = wl["T"]
+        desc += f" [shortened to T={wl['T']:.4g} ns]"
     ctx = Context(local)
     sysm = System.from_workload(ctx, wl)
     sysm.prepare()
@@ -273,6 +278,35 @@ def run_ours(args):
     ctx.close()
     if dist:
         dist.destroy_process_group()
+
+
+def onchip_shapes(ctx, nsteps, only=None):
+    """Per shape class of the serving distribution (kind x modes x levels): one
+    fidelity + gradient solve alone on the GPU, mixed precision, T = nsteps dt;
+    forward and backward (segment replay + pull-back) device time per RK4 step."""
+    from paper_2406_18155_gb300.api import System
+    out, seen = [], set()
+    for seed in range(20000):
+        wl = W.serving_request(np.random.Generator(np.random.PCG64(seed)))
+        if wl["name"] in seen or (only and wl["name"] != only):
+            continue
+        seen.add(wl["name"])
+        wl["T"] = nsteps * wl["dt"]
+        for d in wl["drives"]:
+            d["length"] = wl["T"]
+        s = System.from_workload(ctx, wl)
+        s.prepare()
+        for _ in range(2):
+            s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg", precision="mixed")
+        st = s.last_stats()
+        D = int(np.prod([m["levels"] for m in wl["modes"]]))
+        out.append({"shape": wl["name"], "D": D, "columns": len(wl["col_index"]),
+                    "forward_us_per_step": round(1e3 * st["forward_ms"] / nsteps, 2),
+                    "backward_us_per_step": round(1e3 * st["backward_ms"] / nsteps, 2),
+                    "launches": st["launches"]})
+        if len(seen) == 24 or only:
+            break
+    return sorted(out, key=lambda r: (r["D"], r["shape"]))
 
 
 def serving_bench(ctx, n_requests, slots, seed=7):
@@ -468,8 +502,20 @@ def main():
     ap.add_argument("--serving", type=int, default=64, help="Poisson requests of the serving sample (0: skip); twice as many run saturated first")
     ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
+    ap.add_argument("--t-ns", type=float, default=0.0, help="shorten the workload to T ns (profiling)")
+    ap.add_argument("--onchip-shapes", type=int, default=0,
+                    help="print per-shape on-chip step times over this many RK4 steps and exit")
+    ap.add_argument("--shape", default=None, help="with --onchip-shapes: one shape class only")
     args = ap.parse_args()
-    if args.only_serving:
+    if args.onchip_shapes > 0:
+        import torch
+        from paper_2406_18155_gb300 import build as B
+        B.build()
+        from paper_2406_18155_gb300.api import Context
+        torch.cuda.set_device(0)
+        for r in onchip_shapes(Context(0), args.onchip_shapes, args.shape):
+            print(json.dumps(r), flush=True)
+    elif args.only_serving:
         import torch
         from paper_2406_18155_gb300 import build as B
         B.build()
