@@ -101,6 +101,16 @@ sg_status sg_add_fluxonium(sg_system* sys, double ej, double ec, double el, doub
 sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b,
                           double strength, int* term_out);
 
+/* Mark a mode as a coupler (coupler != 0) or as a qubit (0, the default).  The
+ * computational subspace of the fidelity (Eq. 13, Eq. D2) is every qubit mode in
+ * level 0 or 1 with every coupler mode in its ground state, Dc = 2^(qubit modes):
+ * the schemes of Sec. 4 where qubits interact through a coupler mode (transmon
+ * qubits with a transmon coupler; fluxoniums with a transmon coupler, FTF).  A
+ * coupler evolves like any other mode.  Targets are Dc x Dc over the qubit modes
+ * (mode order, first qubit most significant); a solve needs 1..12 qubit modes.
+ * SG_E_INVALID for a bad mode index. */
+sg_status sg_set_coupler(sg_system* sys, int mode, int coupler);
+
 /* Drive f(t) * op(mode) with f(t) = E(t) cos(omega_d t + phase) (Eq. C1).
  *   SG_ENV_GAUSSIAN: E = amp exp(-(t - t0)^2 / (2 sigma^2))
  *   SG_ENV_PWC:      E = amps[j] on the j-th of nseg equal segments of [0, length);

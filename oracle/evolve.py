@@ -82,14 +82,20 @@ def frame_epilogue(sys, psi_i, nsteps=None):
 # fidelity (Eq. 13, Eq. D2, reading R10)
 # ----------------------------------------------------------------------------
 def comp_map(sys):
-    """Flat indices of the computational states (mode 0 = MSB), and the comp label
-    of each evolved column (-1 if it is not a computational state)."""
-    nq = sys.nq
+    """Flat indices of the computational states and the comp label of each evolved
+    column (-1 if it is not a computational state).  A computational state has
+    every qubit mode in level 0 or 1 and every coupler mode (workload mode flag
+    "coupler") in level 0; label j counts over the qubit modes, first qubit most
+    significant."""
+    qubits = [i for i in range(sys.nq) if not sys.wl["modes"][i].get("coupler")]
     comp = []
-    for j in range(2 ** nq):
+    for j in range(2 ** len(qubits)):
+        level = [0] * sys.nq
+        for b, i in enumerate(qubits):
+            level[i] = (j >> (len(qubits) - 1 - b)) & 1
         r = 0
-        for i in range(nq):
-            r = r * sys.dims[i] + ((j >> (nq - 1 - i)) & 1)
+        for i in range(sys.nq):
+            r = r * sys.dims[i] + level[i]
         comp.append(r)
     label = {r: j for j, r in enumerate(comp)}
     cols = [label.get(int(r), -1) for r in sys.wl["col_index"]]

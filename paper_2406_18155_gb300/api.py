@@ -94,6 +94,10 @@ class System:
         self._chk(lib().sg_add_coupling(self.h, a, _OPS[op_a], b, _OPS[op_b], J, C.byref(t)))
         return t.value
 
+    def set_coupler(self, mode, coupler=True):
+        """Hold `mode` in its ground state in the computational subspace (sg_set_coupler)."""
+        self._chk(lib().sg_set_coupler(self.h, mode, 1 if coupler else 0))
+
     def add_drive(self, mode, op, env, amp=0.0, amps=None, sigma=1.0, t0=0.0, length=1.0,
                   omega_d=0.0, omega_mode=None, phase=0.0):
         p = capi.sg_pulse()
@@ -122,6 +126,9 @@ class System:
             else:
                 s.add_fluxonium(m["ej"], m["ec"], m["el"], m.get("phi_ext", np.pi),
                                 m.get("n_osc", 50), m["levels"])
+        for i, m in enumerate(wl["modes"]):
+            if m.get("coupler"):
+                s.set_coupler(i, True)
         for c in wl["couplings"]:
             s.add_coupling(c["a"], c["op_a"], c["b"], c["op_b"], c["J"])
         for d in wl["drives"]:

@@ -119,6 +119,13 @@ sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int 
   return SG_OK;
 }
 
+sg_status sg_set_coupler(sg_system* sys, int mode, int coupler) {
+  if (!sys) return SG_E_INVALID;
+  if (mode < 0 || mode >= (int)sys->modes.size()) return sg_fail(sys->ctx, SG_E_INVALID, "mode index out of range");
+  sys->modes[mode].coupler = coupler ? 1 : 0;
+  return SG_OK;
+}
+
 sg_status sg_add_drive(sg_system* sys, int mode, int op, const sg_pulse* p, int* drive_out) {
   if (!sys) return SG_E_INVALID;
   if (!p) return sg_fail(sys->ctx, SG_E_INVALID, "pulse is NULL");

@@ -398,6 +398,7 @@ __global__ void k_frame(FrameArgs a, double2* x) {
 
 struct FidArgs {
   int S, Dc, Sc, full, kind, nq;
+  int qpos[SG_MAXQ];          // bit of mode i in a comp label (LSB = 0), -1 for a coupler mode
   const double2* Uc;          // Dc x S   (comp rows of the lab-frame columns)
   const double2* Tg;          // Dc x Dc
   const int* lab;             // S: comp label of each column or -1
@@ -503,7 +504,7 @@ __global__ void k_frame_ebar(FidArgs a) {
       double part = 0.0;
       for (int x = threadIdx.x; x < a.Dc * a.S; x += blockDim.x) {
         int r = x / a.S;
-        int bit = (r >> (a.nq - 1 - i)) & 1;
+        int bit = a.qpos[i] >= 0 ? (r >> a.qpos[i]) & 1 : 0;      // a coupler sits in level 0
         if (bit != c) continue;
         double2 b = a.bar[x], u = a.Uc[x];
         // Re(conj(b) * (-i T) u) = T * (b.x*u.y - b.y*u.x)
@@ -518,10 +519,13 @@ __global__ void k_frame_ebar(FidArgs a) {
 struct CompArgs {
   int nq, S, Dc;
   int dims[SG_MAXQ];
+  int qpos[SG_MAXQ];          // bit of mode i in a comp label (LSB = 0), -1 for a coupler mode
 };
+// Flat row of computational state j: qubit mode i takes bit qpos[i] of j, a
+// coupler mode level 0.
 __device__ long long comp_row(const CompArgs& a, int j) {
   long long r = 0;
-  for (int i = 0; i < a.nq; ++i) r = r * a.dims[i] + ((j >> (a.nq - 1 - i)) & 1);
+  for (int i = 0; i < a.nq; ++i) r = r * a.dims[i] + (a.qpos[i] >= 0 ? ((j >> a.qpos[i]) & 1) : 0);
   return r;
 }
 __global__ void k_gather_comp(CompArgs a, const double2* psi, double2* Uc) {
@@ -819,6 +823,8 @@ struct Setup {
   std::vector<int> s1_of_mode;
   std::vector<int> pulse_off;
   int n_pulse = 0;
+  int nqb = 0;                    // qubit modes (the rest are couplers)
+  int qpos[SG_MAXQ] = {0};        // bit of mode i in a comp label (LSB = 0), -1 for a coupler
 };
 
 sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
@@ -853,7 +859,10 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
   if (D * (long long)s.S > (1ll << 40)) return sg_fail(ctx, SG_E_INVALID, "slab too large");
   long long st = 1;
   for (int i = s.nq - 1; i >= 0; --i) { p.st[i] = st; st *= p.dims[i]; }
-  s.Dc = 1 << s.nq;
+  s.nqb = 0;
+  for (int i = 0; i < s.nq; ++i) s.nqb += sys->modes[i].coupler ? 0 : 1;
+  for (int i = 0, b = s.nqb - 1; i < s.nq; ++i) s.qpos[i] = sys->modes[i].coupler ? -1 : b--;
+  s.Dc = 1 << std::min(s.nqb, 20);
   // energies and operators, flattened
   s.sumd = 0;
   int eoff[SG_MAXQ], ooff[SG_MAXQ];
@@ -1208,7 +1217,7 @@ FrameArgs frame_args(const Setup& s, const double* E_dev, double sign) {
 CompArgs comp_args(const Setup& s) {
   CompArgs c{};
   c.nq = s.nq; c.S = s.S; c.Dc = s.Dc;
-  for (int i = 0; i < s.nq; ++i) c.dims[i] = s.p.dims[i];
+  for (int i = 0; i < s.nq; ++i) { c.dims[i] = s.p.dims[i]; c.qpos[i] = s.qpos[i]; }
   return c;
 }
 
@@ -1484,9 +1493,10 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   sg_status rc = build_setup(sys, o, sv.s);
   if (rc != SG_OK) return rc;
   Setup& s = sv.s;
-  if (s.nq > 12) return sg_fail(ctx, SG_E_UNSUPPORTED, "fidelity supports at most 12 modes");
+  if (s.nqb < 1 || s.nqb > 12) return sg_fail(ctx, SG_E_UNSUPPORTED, "fidelity needs 1..12 qubit (non-coupler) modes");
   for (int i = 0; i < s.nq; ++i)
-    if (s.p.dims[i] < 2) return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per mode");
+    if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
+      return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");
   SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   keep_pool_memory(ctx->device);
   cudaStream_t st = ctx->stream;
@@ -1501,8 +1511,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     bool comp = true;
     for (int i = 0; i < s.nq; ++i) {
       int l = (int)((r / s.p.st[i]) % s.p.dims[i]);
-      if (l > 1) { comp = false; break; }
-      j = (j << 1) | l;
+      if (l > (s.qpos[i] >= 0 ? 1 : 0)) { comp = false; break; }     // couplers in level 0
+      if (s.qpos[i] >= 0) j = (j << 1) | l;
     }
     if (comp) { lab[c] = j; ++Sc; ++seen[j]; }
   }
@@ -1568,6 +1578,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   k_gather_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, sv.psi, Uc);
   FidArgs fa{};
   fa.S = s.S; fa.Dc = s.Dc; fa.Sc = Sc; fa.full = full ? 1 : 0; fa.kind = kind; fa.nq = s.nq;
+  for (int i = 0; i < s.nq; ++i) fa.qpos[i] = s.qpos[i];
   fa.Uc = Uc; fa.Tg = Tg; fa.lab = lab_dev; fa.F = Fd; fa.bar = grad ? barc : nullptr; fa.M = Mbuf;
   fa.T = s.T;
   fa.frame = o->frame;

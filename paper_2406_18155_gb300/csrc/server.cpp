@@ -183,21 +183,25 @@ sg_status sg_server_submit(sg_server* srv, const sg_request* req, uint64_t* tick
   r->kind = req->kind;
   r->want_grad = req->want_grad;
   const int nq = (int)req->sys->modes.size();
-  if (nq < 1 || nq > 12) return sg_fail(srv->ctx, SG_E_INVALID, "request system needs 1..12 modes");
-  std::vector<int> dims;
-  for (const HostMode& m : req->sys->modes) dims.push_back(m.d);
+  int nqb = 0;
+  for (const HostMode& m : req->sys->modes) nqb += m.coupler ? 0 : 1;
+  if (nq < 1 || nq > SG_MAXQ || nqb < 1 || nqb > 12)
+    return sg_fail(srv->ctx, SG_E_INVALID, "request system needs 1..12 qubit modes");
   if (req->opts.col_index) {
     r->cols.assign(req->opts.col_index, req->opts.col_index + req->opts.ncols);
   } else {
-    for (int j = 0; j < (1 << nq); ++j) {
+    // every computational state: qubit modes in {0, 1} (first qubit most significant),
+    // couplers in level 0
+    for (int j = 0; j < (1 << nqb); ++j) {
       long long row = 0;
-      for (int i = 0; i < nq; ++i) row = row * dims[i] + ((j >> (nq - 1 - i)) & 1);
+      int b = nqb - 1;
+      for (const HostMode& m : req->sys->modes) row = row * m.d + (m.coupler ? 0 : (j >> b--) & 1);
       r->cols.push_back(row);
     }
     r->opts.ncols = (int)r->cols.size();
   }
   r->opts.col_index = r->cols.data();
-  const size_t dc = (size_t)1 << nq;
+  const size_t dc = (size_t)1 << nqb;
   r->target.assign(req->target_re_im, req->target_re_im + 2 * dc * dc);
   r->mem = estimate_bytes(req->sys, r->opts, req->want_grad);
   std::lock_guard<std::mutex> lk(srv->mu);

@@ -22,6 +22,7 @@ struct HostMode {
   double ej, ec, el, ng, phi_ext;
   int M;           // basis size
   int d;           // kept levels
+  int coupler;     // 1: held in its ground state in the computational subspace
 };
 struct HostCoupling { int a, op_a, b, op_b; double J; };
 struct HostDrive {

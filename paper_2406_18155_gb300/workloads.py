@@ -11,12 +11,13 @@ A workload is a plain dict::
       "name": str,
       "modes":     [{"kind": "transmon", "ej", "ec", "ng", "ncut", "levels"} |
                     {"kind": "fluxonium", "ej", "ec", "el", "phi_ext", "n_osc", "levels"}],
+                   (optional "coupler": True: held in level 0 in the computational subspace)
       "couplings": [{"a", "op_a", "b", "op_b", "J"}],          # op in {"n", "phi"}
       "drives":    [{"mode", "op", "env", "amp" | "amps", "sigma", "t0", "length",
                      "omega_d" (float) or "omega_mode" (int), "phase"}],
       "T", "dt", "frame" ("interaction" | "lab"),
       "col_index": [flat product-basis index of each evolved column],
-      "target":    complex (Dc, Dc) array, Dc = 2**len(modes),
+      "target":    complex (Dc, Dc) array, Dc = 2**(number of non-coupler modes),
       "fid_kind":  "avg" | "state",
     }
 
@@ -66,11 +67,15 @@ def comp_flat_index(bits, dims):
     return r
 
 
-def comp_states(dims):
-    nq = len(dims)
+def comp_states(dims, couplers=()):
+    """Flat indices of the computational states: qubit modes in {0, 1} (first qubit
+    most significant), coupler modes (indices in `couplers`) in level 0."""
+    qubits = [i for i in range(len(dims)) if i not in set(couplers)]
     out = []
-    for j in range(2 ** nq):
-        bits = [(j >> (nq - 1 - i)) & 1 for i in range(nq)]
+    for j in range(2 ** len(qubits)):
+        bits = [0] * len(dims)
+        for b, i in enumerate(qubits):
+            bits[i] = (j >> (len(qubits) - 1 - b)) & 1
         out.append(comp_flat_index(bits, dims))
     return out
 
@@ -124,6 +129,47 @@ def fluxonium_pair_cr(seed=0, T=100.0, dt=0.01, nseg=20):
             "couplings": [{"a": 0, "op_a": "n", "b": 1, "op_b": "n", "J": J}],
             "drives": [drive], "T": T, "dt": dt, "frame": "interaction",
             "col_index": comp_states(dims), "target": target, "fid_kind": "avg"}
+
+
+def fluxonium_pair_multipath(seed=0, T=50.0, dt=0.01, nseg=10, levels=4):
+    """Two fluxoniums with the multipath coupling of Sec. 3.1, J_C n1 n2 - J_L phi1 phi2
+    (J_C ~ U[10, 30] MHz, J_L ~ U[0.5, 2] MHz: a capacitive and an inductive term on
+    the same pair), PWC flux drives on both qubits at their own 0-1 frequencies,
+    Haar target, all computational states."""
+    rng = _rng(seed)
+    modes = [_fluxonium_mode(rng, levels), _fluxonium_mode(rng, levels)]
+    jc = rng.uniform(10.0, 30.0) * MHZ
+    jl = rng.uniform(0.5, 2.0) * MHZ
+    drives = [_pwc_drive(rng, i, "phi", nseg, T, omega_mode=i) for i in range(2)]
+    dims = [levels, levels]
+    return {"name": f"fluxonium_multipath_l{levels}", "modes": modes,
+            "couplings": [{"a": 0, "op_a": "n", "b": 1, "op_b": "n", "J": jc},
+                          {"a": 0, "op_a": "phi", "b": 1, "op_b": "phi", "J": -jl}],
+            "drives": drives, "T": T, "dt": dt, "frame": "interaction",
+            "col_index": comp_states(dims), "target": haar_unitary(4, rng), "fid_kind": "avg"}
+
+
+def coupler_scheme(seed=0, kind="ftf", T=40.0, dt=0.01, nseg=10, levels=(4, 4, 4)):
+    """Two qubits interacting through a transmon coupler in the middle (Sec. 4: "ttt",
+    transmon qubits with a transmon coupler; "ftf", fluxonium qubits with a transmon
+    coupler).  Qubit-coupler couplings n (x) n with g ~ U[20, 60] MHz and a weaker
+    direct qubit-qubit n (x) n term (U[1, 5] MHz); PWC drives on the two qubits at
+    their own 0-1 frequencies; the coupler is undriven and held in its ground state
+    in the computational subspace (4 states); Haar 4 x 4 target."""
+    rng = _rng(seed)
+    qubit = _fluxonium_mode if kind == "ftf" else _transmon_mode
+    op = "phi" if kind == "ftf" else "n"
+    modes = [qubit(rng, levels[0]), dict(_transmon_mode(rng, levels[1]), coupler=True),
+             qubit(rng, levels[2])]
+    couplings = [{"a": 0, "op_a": "n", "b": 1, "op_b": "n", "J": rng.uniform(20.0, 60.0) * MHZ},
+                 {"a": 1, "op_a": "n", "b": 2, "op_b": "n", "J": rng.uniform(20.0, 60.0) * MHZ},
+                 {"a": 0, "op_a": "n", "b": 2, "op_b": "n", "J": rng.uniform(1.0, 5.0) * MHZ}]
+    drives = [_pwc_drive(rng, i, op, nseg, T, omega_mode=i) for i in (0, 2)]
+    dims = list(levels)
+    return {"name": f"{kind}_l{'_'.join(map(str, levels))}", "modes": modes,
+            "couplings": couplings, "drives": drives, "T": T, "dt": dt, "frame": "interaction",
+            "col_index": comp_states(dims, couplers=(1,)), "target": haar_unitary(4, rng),
+            "fid_kind": "avg"}
 
 
 def fluxonium_chain(seed=0, nq=6, levels=4, T=60.0, dt=0.01, nseg=10, ring=False,

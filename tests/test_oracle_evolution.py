@@ -224,3 +224,36 @@ def test_adjoint_state_fidelity_on_chain():
     fd = finite_difference_gradient(wl, idx)
     for k, p in enumerate(idx):
         assert abs(g[p] - fd[k]) <= 1e-5 * max(abs(g[p]), 1e-7), (prms[p], g[p], fd[k])
+
+
+def test_decoupled_coupler_mode_leaves_fidelity_and_gradient_unchanged():
+    # A coupler mode that nothing couples to or drives stays in its ground state:
+    # the fidelity over the qubit modes and every shared gradient component equal
+    # those of the same qubits without it (checks the coupler's place in the
+    # computational map, the labels and the padded parameter vector).
+    import copy
+    from oracle.evolve import evolve_and_fidelity, adjoint_gradient
+    wl2 = W.fluxonium_pair_multipath(seed=3, T=0.3, dt=0.01, nseg=3, levels=3)
+    wl3 = copy.deepcopy(wl2)
+    coupler = {"kind": "transmon", "ej": 20.0 * GHZ, "ec": 0.25 * GHZ, "ng": 0.0, "ncut": 10,
+               "levels": 3, "coupler": True}
+    wl3["modes"] = [wl2["modes"][0], coupler, wl2["modes"][1]]
+    remap = {0: 0, 1: 2}
+    for c in wl3["couplings"]:
+        c["a"], c["b"] = remap[c["a"]], remap[c["b"]]
+    for d in wl3["drives"]:
+        d["mode"], d["omega_mode"] = remap[d["mode"]], remap[d["omega_mode"]]
+    wl3["col_index"] = W.comp_states([3, 3, 3], couplers=(1,))
+    r2, r3 = evolve_and_fidelity(wl2), evolve_and_fidelity(wl3)
+    assert abs(r2["F_avg"] - r3["F_avg"]) < 1e-12 and abs(r2["F_state"] - r3["F_state"]) < 1e-12
+    assert np.max(np.abs(r2["Uc"] - r3["Uc"])) < 1e-12
+    F2, g2, p2 = adjoint_gradient(wl2)
+    F3, g3, p3 = adjoint_gradient(wl3)
+    assert abs(F2 - F3) < 1e-12
+    g3d = {p: v for p, v in zip(p3, g3)}
+    # pulse amplitudes and couplings keep their index; mode parameters follow the remap
+    for p, v in zip(p2, g2):
+        q = ("ham", remap[p[1]], p[2]) if p[0] == "ham" else p
+        assert abs(g3d[q] - v) <= 1e-10 * max(1.0, abs(v)), p
+    # nothing couples to or drives the coupler, so its own parameters have no effect
+    assert all(abs(g3d[("ham", 1, x)]) < 1e-12 for x in ("ej", "ec", "el"))
