@@ -57,6 +57,7 @@ enum {
 };
 
 enum { SG_OP_N = 0, SG_OP_PHI = 1 };                          /* charge n, phase phi         */
+/* operators 2, 3, ... of a mode: its local operators (sg_add_local_op), at most 6 */
 enum { SG_ENV_GAUSSIAN = 0, SG_ENV_PWC = 1, SG_ENV_COSINE = 2 };
 enum { SG_FP64 = 0, SG_MIXED = 1 };                           /* arithmetic of the evolution */
 enum { SG_FRAME_INTERACTION = 0, SG_FRAME_LAB = 1 };
@@ -100,6 +101,17 @@ sg_status sg_add_fluxonium(sg_system* sys, double ej, double ec, double el, doub
  * SG_OP_N. */
 sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b,
                           double strength, int* term_out);
+
+/* A local operator of one mode for generic Kronecker terms (Eq. 1: every term acts
+ * on one or two subsystems): `re_im` is a d x d Hermitian matrix (d = the mode's
+ * levels, row-major, interleaved real and imaginary parts, copied) in the mode's
+ * truncated eigenbasis (sign gauge of sg_get_spectrum).  It can then be used as the
+ * operator of drives and couplings like SG_OP_N; *op_out receives its id (2, 3, ...).
+ * Its matrix elements are fixed: the gradient w.r.t. E_J, E_C, E_L sees only its
+ * frame phases exp(i (E_a - E_b) t), not a change of the eigenbasis.  Marks the
+ * system unprepared.  SG_E_INVALID: bad mode, NULL, non-finite or non-Hermitian
+ * (|O - O^dag| > 1e-12 max|O|); SG_E_UNSUPPORTED: more than 6 on one mode. */
+sg_status sg_add_local_op(sg_system* sys, int mode, const double* re_im, int* op_out);
 
 /* Mark a mode as a coupler (coupler != 0) or as a qubit (0, the default).  The
  * computational subspace of the fidelity (Eq. 13, Eq. D2) is every qubit mode in

@@ -106,7 +106,18 @@ class OracleSystem:
 
     # ---- local operators ---------------------------------------------------------
     def op(self, mode, name):
-        return self.modes[mode]["ops"][name]
+        """n, phi, or a mode's user-given local operator (workload mode dict
+        "local_ops": {name: d x d Hermitian matrix in the truncated eigenbasis})."""
+        if name in self.modes[mode]["ops"]:
+            return self.modes[mode]["ops"][name]
+        return np.asarray(self.wl["modes"][mode]["local_ops"][name], dtype=np.complex128)
+
+    def dop(self, dops, mode, name):
+        """d(op)/dtheta: local operators have fixed matrix elements in the truncated
+        eigenbasis, so they do not depend on the device parameters."""
+        if name in dops:
+            return dops[name]
+        return np.zeros((self.dims[mode], self.dims[mode]), dtype=np.complex128)
 
     def phases(self, mode, t):
         return np.exp(1j * self.modes[mode]["E"] * t)
@@ -238,7 +249,7 @@ class OracleSystem:
             f = self.coeff(k, n, j)
             if dr["mode"] == i:
                 X = self.op(i, dr["op"])
-                out += f * self.embed({i: dframe(X, dops[dr["op"]])})
+                out += f * self.embed({i: dframe(X, self.dop(dops, i, dr["op"]))})
             if dr.get("omega_mode") == i:
                 # carrier tied to this mode's 0-1 frequency (R8)
                 E, _ = envelope(dr, n, j, self.dt)
@@ -250,10 +261,10 @@ class OracleSystem:
                 A = self.frame_op(self.op(c["a"], c["op_a"]), c["a"], t)
                 B = self.frame_op(self.op(c["b"], c["op_b"]), c["b"], t)
                 if c["a"] == i:
-                    A = dframe(self.op(i, c["op_a"]), dops[c["op_a"]])
+                    A = dframe(self.op(i, c["op_a"]), self.dop(dops, i, c["op_a"]))
                     out += c["J"] * self.embed({c["a"]: A, c["b"]: B})
                 else:
-                    B = dframe(self.op(i, c["op_b"]), dops[c["op_b"]])
+                    B = dframe(self.op(i, c["op_b"]), self.dop(dops, i, c["op_b"]))
                     out += c["J"] * self.embed({c["a"]: A, c["b"]: B})
         return out
 

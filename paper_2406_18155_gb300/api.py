@@ -74,9 +74,30 @@ class System:
         check(lib().sg_system_create(ctx.h, C.byref(h)), ctx.h)
         self.h = h
         self._keep = []
+        self._local = {}              # (mode, name) -> operator id of a local operator
 
     def _chk(self, rc):
         return check(rc, self.ctx.h)
+
+    def _op(self, mode, op):
+        """Operator id: "n", "phi", a local operator's name on this mode, or an id."""
+        if isinstance(op, (int, np.integer)):
+            return int(op)
+        if op in _OPS:
+            return _OPS[op]
+        return self._local[(mode, op)]
+
+    def add_local_op(self, mode, matrix, name=None):
+        """A d x d Hermitian operator of `mode` in its truncated eigenbasis
+        (sg_add_local_op); returns its id, usable by add_drive / add_coupling
+        (by id, or by `name`)."""
+        a = np.ascontiguousarray(np.asarray(matrix, dtype=np.complex128))
+        buf = np.ascontiguousarray(a.view(np.float64).reshape(-1))
+        k = C.c_int()
+        self._chk(lib().sg_add_local_op(self.h, mode, buf.ctypes.data_as(C.POINTER(C.c_double)), C.byref(k)))
+        if name is not None:
+            self._local[(mode, name)] = k.value
+        return k.value
 
     # --- definition -----------------------------------------------------------
     def add_transmon(self, ej, ec, ng=0.0, ncut=10, levels=4):
@@ -91,7 +112,7 @@ class System:
 
     def add_coupling(self, a, op_a, b, op_b, J):
         t = C.c_int()
-        self._chk(lib().sg_add_coupling(self.h, a, _OPS[op_a], b, _OPS[op_b], J, C.byref(t)))
+        self._chk(lib().sg_add_coupling(self.h, a, self._op(a, op_a), b, self._op(b, op_b), J, C.byref(t)))
         return t.value
 
     def set_coupler(self, mode, coupler=True):
@@ -114,7 +135,7 @@ class System:
         p.omega_mode = -1 if omega_mode is None else int(omega_mode)
         p.phase = float(phase)
         k = C.c_int()
-        self._chk(lib().sg_add_drive(self.h, mode, _OPS[op], C.byref(p), C.byref(k)))
+        self._chk(lib().sg_add_drive(self.h, mode, self._op(mode, op), C.byref(p), C.byref(k)))
         return k.value
 
     @classmethod
@@ -129,6 +150,8 @@ class System:
         for i, m in enumerate(wl["modes"]):
             if m.get("coupler"):
                 s.set_coupler(i, True)
+            for name, mat in m.get("local_ops", {}).items():
+                s.add_local_op(i, mat, name)
         for c in wl["couplings"]:
             s.add_coupling(c["a"], c["op_a"], c["b"], c["op_b"], c["J"])
         for d in wl["drives"]:

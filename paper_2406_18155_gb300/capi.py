@@ -72,6 +72,7 @@ SIGNATURES = {
     "sg_add_fluxonium": (_I, [_P, _D, _D, _D, _D, _I, _I, _PI]),
     "sg_add_coupling": (_I, [_P, _I, _I, _I, _I, _D, _PI]),
     "sg_set_coupler": (_I, [_P, _I, _I]),
+    "sg_add_local_op": (_I, [_P, _I, _PD, _PI]),
     "sg_add_drive": (_I, [_P, _I, _I, C.POINTER(sg_pulse), _PI]),
     "sg_param_counts": (_I, [_P, _PI, _PI]),
     "sg_get_params": (_I, [_P, _PD, _PD]),

@@ -1,5 +1,6 @@
 // C ABI: argument checking, system bookkeeping and dispatch.  See include/sg.h.
 #include "sg_internal.h"
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -102,9 +103,35 @@ sg_status sg_add_fluxonium(sg_system* sys, double ej, double ec, double el, doub
 
 static bool op_ok(const sg_system* sys, int mode, int op) {
   if (mode < 0 || mode >= (int)sys->modes.size()) return false;
+  const HostMode& m = sys->modes[mode];
+  if (op >= 2) return (size_t)(op - 2) < m.local.size() / (2 * (size_t)m.d * m.d);
   if (op != SG_OP_N && op != SG_OP_PHI) return false;
-  if (op == SG_OP_PHI && sys->modes[mode].kind == 0) return false;
+  if (op == SG_OP_PHI && m.kind == 0) return false;
   return true;
+}
+
+sg_status sg_add_local_op(sg_system* sys, int mode, const double* re_im, int* op_out) {
+  if (!sys) return SG_E_INVALID;
+  if (mode < 0 || mode >= (int)sys->modes.size()) return sg_fail(sys->ctx, SG_E_INVALID, "mode index out of range");
+  if (!re_im) return sg_fail(sys->ctx, SG_E_INVALID, "operator is NULL");
+  HostMode& m = sys->modes[mode];
+  const int d = m.d;
+  const int nloc = (int)(m.local.size() / (2 * (size_t)d * d));
+  if (nloc >= SG_MAXOP - 2) return sg_fail(sys->ctx, SG_E_UNSUPPORTED, "at most 6 local operators per mode");
+  double mx = 0.0, herm = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      const double xr = re_im[2 * (a * d + b)], xi = re_im[2 * (a * d + b) + 1];
+      const double yr = re_im[2 * (b * d + a)], yi = re_im[2 * (b * d + a) + 1];
+      if (!isfin(xr) || !isfin(xi)) return sg_fail(sys->ctx, SG_E_INVALID, "operator entries must be finite");
+      mx = std::max(mx, std::hypot(xr, xi));
+      herm = std::max(herm, std::hypot(xr - yr, xi + yi));
+    }
+  if (herm > 1e-12 * mx) return sg_fail(sys->ctx, SG_E_INVALID, "local operator must be Hermitian");
+  m.local.insert(m.local.end(), re_im, re_im + 2 * d * d);
+  sys->prepared = false;
+  if (op_out) *op_out = 2 + nloc;
+  return SG_OK;
 }
 
 sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b, double strength,

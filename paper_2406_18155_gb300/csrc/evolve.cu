@@ -741,15 +741,16 @@ struct AssembleArgs {
 __global__ void k_assemble(AssembleArgs a) {
   for (int x = threadIdx.x; x < a.nq * SG_MAXD * SG_MAXD; x += blockDim.x) {
     const int i = x / (SG_MAXD * SG_MAXD), ab = x % (SG_MAXD * SG_MAXD);
+    // n and phi only: local operators have fixed matrix elements (no device-parameter chain)
     double2 o[2] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0)};
     for (int k = 0; k < a.K; ++k)
-      if (a.drv_mode[k] == i) {
+      if (a.drv_mode[k] == i && a.drv_op[k] < 2) {
         double2 v = a.acc.obD[(size_t)k * SG_MAXD * SG_MAXD + ab];
         o[a.drv_op[k]].x += v.x; o[a.drv_op[k]].y += v.y;
       }
     for (int e = 0; e < a.ne; ++e) {
-      if (a.e_a[e] == i) { double2 v = a.acc.obL[(size_t)e * SG_MAXD * SG_MAXD + ab]; o[a.e_opa[e]].x += v.x; o[a.e_opa[e]].y += v.y; }
-      if (a.e_b[e] == i) { double2 v = a.acc.obR[(size_t)e * SG_MAXD * SG_MAXD + ab]; o[a.e_opb[e]].x += v.x; o[a.e_opb[e]].y += v.y; }
+      if (a.e_a[e] == i && a.e_opa[e] < 2) { double2 v = a.acc.obL[(size_t)e * SG_MAXD * SG_MAXD + ab]; o[a.e_opa[e]].x += v.x; o[a.e_opa[e]].y += v.y; }
+      if (a.e_b[e] == i && a.e_opb[e] < 2) { double2 v = a.acc.obR[(size_t)e * SG_MAXD * SG_MAXD + ab]; o[a.e_opb[e]].x += v.x; o[a.e_opb[e]].y += v.y; }
     }
     a.opbar[(i * 2 + 0) * SG_MAXD * SG_MAXD + ab] = o[0];
     a.opbar[(i * 2 + 1) * SG_MAXD * SG_MAXD + ab] = o[1];
@@ -912,7 +913,7 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
     bool has = o->frame == SG_FRAME_LAB;
     bool par = o->frame == SG_FRAME_INTERACTION;
     for (const HostDrive& hd : sys->drives)
-      if (hd.mode == i) { has = true; if (!sys->parity_odd[2 * i + hd.op]) par = false; }
+      if (hd.mode == i) { has = true; if (!sys->parity_odd[SG_MAXOP * i + hd.op]) par = false; }
     if (!has) continue;
     const int u = p.n1++;
     s.s1_of_mode[i] = u;
@@ -933,8 +934,8 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
     p.e_a[e] = c.a; p.e_b[e] = c.b;
     p.e_offL[e] = row; row += p.dims[c.a] * p.dims[c.a];
     p.e_offR[e] = row; row += p.dims[c.b] * p.dims[c.b];
-    if (sys->parity_odd[2 * c.a + c.op_a]) p.parL |= 1ull << e;
-    if (sys->parity_odd[2 * c.b + c.op_b]) p.parR |= 1ull << e;
+    if (sys->parity_odd[SG_MAXOP * c.a + c.op_a]) p.parL |= 1ull << e;
+    if (sys->parity_odd[SG_MAXOP * c.b + c.op_b]) p.parR |= 1ull << e;
     ta.e_opa[e] = c.op_a; ta.e_opb[e] = c.op_b; ta.J[e] = c.J;
   }
   p.row = std::max(row, 1);

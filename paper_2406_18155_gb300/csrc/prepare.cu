@@ -414,7 +414,7 @@ sg_status sg_prepare_impl(sg_system* sys) {
   // host copies of the truncated data
   sys->E_host.assign(nq, {});
   sys->opd_host.assign(nq, {});
-  sys->parity_odd.assign(2 * nq, 0);
+  sys->parity_odd.assign(SG_MAXOP * nq, 0);
   for (int q = 0; q < nq; ++q) {
     const int d = sys->modes[q].d;
     sys->E_host[q].resize(d);
@@ -426,11 +426,15 @@ sg_status sg_prepare_impl(sg_system* sys) {
                                      ctx->stream));
   }
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  // local operators follow n and phi in each mode's block
+  for (int q = 0; q < nq; ++q)
+    sys->opd_host[q].insert(sys->opd_host[q].end(), sys->modes[q].local.begin(), sys->modes[q].local.end());
   // parity structure: entries with (a + b) even negligible -> the operator only
   // couples levels of opposite parity (true at n_g = 0 and phi_ext = pi)
   for (int q = 0; q < nq; ++q) {
     const int d = sys->modes[q].d;
-    for (int op = 0; op < 2; ++op) {
+    const int nop = (int)(sys->opd_host[q].size() / (2 * (size_t)d * d));
+    for (int op = 0; op < nop; ++op) {
       const double* o = sys->opd_host[q].data() + op * 2 * d * d;
       double mx = 0.0, even = 0.0;
       for (int a = 0; a < d; ++a)
@@ -439,7 +443,7 @@ sg_status sg_prepare_impl(sg_system* sys) {
           mx = std::max(mx, m);
           if (((a + b) & 1) == 0) even = std::max(even, m);
         }
-      sys->parity_odd[2 * q + op] = (mx > 0.0 && even <= 1e-13 * mx) ? 1 : 0;
+      sys->parity_odd[SG_MAXOP * q + op] = (mx > 0.0 && even <= 1e-13 * mx) ? 1 : 0;
     }
   }
   sys->prepared = true;

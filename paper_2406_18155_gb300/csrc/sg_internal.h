@@ -13,6 +13,7 @@
 #define SG_MAXM 64        // subsystem basis size (charge states or oscillator states)
 #define SG_MAXEDGE 48     // 2-body terms per system
 #define SG_MAXDRIVE 48    // drives per system
+#define SG_MAXOP 8        // operators per mode: n, phi and up to 6 local operators
 
 // ---------------------------------------------------------------------------
 // Host-side model of a system
@@ -23,6 +24,7 @@ struct HostMode {
   int M;           // basis size
   int d;           // kept levels
   int coupler;     // 1: held in its ground state in the computational subspace
+  std::vector<double> local;   // local operators, 2 d^2 doubles each (truncated eigenbasis)
 };
 struct HostCoupling { int a, op_a, b, op_b; double J; };
 struct HostDrive {
@@ -68,7 +70,7 @@ struct sg_system {
   // host copies of the prepared truncated data
   std::vector<std::vector<double>> E_host;       // per mode, d
   std::vector<std::vector<double>> opd_host;     // per mode, 2*d*d complex -> 4*d*d doubles
-  std::vector<int> parity_odd;                   // per mode*2+op: operator is parity-odd
+  std::vector<int> parity_odd;                   // per mode*SG_MAXOP+op: operator is parity-odd
   double last_stats[5] = {0, 0, 0, 0, 0};
   double ktimes[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };

@@ -11,8 +11,10 @@ A workload is a plain dict::
       "name": str,
       "modes":     [{"kind": "transmon", "ej", "ec", "ng", "ncut", "levels"} |
                     {"kind": "fluxonium", "ej", "ec", "el", "phi_ext", "n_osc", "levels"}],
-                   (optional "coupler": True: held in level 0 in the computational subspace)
-      "couplings": [{"a", "op_a", "b", "op_b", "J"}],          # op in {"n", "phi"}
+                   (optional "coupler": True: held in level 0 in the computational subspace;
+                    optional "local_ops": {name: d x d Hermitian matrix in the truncated
+                    eigenbasis}, usable as an operator name on that mode)
+      "couplings": [{"a", "op_a", "b", "op_b", "J"}],          # op: "n", "phi" or a local name
       "drives":    [{"mode", "op", "env", "amp" | "amps", "sigma", "t0", "length",
                      "omega_d" (float) or "omega_mode" (int), "phase"}],
       "T", "dt", "frame" ("interaction" | "lab"),
@@ -145,6 +147,29 @@ def fluxonium_pair_multipath(seed=0, T=50.0, dt=0.01, nseg=10, levels=4):
     return {"name": f"fluxonium_multipath_l{levels}", "modes": modes,
             "couplings": [{"a": 0, "op_a": "n", "b": 1, "op_b": "n", "J": jc},
                           {"a": 0, "op_a": "phi", "b": 1, "op_b": "phi", "J": -jl}],
+            "drives": drives, "T": T, "dt": dt, "frame": "interaction",
+            "col_index": comp_states(dims), "target": haar_unitary(4, rng), "fid_kind": "avg"}
+
+
+def local_op_pair(seed=0, T=30.0, dt=0.01, nseg=10, levels=4):
+    """Two fluxoniums with generic Kronecker terms (Eq. 1) built from local operators
+    given in the truncated eigenbasis: a drive on qubit 0 through sx = |0><1| + |1><0|
+    (parity-odd), a seeded random Hermitian h on each mode (no parity structure,
+    entries ~ 0.1) coupled as J_h h (x) h with J_h ~ U[1, 5] MHz next to the n (x) n
+    coupling, and a PWC flux drive on qubit 1; Haar target."""
+    rng = _rng(seed)
+    modes = [_fluxonium_mode(rng, levels), _fluxonium_mode(rng, levels)]
+    sx = np.zeros((levels, levels), dtype=np.complex128)
+    sx[0, 1] = sx[1, 0] = 1.0
+    for m in modes:
+        g = (rng.standard_normal((levels, levels)) + 1j * rng.standard_normal((levels, levels))) * 0.05
+        m["local_ops"] = {"sx": sx.copy(), "h": g + g.conj().T}
+    couplings = [{"a": 0, "op_a": "n", "b": 1, "op_b": "n", "J": rng.uniform(10.0, 30.0) * MHZ},
+                 {"a": 0, "op_a": "h", "b": 1, "op_b": "h", "J": rng.uniform(1.0, 5.0) * MHZ}]
+    drives = [_pwc_drive(rng, 0, "sx", nseg, T, omega_mode=0),
+              _pwc_drive(rng, 1, "phi", nseg, T, omega_mode=1)]
+    dims = [levels, levels]
+    return {"name": f"local_op_pair_l{levels}", "modes": modes, "couplings": couplings,
             "drives": drives, "T": T, "dt": dt, "frame": "interaction",
             "col_index": comp_states(dims), "target": haar_unitary(4, rng), "fid_kind": "avg"}
 

@@ -257,3 +257,28 @@ def test_decoupled_coupler_mode_leaves_fidelity_and_gradient_unchanged():
         assert abs(g3d[q] - v) <= 1e-10 * max(1.0, abs(v)), p
     # nothing couples to or drives the coupler, so its own parameters have no effect
     assert all(abs(g3d[("ham", 1, x)]) < 1e-12 for x in ("ej", "ec", "el"))
+
+
+def test_local_operator_equal_to_n_reproduces_the_builtin_term():
+    # A local operator given as the mode's own truncated n must drive the same
+    # evolution as "n": same F and the same pulse and coupling gradients.  Only the
+    # device-parameter gradients differ (a local operator's matrix elements are
+    # fixed, the builtin n moves with the eigenbasis).
+    import copy
+    from oracle.evolve import evolve_and_fidelity, adjoint_gradient
+    from oracle.subsystems import build_mode
+    wl = W.fluxonium_pair_multipath(seed=9, T=0.3, dt=0.01, nseg=3, levels=3)
+    wl2 = copy.deepcopy(wl)
+    for i, m in enumerate(wl2["modes"]):
+        spec = {k: v for k, v in m.items() if k != "local_ops"}
+        m["local_ops"] = {"nn": build_mode(spec)["ops"]["n"]}
+    wl2["couplings"][0]["op_a"] = wl2["couplings"][0]["op_b"] = "nn"
+    r1, r2 = evolve_and_fidelity(wl), evolve_and_fidelity(wl2)
+    assert abs(r1["F_avg"] - r2["F_avg"]) < 1e-13
+    F1, g1, p1 = adjoint_gradient(wl)
+    F2, g2, p2 = adjoint_gradient(wl2)
+    assert p1 == p2 and abs(F1 - F2) < 1e-13
+    for p, a, b in zip(p1, g1, g2):
+        if p[0] != "ham":
+            assert abs(a - b) <= 1e-11 * max(1.0, abs(a)), p
+    assert any(abs(a - b) > 1e-9 for p, a, b in zip(p1, g1, g2) if p[0] == "ham")
