@@ -179,10 +179,14 @@ def run_ours(args):
     prec = args.precision
     stream = torch.cuda.current_stream(local)
 
-    def one_step():
+    # gradient set of the configuration: the ring asks for the pulse segments only
+    grad = args.grad if args.grad != "config" else ("pulse" if args.workload == "fluxonium_ring10" else "all")
+    args.grad_set = grad
+
+    def one_step(ham=(grad == "all")):
         sysm.prepare()
         return sysm.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
-                                  kind=wl["fid_kind"], precision=prec, ckpt=args.ckpt)
+                                  kind=wl["fid_kind"], precision=prec, ckpt=args.ckpt, ham=ham)
 
     for _ in range(args.warmup):
         one_step()
@@ -255,6 +259,7 @@ def run_ours(args):
                "data": "synthetic (seeded, shapes and value ranges of the paper's fluxonium workloads)",
                "config": {"workload": f"{args.workload}: {desc}", "columns": S, "rk4_steps": N,
                           "composite_dim": D, "precision": prec,
+                          "gradient": "pulse parameters" if grad == "pulse" else "pulse and Hamiltonian parameters",
                           "l2": "inputs larger than L2 (slab 128 MiB c64 / 256 MiB c128)"
                           if D * S * 8 > 129e6 else "L2-resident working set; no flush",
                           "parallelism": f"{world} independent replica(s), one per GPU"},
@@ -266,6 +271,17 @@ def run_ours(args):
                "gpu_launches": int(launches), "clocks": clocks}
         # ---- roofline of the dominant kernel family
         out["roofline"], out["kernel_families"] = roofline(fam, D, S, N, prec, sysm, args)
+        if grad == "pulse" and args.full_gradient:
+            # the same solve with the Hamiltonian-parameter gradient too (one run, for reference)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            one_step(ham=True)
+            torch.cuda.synchronize()
+            tf = time.perf_counter() - t0
+            st = sysm.last_stats()
+            out["full_gradient"] = {"col_steps_per_s": S * N / tf, "forward_ms": st["forward_ms"],
+                                    "gradient_ms": st["backward_ms"],
+                                    "note": "pulse + Hamiltonian parameters, one untimed-by-events run"}
         # ---- the plain FP64 GPU path on a bounded number of steps
         if args.fp64_steps > 0:
             out["fp64_vs_mixed"] = fp64_comparison(sysm, wl, args.fp64_steps, stream)
@@ -410,7 +426,7 @@ def roofline(fam, D, S, N, prec, sysm, args):
     if os.path.exists(tf):
         with open(tf) as fh:
             t = json.load(fh)
-        key = f"{args.workload}:{prec}:{dom}"
+        key = f"{args.workload}:{prec}:{getattr(args, 'grad_set', 'all')}:{dom}"
         if key in t:
             traffic = t[key]
     return ({"bound": "hbm", "kernel": dom, "achieved": f["achieved_gbs"], "peak": hbm,
@@ -503,6 +519,10 @@ def main():
     ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
     ap.add_argument("--t-ns", type=float, default=0.0, help="shorten the workload to T ns (profiling)")
+    ap.add_argument("--grad", default="config", choices=["config", "pulse", "all"],
+                    help="gradient set: the configuration's (ring: pulse segments), pulse only, or all")
+    ap.add_argument("--no-full-gradient", dest="full_gradient", action="store_false",
+                    help="skip the reference run with the Hamiltonian gradient too")
     ap.add_argument("--onchip-shapes", type=int, default=0,
                     help="print per-shape on-chip step times over this many RK4 steps and exit")
     ap.add_argument("--shape", default=None, help="with --onchip-shapes: one shape class only")

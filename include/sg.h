@@ -224,6 +224,9 @@ sg_status sg_fidelity(sg_system* sys, const sg_evolve_opts* opts, const double* 
 /* F (of `kind`) and dF/dtheta by the exact discrete adjoint of RK4, with the forward
  * states recomputed per segment from checkpoints every `ckpt_interval` steps (0 =
  * about sqrt(N)).  grad_pulse / grad_ham are host arrays of sg_param_counts sizes.
+ * grad_ham may be NULL: the Hamiltonian-parameter gradient is then not computed,
+ * which skips the cross-densities of the coupling terms (the pulse gradient needs
+ * only those of the driven terms) and gives the same grad_pulse.
  * F_out receives {F_avg, F_state}. */
 sg_status sg_fidelity_grad(sg_system* sys, const sg_evolve_opts* opts,
                            const double* target_re_im, int kind, double* F_out,

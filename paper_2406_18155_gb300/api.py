@@ -232,15 +232,17 @@ class System:
         return F[0], F[1], U.view(np.complex128).reshape(Dc, len(col_index))
 
     def fidelity_grad(self, T, dt, target, col_index, kind="avg", precision="mixed",
-                      frame="interaction", ckpt=0):
+                      frame="interaction", ckpt=0, ham=True):
+        """F and the gradient w.r.t. the pulse and (ham=True) Hamiltonian parameters;
+        with ham=False the Hamiltonian part is not computed and returned as None."""
         o, keep = evolve_opts(T, dt, precision, frame, col_index)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         npul, nham = self.param_counts()
         gp, gh = np.zeros(max(npul, 1)), np.zeros(max(nham, 1))
         self._chk(lib().sg_fidelity_grad(self.h, C.byref(o), _dptr(tg), _KIND[kind], _dptr(F),
-                                         _dptr(gp), _dptr(gh), int(ckpt)))
-        return F, gp[:npul], gh[:nham]
+                                         _dptr(gp), _dptr(gh) if ham else None, int(ckpt)))
+        return F, gp[:npul], (gh[:nham] if ham else None)
 
     def last_stats(self):
         out = np.zeros(5)

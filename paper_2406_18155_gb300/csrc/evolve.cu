@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* 
     block_reduce_store<C, DL>(acc, mypart + (size_t)w * DL * DL, red);
   }
   // ---- 2-body slots: L side (fibres along mode a with R applied on mode b), then R side
-  for (int side = 0; side < 2; ++side) {
+  for (int side = 0; side < (a.ham ? 2 : 0); ++side) {
     for (int q = 0; q < p.ne; ++q, ++w) {
       const int i = side == 0 ? p.e_a[q] : p.e_b[q];      // fibre mode
       const int j = side == 0 ? p.e_b[q] : p.e_a[q];      // mode of the other factor
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* 
   __syncthreads();
   if (threadIdx.x == 0) *a.ticket = 0u;
   const int slot = threadIdx.x;
-  if (slot < a.nW) contract_slot(a, slot, Wt + slot * DL * DL, DL);
+  if (slot < a.nW && (a.ham || slot < a.p.n1)) contract_slot(a, slot, Wt + slot * DL * DL, DL);
 }
 
 // Pulse-parameter chain, one block per drive: dF/dparam = sum over stages of
@@ -1031,6 +1031,7 @@ struct Solve {
   bool mixed = false;
   SlabPlanHost* slab = nullptr;
   OnchipPlan* oc = nullptr;
+  bool want_ham = true;           // Hamiltonian-parameter gradient requested
   ~Solve() {
     slab_plan_destroy(slab);
     onchip_plan_destroy(oc);
@@ -1238,6 +1239,7 @@ XArgs make_xargs(const Solve& sv, GradAcc acc) {
   for (int k = 0; k < s.K; ++k) xa.drv_op[k] = s.drives[k].op;
   for (int e = 0; e < s.p.ne; ++e) { xa.e_opa[e] = s.ta.e_opa[e]; xa.e_opb[e] = s.ta.e_opb[e]; xa.J[e] = s.ta.J[e]; }
   xa.acc = acc;
+  xa.ham = sv.want_ham ? 1 : 0;
   return xa;
 }
 
@@ -1491,6 +1493,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (kind != SG_FID_AVG && kind != SG_FID_STATE) return sg_fail(ctx, SG_E_INVALID, "bad fidelity kind");
   Solve sv;
   sv.ar.st = ctx->stream;
+  sv.want_ham = grad_ham != nullptr;     // no Hamiltonian gradient: skip the coupling slots
   sg_status rc = build_setup(sys, o, sv.s);
   if (rc != SG_OK) return rc;
   Setup& s = sv.s;
@@ -1654,20 +1657,25 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
       aa.e_a[e] = s.p.e_a[e]; aa.e_b[e] = s.p.e_b[e]; aa.e_opa[e] = s.ta.e_opa[e]; aa.e_opb[e] = s.ta.e_opb[e];
     }
     aa.acc = acc; aa.omega_bar = omega_bar; aa.ebar_frame = ebar_frame; aa.opbar = opbar; aa.ebar = ebar;
-    k_assemble<<<1, kT, 0, st>>>(aa);
-    sv.launches += 2;
-    SG_CUDA_TRY(ctx, cudaGetLastError());
-    rc = sg_chain_device_params(sys, opbar, ebar, gdev);
-    if (rc != SG_OK) return rc;
     ++sv.launches;
+    if (grad_ham) {
+      k_assemble<<<1, kT, 0, st>>>(aa);
+      ++sv.launches;
+      SG_CUDA_TRY(ctx, cudaGetLastError());
+      rc = sg_chain_device_params(sys, opbar, ebar, gdev);
+      if (rc != SG_OK) return rc;
+      ++sv.launches;
+    }
     cudaEventRecord(ev2, st);
     SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));   // reads only from an idle stream (see dcopy)
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     std::vector<double> gd(3 * s.nq), jb(std::max(1, ne));
     if (s.n_pulse && grad_pulse)
       SG_CUDA_TRY(ctx, cudaMemcpyAsync(grad_pulse, gpulse, s.n_pulse * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(ctx, cudaMemcpyAsync(gd.data(), gdev, 3 * s.nq * sizeof(double), cudaMemcpyDeviceToHost, st));
-    SG_CUDA_TRY(ctx, cudaMemcpyAsync(jb.data(), acc.jb, std::max(1, ne) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (grad_ham) {
+      SG_CUDA_TRY(ctx, cudaMemcpyAsync(gd.data(), gdev, 3 * s.nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+      SG_CUDA_TRY(ctx, cudaMemcpyAsync(jb.data(), acc.jb, std::max(1, ne) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    }
     SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
     if (grad_ham) {
       for (int i = 0; i < s.nq; ++i) {

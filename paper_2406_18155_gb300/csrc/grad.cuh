@@ -22,6 +22,8 @@ struct GradAcc {
 struct XArgs {
   KPlan p;
   int K, nW, frame;
+  int ham;             // 0: the caller wants no Hamiltonian-parameter gradient, so the
+                       // coupling-term slots (slot >= p.n1) are skipped
   double t;            // stage time
   int q;               // stage slot 3n + j
   const double2* tabrow;      // FP64 row of this stage

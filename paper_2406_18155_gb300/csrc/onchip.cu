@@ -535,6 +535,7 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
         for (int slot = warp - oa.npw; slot < sp.nx; slot += nxw) {
           const Phase& P = sp.ph[sp.x_ph[slot]];
           const int type = sp.x_type[slot];
+          if (type >= 2 && !xa.ham) continue;         // coupling slot, not wanted (warp-uniform)
           C acc[NA];
 #pragma unroll
           for (int a = 0; a < NA; ++a) acc[a] = cmk<C>(0.0, 0.0);

@@ -176,6 +176,7 @@ k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename 
       if (slot >= sp.nx) continue;                  // warp-uniform
       const Phase& P = sp.ph[sp.x_ph[slot]];
       const int type = sp.x_type[slot];
+      if (type >= 2 && !xa.ham) continue;           // coupling slot, not wanted
       for (int b = lane; b < nb; b += 32)
         xd_slot<DL, PARX>(P, type, M, xs, ys, blk_pos<DL>(P, b), acc[s]);
     }
@@ -186,6 +187,7 @@ k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename 
   for (int s = 0; s < kSPW; ++s) {
     const int slot = warp + s * (kST / 32);
     if (slot >= sp.nx) continue;                    // warp-uniform
+    if (sp.x_type[slot] >= 2 && !xa.ham) continue;
 #pragma unroll
     for (int a = 0; a < DL; ++a)
 #pragma unroll
@@ -221,7 +223,8 @@ k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename 
   }
   __syncthreads();
   if (threadIdx.x == 0) *xa.ticket = 0u;
-  if (threadIdx.x < sp.nx) contract_slot(xa, sp.x_gslot[threadIdx.x], Wt + threadIdx.x * DL * DL, DL);
+  if (threadIdx.x < sp.nx && (xa.ham || sp.x_type[threadIdx.x] < 2))
+    contract_slot(xa, sp.x_gslot[threadIdx.x], Wt + threadIdx.x * DL * DL, DL);
 }
 
 

@@ -213,3 +213,18 @@ def test_two_pass_ring7_against_matrix_free_oracle(sgctx, monkeypatch):
         g[pth] = (F, np.concatenate([gp, gh]))
     assert abs(g["slab"][0][1] - g["gather"][0][1]) < 1e-12
     assert np.max(np.abs(g["slab"][1] - g["gather"][1])) <= 1e-10 * np.max(np.abs(g["gather"][1]))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_pulse_only_gradient_equals_the_pulse_part(sgctx, path, precision):
+    # without a Hamiltonian-gradient buffer the coupling-term cross-densities are
+    # skipped; the pulse gradient comes from the driven terms alone and is unchanged
+    wl = W.fluxonium_chain(seed=12, nq=4, levels=3, T=0.3, dt=0.01, nseg=3, ring=True)
+    s = _system(sgctx, wl)
+    F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                precision=precision, ckpt=5)
+    F2, gp2, gh2 = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                   precision=precision, ckpt=5, ham=False)
+    assert gh2 is None and gh is not None
+    assert np.array_equal(F, F2)
+    assert np.max(np.abs(gp2 - gp)) <= 1e-14 * np.max(np.abs(gp))
