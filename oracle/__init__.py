@@ -13,6 +13,7 @@ What it computes (paper sections in brackets):
 * the composite Hamiltonian as an explicit sum of Kronecker
   products of local operators, dense (np.kron) or matrix-free    [Eq. 1, App. B]
 * fixed-step classic RK4 time evolution of a batch of columns   (solver reading R1)
+* second-order Suzuki-Trotter evolution (the paper's solver)    [Sec. 2.3, App. A]
 * the composite state-transfer cost and the average gate
   fidelity                                                      [Eq. 13, Eq. D2]
 * the exact discrete adjoint of RK4 (the discretise-then-
@@ -31,11 +32,12 @@ from .evolve import (rk4_evolve, rk4_evolve_matrix_free, frame_epilogue,
                      fidelities, fidelity_and_costate, evolve_and_fidelity,
                      adjoint_gradient, tangent_linear_derivative,
                      finite_difference_gradient, param_vector, set_param_vector)
+from .trotter import q2_evolve, q2_evolve_and_fidelity
 
 __all__ = [
     "transmon", "fluxonium", "diagonalise", "build_mode", "mathieu_transmon_levels",
     "OracleSystem", "rk4_evolve", "rk4_evolve_matrix_free", "frame_epilogue",
     "fidelities", "fidelity_and_costate", "evolve_and_fidelity",
     "adjoint_gradient", "tangent_linear_derivative", "finite_difference_gradient",
-    "param_vector", "set_param_vector",
+    "param_vector", "set_param_vector", "q2_evolve", "q2_evolve_and_fidelity",
 ]
