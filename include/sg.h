@@ -186,7 +186,18 @@ typedef struct {
   int ncols;                    /* S, number of evolved columns                           */
   const long long* col_index;   /* host, S flat initial basis indices, or NULL: the
                                    columns of psi are the initial states                  */
+  int solver;                   /* SG_SOLVER_RK4 (0, default) or SG_SOLVER_Q2             */
 } sg_evolve_opts;
+
+/* Solvers.  SG_SOLVER_Q2: the second-order Suzuki-Trotter product of Sec. 2.3 and
+ * App. A, Q2(dt) = prod_k exp(-i H_k dt/2) prod_k' exp(-i H_k' dt/2) (k' reversed)
+ * over the local terms H_i = diag(E^(i)) + sum_{drives on i} f(t) O (every mode, in mode
+ * order) and J A (x) B (the couplings, in order), with the time-dependent terms at the
+ * step's midpoint; always in the lab frame (`frame` is ignored).  Runs on the on-chip
+ * kernels (every mode with the same level count 2..5, D <= 4096), else
+ * SG_E_UNSUPPORTED; sg_evolve and sg_fidelity only (sg_fidelity_grad:
+ * SG_E_UNSUPPORTED). */
+enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q2 = 2 };
 
 /* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev
  * (device, D*S complex128, column innermost).  If opts->col_index is NULL psi_dev

@@ -51,11 +51,15 @@ class Context:
             pass
 
 
-def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None):
+_SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q2": capi.SG_SOLVER_Q2}
+
+
+def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None, solver="rk4"):
     o = capi.sg_evolve_opts()
     o.T, o.dt = float(T), float(dt)
     o.precision = _PREC[precision]
     o.frame = _FRAME[frame]
+    o.solver = _SOLVER[solver]
     keep = None
     if col_index is not None:
         keep = np.ascontiguousarray(np.asarray(col_index, dtype=np.int64))
@@ -207,23 +211,24 @@ class System:
                                       None if ha is None else _dptr(ha)))
 
     # --- evolution -----------------------------------------------------------------
-    def evolve(self, T, dt, precision="mixed", frame="interaction", col_index=None, psi=None):
+    def evolve(self, T, dt, precision="mixed", frame="interaction", col_index=None, psi=None, solver="rk4"):
         """Lab-frame columns after T, as a (D, S) complex128 torch tensor on the device.
-        Starts from basis states col_index, or from the given device tensor psi."""
+        Starts from basis states col_index, or from the given device tensor psi.
+        solver: "rk4" or "q2" (second-order Suzuki-Trotter, lab frame)."""
         import torch
         D, _ = self.dims()
         if psi is None:
             S = len(col_index)
             psi = torch.empty((D, S), dtype=torch.complex128, device=f"cuda:{self.ctx.device}")
-            o, keep = evolve_opts(T, dt, precision, frame, col_index)
+            o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
         else:
             assert psi.dtype == torch.complex128 and psi.is_contiguous() and psi.shape[0] == D
-            o, keep = evolve_opts(T, dt, precision, frame, None, ncols=psi.shape[1])
+            o, keep = evolve_opts(T, dt, precision, frame, None, ncols=psi.shape[1], solver=solver)
         self._chk(lib().sg_evolve(self.h, C.byref(o), C.c_void_p(psi.data_ptr())))
         return psi
 
-    def fidelity(self, T, dt, target, col_index, precision="mixed", frame="interaction"):
-        o, keep = evolve_opts(T, dt, precision, frame, col_index)
+    def fidelity(self, T, dt, target, col_index, precision="mixed", frame="interaction", solver="rk4"):
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         Dc = target.shape[0]

@@ -216,6 +216,129 @@ __global__ void k_tables32(TabArgs a, float* __restrict__ coef32, float2* __rest
 }
 
 // ---------------------------------------------------------------------------
+// Second-order Suzuki-Trotter tables (Sec. 2.3, App. A), lab frame
+// ---------------------------------------------------------------------------
+// exp(A) of a small complex matrix (n x n, row-major) by scaling and squaring of
+// the Taylor series (Moler and Van Loan's method 3): A / 2^s with |A / 2^s|_1 <= 1/2,
+// 18 Taylor terms (remainder below 1e-22 of the norm), then s squarings.  Serial,
+// one thread: R = exp(A); W1, W2 are n x n scratch.
+__device__ void expm_serial(const double2* A, int n, double2* R, double2* W1, double2* W2) {
+  double nrm = 0.0;
+  for (int c = 0; c < n; ++c) {
+    double col = 0.0;
+    for (int r = 0; r < n; ++r) col += hypot(A[r * n + c].x, A[r * n + c].y);
+    nrm = fmax(nrm, col);
+  }
+  int sq = 0;
+  while (nrm > 0.5 && sq < 60) { nrm *= 0.5; ++sq; }
+  const double sc = ldexp(1.0, -sq);
+  for (int i = 0; i < n * n; ++i) {
+    W1[i] = make_double2((i / n == i % n) ? 1.0 : 0.0, 0.0);    // current term
+    R[i] = W1[i];
+  }
+  for (int k = 1; k <= 18; ++k) {
+    for (int r = 0; r < n; ++r)                                 // W2 = W1 (A sc) / k
+      for (int c = 0; c < n; ++c) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int m = 0; m < n; ++m) acc = cfma(W1[r * n + m], A[m * n + c], acc);
+        W2[r * n + c] = make_double2(acc.x * sc / k, acc.y * sc / k);
+      }
+    for (int i = 0; i < n * n; ++i) {
+      W1[i] = W2[i];
+      R[i].x += W2[i].x;
+      R[i].y += W2[i].y;
+    }
+  }
+  for (int q = 0; q < sq; ++q) {
+    for (int r = 0; r < n; ++r)
+      for (int c = 0; c < n; ++c) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int m = 0; m < n; ++m) acc = cfma(R[r * n + m], R[m * n + c], acc);
+        W2[r * n + c] = acc;
+      }
+    for (int i = 0; i < n * n; ++i) R[i] = W2[i];
+  }
+}
+
+// U_i(n) = exp(-i H_i(t_n + dt/2) dt/2), H_i = diag(E) + sum_{drives k on i} f_k O_k.
+__device__ void q2_onebody(const TabArgs& a, int i, int n, double2* U, double2* A, double2* W1, double2* W2) {
+  const int d = a.dims[i];
+  const double t = (double)(2 * n + 1) * a.dt * 0.5;
+  for (int x = 0; x < d * d; ++x) A[x] = make_double2(0.0, 0.0);
+  for (int x = 0; x < d; ++x) A[x * d + x].x = a.E[a.eoff[i] + x];
+  for (int k = 0; k < a.K; ++k) {
+    const DriveDev& dr = a.drives[k];
+    if (dr.mode != i) continue;
+    const double f = envelope_dev(dr, a.amps, n, 1, t) * cos(dr.omega * t + dr.phase);
+    const double2* O = a.opd + a.opd_off[i] + dr.op * d * d;
+    for (int x = 0; x < d * d; ++x) { A[x].x += f * O[x].x; A[x].y += f * O[x].y; }
+  }
+  const double h = a.dt * 0.5;
+  for (int x = 0; x < d * d; ++x) A[x] = make_double2(h * A[x].y, -h * A[x].x);    // -i H dt/2
+  expm_serial(A, d, U, W1, W2);
+}
+
+// Row n < N: V_i(n) = U_i(n+1) U_i(n) (the second half step of step n followed by the
+// first of step n + 1); row N - 1: U_i(N - 1); row N: U_i(0).  One thread per (row, mode).
+__global__ void k_q2_onebody(TabArgs a, int DL, double2* __restrict__ rows) {
+  const int nrow = a.N + 1;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nrow * a.nq; x += gridDim.x * blockDim.x) {
+    const int n = x / a.nq, i = x - n * a.nq, d = a.dims[i];
+    double2 U0[SG_MAXD * SG_MAXD], U1[SG_MAXD * SG_MAXD], A[SG_MAXD * SG_MAXD];
+    double2 W1[SG_MAXD * SG_MAXD], W2[SG_MAXD * SG_MAXD];
+    double2* out = rows + ((size_t)n * a.nq + i) * DL * DL;
+    if (n == a.N) {
+      q2_onebody(a, i, 0, U0, A, W1, W2);
+      for (int y = 0; y < d * d; ++y) out[y] = U0[y];
+      continue;
+    }
+    q2_onebody(a, i, n, U0, A, W1, W2);
+    if (n == a.N - 1) {
+      for (int y = 0; y < d * d; ++y) out[y] = U0[y];
+      continue;
+    }
+    q2_onebody(a, i, n + 1, U1, A, W1, W2);
+    for (int r = 0; r < d; ++r)
+      for (int c = 0; c < d; ++c) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int m = 0; m < d; ++m) acc = cfma(U1[r * d + m], U0[m * d + c], acc);
+        out[r * d + c] = acc;
+      }
+  }
+}
+
+// Per coupling e: G_half = exp(-i J A (x) B dt/2) and G_full = G_half^2 (the two
+// middle half steps of the palindrome), d_a d_b x d_a d_b with row index x d_b + z.
+// One thread per coupling.
+__global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double2* __restrict__ scratch) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= a.p.ne) return;
+  const int ia = a.p.e_a[e], ib = a.p.e_b[e], da = a.dims[ia], db = a.dims[ib], n = da * db;
+  const double2* Aop = a.opd + a.opd_off[ia] + a.e_opa[e] * da * da;
+  const double2* Bop = a.opd + a.opd_off[ib] + a.e_opb[e] * db * db;
+  double2* M = scratch + (size_t)e * 3 * n * n;
+  double2* W1 = M + n * n;
+  double2* W2 = W1 + n * n;
+  double2* Gh = mats + (size_t)e * 2 * DL * DL * DL * DL;
+  double2* Gf = Gh + DL * DL * DL * DL;
+  const double h = a.J[e] * a.dt * 0.5;
+  for (int x = 0; x < da; ++x)
+    for (int z = 0; z < db; ++z)
+      for (int p = 0; p < da; ++p)
+        for (int c = 0; c < db; ++c) {
+          const double2 v = cmul(Aop[x * da + p], Bop[z * db + c]);
+          M[(x * db + z) * n + p * db + c] = make_double2(h * v.y, -h * v.x);   // -i J (A x B) dt/2
+        }
+  expm_serial(M, n, Gh, W1, W2);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int m = 0; m < n; ++m) acc = cfma(Gh[r * n + m], Gh[m * n + c], acc);
+      Gf[r * n + c] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // H y at one slab entry (gather form)
 // ---------------------------------------------------------------------------
 template <typename C>
@@ -824,6 +947,8 @@ struct Setup {
   std::vector<int> s1_of_mode;
   std::vector<int> pulse_off;
   int n_pulse = 0;
+  bool q2 = false;                // second-order Suzuki-Trotter solver (lab frame)
+  int frame = SG_FRAME_INTERACTION;
   int nqb = 0;                    // qubit modes (the rest are couplers)
   int qpos[SG_MAXQ] = {0};        // bit of mode i in a comp label (LSB = 0), -1 for a coupler
 };
@@ -842,6 +967,10 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
     return sg_fail(ctx, SG_E_INVALID, "precision must be SG_FP64 or SG_MIXED");
   if (o->frame != SG_FRAME_INTERACTION && o->frame != SG_FRAME_LAB)
     return sg_fail(ctx, SG_E_INVALID, "frame must be SG_FRAME_INTERACTION or SG_FRAME_LAB");
+  if (o->solver != SG_SOLVER_RK4 && o->solver != SG_SOLVER_Q2)
+    return sg_fail(ctx, SG_E_INVALID, "solver must be SG_SOLVER_RK4 or SG_SOLVER_Q2");
+  s.q2 = o->solver == SG_SOLVER_Q2;
+  s.frame = s.q2 ? SG_FRAME_LAB : o->frame;          // Q2 always runs in the lab frame
   if (o->ncols < 1) return sg_fail(ctx, SG_E_INVALID, "ncols must be >= 1");
   s.N = (int)N;
   s.dt = o->dt;
@@ -910,8 +1039,8 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
   s.s1_of_mode.assign(s.nq, -1);
   int ndl = 0;
   for (int i = 0; i < s.nq; ++i) {
-    bool has = o->frame == SG_FRAME_LAB;
-    bool par = o->frame == SG_FRAME_INTERACTION;
+    bool has = s.frame == SG_FRAME_LAB;
+    bool par = s.frame == SG_FRAME_INTERACTION;
     for (const HostDrive& hd : sys->drives)
       if (hd.mode == i) { has = true; if (!sys->parity_odd[SG_MAXOP * i + hd.op]) par = false; }
     if (!has) continue;
@@ -947,7 +1076,7 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
     if (need > 48 * 1024) return sg_fail(ctx, SG_E_UNSUPPORTED, "too many terms for the stage kernels");
   }
   ta.p = p;
-  ta.nq = s.nq; ta.K = s.K; ta.N = s.N; ta.frame = o->frame;
+  ta.nq = s.nq; ta.K = s.K; ta.N = s.N; ta.frame = s.frame;
   for (int i = 0; i < s.nq; ++i) { ta.dims[i] = p.dims[i]; ta.eoff[i] = eoff[i]; ta.opd_off[i] = ooff[i]; }
   ta.sumd = s.sumd;
   ta.dt = o->dt;
@@ -1032,6 +1161,8 @@ struct Solve {
   SlabPlanHost* slab = nullptr;
   OnchipPlan* oc = nullptr;
   bool want_ham = true;           // Hamiltonian-parameter gradient requested
+  const void* q2rows = nullptr;   // Q2: 1-body unitaries and coupling unitaries (stage precision)
+  const void* q2edges = nullptr;
   ~Solve() {
     slab_plan_destroy(slab);
     onchip_plan_destroy(oc);
@@ -1066,8 +1197,12 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   sv.amps_dev = sv.ar.get<double>(std::max<size_t>(1, s.amps.size()));
   sv.E_dev = sv.ar.get<double>(s.sumd);
   sv.opd_dev = sv.ar.get<double2>(s.opdflat.size());
-  const size_t nst = 3ull * s.N;
-  if (f32only) {
+  const size_t nst = s.q2 ? 0 : 3ull * s.N;
+  if (s.q2) {
+    // Q2 reads no RK4 tables; it needs the on-chip kernels
+    if (!sv.oc) return sg_fail(ctx, SG_E_UNSUPPORTED, "the Q2 solver runs on the on-chip kernels: every mode "
+                                                    "with the same level count 2..5 and D <= 4096");
+  } else if (f32only) {
     sv.coef32 = sv.ar.get<float>(nst * std::max(1, s.K));
     sv.ph32 = sv.ar.get<float2>(nst * s.sumd);
   } else {
@@ -1075,9 +1210,9 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
     sv.ph = sv.ar.get<double2>(nst * s.sumd);
     sv.tab = sv.ar.get<double2>(nst * s.p.row);
   }
-  if (sv.mixed) sv.tab32 = sv.ar.get<float2>(nst * s.p.row);
-  if (!sv.drives_dev || !sv.amps_dev || !sv.E_dev || !sv.opd_dev || (sv.mixed && !sv.tab32) ||
-      (f32only ? (!sv.coef32 || !sv.ph32) : (!sv.coef || !sv.ph || !sv.tab)))
+  if (sv.mixed && !s.q2) sv.tab32 = sv.ar.get<float2>(nst * s.p.row);
+  if (!sv.drives_dev || !sv.amps_dev || !sv.E_dev || !sv.opd_dev ||
+      (!s.q2 && ((sv.mixed && !sv.tab32) || (f32only ? (!sv.coef32 || !sv.ph32) : (!sv.coef || !sv.ph || !sv.tab)))))
     return sg_fail(ctx, SG_E_NOMEM, "device allocation of the stage tables failed");
   if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.drives_dev, s.drives.data(), s.K * sizeof(DriveDev), cudaMemcpyHostToDevice, st));
   if (!s.amps.empty()) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.amps_dev, s.amps.data(), s.amps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -1093,8 +1228,33 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   ta.tab = sv.tab;
   ta.tab32 = sv.tab32;
   s.ta = ta;
-  if (f32only) k_tables32<<<(unsigned)nst, 64, 0, st>>>(ta, sv.coef32, sv.ph32);
-  else k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
+  if (s.q2) {
+    const int DL = onchip_dl(sv.oc);
+    const size_t nrow = (size_t)(s.N + 1) * s.nq * DL * DL, nedge = (size_t)std::max(1, s.p.ne) * 2 * DL * DL * DL * DL;
+    double2* rows = sv.ar.get<double2>(nrow);
+    double2* edges = sv.ar.get<double2>(nedge);
+    double2* scratch = sv.ar.get<double2>((size_t)std::max(1, s.p.ne) * 3 * DL * DL * DL * DL);
+    if (!rows || !edges || !scratch) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 tables failed");
+    k_q2_onebody<<<grid_for((long long)(s.N + 1) * s.nq), kT, 0, st>>>(ta, DL, rows);
+    if (s.p.ne) k_q2_edges<<<(s.p.ne + 31) / 32, 32, 0, st>>>(ta, DL, edges, scratch);
+    sv.launches += 2;
+    sv.q2rows = rows;
+    sv.q2edges = edges;
+    if (sv.mixed) {
+      float* r32 = sv.ar.get<float>(2 * nrow);
+      float* e32 = sv.ar.get<float>(2 * nedge);
+      if (!r32 || !e32) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 tables failed");
+      onchip_to_f32(reinterpret_cast<const double*>(rows), r32, 2 * (long long)nrow, st);
+      onchip_to_f32(reinterpret_cast<const double*>(edges), e32, 2 * (long long)nedge, st);
+      sv.launches += 2;
+      sv.q2rows = r32;
+      sv.q2edges = e32;
+    }
+  } else if (f32only) {
+    k_tables32<<<(unsigned)nst, 64, 0, st>>>(ta, sv.coef32, sv.ph32);
+  } else {
+    k_tables<<<(unsigned)nst, 64, 0, st>>>(ta);
+  }
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
   {
@@ -1443,6 +1603,21 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
 
 }  // namespace
 
+// Q2 evolution (on-chip) of the solve's columns, lab frame, in place in sv.psi.
+sg_status run_q2(sg_system* sys, Solve& sv, const long long* cols_dev, bool init_from_psi) {
+  sg_ctx* ctx = sys->ctx;
+  cudaStream_t st = ctx->stream;
+  Setup& s = sv.s;
+  if (!init_from_psi) {
+    k_init_cols<<<grid_for(s.D * s.S), kT, 0, st>>>(sv.psi, s.D, s.S, cols_dev);
+    ++sv.launches;
+  }
+  sg_status rc = onchip_q2_forward(sv.oc, s.p, sv.q2rows, sv.q2edges, sv.psi, sv.psi, s.N, st, &sv.launches);
+  if (rc != SG_OK) return sg_fail(ctx, rc, "the Q2 solver supports at most 16 modes and 32 couplings");
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  return SG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // entry points used by the C ABI
 // ---------------------------------------------------------------------------
@@ -1469,10 +1644,11 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
   rc = upload_and_tables(sys, o, sv, false);
   if (rc != SG_OK) return rc;
   sv.psi = static_cast<double2*>(psi_dev);
-  rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, !o->col_index, 0, nullptr)
-                                : run_forward<double>(sys, sv, cols_dev, !o->col_index, 0, nullptr);
+  if (s.q2) rc = run_q2(sys, sv, cols_dev, !o->col_index);
+  else rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, !o->col_index, 0, nullptr)
+                                     : run_forward<double>(sys, sv, cols_dev, !o->col_index, 0, nullptr);
   if (rc != SG_OK) return rc;
-  if (o->frame == SG_FRAME_INTERACTION) {
+  if (s.frame == SG_FRAME_INTERACTION) {
     k_frame<<<grid_for(s.D * s.S), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
     SG_CUDA_TRY(ctx, cudaGetLastError());
   }
@@ -1498,6 +1674,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (rc != SG_OK) return rc;
   Setup& s = sv.s;
   if (s.nqb < 1 || s.nqb > 12) return sg_fail(ctx, SG_E_UNSUPPORTED, "fidelity needs 1..12 qubit (non-coupler) modes");
+  if (s.q2 && grad) return sg_fail(ctx, SG_E_UNSUPPORTED, "gradients are computed with the RK4 solver only");
   for (int i = 0; i < s.nq; ++i)
     if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
       return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");
@@ -1573,10 +1750,11 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   cudaEvent_t ev0, ev1, ev2;
   cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&ev2);
   cudaEventRecord(ev0, st);
-  rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr)
-                                : run_forward<double>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr);
+  if (s.q2) rc = run_q2(sys, sv, cols_dev, false);
+  else rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr)
+                                     : run_forward<double>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr);
   if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
-  if (o->frame == SG_FRAME_INTERACTION)
+  if (s.frame == SG_FRAME_INTERACTION)
     k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
   CompArgs ca = comp_args(s);
   k_gather_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, sv.psi, Uc);
@@ -1585,7 +1763,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   for (int i = 0; i < s.nq; ++i) fa.qpos[i] = s.qpos[i];
   fa.Uc = Uc; fa.Tg = Tg; fa.lab = lab_dev; fa.F = Fd; fa.bar = grad ? barc : nullptr; fa.M = Mbuf;
   fa.T = s.T;
-  fa.frame = o->frame;
+  fa.frame = s.frame;
   k_fidelity<<<1, kT, 0, st>>>(fa);
   sv.launches += 3;
   SG_CUDA_TRY(ctx, cudaGetLastError());
@@ -1627,7 +1805,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     SG_CUDA_TRY(ctx, cudaMemsetAsync(pbar, 0, n * sizeof(double2), st));
     // co-state of the lab-frame columns, its frame-phase energy term, pull back to the frame
     k_scatter_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, barc, pbar);
-    if (o->frame == SG_FRAME_INTERACTION) {
+    if (s.frame == SG_FRAME_INTERACTION) {
       fa.ebar_frame = ebar_frame;
       k_frame_ebar<<<1, kT, 0, st>>>(fa);
       k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, +1.0), pbar);
@@ -1753,6 +1931,7 @@ static sg_status noalloc_run(sg_system* sys, const sg_evolve_opts* o, double2* p
   Solve sv;
   sg_status rc = build_setup(sys, o, sv.s);
   if (rc != SG_OK) return rc;
+  if (sv.s.q2) return sg_fail(ctx, SG_E_UNSUPPORTED, "sg_evolve_noalloc runs the RK4 solver only");
   Setup& s = sv.s;
   if (o->col_index)
     for (int c = 0; c < s.S; ++c)

@@ -607,6 +607,120 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   for (int i = threadIdx.x; i < oa.ne; i += blockDim.x) gjb[i] += (double)A.jb[i];
 }
 
+// ---------------------------------------------------------------------------
+// second-order Suzuki-Trotter (Sec. 2.3, App. A): products of local unitaries
+// ---------------------------------------------------------------------------
+// Factor kinds: 0 = L (x) R of two modes' 1-body unitaries (row offsets offL, offR),
+// 1 = one mode's 1-body unitary (offA), 2 = a coupling's d^2 x d^2 unitary (dense).
+constexpr int kMaxQ2F = 40;
+struct Q2Factor {
+  Phase P;
+  int kind;
+  int mat;                        // kind 2: index of the d^4 matrix in the edge table
+};
+struct Q2Args {
+  int nf0;                        // 1-body factors (applied first with the initial row,
+                                  // and at the end of every step)
+  int nfe;                        // coupling factors per step
+  Q2Factor f[kMaxQ2F];            // [0, nf0): 1-body; [nf0, nf0 + nfe): couplings in order
+};
+
+// o[x][z] = sum_{a,c} G[(x d + z), (a d + c)] y[a][c] over one block (digits ka, kb).
+template <int DL, typename C>
+__device__ __forceinline__ void block_dense(const C* __restrict__ G, const C* __restrict__ ys, C* __restrict__ ks,
+                                            int pb, int psa, int psb) {
+  C y[DL][DL];
+#pragma unroll
+  for (int a = 0; a < DL; ++a)
+#pragma unroll
+    for (int c = 0; c < DL; ++c) y[a][c] = ys[pb + a * psa + c * psb];
+#pragma unroll
+  for (int x = 0; x < DL; ++x)
+#pragma unroll
+    for (int z = 0; z < DL; ++z) {
+      const C* g = G + (x * DL + z) * DL * DL;
+      C acc = cmk<C>(0.0, 0.0);
+#pragma unroll
+      for (int a = 0; a < DL; ++a)
+#pragma unroll
+        for (int c = 0; c < DL; ++c) acc = cfma(__ldg(g + a * DL + c), y[a][c], acc);
+      ks[pb + x * psa + z * psb] = acc;
+    }
+}
+
+template <int DL, typename C>
+__device__ __forceinline__ void q2_apply(const Q2Factor& F, const OcArgs& oa, const C* __restrict__ M,
+                                         const C* __restrict__ edges, const C* __restrict__ ys, C* __restrict__ ks) {
+  const Phase& P = F.P;
+  for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
+    const int c = b / oa.nbc;
+    const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
+    if (F.kind == 2) block_dense<DL>(edges + (size_t)F.mat * DL * DL * DL * DL, ys, ks, pb, P.psa, P.psb);
+    else phase_block<DL, false>(P, M, ys, ks, pb, true);
+  }
+  __syncthreads();
+}
+
+// N steps of Q2 for the CTA's columns, lab frame.  rows: (N + 1) x nq x d^2 1-body
+// unitaries (row N = the first half step, row n = the last half step of step n merged
+// with the first of step n + 1); edges: per coupling the half-step and the full-step
+// (middle) unitary.  Per step: couplings 0 .. ne-2 (half), ne-1 (full), ne-2 .. 0
+// (half), then the 1-body row n.
+template <typename R, int DL>
+__global__ void __launch_bounds__(kST, 1)
+k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__ rows,
+        const typename CT<R>::T* __restrict__ edges, const double2* __restrict__ psi_api,
+        double2* __restrict__ psi_out, int N, int rowlen) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char sm[];
+  C* ys = reinterpret_cast<C*>(sm + oa.f_ys);
+  C* ks = reinterpret_cast<C*>(sm + oa.f_ks);
+  C* const M0 = reinterpret_cast<C*>(sm + oa.f_M);
+  C* const M1 = M0 + oa.rowA;
+  const int cta = blockIdx.x;
+  for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
+    const int c = e / oa.D, t = e - c * oa.D;
+    const int col = cta * oa.Sc + c;
+    const double2 v = col < oa.S ? psi_api[(size_t)t * oa.S + col] : make_double2(0.0, 0.0);
+    ys[oc_pos<DL>(oa, e)] = to_c(v, R(0));
+  }
+  issue_rows<C>(rows, rowlen, N, M0, threadIdx.x, blockDim.x);       // first half step
+  if (N > 0) issue_rows<C>(rows, rowlen, 0, M1, threadIdx.x, blockDim.x);
+  cp_wait_all();
+  __syncthreads();
+  for (int q = 0; q < qa.nf0; ++q) {
+    q2_apply<DL>(qa.f[q], oa, M0, edges, ys, ks);
+    C* t = ys; ys = ks; ks = t;
+  }
+  int buf = 1;
+  for (int n = 0; n < N; ++n) {
+    C* const Mc = buf ? M1 : M0;
+    if (n + 1 < N) issue_rows<C>(rows, rowlen, n + 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
+    for (int q = 0; q < 2 * qa.nfe - 1; ++q) {
+      const int e = q < qa.nfe ? q : 2 * qa.nfe - 2 - q;             // palindrome over couplings
+      Q2Factor F = qa.f[qa.nf0 + e];
+      if (q == qa.nfe - 1) F.mat += 1;                                  // the middle: full step
+      q2_apply<DL>(F, oa, Mc, edges, ys, ks);
+      C* t = ys; ys = ks; ks = t;
+    }
+    for (int q = 0; q < qa.nf0; ++q) {
+      q2_apply<DL>(qa.f[q], oa, Mc, edges, ys, ks);
+      C* t = ys; ys = ks; ks = t;
+    }
+    cp_wait_all();
+    __syncthreads();
+    buf ^= 1;
+  }
+  for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
+    const int c = e / oa.D, t = e - c * oa.D;
+    const int col = cta * oa.Sc + c;
+    if (col < oa.S) {
+      const C v = ys[oc_pos<DL>(oa, e)];
+      psi_out[(size_t)t * oa.S + col] = make_double2((double)v.x, (double)v.y);
+    }
+  }
+}
+
 // API layout [D][S] -> state image [cta][Sc][D]
 __global__ void k_oc_image(OcArgs oa, const double2* __restrict__ api, double2* __restrict__ img) {
   const long long total = (long long)oa.ncta * oa.ent;
@@ -894,6 +1008,70 @@ int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* seg
                    void* colow, cudaStream_t st) {
   OC_DISPATCH(adj_t, oc, tb, segY, pbar_img, n0, n1, dt, xa, nst, gF_cta, acc_cta, err, colow, st);
 }
+
+namespace {
+
+template <typename R, int DL>
+int q2_t(const OnchipPlan* oc, const Q2Args& qa, const void* rows, const void* edges, const double2* psi_in,
+         double2* psi_out, int N, int rowlen, cudaStream_t st) {
+  typedef typename CT<R>::T C;
+  smem_limit_once<k_oc_q2<R, DL>>();
+  k_oc_q2<R, DL><<<oc->oa.ncta, kST, oc->sm_fwd, st>>>(oc->h->pass[0], oc->oa, qa, (const C*)rows,
+                                                      (const C*)edges, psi_in, psi_out, N, rowlen);
+  return 1;
+}
+
+}  // namespace
+
+sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
+                            const double2* psi_in, double2* psi_out, int N, cudaStream_t st, int* launches) {
+  const SlabPass& sp = oc->h->pass[0];
+  const int DL = oc->h->DL;
+  if (p.nq > 2 * 8 || p.ne > kMaxQ2F - 8) return SG_E_UNSUPPORTED;
+  if (p.nq * DL * DL > oc->oa.rowA) return SG_E_UNSUPPORTED;        // 1-body row must fit the row buffer
+  Q2Args qa{};
+  // 1-body factors: modes in pairs (Kronecker L (x) R), an odd last mode alone
+  for (int i = 0; i < p.nq; i += 2) {
+    Q2Factor& F = qa.f[qa.nf0++];
+    if (i + 1 < p.nq) {
+      F.P = make_phase(sp, DL, i, i + 1);
+      F.P.offL = i * DL * DL;
+      F.P.offR = (i + 1) * DL * DL;
+      F.kind = 0;
+    } else {
+      F.P = make_phase(sp, DL, i, i - 1);
+      F.P.offA = i * DL * DL;
+      F.kind = 1;
+    }
+  }
+  for (int e = 0; e < p.ne; ++e) {
+    Q2Factor& F = qa.f[qa.nf0 + qa.nfe++];
+    F.P = make_phase(sp, DL, p.e_a[e], p.e_b[e]);
+    F.kind = 2;
+    F.mat = 2 * e;
+  }
+  const int rowlen = p.nq * DL * DL;
+  int n = 0;
+  if (oc->mixed) {
+    switch (DL) {
+      case 2: n = q2_t<float, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      case 3: n = q2_t<float, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      case 4: n = q2_t<float, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      default: n = q2_t<float, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+    }
+  } else {
+    switch (DL) {
+      case 2: n = q2_t<double, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      case 3: n = q2_t<double, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      case 4: n = q2_t<double, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      default: n = q2_t<double, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+    }
+  }
+  if (launches) *launches += n;
+  return SG_OK;
+}
+
+int onchip_dl(const OnchipPlan* oc) { return oc->h->DL; }
 
 void onchip_to_image(const OnchipPlan* oc, const double2* api, double2* img, cudaStream_t st) {
   k_oc_image<<<grid_of(onchip_state_elems(oc)), 256, 0, st>>>(oc->oa, api, img);

@@ -67,3 +67,12 @@ bool onchip_mixed(const OnchipPlan* oc);
 // acc += sum over CTAs (in CTA order) of the per-CTA accumulators.
 void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc_cta, long long nst, int K,
                    int n1, int ne, GradAcc acc, cudaStream_t st);
+
+// Second-order Suzuki-Trotter evolution (Sec. 2.3, App. A) of N steps, lab frame, from
+// psi_in to psi_out (API layout, may alias).  rows: (N + 1) x nq x d^2 1-body unitaries
+// of the stage precision (row N = the first half step; row n = the last half step of
+// step n followed by the first of step n + 1); edges: per coupling its half-step and
+// full-step d^2 x d^2 unitaries.  SG_E_UNSUPPORTED beyond 16 modes or 32 couplings.
+sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
+                            const double2* psi_in, double2* psi_out, int N, cudaStream_t st, int* launches);
+int onchip_dl(const OnchipPlan* oc);

@@ -367,6 +367,44 @@ __device__ __forceinline__ void xd_slot(const Phase& P, int type, const C* __res
   }
 }
 
+// Host: a phase over tile digits (ka, kb) of a single-pass plan with no terms set
+// (offsets -1): the other digits in the bank-conflict-free mapping order (the lowest
+// even-exponent digit, the lowest odd-exponent one, then the rest) and the padded
+// shared-memory strides.  The tiled plans build their phases the same way.
+inline Phase make_phase(const SlabPass& sp, int DL, int ka, int kb) {
+  Phase P{};
+  P.ka = ka;
+  P.kb = kb;
+  P.offL = P.offR = P.offA = P.offB = -1;
+  P.ge = P.gA = P.gB = -1;
+  P.par = 0;
+  P.allpar = 0;
+  int ord[SG_MAXQ], no = 0;
+  const int ng = sp.ng;
+  for (int pass = 0; pass < 3; ++pass)
+    for (int k = ng - 1; k >= 0; --k) {
+      if (k == ka || k == kb) continue;
+      bool used = false;
+      for (int j = 0; j < no; ++j) used = used || ord[j] == k;
+      if (used) continue;
+      const int ex = ng - 1 - k;
+      if (pass == 0 && ex % 2 != 0) continue;
+      if (pass == 1 && ex % 2 != 1) continue;
+      ord[no++] = k;
+      if (pass < 2) break;
+    }
+  const bool pw2 = DL == 2 || DL == 4;
+  auto pad = [&](int o) { return pw2 ? o + (o >> 4) + (o >> 8) : o; };
+  P.no = no;
+  for (int j = 0; j < no; ++j) {
+    P.ost[j] = sp.tsh[ord[j]];
+    P.pst[j] = pad(P.ost[j]);
+  }
+  P.psa = pad(sp.tsh[ka]);
+  P.psb = pad(sp.tsh[kb]);
+  return P;
+}
+
 struct PermArgs {
   int nq, S;
   long long D;

@@ -1,0 +1,82 @@
+"""GPU parity of the second-order Suzuki-Trotter solver (Sec. 2.3, App. A) against
+the oracle's Q2: lab-frame states and fidelities, FP64 within 1e-10, FP32 factors
+and state within 1e-5 on short evolutions; unsupported requests are rejected."""
+import numpy as np
+import pytest
+
+from oracle.evolve import initial_columns, fidelities
+from oracle.system import OracleSystem
+from oracle.trotter import q2_evolve
+from paper_2406_18155_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _system(sgctx, wl):
+    from paper_2406_18155_gb300.api import System
+    s = System.from_workload(sgctx, wl)
+    s.prepare()
+    return s
+
+
+def _short(wl, T=0.3):
+    wl["T"] = T
+    for d in wl["drives"]:
+        d["length"] = T
+        if d.get("env") == "gaussian":
+            d["sigma"], d["t0"] = T / 4, T / 2
+    return wl
+
+
+CASES = {
+    "transmon_pair": lambda: _short(W.transmon_pair(seed=2)),                  # 2 modes: one pair factor
+    "chain3_l3": lambda: _short(W.fluxonium_chain(seed=3, nq=3, levels=3, nseg=3)),   # odd: last mode alone
+    "ring4_l3": lambda: _short(W.fluxonium_chain(seed=4, nq=4, levels=3, nseg=3, ring=True)),
+    "pair_cr_l5": lambda: _short(W.fluxonium_pair_cr(seed=5, nseg=4)),
+    "ftf_l4": lambda: _short(W.coupler_scheme(seed=6, kind="ftf", nseg=3)),
+    "multipath_l4": lambda: _short(W.fluxonium_pair_multipath(seed=7, levels=4, nseg=3)),
+    "local_ops_l3": lambda: _short(W.local_op_pair(seed=8, levels=3, nseg=3)),
+}
+
+
+@pytest.fixture
+def default_path(monkeypatch):
+    monkeypatch.delenv("SG_PATH", raising=False)
+    monkeypatch.delenv("SG_SLAB_TMAX", raising=False)
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_q2_matches_oracle(sgctx, default_path, name):
+    wl = CASES[name]()
+    s = _system(sgctx, wl)
+    so = OracleSystem(dict(wl, frame="lab"))
+    ref = q2_evolve(so, initial_columns(so, wl["col_index"]))
+    psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver="q2").cpu().numpy()
+    assert np.max(np.abs(psi - ref)) < 1e-10
+    Fa_r, Fs_r, Uc_r = fidelities(so, ref)
+    Fa, Fs, Uc = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver="q2")
+    assert abs(Fs - Fs_r) < 1e-10 and np.max(np.abs(Uc - Uc_r)) < 1e-10
+    assert (np.isnan(Fa) and np.isnan(Fa_r)) or abs(Fa - Fa_r) < 1e-10
+    psi32 = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"], solver="q2").cpu().numpy()
+    assert np.max(np.abs(psi32 - ref)) < 1e-5
+
+
+def test_q2_rejects_what_it_does_not_run(sgctx, default_path):
+    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
+    wl = CASES["transmon_pair"]()
+    s = _system(sgctx, wl)
+    with pytest.raises(SGError) as e:                       # gradients: RK4 only
+        from paper_2406_18155_gb300.api import evolve_opts
+        import ctypes as C
+        from paper_2406_18155_gb300.capi import lib
+        o, keep = evolve_opts(wl["T"], wl["dt"], "fp64", "interaction", wl["col_index"], solver="q2")
+        tg = np.ascontiguousarray(np.asarray(wl["target"], complex).view(np.float64).reshape(-1))
+        F, gp, gh = np.zeros(2), np.zeros(8), np.zeros(16)
+        p = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        s._chk(lib().sg_fidelity_grad(s.h, C.byref(o), p(tg), 0, p(F), p(gp), p(gh), 0))
+    assert e.value.code == SG_E_UNSUPPORTED
+    mixed_levels = W.coupler_scheme(seed=9, kind="ftf", nseg=3, levels=(4, 3, 4))
+    s2 = _system(sgctx, _short(mixed_levels))
+    with pytest.raises(SGError) as e:                       # unequal level counts: not on-chip
+        s2.evolve(0.3, 0.01, precision="fp64", col_index=mixed_levels["col_index"], solver="q2")
+    assert e.value.code == SG_E_UNSUPPORTED
