@@ -285,6 +285,8 @@ def run_ours(args):
         # ---- the plain FP64 GPU path on a bounded number of steps
         if args.fp64_steps > 0:
             out["fp64_vs_mixed"] = fp64_comparison(sysm, wl, args.fp64_steps, stream)
+        if args.q2 and D <= 4096:
+            out["q2_vs_rk4"] = q2_comparison(sysm, wl, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
     if rank == 0 and args.serving > 0:
@@ -455,6 +457,34 @@ def fp64_comparison(sysm, wl, nsteps, stream):
     return out
 
 
+def q2_comparison(sysm, wl, stream):
+    """The paper's second-order Suzuki-Trotter solver against RK4 on the whole
+    workload (single-tile systems only): forward col-steps/s of each in FP64 and
+    mixed precision (device time), and the fidelity difference at the workload's dt."""
+    import torch
+    out = {}
+    for solver in ("rk4", "q2"):
+        for prec in ("fp64", "mixed"):
+            kw = dict(precision=prec, col_index=wl["col_index"], solver=solver)
+            sysm.evolve(wl["T"], wl["dt"], **kw)                          # warm
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sysm.evolve(wl["T"], wl["dt"], **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            out[f"{solver}_{prec}_forward_col_steps_per_s"] = len(wl["col_index"]) * round(wl["T"] / wl["dt"]) / t
+    F = {sv: sysm.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver=sv)
+         for sv in ("rk4", "q2")}
+    k = 0 if wl["fid_kind"] == "avg" else 1
+    out["fidelity_rk4_fp64"] = float(F["rk4"][k])
+    out["fidelity_q2_fp64"] = float(F["q2"][k])
+    out["abs_dF_q2_vs_rk4"] = abs(float(F["q2"][k]) - float(F["rk4"][k]))
+    return out
+
+
 def cpu_baseline(wl, nsteps):
     """The FP64 oracle as it stands on this host: matrix-free RK4 (per-mode tensor
     contraction) of one column for nsteps steps.  numpy.einsum without path
@@ -519,6 +549,8 @@ def main():
     ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
     ap.add_argument("--t-ns", type=float, default=0.0, help="shorten the workload to T ns (profiling)")
+    ap.add_argument("--q2", action="store_true",
+                    help="also time the second-order Suzuki-Trotter solver against RK4 (D <= 4096)")
     ap.add_argument("--grad", default="config", choices=["config", "pulse", "all"],
                     help="gradient set: the configuration's (ring: pulse segments), pulse only, or all")
     ap.add_argument("--no-full-gradient", dest="full_gradient", action="store_false",

@@ -1168,7 +1168,7 @@ struct Solve {
     onchip_plan_destroy(oc);
   }
   // the on-chip kernels evolve this solve (gradient solves need the adjoint to fit too)
-  bool onchip(bool grad) const { return oc && (!grad || onchip_adjoint_ok(oc)); }
+  bool onchip(bool grad) const { return oc && (grad ? onchip_adjoint_ok(oc) : onchip_forward_ok(oc)); }
 };
 
 // Kernel family, a test knob: SG_PATH=gather forces the generic gather kernels,

@@ -163,6 +163,8 @@ struct OcArgs {
   int pblo_g;            // adjoint, mixed: co-state low words in global memory (shared memory short)
   // forward shared-memory byte offsets
   int f_ys, f_ks, f_ps, f_dl, f_M;
+  // Q2 (products of local unitaries) shared-memory byte offsets: state, scratch, 1-body rows
+  int q_ys, q_ks, q_M, q_G;
   // adjoint shared-memory byte offsets
   int a_xs, a_ks, a_ys, a_yn, a_db, a_pb, a_M, a_cf, a_ph, a_obD, a_obL, a_obR, a_ebB, a_ebL, a_ebR,
       a_jb, a_gs, a_sq;
@@ -634,28 +636,31 @@ __device__ __forceinline__ void block_dense(const C* __restrict__ G, const C* __
   for (int a = 0; a < DL; ++a)
 #pragma unroll
     for (int c = 0; c < DL; ++c) y[a][c] = ys[pb + a * psa + c * psb];
+  // one output per iteration (a runtime loop keeps the d^4 code small)
+#pragma unroll 1
+  for (int xz = 0; xz < DL * DL; ++xz) {
+    const C* g = G + xz * DL * DL;
+    C acc0 = cmk<C>(0.0, 0.0), acc1 = cmk<C>(0.0, 0.0);       // two chains for latency
 #pragma unroll
-  for (int x = 0; x < DL; ++x)
+    for (int a = 0; a < DL; ++a)
 #pragma unroll
-    for (int z = 0; z < DL; ++z) {
-      const C* g = G + (x * DL + z) * DL * DL;
-      C acc = cmk<C>(0.0, 0.0);
-#pragma unroll
-      for (int a = 0; a < DL; ++a)
-#pragma unroll
-        for (int c = 0; c < DL; ++c) acc = cfma(__ldg(g + a * DL + c), y[a][c], acc);
-      ks[pb + x * psa + z * psb] = acc;
-    }
+      for (int c = 0; c < DL; ++c) {
+        if ((a * DL + c) & 1) acc1 = cfma(g[a * DL + c], y[a][c], acc1);
+        else acc0 = cfma(g[a * DL + c], y[a][c], acc0);
+      }
+    const int x = xz / DL, z = xz - x * DL;
+    ks[pb + x * psa + z * psb] = cmk<C>(acc0.x + acc1.x, acc0.y + acc1.y);
+  }
 }
 
 template <int DL, typename C>
-__device__ __forceinline__ void q2_apply(const Q2Factor& F, const OcArgs& oa, const C* __restrict__ M,
+__device__ __forceinline__ void q2_apply(const Q2Factor& F, int mat, const OcArgs& oa, const C* __restrict__ M,
                                          const C* __restrict__ edges, const C* __restrict__ ys, C* __restrict__ ks) {
   const Phase& P = F.P;
   for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
     const int c = b / oa.nbc;
     const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
-    if (F.kind == 2) block_dense<DL>(edges + (size_t)F.mat * DL * DL * DL * DL, ys, ks, pb, P.psa, P.psb);
+    if (F.kind == 2) block_dense<DL>(edges + (size_t)mat * DL * DL * DL * DL, ys, ks, pb, P.psa, P.psb);
     else phase_block<DL, false>(P, M, ys, ks, pb, true);
   }
   __syncthreads();
@@ -670,14 +675,21 @@ template <typename R, int DL>
 __global__ void __launch_bounds__(kST, 1)
 k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__ rows,
         const typename CT<R>::T* __restrict__ edges, const double2* __restrict__ psi_api,
-        double2* __restrict__ psi_out, int N, int rowlen) {
+        double2* __restrict__ psi_out, int N, int rowlen, int nedge) {
   typedef typename CT<R>::T C;
   extern __shared__ __align__(16) unsigned char sm[];
-  C* ys = reinterpret_cast<C*>(sm + oa.f_ys);
-  C* ks = reinterpret_cast<C*>(sm + oa.f_ks);
-  C* const M0 = reinterpret_cast<C*>(sm + oa.f_M);
+  C* ys = reinterpret_cast<C*>(sm + oa.q_ys);
+  C* ks = reinterpret_cast<C*>(sm + oa.q_ks);
+  C* const M0 = reinterpret_cast<C*>(sm + oa.q_M);
   C* const M1 = M0 + oa.rowA;
   const int cta = blockIdx.x;
+  // the coupling unitaries (constant for the solve) in shared memory when they fit
+  const C* G = edges;
+  if (nedge > 0) {
+    C* Gs = reinterpret_cast<C*>(sm + oa.q_G);
+    for (int i = threadIdx.x; i < nedge; i += blockDim.x) Gs[i] = edges[i];
+    G = Gs;
+  }
   for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
     const int c = e / oa.D, t = e - c * oa.D;
     const int col = cta * oa.Sc + c;
@@ -689,7 +701,7 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
   cp_wait_all();
   __syncthreads();
   for (int q = 0; q < qa.nf0; ++q) {
-    q2_apply<DL>(qa.f[q], oa, M0, edges, ys, ks);
+    q2_apply<DL>(qa.f[q], 0, oa, M0, G, ys, ks);
     C* t = ys; ys = ks; ks = t;
   }
   int buf = 1;
@@ -698,13 +710,12 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
     if (n + 1 < N) issue_rows<C>(rows, rowlen, n + 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
     for (int q = 0; q < 2 * qa.nfe - 1; ++q) {
       const int e = q < qa.nfe ? q : 2 * qa.nfe - 2 - q;             // palindrome over couplings
-      Q2Factor F = qa.f[qa.nf0 + e];
-      if (q == qa.nfe - 1) F.mat += 1;                                  // the middle: full step
-      q2_apply<DL>(F, oa, Mc, edges, ys, ks);
+      const Q2Factor& F = qa.f[qa.nf0 + e];
+      q2_apply<DL>(F, F.mat + (q == qa.nfe - 1 ? 1 : 0), oa, Mc, G, ys, ks);   // middle: full step
       C* t = ys; ys = ks; ks = t;
     }
     for (int q = 0; q < qa.nf0; ++q) {
-      q2_apply<DL>(qa.f[q], oa, Mc, edges, ys, ks);
+      q2_apply<DL>(qa.f[q], 0, oa, Mc, G, ys, ks);
       C* t = ys; ys = ks; ks = t;
     }
     cp_wait_all();
@@ -784,8 +795,8 @@ int grid_of(long long n) { return (int)std::max<long long>(1, std::min<long long
 struct OnchipPlan {
   SlabPlanHost* h = nullptr;
   OcArgs oa{};
-  bool mixed = false, adj_ok = false;
-  size_t sm_fwd = 0, sm_adj = 0;
+  bool mixed = false, adj_ok = false, fwd_ok = false;
+  size_t sm_fwd = 0, sm_adj = 0, limit = 0;
 };
 
 namespace {
@@ -813,6 +824,11 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   a.f_M = take(2 * (size_t)a.rowA * cs);
   fwd = o;
   o = 0;
+  a.q_ys = take(a.CSP * cs);
+  a.q_ks = take(a.CSP * cs);
+  a.q_M = take(2 * (size_t)a.rowA * cs);
+  a.q_G = (int)o;                 // coupling unitaries follow (sized per solve)
+  o = 0;
   a.a_xs = take(a.CSP * cs);
   a.a_ks = take(a.CSP * cs);
   a.a_ys = take(a.CSP * cs);
@@ -839,7 +855,7 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
 
 OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cudaStream_t st) {
   if (p.nq < 2 || p.nq > SG_MAXQ) return nullptr;
-  SlabPlanHost* h = slab_plan_create(p, mixed, st);
+  SlabPlanHost* h = slab_plan_create(p, mixed, st, true);
   if (!h) return nullptr;
   const int DL = h->DL;
   bool ok = h->np == 1 && DL >= 2 && DL <= 5 && p.D <= kTmax;
@@ -884,15 +900,25 @@ OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cuda
     if (best_adj) break;
   }
   if (!best_adj) a.pblo_g = 0;
-  const int sc = best_adj ? best_adj : best_fwd;
-  if (!sc) { onchip_plan_destroy(oc); return nullptr; }
+  int sc = best_adj ? best_adj : best_fwd;
+  if (!sc) {
+    // neither RK4 kernel fits: one column per CTA may still fit the Q2 kernel (state,
+    // scratch and the 1-body rows only; the coupling unitaries go to shared memory only
+    // if they fit too)
+    a.Sc = 1;
+    layout(a, DL, cs, fwd, adj);
+    if ((size_t)a.q_G > limit) { onchip_plan_destroy(oc); return nullptr; }
+    sc = 1;
+  }
   // balance the columns over the CTAs
   a.ncta = (p.S + sc - 1) / sc;
   a.Sc = (p.S + a.ncta - 1) / a.ncta;
   layout(a, DL, cs, fwd, adj);
   oc->adj_ok = adj <= limit;
+  oc->fwd_ok = fwd <= limit;
   oc->sm_fwd = fwd;
   oc->sm_adj = adj;
+  oc->limit = limit;
   // Adjoint warp split from the complex multiply-adds per stage: a phase block costs
   // 2 d^3 per edge and d^3 per 1-body term, a slot's cross-density d^3 (1-body) or
   // 2 d^3 (edge side); parity-odd operators halve both.  SG_OC_PW overrides (1..7).
@@ -924,6 +950,7 @@ void onchip_plan_destroy(OnchipPlan* oc) {
 }
 
 bool onchip_adjoint_ok(const OnchipPlan* oc) { return oc && oc->adj_ok; }
+bool onchip_forward_ok(const OnchipPlan* oc) { return oc && oc->fwd_ok; }
 bool onchip_colow_global(const OnchipPlan* oc) { return oc->oa.pblo_g != 0; }
 bool onchip_mixed(const OnchipPlan* oc) { return oc->mixed; }
 long long onchip_state_elems(const OnchipPlan* oc) { return (long long)oc->oa.ncta * oc->oa.ent; }
@@ -1013,11 +1040,16 @@ namespace {
 
 template <typename R, int DL>
 int q2_t(const OnchipPlan* oc, const Q2Args& qa, const void* rows, const void* edges, const double2* psi_in,
-         double2* psi_out, int N, int rowlen, cudaStream_t st) {
+         double2* psi_out, int N, int rowlen, int ne, cudaStream_t st) {
   typedef typename CT<R>::T C;
   smem_limit_once<k_oc_q2<R, DL>>();
-  k_oc_q2<R, DL><<<oc->oa.ncta, kST, oc->sm_fwd, st>>>(oc->h->pass[0], oc->oa, qa, (const C*)rows,
-                                                      (const C*)edges, psi_in, psi_out, N, rowlen);
+  // coupling unitaries in shared memory when they fit, else read from global memory
+  const int nedge = 2 * std::max(0, ne) * DL * DL * DL * DL;
+  const size_t gbytes = (size_t)nedge * sizeof(C);
+  const bool gsm = oc->oa.q_G + gbytes <= oc->limit;
+  const size_t smem = oc->oa.q_G + (gsm ? gbytes : 0);
+  k_oc_q2<R, DL><<<oc->oa.ncta, kST, smem, st>>>(oc->h->pass[0], oc->oa, qa, (const C*)rows, (const C*)edges,
+                                                 psi_in, psi_out, N, rowlen, gsm ? nedge : 0);
   return 1;
 }
 
@@ -1054,17 +1086,17 @@ sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* ro
   int n = 0;
   if (oc->mixed) {
     switch (DL) {
-      case 2: n = q2_t<float, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
-      case 3: n = q2_t<float, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
-      case 4: n = q2_t<float, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
-      default: n = q2_t<float, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      case 2: n = q2_t<float, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      case 3: n = q2_t<float, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      case 4: n = q2_t<float, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      default: n = q2_t<float, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
     }
   } else {
     switch (DL) {
-      case 2: n = q2_t<double, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
-      case 3: n = q2_t<double, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
-      case 4: n = q2_t<double, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
-      default: n = q2_t<double, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, st); break;
+      case 2: n = q2_t<double, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      case 3: n = q2_t<double, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      case 4: n = q2_t<double, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      default: n = q2_t<double, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
     }
   }
   if (launches) *launches += n;

@@ -14,8 +14,9 @@
 struct OnchipPlan;   // opaque
 
 // nullptr unless the plan is a single tile (one pass of the tiled kernels), every
-// mode has the same level count (2..5) and at least the forward state fits in
-// shared memory.  K drives and sumd = sum of level counts size the adjoint's
+// mode has the same level count (2..5) and at least one column fits in shared memory
+// for the Q2 kernel (onchip_forward_ok / onchip_adjoint_ok tell whether the RK4
+// kernels fit too).  K drives and sumd = sum of level counts size the adjoint's
 // per-stage buffers.
 OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cudaStream_t st);
 void onchip_plan_destroy(OnchipPlan* oc);
@@ -61,6 +62,8 @@ int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* seg
                    int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
                    void* colow, cudaStream_t st);
 bool onchip_colow_global(const OnchipPlan* oc);
+// The RK4 forward kernel fits (a plan may hold only the Q2 layout).
+bool onchip_forward_ok(const OnchipPlan* oc);
 // Element-wise FP64 -> FP32 copy (tables for the mixed-precision adjoint).
 void onchip_to_f32(const double* src, float* dst, long long n, cudaStream_t st);
 bool onchip_mixed(const OnchipPlan* oc);

@@ -245,7 +245,7 @@ __global__ void k_perm(PermArgs a, const double2* __restrict__ src, double2* __r
 }  // namespace
 
 
-SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
+SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool metadata_only) {
   const int nq = p.nq;
   const int DL = p.dims[0];
   for (int i = 0; i < nq; ++i) if (p.dims[i] != DL) return nullptr;
@@ -479,7 +479,7 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st) {
     sp.off = h->off_dev[g];
     h->sm_fwd[g] = 2 * spad(sp.T) * csz + p.row * csz;
     h->sm_adj[g] = std::max(3 * spad(sp.T) * csz + p.row * csz, (size_t)kMaxX * DL * DL * sizeof(double2));
-    if (h->sm_adj[g] > 200 * 1024) { slab_plan_destroy(h); return nullptr; }
+    if (h->sm_adj[g] > 200 * 1024 && !metadata_only) { slab_plan_destroy(h); return nullptr; }
   }
   h->allpar = true;
   for (int g = 0; g < np; ++g)

@@ -13,7 +13,9 @@ struct SlabPlanHost;   // opaque
 // Returns nullptr when the plan is not handled by the slab kernels (non-uniform
 // level counts, more than 4 passes, too many terms per pass); the caller then
 // uses the gather kernels.
-SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st);
+// metadata_only: the plan is only read for its tiles and phases (the on-chip kernels),
+// so the tiled kernels' own shared-memory limit does not apply.
+SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool metadata_only = false);
 void slab_plan_destroy(SlabPlanHost* sp);
 int slab_passes(const SlabPlanHost* sp);
 
