@@ -83,3 +83,68 @@ def q2_evolve_and_fidelity(wl):
     psi = q2_evolve(sys, initial_columns(sys, wl["col_index"]))
     Favg, Fst, Uc = fidelities(sys, psi)
     return {"psi_lab": psi, "F_avg": Favg, "F_state": Fst, "Uc": Uc, "sys": sys}
+
+
+def q2_pulse_gradient(wl, kind=None):
+    """F and dF/d(pulse parameters) of the Q2 evolution, by its discrete adjoint.
+
+    With psi_m = X_m psi_{m-1} over the factors X_m of every step in order and the
+    co-state psibar = dF/dRe psi + i dF/dIm psi of the final lab-frame columns,
+    psibar_{m-1} = X_m^dag psibar_m and dF/dtheta = sum_m Re <psibar_m, dX_m/dtheta psi_{m-1}>.
+    A 1-body factor is X = exp(A), A = -i (dt/2) H_i(t_n + dt/2), so
+    dX/df_k = L(A, -i (dt/2) O_k), the Frechet derivative of expm (scipy's
+    expm_frechet), for each drive k on mode i; f_k(t) = E_k(t) cos(omega t + phase)
+    carries the pulse parameters through the envelope (reading R8 for PWC).
+    Returns (F, gradient over the pulse parameters in sg_param order)."""
+    from scipy.linalg import expm_frechet
+    from .evolve import initial_columns, fidelity_and_costate
+    from .system import envelope, n_pulse_params, stage_time
+    sys = OracleSystem(dict(wl, frame="lab"))
+    kind = kind or wl["fid_kind"]
+    dt, N, S = sys.dt, sys.N, len(wl["col_index"])
+    psi = initial_columns(sys, wl["col_index"]).reshape(list(sys.dims) + [S])
+    _, two = local_terms(sys, 0)
+    G = [(a, b, expm(-1j * M * dt / 2)) for a, b, M in two]
+    tape = []                                   # (factor, mode/edge, state before, step)
+    for n in range(N):
+        one, _ = local_terms(sys, n)
+        A = [-1j * (dt / 2) * H for H in one]
+        seq = [("1", i, A[i]) for i in range(sys.nq)] + [("2", e, None) for e in range(len(G))]
+        for kind_f, idx, Ai in seq + seq[::-1]:
+            tape.append((kind_f, idx, Ai, psi.copy(), n))
+            if kind_f == "1":
+                psi = _apply_1body(psi, expm(Ai), idx)
+            else:
+                a, b, M = G[idx]
+                psi = _apply_2body(psi, M, a, b, sys.dims[a], sys.dims[b])
+    F, bar = fidelity_and_costate(sys, psi.reshape(sys.D, S), kind)
+    bar = bar.reshape(list(sys.dims) + [S])
+    gf = np.zeros((len(sys.drives), N))          # dF/df_k at the midpoint of step n
+    for kind_f, idx, Ai, before, n in reversed(tape):
+        if kind_f == "1":
+            X = expm(Ai)
+            for k, dr in enumerate(sys.drives):
+                if dr["mode"] != idx:
+                    continue
+                L = expm_frechet(Ai, -1j * (dt / 2) * sys.op(idx, dr["op"]), compute_expm=False)
+                gf[k, n] += np.real(np.vdot(bar, _apply_1body(before, L, idx)))
+            bar = _apply_1body(bar, X.conj().T, idx)
+        else:
+            a, b, M = G[idx]
+            bar = _apply_2body(bar, M.conj().T, a, b, sys.dims[a], sys.dims[b])
+    grad = []
+    for k, dr in enumerate(sys.drives):
+        g = np.zeros(n_pulse_params(dr))
+        for n in range(N):
+            t = stage_time(n, 1, dt)
+            _, dE = envelope(dr, n, 1, dt)
+            c = np.cos(sys.omega_d[k] * t + dr.get("phase", 0.0))
+            g += gf[k, n] * c * np.asarray(dE)
+        grad.extend(g)
+    return F, np.array(grad)
+
+
+def q2_fidelity(wl, kind=None):
+    """F of the Q2 evolution (for finite differences)."""
+    r = q2_evolve_and_fidelity(wl)
+    return r["F_avg"] if (kind or wl["fid_kind"]) == "avg" else r["F_state"]

@@ -59,3 +59,32 @@ def test_unitary_to_round_off():
     sys = OracleSystem(wl)
     U = q2_evolve(sys, initial_columns(sys, range(sys.D)))
     assert np.max(np.abs(U.conj().T @ U - np.eye(sys.D))) < 1e-12
+
+
+def test_q2_pulse_gradient_matches_central_differences():
+    import copy
+    from oracle.trotter import q2_pulse_gradient, q2_fidelity
+    for wl in (W.fluxonium_pair_multipath(seed=11, levels=3, nseg=3),
+               W.transmon_pair(seed=12)):
+        wl = _lab(wl, 0.2, 0.01)
+        if wl["modes"][0]["kind"] == "transmon":
+            wl["modes"] = [dict(m, levels=3) for m in wl["modes"]]
+            wl["col_index"] = W.comp_states([3, 3])
+        F, g = q2_pulse_gradient(wl)
+        assert abs(F - q2_fidelity(wl)) < 1e-14
+        fd = []
+        for k, dr in enumerate(wl["drives"]):
+            keys = [("amps", j) for j in range(len(dr["amps"]))] if dr["env"] == "pwc" else [("amp", None)]
+            for key, j in keys:
+                vals = []
+                for sgn in (1, -1):
+                    w2 = copy.deepcopy(wl)
+                    h = 1e-5 * max(1.0, abs(dr[key][j] if j is not None else dr[key]))
+                    if j is None:
+                        w2["drives"][k][key] += sgn * h
+                    else:
+                        w2["drives"][k][key][j] += sgn * h
+                    vals.append(q2_fidelity(w2))
+                fd.append((vals[0] - vals[1]) / (2 * h))
+        fd = np.array(fd)
+        assert np.max(np.abs(g - fd)) <= 1e-6 * max(1e-3, np.max(np.abs(fd))), (g, fd)
