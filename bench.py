@@ -476,6 +476,34 @@ def q2_comparison(sysm, wl, stream):
             torch.cuda.synchronize()
             t = e0.elapsed_time(e1) / 1e3
             out[f"{solver}_{prec}_forward_col_steps_per_s"] = len(wl["col_index"]) * round(wl["T"] / wl["dt"]) / t
+    # pulse-parameter gradient solves (fidelity + adjoint), each solver in the frame
+    # it runs in; a solve the plan cannot hold is reported as null
+    from paper_2406_18155_gb300.capi import SGError
+    gq = {}
+    for solver in ("rk4", "q2"):
+        for prec in ("fp64", "mixed"):
+            kw = dict(kind=wl["fid_kind"], precision=prec, ham=False, solver=solver,
+                      frame="lab" if solver == "q2" else wl.get("frame", "interaction"))
+            key = f"{solver}_{prec}_pulse_gradient_col_steps_per_s"
+            try:
+                sysm.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], **kw)   # warm
+            except SGError as e:
+                out[key] = None
+                out[f"{solver}_{prec}_pulse_gradient_unsupported"] = str(e)[:120]
+                continue
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, gp, _ = sysm.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], **kw)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[key] = len(wl["col_index"]) * round(wl["T"] / wl["dt"]) / (e0.elapsed_time(e1) / 1e3)
+            if prec == "mixed":
+                gq[solver] = gp
+    if len(gq) == 2:
+        out["rel_dgrad_q2_vs_rk4_mixed"] = float(np.max(np.abs(gq["q2"] - gq["rk4"])) /
+                                                 max(1e-300, np.max(np.abs(gq["rk4"]))))
     F = {sv: sysm.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver=sv)
          for sv in ("rk4", "q2")}
     k = 0 if wl["fid_kind"] == "avg" else 1

@@ -195,8 +195,12 @@ typedef struct {
  * order) and J A (x) B (the couplings, in order), with the time-dependent terms at the
  * step's midpoint; always in the lab frame (`frame` is ignored).  Runs on the on-chip
  * kernels (every mode with the same level count 2..5, D <= 4096), else
- * SG_E_UNSUPPORTED; sg_evolve and sg_fidelity only (sg_fidelity_grad:
- * SG_E_UNSUPPORTED). */
+ * SG_E_UNSUPPORTED.  sg_fidelity_grad with Q2 computes the pulse-parameter gradient
+ * only (grad_ham must be NULL, else SG_E_UNSUPPORTED): the exact discrete adjoint of
+ * the product (Sec. 2.5), the state and co-state pulled back through each factor's
+ * inverse (no checkpoints), dU/df by the Frechet derivative of the local exponential;
+ * it needs >= 2 modes, <= 32 couplings and four state images of a CTA's columns in
+ * shared memory (mixed precision at D = 4096; FP64 up to D = 1024). */
 enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q2 = 2 };
 
 /* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev

@@ -237,10 +237,11 @@ class System:
         return F[0], F[1], U.view(np.complex128).reshape(Dc, len(col_index))
 
     def fidelity_grad(self, T, dt, target, col_index, kind="avg", precision="mixed",
-                      frame="interaction", ckpt=0, ham=True):
+                      frame="interaction", ckpt=0, ham=True, solver="rk4"):
         """F and the gradient w.r.t. the pulse and (ham=True) Hamiltonian parameters;
-        with ham=False the Hamiltonian part is not computed and returned as None."""
-        o, keep = evolve_opts(T, dt, precision, frame, col_index)
+        with ham=False the Hamiltonian part is not computed and returned as None.
+        solver="q2" (lab frame) computes the pulse-parameter gradient only: pass ham=False."""
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         npul, nham = self.param_counts()

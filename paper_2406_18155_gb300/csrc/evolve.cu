@@ -319,7 +319,7 @@ __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double
   double2* M = scratch + (size_t)e * 3 * n * n;
   double2* W1 = M + n * n;
   double2* W2 = W1 + n * n;
-  double2* Gh = mats + (size_t)e * 2 * DL * DL * DL * DL;
+  double2* Gh = mats + (size_t)e * 4 * DL * DL * DL * DL;
   double2* Gf = Gh + DL * DL * DL * DL;
   const double h = a.J[e] * a.dt * 0.5;
   for (int x = 0; x < da; ++x)
@@ -336,6 +336,58 @@ __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double
       for (int m = 0; m < n; ++m) acc = cfma(Gh[r * n + m], Gh[m * n + c], acc);
       Gf[r * n + c] = acc;
     }
+  // their adjoints (the pull-back of the gradient), after them
+  double2* Ghd = Gf + DL * DL * DL * DL;
+  double2* Gfd = Ghd + DL * DL * DL * DL;
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      Ghd[r * n + c] = cconj(Gh[c * n + r]);
+      Gfd[r * n + c] = cconj(Gf[c * n + r]);
+    }
+}
+
+// Gradient tables of Q2 (pulse parameters), rows [N][nq + K][d^2]: per step n the
+// adjoint U_i(n)^dag of each mode's (unmerged) 1-body half step, then per drive k on
+// mode i, M_k(n) = U_i(n)^dag L_k(n) with L_k(n) = L(A, -i (dt/2) O_k) the Frechet
+// derivative of expm at A = -i (dt/2) H_i(t_n + dt/2), the top-right block of
+// exp([[A, E], [0, A]]) (Sec. 2.5: dU/df_k).  One thread per (n, row).
+constexpr int kQ2MaxD = 5;
+__global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
+  const int per = a.nq + a.K;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < a.N * per; x += gridDim.x * blockDim.x) {
+    const int n = x / per, r = x - n * per;
+    double2 U[SG_MAXD * SG_MAXD], A[SG_MAXD * SG_MAXD], W1[SG_MAXD * SG_MAXD], W2[SG_MAXD * SG_MAXD];
+    double2* out = rows + ((size_t)n * per + r) * DL * DL;
+    if (r < a.nq) {
+      const int i = r, d = a.dims[i];
+      q2_onebody(a, i, n, U, A, W1, W2);
+      for (int p = 0; p < d; ++p)
+        for (int c = 0; c < d; ++c) out[p * d + c] = cconj(U[c * d + p]);
+      continue;
+    }
+    const DriveDev& dr = a.drives[r - a.nq];
+    const int i = dr.mode, d = a.dims[i], m = 2 * d;
+    if (d > kQ2MaxD) continue;                      // the on-chip Q2 plan has d <= 5
+    q2_onebody(a, i, n, U, A, W1, W2);              // U_i(n), and A = -i (dt/2) H_i on return
+    constexpr int MM = 4 * kQ2MaxD * kQ2MaxD;
+    double2 Z[MM], RZ[MM], Z1[MM], Z2[MM];
+    const double2* O = a.opd + a.opd_off[i] + dr.op * d * d;
+    const double h = a.dt * 0.5;
+    for (int p = 0; p < m * m; ++p) Z[p] = make_double2(0.0, 0.0);
+    for (int p = 0; p < d; ++p)
+      for (int c = 0; c < d; ++c) {
+        Z[p * m + c] = A[p * d + c];
+        Z[(p + d) * m + c + d] = A[p * d + c];
+        Z[p * m + c + d] = make_double2(h * O[p * d + c].y, -h * O[p * d + c].x);   // -i (dt/2) O
+      }
+    expm_serial(Z, m, RZ, Z1, Z2);
+    for (int p = 0; p < d; ++p)                     // M = U^dag L
+      for (int c = 0; c < d; ++c) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int q = 0; q < d; ++q) acc = cfma(cconj(U[q * d + p]), RZ[q * m + c + d], acc);
+        out[p * d + c] = acc;
+      }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -1163,6 +1215,7 @@ struct Solve {
   bool want_ham = true;           // Hamiltonian-parameter gradient requested
   const void* q2rows = nullptr;   // Q2: 1-body unitaries and coupling unitaries (stage precision)
   const void* q2edges = nullptr;
+  const void* q2grad = nullptr;   // Q2 pulse gradient: per step U_i(n)^dag and U_i(n)^dag L_k(n)
   ~Solve() {
     slab_plan_destroy(slab);
     onchip_plan_destroy(oc);
@@ -1230,7 +1283,7 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   s.ta = ta;
   if (s.q2) {
     const int DL = onchip_dl(sv.oc);
-    const size_t nrow = (size_t)(s.N + 1) * s.nq * DL * DL, nedge = (size_t)std::max(1, s.p.ne) * 2 * DL * DL * DL * DL;
+    const size_t nrow = (size_t)(s.N + 1) * s.nq * DL * DL, nedge = (size_t)std::max(1, s.p.ne) * 4 * DL * DL * DL * DL;
     double2* rows = sv.ar.get<double2>(nrow);
     double2* edges = sv.ar.get<double2>(nedge);
     double2* scratch = sv.ar.get<double2>((size_t)std::max(1, s.p.ne) * 3 * DL * DL * DL * DL);
@@ -1240,6 +1293,15 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
     sv.launches += 2;
     sv.q2rows = rows;
     sv.q2edges = edges;
+    const size_t ngr = grad ? (size_t)s.N * (s.nq + s.K) * DL * DL : 0;
+    double2* gtab = nullptr;
+    if (grad) {
+      gtab = sv.ar.get<double2>(ngr);
+      if (!gtab) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 gradient tables failed");
+      k_q2_gradtabs<<<grid_for((long long)s.N * (s.nq + s.K)), 64, 0, st>>>(ta, DL, gtab);
+      ++sv.launches;
+      sv.q2grad = gtab;
+    }
     if (sv.mixed) {
       float* r32 = sv.ar.get<float>(2 * nrow);
       float* e32 = sv.ar.get<float>(2 * nedge);
@@ -1249,6 +1311,13 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
       sv.launches += 2;
       sv.q2rows = r32;
       sv.q2edges = e32;
+      if (grad) {
+        float* g32 = sv.ar.get<float>(2 * ngr);
+        if (!g32) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 gradient tables failed");
+        onchip_to_f32(reinterpret_cast<const double*>(gtab), g32, 2 * (long long)ngr, st);
+        ++sv.launches;
+        sv.q2grad = g32;
+      }
     }
   } else if (f32only) {
     k_tables32<<<(unsigned)nst, 64, 0, st>>>(ta, sv.coef32, sv.ph32);
@@ -1618,6 +1687,32 @@ sg_status run_q2(sg_system* sys, Solve& sv, const long long* cols_dev, bool init
   return SG_OK;
 }
 
+// Q2 pulse gradient: the co-state pbar of the final lab-frame columns in sv.psi is
+// pulled back through every factor with the state (Sec. 2.5 applied to the product
+// of unitaries of Sec. 2.3); dF/df_k(n) lands at stage slot 3n + 1 of acc.gF.
+sg_status run_backward_q2(sg_system* sys, Solve& sv, double2* pbar, GradAcc acc) {
+  sg_ctx* ctx = sys->ctx;
+  cudaStream_t st = ctx->stream;
+  Setup& s = sv.s;
+  const int ncta = onchip_ctas(sv.oc);
+  const long long nst = 3ll * s.N;
+  const int Kd = std::max(1, s.K);
+  double* gFc = sv.ar.get<double>((size_t)ncta * nst * Kd);
+  if (!gFc) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 adjoint buffers failed");
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(gFc, 0, (size_t)ncta * nst * Kd * sizeof(double), st));
+  int drv_mode[SG_MAXDRIVE];
+  for (int k = 0; k < s.K; ++k) drv_mode[k] = s.drives[k].mode;
+  sg_status rc = onchip_q2_pulse_adjoint(sv.oc, s.p, drv_mode, s.K, sv.q2grad, sv.q2edges, sv.psi, pbar, s.N, gFc,
+                                         st, &sv.launches);
+  if (rc != SG_OK)
+    return sg_fail(ctx, rc, "the Q2 gradient needs 2..16 modes, <= 32 couplings, <= 16 drives and its buffers "
+                            "in shared memory");
+  onchip_reduce(sv.oc, gFc, nullptr, nst, s.K, s.p.n1, s.p.ne, acc, st);
+  ++sv.launches;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  return SG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // entry points used by the C ABI
 // ---------------------------------------------------------------------------
@@ -1674,7 +1769,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (rc != SG_OK) return rc;
   Setup& s = sv.s;
   if (s.nqb < 1 || s.nqb > 12) return sg_fail(ctx, SG_E_UNSUPPORTED, "fidelity needs 1..12 qubit (non-coupler) modes");
-  if (s.q2 && grad) return sg_fail(ctx, SG_E_UNSUPPORTED, "gradients are computed with the RK4 solver only");
+  if (s.q2 && grad && grad_ham)
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the Q2 solver computes the pulse-parameter gradient only (grad_ham = NULL)");
   for (int i = 0; i < s.nq; ++i)
     if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
       return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");
@@ -1729,7 +1825,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   // checkpoints
   int K = 0;
   std::vector<double2*> ckpts;
-  if (grad) {
+  if (grad && !s.q2) {             // the Q2 adjoint recomputes the states by inverse factors
     K = ckpt > 0 ? ckpt : std::max(1, (int)std::lround(std::sqrt((double)s.N)));
     K = std::min(K, s.N);
     const int nck = (s.N + K - 1) / K;
@@ -1811,8 +1907,9 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
       k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, +1.0), pbar);
     }
     sv.launches += 3;
-    rc = o->precision == SG_MIXED ? run_backward<float>(sys, sv, ckpts, K, pbar, acc)
-                                  : run_backward<double>(sys, sv, ckpts, K, pbar, acc);
+    if (s.q2) rc = run_backward_q2(sys, sv, pbar, acc);
+    else rc = o->precision == SG_MIXED ? run_backward<float>(sys, sv, ckpts, K, pbar, acc)
+                                       : run_backward<double>(sys, sv, ckpts, K, pbar, acc);
     if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
     // chains
     if (s.K) {

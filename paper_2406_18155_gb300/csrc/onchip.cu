@@ -165,6 +165,9 @@ struct OcArgs {
   int f_ys, f_ks, f_ps, f_dl, f_M;
   // Q2 (products of local unitaries) shared-memory byte offsets: state, scratch, 1-body rows
   int q_ys, q_ks, q_M, q_G;
+  // Q2 pulse-gradient backward: psi, psibar, two scratch images, rows (U^dag, L), warp
+  // partials, then the coupling unitaries when they fit
+  int b_x0, b_x1, b_x2, b_x3, b_rows, b_rowcap, b_red, b_G;
   // adjoint shared-memory byte offsets
   int a_xs, a_ks, a_ys, a_yn, a_db, a_pb, a_M, a_cf, a_ph, a_obD, a_obL, a_obR, a_ebB, a_ebL, a_ebR,
       a_jb, a_gs, a_sq;
@@ -732,6 +735,144 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
   }
 }
 
+// Backward of Q2 for the pulse gradient (Sec. 2.5 on the product of Sec. 2.3).  The
+// final states psi and the co-state psibar (lab frame) are pulled back through every
+// factor in reverse order, psi <- X^dag psi and psibar <- X^dag psibar.  A 1-body half
+// step is X = prod_i U_i (commuting factors on distinct modes), and for a drive k on
+// mode i, dX/df_k = (prod_{j != i} U_j) L_k with L_k the Frechet derivative of the
+// local exponential, so with the states before the half step
+//   Re <psibar_after, dX/df_k psi_before> = Re <psibar_before, U_i^dag L_k psi_before>
+//                                         = Re sum_ab M_k[a][b] C_i[a][b],
+// M_k = U_i^dag L_k and C_i[a][b] = sum conj(psibar_before[a, ..]) psi_before[b, ..]
+// the cross-density over mode i.  Each thread contracts its blocks' cross-densities
+// with M_k at once, so a step reduces one scalar per drive over the CTA (warp
+// shuffles, then the warps in fixed order) into stage slot 3n + 1 of the CTA's gF
+// block.  The 1-body factors are applied as Kronecker pairs like the forward.
+constexpr int kQ2G = 16;          // drives of a Q2 gradient solve (per-thread partials)
+struct Q2AdjArgs {
+  int nq, K, ne, n1f;             // modes, drives, couplings, 1-body factors of a half step
+  int row;                        // (nq + K) d^2: U_i(n)^dag then M_k(n)
+  unsigned driven;                // bit i: a drive acts on mode i
+  Phase one[SG_MAXQ / 2 + 1];     // pairs (offL, offR) and an odd last mode (offA)
+  Phase mode[SG_MAXQ];            // cross-density block layout of mode i
+  Phase edge[32];
+  int drv_mode[kQ2G];
+};
+
+template <typename R, int DL>
+__global__ void __launch_bounds__(kST, 1)
+k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __restrict__ rows,
+            const typename CT<R>::T* __restrict__ edges, const double2* __restrict__ psi_api,
+            const double2* __restrict__ bar_api, int N, double* __restrict__ gF_cta, long long nstK,
+            int nedge) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char sm[];
+  C* xs = reinterpret_cast<C*>(sm + oa.b_x0);         // psi
+  C* xb = reinterpret_cast<C*>(sm + oa.b_x1);         // psibar
+  C* t1 = reinterpret_cast<C*>(sm + oa.b_x2);
+  C* t2 = reinterpret_cast<C*>(sm + oa.b_x3);
+  C* const M0 = reinterpret_cast<C*>(sm + oa.b_rows);
+  C* const M1 = M0 + oa.b_rowcap;
+  double* red = reinterpret_cast<double*>(sm + oa.b_red);   // warps x kQ2G
+  const C* G = edges;
+  if (nedge > 0) {
+    C* Gs = reinterpret_cast<C*>(sm + oa.b_G);
+    for (int i = threadIdx.x; i < nedge; i += blockDim.x) Gs[i] = edges[i];
+    G = Gs;
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, cta = blockIdx.x;
+  for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
+    const int c = e / oa.D, t = e - c * oa.D;
+    const int col = cta * oa.Sc + c;
+    const int pos = oc_pos<DL>(oa, e);
+    xs[pos] = to_c(col < oa.S ? psi_api[(size_t)t * oa.S + col] : make_double2(0.0, 0.0), R(0));
+    xb[pos] = to_c(col < oa.S ? bar_api[(size_t)t * oa.S + col] : make_double2(0.0, 0.0), R(0));
+  }
+  if (N > 0) issue_rows<C>(rows, qa.row, N - 1, M0, threadIdx.x, blockDim.x);
+  cp_wait_all();
+  __syncthreads();
+  double* gFc = gF_cta + (size_t)cta * nstK;
+  int buf = 0;
+  for (int n = N - 1; n >= 0; --n) {
+    const C* U = buf ? M1 : M0;
+    const C* Mk = U + qa.nq * DL * DL;
+    if (n > 0) issue_rows<C>(rows, qa.row, n - 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
+    R g[kQ2G];
+#pragma unroll
+    for (int k = 0; k < kQ2G; ++k) g[k] = R(0);
+    for (int h = 0; h < 2; ++h) {
+      if (h == 1) {                                                  // couplings (palindrome)
+        for (int q = 0; q < 2 * qa.ne - 1; ++q) {
+          const int e = q < qa.ne ? q : 2 * qa.ne - 2 - q;
+          const C* Gd = G + (size_t)(4 * e + (q == qa.ne - 1 ? 3 : 2)) * DL * DL * DL * DL;
+          const Phase& P = qa.edge[e];
+          for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
+            const int c = b / oa.nbc;
+            const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
+            block_dense<DL>(Gd, xs, t1, pb, P.psa, P.psb);
+            block_dense<DL>(Gd, xb, t2, pb, P.psa, P.psb);
+          }
+          __syncthreads();
+          C* tmp = xs; xs = t1; t1 = tmp;
+          tmp = xb; xb = t2; t2 = tmp;
+        }
+      }
+      // the 1-body half step of step n (the second half first)
+      for (int f = 0; f < qa.n1f; ++f) {
+        const Phase& P = qa.one[f];
+        for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
+          const int c = b / oa.nbc;
+          const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
+          phase_block<DL, false>(P, U, xs, t1, pb, true);
+          phase_block<DL, false>(P, U, xb, t2, pb, true);
+        }
+        __syncthreads();
+        C* tmp = xs; xs = t1; t1 = tmp;
+        tmp = xb; xb = t2; t2 = tmp;
+      }
+      // cross-densities of the driven modes against the states before the half step
+      for (int i = 0; i < qa.nq; ++i) {
+        if (!((qa.driven >> i) & 1u)) continue;
+        const Phase& P = qa.mode[i];
+        for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
+          const int c = b / oa.nbc;
+          C acc[DL * DL];
+#pragma unroll
+          for (int a = 0; a < DL * DL; ++a) acc[a] = cmk<C>(0.0, 0.0);
+          xd_slot<DL, false>(P, 0, U, xb, xs, blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS, acc);
+#pragma unroll
+          for (int k = 0; k < kQ2G; ++k) {
+            if (k < qa.K && qa.drv_mode[k] == i) {
+              const C* M = Mk + k * DL * DL;
+              R v = R(0);
+#pragma unroll
+              for (int ab = 0; ab < DL * DL; ++ab) v += M[ab].x * acc[ab].x - M[ab].y * acc[ab].y;
+              g[k] += v;
+            }
+          }
+        }
+      }
+    }
+    // one scalar per drive over the CTA: warps, then the warps in order
+#pragma unroll
+    for (int k = 0; k < kQ2G; ++k) {
+      if (k < qa.K) {
+        R v = g[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp * kQ2G + k] = (double)v;
+      }
+    }
+    cp_wait_all();
+    __syncthreads();
+    if (threadIdx.x < qa.K) {
+      double sacc = 0.0;
+      for (int w = 0; w < kST / 32; ++w) sacc += red[w * kQ2G + threadIdx.x];
+      gFc[(size_t)(3 * n + 1) * qa.K + threadIdx.x] += sacc;
+    }
+    buf ^= 1;
+  }
+}
+
 // API layout [D][S] -> state image [cta][Sc][D]
 __global__ void k_oc_image(OcArgs oa, const double2* __restrict__ api, double2* __restrict__ img) {
   const long long total = (long long)oa.ncta * oa.ent;
@@ -828,6 +969,16 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   a.q_ks = take(a.CSP * cs);
   a.q_M = take(2 * (size_t)a.rowA * cs);
   a.q_G = (int)o;                 // coupling unitaries follow (sized per solve)
+  o = 0;
+  a.b_x0 = take(a.CSP * cs);
+  a.b_x1 = take(a.CSP * cs);
+  a.b_x2 = take(a.CSP * cs);
+  a.b_x3 = take(a.CSP * cs);
+  a.b_rowcap = a.rowA + a.K * DL * DL;                     // rowA >= nq d^2 in the lab frame
+  a.b_rowcap += a.b_rowcap & 1;
+  a.b_rows = take(2 * (size_t)a.b_rowcap * cs);            // double-buffered step rows
+  a.b_red = take((size_t)(kST / 32) * 16 * sizeof(double));
+  a.b_G = (int)o;
   o = 0;
   a.a_xs = take(a.CSP * cs);
   a.a_ks = take(a.CSP * cs);
@@ -1044,7 +1195,7 @@ int q2_t(const OnchipPlan* oc, const Q2Args& qa, const void* rows, const void* e
   typedef typename CT<R>::T C;
   smem_limit_once<k_oc_q2<R, DL>>();
   // coupling unitaries in shared memory when they fit, else read from global memory
-  const int nedge = 2 * std::max(0, ne) * DL * DL * DL * DL;
+  const int nedge = 4 * std::max(0, ne) * DL * DL * DL * DL;
   const size_t gbytes = (size_t)nedge * sizeof(C);
   const bool gsm = oc->oa.q_G + gbytes <= oc->limit;
   const size_t smem = oc->oa.q_G + (gsm ? gbytes : 0);
@@ -1080,7 +1231,7 @@ sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* ro
     Q2Factor& F = qa.f[qa.nf0 + qa.nfe++];
     F.P = make_phase(sp, DL, p.e_a[e], p.e_b[e]);
     F.kind = 2;
-    F.mat = 2 * e;
+    F.mat = 4 * e;                // per coupling: half, full, half^dag, full^dag
   }
   const int rowlen = p.nq * DL * DL;
   int n = 0;
@@ -1105,6 +1256,74 @@ sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* ro
 
 int onchip_dl(const OnchipPlan* oc) { return oc->h->DL; }
 
+namespace {
+
+template <typename R, int DL>
+int q2adj_t(const OnchipPlan* oc, const Q2AdjArgs& qa, const void* rows, const void* edges, const double2* psi,
+            const double2* bar, int N, double* gF_cta, long long nstK, cudaStream_t st) {
+  typedef typename CT<R>::T C;
+  smem_limit_once<k_oc_q2_adj<R, DL>>();
+  const int nedge = 4 * qa.ne * DL * DL * DL * DL;
+  const bool gsm = oc->oa.b_G + (size_t)nedge * sizeof(C) <= oc->limit;
+  const size_t smem = oc->oa.b_G + (gsm ? (size_t)nedge * sizeof(C) : 0);
+  k_oc_q2_adj<R, DL><<<oc->oa.ncta, kST, smem, st>>>(oc->h->pass[0], oc->oa, qa, (const C*)rows, (const C*)edges,
+                                                           psi, bar, N, gF_cta, nstK, gsm ? nedge : 0);
+  return 1;
+}
+
+}  // namespace
+
+sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
+                                  const void* edges, const double2* psi, const double2* bar, int N, double* gF_cta,
+                                  cudaStream_t st, int* launches) {
+  const SlabPass& sp = oc->h->pass[0];
+  const int DL = oc->h->DL;
+  if ((size_t)oc->oa.b_G > oc->limit || p.nq < 2 || p.ne > 32 || K > kQ2G || K != oc->oa.K)
+    return SG_E_UNSUPPORTED;
+  if (p.nq * DL * DL > oc->oa.rowA) return SG_E_UNSUPPORTED;
+  Q2AdjArgs qa{};
+  qa.nq = p.nq;
+  qa.K = K;
+  qa.ne = p.ne;
+  qa.row = (p.nq + K) * DL * DL;
+  for (int i = 0; i < p.nq; i += 2) {
+    Phase& P = qa.one[qa.n1f++];
+    if (i + 1 < p.nq) {
+      P = make_phase(sp, DL, i, i + 1);
+      P.offL = i * DL * DL;
+      P.offR = (i + 1) * DL * DL;
+    } else {
+      P = make_phase(sp, DL, i, i - 1);
+      P.offA = i * DL * DL;
+    }
+  }
+  for (int i = 0; i < p.nq; ++i) qa.mode[i] = make_phase(sp, DL, i, i == 0 ? 1 : 0);
+  for (int e = 0; e < p.ne; ++e) qa.edge[e] = make_phase(sp, DL, p.e_a[e], p.e_b[e]);
+  for (int k = 0; k < K; ++k) {
+    qa.drv_mode[k] = drv_mode[k];
+    qa.driven |= 1u << drv_mode[k];
+  }
+  const long long nstK = 3ll * N * std::max(1, K);
+  int n = 0;
+  if (oc->mixed) {
+    switch (DL) {
+      case 2: n = q2adj_t<float, 2>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      case 3: n = q2adj_t<float, 3>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      case 4: n = q2adj_t<float, 4>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      default: n = q2adj_t<float, 5>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+    }
+  } else {
+    switch (DL) {
+      case 2: n = q2adj_t<double, 2>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      case 3: n = q2adj_t<double, 3>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      case 4: n = q2adj_t<double, 4>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      default: n = q2adj_t<double, 5>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+    }
+  }
+  if (launches) *launches += n;
+  return SG_OK;
+}
+
 void onchip_to_image(const OnchipPlan* oc, const double2* api, double2* img, cudaStream_t st) {
   k_oc_image<<<grid_of(onchip_state_elems(oc)), 256, 0, st>>>(oc->oa, api, img);
 }
@@ -1117,7 +1336,7 @@ void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc
                    int n1, int ne, GradAcc acc, cudaStream_t st) {
   RedArgs r{};
   r.nstK = nst * std::max(1, K);
-  r.accd = oc->oa.accd;
+  r.accd = acc_cta ? oc->oa.accd : 0;   // no per-CTA accumulator blocks: dF/df only
   r.ncta = oc->oa.ncta;
   r.K = K;
   r.n1 = n1;

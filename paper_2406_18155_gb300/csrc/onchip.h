@@ -79,3 +79,14 @@ void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc
 sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
                             const double2* psi_in, double2* psi_out, int N, cudaStream_t st, int* launches);
 int onchip_dl(const OnchipPlan* oc);
+// Q2 pulse gradient: pulls the final states psi and the co-state bar (API layout, lab
+// frame) back through every factor and adds dF/df_k at the midpoint of step n to
+// gF_cta (CTA-major, 3N x K each, slot 3n + 1; zeroed by the caller).  rows:
+// [N][nq + K][d^2], per step the adjoint 1-body half-step unitaries U_i(n)^dag, then
+// M_k(n) = U_i(n)^dag L_k(n) with L_k the Frechet derivative of the local exponential
+// along drive k's operator; edges: per coupling half, full, half^dag, full^dag.
+// SG_E_UNSUPPORTED for one mode, more than 32 couplings or 16 drives, or when the
+// layout does not fit in shared memory.
+sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
+                                  const void* edges, const double2* psi, const double2* bar, int N, double* gF_cta,
+                                  cudaStream_t st, int* launches);

@@ -1,12 +1,15 @@
 """GPU parity of the second-order Suzuki-Trotter solver (Sec. 2.3, App. A) against
 the oracle's Q2: lab-frame states and fidelities, FP64 within 1e-10, FP32 factors
-and state within 1e-5 on short evolutions; unsupported requests are rejected."""
+and state within 1e-5 on short evolutions; the pulse-parameter gradient (discrete
+adjoint of the product of unitaries, Sec. 2.5) against the oracle's adjoint, FP64
+within 1e-9 and FP32 within 2e-4 of the largest component; unsupported requests
+are rejected."""
 import numpy as np
 import pytest
 
 from oracle.evolve import initial_columns, fidelities
 from oracle.system import OracleSystem
-from oracle.trotter import q2_evolve
+from oracle.trotter import q2_evolve, q2_pulse_gradient
 from paper_2406_18155_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -65,7 +68,7 @@ def test_q2_rejects_what_it_does_not_run(sgctx, default_path):
     from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
     wl = CASES["transmon_pair"]()
     s = _system(sgctx, wl)
-    with pytest.raises(SGError) as e:                       # gradients: RK4 only
+    with pytest.raises(SGError) as e:                       # Hamiltonian gradient: RK4 only
         from paper_2406_18155_gb300.api import evolve_opts
         import ctypes as C
         from paper_2406_18155_gb300.capi import lib
@@ -80,3 +83,34 @@ def test_q2_rejects_what_it_does_not_run(sgctx, default_path):
     with pytest.raises(SGError) as e:                       # unequal level counts: not on-chip
         s2.evolve(0.3, 0.01, precision="fp64", col_index=mixed_levels["col_index"], solver="q2")
     assert e.value.code == SG_E_UNSUPPORTED
+
+
+GRAD_CASES = ["transmon_pair", "chain3_l3", "ring4_l3", "pair_cr_l5", "ftf_l4", "local_ops_l3"]
+
+
+@pytest.mark.parametrize("name", GRAD_CASES)
+def test_q2_pulse_gradient_matches_oracle(sgctx, default_path, name):
+    wl = CASES[name]()
+    s = _system(sgctx, wl)
+    F_r, g_r = q2_pulse_gradient(wl)
+    scale = max(1.0, np.max(np.abs(g_r)))
+    for prec, tol_F, tol_g in (("fp64", 1e-10, 1e-9), ("mixed", 1e-5, 2e-4)):
+        F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
+                                    precision=prec, ham=False, solver="q2")
+        assert gh is None and gp.shape == g_r.shape
+        Fk = F[0] if wl["fid_kind"] == "avg" else F[1]
+        assert abs(Fk - F_r) < tol_F, (prec, Fk, F_r)
+        assert np.max(np.abs(gp - g_r)) < tol_g * scale, (prec, np.max(np.abs(gp - g_r)), scale)
+
+
+def test_q2_pulse_gradient_longer_evolution(sgctx, default_path):
+    """A CR pulse of 4 ns (N = 400 steps, 5 levels per fluxonium, 6 PWC segments):
+    the reconstruction of the states by inverse factors stays within the bars."""
+    wl = _short(W.fluxonium_pair_cr(seed=11, nseg=6), T=4.0)
+    s = _system(sgctx, wl)
+    F_r, g_r = q2_pulse_gradient(wl)
+    scale = max(1.0, np.max(np.abs(g_r)))
+    for prec, tol in (("fp64", 1e-9), ("mixed", 1e-3)):
+        F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
+                                   precision=prec, ham=False, solver="q2")
+        assert np.max(np.abs(gp - g_r)) < tol * scale, (prec, np.max(np.abs(gp - g_r)), scale)
