@@ -199,8 +199,8 @@ typedef struct {
  * only (grad_ham must be NULL, else SG_E_UNSUPPORTED): the exact discrete adjoint of
  * the product (Sec. 2.5), the state and co-state pulled back through each factor's
  * inverse (no checkpoints), dU/df by the Frechet derivative of the local exponential;
- * it needs >= 2 modes, <= 32 couplings and four state images of a CTA's columns in
- * shared memory (mixed precision at D = 4096; FP64 up to D = 1024). */
+ * it needs >= 2 modes, <= 16 drives, <= 32 couplings and four state images of a
+ * CTA's columns in shared memory (mixed precision fits D = 4096, FP64 does not). */
 enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q2 = 2 };
 
 /* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev
