@@ -1,7 +1,9 @@
-"""Pins of the oracle's second-order Suzuki-Trotter evolution (Sec. 2.3, App. A)
-against what the mathematics fixes: exactness when the local terms commute,
-second-order convergence, unitarity."""
+"""Pins of the oracle's Suzuki-Trotter evolutions (Sec. 2.3, App. A) against what
+the mathematics fixes: exactness when the local terms commute, the convergence
+order of Q2 (2), Q4 (4) and Q4j (3: see oracle/trotter.py), unitarity, and the
+pulse gradient against central differences."""
 import numpy as np
+import pytest
 from scipy.linalg import expm
 
 from oracle.evolve import initial_columns, rk4_evolve, frame_epilogue
@@ -54,14 +56,54 @@ def test_second_order_convergence():
     assert 3.3 < r1 < 4.7 and 3.3 < r2 < 4.7, errs
 
 
+def _converged_reference(base, T):
+    # RK4 in the interaction frame at a fine step (the level energies removed, so it
+    # is converged) and the exact frame phase back to the lab frame
+    ref_wl = dict(_lab(base, T, 0.000625), frame="interaction")
+    ref_sys = OracleSystem(ref_wl)
+    return frame_epilogue(ref_sys, rk4_evolve(ref_sys, initial_columns(ref_sys, base["col_index"])))
+
+
+def _errors(base, T, ref, scheme, dts):
+    errs = []
+    for dt in dts:
+        s = OracleSystem(_lab(base, T, dt))
+        errs.append(np.max(np.abs(q2_evolve(s, initial_columns(s, base["col_index"]), scheme=scheme) - ref)))
+    return errs
+
+
+def test_fourth_order_convergence_of_q4_and_third_of_q4j():
+    # Gaussian-driven coupled pair: Q4's error falls 16x per halving of dt; the
+    # complex Q4j's 8x (p + p* = 1 and p^3 + p*^3 = 0 cancel the dt^3 local term);
+    # a wrong p, or the sub-step times off their midpoints, drops either to order 2
+    # or below
+    base = W.transmon_pair(seed=4)
+    base["modes"] = [dict(m, levels=3) for m in base["modes"]]
+    base["col_index"] = list(range(9))
+    ref = _converged_reference(base, 1.0)
+    e4 = _errors(base, 1.0, ref, "q4", (0.02, 0.01, 0.005))
+    assert 14.0 < e4[0] / e4[1] < 17.0 and 14.0 < e4[1] / e4[2] < 17.0, e4
+    e4j = _errors(base, 1.0, ref, "q4j", (0.02, 0.01, 0.005))
+    assert 7.0 < e4j[0] / e4j[1] < 11.0 and 7.0 < e4j[1] / e4j[2] < 11.0, e4j
+    e2 = _errors(base, 1.0, ref, "q2", (0.01,))
+    assert e4[1] < e4j[1] < e2[0]
+
+
 def test_unitary_to_round_off():
     wl = _lab(W.coupler_scheme(seed=5, kind="ftf", nseg=4, levels=(3, 3, 3)), 0.3, 0.01)
     sys = OracleSystem(wl)
     U = q2_evolve(sys, initial_columns(sys, range(sys.D)))
     assert np.max(np.abs(U.conj().T @ U - np.eye(sys.D))) < 1e-12
+    U4 = q2_evolve(sys, initial_columns(sys, range(sys.D)), scheme="q4")
+    assert np.max(np.abs(U4.conj().T @ U4 - np.eye(sys.D))) < 1e-12
+    # Q4j's factors are not unitary (complex time steps); its product is, to its order
+    U4j = q2_evolve(sys, initial_columns(sys, range(sys.D)), scheme="q4j")
+    dev = np.max(np.abs(U4j.conj().T @ U4j - np.eye(sys.D)))
+    assert 1e-12 < dev < 1e-4, dev
 
 
-def test_q2_pulse_gradient_matches_central_differences():
+@pytest.mark.parametrize("scheme", ["q2", "q4", "q4j"])
+def test_pulse_gradient_matches_central_differences(scheme):
     import copy
     from oracle.trotter import q2_pulse_gradient, q2_fidelity
     for wl in (W.fluxonium_pair_multipath(seed=11, levels=3, nseg=3),
@@ -70,8 +112,8 @@ def test_q2_pulse_gradient_matches_central_differences():
         if wl["modes"][0]["kind"] == "transmon":
             wl["modes"] = [dict(m, levels=3) for m in wl["modes"]]
             wl["col_index"] = W.comp_states([3, 3])
-        F, g = q2_pulse_gradient(wl)
-        assert abs(F - q2_fidelity(wl)) < 1e-14
+        F, g = q2_pulse_gradient(wl, scheme=scheme)
+        assert abs(F - q2_fidelity(wl, scheme=scheme)) < 1e-14
         fd = []
         for k, dr in enumerate(wl["drives"]):
             keys = [("amps", j) for j in range(len(dr["amps"]))] if dr["env"] == "pwc" else [("amp", None)]
@@ -84,7 +126,7 @@ def test_q2_pulse_gradient_matches_central_differences():
                         w2["drives"][k][key] += sgn * h
                     else:
                         w2["drives"][k][key][j] += sgn * h
-                    vals.append(q2_fidelity(w2))
+                    vals.append(q2_fidelity(w2, scheme=scheme))
                 fd.append((vals[0] - vals[1]) / (2 * h))
         fd = np.array(fd)
         assert np.max(np.abs(g - fd)) <= 1e-6 * max(1e-3, np.max(np.abs(fd))), (g, fd)
