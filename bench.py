@@ -458,12 +458,13 @@ def fp64_comparison(sysm, wl, nsteps, stream):
 
 
 def q2_comparison(sysm, wl, stream):
-    """The paper's second-order Suzuki-Trotter solver against RK4 on the whole
-    workload (single-tile systems only): forward col-steps/s of each in FP64 and
-    mixed precision (device time), and the fidelity difference at the workload's dt."""
+    """The paper's Suzuki-Trotter solvers (Q2, Q4, Q4j) against RK4 on the whole
+    workload (single-tile systems only): forward and pulse-gradient col-steps/s of
+    each in FP64 and mixed precision (device time), and the fidelity differences at
+    the workload's dt."""
     import torch
     out = {}
-    for solver in ("rk4", "q2"):
+    for solver in ("rk4", "q2", "q4", "q4j"):
         for prec in ("fp64", "mixed"):
             kw = dict(precision=prec, col_index=wl["col_index"], solver=solver)
             sysm.evolve(wl["T"], wl["dt"], **kw)                          # warm
@@ -480,7 +481,7 @@ def q2_comparison(sysm, wl, stream):
     # it runs in; a solve the plan cannot hold is reported as null
     from paper_2406_18155_gb300.capi import SGError
     gq = {}
-    for solver in ("rk4", "q2"):
+    for solver in ("rk4", "q2", "q4"):
         for prec in ("fp64", "mixed"):
             kw = dict(kind=wl["fid_kind"], precision=prec, ham=False, solver=solver,
                       frame="lab" if solver == "q2" else wl.get("frame", "interaction"))
@@ -501,15 +502,17 @@ def q2_comparison(sysm, wl, stream):
             out[key] = len(wl["col_index"]) * round(wl["T"] / wl["dt"]) / (e0.elapsed_time(e1) / 1e3)
             if prec == "mixed":
                 gq[solver] = gp
-    if len(gq) == 2:
-        out["rel_dgrad_q2_vs_rk4_mixed"] = float(np.max(np.abs(gq["q2"] - gq["rk4"])) /
-                                                 max(1e-300, np.max(np.abs(gq["rk4"]))))
+    for sv in ("q2", "q4"):
+        if sv in gq and "rk4" in gq:
+            out[f"rel_dgrad_{sv}_vs_rk4_mixed"] = float(np.max(np.abs(gq[sv] - gq["rk4"])) /
+                                                        max(1e-300, np.max(np.abs(gq["rk4"]))))
     F = {sv: sysm.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver=sv)
-         for sv in ("rk4", "q2")}
+         for sv in ("rk4", "q2", "q4", "q4j")}
     k = 0 if wl["fid_kind"] == "avg" else 1
-    out["fidelity_rk4_fp64"] = float(F["rk4"][k])
-    out["fidelity_q2_fp64"] = float(F["q2"][k])
-    out["abs_dF_q2_vs_rk4"] = abs(float(F["q2"][k]) - float(F["rk4"][k]))
+    for sv in ("rk4", "q2", "q4", "q4j"):
+        out[f"fidelity_{sv}_fp64"] = float(F[sv][k])
+    for sv in ("q2", "q4", "q4j"):
+        out[f"abs_dF_{sv}_vs_rk4"] = abs(float(F[sv][k]) - float(F["rk4"][k]))
     return out
 
 

@@ -186,22 +186,27 @@ typedef struct {
   int ncols;                    /* S, number of evolved columns                           */
   const long long* col_index;   /* host, S flat initial basis indices, or NULL: the
                                    columns of psi are the initial states                  */
-  int solver;                   /* SG_SOLVER_RK4 (0, default) or SG_SOLVER_Q2             */
+  int solver;                   /* SG_SOLVER_RK4 (0, default), _Q2, _Q4 or _Q4J            */
 } sg_evolve_opts;
 
 /* Solvers.  SG_SOLVER_Q2: the second-order Suzuki-Trotter product of Sec. 2.3 and
  * App. A, Q2(dt) = prod_k exp(-i H_k dt/2) prod_k' exp(-i H_k' dt/2) (k' reversed)
  * over the local terms H_i = diag(E^(i)) + sum_{drives on i} f(t) O (every mode, in mode
  * order) and J A (x) B (the couplings, in order), with the time-dependent terms at the
- * step's midpoint; always in the lab frame (`frame` is ignored).  Runs on the on-chip
- * kernels (every mode with the same level count 2..5, D <= 4096), else
- * SG_E_UNSUPPORTED.  sg_fidelity_grad with Q2 computes the pulse-parameter gradient
- * only (grad_ham must be NULL, else SG_E_UNSUPPORTED): the exact discrete adjoint of
- * the product (Sec. 2.5), the state and co-state pulled back through each factor's
- * inverse (no checkpoints), dU/df by the Frechet derivative of the local exponential;
- * it needs >= 2 modes, <= 16 drives, <= 32 couplings and four state images of a
- * CTA's columns in shared memory (mixed precision fits D = 4096, FP64 does not). */
-enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q2 = 2 };
+ * step's midpoint; always in the lab frame (`frame` is ignored).  SG_SOLVER_Q4: the real
+ * fourth-order product Q2(p dt) Q2((1-2p) dt) Q2(p dt), p = 1/(2 - 2^(1/3)), each Q2
+ * sub-step with its time-dependent terms at its own midpoint.  SG_SOLVER_Q4J: the complex
+ * product Q2(p dt) Q2(p* dt), p = (3 - i sqrt 3)/6, the drive coefficients continued to
+ * the complex sub-step midpoints; third order (the composition is not palindromic).
+ * They run on the on-chip kernels (every mode with the same level count 2..5,
+ * D <= 4096), else SG_E_UNSUPPORTED.  sg_fidelity_grad with Q2 or Q4 computes the
+ * pulse-parameter gradient only (grad_ham must be NULL, else SG_E_UNSUPPORTED): the exact
+ * discrete adjoint of the product (Sec. 2.5), the state and co-state pulled back through
+ * each factor's inverse (no checkpoints), dU/df by the Frechet derivative of the local
+ * exponential; it needs >= 2 modes, <= 16 drives, <= 32 couplings and four state images
+ * of a CTA's columns in shared memory (mixed precision fits D = 4096, FP64 does not).
+ * Q4j's factors are not unitary: its gradient returns SG_E_UNSUPPORTED. */
+enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q2 = 2, SG_SOLVER_Q4 = 4, SG_SOLVER_Q4J = 5 };
 
 /* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev
  * (device, D*S complex128, column innermost).  If opts->col_index is NULL psi_dev

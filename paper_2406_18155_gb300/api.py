@@ -51,7 +51,7 @@ class Context:
             pass
 
 
-_SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q2": capi.SG_SOLVER_Q2}
+_SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q2": capi.SG_SOLVER_Q2, "q4": capi.SG_SOLVER_Q4, "q4j": capi.SG_SOLVER_Q4J}
 
 
 def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None, solver="rk4"):
@@ -214,7 +214,7 @@ class System:
     def evolve(self, T, dt, precision="mixed", frame="interaction", col_index=None, psi=None, solver="rk4"):
         """Lab-frame columns after T, as a (D, S) complex128 torch tensor on the device.
         Starts from basis states col_index, or from the given device tensor psi.
-        solver: "rk4" or "q2" (second-order Suzuki-Trotter, lab frame)."""
+        solver: "rk4", or the Suzuki-Trotter "q2", "q4", "q4j" (App. A; lab frame)."""
         import torch
         D, _ = self.dims()
         if psi is None:
@@ -240,7 +240,7 @@ class System:
                       frame="interaction", ckpt=0, ham=True, solver="rk4"):
         """F and the gradient w.r.t. the pulse and (ham=True) Hamiltonian parameters;
         with ham=False the Hamiltonian part is not computed and returned as None.
-        solver="q2" (lab frame) computes the pulse-parameter gradient only: pass ham=False."""
+        solver "q2" or "q4" (lab frame) computes the pulse-parameter gradient only: pass ham=False."""
         o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
         tg = _c128_pairs(target)
         F = np.zeros(2)

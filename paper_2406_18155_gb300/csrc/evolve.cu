@@ -60,6 +60,12 @@ struct TabArgs {
   double2* ph;                // 3N x sumd
   double2* tab;               // 3N x row (FP64)
   float2* tab32;              // 3N x row (FP32 copy) or null
+  // Suzuki-Trotter schedule: nsub Q2 sub-steps per step, sub-step j of length sc[j] dt with
+  // its time-dependent terms at t_n + tau[j] dt (complex for Q4j) and its coupling
+  // unitaries from set set_of[j]; set s has length setc[s] dt
+  int nsub, nset;
+  int set_of[3];
+  double2 sc[3], tau[3], setc[3];
 };
 
 __device__ double envelope_dev(const DriveDev& dr, const double* amps, int n, int j, double t) {
@@ -216,7 +222,7 @@ __global__ void k_tables32(TabArgs a, float* __restrict__ coef32, float2* __rest
 }
 
 // ---------------------------------------------------------------------------
-// Second-order Suzuki-Trotter tables (Sec. 2.3, App. A), lab frame
+// Suzuki-Trotter tables (Sec. 2.3, App. A), lab frame
 // ---------------------------------------------------------------------------
 // exp(A) of a small complex matrix (n x n, row-major) by scaling and squaring of
 // the Taylor series (Moler and Van Loan's method 3): A / 2^s with |A / 2^s|_1 <= 1/2,
@@ -260,132 +266,166 @@ __device__ void expm_serial(const double2* A, int n, double2* R, double2* W1, do
   }
 }
 
-// U_i(n) = exp(-i H_i(t_n + dt/2) dt/2), H_i = diag(E) + sum_{drives k on i} f_k O_k.
-__device__ void q2_onebody(const TabArgs& a, int i, int n, double2* U, double2* A, double2* W1, double2* W2) {
+// Drive coefficient f_k = E(t) cos(omega t + phase) at the complex time t = tr + i ti
+// inside step n: Gaussian and cosine envelopes and the carrier continued analytically,
+// a piecewise-constant envelope from the segment of the step's midpoint (R8).  For
+// ti = 0 it equals envelope_dev(dr, amps, n, 1, tr) cos(omega tr + phase) exactly.
+__device__ double2 coef_complex(const DriveDev& dr, const double* amps, int n, double tr, double ti) {
+  double2 E;
+  if (dr.kind == SG_ENV_GAUSSIAN) {
+    const double x = tr - dr.t0, y = ti, s2 = dr.sigma * dr.sigma;
+    const double mag = dr.amp * exp(-(x * x - y * y) / (2.0 * s2)), ang = -(x * y) / s2;
+    E = make_double2(mag * cos(ang), mag * sin(ang));
+  } else if (dr.kind == SG_ENV_COSINE) {
+    if (2 * n + 1 > dr.mp) return make_double2(0.0, 0.0);
+    const double a = 2.0 * M_PI * tr / dr.length, b = 2.0 * M_PI * ti / dr.length;
+    E = make_double2(dr.amp * 0.5 * (1.0 - cos(a) * cosh(b)), dr.amp * 0.5 * (sin(a) * sinh(b)));
+  } else {
+    E = make_double2(envelope_dev(dr, amps, n, 1, tr), 0.0);
+  }
+  const double a = dr.omega * tr + dr.phase, b = dr.omega * ti;
+  return cmul(E, make_double2(cos(a) * cosh(b), -(sin(a) * sinh(b))));
+}
+
+// U_i(m) = exp(A), A = -i c_j (dt/2) H_i(t_n + tau_j dt) for sub-step m = J n + j,
+// H_i = diag(E) + sum_{drives k on i} f_k O_k.  A is left in A.
+__device__ void q2_onebody(const TabArgs& a, int i, int m, double2* U, double2* A, double2* W1, double2* W2) {
   const int d = a.dims[i];
-  const double t = (double)(2 * n + 1) * a.dt * 0.5;
+  const int n = m / a.nsub, j = m - n * a.nsub;
+  const double tr = (double)(2 * n + 1) * a.dt * 0.5 + (a.tau[j].x - 0.5) * a.dt;
+  const double ti = a.tau[j].y * a.dt;
   for (int x = 0; x < d * d; ++x) A[x] = make_double2(0.0, 0.0);
   for (int x = 0; x < d; ++x) A[x * d + x].x = a.E[a.eoff[i] + x];
   for (int k = 0; k < a.K; ++k) {
     const DriveDev& dr = a.drives[k];
     if (dr.mode != i) continue;
-    const double f = envelope_dev(dr, a.amps, n, 1, t) * cos(dr.omega * t + dr.phase);
+    const double2 f = coef_complex(dr, a.amps, n, tr, ti);
     const double2* O = a.opd + a.opd_off[i] + dr.op * d * d;
-    for (int x = 0; x < d * d; ++x) { A[x].x += f * O[x].x; A[x].y += f * O[x].y; }
+    for (int x = 0; x < d * d; ++x) A[x] = cfma(f, O[x], A[x]);
   }
   const double h = a.dt * 0.5;
-  for (int x = 0; x < d * d; ++x) A[x] = make_double2(h * A[x].y, -h * A[x].x);    // -i H dt/2
+  for (int x = 0; x < d * d; ++x) {
+    const double2 cH = cmul(a.sc[j], A[x]);
+    A[x] = make_double2(h * cH.y, -h * cH.x);                                     // -i c H dt/2
+  }
   expm_serial(A, d, U, W1, W2);
 }
 
-// Row n < N: V_i(n) = U_i(n+1) U_i(n) (the second half step of step n followed by the
-// first of step n + 1); row N - 1: U_i(N - 1); row N: U_i(0).  One thread per (row, mode).
+// Row m < M - 1 (M = J N sub-steps): V_i(m) = U_i(m+1) U_i(m) (the second half of
+// sub-step m followed by the first of sub-step m + 1); row M - 1: U_i(M - 1); row M:
+// U_i(0).  One thread per (row, mode).
 __global__ void k_q2_onebody(TabArgs a, int DL, double2* __restrict__ rows) {
-  const int nrow = a.N + 1;
+  const int M = a.N * a.nsub, nrow = M + 1;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nrow * a.nq; x += gridDim.x * blockDim.x) {
-    const int n = x / a.nq, i = x - n * a.nq, d = a.dims[i];
+    const int m = x / a.nq, i = x - m * a.nq, d = a.dims[i];
     double2 U0[SG_MAXD * SG_MAXD], U1[SG_MAXD * SG_MAXD], A[SG_MAXD * SG_MAXD];
     double2 W1[SG_MAXD * SG_MAXD], W2[SG_MAXD * SG_MAXD];
-    double2* out = rows + ((size_t)n * a.nq + i) * DL * DL;
-    if (n == a.N) {
+    double2* out = rows + ((size_t)m * a.nq + i) * DL * DL;
+    if (m == M) {
       q2_onebody(a, i, 0, U0, A, W1, W2);
       for (int y = 0; y < d * d; ++y) out[y] = U0[y];
       continue;
     }
-    q2_onebody(a, i, n, U0, A, W1, W2);
-    if (n == a.N - 1) {
+    q2_onebody(a, i, m, U0, A, W1, W2);
+    if (m == M - 1) {
       for (int y = 0; y < d * d; ++y) out[y] = U0[y];
       continue;
     }
-    q2_onebody(a, i, n + 1, U1, A, W1, W2);
+    q2_onebody(a, i, m + 1, U1, A, W1, W2);
     for (int r = 0; r < d; ++r)
       for (int c = 0; c < d; ++c) {
         double2 acc = make_double2(0.0, 0.0);
-        for (int m = 0; m < d; ++m) acc = cfma(U1[r * d + m], U0[m * d + c], acc);
+        for (int q = 0; q < d; ++q) acc = cfma(U1[r * d + q], U0[q * d + c], acc);
         out[r * d + c] = acc;
       }
   }
 }
 
-// Per coupling e: G_half = exp(-i J A (x) B dt/2) and G_full = G_half^2 (the two
-// middle half steps of the palindrome), d_a d_b x d_a d_b with row index x d_b + z.
-// One thread per coupling.
+// Per set s and coupling e: G_half = exp(-i c_s J A (x) B dt/2) and G_full = G_half^2 (the
+// two middle half steps of the palindrome), d_a d_b x d_a d_b with row index x d_b + z,
+// at matrices (s ne + e) 2 + {0, 1}; their adjoints (the pull-back of the gradient) at
+// 2 ne nset + (s ne + e) 2 + {0, 1}.  One thread per (set, coupling).
 __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double2* __restrict__ scratch) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= a.p.ne) return;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int ne = a.p.ne;
+  if (x >= ne * a.nset) return;
+  const int sidx = x / ne, e = x - sidx * ne;
   const int ia = a.p.e_a[e], ib = a.p.e_b[e], da = a.dims[ia], db = a.dims[ib], n = da * db;
   const double2* Aop = a.opd + a.opd_off[ia] + a.e_opa[e] * da * da;
   const double2* Bop = a.opd + a.opd_off[ib] + a.e_opb[e] * db * db;
-  double2* M = scratch + (size_t)e * 3 * n * n;
+  double2* M = scratch + (size_t)x * 3 * n * n;
   double2* W1 = M + n * n;
   double2* W2 = W1 + n * n;
-  double2* Gh = mats + (size_t)e * 4 * DL * DL * DL * DL;
-  double2* Gf = Gh + DL * DL * DL * DL;
+  const size_t D4 = (size_t)DL * DL * DL * DL;
+  double2* Gh = mats + (size_t)x * 2 * D4;
+  double2* Gf = Gh + D4;
+  double2* Ghd = mats + ((size_t)2 * ne * a.nset + (size_t)x * 2) * D4;
+  double2* Gfd = Ghd + D4;
   const double h = a.J[e] * a.dt * 0.5;
-  for (int x = 0; x < da; ++x)
+  const double2 c = a.setc[sidx];
+  for (int xx = 0; xx < da; ++xx)
     for (int z = 0; z < db; ++z)
       for (int p = 0; p < da; ++p)
-        for (int c = 0; c < db; ++c) {
-          const double2 v = cmul(Aop[x * da + p], Bop[z * db + c]);
-          M[(x * db + z) * n + p * db + c] = make_double2(h * v.y, -h * v.x);   // -i J (A x B) dt/2
+        for (int q = 0; q < db; ++q) {
+          const double2 v = cmul(c, cmul(Aop[xx * da + p], Bop[z * db + q]));
+          M[(xx * db + z) * n + p * db + q] = make_double2(h * v.y, -h * v.x);   // -i c J (A x B) dt/2
         }
   expm_serial(M, n, Gh, W1, W2);
   for (int r = 0; r < n; ++r)
-    for (int c = 0; c < n; ++c) {
+    for (int q = 0; q < n; ++q) {
       double2 acc = make_double2(0.0, 0.0);
-      for (int m = 0; m < n; ++m) acc = cfma(Gh[r * n + m], Gh[m * n + c], acc);
-      Gf[r * n + c] = acc;
+      for (int m = 0; m < n; ++m) acc = cfma(Gh[r * n + m], Gh[m * n + q], acc);
+      Gf[r * n + q] = acc;
     }
-  // their adjoints (the pull-back of the gradient), after them
-  double2* Ghd = Gf + DL * DL * DL * DL;
-  double2* Gfd = Ghd + DL * DL * DL * DL;
   for (int r = 0; r < n; ++r)
-    for (int c = 0; c < n; ++c) {
-      Ghd[r * n + c] = cconj(Gh[c * n + r]);
-      Gfd[r * n + c] = cconj(Gf[c * n + r]);
+    for (int q = 0; q < n; ++q) {
+      Ghd[r * n + q] = cconj(Gh[q * n + r]);
+      Gfd[r * n + q] = cconj(Gf[q * n + r]);
     }
 }
 
-// Gradient tables of Q2 (pulse parameters), rows [N][nq + K][d^2]: per step n the
-// adjoint U_i(n)^dag of each mode's (unmerged) 1-body half step, then per drive k on
-// mode i, M_k(n) = U_i(n)^dag L_k(n) with L_k(n) = L(A, -i (dt/2) O_k) the Frechet
-// derivative of expm at A = -i (dt/2) H_i(t_n + dt/2), the top-right block of
-// exp([[A, E], [0, A]]) (Sec. 2.5: dU/df_k).  One thread per (n, row).
+// Gradient tables (pulse parameters), rows [J N][nq + K][d^2]: per sub-step m the
+// adjoint U_i(m)^dag of each mode's (unmerged) 1-body half step, then per drive k on
+// mode i, M_k(m) = U_i(m)^dag L_k(m) with L_k(m) = L(A, -i c_j (dt/2) O_k) the Frechet
+// derivative of expm at A = -i c_j (dt/2) H_i(t_n + tau_j dt), the top-right block of
+// exp([[A, E], [0, A]]) (Sec. 2.5: dU/df_k).  One thread per (m, row).
 constexpr int kQ2MaxD = 5;
 __global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
-  const int per = a.nq + a.K;
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < a.N * per; x += gridDim.x * blockDim.x) {
-    const int n = x / per, r = x - n * per;
+  const int per = a.nq + a.K, M = a.N * a.nsub;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < M * per; x += gridDim.x * blockDim.x) {
+    const int m = x / per, r = x - m * per;
     double2 U[SG_MAXD * SG_MAXD], A[SG_MAXD * SG_MAXD], W1[SG_MAXD * SG_MAXD], W2[SG_MAXD * SG_MAXD];
-    double2* out = rows + ((size_t)n * per + r) * DL * DL;
+    double2* out = rows + ((size_t)m * per + r) * DL * DL;
     if (r < a.nq) {
       const int i = r, d = a.dims[i];
-      q2_onebody(a, i, n, U, A, W1, W2);
+      q2_onebody(a, i, m, U, A, W1, W2);
       for (int p = 0; p < d; ++p)
         for (int c = 0; c < d; ++c) out[p * d + c] = cconj(U[c * d + p]);
       continue;
     }
     const DriveDev& dr = a.drives[r - a.nq];
-    const int i = dr.mode, d = a.dims[i], m = 2 * d;
-    if (d > kQ2MaxD) continue;                      // the on-chip Q2 plan has d <= 5
-    q2_onebody(a, i, n, U, A, W1, W2);              // U_i(n), and A = -i (dt/2) H_i on return
+    const int i = dr.mode, d = a.dims[i], mm = 2 * d;
+    if (d > kQ2MaxD) continue;                      // the on-chip Suzuki-Trotter plan has d <= 5
+    q2_onebody(a, i, m, U, A, W1, W2);              // U_i(m), and A = -i c (dt/2) H_i on return
     constexpr int MM = 4 * kQ2MaxD * kQ2MaxD;
     double2 Z[MM], RZ[MM], Z1[MM], Z2[MM];
     const double2* O = a.opd + a.opd_off[i] + dr.op * d * d;
     const double h = a.dt * 0.5;
-    for (int p = 0; p < m * m; ++p) Z[p] = make_double2(0.0, 0.0);
+    const double2 c = a.sc[m % a.nsub];
+    for (int p = 0; p < mm * mm; ++p) Z[p] = make_double2(0.0, 0.0);
     for (int p = 0; p < d; ++p)
-      for (int c = 0; c < d; ++c) {
-        Z[p * m + c] = A[p * d + c];
-        Z[(p + d) * m + c + d] = A[p * d + c];
-        Z[p * m + c + d] = make_double2(h * O[p * d + c].y, -h * O[p * d + c].x);   // -i (dt/2) O
+      for (int q = 0; q < d; ++q) {
+        Z[p * mm + q] = A[p * d + q];
+        Z[(p + d) * mm + q + d] = A[p * d + q];
+        const double2 cO = cmul(c, O[p * d + q]);
+        Z[p * mm + q + d] = make_double2(h * cO.y, -h * cO.x);                 // -i c (dt/2) O
       }
-    expm_serial(Z, m, RZ, Z1, Z2);
+    expm_serial(Z, mm, RZ, Z1, Z2);
     for (int p = 0; p < d; ++p)                     // M = U^dag L
-      for (int c = 0; c < d; ++c) {
+      for (int q = 0; q < d; ++q) {
         double2 acc = make_double2(0.0, 0.0);
-        for (int q = 0; q < d; ++q) acc = cfma(cconj(U[q * d + p]), RZ[q * m + c + d], acc);
-        out[p * d + c] = acc;
+        for (int w = 0; w < d; ++w) acc = cfma(cconj(U[w * d + p]), RZ[w * mm + q + d], acc);
+        out[p * d + q] = acc;
       }
   }
 }
@@ -854,9 +894,13 @@ __global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* 
 
 // Pulse-parameter chain, one block per drive: dF/dparam = sum over stages of
 // dF/df * df/dparam, and the carrier-frequency co-gradient sum dF/df * E (-sin) t.
+// J = 0: the 3N RK4 stage slots (stage j of step n at t = (2n + j) dt/2); J >= 1: the
+// J N Suzuki-Trotter sub-steps (sub-step j of step n at t_n + tau_j dt, its envelope
+// taken as at the step's midpoint stage, reading R8).
+struct SubTimes { double tau[3]; };
 __global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const double* gF,
                               int K, int N, double dt, const int* pulse_off, int n_pulse, double* grad_pulse,
-                              double* omega_bar) {
+                              double* omega_bar, int J, SubTimes sub) {
   const int k = blockIdx.x;
   const DriveDev dr = drives[k];
   const int np = dr.kind == SG_ENV_PWC ? dr.nseg : 1;
@@ -864,9 +908,11 @@ __global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const 
   const int tid = threadIdx.x;
   double* mine = part + tid * (np + 1);
   for (int x = 0; x <= np; ++x) mine[x] = 0.0;
-  for (int q = tid; q < 3 * N; q += blockDim.x) {
-    const int n = q / 3, j = q % 3;
-    const double t = (double)(2 * n + j) * dt * 0.5;
+  const int per = J > 0 ? J : 3;
+  for (int q = tid; q < per * N; q += blockDim.x) {
+    const int n = q / per, jq = q % per;
+    const int j = J > 0 ? 1 : jq;
+    const double t = J > 0 ? (double)(2 * n + 1) * dt * 0.5 + (sub.tau[jq] - 0.5) * dt : (double)(2 * n + j) * dt * 0.5;
     const double g = gF[(size_t)q * K + k];
     const double c = cos(dr.omega * t + dr.phase);
     const double E = envelope_dev(dr, amps, n, j, t);
@@ -999,11 +1045,44 @@ struct Setup {
   std::vector<int> s1_of_mode;
   std::vector<int> pulse_off;
   int n_pulse = 0;
-  bool q2 = false;                // second-order Suzuki-Trotter solver (lab frame)
+  bool q2 = false;                // a Suzuki-Trotter solver (Q2, Q4, Q4j; lab frame)
+  int solver = SG_SOLVER_RK4;
   int frame = SG_FRAME_INTERACTION;
   int nqb = 0;                    // qubit modes (the rest are couplers)
   int qpos[SG_MAXQ] = {0};        // bit of mode i in a comp label (LSB = 0), -1 for a coupler
 };
+
+// The Suzuki-Trotter schedules of App. A as Q2 sub-steps (c dt at t_n + tau dt):
+// Q2 (1, 1/2); Q4 (p, p/2), (1 - 2p, 1/2), (p, 1 - p/2) with p = 1 / (2 - 2^(1/3));
+// Q4j (p, p/2), (p*, p + p*/2) with p = (3 - i sqrt 3) / 6, the complex sub-step times
+// of Q4j being where its drive coefficients are continued (coef_complex).
+void set_schedule(int solver, TabArgs& ta) {
+  const double p4 = 1.0 / (2.0 - std::cbrt(2.0));
+  const double2 pj = make_double2(0.5, -std::sqrt(3.0) / 6.0);
+  const double2 pjc = make_double2(pj.x, -pj.y);
+  if (solver == SG_SOLVER_Q4) {
+    ta.nsub = 3; ta.nset = 2;
+    ta.sc[0] = ta.sc[2] = make_double2(p4, 0.0);
+    ta.sc[1] = make_double2(1.0 - 2.0 * p4, 0.0);
+    ta.tau[0] = make_double2(p4 / 2.0, 0.0);
+    ta.tau[1] = make_double2(0.5, 0.0);
+    ta.tau[2] = make_double2(1.0 - p4 / 2.0, 0.0);
+    ta.set_of[0] = ta.set_of[2] = 0; ta.set_of[1] = 1;
+    ta.setc[0] = ta.sc[0]; ta.setc[1] = ta.sc[1];
+  } else if (solver == SG_SOLVER_Q4J) {
+    ta.nsub = 2; ta.nset = 2;
+    ta.sc[0] = pj; ta.sc[1] = pjc;
+    ta.tau[0] = make_double2(pj.x / 2.0, pj.y / 2.0);
+    ta.tau[1] = make_double2(pj.x + pjc.x / 2.0, pj.y + pjc.y / 2.0);
+    ta.set_of[0] = 0; ta.set_of[1] = 1;
+    ta.setc[0] = pj; ta.setc[1] = pjc;
+  } else {
+    ta.nsub = 1; ta.nset = 1;
+    ta.sc[0] = ta.setc[0] = make_double2(1.0, 0.0);
+    ta.tau[0] = make_double2(0.5, 0.0);
+    ta.set_of[0] = 0;
+  }
+}
 
 sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
   sg_ctx* ctx = sys->ctx;
@@ -1019,10 +1098,12 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
     return sg_fail(ctx, SG_E_INVALID, "precision must be SG_FP64 or SG_MIXED");
   if (o->frame != SG_FRAME_INTERACTION && o->frame != SG_FRAME_LAB)
     return sg_fail(ctx, SG_E_INVALID, "frame must be SG_FRAME_INTERACTION or SG_FRAME_LAB");
-  if (o->solver != SG_SOLVER_RK4 && o->solver != SG_SOLVER_Q2)
-    return sg_fail(ctx, SG_E_INVALID, "solver must be SG_SOLVER_RK4 or SG_SOLVER_Q2");
-  s.q2 = o->solver == SG_SOLVER_Q2;
-  s.frame = s.q2 ? SG_FRAME_LAB : o->frame;          // Q2 always runs in the lab frame
+  if (o->solver != SG_SOLVER_RK4 && o->solver != SG_SOLVER_Q2 && o->solver != SG_SOLVER_Q4 &&
+      o->solver != SG_SOLVER_Q4J)
+    return sg_fail(ctx, SG_E_INVALID, "solver must be SG_SOLVER_RK4, SG_SOLVER_Q2, SG_SOLVER_Q4 or SG_SOLVER_Q4J");
+  s.solver = o->solver;
+  s.q2 = o->solver != SG_SOLVER_RK4;
+  s.frame = s.q2 ? SG_FRAME_LAB : o->frame;          // Suzuki-Trotter always runs in the lab frame
   if (o->ncols < 1) return sg_fail(ctx, SG_E_INVALID, "ncols must be >= 1");
   s.N = (int)N;
   s.dt = o->dt;
@@ -1132,6 +1213,7 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
   for (int i = 0; i < s.nq; ++i) { ta.dims[i] = p.dims[i]; ta.eoff[i] = eoff[i]; ta.opd_off[i] = ooff[i]; }
   ta.sumd = s.sumd;
   ta.dt = o->dt;
+  set_schedule(s.solver, ta);
   return SG_OK;
 }
 
@@ -1283,22 +1365,25 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   s.ta = ta;
   if (s.q2) {
     const int DL = onchip_dl(sv.oc);
-    const size_t nrow = (size_t)(s.N + 1) * s.nq * DL * DL, nedge = (size_t)std::max(1, s.p.ne) * 4 * DL * DL * DL * DL;
+    const long long M = (long long)s.N * ta.nsub;                  // Q2 sub-steps
+    const int nset = ta.nset, ne1 = std::max(1, s.p.ne);
+    const size_t D4 = (size_t)DL * DL * DL * DL;
+    const size_t nrow = (size_t)(M + 1) * s.nq * DL * DL, nedge = (size_t)4 * ne1 * nset * D4;
     double2* rows = sv.ar.get<double2>(nrow);
     double2* edges = sv.ar.get<double2>(nedge);
-    double2* scratch = sv.ar.get<double2>((size_t)std::max(1, s.p.ne) * 3 * DL * DL * DL * DL);
+    double2* scratch = sv.ar.get<double2>((size_t)ne1 * nset * 3 * D4);
     if (!rows || !edges || !scratch) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 tables failed");
-    k_q2_onebody<<<grid_for((long long)(s.N + 1) * s.nq), kT, 0, st>>>(ta, DL, rows);
-    if (s.p.ne) k_q2_edges<<<(s.p.ne + 31) / 32, 32, 0, st>>>(ta, DL, edges, scratch);
+    k_q2_onebody<<<grid_for((M + 1) * s.nq), kT, 0, st>>>(ta, DL, rows);
+    if (s.p.ne) k_q2_edges<<<(s.p.ne * nset + 31) / 32, 32, 0, st>>>(ta, DL, edges, scratch);
     sv.launches += 2;
     sv.q2rows = rows;
     sv.q2edges = edges;
-    const size_t ngr = grad ? (size_t)s.N * (s.nq + s.K) * DL * DL : 0;
+    const size_t ngr = grad ? (size_t)M * (s.nq + s.K) * DL * DL : 0;
     double2* gtab = nullptr;
     if (grad) {
       gtab = sv.ar.get<double2>(ngr);
       if (!gtab) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 gradient tables failed");
-      k_q2_gradtabs<<<grid_for((long long)s.N * (s.nq + s.K)), 64, 0, st>>>(ta, DL, gtab);
+      k_q2_gradtabs<<<grid_for(M * (s.nq + s.K)), 64, 0, st>>>(ta, DL, gtab);
       ++sv.launches;
       sv.q2grad = gtab;
     }
@@ -1681,8 +1766,9 @@ sg_status run_q2(sg_system* sys, Solve& sv, const long long* cols_dev, bool init
     k_init_cols<<<grid_for(s.D * s.S), kT, 0, st>>>(sv.psi, s.D, s.S, cols_dev);
     ++sv.launches;
   }
-  sg_status rc = onchip_q2_forward(sv.oc, s.p, sv.q2rows, sv.q2edges, sv.psi, sv.psi, s.N, st, &sv.launches);
-  if (rc != SG_OK) return sg_fail(ctx, rc, "the Q2 solver supports at most 16 modes and 32 couplings");
+  sg_status rc = onchip_q2_forward(sv.oc, s.p, sv.q2rows, sv.q2edges, sv.psi, sv.psi, s.N * s.ta.nsub, s.ta.nsub,
+                                   s.ta.set_of, s.ta.nset, st, &sv.launches);
+  if (rc != SG_OK) return sg_fail(ctx, rc, "the Suzuki-Trotter solvers support at most 16 modes and 32 couplings");
   SG_CUDA_TRY(ctx, cudaGetLastError());
   return SG_OK;
 }
@@ -1702,8 +1788,14 @@ sg_status run_backward_q2(sg_system* sys, Solve& sv, double2* pbar, GradAcc acc)
   SG_CUDA_TRY(ctx, cudaMemsetAsync(gFc, 0, (size_t)ncta * nst * Kd * sizeof(double), st));
   int drv_mode[SG_MAXDRIVE];
   for (int k = 0; k < s.K; ++k) drv_mode[k] = s.drives[k].mode;
-  sg_status rc = onchip_q2_pulse_adjoint(sv.oc, s.p, drv_mode, s.K, sv.q2grad, sv.q2edges, sv.psi, pbar, s.N, gFc,
-                                         st, &sv.launches);
+  // the adjoint coupling unitaries follow the forward ones (2 ne nset matrices)
+  const size_t es = sv.mixed ? sizeof(float2) : sizeof(double2);
+  const int DL = onchip_dl(sv.oc);
+  const void* adj_edges = static_cast<const char*>(sv.q2edges) +
+                          (size_t)2 * std::max(1, s.p.ne) * s.ta.nset * DL * DL * DL * DL * es;
+  sg_status rc = onchip_q2_pulse_adjoint(sv.oc, s.p, drv_mode, s.K, sv.q2grad, adj_edges, sv.psi, pbar,
+                                         s.N * s.ta.nsub, s.ta.nsub, s.ta.set_of, s.ta.nset, nst * Kd, gFc, st,
+                                         &sv.launches);
   if (rc != SG_OK)
     return sg_fail(ctx, rc, "the Q2 gradient needs 2..16 modes, <= 32 couplings, <= 16 drives and its buffers "
                             "in shared memory");
@@ -1770,7 +1862,10 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   Setup& s = sv.s;
   if (s.nqb < 1 || s.nqb > 12) return sg_fail(ctx, SG_E_UNSUPPORTED, "fidelity needs 1..12 qubit (non-coupler) modes");
   if (s.q2 && grad && grad_ham)
-    return sg_fail(ctx, SG_E_UNSUPPORTED, "the Q2 solver computes the pulse-parameter gradient only (grad_ham = NULL)");
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter solvers compute the pulse-parameter gradient only "
+                                          "(grad_ham = NULL)");
+  if (grad && s.solver == SG_SOLVER_Q4J)
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "Q4j's factors are not unitary: its gradient is not computed");
   for (int i = 0; i < s.nq; ++i)
     if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
       return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");
@@ -1916,8 +2011,11 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
       int np_max = 1;
       for (auto& d : s.drives) np_max = std::max(np_max, d.kind == SG_ENV_PWC ? d.nseg : 1);
       const int pt = 64;
+      SubTimes sub{};
+      for (int j = 0; j < s.ta.nsub; ++j) sub.tau[j] = s.ta.tau[j].x;
       k_pulse_chain<<<s.K, pt, pt * (np_max + 1) * sizeof(double), st>>>(
-          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar);
+          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar, s.q2 ? s.ta.nsub : 0,
+          sub);
     } else {
       SG_CUDA_TRY(ctx, cudaMemsetAsync(omega_bar, 0, sizeof(double), st));
     }

@@ -627,6 +627,8 @@ struct Q2Args {
   int nf0;                        // 1-body factors (applied first with the initial row,
                                   // and at the end of every step)
   int nfe;                        // coupling factors per step
+  int J;                          // Q2 sub-steps per step (Q2 1, Q4 3, Q4j 2)
+  int setoff[3];                  // sub-step j's coupling unitaries: 2 ne set(j) matrices in
   Q2Factor f[kMaxQ2F];            // [0, nf0): 1-body; [nf0, nf0 + nfe): couplings in order
 };
 
@@ -669,11 +671,11 @@ __device__ __forceinline__ void q2_apply(const Q2Factor& F, int mat, const OcArg
   __syncthreads();
 }
 
-// N steps of Q2 for the CTA's columns, lab frame.  rows: (N + 1) x nq x d^2 1-body
-// unitaries (row N = the first half step, row n = the last half step of step n merged
-// with the first of step n + 1); edges: per coupling the half-step and the full-step
-// (middle) unitary.  Per step: couplings 0 .. ne-2 (half), ne-1 (full), ne-2 .. 0
-// (half), then the 1-body row n.
+// N Q2 sub-steps for the CTA's columns, lab frame.  rows: (N + 1) x nq x d^2 1-body
+// unitaries (row N = the first half of sub-step 0, row n = the last half of sub-step n
+// merged with the first of sub-step n + 1); edges: per coupling set (one per distinct
+// sub-step length) and coupling the half-step and the full-step (middle) unitary.  Per
+// sub-step: couplings 0 .. ne-2 (half), ne-1 (full), ne-2 .. 0 (half), then row n.
 template <typename R, int DL>
 __global__ void __launch_bounds__(kST, 1)
 k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__ rows,
@@ -710,11 +712,12 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
   int buf = 1;
   for (int n = 0; n < N; ++n) {
     C* const Mc = buf ? M1 : M0;
+    const int so = qa.setoff[n % qa.J];
     if (n + 1 < N) issue_rows<C>(rows, rowlen, n + 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
     for (int q = 0; q < 2 * qa.nfe - 1; ++q) {
       const int e = q < qa.nfe ? q : 2 * qa.nfe - 2 - q;             // palindrome over couplings
       const Q2Factor& F = qa.f[qa.nf0 + e];
-      q2_apply<DL>(F, F.mat + (q == qa.nfe - 1 ? 1 : 0), oa, Mc, G, ys, ks);   // middle: full step
+      q2_apply<DL>(F, F.mat + so + (q == qa.nfe - 1 ? 1 : 0), oa, Mc, G, ys, ks);   // middle: full step
       C* t = ys; ys = ks; ks = t;
     }
     for (int q = 0; q < qa.nf0; ++q) {
@@ -745,12 +748,14 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
 //                                         = Re sum_ab M_k[a][b] C_i[a][b],
 // M_k = U_i^dag L_k and C_i[a][b] = sum conj(psibar_before[a, ..]) psi_before[b, ..]
 // the cross-density over mode i.  Each thread contracts its blocks' cross-densities
-// with M_k at once, so a step reduces one scalar per drive over the CTA (warp
-// shuffles, then the warps in fixed order) into stage slot 3n + 1 of the CTA's gF
+// with M_k at once, so a sub-step reduces one scalar per drive over the CTA (warp
+// shuffles, then the warps in fixed order) into slot n (the sub-step) of the CTA's gF
 // block.  The 1-body factors are applied as Kronecker pairs like the forward.
 constexpr int kQ2G = 16;          // drives of a Q2 gradient solve (per-thread partials)
 struct Q2AdjArgs {
   int nq, K, ne, n1f;             // modes, drives, couplings, 1-body factors of a half step
+  int J;                          // Q2 sub-steps per step
+  int setoff[3];                  // sub-step j's adjoint coupling unitaries: 2 ne set(j) matrices in
   int row;                        // (nq + K) d^2: U_i(n)^dag then M_k(n)
   unsigned driven;                // bit i: a drive acts on mode i
   Phase one[SG_MAXQ / 2 + 1];     // pairs (offL, offR) and an odd last mode (offA)
@@ -796,6 +801,7 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
   for (int n = N - 1; n >= 0; --n) {
     const C* U = buf ? M1 : M0;
     const C* Mk = U + qa.nq * DL * DL;
+    const int so = qa.setoff[n % qa.J];
     if (n > 0) issue_rows<C>(rows, qa.row, n - 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
     R g[kQ2G];
 #pragma unroll
@@ -804,7 +810,7 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
       if (h == 1) {                                                  // couplings (palindrome)
         for (int q = 0; q < 2 * qa.ne - 1; ++q) {
           const int e = q < qa.ne ? q : 2 * qa.ne - 2 - q;
-          const C* Gd = G + (size_t)(4 * e + (q == qa.ne - 1 ? 3 : 2)) * DL * DL * DL * DL;
+          const C* Gd = G + (size_t)(so + 2 * e + (q == qa.ne - 1 ? 1 : 0)) * DL * DL * DL * DL;
           const Phase& P = qa.edge[e];
           for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
             const int c = b / oa.nbc;
@@ -867,7 +873,7 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
     if (threadIdx.x < qa.K) {
       double sacc = 0.0;
       for (int w = 0; w < kST / 32; ++w) sacc += red[w * kQ2G + threadIdx.x];
-      gFc[(size_t)(3 * n + 1) * qa.K + threadIdx.x] += sacc;
+      gFc[(size_t)n * qa.K + threadIdx.x] += sacc;
     }
     buf ^= 1;
   }
@@ -1191,11 +1197,11 @@ namespace {
 
 template <typename R, int DL>
 int q2_t(const OnchipPlan* oc, const Q2Args& qa, const void* rows, const void* edges, const double2* psi_in,
-         double2* psi_out, int N, int rowlen, int ne, cudaStream_t st) {
+         double2* psi_out, int N, int rowlen, int nmat, cudaStream_t st) {
   typedef typename CT<R>::T C;
   smem_limit_once<k_oc_q2<R, DL>>();
   // coupling unitaries in shared memory when they fit, else read from global memory
-  const int nedge = 4 * std::max(0, ne) * DL * DL * DL * DL;
+  const int nedge = nmat * DL * DL * DL * DL;
   const size_t gbytes = (size_t)nedge * sizeof(C);
   const bool gsm = oc->oa.q_G + gbytes <= oc->limit;
   const size_t smem = oc->oa.q_G + (gsm ? gbytes : 0);
@@ -1207,10 +1213,11 @@ int q2_t(const OnchipPlan* oc, const Q2Args& qa, const void* rows, const void* e
 }  // namespace
 
 sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
-                            const double2* psi_in, double2* psi_out, int N, cudaStream_t st, int* launches) {
+                            const double2* psi_in, double2* psi_out, int N, int J, const int* set_of, int nset,
+                            cudaStream_t st, int* launches) {
   const SlabPass& sp = oc->h->pass[0];
   const int DL = oc->h->DL;
-  if (p.nq > 2 * 8 || p.ne > kMaxQ2F - 8) return SG_E_UNSUPPORTED;
+  if (p.nq > 2 * 8 || p.ne > kMaxQ2F - 8 || J < 1 || J > 3) return SG_E_UNSUPPORTED;
   if (p.nq * DL * DL > oc->oa.rowA) return SG_E_UNSUPPORTED;        // 1-body row must fit the row buffer
   Q2Args qa{};
   // 1-body factors: modes in pairs (Kronecker L (x) R), an odd last mode alone
@@ -1231,23 +1238,26 @@ sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* ro
     Q2Factor& F = qa.f[qa.nf0 + qa.nfe++];
     F.P = make_phase(sp, DL, p.e_a[e], p.e_b[e]);
     F.kind = 2;
-    F.mat = 4 * e;                // per coupling: half, full, half^dag, full^dag
+    F.mat = 2 * e;                // per set and coupling: half, full
   }
+  qa.J = J;
+  for (int j = 0; j < J; ++j) qa.setoff[j] = 2 * p.ne * set_of[j];
   const int rowlen = p.nq * DL * DL;
+  const int nmat = 2 * p.ne * nset;
   int n = 0;
   if (oc->mixed) {
     switch (DL) {
-      case 2: n = q2_t<float, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
-      case 3: n = q2_t<float, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
-      case 4: n = q2_t<float, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
-      default: n = q2_t<float, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      case 2: n = q2_t<float, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
+      case 3: n = q2_t<float, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
+      case 4: n = q2_t<float, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
+      default: n = q2_t<float, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
     }
   } else {
     switch (DL) {
-      case 2: n = q2_t<double, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
-      case 3: n = q2_t<double, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
-      case 4: n = q2_t<double, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
-      default: n = q2_t<double, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, p.ne, st); break;
+      case 2: n = q2_t<double, 2>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
+      case 3: n = q2_t<double, 3>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
+      case 4: n = q2_t<double, 4>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
+      default: n = q2_t<double, 5>(oc, qa, rows, edges, psi_in, psi_out, N, rowlen, nmat, st); break;
     }
   }
   if (launches) *launches += n;
@@ -1260,10 +1270,10 @@ namespace {
 
 template <typename R, int DL>
 int q2adj_t(const OnchipPlan* oc, const Q2AdjArgs& qa, const void* rows, const void* edges, const double2* psi,
-            const double2* bar, int N, double* gF_cta, long long nstK, cudaStream_t st) {
+            const double2* bar, int N, int nset, double* gF_cta, long long nstK, cudaStream_t st) {
   typedef typename CT<R>::T C;
   smem_limit_once<k_oc_q2_adj<R, DL>>();
-  const int nedge = 4 * qa.ne * DL * DL * DL * DL;
+  const int nedge = 2 * qa.ne * nset * DL * DL * DL * DL;
   const bool gsm = oc->oa.b_G + (size_t)nedge * sizeof(C) <= oc->limit;
   const size_t smem = oc->oa.b_G + (gsm ? (size_t)nedge * sizeof(C) : 0);
   k_oc_q2_adj<R, DL><<<oc->oa.ncta, kST, smem, st>>>(oc->h->pass[0], oc->oa, qa, (const C*)rows, (const C*)edges,
@@ -1274,11 +1284,13 @@ int q2adj_t(const OnchipPlan* oc, const Q2AdjArgs& qa, const void* rows, const v
 }  // namespace
 
 sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
-                                  const void* edges, const double2* psi, const double2* bar, int N, double* gF_cta,
-                                  cudaStream_t st, int* launches) {
+                                  const void* edges, const double2* psi, const double2* bar, int N, int J,
+                                  const int* set_of, int nset, long long nstK, double* gF_cta, cudaStream_t st,
+                                  int* launches) {
   const SlabPass& sp = oc->h->pass[0];
   const int DL = oc->h->DL;
-  if ((size_t)oc->oa.b_G > oc->limit || p.nq < 2 || p.ne > 32 || K > kQ2G || K != oc->oa.K)
+  if ((size_t)oc->oa.b_G > oc->limit || p.nq < 2 || p.ne > 32 || K > kQ2G || K != oc->oa.K || J < 1 || J > 3 ||
+      (long long)N * std::max(1, K) > nstK)
     return SG_E_UNSUPPORTED;
   if (p.nq * DL * DL > oc->oa.rowA) return SG_E_UNSUPPORTED;
   Q2AdjArgs qa{};
@@ -1303,21 +1315,22 @@ sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const in
     qa.drv_mode[k] = drv_mode[k];
     qa.driven |= 1u << drv_mode[k];
   }
-  const long long nstK = 3ll * N * std::max(1, K);
+  qa.J = J;
+  for (int j = 0; j < J; ++j) qa.setoff[j] = 2 * p.ne * set_of[j];
   int n = 0;
   if (oc->mixed) {
     switch (DL) {
-      case 2: n = q2adj_t<float, 2>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
-      case 3: n = q2adj_t<float, 3>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
-      case 4: n = q2adj_t<float, 4>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
-      default: n = q2adj_t<float, 5>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      case 2: n = q2adj_t<float, 2>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
+      case 3: n = q2adj_t<float, 3>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
+      case 4: n = q2adj_t<float, 4>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
+      default: n = q2adj_t<float, 5>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
     }
   } else {
     switch (DL) {
-      case 2: n = q2adj_t<double, 2>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
-      case 3: n = q2adj_t<double, 3>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
-      case 4: n = q2adj_t<double, 4>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
-      default: n = q2adj_t<double, 5>(oc, qa, rows, edges, psi, bar, N, gF_cta, nstK, st); break;
+      case 2: n = q2adj_t<double, 2>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
+      case 3: n = q2adj_t<double, 3>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
+      case 4: n = q2adj_t<double, 4>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
+      default: n = q2adj_t<double, 5>(oc, qa, rows, edges, psi, bar, N, nset, gF_cta, nstK, st); break;
     }
   }
   if (launches) *launches += n;

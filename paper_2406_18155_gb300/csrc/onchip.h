@@ -71,22 +71,26 @@ bool onchip_mixed(const OnchipPlan* oc);
 void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc_cta, long long nst, int K,
                    int n1, int ne, GradAcc acc, cudaStream_t st);
 
-// Second-order Suzuki-Trotter evolution (Sec. 2.3, App. A) of N steps, lab frame, from
-// psi_in to psi_out (API layout, may alias).  rows: (N + 1) x nq x d^2 1-body unitaries
-// of the stage precision (row N = the first half step; row n = the last half step of
-// step n followed by the first of step n + 1); edges: per coupling its half-step and
-// full-step d^2 x d^2 unitaries.  SG_E_UNSUPPORTED beyond 16 modes or 32 couplings.
+// Suzuki-Trotter evolution (Sec. 2.3, App. A) of N Q2 sub-steps, lab frame, from psi_in
+// to psi_out (API layout, may alias).  rows: (N + 1) x nq x d^2 1-body unitaries of the
+// stage precision (row N = the first half of sub-step 0; row n = the last half of
+// sub-step n followed by the first of sub-step n + 1); edges: per set s < nset and
+// coupling e the half-step and full-step d^2 x d^2 unitaries at matrix (s ne + e) 2 + {0, 1};
+// sub-step n uses set set_of[n % J].  SG_E_UNSUPPORTED beyond 16 modes or 32 couplings.
 sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
-                            const double2* psi_in, double2* psi_out, int N, cudaStream_t st, int* launches);
+                            const double2* psi_in, double2* psi_out, int N, int J, const int* set_of, int nset,
+                            cudaStream_t st, int* launches);
 int onchip_dl(const OnchipPlan* oc);
-// Q2 pulse gradient: pulls the final states psi and the co-state bar (API layout, lab
-// frame) back through every factor and adds dF/df_k at the midpoint of step n to
-// gF_cta (CTA-major, 3N x K each, slot 3n + 1; zeroed by the caller).  rows:
-// [N][nq + K][d^2], per step the adjoint 1-body half-step unitaries U_i(n)^dag, then
-// M_k(n) = U_i(n)^dag L_k(n) with L_k the Frechet derivative of the local exponential
-// along drive k's operator; edges: per coupling half, full, half^dag, full^dag.
-// SG_E_UNSUPPORTED for one mode, more than 32 couplings or 16 drives, or when the
-// layout does not fit in shared memory.
+// Suzuki-Trotter pulse gradient: pulls the final states psi and the co-state bar (API
+// layout, lab frame) back through every factor of the N Q2 sub-steps and adds dF/df_k
+// at sub-step n to gF_cta (CTA-major blocks of nstK >= N K doubles, slot n K + k;
+// zeroed by the caller).  rows: [N][nq + K][d^2], per sub-step the adjoint 1-body
+// half-step unitaries U_i(n)^dag, then M_k(n) = U_i(n)^dag L_k(n) with L_k the Frechet
+// derivative of the local exponential along drive k's operator; edges: the adjoint
+// coupling unitaries (half^dag, full^dag) in the forward's set layout.  Unitary factors
+// only (the inverse of a factor is its adjoint).  SG_E_UNSUPPORTED for one mode, more
+// than 32 couplings or 16 drives, or when the layout does not fit in shared memory.
 sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
-                                  const void* edges, const double2* psi, const double2* bar, int N, double* gF_cta,
-                                  cudaStream_t st, int* launches);
+                                  const void* edges, const double2* psi, const double2* bar, int N, int J,
+                                  const int* set_of, int nset, long long nstK, double* gF_cta, cudaStream_t st,
+                                  int* launches);

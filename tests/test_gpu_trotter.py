@@ -1,9 +1,9 @@
-"""GPU parity of the second-order Suzuki-Trotter solver (Sec. 2.3, App. A) against
-the oracle's Q2: lab-frame states and fidelities, FP64 within 1e-10, FP32 factors
-and state within 1e-5 on short evolutions; the pulse-parameter gradient (discrete
-adjoint of the product of unitaries, Sec. 2.5) against the oracle's adjoint, FP64
-within 1e-9 and FP32 within 2e-4 of the largest component; unsupported requests
-are rejected."""
+"""GPU parity of the Suzuki-Trotter solvers (Sec. 2.3, App. A: Q2, Q4, Q4j) against
+the oracle's: lab-frame states and fidelities, FP64 within 1e-10, FP32 factors and
+state within 1e-5 on short evolutions; the pulse-parameter gradient of Q2 and Q4
+(discrete adjoint of the product of unitaries, Sec. 2.5) against the oracle's
+adjoint, FP64 within 1e-9 and FP32 within 2e-4 of the largest component;
+unsupported requests are rejected."""
 import numpy as np
 import pytest
 
@@ -114,3 +114,40 @@ def test_q2_pulse_gradient_longer_evolution(sgctx, default_path):
         F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
                                    precision=prec, ham=False, solver="q2")
         assert np.max(np.abs(gp - g_r)) < tol * scale, (prec, np.max(np.abs(gp - g_r)), scale)
+
+
+@pytest.mark.parametrize("scheme", ["q4", "q4j"])
+@pytest.mark.parametrize("name", ["transmon_pair", "chain3_l3", "pair_cr_l5", "ftf_l4"])
+def test_fourth_order_products_match_oracle(sgctx, default_path, name, scheme):
+    wl = CASES[name]()
+    s = _system(sgctx, wl)
+    so = OracleSystem(dict(wl, frame="lab"))
+    ref = q2_evolve(so, initial_columns(so, wl["col_index"]), scheme=scheme)
+    psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver=scheme).cpu().numpy()
+    assert np.max(np.abs(psi - ref)) < 1e-10
+    psi32 = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"], solver=scheme).cpu().numpy()
+    assert np.max(np.abs(psi32 - ref)) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["transmon_pair", "ring4_l3", "pair_cr_l5", "local_ops_l3"])
+def test_q4_pulse_gradient_matches_oracle(sgctx, default_path, name):
+    wl = CASES[name]()
+    s = _system(sgctx, wl)
+    F_r, g_r = q2_pulse_gradient(wl, scheme="q4")
+    scale = max(1.0, np.max(np.abs(g_r)))
+    for prec, tol_F, tol_g in (("fp64", 1e-10, 1e-9), ("mixed", 1e-5, 2e-4)):
+        F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
+                                   precision=prec, ham=False, solver="q4")
+        Fk = F[0] if wl["fid_kind"] == "avg" else F[1]
+        assert abs(Fk - F_r) < tol_F, (prec, Fk, F_r)
+        assert np.max(np.abs(gp - g_r)) < tol_g * scale, (prec, np.max(np.abs(gp - g_r)), scale)
+
+
+def test_q4j_gradient_is_refused(sgctx, default_path):
+    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
+    wl = CASES["transmon_pair"]()
+    s = _system(sgctx, wl)
+    with pytest.raises(SGError) as e:
+        s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
+                        precision="fp64", ham=False, solver="q4j")
+    assert e.value.code == SG_E_UNSUPPORTED
