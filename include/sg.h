@@ -187,7 +187,18 @@ typedef struct {
   const long long* col_index;   /* host, S flat initial basis indices, or NULL: the
                                    columns of psi are the initial states                  */
   int solver;                   /* SG_SOLVER_RK4 (0, default), _Q2, _Q4 or _Q4J            */
+  int compensation;             /* SG_COMP_NONE (0, default) or SG_COMP_VZ (fidelities)    */
 } sg_evolve_opts;
+
+/* Compensation of the gate fidelity (sg_fidelity, sg_fidelity_grad): the paper's gate
+ * metric assumes errorless single-qubit gates around the pulses.  SG_COMP_VZ takes
+ * M = T^dag Z(a) U Z(b) with a virtual Z gate diag(1, e^{i phase}) on every qubit
+ * before and after, the phases maximising |tr M| (coordinate ascent from zero phases,
+ * qubit by qubit, each phase set to its exact maximiser, until a sweep does not raise
+ * |tr M|, at most 2000 sweeps); F_avg and F_state are those of M.  Needs every
+ * computational state evolved exactly once (D_c <= 256), else SG_E_INVALID.  The
+ * gradient is that of F at the found phases (F is stationary in them). */
+enum { SG_COMP_NONE = 0, SG_COMP_VZ = 1 };
 
 /* Solvers.  SG_SOLVER_Q2: the second-order Suzuki-Trotter product of Sec. 2.3 and
  * App. A, Q2(dt) = prod_k exp(-i H_k dt/2) prod_k' exp(-i H_k' dt/2) (k' reversed)

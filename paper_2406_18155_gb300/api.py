@@ -52,14 +52,17 @@ class Context:
 
 
 _SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q2": capi.SG_SOLVER_Q2, "q4": capi.SG_SOLVER_Q4, "q4j": capi.SG_SOLVER_Q4J}
+_COMP = {"none": capi.SG_COMP_NONE, "vz": capi.SG_COMP_VZ}
 
 
-def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None, solver="rk4"):
+def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None, solver="rk4",
+                compensation="none"):
     o = capi.sg_evolve_opts()
     o.T, o.dt = float(T), float(dt)
     o.precision = _PREC[precision]
     o.frame = _FRAME[frame]
     o.solver = _SOLVER[solver]
+    o.compensation = _COMP[compensation]
     keep = None
     if col_index is not None:
         keep = np.ascontiguousarray(np.asarray(col_index, dtype=np.int64))
@@ -227,8 +230,11 @@ class System:
         self._chk(lib().sg_evolve(self.h, C.byref(o), C.c_void_p(psi.data_ptr())))
         return psi
 
-    def fidelity(self, T, dt, target, col_index, precision="mixed", frame="interaction", solver="rk4"):
-        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
+    def fidelity(self, T, dt, target, col_index, precision="mixed", frame="interaction", solver="rk4",
+                 compensation="none"):
+        """(F_avg, F_state, computational block); compensation "vz": the fidelities with
+        the virtual Z gates around the pulses that maximise them."""
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         Dc = target.shape[0]
@@ -237,11 +243,12 @@ class System:
         return F[0], F[1], U.view(np.complex128).reshape(Dc, len(col_index))
 
     def fidelity_grad(self, T, dt, target, col_index, kind="avg", precision="mixed",
-                      frame="interaction", ckpt=0, ham=True, solver="rk4"):
+                      frame="interaction", ckpt=0, ham=True, solver="rk4", compensation="none"):
         """F and the gradient w.r.t. the pulse and (ham=True) Hamiltonian parameters;
         with ham=False the Hamiltonian part is not computed and returned as None.
-        solver "q2" or "q4" (lab frame) computes the pulse-parameter gradient only: pass ham=False."""
-        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
+        solver "q2" or "q4" (lab frame) computes the pulse-parameter gradient only: pass ham=False.
+        compensation "vz": F with the virtual Z gates that maximise it, and its gradient."""
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         npul, nham = self.param_counts()

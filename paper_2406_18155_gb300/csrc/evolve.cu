@@ -709,6 +709,115 @@ __global__ void k_fidelity(FidArgs a) {
   }
 }
 
+// Virtual-Z compensation: phases a (rows) and b (columns) of diag(1, e^{i phase}) gates
+// on the qubits maximising |tr M|, M = T^dag Z(a) U Z(b), tr M = sum_rl W[r][l]
+// za[r] zb[l] with W = conj(T) o U and za[r] = exp(i sum_q a_q bit_q(r)).  Coordinate
+// ascent from zero phases, a_1..a_n then b_1..b_n (qubit q on label bit n - 1 - q):
+// with the other phases fixed tr M = X_0 + e^{i phi} X_1 over the labels whose bit is
+// 0 / 1, largest in modulus at phi = arg X_0 - arg X_1.  Stops at the first sweep that
+// does not raise |tr M|, at most 2000 sweeps.  Writes T_eff = conj(za) o T o conj(zb)
+// (tr(T_eff^dag U) = tr M), whose plain fidelity and co-state are the compensated ones.
+// One block; warp 0 runs the O(D_c) coordinate updates, all threads the O(D_c^2) sums.
+struct VzArgs {
+  int S, Dc, n;
+  const double2* Uc;          // Dc x S
+  const double2* Tg;          // Dc x Dc
+  const int* lab;             // S
+  double2* W;                 // Dc x Dc scratch
+  double2* Teff;              // Dc x Dc out
+};
+__global__ void k_vz_comp(VzArgs a) {
+  constexpr int MAXDC = 256;
+  __shared__ double2 v[MAXDC], za[MAXDC], zb[MAXDC];
+  __shared__ int colof[MAXDC];
+  __shared__ double ph[2][8];
+  __shared__ int stop;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, Dc = a.Dc, n = a.n;
+  for (int s = tid; s < a.S; s += nt)
+    if (a.lab[s] >= 0) colof[a.lab[s]] = s;
+  if (tid < 16) ph[tid / 8][tid % 8] = 0.0;
+  for (int r = tid; r < Dc; r += nt) { za[r] = make_double2(1.0, 0.0); zb[r] = make_double2(1.0, 0.0); }
+  __syncthreads();
+  for (int i = tid; i < Dc * Dc; i += nt) {
+    const int r = i / Dc, l = i - r * Dc;
+    a.W[i] = cmul(cconj(a.Tg[i]), a.Uc[(size_t)r * a.S + colof[l]]);
+  }
+  __syncthreads();
+  // warp 0: sum over labels of z[r] w[r] split by bit (fixed lane order)
+  auto wsum = [&](const double2* z, const double2* w, int bit, int want) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int r = lane; r < Dc; r += 32)
+      if (bit < 0 || ((r >> bit) & 1) == want) acc = cfma(z[r], w[r], acc);
+    for (int o = 16; o > 0; o >>= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    return acc;
+  };
+  auto refresh = [&](double2* z, const double* p) {   // z[r] = exp(i sum_q p_q bit_q(r))
+    for (int r = lane; r < Dc; r += 32) {
+      double t = 0.0;
+      for (int q = 0; q < n; ++q) t += ((r >> (n - 1 - q)) & 1) ? p[q] : 0.0;
+      double sn, cs;
+      sincos(t, &sn, &cs);
+      z[r] = make_double2(cs, sn);
+    }
+    __syncwarp();
+  };
+  double best = 0.0;
+  // |tr M| at zero phases: v = W 1, tr = sum v
+  for (int r = tid; r < Dc; r += nt) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int l = 0; l < Dc; ++l) { acc.x += a.W[(size_t)r * Dc + l].x; acc.y += a.W[(size_t)r * Dc + l].y; }
+    v[r] = acc;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const double2 t = wsum(za, v, -1, 0);
+    best = hypot(t.x, t.y);
+  }
+  for (int sweep = 0; sweep < 2000; ++sweep) {
+    for (int side = 0; side < 2; ++side) {
+      double2* zs = side == 0 ? za : zb;                  // the side being updated
+      const double2* zo = side == 0 ? zb : za;
+      // v = W zo (rows, side 0) or W^T zo (columns, side 1)
+      for (int r = tid; r < Dc; r += nt) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int l = 0; l < Dc; ++l)
+          acc = cfma(side == 0 ? a.W[(size_t)r * Dc + l] : a.W[(size_t)l * Dc + r], zo[l], acc);
+        v[r] = acc;
+      }
+      __syncthreads();
+      if (tid < 32) {
+        for (int q = 0; q < n; ++q) {
+          const int bit = n - 1 - q;
+          if (lane == 0) ph[side][q] = 0.0;
+          __syncwarp();
+          refresh(zs, ph[side]);
+          const double2 x0 = wsum(zs, v, bit, 0), x1 = wsum(zs, v, bit, 1);
+          const double m1 = hypot(x1.x, x1.y);
+          if (lane == 0) ph[side][q] = m1 > 0.0 ? atan2(x0.y, x0.x) - atan2(x1.y, x1.x) : 0.0;
+          __syncwarp();
+          refresh(zs, ph[side]);
+        }
+      }
+      __syncthreads();
+    }
+    if (tid < 32) {
+      const double2 t = wsum(zb, v, -1, 0);              // v = W^T za from the column side
+      const double now = hypot(t.x, t.y);
+      if (lane == 0) stop = !(now > best);
+      best = now;
+    }
+    __syncthreads();
+    if (stop) break;
+  }
+  for (int i = tid; i < Dc * Dc; i += nt) {
+    const int r = i / Dc, l = i - r * Dc;
+    a.Teff[i] = cmul(cconj(za[r]), cmul(a.Tg[i], cconj(zb[l])));
+  }
+}
+
 // Energy co-gradient of the frame epilogue psi_lab = exp(-i Hd T) psi_I:
 // ebar[i][c] += sum over comp rows with digit_i = c of Re(conj(bar) (-i T) psi_lab).
 // Comp rows only have digits 0 and 1.  Single block.
@@ -1894,6 +2003,12 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (full && s.Dc > 256) full = false;
   if (grad && kind == SG_FID_AVG && !full)
     return sg_fail(ctx, SG_E_INVALID, "F_avg needs every computational state evolved exactly once (Dc <= 256)");
+  if (o->compensation != SG_COMP_NONE && o->compensation != SG_COMP_VZ)
+    return sg_fail(ctx, SG_E_INVALID, "compensation must be SG_COMP_NONE or SG_COMP_VZ");
+  const bool vz = o->compensation == SG_COMP_VZ;
+  if (vz && (!full || s.nqb > 8))
+    return sg_fail(ctx, SG_E_INVALID, "virtual-Z compensation needs every computational state evolved exactly once "
+                                      "(Dc <= 256)");
   auto t0 = std::chrono::steady_clock::now();
   long long* cols_dev = sv.ar.get<long long>(s.S);
   int* lab_dev = sv.ar.get<int>(s.S);
@@ -1949,10 +2064,22 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
   CompArgs ca = comp_args(s);
   k_gather_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, sv.psi, Uc);
+  const double2* Tfid = Tg;
+  if (vz) {
+    // the compensated fidelity is the plain one against the effective target
+    VzArgs va{};
+    va.S = s.S; va.Dc = s.Dc; va.n = s.nqb; va.Uc = Uc; va.Tg = Tg; va.lab = lab_dev;
+    va.W = sv.ar.get<double2>((size_t)s.Dc * s.Dc);
+    va.Teff = sv.ar.get<double2>((size_t)s.Dc * s.Dc);
+    if (!va.W || !va.Teff) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+    k_vz_comp<<<1, kT, 0, st>>>(va);
+    ++sv.launches;
+    Tfid = va.Teff;
+  }
   FidArgs fa{};
   fa.S = s.S; fa.Dc = s.Dc; fa.Sc = Sc; fa.full = full ? 1 : 0; fa.kind = kind; fa.nq = s.nq;
   for (int i = 0; i < s.nq; ++i) fa.qpos[i] = s.qpos[i];
-  fa.Uc = Uc; fa.Tg = Tg; fa.lab = lab_dev; fa.F = Fd; fa.bar = grad ? barc : nullptr; fa.M = Mbuf;
+  fa.Uc = Uc; fa.Tg = Tfid; fa.lab = lab_dev; fa.F = Fd; fa.bar = grad ? barc : nullptr; fa.M = Mbuf;
   fa.T = s.T;
   fa.frame = s.frame;
   k_fidelity<<<1, kT, 0, st>>>(fa);
