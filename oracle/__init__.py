@@ -13,7 +13,9 @@ What it computes (paper sections in brackets):
 * the composite Hamiltonian as an explicit sum of Kronecker
   products of local operators, dense (np.kron) or matrix-free    [Eq. 1, App. B]
 * fixed-step classic RK4 time evolution of a batch of columns   (solver reading R1)
-* second-order Suzuki-Trotter evolution (the paper's solver)    [Sec. 2.3, App. A]
+* Suzuki-Trotter evolution Q2, Q4, Q4j (the paper's solvers)    [Sec. 2.3, App. A]
+  and its discrete adjoint for the pulse parameters              [Sec. 2.5]
+* virtual-Z compensation of the gate fidelity                    [App. C]
 * the composite state-transfer cost and the average gate
   fidelity                                                      [Eq. 13, Eq. D2]
 * the exact discrete adjoint of RK4 (the discretise-then-
