@@ -128,17 +128,24 @@ def fidelity_and_costate(sys, psi_lab, kind):
     (lab frame, shape D x S)."""
     comp, cols = comp_map(sys)
     T = np.asarray(sys.wl["target"], dtype=np.complex128)
-    Dc = len(comp)
-    Uc = psi_lab[comp, :]
-    sel = [s for s, j in enumerate(cols) if j >= 0]
+    F, barc = block_fidelity_and_costate(T, psi_lab[comp, :], cols, kind)
     bar = np.zeros_like(psi_lab)
+    bar[comp, :] = barc
+    return F, bar
+
+
+def block_fidelity_and_costate(T, Uc, cols, kind):
+    """F of the computational block Uc[j', s] = <c_j'|psi_s> (column s carrying label
+    cols[s], -1 for none) and its co-state dF/dRe Uc + i dF/dIm Uc (D_c x S)."""
+    Dc = T.shape[0]
+    sel = [s for s, j in enumerate(cols) if j >= 0]
+    barc = np.zeros_like(Uc)
     if kind == "state":
         S = len(sel)
         z = sum(np.vdot(T[:, cols[s]], Uc[:, s]) for s in sel)
-        F = abs(z / S) ** 2
         for s in sel:
-            bar[comp, s] = (2.0 * z / S ** 2) * T[:, cols[s]]
-        return F, bar
+            barc[:, s] = (2.0 * z / S ** 2) * T[:, cols[s]]
+        return abs(z / S) ** 2, barc
     U = np.zeros((Dc, Dc), dtype=np.complex128)
     for s in sel:
         U[:, cols[s]] = Uc[:, s]
@@ -147,8 +154,8 @@ def fidelity_and_costate(sys, psi_lab, kind):
     F = (np.real(np.trace(M @ M.conj().T)) + abs(trM) ** 2) / (Dc * (Dc + 1))
     Ubar = 2.0 * (T @ M + trM * T) / (Dc * (Dc + 1))
     for s in sel:
-        bar[comp, s] = Ubar[:, cols[s]]
-    return F, bar
+        barc[:, s] = Ubar[:, cols[s]]
+    return F, barc
 
 
 def evolve_and_fidelity(wl, matrix_free=False):

@@ -1,0 +1,79 @@
+"""Pins of the oracle's dressed (idle-Hamiltonian eigen-) basis of the gate metric
+(App. C): reduction to the product basis without couplings, eigen-residual, the
+phase gauge, second-order perturbation theory for the leaked weight of a dressed
+state, and the pulse gradient against central differences."""
+import copy
+
+import numpy as np
+
+from oracle.dressed import (dressed_fidelities, dressed_pulse_gradient, dressed_vectors,
+                            idle_hamiltonian)
+from oracle.evolve import comp_map, evolve_and_fidelity
+from oracle.system import OracleSystem
+from paper_2406_18155_gb300 import workloads as W
+
+
+def _pair(seed=3, T=0.5, J_scale=1.0):
+    wl = W.fluxonium_pair_cr(seed=seed, nseg=4, T=T)
+    wl["drives"][0]["length"] = T
+    for c in wl["couplings"]:
+        c["J"] *= J_scale
+    return wl
+
+
+def test_without_couplings_the_dressed_basis_is_the_product_basis():
+    wl = _pair(J_scale=0.0)
+    sys = OracleSystem(wl)
+    Vc, _ = dressed_vectors(sys)
+    comp, _ = comp_map(sys)
+    E = np.zeros((sys.D, len(comp)))
+    E[comp, range(len(comp))] = 1.0
+    assert np.max(np.abs(Vc - E)) < 1e-12
+    Fa, Fs, _ = dressed_fidelities(wl)
+    r = evolve_and_fidelity(wl)
+    assert abs(Fa - r["F_avg"]) < 1e-12 and abs(Fs - r["F_state"]) < 1e-12
+
+
+def test_dressed_vectors_are_gauged_eigenvectors():
+    wl = _pair()
+    sys = OracleSystem(wl)
+    Vc, lam = dressed_vectors(sys)
+    H = idle_hamiltonian(sys)
+    assert np.max(np.abs(H @ Vc - Vc * lam[None, :])) < 1e-10
+    assert np.max(np.abs(Vc.conj().T @ Vc - np.eye(Vc.shape[1]))) < 1e-12
+    comp, _ = comp_map(sys)
+    diag = Vc[comp, range(len(comp))]
+    assert np.all(np.abs(diag.imag) < 1e-15) and np.all(diag.real > 0.5)
+
+
+def test_leaked_weight_follows_second_order_perturbation_theory():
+    # weak coupling: 1 - |<bare_j|v_j>|^2 = sum_k |<k|V|bare_j>|^2 / (E_j - E_k)^2 + O(J^3)
+    wl = _pair(J_scale=0.05)
+    sys = OracleSystem(wl)
+    Vc, _ = dressed_vectors(sys)
+    comp, _ = comp_map(sys)
+    H = idle_hamiltonian(sys)
+    E0 = np.real(np.diag(H))
+    Vcp = H - np.diag(np.diag(H))
+    for j, r in enumerate(comp):
+        leaked = 1.0 - abs(Vc[r, j]) ** 2
+        pt = sum(abs(Vcp[k, r]) ** 2 / (E0[r] - E0[k]) ** 2 for k in range(sys.D) if k != r)
+        assert abs(leaked - pt) <= 0.05 * pt + 1e-14, (j, leaked, pt)
+
+
+def test_dressed_pulse_gradient_matches_central_differences():
+    wl = _pair(T=0.4)
+    F, g = dressed_pulse_gradient(wl)
+    assert abs(F - dressed_fidelities(wl)[0 if wl["fid_kind"] == "avg" else 1]) < 1e-14
+    k = 0 if wl["fid_kind"] == "avg" else 1
+    fd = []
+    for j in range(len(wl["drives"][0]["amps"])):
+        vals = []
+        h = 1e-7 * max(1.0, abs(wl["drives"][0]["amps"][j]))
+        for sgn in (1, -1):
+            w2 = copy.deepcopy(wl)
+            w2["drives"][0]["amps"][j] += sgn * h
+            vals.append(dressed_fidelities(w2)[k])
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    assert np.max(np.abs(g - fd)) <= 1e-6 * max(1e-6, np.max(np.abs(fd))), (g, fd)
