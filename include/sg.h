@@ -188,7 +188,19 @@ typedef struct {
                                    columns of psi are the initial states                  */
   int solver;                   /* SG_SOLVER_RK4 (0, default), _Q2, _Q4 or _Q4J            */
   int compensation;             /* SG_COMP_NONE (0, default) or SG_COMP_VZ (fidelities)    */
+  int basis;                    /* SG_BASIS_PRODUCT (0, default) or SG_BASIS_DRESSED        */
 } sg_evolve_opts;
+
+/* Basis of the gate (sg_fidelity, sg_fidelity_grad; App. C).  SG_BASIS_PRODUCT: the
+ * computational states are bare product states.  SG_BASIS_DRESSED: they are the
+ * eigenstates of the idle Hamiltonian (lab frame, no drives: level energies and
+ * couplings) of largest overlap with the bare computational states, each signed so
+ * that overlap is positive; the evolved columns start in them and are projected on
+ * them (U -> V^dag U V restricted to the computational states).  Needs D <= 64, a real
+ * idle Hamiltonian, non-degenerate dressed computational levels and every evolved
+ * column a computational state (each once), else SG_E_INVALID / SG_E_UNSUPPORTED; with
+ * sg_fidelity_grad, grad_ham must be NULL (the pulse gradient only). */
+enum { SG_BASIS_PRODUCT = 0, SG_BASIS_DRESSED = 1 };
 
 /* Compensation of the gate fidelity (sg_fidelity, sg_fidelity_grad): the paper's gate
  * metric assumes errorless single-qubit gates around the pulses.  SG_COMP_VZ takes

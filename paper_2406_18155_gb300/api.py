@@ -53,16 +53,18 @@ class Context:
 
 _SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q2": capi.SG_SOLVER_Q2, "q4": capi.SG_SOLVER_Q4, "q4j": capi.SG_SOLVER_Q4J}
 _COMP = {"none": capi.SG_COMP_NONE, "vz": capi.SG_COMP_VZ}
+_BASIS = {"product": capi.SG_BASIS_PRODUCT, "dressed": capi.SG_BASIS_DRESSED}
 
 
 def evolve_opts(T, dt, precision="mixed", frame="interaction", col_index=None, ncols=None, solver="rk4",
-                compensation="none"):
+                compensation="none", basis="product"):
     o = capi.sg_evolve_opts()
     o.T, o.dt = float(T), float(dt)
     o.precision = _PREC[precision]
     o.frame = _FRAME[frame]
     o.solver = _SOLVER[solver]
     o.compensation = _COMP[compensation]
+    o.basis = _BASIS[basis]
     keep = None
     if col_index is not None:
         keep = np.ascontiguousarray(np.asarray(col_index, dtype=np.int64))
@@ -231,10 +233,12 @@ class System:
         return psi
 
     def fidelity(self, T, dt, target, col_index, precision="mixed", frame="interaction", solver="rk4",
-                 compensation="none"):
+                 compensation="none", basis="product"):
         """(F_avg, F_state, computational block); compensation "vz": the fidelities with
-        the virtual Z gates around the pulses that maximise them."""
-        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation)
+        the virtual Z gates around the pulses that maximise them; basis "dressed": the
+        gate in the eigenbasis of the idle Hamiltonian."""
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation,
+                              basis=basis)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         Dc = target.shape[0]
@@ -243,12 +247,15 @@ class System:
         return F[0], F[1], U.view(np.complex128).reshape(Dc, len(col_index))
 
     def fidelity_grad(self, T, dt, target, col_index, kind="avg", precision="mixed",
-                      frame="interaction", ckpt=0, ham=True, solver="rk4", compensation="none"):
+                      frame="interaction", ckpt=0, ham=True, solver="rk4", compensation="none",
+                      basis="product"):
         """F and the gradient w.r.t. the pulse and (ham=True) Hamiltonian parameters;
         with ham=False the Hamiltonian part is not computed and returned as None.
         solver "q2" or "q4" (lab frame) computes the pulse-parameter gradient only: pass ham=False.
-        compensation "vz": F with the virtual Z gates that maximise it, and its gradient."""
-        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation)
+        compensation "vz": F with the virtual Z gates that maximise it, and its gradient;
+        basis "dressed" (pulse gradient only: ham=False): the gate in the idle eigenbasis."""
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation,
+                              basis=basis)
         tg = _c128_pairs(target)
         F = np.zeros(2)
         npul, nham = self.param_counts()

@@ -14,6 +14,7 @@ SG_OK = 0
 SG_E_INVALID, SG_E_NOMEM, SG_E_STATE, SG_E_CUDA, SG_E_TIMEOUT = -1, -2, -3, -4, -5
 SG_SOLVER_RK4, SG_SOLVER_Q2, SG_SOLVER_Q4, SG_SOLVER_Q4J = 0, 2, 4, 5
 SG_COMP_NONE, SG_COMP_VZ = 0, 1
+SG_BASIS_PRODUCT, SG_BASIS_DRESSED = 0, 1
 SG_E_PENDING, SG_E_NOMEM_RETRY, SG_E_CANCELLED, SG_E_NOTFOUND, SG_E_UNSUPPORTED = -6, -7, -8, -9, -10
 SG_OP_N, SG_OP_PHI = 0, 1
 SG_ENV_GAUSSIAN, SG_ENV_PWC, SG_ENV_COSINE = 0, 1, 2
@@ -32,7 +33,8 @@ class sg_pulse(C.Structure):
 class sg_evolve_opts(C.Structure):
     _fields_ = [("T", C.c_double), ("dt", C.c_double), ("precision", C.c_int),
                 ("frame", C.c_int), ("ncols", C.c_int),
-                ("col_index", C.POINTER(C.c_longlong)), ("solver", C.c_int), ("compensation", C.c_int)]
+                ("col_index", C.POINTER(C.c_longlong)), ("solver", C.c_int), ("compensation", C.c_int),
+                ("basis", C.c_int)]
 
 
 class sg_request(C.Structure):

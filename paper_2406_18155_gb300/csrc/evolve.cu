@@ -852,6 +852,37 @@ __device__ long long comp_row(const CompArgs& a, int j) {
   for (int i = 0; i < a.nq; ++i) r = r * a.dims[i] + (a.qpos[i] >= 0 ? ((j >> a.qpos[i]) & 1) : 0);
   return r;
 }
+// Dressed basis: columns start in the dressed computational states, psi[r][s] =
+// Vc[r][lab(s)]; the block is Uc[j][s] = <v_j|psi_s>; the co-state of the final states
+// is pbar[r][s] = sum_j Vc[r][j] barc[j][s].  Vc is D x Dc, row-major.
+__global__ void k_init_dressed(const double2* __restrict__ Vc, const int* __restrict__ lab, long long D, int S,
+                               int Dc, double2* __restrict__ psi) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < D * S; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / S;
+    const int s = (int)(i - r * S);
+    psi[i] = Vc[r * Dc + lab[s]];
+  }
+}
+__global__ void k_gather_dressed(const double2* __restrict__ Vc, const double2* __restrict__ psi, long long D, int S,
+                                 int Dc, double2* __restrict__ Uc) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Dc * S; i += gridDim.x * blockDim.x) {
+    const int j = i / S, s = i - j * S;
+    double2 acc = make_double2(0.0, 0.0);
+    for (long long r = 0; r < D; ++r) acc = cfma(cconj(Vc[r * Dc + j]), psi[r * S + s], acc);
+    Uc[i] = acc;
+  }
+}
+__global__ void k_scatter_dressed(const double2* __restrict__ Vc, const double2* __restrict__ barc, long long D,
+                                  int S, int Dc, double2* __restrict__ pbar) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < D * S; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / S;
+    const int s = (int)(i - r * S);
+    double2 acc = make_double2(0.0, 0.0);
+    for (int j = 0; j < Dc; ++j) acc = cfma(Vc[r * Dc + j], barc[(size_t)j * S + s], acc);
+    pbar[i] = acc;
+  }
+}
+
 __global__ void k_gather_comp(CompArgs a, const double2* psi, double2* Uc) {
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < a.Dc * a.S; x += gridDim.x * blockDim.x) {
     int j = x / a.S, s = x % a.S;
@@ -2009,6 +2040,15 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (vz && (!full || s.nqb > 8))
     return sg_fail(ctx, SG_E_INVALID, "virtual-Z compensation needs every computational state evolved exactly once "
                                       "(Dc <= 256)");
+  if (o->basis != SG_BASIS_PRODUCT && o->basis != SG_BASIS_DRESSED)
+    return sg_fail(ctx, SG_E_INVALID, "basis must be SG_BASIS_PRODUCT or SG_BASIS_DRESSED");
+  const bool dressed = o->basis == SG_BASIS_DRESSED;
+  if (dressed && (s.D > SG_MAXM || !full || Sc != s.S))
+    return sg_fail(ctx, SG_E_INVALID, "the dressed basis needs D <= 64 and the evolved columns to be the "
+                                      "computational states, each once");
+  if (dressed && grad && grad_ham)
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the dressed basis computes the pulse-parameter gradient only "
+                                          "(grad_ham = NULL)");
   auto t0 = std::chrono::steady_clock::now();
   long long* cols_dev = sv.ar.get<long long>(s.S);
   int* lab_dev = sv.ar.get<int>(s.S);
@@ -2032,6 +2072,40 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   }
   rc = upload_and_tables(sys, o, sv, grad);
   if (rc != SG_OK) return rc;
+  double2* Vc = nullptr;
+  if (dressed) {
+    // dressed computational states of the idle Hamiltonian (one block, FP64 Jacobi)
+    DressArgs da{};
+    da.D = (int)s.D; da.nq = s.nq; da.ne = s.p.ne; da.Dc = s.Dc;
+    for (int i = 0; i < s.nq; ++i) {
+      da.dims[i] = s.p.dims[i]; da.st[i] = s.p.st[i]; da.eoff[i] = s.ta.eoff[i]; da.opd_off[i] = s.ta.opd_off[i];
+    }
+    for (int e = 0; e < s.p.ne; ++e) {
+      da.e_a[e] = s.p.e_a[e]; da.e_b[e] = s.p.e_b[e];
+      da.e_opa[e] = s.ta.e_opa[e]; da.e_opb[e] = s.ta.e_opb[e]; da.J[e] = s.ta.J[e];
+    }
+    std::vector<long long> comp(s.Dc);
+    for (int j = 0; j < s.Dc; ++j) {
+      long long r = 0;
+      for (int i = 0; i < s.nq; ++i) r += (long long)(s.qpos[i] >= 0 ? (j >> s.qpos[i]) & 1 : 0) * s.p.st[i];
+      comp[j] = r;
+    }
+    long long* comp_dev = sv.ar.get<long long>(s.Dc);
+    int* derr = sv.ar.get<int>(1);
+    Vc = sv.ar.get<double2>((size_t)s.D * s.Dc);
+    if (!comp_dev || !derr || !Vc) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(comp_dev, comp.data(), s.Dc * sizeof(long long), cudaMemcpyHostToDevice, st));
+    da.E = sv.E_dev; da.opd = sv.opd_dev; da.comp = comp_dev; da.Vc = Vc; da.err = derr;
+    SG_CUDA_TRY(ctx, launch_dressed(da, st));
+    ++sv.launches;
+    int herr = 0;
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));     // reads only from an idle stream (see dcopy)
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (herr == 1) return sg_fail(ctx, SG_E_UNSUPPORTED, "the dressed basis needs a real idle Hamiltonian");
+    if (herr == 2) return sg_fail(ctx, SG_E_INVALID, "two computational states share a dressed state");
+    if (herr == 3) return sg_fail(ctx, SG_E_INVALID, "a dressed computational level is degenerate");
+  }
   // checkpoints
   int K = 0;
   std::vector<double2*> ckpts;
@@ -2056,14 +2130,19 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   cudaEvent_t ev0, ev1, ev2;
   cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&ev2);
   cudaEventRecord(ev0, st);
-  if (s.q2) rc = run_q2(sys, sv, cols_dev, false);
-  else rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr)
-                                     : run_forward<double>(sys, sv, cols_dev, false, K, grad ? &ckpts : nullptr);
+  if (dressed) {
+    k_init_dressed<<<grid_for(n), kT, 0, st>>>(Vc, lab_dev, s.D, s.S, s.Dc, sv.psi);
+    ++sv.launches;
+  }
+  if (s.q2) rc = run_q2(sys, sv, cols_dev, dressed);
+  else rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, dressed, K, grad ? &ckpts : nullptr)
+                                     : run_forward<double>(sys, sv, cols_dev, dressed, K, grad ? &ckpts : nullptr);
   if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
   if (s.frame == SG_FRAME_INTERACTION)
     k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
   CompArgs ca = comp_args(s);
-  k_gather_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, sv.psi, Uc);
+  if (dressed) k_gather_dressed<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(Vc, sv.psi, s.D, s.S, s.Dc, Uc);
+  else k_gather_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, sv.psi, Uc);
   const double2* Tfid = Tg;
   if (vz) {
     // the compensated fidelity is the plain one against the effective target
@@ -2122,10 +2201,11 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     SG_CUDA_TRY(ctx, cudaMemsetAsync(ebar_frame, 0, s.nq * SG_MAXD * sizeof(double), st));
     SG_CUDA_TRY(ctx, cudaMemsetAsync(pbar, 0, n * sizeof(double2), st));
     // co-state of the lab-frame columns, its frame-phase energy term, pull back to the frame
-    k_scatter_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, barc, pbar);
+    if (dressed) k_scatter_dressed<<<grid_for(n), kT, 0, st>>>(Vc, barc, s.D, s.S, s.Dc, pbar);
+    else k_scatter_comp<<<grid_for((long long)s.Dc * s.S), kT, 0, st>>>(ca, barc, pbar);
     if (s.frame == SG_FRAME_INTERACTION) {
       fa.ebar_frame = ebar_frame;
-      k_frame_ebar<<<1, kT, 0, st>>>(fa);
+      if (!dressed) k_frame_ebar<<<1, kT, 0, st>>>(fa);    // energy co-gradient: Hamiltonian gradient only
       k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, +1.0), pbar);
     }
     sv.launches += 3;

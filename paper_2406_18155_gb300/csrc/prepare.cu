@@ -346,6 +346,76 @@ __global__ void __launch_bounds__(kThreads) k_chain(ChainArgs a) {
   if (tid == 0) a.out[q * 3 + p] = red[0];
 }
 
+// One block: the idle Hamiltonian H[r][c] = delta_rc sum_i E_i[l_i(r)] + sum_e J_e
+// A_e[l_a(r)][l_a(c)] B_e[l_b(r)][l_b(c)] (other digits equal), real symmetric (flag 1
+// otherwise), Jacobi eigenpairs, then per label j the eigenvector k of largest
+// |V[comp_j][k]| (flag 2 if two labels share one, flag 3 if its eigenvalue is within
+// 1e-9 of another), signed so that V[comp_j][k] > 0.
+__global__ void __launch_bounds__(kThreads) k_dressed(DressArgs a) {
+  extern __shared__ __align__(16) unsigned char smd[];
+  const int D = a.D, tid = threadIdx.x, nt = blockDim.x;
+  double* A = reinterpret_cast<double*>(smd);
+  double* V = A + D * D;
+  double* cs = V + D * D;                                    // 2 SG_MAXM
+  int* pairs = reinterpret_cast<int*>(cs + 2 * SG_MAXM);     // 2 SG_MAXM
+  __shared__ int kk[SG_MAXM];
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int i = tid; i < D * D; i += nt) {
+    const int r = i / D, c = i - r * D;
+    double h = 0.0, hi = 0.0;
+    if (r == c)
+      for (int q = 0; q < a.nq; ++q) h += a.E[a.eoff[q] + (int)((r / a.st[q]) % a.dims[q])];
+    for (int e = 0; e < a.ne; ++e) {
+      const int qa = a.e_a[e], qb = a.e_b[e];
+      bool same = true;
+      for (int q = 0; q < a.nq; ++q)
+        if (q != qa && q != qb && (r / a.st[q]) % a.dims[q] != (c / a.st[q]) % a.dims[q]) same = false;
+      if (!same) continue;
+      const int da = a.dims[qa], db = a.dims[qb];
+      const int ra = (int)((r / a.st[qa]) % da), ca = (int)((c / a.st[qa]) % da);
+      const int rb = (int)((r / a.st[qb]) % db), cb = (int)((c / a.st[qb]) % db);
+      const double2 x = a.opd[a.opd_off[qa] + a.e_opa[e] * da * da + ra * da + ca];
+      const double2 y = a.opd[a.opd_off[qb] + a.e_opb[e] * db * db + rb * db + cb];
+      h += a.J[e] * (x.x * y.x - x.y * y.y);
+      hi += a.J[e] * (x.x * y.y + x.y * y.x);
+    }
+    if (fabs(hi) > 1e-12 * (fabs(h) + 1.0)) atomicOr(&bad, 1);
+    A[i] = h;
+  }
+  __syncthreads();
+  jacobi_eigen(A, V, D, cs, pairs);
+  for (int j = tid; j < a.Dc; j += nt) {
+    const int r = (int)a.comp[j];
+    int best = 0;
+    double bv = -1.0;
+    for (int k = 0; k < D; ++k) {
+      const double v = fabs(V[r * D + k]);
+      if (v > bv) { bv = v; best = k; }
+    }
+    kk[j] = best;
+  }
+  __syncthreads();
+  double scale = 0.0;
+  for (int k = 0; k < D; ++k) scale = fmax(scale, fabs(A[k * D + k]));
+  for (int j = tid; j < a.Dc; j += nt) {
+    for (int m = 0; m < j; ++m)
+      if (kk[m] == kk[j]) atomicOr(&bad, 2);
+    const double lk = A[kk[j] * D + kk[j]];
+    for (int k = 0; k < D; ++k)
+      if (k != kk[j] && fabs(A[k * D + k] - lk) <= 1e-9 * fmax(1.0, scale)) atomicOr(&bad, 4);
+  }
+  __syncthreads();
+  for (int i = tid; i < D * a.Dc; i += nt) {
+    const int r = i / a.Dc, j = i - r * a.Dc;
+    const int k = kk[j];
+    const double sg = V[(int)a.comp[j] * D + k] < 0.0 ? -1.0 : 1.0;
+    a.Vc[i] = make_double2(sg * V[r * D + k], 0.0);
+  }
+  if (tid == 0) *a.err = bad & 1 ? 1 : (bad & 2 ? 2 : (bad & 4 ? 3 : 0));
+}
+
 }  // namespace
 
 sg_status sg_prepare_impl(sg_system* sys) {
@@ -471,4 +541,13 @@ sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev, const
   k_chain<<<dim3(nq, 3), kThreads, 0, ctx->stream>>>(a);
   SG_CUDA_TRY(ctx, cudaGetLastError());
   return SG_OK;
+}
+
+cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st) {
+  const size_t smem = (2 * (size_t)SG_MAXM * SG_MAXM + 2 * SG_MAXM) * sizeof(double) + 2 * SG_MAXM * sizeof(int);
+  static const cudaError_t attr = cudaFuncSetAttribute(k_dressed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)smem);
+  if (attr != cudaSuccess) return attr;
+  k_dressed<<<1, kThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }

@@ -97,3 +97,24 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
 sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target,
                            int kind, double* F_out, double* Ucomp_out, bool grad,
                            double* grad_pulse, double* grad_ham, int ckpt);
+
+// Dressed computational states (the eigenbasis of the idle Hamiltonian, App. C): one
+// block builds the D x D idle Hamiltonian (D <= SG_MAXM), diagonalises it with the
+// parallel Jacobi solver, assigns every computational label the eigenvector of largest
+// overlap on its bare state, and fixes the sign so that overlap is positive.
+struct DressArgs {
+  int D, nq, ne, Dc;
+  int dims[SG_MAXQ];
+  long long st[SG_MAXQ];
+  int eoff[SG_MAXQ], opd_off[SG_MAXQ];
+  int e_a[SG_MAXEDGE], e_b[SG_MAXEDGE], e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
+  double J[SG_MAXEDGE];
+  const double* E;              // flat level energies (lab frame, E_k - E_0)
+  const double2* opd;           // flat truncated operators
+  const long long* comp;        // Dc flat rows of the bare computational states
+  double2* Vc;                  // out: D x Dc (row-major)
+  int* err;                     // out: 0, 1 complex idle Hamiltonian, 2 shared dressed
+                                // state, 3 degenerate dressed level
+};
+// Launches the dressed-state kernel on stream st (no synchronisation).
+cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st);
