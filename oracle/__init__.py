@@ -15,7 +15,8 @@ What it computes (paper sections in brackets):
 * fixed-step classic RK4 time evolution of a batch of columns   (solver reading R1)
 * Suzuki-Trotter evolution Q2, Q4, Q4j (the paper's solvers)    [Sec. 2.3, App. A]
   and its discrete adjoint for the pulse parameters              [Sec. 2.5]
-* virtual-Z compensation of the gate fidelity                    [App. C]
+* virtual-Z compensation of the gate fidelity and the dressed
+  (idle-Hamiltonian eigen-) basis of the gate metric              [App. C]
 * the composite state-transfer cost and the average gate
   fidelity                                                      [Eq. 13, Eq. D2]
 * the exact discrete adjoint of RK4 (the discretise-then-
