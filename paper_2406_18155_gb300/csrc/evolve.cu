@@ -2043,8 +2043,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (o->basis != SG_BASIS_PRODUCT && o->basis != SG_BASIS_DRESSED)
     return sg_fail(ctx, SG_E_INVALID, "basis must be SG_BASIS_PRODUCT or SG_BASIS_DRESSED");
   const bool dressed = o->basis == SG_BASIS_DRESSED;
-  if (dressed && (s.D > SG_MAXM || !full || Sc != s.S))
-    return sg_fail(ctx, SG_E_INVALID, "the dressed basis needs D <= 64 and the evolved columns to be the "
+  if (dressed && (s.D > kMaxDressed || !full || Sc != s.S))
+    return sg_fail(ctx, SG_E_INVALID, "the dressed basis needs D <= 256 and the evolved columns to be the "
                                       "computational states, each once");
   if (dressed && grad && grad_ham)
     return sg_fail(ctx, SG_E_UNSUPPORTED, "the dressed basis computes the pulse-parameter gradient only "
@@ -2093,7 +2093,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     long long* comp_dev = sv.ar.get<long long>(s.Dc);
     int* derr = sv.ar.get<int>(1);
     Vc = sv.ar.get<double2>((size_t)s.D * s.Dc);
-    if (!comp_dev || !derr || !Vc) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+    da.work = sv.ar.get<double>(2 * (size_t)s.D * s.D);
+    if (!comp_dev || !derr || !Vc || !da.work) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(comp_dev, comp.data(), s.Dc * sizeof(long long), cudaMemcpyHostToDevice, st));
     da.E = sv.E_dev; da.opd = sv.opd_dev; da.comp = comp_dev; da.Vc = Vc; da.err = derr;
     SG_CUDA_TRY(ctx, launch_dressed(da, st));

@@ -352,13 +352,12 @@ __global__ void __launch_bounds__(kThreads) k_chain(ChainArgs a) {
 // |V[comp_j][k]| (flag 2 if two labels share one, flag 3 if its eigenvalue is within
 // 1e-9 of another), signed so that V[comp_j][k] > 0.
 __global__ void __launch_bounds__(kThreads) k_dressed(DressArgs a) {
-  extern __shared__ __align__(16) unsigned char smd[];
   const int D = a.D, tid = threadIdx.x, nt = blockDim.x;
-  double* A = reinterpret_cast<double*>(smd);
-  double* V = A + D * D;
-  double* cs = V + D * D;                                    // 2 SG_MAXM
-  int* pairs = reinterpret_cast<int*>(cs + 2 * SG_MAXM);     // 2 SG_MAXM
-  __shared__ int kk[SG_MAXM];
+  double* A = a.work;                                        // D x D, then V (global: D <= 256)
+  double* V = A + (size_t)D * D;
+  __shared__ double cs[kMaxDressed];                         // 2 x (D / 2 rounded up) rotations
+  __shared__ int pairs[kMaxDressed];
+  __shared__ int kk[kMaxDressed];
   __shared__ int bad;
   if (tid == 0) bad = 0;
   __syncthreads();
@@ -544,10 +543,7 @@ sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev, const
 }
 
 cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st) {
-  const size_t smem = (2 * (size_t)SG_MAXM * SG_MAXM + 2 * SG_MAXM) * sizeof(double) + 2 * SG_MAXM * sizeof(int);
-  static const cudaError_t attr = cudaFuncSetAttribute(k_dressed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       (int)smem);
-  if (attr != cudaSuccess) return attr;
-  k_dressed<<<1, kThreads, smem, st>>>(a);
+  if (a.D < 2 || a.D > kMaxDressed || a.Dc > a.D) return cudaErrorInvalidValue;
+  k_dressed<<<1, kThreads, 0, st>>>(a);
   return cudaGetLastError();
 }

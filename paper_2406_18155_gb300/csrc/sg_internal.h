@@ -99,9 +99,11 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
                            double* grad_pulse, double* grad_ham, int ckpt);
 
 // Dressed computational states (the eigenbasis of the idle Hamiltonian, App. C): one
-// block builds the D x D idle Hamiltonian (D <= SG_MAXM), diagonalises it with the
-// parallel Jacobi solver, assigns every computational label the eigenvector of largest
-// overlap on its bare state, and fixes the sign so that overlap is positive.
+// block builds the D x D idle Hamiltonian (D <= kMaxDressed) in global scratch,
+// diagonalises it with the parallel Jacobi solver, assigns every computational label
+// the eigenvector of largest overlap on its bare state, and fixes the sign so that
+// overlap is positive.
+constexpr int kMaxDressed = 256;
 struct DressArgs {
   int D, nq, ne, Dc;
   int dims[SG_MAXQ];
@@ -113,6 +115,7 @@ struct DressArgs {
   const double2* opd;           // flat truncated operators
   const long long* comp;        // Dc flat rows of the bare computational states
   double2* Vc;                  // out: D x Dc (row-major)
+  double* work;                 // scratch: 2 D^2 doubles (the matrix, then its eigenvectors)
   int* err;                     // out: 0, 1 complex idle Hamiltonian, 2 shared dressed
                                 // state, 3 degenerate dressed level
 };

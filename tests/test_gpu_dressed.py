@@ -37,6 +37,7 @@ CASES = {
     "transmon_pair": _transmon_pair,
     "pair_cr_l5": lambda: _short(W.fluxonium_pair_cr(seed=5, nseg=4), 0.4),
     "chain3_l3": lambda: W.fluxonium_chain(seed=7, nq=3, levels=3, T=0.3, dt=0.01, nseg=2),
+    "chain4_l3": lambda: W.fluxonium_chain(seed=9, nq=4, levels=3, T=0.2, dt=0.01, nseg=2),   # D = 81
 }
 
 
@@ -80,7 +81,7 @@ def test_dressed_requests_that_are_refused(sgctx):
         s.fidelity(wl["T"], wl["dt"], wl["target"], list(wl["col_index"]) + [2], precision="fp64",
                    basis="dressed")
     assert e.value.code == SG_E_INVALID
-    big = W.fluxonium_chain(seed=8, nq=4, levels=3, T=0.2, dt=0.01, nseg=2)          # D = 81 > 64
+    big = W.fluxonium_chain(seed=8, nq=4, levels=5, T=0.2, dt=0.01, nseg=2)          # D = 625 > 256
     s2 = _system(sgctx, big)
     with pytest.raises(SGError) as e:
         s2.fidelity(big["T"], big["dt"], big["target"], big["col_index"], precision="fp64", basis="dressed")

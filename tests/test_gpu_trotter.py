@@ -151,3 +151,24 @@ def test_q4j_gradient_is_refused(sgctx, default_path):
         s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
                         precision="fp64", ham=False, solver="q4j")
     assert e.value.code == SG_E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("steps", [1, 3])
+@pytest.mark.parametrize("scheme", ["q2", "q4", "q4j"])
+def test_edge_cases_single_step_and_no_couplings(sgctx, default_path, steps, scheme):
+    # one step (the first and last 1-body rows coincide) and a system without couplings
+    # (empty palindrome, no coupling unitaries)
+    wl = W.fluxonium_pair_multipath(seed=13, levels=3, nseg=1)
+    wl["couplings"] = []
+    wl = _short(wl, T=steps * wl["dt"])
+    s = _system(sgctx, wl)
+    so = OracleSystem(dict(wl, frame="lab"))
+    ref = q2_evolve(so, initial_columns(so, wl["col_index"]), scheme=scheme)
+    psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver=scheme).cpu().numpy()
+    assert np.max(np.abs(psi - ref)) < 1e-12
+    if scheme == "q4j":
+        return
+    F_r, g_r = q2_pulse_gradient(wl, scheme=scheme)
+    F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
+                               precision="fp64", ham=False, solver=scheme)
+    assert np.max(np.abs(gp - g_r)) < 1e-9 * max(1.0, np.max(np.abs(g_r)))
