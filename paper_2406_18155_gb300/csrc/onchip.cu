@@ -628,7 +628,7 @@ struct Q2Args {
                                   // and at the end of every step)
   int nfe;                        // coupling factors per step
   int J;                          // Q2 sub-steps per step (Q2 1, Q4 3, Q4j 2)
-  int setoff[3];                  // sub-step j's coupling unitaries: 2 ne set(j) matrices in
+  int setoff[3];                  // first matrix of sub-step j's coupling set: 2 ne set(j)
   Q2Factor f[kMaxQ2F];            // [0, nf0): 1-body; [nf0, nf0 + nfe): couplings in order
 };
 
@@ -755,7 +755,7 @@ constexpr int kQ2G = 16;          // drives of a Q2 gradient solve (per-thread p
 struct Q2AdjArgs {
   int nq, K, ne, n1f;             // modes, drives, couplings, 1-body factors of a half step
   int J;                          // Q2 sub-steps per step
-  int setoff[3];                  // sub-step j's adjoint coupling unitaries: 2 ne set(j) matrices in
+  int setoff[3];                  // first matrix of sub-step j's adjoint coupling set: 2 ne set(j)
   int row;                        // (nq + K) d^2: U_i(n)^dag then M_k(n)
   unsigned driven;                // bit i: a drive acts on mode i
   Phase one[SG_MAXQ / 2 + 1];     // pairs (offL, offR) and an odd last mode (offA)
