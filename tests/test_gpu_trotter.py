@@ -172,3 +172,19 @@ def test_edge_cases_single_step_and_no_couplings(sgctx, default_path, steps, sch
     F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
                                precision="fp64", ham=False, solver=scheme)
     assert np.max(np.abs(gp - g_r)) < 1e-9 * max(1.0, np.max(np.abs(g_r)))
+
+
+def test_q2_full_size_chain6_sampled_columns(sgctx, default_path):
+    """The 6-fluxonium chain at its full size (D = 4096, all 64 computational columns,
+    the on-chip launch of the bench) over 200 steps: two sampled columns against the
+    oracle's Q2, FP64 within 1e-10 and mixed within 1e-5."""
+    wl = W.fluxonium_chain6(seed=1)
+    wl = _short(wl, T=2.0)
+    s = _system(sgctx, wl)
+    so = OracleSystem(dict(wl, frame="lab"))
+    pick = [0, 37]
+    ref = q2_evolve(so, initial_columns(so, [wl["col_index"][c] for c in pick]))
+    for prec, tol in (("fp64", 1e-10), ("mixed", 1e-5)):
+        psi = s.evolve(wl["T"], wl["dt"], precision=prec, col_index=wl["col_index"], solver="q2").cpu().numpy()
+        assert psi.shape == (4096, 64)
+        assert np.max(np.abs(psi[:, pick] - ref)) < tol, prec
