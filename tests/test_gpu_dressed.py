@@ -86,3 +86,23 @@ def test_dressed_requests_that_are_refused(sgctx):
     with pytest.raises(SGError) as e:
         s2.fidelity(big["T"], big["dt"], big["target"], big["col_index"], precision="fp64", basis="dressed")
     assert e.value.code == SG_E_INVALID
+
+
+def test_dressed_basis_with_the_q2_solver(sgctx):
+    from oracle.dressed import dressed_vectors
+    from oracle.evolve import block_fidelity_and_costate, comp_map
+    from oracle.system import OracleSystem
+    from oracle.trotter import q2_evolve
+    wl = CASES["pair_cr_l5"]()
+    s = _system(sgctx, wl)
+    so = OracleSystem(dict(wl, frame="lab"))
+    Vc, _ = dressed_vectors(so)
+    _, cols = comp_map(so)
+    Uc_r = Vc.conj().T @ q2_evolve(so, Vc[:, cols])
+    T = np.asarray(wl["target"], dtype=complex)
+    Fa_r, _ = block_fidelity_and_costate(T, Uc_r, cols, "avg")
+    Fs_r, _ = block_fidelity_and_costate(T, Uc_r, cols, "state")
+    Fa, Fs, Uc = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver="q2",
+                            basis="dressed")
+    assert abs(Fa - Fa_r) < 1e-10 and abs(Fs - Fs_r) < 1e-10
+    assert np.max(np.abs(Uc - Uc_r)) < 1e-10
