@@ -343,8 +343,10 @@ __global__ void k_q2_onebody(TabArgs a, int DL, double2* __restrict__ rows) {
 
 // Per set s and coupling e: G_half = exp(-i c_s J A (x) B dt/2) and G_full = G_half^2 (the
 // two middle half steps of the palindrome), d_a d_b x d_a d_b with row index x d_b + z,
-// at matrices (s ne + e) 2 + {0, 1}; their adjoints (the pull-back of the gradient) at
-// 2 ne nset + (s ne + e) 2 + {0, 1}.  One thread per (set, coupling).
+// at matrices (s ne + e) 2 + {0, 1}; for the pull-back of the gradient, from matrix
+// 2 ne nset on, per (s, e) four: the inverses G_half^-1, G_full^-1 (the states) and the
+// adjoints G_half^dag, G_full^dag (the co-states), equal pairs when c_s is real.  One
+// thread per (set, coupling).
 __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double2* __restrict__ scratch) {
   const int x = blockIdx.x * blockDim.x + threadIdx.x;
   const int ne = a.p.ne;
@@ -359,7 +361,9 @@ __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double
   const size_t D4 = (size_t)DL * DL * DL * DL;
   double2* Gh = mats + (size_t)x * 2 * D4;
   double2* Gf = Gh + D4;
-  double2* Ghd = mats + ((size_t)2 * ne * a.nset + (size_t)x * 2) * D4;
+  double2* Ghi = mats + ((size_t)2 * ne * a.nset + (size_t)x * 4) * D4;
+  double2* Gfi = Ghi + D4;
+  double2* Ghd = Gfi + D4;
   double2* Gfd = Ghd + D4;
   const double h = a.J[e] * a.dt * 0.5;
   const double2 c = a.setc[sidx];
@@ -382,28 +386,45 @@ __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double
       Ghd[r * n + q] = cconj(Gh[q * n + r]);
       Gfd[r * n + q] = cconj(Gf[q * n + r]);
     }
+  for (int i = 0; i < n * n; ++i) M[i] = make_double2(-M[i].x, -M[i].y);
+  expm_serial(M, n, Ghi, W1, W2);                                                // exp(+i c J (A x B) dt/2)
+  for (int r = 0; r < n; ++r)
+    for (int q = 0; q < n; ++q) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int m = 0; m < n; ++m) acc = cfma(Ghi[r * n + m], Ghi[m * n + q], acc);
+      Gfi[r * n + q] = acc;
+    }
 }
 
-// Gradient tables (pulse parameters), rows [J N][nq + K][d^2]: per sub-step m the
-// adjoint U_i(m)^dag of each mode's (unmerged) 1-body half step, then per drive k on
-// mode i, M_k(m) = U_i(m)^dag L_k(m) with L_k(m) = L(A, -i c_j (dt/2) O_k) the Frechet
-// derivative of expm at A = -i c_j (dt/2) H_i(t_n + tau_j dt), the top-right block of
+// Gradient tables (pulse parameters), rows [J N][2 nq + K][d^2]: per sub-step m the
+// inverses U_i(m)^-1 = exp(-A) of each mode's (unmerged) 1-body half step (they pull the
+// states back), their adjoints U_i(m)^dag (they pull the co-states back; equal to the
+// inverses when the step length is real), then per drive k on mode i,
+// M_k(m) = U_i(m)^-1 L_k(m) with L_k(m) = L(A, -i c_j (dt/2) O_k) the Frechet derivative
+// of expm at A = -i c_j (dt/2) H_i(t_n + tau_j dt), the top-right block of
 // exp([[A, E], [0, A]]) (Sec. 2.5: dU/df_k).  One thread per (m, row).
 constexpr int kQ2MaxD = 5;
 __global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
-  const int per = a.nq + a.K, M = a.N * a.nsub;
+  const int per = 2 * a.nq + a.K, M = a.N * a.nsub;
   for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < M * per; x += gridDim.x * blockDim.x) {
     const int m = x / per, r = x - m * per;
     double2 U[SG_MAXD * SG_MAXD], A[SG_MAXD * SG_MAXD], W1[SG_MAXD * SG_MAXD], W2[SG_MAXD * SG_MAXD];
+    double2 Ui[SG_MAXD * SG_MAXD];
     double2* out = rows + ((size_t)m * per + r) * DL * DL;
-    if (r < a.nq) {
-      const int i = r, d = a.dims[i];
+    if (r < 2 * a.nq) {
+      const int i = r < a.nq ? r : r - a.nq, d = a.dims[i];
       q2_onebody(a, i, m, U, A, W1, W2);
-      for (int p = 0; p < d; ++p)
-        for (int c = 0; c < d; ++c) out[p * d + c] = cconj(U[c * d + p]);
+      if (r >= a.nq) {
+        for (int p = 0; p < d; ++p)
+          for (int c = 0; c < d; ++c) out[p * d + c] = cconj(U[c * d + p]);
+      } else {
+        for (int p = 0; p < d * d; ++p) A[p] = make_double2(-A[p].x, -A[p].y);
+        expm_serial(A, d, Ui, W1, W2);
+        for (int p = 0; p < d * d; ++p) out[p] = Ui[p];
+      }
       continue;
     }
-    const DriveDev& dr = a.drives[r - a.nq];
+    const DriveDev& dr = a.drives[r - 2 * a.nq];
     const int i = dr.mode, d = a.dims[i], mm = 2 * d;
     if (d > kQ2MaxD) continue;                      // the on-chip Suzuki-Trotter plan has d <= 5
     q2_onebody(a, i, m, U, A, W1, W2);              // U_i(m), and A = -i c (dt/2) H_i on return
@@ -421,11 +442,32 @@ __global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
         Z[p * mm + q + d] = make_double2(h * cO.y, -h * cO.x);                 // -i c (dt/2) O
       }
     expm_serial(Z, mm, RZ, Z1, Z2);
-    for (int p = 0; p < d; ++p)                     // M = U^dag L
+    for (int p = 0; p < d * d; ++p) A[p] = make_double2(-A[p].x, -A[p].y);
+    expm_serial(A, d, Ui, W1, W2);                  // U^-1 = exp(-A)
+    // df_k/dtheta = z (a segment or amplitude indicator): z = carrier x envelope shape at
+    // the sub-step time (complex for Q4j), folded in here so that the real part the
+    // adjoint takes is Re(<psibar, L psi> df/dtheta)
+    const int n = m / a.nsub, j = m - n * a.nsub;
+    const double tr = (double)(2 * n + 1) * a.dt * 0.5 + (a.tau[j].x - 0.5) * a.dt, ti = a.tau[j].y * a.dt;
+    double2 z;
+    if (dr.kind == SG_ENV_GAUSSIAN) {
+      const double xg = tr - dr.t0, s2 = dr.sigma * dr.sigma;
+      const double mag = exp(-(xg * xg - ti * ti) / (2.0 * s2)), ang = -(xg * ti) / s2;
+      z = make_double2(mag * cos(ang), mag * sin(ang));
+    } else if (dr.kind == SG_ENV_COSINE) {
+      const double ca = 2.0 * M_PI * tr / dr.length, cb = 2.0 * M_PI * ti / dr.length;
+      z = 2 * n + 1 > dr.mp ? make_double2(0.0, 0.0)
+                            : make_double2(0.5 * (1.0 - cos(ca) * cosh(cb)), 0.5 * (sin(ca) * sinh(cb)));
+    } else {
+      z = make_double2(2 * n + 1 < dr.mp ? 1.0 : 0.0, 0.0);
+    }
+    const double wa = dr.omega * tr + dr.phase, wb = dr.omega * ti;
+    z = cmul(z, make_double2(cos(wa) * cosh(wb), -(sin(wa) * sinh(wb))));
+    for (int p = 0; p < d; ++p)                     // M = z U^-1 L
       for (int q = 0; q < d; ++q) {
         double2 acc = make_double2(0.0, 0.0);
-        for (int w = 0; w < d; ++w) acc = cfma(cconj(U[w * d + p]), RZ[w * mm + q + d], acc);
-        out[p * d + q] = acc;
+        for (int w = 0; w < d; ++w) acc = cfma(Ui[p * d + w], RZ[w * mm + q + d], acc);
+        out[p * d + q] = cmul(z, acc);
       }
   }
 }
@@ -1034,13 +1076,13 @@ __global__ void __launch_bounds__(kT) k_xdens(XArgs a, const typename CT<R>::T* 
 
 // Pulse-parameter chain, one block per drive: dF/dparam = sum over stages of
 // dF/df * df/dparam, and the carrier-frequency co-gradient sum dF/df * E (-sin) t.
-// J = 0: the 3N RK4 stage slots (stage j of step n at t = (2n + j) dt/2); J >= 1: the
-// J N Suzuki-Trotter sub-steps (sub-step j of step n at t_n + tau_j dt, its envelope
-// taken as at the step's midpoint stage, reading R8).
-struct SubTimes { double tau[3]; };
+// J = 0: the 3N RK4 stage slots (stage j of step n at t = (2n + j) dt/2).  J >= 1: the
+// J N Suzuki-Trotter sub-steps, whose gF already carries df/dtheta up to the parameter
+// indicator (k_q2_gradtabs); a PWC sub-step feeds the segment of its step's midpoint
+// (reading R8), and no carrier co-gradient is formed.
 __global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const double* gF,
                               int K, int N, double dt, const int* pulse_off, int n_pulse, double* grad_pulse,
-                              double* omega_bar, int J, SubTimes sub) {
+                              double* omega_bar, int J) {
   const int k = blockIdx.x;
   const DriveDev dr = drives[k];
   const int np = dr.kind == SG_ENV_PWC ? dr.nseg : 1;
@@ -1051,8 +1093,21 @@ __global__ void k_pulse_chain(const DriveDev* drives, const double* amps, const 
   const int per = J > 0 ? J : 3;
   for (int q = tid; q < per * N; q += blockDim.x) {
     const int n = q / per, jq = q % per;
-    const int j = J > 0 ? 1 : jq;
-    const double t = J > 0 ? (double)(2 * n + 1) * dt * 0.5 + (sub.tau[jq] - 0.5) * dt : (double)(2 * n + j) * dt * 0.5;
+    if (J > 0) {
+      // Suzuki-Trotter: the carrier and the envelope shape are already in gF (the
+      // gradient tables carry them); only the parameter each sub-step feeds is left
+      const double g = gF[(size_t)q * K + k];
+      if (dr.kind != SG_ENV_PWC) {
+        mine[0] += g;
+      } else {
+        int seg = (int)(((long long)(2 * n + 1) * dr.nseg) / dr.mp);
+        if (seg > dr.nseg - 1) seg = dr.nseg - 1;
+        if (2 * n + 1 < dr.mp) mine[seg] += g;
+      }
+      continue;
+    }
+    const int j = jq;
+    const double t = (double)(2 * n + j) * dt * 0.5;
     const double g = gF[(size_t)q * K + k];
     const double c = cos(dr.omega * t + dr.phase);
     const double E = envelope_dev(dr, amps, n, j, t);
@@ -1508,7 +1563,7 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
     const long long M = (long long)s.N * ta.nsub;                  // Q2 sub-steps
     const int nset = ta.nset, ne1 = std::max(1, s.p.ne);
     const size_t D4 = (size_t)DL * DL * DL * DL;
-    const size_t nrow = (size_t)(M + 1) * s.nq * DL * DL, nedge = (size_t)4 * ne1 * nset * D4;
+    const size_t nrow = (size_t)(M + 1) * s.nq * DL * DL, nedge = (size_t)6 * ne1 * nset * D4;
     double2* rows = sv.ar.get<double2>(nrow);
     double2* edges = sv.ar.get<double2>(nedge);
     double2* scratch = sv.ar.get<double2>((size_t)ne1 * nset * 3 * D4);
@@ -1518,12 +1573,12 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
     sv.launches += 2;
     sv.q2rows = rows;
     sv.q2edges = edges;
-    const size_t ngr = grad ? (size_t)M * (s.nq + s.K) * DL * DL : 0;
+    const size_t ngr = grad ? (size_t)M * (2 * s.nq + s.K) * DL * DL : 0;
     double2* gtab = nullptr;
     if (grad) {
       gtab = sv.ar.get<double2>(ngr);
       if (!gtab) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 gradient tables failed");
-      k_q2_gradtabs<<<grid_for(M * (s.nq + s.K)), 64, 0, st>>>(ta, DL, gtab);
+      k_q2_gradtabs<<<grid_for(M * (2 * s.nq + s.K)), 64, 0, st>>>(ta, DL, gtab);
       ++sv.launches;
       sv.q2grad = gtab;
     }
@@ -2004,8 +2059,6 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (s.q2 && grad && grad_ham)
     return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter solvers compute the pulse-parameter gradient only "
                                           "(grad_ham = NULL)");
-  if (grad && s.solver == SG_SOLVER_Q4J)
-    return sg_fail(ctx, SG_E_UNSUPPORTED, "Q4j's factors are not unitary: its gradient is not computed");
   for (int i = 0; i < s.nq; ++i)
     if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
       return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");
@@ -2219,11 +2272,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
       int np_max = 1;
       for (auto& d : s.drives) np_max = std::max(np_max, d.kind == SG_ENV_PWC ? d.nseg : 1);
       const int pt = 64;
-      SubTimes sub{};
-      for (int j = 0; j < s.ta.nsub; ++j) sub.tau[j] = s.ta.tau[j].x;
       k_pulse_chain<<<s.K, pt, pt * (np_max + 1) * sizeof(double), st>>>(
-          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar, s.q2 ? s.ta.nsub : 0,
-          sub);
+          sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar, s.q2 ? s.ta.nsub : 0);
     } else {
       SG_CUDA_TRY(ctx, cudaMemsetAsync(omega_bar, 0, sizeof(double), st));
     }

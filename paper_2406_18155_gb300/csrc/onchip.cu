@@ -740,13 +740,14 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
 
 // Backward of Q2 for the pulse gradient (Sec. 2.5 on the product of Sec. 2.3).  The
 // final states psi and the co-state psibar (lab frame) are pulled back through every
-// factor in reverse order, psi <- X^dag psi and psibar <- X^dag psibar.  A 1-body half
+// factor in reverse order, psi <- X^-1 psi and psibar <- X^dag psibar (X^-1 = X^dag for
+// the unitary factors of Q2 and Q4; not for the complex steps of Q4j).  A 1-body half
 // step is X = prod_i U_i (commuting factors on distinct modes), and for a drive k on
 // mode i, dX/df_k = (prod_{j != i} U_j) L_k with L_k the Frechet derivative of the
 // local exponential, so with the states before the half step
-//   Re <psibar_after, dX/df_k psi_before> = Re <psibar_before, U_i^dag L_k psi_before>
+//   Re <psibar_after, dX/df_k psi_before> = Re <psibar_before, U_i^-1 L_k psi_before>
 //                                         = Re sum_ab M_k[a][b] C_i[a][b],
-// M_k = U_i^dag L_k and C_i[a][b] = sum conj(psibar_before[a, ..]) psi_before[b, ..]
+// M_k = U_i^-1 L_k and C_i[a][b] = sum conj(psibar_before[a, ..]) psi_before[b, ..]
 // the cross-density over mode i.  Each thread contracts its blocks' cross-densities
 // with M_k at once, so a sub-step reduces one scalar per drive over the CTA (warp
 // shuffles, then the warps in fixed order) into slot n (the sub-step) of the CTA's gF
@@ -755,7 +756,7 @@ constexpr int kQ2G = 16;          // drives of a Q2 gradient solve (per-thread p
 struct Q2AdjArgs {
   int nq, K, ne, n1f;             // modes, drives, couplings, 1-body factors of a half step
   int J;                          // Q2 sub-steps per step
-  int setoff[3];                  // first matrix of sub-step j's adjoint coupling set: 2 ne set(j)
+  int setoff[3];                  // first matrix of sub-step j's pull-back coupling set: 4 ne set(j)
   int row;                        // (nq + K) d^2: U_i(n)^dag then M_k(n)
   unsigned driven;                // bit i: a drive acts on mode i
   Phase one[SG_MAXQ / 2 + 1];     // pairs (offL, offR) and an odd last mode (offA)
@@ -799,8 +800,9 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
   double* gFc = gF_cta + (size_t)cta * nstK;
   int buf = 0;
   for (int n = N - 1; n >= 0; --n) {
-    const C* U = buf ? M1 : M0;
-    const C* Mk = U + qa.nq * DL * DL;
+    const C* U = buf ? M1 : M0;                                        // U^-1 (states)
+    const C* Ud = U + qa.nq * DL * DL;                                 // U^dag (co-states)
+    const C* Mk = Ud + qa.nq * DL * DL;
     const int so = qa.setoff[n % qa.J];
     if (n > 0) issue_rows<C>(rows, qa.row, n - 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
     R g[kQ2G];
@@ -810,12 +812,13 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
       if (h == 1) {                                                  // couplings (palindrome)
         for (int q = 0; q < 2 * qa.ne - 1; ++q) {
           const int e = q < qa.ne ? q : 2 * qa.ne - 2 - q;
-          const C* Gd = G + (size_t)(so + 2 * e + (q == qa.ne - 1 ? 1 : 0)) * DL * DL * DL * DL;
+          const C* Gi = G + (size_t)(so + 4 * e + (q == qa.ne - 1 ? 1 : 0)) * DL * DL * DL * DL;
+          const C* Gd = Gi + (size_t)2 * DL * DL * DL * DL;
           const Phase& P = qa.edge[e];
           for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
             const int c = b / oa.nbc;
             const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
-            block_dense<DL>(Gd, xs, t1, pb, P.psa, P.psb);
+            block_dense<DL>(Gi, xs, t1, pb, P.psa, P.psb);
             block_dense<DL>(Gd, xb, t2, pb, P.psa, P.psb);
           }
           __syncthreads();
@@ -830,7 +833,7 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
           const int c = b / oa.nbc;
           const int pb = blk_pos<DL>(P, b - c * oa.nbc) + c * oa.CS;
           phase_block<DL, false>(P, U, xs, t1, pb, true);
-          phase_block<DL, false>(P, U, xb, t2, pb, true);
+          phase_block<DL, false>(P, Ud, xb, t2, pb, true);
         }
         __syncthreads();
         C* tmp = xs; xs = t1; t1 = tmp;
@@ -980,7 +983,7 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
   a.b_x1 = take(a.CSP * cs);
   a.b_x2 = take(a.CSP * cs);
   a.b_x3 = take(a.CSP * cs);
-  a.b_rowcap = a.rowA + a.K * DL * DL;                     // rowA >= nq d^2 in the lab frame
+  a.b_rowcap = 2 * a.rowA + a.K * DL * DL;                 // rowA >= nq d^2 in the lab frame
   a.b_rowcap += a.b_rowcap & 1;
   a.b_rows = take(2 * (size_t)a.b_rowcap * cs);            // double-buffered step rows
   a.b_red = take((size_t)(kST / 32) * 16 * sizeof(double));
@@ -1273,7 +1276,7 @@ int q2adj_t(const OnchipPlan* oc, const Q2AdjArgs& qa, const void* rows, const v
             const double2* bar, int N, int nset, double* gF_cta, long long nstK, cudaStream_t st) {
   typedef typename CT<R>::T C;
   smem_limit_once<k_oc_q2_adj<R, DL>>();
-  const int nedge = 2 * qa.ne * nset * DL * DL * DL * DL;
+  const int nedge = 4 * qa.ne * nset * DL * DL * DL * DL;
   const bool gsm = oc->oa.b_G + (size_t)nedge * sizeof(C) <= oc->limit;
   const size_t smem = oc->oa.b_G + (gsm ? (size_t)nedge * sizeof(C) : 0);
   k_oc_q2_adj<R, DL><<<oc->oa.ncta, kST, smem, st>>>(oc->h->pass[0], oc->oa, qa, (const C*)rows, (const C*)edges,
@@ -1297,7 +1300,7 @@ sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const in
   qa.nq = p.nq;
   qa.K = K;
   qa.ne = p.ne;
-  qa.row = (p.nq + K) * DL * DL;
+  qa.row = (2 * p.nq + K) * DL * DL;
   for (int i = 0; i < p.nq; i += 2) {
     Phase& P = qa.one[qa.n1f++];
     if (i + 1 < p.nq) {
@@ -1316,7 +1319,7 @@ sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const in
     qa.driven |= 1u << drv_mode[k];
   }
   qa.J = J;
-  for (int j = 0; j < J; ++j) qa.setoff[j] = 2 * p.ne * set_of[j];
+  for (int j = 0; j < J; ++j) qa.setoff[j] = 4 * p.ne * set_of[j];      // per set and coupling: inverse and adjoint pairs
   int n = 0;
   if (oc->mixed) {
     switch (DL) {

@@ -84,12 +84,12 @@ int onchip_dl(const OnchipPlan* oc);
 // Suzuki-Trotter pulse gradient: pulls the final states psi and the co-state bar (API
 // layout, lab frame) back through every factor of the N Q2 sub-steps and adds dF/df_k
 // at sub-step n to gF_cta (CTA-major blocks of nstK >= N K doubles, slot n K + k;
-// zeroed by the caller).  rows: [N][nq + K][d^2], per sub-step the adjoint 1-body
-// half-step unitaries U_i(n)^dag, then M_k(n) = U_i(n)^dag L_k(n) with L_k the Frechet
-// derivative of the local exponential along drive k's operator; edges: the adjoint
-// coupling unitaries (half^dag, full^dag) in the forward's set layout.  Unitary factors
-// only (the inverse of a factor is its adjoint).  SG_E_UNSUPPORTED for one mode, more
-// than 32 couplings or 16 drives, or when the layout does not fit in shared memory.
+// zeroed by the caller).  rows: [N][2 nq + K][d^2], per sub-step the inverse 1-body
+// half-step factors U_i(n)^-1 (states), their adjoints U_i(n)^dag (co-states), then
+// M_k(n) = U_i(n)^-1 L_k(n) with L_k the Frechet derivative of the local exponential
+// along drive k's operator; edges: per set and coupling the inverse (half, full) and
+// adjoint (half, full) coupling factors.  SG_E_UNSUPPORTED for one mode, more than 32
+// couplings or 16 drives, or when the layout does not fit in shared memory.
 sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
                                   const void* edges, const double2* psi, const double2* bar, int N, int J,
                                   const int* set_of, int nset, long long nstK, double* gF_cta, cudaStream_t st,

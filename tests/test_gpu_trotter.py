@@ -1,8 +1,8 @@
 """GPU parity of the Suzuki-Trotter solvers (Sec. 2.3, App. A: Q2, Q4, Q4j) against
 the oracle's: lab-frame states and fidelities, FP64 within 1e-10, FP32 factors and
-state within 1e-5 on short evolutions; the pulse-parameter gradient of Q2 and Q4
-(discrete adjoint of the product of unitaries, Sec. 2.5) against the oracle's
-adjoint, FP64 within 1e-9 and FP32 within 2e-4 of the largest component;
+state within 1e-5 on short evolutions; the pulse-parameter gradient of Q2, Q4 and
+Q4j (discrete adjoint of the product of local factors, Sec. 2.5) against the
+oracle's adjoint, FP64 within 1e-9 and FP32 within 2e-4 of the largest component;
 unsupported requests are rejected."""
 import numpy as np
 import pytest
@@ -129,28 +129,21 @@ def test_fourth_order_products_match_oracle(sgctx, default_path, name, scheme):
     assert np.max(np.abs(psi32 - ref)) < 1e-5
 
 
+@pytest.mark.parametrize("scheme", ["q4", "q4j"])
 @pytest.mark.parametrize("name", ["transmon_pair", "ring4_l3", "pair_cr_l5", "local_ops_l3"])
-def test_q4_pulse_gradient_matches_oracle(sgctx, default_path, name):
+def test_fourth_order_pulse_gradient_matches_oracle(sgctx, default_path, name, scheme):
+    # Q4j's complex steps make its factors non-unitary: the states are pulled back by
+    # the inverses and the co-states by the adjoints
     wl = CASES[name]()
     s = _system(sgctx, wl)
-    F_r, g_r = q2_pulse_gradient(wl, scheme="q4")
+    F_r, g_r = q2_pulse_gradient(wl, scheme=scheme)
     scale = max(1.0, np.max(np.abs(g_r)))
     for prec, tol_F, tol_g in (("fp64", 1e-10, 1e-9), ("mixed", 1e-5, 2e-4)):
         F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
-                                   precision=prec, ham=False, solver="q4")
+                                   precision=prec, ham=False, solver=scheme)
         Fk = F[0] if wl["fid_kind"] == "avg" else F[1]
         assert abs(Fk - F_r) < tol_F, (prec, Fk, F_r)
         assert np.max(np.abs(gp - g_r)) < tol_g * scale, (prec, np.max(np.abs(gp - g_r)), scale)
-
-
-def test_q4j_gradient_is_refused(sgctx, default_path):
-    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
-    wl = CASES["transmon_pair"]()
-    s = _system(sgctx, wl)
-    with pytest.raises(SGError) as e:
-        s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
-                        precision="fp64", ham=False, solver="q4j")
-    assert e.value.code == SG_E_UNSUPPORTED
 
 
 @pytest.mark.parametrize("steps", [1, 3])
@@ -166,8 +159,6 @@ def test_edge_cases_single_step_and_no_couplings(sgctx, default_path, steps, sch
     ref = q2_evolve(so, initial_columns(so, wl["col_index"]), scheme=scheme)
     psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver=scheme).cpu().numpy()
     assert np.max(np.abs(psi - ref)) < 1e-12
-    if scheme == "q4j":
-        return
     F_r, g_r = q2_pulse_gradient(wl, scheme=scheme)
     F, gp, _ = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
                                precision="fp64", ham=False, solver=scheme)
