@@ -251,7 +251,7 @@ class System:
                       basis="product"):
         """F and the gradient w.r.t. the pulse and (ham=True) Hamiltonian parameters;
         with ham=False the Hamiltonian part is not computed and returned as None.
-        solver "q2" or "q4" (lab frame) computes the pulse-parameter gradient only: pass ham=False.
+        solver "q2", "q4" or "q4j" (lab frame) computes the pulse-parameter gradient only: pass ham=False.
         compensation "vz": F with the virtual Z gates that maximise it, and its gradient;
         basis "dressed" (pulse gradient only: ham=False): the gate in the idle eigenbasis."""
         o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver, compensation=compensation,
