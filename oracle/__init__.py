@@ -17,6 +17,7 @@ What it computes (paper sections in brackets):
   and its discrete adjoint for the pulse parameters              [Sec. 2.5]
 * virtual-Z compensation of the gate fidelity and the dressed
   (idle-Hamiltonian eigen-) basis of the gate metric              [App. C]
+* the vectorised Lindblad master equation (density matrices)     [App. C]
 * the composite state-transfer cost and the average gate
   fidelity                                                      [Eq. 13, Eq. D2]
 * the exact discrete adjoint of RK4 (the discretise-then-

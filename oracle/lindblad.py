@@ -1,0 +1,72 @@
+"""Open-system evolution by the vectorised Lindblad master equation (oracle; test
+infrastructure).
+
+The paper notes (App. C, last paragraph; Sec. 2) that the dynamics of a density
+matrix is characterised by a superoperator obtained from the vectorised Lindblad
+master equation, and that its solver and back-propagation carry over to it.  What is
+computed here, in the frame of the workload (R1):
+
+    d rho / dt = -i [H(t), rho] + sum_c gamma_c (L_c rho L_c^dag - {L_c^dag L_c, rho} / 2),
+
+with row-major vectorisation vec(A rho B) = (A (x) B^T) vec(rho), so that
+
+    Lv(t) = -i (H (x) I - I (x) H^T)
+            + sum_c gamma_c (L (x) L^* - (L^dag L) (x) I / 2 - I (x) (L^dag L)^T / 2),
+
+evolved by the same fixed-step RK4 as the state columns (stage times of R2).
+Readings taken here (the paper gives no formulas for it):
+
+* a collapse operator acts on one mode: workload key "collapse", a list of
+  {"mode": i, "L": d x d matrix in the truncated eigenbasis, "rate": gamma (1/ns)};
+* in the interaction frame the collapse operators rotate with the frame like every
+  other operator, L_I(t) = exp(i H_d t) L exp(-i H_d t), and the lab-frame density
+  matrix is exp(-i H_d T) rho_I exp(i H_d T);
+* the state fidelity of rho against a pure target |t> is <t| rho |t>.
+"""
+import numpy as np
+
+from .system import OracleSystem, stage_time
+
+
+def liouvillian(sys, n, j):
+    """Dense D^2 x D^2 generator at stage j of step n (frame of the system)."""
+    D = sys.D
+    H = sys.hamiltonian(n, j)
+    I = np.eye(D, dtype=np.complex128)
+    Lv = -1j * (np.kron(H, I) - np.kron(I, H.T))
+    t = stage_time(n, j, sys.dt)
+    for c in sys.wl.get("collapse", []):
+        L = sys.embed({c["mode"]: sys.frame_op(np.asarray(c["L"], dtype=np.complex128), c["mode"], t)})
+        LdL = L.conj().T @ L
+        Lv += c["rate"] * (np.kron(L, L.conj()) - 0.5 * np.kron(LdL, I) - 0.5 * np.kron(I, LdL.T))
+    return Lv
+
+
+def rk4_density(sys, rho0, nsteps=None):
+    """RK4 of vec(rho) under the generator; rho0 and the result are D x D."""
+    N = sys.N if nsteps is None else nsteps
+    dt = sys.dt
+    v = np.array(rho0, dtype=np.complex128).reshape(-1)
+    for n in range(N):
+        A1, A2, A4 = liouvillian(sys, n, 0), liouvillian(sys, n, 1), liouvillian(sys, n, 2)
+        k1 = A1 @ v
+        k2 = A2 @ (v + 0.5 * dt * k1)
+        k3 = A2 @ (v + 0.5 * dt * k2)
+        k4 = A4 @ (v + dt * k3)
+        v = v + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+    return v.reshape(sys.D, sys.D)
+
+
+def to_lab(sys, rho_frame, nsteps=None):
+    """Lab-frame density matrix from the frame's (exact diagonal phases, R1)."""
+    if sys.frame == "lab":
+        return rho_frame
+    N = sys.N if nsteps is None else nsteps
+    ph = np.exp(-1j * sys.hd_diag() * N * sys.dt)
+    return ph[:, None] * rho_frame * np.conj(ph)[None, :]
+
+
+def evolve_density(wl, rho0, nsteps=None):
+    """Lab-frame rho(T) of the workload from rho0 (D x D)."""
+    sys = OracleSystem(wl)
+    return to_lab(sys, rk4_density(sys, rho0, nsteps), nsteps)
