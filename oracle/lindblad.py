@@ -70,3 +70,31 @@ def evolve_density(wl, rho0, nsteps=None):
     """Lab-frame rho(T) of the workload from rho0 (D x D)."""
     sys = OracleSystem(wl)
     return to_lab(sys, rk4_density(sys, rho0, nsteps), nsteps)
+
+
+def gate_fidelity(wl, nsteps=None):
+    """Average gate fidelity of the open evolution on the computational states against
+    the workload's target unitary T (D_c x D_c): the channel's superoperator on the
+    computational block, S[(a, b), (j, k)] = <c_a| E(|c_j><c_k|) |c_b>, one density-matrix
+    evolution per (j, k); the entanglement (process) fidelity F_pro = sum conj(S_T) S / D_c^2
+    with S_T = T (x) T^*; and F_avg = (D_c^2 F_pro + P) / (D_c (D_c + 1)) with P = sum_j
+    tr P_c E(|c_j><c_j|) P_c the population kept in the computational block (Nielsen's
+    relation, which Eq. D2 restates through an operator basis, written for a channel
+    that may leak: P = D_c without leakage, and F_avg reduces to R10's
+    (tr M M^dag + |tr M|^2) / (D_c (D_c + 1)) for a closed evolution)."""
+    from .evolve import comp_map
+    sys = OracleSystem(wl)
+    comp, _ = comp_map(sys)
+    Dc = len(comp)
+    T = np.asarray(wl["target"], dtype=np.complex128)
+    S = np.zeros((Dc * Dc, Dc * Dc), dtype=np.complex128)
+    for j in range(Dc):
+        for k in range(Dc):
+            rho0 = np.zeros((sys.D, sys.D), dtype=np.complex128)
+            rho0[comp[j], comp[k]] = 1.0
+            rho = to_lab(sys, rk4_density(sys, rho0, nsteps), nsteps)
+            S[:, j * Dc + k] = rho[np.ix_(comp, comp)].reshape(-1)
+    S_T = np.kron(T, T.conj())
+    F_pro = np.real(np.sum(np.conj(S_T) * S)) / Dc ** 2
+    kept = sum(np.real(S[a * Dc + a, j * Dc + j]) for a in range(Dc) for j in range(Dc))
+    return (Dc * Dc * F_pro + kept) / (Dc * (Dc + 1.0)), F_pro

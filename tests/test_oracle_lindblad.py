@@ -80,3 +80,28 @@ def test_without_collapse_the_density_matrix_follows_the_pure_states():
     rho = evolve_density(wl, rho0)
     # RK4 of the superoperator and U rho U^dag with RK4's U agree to the RK4 error
     assert np.max(np.abs(rho - psi @ psi.conj().T)) < 1e-8
+
+
+def test_gate_fidelity_of_amplitude_damping_closed_form():
+    # the idle qubit under amplitude damping against the ideal idle gate diag(1, e^{-iET}):
+    # Kraus operators diag(1, sqrt(1-p)) and sqrt(p)|0><1|, p = 1 - e^{-g T}, so
+    # F_avg = (|1 + sqrt(1-p)|^2 + 2) / 6
+    from oracle.lindblad import gate_fidelity
+    g = 0.4
+    wl = _two_level([{"mode": 0, "L": [[0, 1], [0, 0]], "rate": g}], frame="interaction")
+    sys = OracleSystem(wl)
+    E = sys.modes[0]["E"][1] - sys.modes[0]["E"][0]
+    T = wl["T"]
+    wl["target"] = np.diag([1.0, np.exp(-1j * E * T)])
+    F, _ = gate_fidelity(wl)
+    p = 1.0 - np.exp(-g * T)
+    assert abs(F - ((1.0 + np.sqrt(1.0 - p)) ** 2 + 2.0) / 6.0) < 1e-12
+
+
+def test_gate_fidelity_without_collapse_matches_the_closed_system():
+    from oracle.evolve import evolve_and_fidelity
+    from oracle.lindblad import gate_fidelity
+    wl = W.fluxonium_pair_cr(seed=6, nseg=3, T=0.2)
+    wl["drives"][0]["length"] = 0.2
+    F, _ = gate_fidelity(wl)
+    assert abs(F - evolve_and_fidelity(wl)["F_avg"]) < 1e-8
