@@ -209,3 +209,100 @@ def q2_fidelity(wl, kind=None, scheme="q2"):
     """F of the scheme's evolution (for finite differences)."""
     r = q2_evolve_and_fidelity(wl, scheme)
     return r["F_avg"] if (kind or wl["fid_kind"]) == "avg" else r["F_state"]
+
+
+def trotter_full_gradient(wl, kind=None, scheme="q2"):
+    """F and dF/dtheta for every parameter (pulse, device E_J/E_C/E_L, couplings J) of
+    the scheme's evolution, by the discrete adjoint over its factors: for a factor
+    X = exp(G) with generator G = -i c (dt/2) H_loc, dX/dtheta = L(G, -i c (dt/2) dH_loc/dtheta)
+    (expm_frechet); a 1-body H_loc = diag(E_i) + sum f_k O_k varies with the pulse
+    parameters (through f_k), the mode's device parameters (energies and operators,
+    through the eigen-derivatives, and carriers tied to its 0-1 frequency); a coupling
+    H_loc = J A (x) B with J and the two modes' device parameters.  Lab frame.  Returns
+    (F, gradient in OracleSystem.param_list order)."""
+    from scipy.linalg import expm_frechet
+    from .evolve import initial_columns, fidelity_and_costate
+    sys = OracleSystem(dict(wl, frame="lab"))
+    kind = kind or wl["fid_kind"]
+    dt, N, S = sys.dt, sys.N, len(wl["col_index"])
+    subs = SCHEMES[scheme]
+    prms = sys.param_list()
+    derivs = {(i, p): sys.mode_derivs(i, p) for (pk, i, p) in prms if pk == "ham"}
+    psi = initial_columns(sys, wl["col_index"]).reshape(list(sys.dims) + [S])
+    _, two = local_terms(sys, 0)
+    tape = []
+    for n in range(N):
+        for j, (c, tau) in enumerate(subs):
+            one, _ = local_terms(sys, n, tau)
+            seq = [("1", i, -1j * c * (dt / 2) * one[i]) for i in range(sys.nq)]
+            seq += [("2", e, -1j * c * (dt / 2) * two[e][2]) for e in range(len(two))]
+            for kind_f, idx, G in seq + seq[::-1]:
+                tape.append((kind_f, idx, G, psi.copy(), n, j))
+                X = expm(G)
+                if kind_f == "1":
+                    psi = _apply_1body(psi, X, idx)
+                else:
+                    a, b, _ = two[idx]
+                    psi = _apply_2body(psi, X, a, b, sys.dims[a], sys.dims[b])
+    F, bar = fidelity_and_costate(sys, psi.reshape(sys.D, S), kind)
+    bar = bar.reshape(list(sys.dims) + [S])
+    grad = np.zeros(len(prms))
+    for kind_f, idx, G, before, n, j in reversed(tape):
+        c, tau = subs[j]
+        t = sub_time(sys, n, tau)
+        scale = -1j * c * (dt / 2)
+        for p, prm in enumerate(prms):
+            pk, a, b = prm
+            dH = None
+            if kind_f == "1":
+                i = idx
+                if pk == "pulse" and sys.drives[a]["mode"] == i:
+                    dr = sys.drives[a]
+                    _, dE = sub_envelope(dr, n, t, dt)
+                    dH = dE[b] * np.cos(sys.omega_d[a] * t + dr.get("phase", 0.0)) * sys.op(i, dr["op"])
+                elif pk == "ham":
+                    dEm, dops = derivs[(a, b)]
+                    dH = np.zeros((sys.dims[i], sys.dims[i]), dtype=np.complex128)
+                    if a == i:
+                        dH += np.diag(dEm)
+                    for k, dr in enumerate(sys.drives):
+                        if dr["mode"] != i:
+                            continue
+                        E, _ = sub_envelope(dr, n, t, dt)
+                        f = E * np.cos(sys.omega_d[k] * t + dr.get("phase", 0.0))
+                        if a == i:
+                            dH += f * sys.dop(dops, i, dr["op"])
+                        if dr.get("omega_mode") == a:
+                            df = -E * np.sin(sys.omega_d[k] * t + dr.get("phase", 0.0)) * t * dEm[1]
+                            dH += df * sys.op(i, dr["op"])
+                    if not np.any(dH):
+                        dH = None
+            else:
+                cpl = sys.couplings[idx]
+                A, B = sys.op(cpl["a"], cpl["op_a"]), sys.op(cpl["b"], cpl["op_b"])
+                if pk == "J" and a == idx:
+                    dH = np.kron(A, B)
+                elif pk == "ham" and a in (cpl["a"], cpl["b"]):
+                    dEm, dops = derivs[(a, b)]
+                    if a == cpl["a"]:
+                        dH = cpl["J"] * np.kron(sys.dop(dops, a, cpl["op_a"]), B)
+                    else:
+                        dH = cpl["J"] * np.kron(A, sys.dop(dops, a, cpl["op_b"]))
+                    if not np.any(dH):
+                        dH = None
+            if dH is None:
+                continue
+            L = expm_frechet(G, scale * dH, compute_expm=False)
+            if kind_f == "1":
+                dpsi = _apply_1body(before, L, idx)
+            else:
+                aa, bb, _ = two[idx]
+                dpsi = _apply_2body(before, L, aa, bb, sys.dims[aa], sys.dims[bb])
+            grad[p] += np.real(np.vdot(bar, dpsi))
+        X = expm(G)                                   # the co-state goes back through X^dag
+        if kind_f == "1":
+            bar = _apply_1body(bar, X.conj().T, idx)
+        else:
+            aa, bb, _ = two[idx]
+            bar = _apply_2body(bar, X.conj().T, aa, bb, sys.dims[aa], sys.dims[bb])
+    return F, grad

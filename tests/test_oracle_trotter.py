@@ -130,3 +130,27 @@ def test_pulse_gradient_matches_central_differences(scheme):
                 fd.append((vals[0] - vals[1]) / (2 * h))
         fd = np.array(fd)
         assert np.max(np.abs(g - fd)) <= 1e-6 * max(1e-3, np.max(np.abs(fd))), (g, fd)
+
+
+@pytest.mark.parametrize("scheme", ["q2", "q4"])
+def test_full_gradient_matches_central_differences_through_the_eigensolve(scheme):
+    # every parameter: pulse segments, E_J / E_C / E_L of each mode (through the
+    # subsystem eigendecomposition) and the coupling J
+    from oracle.evolve import param_vector, set_param_vector
+    from oracle.system import OracleSystem
+    from oracle.trotter import trotter_full_gradient, q2_fidelity, q2_pulse_gradient
+    wl = _lab(W.fluxonium_pair_multipath(seed=11, levels=3, nseg=2), 0.1, 0.01)
+    F, g = trotter_full_gradient(wl, scheme=scheme)
+    Fp, gp = q2_pulse_gradient(wl, scheme=scheme)
+    assert abs(F - Fp) < 1e-14 and np.max(np.abs(g[:len(gp)] - gp)) < 1e-12
+    theta = param_vector(wl)
+    prms = OracleSystem(wl).param_list()
+    for p, prm in enumerate(prms):
+        h = 1e-7 if prm[0] == "pulse" else 1e-5 * max(abs(theta[p]), 1e-3)
+        vals = []
+        for sgn in (1, -1):
+            th = theta.copy()
+            th[p] += sgn * h
+            vals.append(q2_fidelity(set_param_vector(wl, th), scheme=scheme))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(g[p] - fd) <= 1e-6 * max(1e-4, np.max(np.abs(g))), (prm, g[p], fd)
