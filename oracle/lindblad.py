@@ -98,3 +98,76 @@ def gate_fidelity(wl, nsteps=None):
     F_pro = np.real(np.sum(np.conj(S_T) * S)) / Dc ** 2
     kept = sum(np.real(S[a * Dc + a, j * Dc + j]) for a in range(Dc) for j in range(Dc))
     return (Dc * Dc * F_pro + kept) / (Dc * (Dc + 1.0)), F_pro
+
+
+def gate_fidelity_pulse_gradient(wl):
+    """F_avg of gate_fidelity and dF/d(pulse parameters) by the discrete adjoint of the
+    superoperator RK4.  F is linear in S, F = Re sum conj(W) S with W = (S_T + K) /
+    (D_c (D_c + 1)), K[(a, a), (j, j)] = 1 the kept-population indicator, so the co-state
+    of each evolved |c_j><c_k| is W's column (j, k) on the computational block; it is
+    pulled back through the frame phases and the RK4 steps with the generator's adjoint
+    and contracted with dLv/dtheta = -i (dH (x) I - I (x) dH^T) at every stage (Sec. 2.5
+    on the vectorised equation).  Pulse parameters only."""
+    from .evolve import comp_map
+    from .system import n_pulse_params
+    sys = OracleSystem(wl)
+    comp, _ = comp_map(sys)
+    Dc, D, N, dt = len(comp), sys.D, sys.N, sys.dt
+    T = np.asarray(wl["target"], dtype=np.complex128)
+    S_T = np.kron(T, T.conj())
+    W = S_T / (Dc * (Dc + 1.0))
+    for a in range(Dc):
+        for j in range(Dc):
+            W[a * Dc + a, j * Dc + j] += 1.0 / (Dc * (Dc + 1.0))
+    prms = [p for p in sys.param_list() if p[0] == "pulse"]
+    I = np.eye(D, dtype=np.complex128)
+    grad = np.zeros(len(prms))
+    F = 0.0
+    for j in range(Dc):
+        for k in range(Dc):
+            v = np.zeros(D * D, dtype=np.complex128)
+            v[comp[j] * D + comp[k]] = 1.0
+            hist = [v.copy()]
+            for n in range(N):
+                A1, A2, A4 = liouvillian(sys, n, 0), liouvillian(sys, n, 1), liouvillian(sys, n, 2)
+                k1 = A1 @ v
+                k2 = A2 @ (v + 0.5 * dt * k1)
+                k3 = A2 @ (v + 0.5 * dt * k2)
+                k4 = A4 @ (v + dt * k3)
+                v = v + (dt / 6.0) * (k1 + 2.0 * k2 + 2.0 * k3 + k4)
+                hist.append(v.copy())
+            rho = to_lab(sys, v.reshape(D, D))
+            col = W[:, j * Dc + k].reshape(Dc, Dc)
+            F += np.real(np.sum(np.conj(col) * rho[np.ix_(comp, comp)]))
+            bar_lab = np.zeros((D, D), dtype=np.complex128)
+            bar_lab[np.ix_(comp, comp)] = col
+            if sys.frame == "lab":
+                bar = bar_lab.reshape(-1)
+            else:
+                ph = np.exp(-1j * sys.hd_diag() * N * dt)
+                bar = (np.conj(ph)[:, None] * bar_lab * ph[None, :]).reshape(-1)
+            for n in range(N - 1, -1, -1):
+                y1 = hist[n]
+                A1, A2, A4 = liouvillian(sys, n, 0), liouvillian(sys, n, 1), liouvillian(sys, n, 2)
+                k1 = A1 @ y1
+                y2 = y1 + 0.5 * dt * k1
+                k2 = A2 @ y2
+                y3 = y1 + 0.5 * dt * k2
+                k3 = A2 @ y3
+                y4 = y1 + dt * k3
+                kb4 = (dt / 6.0) * bar
+                yb4 = A4.conj().T @ kb4
+                kb3 = (dt / 3.0) * bar + dt * yb4
+                yb3 = A2.conj().T @ kb3
+                kb2 = (dt / 3.0) * bar + 0.5 * dt * yb3
+                yb2 = A2.conj().T @ kb2
+                kb1 = (dt / 6.0) * bar + 0.5 * dt * yb2
+                for p, prm in enumerate(prms):
+                    d = []
+                    for jj in (0, 1, 2):
+                        dH = sys.dH(n, jj, prm)
+                        d.append(-1j * (np.kron(dH, I) - np.kron(I, dH.T)))
+                    grad[p] += np.real(np.vdot(kb1, d[0] @ y1) + np.vdot(kb2, d[1] @ y2)
+                                       + np.vdot(kb3, d[1] @ y3) + np.vdot(kb4, d[2] @ y4))
+                bar = bar + yb2 + yb3 + yb4 + A1.conj().T @ kb1
+    return F, grad

@@ -105,3 +105,25 @@ def test_gate_fidelity_without_collapse_matches_the_closed_system():
     wl["drives"][0]["length"] = 0.2
     F, _ = gate_fidelity(wl)
     assert abs(F - evolve_and_fidelity(wl)["F_avg"]) < 1e-8
+
+
+def test_gate_fidelity_pulse_gradient_matches_central_differences():
+    import copy
+    from oracle.lindblad import gate_fidelity, gate_fidelity_pulse_gradient
+    wl = W.transmon_pair(seed=2, T=0.06, dt=0.01)
+    wl["modes"] = [dict(m, levels=2) for m in wl["modes"]]
+    wl["col_index"] = [0, 1, 2, 3]
+    wl["drives"][0]["length"] = 0.06
+    wl["drives"][0]["sigma"], wl["drives"][0]["t0"] = 0.015, 0.03
+    wl["collapse"] = [{"mode": 0, "L": [[0, 1], [0, 0]], "rate": 0.5}, {"mode": 1, "L": [[0, 0], [0, 1]], "rate": 0.3}]
+    F, g = gate_fidelity_pulse_gradient(wl)
+    assert abs(F - gate_fidelity(wl)[0]) < 1e-13
+    amp = wl["drives"][0]["amp"]
+    h = 1e-6 * max(1.0, abs(amp))
+    vals = []
+    for sgn in (1, -1):
+        w2 = copy.deepcopy(wl)
+        w2["drives"][0]["amp"] = amp + sgn * h
+        vals.append(gate_fidelity(w2)[0])
+    fd = (vals[0] - vals[1]) / (2 * h)
+    assert abs(g[0] - fd) <= 1e-6 * max(1e-6, abs(fd)), (g[0], fd)
