@@ -73,3 +73,27 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         assert got[(name, "size")] == ctypes.sizeof(st), name
         for f in st._fields_:
             assert got[(name, f[0])] == getattr(st, f[0]).offset, (name, f[0])
+
+
+def test_binding_constants_match_the_header(tmp_path):
+    """Every SG_* constant of the binding has the header's value (status codes,
+    solvers, compensation, basis, operators, envelopes, precisions, frames, kinds)."""
+    import shutil
+    import subprocess
+    from paper_2406_18155_gb300 import capi
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    names = sorted(n for n in dir(capi) if re.fullmatch(r"SG_[A-Z0-9_]+", n) and isinstance(getattr(capi, n), int))
+    assert len(names) > 20
+    lines = ['#include <stdio.h>', '#include "sg.h"', "int main(void) {"]
+    lines += [f'  printf("{n} %d\\n", (int)({n}));' for n in names]
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "consts"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {l.split()[0]: int(l.split()[1]) for l in out if l.strip()}
+    for n in names:
+        assert got[n] == getattr(capi, n), n
