@@ -77,3 +77,40 @@ def test_dressed_pulse_gradient_matches_central_differences():
         fd.append((vals[0] - vals[1]) / (2 * h))
     fd = np.array(fd)
     assert np.max(np.abs(g - fd)) <= 1e-6 * max(1e-6, np.max(np.abs(fd))), (g, fd)
+
+
+def test_paper_multipath_chain_dressed_frequencies_and_zero_zz_coupling():
+    # Sec. 3.1's 3-qubit multipath chain: the printed dressed 0-1 frequencies, and the
+    # capacitive coupling at which the static ZZ rate of the left pair vanishes
+    import json
+    import os
+    from scipy.optimize import brentq
+    with open(os.path.join(os.path.dirname(__file__), "golden", "multipath_zz.json")) as f:
+        g = json.load(f)
+    GHZ, MHZ = W.GHZ, W.MHZ
+
+    def chain(jc):
+        modes = [dict(kind="fluxonium", ej=m["ej_GHz"] * GHZ, ec=m["ec_GHz"] * GHZ, el=m["el_GHz"] * GHZ,
+                      phi_ext=np.pi, levels=5, n_osc=50) for m in g["modes"]]
+        cpl = []
+        for a, b in ((0, 1), (1, 2)):
+            cpl.append({"a": a, "op_a": "n", "b": b, "op_b": "n", "J": jc})
+            cpl.append({"a": a, "op_a": "phi", "b": b, "op_b": "phi", "J": -g["J_L_MHz"] * MHZ})
+        return {"modes": modes, "couplings": cpl, "drives": [], "T": 1.0, "dt": 0.01, "frame": "lab",
+                "col_index": list(range(8)), "target": np.eye(8), "fid_kind": "avg"}
+
+    def levels(jc):
+        _, lam = dressed_vectors(OracleSystem(chain(jc)))
+        return lam                                  # labels |q1 q2 q3>, first qubit most significant
+
+    lam = levels(g["J_C_spectrum_MHz"] * MHZ)
+    f1, f2 = (lam[4] - lam[0]) / GHZ, (lam[2] - lam[0]) / GHZ
+    assert abs(f1 - g["dressed_f01_GHz"][0]) < g["f01_tolerance_GHz"]
+    assert abs(f2 - g["dressed_f01_GHz"][1]) < g["f01_tolerance_GHz"]
+
+    def zz(jc):
+        lam = levels(jc)
+        return lam[0] + lam[6] - lam[4] - lam[2]
+
+    root = brentq(zz, 5.0 * MHZ, 20.0 * MHZ, xtol=1e-9) / MHZ
+    assert abs(root - g["zz_zero_J_C_MHz"]) < g["J_C_tolerance_MHz"], root
