@@ -171,3 +171,46 @@ def gate_fidelity_pulse_gradient(wl):
                                        + np.vdot(kb3, d[1] @ y3) + np.vdot(kb4, d[2] @ y4))
                 bar = bar + yb2 + yb3 + yb4 + A1.conj().T @ kb1
     return F, grad
+
+
+def doubled_terms(sys, n, j):
+    """The generator as local terms on 2 nq doubled modes (ket modes 0..nq-1, bra modes
+    nq..2nq-1, row-major vec(rho) index = ket index * D + bra index): Lv = -i H_eff with
+    H_eff = sum of 1-body terms {mode: d x d} and 2-body terms (mode a, A, mode b, B)
+    of the Kronecker form the evolution kernels apply, with complex, non-Hermitian
+    factors:
+      ket 1-body  H_i(t) - (i/2) sum_c gamma_c L_c^dag L_c        (c on mode i)
+      bra 1-body -H_i(t)^T - (i/2) sum_c gamma_c (L_c^dag L_c)^T
+      ket 2-body  J A (x) B;   bra 2-body  -J A^T (x) B^T
+      jump        i gamma_c L_c (ket i) (x) L_c^* (bra i).
+    Returns (one, two): one[m] a d x d matrix per doubled mode, two a list of
+    (a, A, b, B)."""
+    t = stage_time(n, j, sys.dt)
+    nq = sys.nq
+    one = []
+    for side in (0, 1):
+        for i in range(nq):
+            d = sys.dims[i]
+            h = np.zeros((d, d), dtype=np.complex128)
+            if sys.frame == "lab":
+                h += np.diag(sys.modes[i]["E"])
+            for k, dr in enumerate(sys.drives):
+                if dr["mode"] == i:
+                    h += sys.coeff(k, n, j) * sys.frame_op(sys.op(i, dr["op"]), i, t)
+            anti = np.zeros((d, d), dtype=np.complex128)
+            for c in sys.wl.get("collapse", []):
+                if c["mode"] == i:
+                    L = sys.frame_op(np.asarray(c["L"], dtype=np.complex128), i, t)
+                    anti += c["rate"] * (L.conj().T @ L)
+            one.append(h - 0.5j * anti if side == 0 else -h.T - 0.5j * anti.T)
+    two = []
+    for cpl in sys.couplings:
+        A = sys.frame_op(sys.op(cpl["a"], cpl["op_a"]), cpl["a"], t)
+        B = sys.frame_op(sys.op(cpl["b"], cpl["op_b"]), cpl["b"], t)
+        two.append((cpl["a"], cpl["J"] * A, cpl["b"], B))
+        two.append((nq + cpl["a"], -cpl["J"] * A.T, nq + cpl["b"], B.T))
+    for c in sys.wl.get("collapse", []):
+        i = c["mode"]
+        L = sys.frame_op(np.asarray(c["L"], dtype=np.complex128), i, t)
+        two.append((i, 1j * c["rate"] * L, nq + i, L.conj()))
+    return one, two
