@@ -112,8 +112,15 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# algorithmic bytes per entry of each kernel family (see DESIGN.md)
+# algorithmic bytes per entry of each kernel family
 # ----------------------------------------------------------------------------
+# Minimal fused two-pass RK4 step on a slab that exceeds one tile (two overlapping
+# mode groups per stage), bytes per entry and step: complex64 stages with the
+# complex128 state 304, all complex128 448.  The forward stage pass's roofline uses
+# this figure, one eighth of it per launch (four stages x two passes).
+FWD_STEP_BYTES_TWO_PASS = {8: 304, 16: 448}
+
+
 def fwd_bytes_per_entry_step(c, npass):
     """Forward RK4 step, bytes per slab entry: c = bytes of a stage value (8 mixed,
     16 FP64); the state psi is complex128 (16)."""
@@ -148,6 +155,34 @@ def store_bytes_per_entry_step(c, npass):
     return 3 * (2 * c + (npass - 2) * 3 * c + (c + c + p + c))
 
 
+def grad_set(args):
+    """Gradient set of the configuration: the ring asks for its pulse segments,
+    the others for every parameter."""
+    if args.grad != "config":
+        return args.grad
+    return "pulse" if args.workload == "fluxonium_ring10" else "all"
+
+
+def bench_config(args, wl, desc, world):
+    """The workload description printed by both arms (identical by construction)."""
+    S = len(wl["col_index"])
+    N = int(round(wl["T"] / wl["dt"]))
+    D = int(np.prod([m["levels"] for m in wl["modes"]]))
+    return {"workload": f"{args.workload}: {desc}", "columns": S, "rk4_steps": N,
+            "composite_dim": D, "precision": args.precision,
+            "gradient": "pulse parameters" if grad_set(args) == "pulse"
+            else "pulse and Hamiltonian parameters",
+            "l2": "inputs larger than L2 (slab 128 MiB c64 / 256 MiB c128)"
+            if D * S * 8 > 129e6 else "L2-resident working set; no flush",
+            "parallelism": f"{world} independent replica(s), one per GPU"}
+
+
+def _json_num(x):
+    """A float for the JSON line; None where it is undefined (NaN)."""
+    x = float(x)
+    return None if x != x else x
+
+
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
@@ -179,8 +214,7 @@ def run_ours(args):
     prec = args.precision
     stream = torch.cuda.current_stream(local)
 
-    # gradient set of the configuration: the ring asks for the pulse segments only
-    grad = args.grad if args.grad != "config" else ("pulse" if args.workload == "fluxonium_ring10" else "all")
+    grad = grad_set(args)
     args.grad_set = grad
 
     def one_step(ham=(grad == "all")):
@@ -257,15 +291,10 @@ def run_ours(args):
                "scaling": "weak", "vs_baseline": None,
                "dtype": "c64 stages, c128 state/co-state, f64 reductions" if prec == "mixed" else "c128",
                "data": "synthetic (seeded, shapes and value ranges of the paper's fluxonium workloads)",
-               "config": {"workload": f"{args.workload}: {desc}", "columns": S, "rk4_steps": N,
-                          "composite_dim": D, "precision": prec,
-                          "gradient": "pulse parameters" if grad == "pulse" else "pulse and Hamiltonian parameters",
-                          "l2": "inputs larger than L2 (slab 128 MiB c64 / 256 MiB c128)"
-                          if D * S * 8 > 129e6 else "L2-resident working set; no flush",
-                          "parallelism": f"{world} independent replica(s), one per GPU"},
+               "config": bench_config(args, wl, desc, world),
                "forward_ms": statistics.mean(fwd_ms), "gradient_ms": statistics.mean(bwd_ms),
                "O_t": (statistics.mean(fwd_ms) + statistics.mean(bwd_ms)) / statistics.mean(fwd_ms),
-               "peak_library_bytes": peak, "F": [float(F[0]), float(F[1])],
+               "peak_library_bytes": peak, "F": [_json_num(F[0]), _json_num(F[1])],
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                        "d2h_bytes_per_step": int(d2h)},
                "gpu_launches": int(launches), "clocks": clocks}
@@ -284,7 +313,8 @@ def run_ours(args):
                                     "note": "pulse + Hamiltonian parameters, one untimed-by-events run"}
         # ---- the plain FP64 GPU path on a bounded number of steps
         if args.fp64_steps > 0:
-            out["fp64_vs_mixed"] = fp64_comparison(sysm, wl, args.fp64_steps, stream)
+            out["fp64_vs_mixed"] = fp64_comparison(sysm, wl, args.fp64_steps, args.fp64_grad_steps,
+                                                   grad == "all", stream)
         if args.q2 and D <= 4096:
             out["q2_vs_rk4"] = q2_comparison(sysm, wl, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -403,7 +433,8 @@ def roofline(fam, D, S, N, prec, sysm, args):
     c = 8 if prec == "mixed" else 16
     npass = slab_passes(D)
     E = D * S
-    per_step = {"forward_stage_pass": fwd_bytes_per_entry_step(c, npass),
+    fwd_step = FWD_STEP_BYTES_TWO_PASS[c] if npass == 2 else fwd_bytes_per_entry_step(c, npass)
+    per_step = {"forward_stage_pass": fwd_step,
                 "adjoint_stage_pass": adj_bytes_per_entry_step(c, npass),
                 "recompute_stage_pass": store_bytes_per_entry_step(c, npass)}
     launches_per_step = {"forward_stage_pass": 4 * npass, "adjoint_stage_pass": 4 * npass,
@@ -433,27 +464,76 @@ def roofline(fam, D, S, N, prec, sysm, args):
             traffic = t[key]
     return ({"bound": "hbm", "kernel": dom, "achieved": f["achieved_gbs"], "peak": hbm,
              "unit": "GB/s", "frac": f["achieved_gbs"] / hbm, "peak_source": src,
-             "traffic": traffic}, fams)
+             "traffic": traffic,
+             "bytes_per_entry_step": per_step[dom], "launches_per_step": launches_per_step[dom]}, fams)
 
 
-def fp64_comparison(sysm, wl, nsteps, stream):
-    """The plain FP64 GPU path against the mixed one, forward RK4 over the first
-    nsteps steps of the same workload (same columns), device time."""
+def _normalised_target(wl, psi):
+    """Target whose column for each evolved computational state is that column's
+    normalised computational rows in psi: F_state is then close to 1, so a
+    difference in F is a difference in infidelity."""
+    dims = [m["levels"] for m in wl["modes"]]
+    comp = W.comp_states(dims)
+    lab = {r: j for j, r in enumerate(comp)}
+    T = np.zeros((len(comp), len(comp)), dtype=np.complex128)
+    for s_, r in enumerate(wl["col_index"]):
+        if r in lab:
+            v = psi[comp, s_]
+            T[:, lab[r]] = v / max(np.linalg.norm(v), 1e-300)
+    return T
+
+
+def _timed(stream, fn):
     import torch
-    T = nsteps * wl["dt"]
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return r, e0.elapsed_time(e1) / 1e3
+
+
+def fp64_comparison(sysm, wl, nsteps, grad_steps, ham, stream):
+    """The plain FP64 GPU path against the mixed one on the same workload and
+    columns, device time of the public calls after a warm call:
+      forward  - sg_evolve over the first nsteps steps; the mixed result's largest
+                 amplitude error against FP64;
+      gradient - sg_fidelity_grad over the first grad_steps steps (the
+                 configuration's gradient set) with the FP64 forward's normalised
+                 computational rows as target (F_state close to 1); |dF| and the
+                 gradient error relative to its largest component."""
+    S = len(wl["col_index"])
     out = {"steps": nsteps}
+    psi = {}
     for prec in ("fp64", "mixed"):
+        T = nsteps * wl["dt"]
         sysm.evolve(T, wl["dt"], precision=prec, col_index=wl["col_index"])   # warm
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sysm.evolve(T, wl["dt"], precision=prec, col_index=wl["col_index"])
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t = e0.elapsed_time(e1) / 1e3
-        out[f"{prec}_forward_col_steps_per_s"] = len(wl["col_index"]) * nsteps / t
+        p, t = _timed(stream, lambda: sysm.evolve(T, wl["dt"], precision=prec, col_index=wl["col_index"]))
+        psi[prec] = p.cpu().numpy()
+        out[f"{prec}_forward_col_steps_per_s"] = S * nsteps / t
     out["mixed_over_fp64"] = out["mixed_forward_col_steps_per_s"] / out["fp64_forward_col_steps_per_s"]
+    out["max_abs_dpsi"] = float(np.max(np.abs(psi["mixed"] - psi["fp64"])))
+    if grad_steps > 0:
+        Tg = grad_steps * wl["dt"]
+        p64 = sysm.evolve(Tg, wl["dt"], precision="fp64", col_index=wl["col_index"]).cpu().numpy()
+        target = _normalised_target(wl, p64)
+        g = {"steps": grad_steps, "gradient": "pulse and Hamiltonian parameters" if ham else "pulse parameters"}
+        res = {}
+        for prec in ("fp64", "mixed"):
+            call = lambda: sysm.fidelity_grad(Tg, wl["dt"], target, wl["col_index"], kind="state",
+                                              precision=prec, ham=ham)
+            call()                                                            # warm
+            (F, gp, gh), t = _timed(stream, call)
+            res[prec] = (F, np.concatenate([gp, gh]) if ham else gp)
+            g[f"{prec}_col_steps_per_s"] = S * grad_steps / t
+        g["mixed_over_fp64"] = g["mixed_col_steps_per_s"] / g["fp64_col_steps_per_s"]
+        g["F_state_fp64"] = float(res["fp64"][0][1])
+        g["abs_dF_state"] = abs(float(res["mixed"][0][1]) - float(res["fp64"][0][1]))
+        gm = np.max(np.abs(res["fp64"][1]))
+        g["rel_dgrad"] = float(np.max(np.abs(res["mixed"][1] - res["fp64"][1])) / max(gm, 1e-300))
+        out["gradient"] = g
     return out
 
 
@@ -516,23 +596,71 @@ def q2_comparison(sysm, wl, stream):
     return out
 
 
-def cpu_baseline(wl, nsteps):
-    """The FP64 oracle as it stands on this host: matrix-free RK4 (per-mode tensor
-    contraction) of one column for nsteps steps.  numpy.einsum without path
-    optimisation runs on one thread."""
-    import oracle
+_W_SYS = None
+
+
+def _oracle_worker_init(wl):
+    """Pool worker: the oracle's system of the workload, built once per process."""
+    global _W_SYS
+    from oracle.system import OracleSystem
+    _W_SYS = OracleSystem(wl)
+
+
+def _oracle_worker_run(job):
+    col, nsteps = job
+    from oracle.evolve import initial_columns, rk4_evolve_matrix_free
+    rk4_evolve_matrix_free(_W_SYS, initial_columns(_W_SYS, [col]), nsteps=nsteps)
+    return col
+
+
+class OraclePool:
+    """The FP64 oracle's matrix-free RK4 forward on the host cores: one spawned
+    process per core (numpy.einsum without path optimisation runs on one thread),
+    each evolving whole columns of the workload."""
+
+    def __init__(self, wl, cores):
+        import multiprocessing as mp
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        self.cores = max(1, cores)
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_worker_init,
+                                                 initargs=(wl,))
+        self.pool.map(_oracle_worker_run, [(wl["col_index"][0], 0)] * self.cores)   # start-up
+
+    def run(self, cols, nsteps):
+        t0 = time.perf_counter()
+        self.pool.map(_oracle_worker_run, [(c, nsteps) for c in cols], chunksize=1)
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(wl, nsteps, repeats=3):
+    """The FP64 oracle as it stands on this host, forward part of the step only
+    (its adjoint forms dense D x D matrices and cannot run at D = 2^20): the
+    matrix-free RK4 of nsteps steps, on one core (one column) and on every core
+    (as many columns as cores, at most the workload's), each the best of
+    `repeats` runs."""
     from oracle.evolve import initial_columns, rk4_evolve_matrix_free
     from oracle.system import OracleSystem
     s = OracleSystem(wl)
-    psi0 = initial_columns(s, wl["col_index"][:1])
-    t0 = time.perf_counter()
-    rk4_evolve_matrix_free(s, psi0, nsteps=nsteps)
-    t = time.perf_counter() - t0
-    return {"value": nsteps / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"matrix-free FP64 forward RK4, 1 of {len(wl['col_index'])} columns, "
-                      f"{nsteps} steps ({t:.1f} s); the oracle's adjoint forms dense D x D "
-                      "matrices and cannot run at this D, so the sample covers the forward "
-                      "part of the step"}
+    one = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        rk4_evolve_matrix_free(s, initial_columns(s, wl["col_index"][:1]), nsteps=nsteps)
+        one.append(nsteps / (time.perf_counter() - t0))
+    cores = min(os.cpu_count() or 1, len(wl["col_index"]))
+    pool = OraclePool(wl, cores)
+    cols = wl["col_index"][:cores]
+    allc = [len(cols) * nsteps / pool.run(cols, nsteps) for _ in range(repeats)]
+    pool.close()
+    return {"value": max(allc), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "one_core": {"value": max(one), "cores": 1},
+            "sample": f"forward only: matrix-free FP64 RK4, {nsteps} steps of {len(cols)} of the "
+                      f"{len(wl['col_index'])} columns, one process per core; best of {repeats} "
+                      f"(one core: 1 column, {max(one):.3g} col-steps/s). The oracle's adjoint forms "
+                      "dense D x D matrices and cannot run at this D"}
 
 
 # ----------------------------------------------------------------------------
@@ -544,21 +672,28 @@ def run_reference(args):
         return
     desc, make = WORKLOADS[args.workload]
     wl = make(1000)
-    vals = []
-    for i in range(args.warmup + args.steps):
-        r = cpu_baseline(wl, args.cpu_sample_steps)
-        if i >= args.warmup:
-            vals.append(r["value"])
-    v = statistics.mean(vals)
-    N = int(round(wl["T"] / wl["dt"]))
+    cores = min(os.cpu_count() or 1, len(wl["col_index"]))
+    pool = OraclePool(wl, cores)
+    cols = wl["col_index"][:cores]
+    ns = args.ref_sample_steps
+    for _ in range(args.warmup):
+        pool.run(cols, ns)
+    tot = 0.0
+    for _ in range(args.steps):
+        tot += pool.run(cols, ns)
+    pool.close()
+    units = len(cols) * ns * args.steps
+    v = units / tot
+    sample = (f"forward only: matrix-free FP64 RK4, {ns} step(s) of {len(cols)} "
+              f"of the {len(wl['col_index'])} columns per step, one process per core; the "
+              "oracle's adjoint forms dense D x D matrices and cannot run at this D")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": args.cpu_sample_steps / v * 1e3, "higher_is_better": True,
+           "ms_per_step": tot / args.steps * 1e3, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-           "config": {"workload": f"{args.workload}: {desc}", "columns": len(wl["col_index"]),
-                      "rk4_steps": N, "precision": "fp64"},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": r["sample"]},
+           "config": bench_config(args, wl, desc, world),
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": sample},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -572,9 +707,15 @@ def main():
     ap.add_argument("--workload", default="fluxonium_ring10", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--ckpt", type=int, default=0)
-    ap.add_argument("--fp64-steps", type=int, default=32)
+    ap.add_argument("--fp64-steps", type=int, default=64,
+                    help="forward steps of the FP64-vs-mixed comparison (0: skip)")
+    ap.add_argument("--fp64-grad-steps", type=int, default=64,
+                    help="steps of the FP64-vs-mixed gradient-solve comparison (0: skip)")
     ap.add_argument("--e2e-steps", type=int, default=1)
-    ap.add_argument("--cpu-sample-steps", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=2,
+                    help="RK4 steps per column of the oracle sample beside our line")
+    ap.add_argument("--ref-sample-steps", type=int, default=1,
+                    help="RK4 steps per column of each reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=64, help="Poisson requests of the serving sample (0: skip); twice as many run saturated first")
     ap.add_argument("--serving-slots", type=int, default=32)
