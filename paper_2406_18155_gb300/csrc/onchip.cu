@@ -83,16 +83,14 @@ __device__ __forceinline__ bool mb_try(uint64_t* mb, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase `parity` of mb: gives up after about a second,
-// records the failure in *err and lets the kernel run to its end without waiting
-// again (once *err is set every later wait returns at once).
-__device__ __forceinline__ void mb_wait(uint64_t* mb, unsigned parity, int* err) {
-  if (*(volatile int*)err) return;
-  for (int it = 0; it < (1 << 22); ++it) {
-    if (mb_try(mb, parity)) return;
+// Bounded wait for the phase `parity` of mb: true once the phase has completed,
+// false after `limit` polls (about a second at the default limit).
+__device__ __forceinline__ bool mb_wait_for(uint64_t* mb, unsigned parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    if (mb_try(mb, parity)) return true;
     __nanosleep(64);
   }
-  atomicExch(err, 1);
+  return false;
 }
 // Barrier among the first n threads of the CTA (n a multiple of 32); id 0 is __syncthreads.
 __device__ __forceinline__ void bar_sub(int id, int n) {
@@ -173,6 +171,9 @@ struct OcArgs {
       a_jb, a_gs, a_sq;
   int rowA, Kp, sumdA;   // row, K and sumd rounded up to even counts
   long long accd;        // doubles per CTA accumulator block (global layout)
+  // adjoint: polls of a bounded mbarrier wait, and a test knob (non-zero: CTA 0
+  // skips the bulk copy of its first stage input, so that wait runs out)
+  int wlim, skip_first;
 };
 
 template <int DL>
@@ -479,22 +480,35 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   const unsigned img_bytes = (unsigned)(oa.CSP * sizeof(C));
   double* gFc = gF_cta + (size_t)cta * nstK;
   // prefetch of stage s of step n: its input into ydst, its rows into buffer b
-  auto issue = [&](int n, int s, C* ydst, int b) {
-    if (threadIdx.x == 0)
+  auto issue = [&](int n, int s, C* ydst, int b, bool skip) {
+    if (threadIdx.x == 0 && !skip)
       bulk_load(ydst, segY + ((size_t)(4 * (n - n0) + s) * oa.ncta + cta) * oa.CSP, img_bytes, &mbar);
     const int q = 3 * n + stage_row(s);
     issue_rows<C>(tab, oa.row, q, b ? M1 : M0, threadIdx.x, blockDim.x);
     issue_rows<R>(coef, oa.K, q, b ? cf1 : cf0, threadIdx.x, blockDim.x);
     issue_rows<C>(ph, oa.sumd, q, b ? ph1 : ph0, threadIdx.x, blockDim.x);
   };
-  unsigned parity = 0;
+  // A wait that runs out sets *err and stops the CTA's bulk copies (the CTA computes
+  // on to its end with what it has, every access in bounds); before it exits it
+  // waits, again bounded, for the copy it gave up on.  The CTA agrees on each
+  // outcome by a barrier vote, so `aborted` is uniform.
+  unsigned parity = 0, lost_parity = 0;
+  bool aborted = false;
+  auto vote = [&](bool ok, unsigned par) {
+    if (!__syncthreads_and(ok ? 1 : 0) && !aborted) {
+      aborted = true;
+      lost_parity = par;
+      if (threadIdx.x == 0) atomicExch(err, 1);
+    }
+  };
+  bool ok0 = true;
   if (n0 < n1) {
-    issue(n1 - 1, 3, ys, 0);
+    issue(n1 - 1, 3, ys, 0, oa.skip_first != 0 && cta == 0);
     cp_wait_all();
-    mb_wait(&mbar, parity, err);
+    ok0 = mb_wait_for(&mbar, parity, oa.wlim);
     parity ^= 1;
   }
-  __syncthreads();
+  vote(ok0, parity ^ 1);
   int buf = 0;
   constexpr int NA = xd_n<DL, PARX>();
   for (int step = n1 - 1; step >= n0; --step) {
@@ -505,7 +519,7 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
       const int pn = s > 0 ? step : step - 1, psn = s > 0 ? s - 1 : 3;
       const bool more = pn >= n0;
       const C* Mc = buf ? M1 : M0;
-      if (more) issue(pn, psn, yn, buf ^ 1);
+      if (more) issue(pn, psn, yn, buf ^ 1, aborted);
       if (warp < oa.npw) {
         // phase warps: ks = H kbar_s, then the adjoint epilogue
         oc_apply<DL>(sp, oa, Mc, xs, ks, nphase, 1);
@@ -567,17 +581,19 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
           oc_contract<DL, R>(xa, opd, sp.x_gslot[slot], w, lane, Mc, cfs, phs, tq, q, s, A, sq, gFc);
         }
       }
+      bool ok = true;
       if (more) {
         cp_wait_all();
-        mb_wait(&mbar, parity, err);
+        if (!aborted) ok = mb_wait_for(&mbar, parity, oa.wlim);
         parity ^= 1;
       }
-      __syncthreads();
+      vote(ok, parity ^ 1);
       C* tswap = xs; xs = ks; ks = tswap;
       tswap = ys; ys = yn; yn = tswap;
       buf ^= 1;
     }
   }
+  if (aborted) mb_wait_for(&mbar, lost_parity, oa.wlim);   // the copy given up on, if it is still in flight
   for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) pbar_img[(size_t)cta * oa.ent + e] = pb.get(e);
   // add the segment's accumulators to the CTA's global block (GradAcc layout, SG_MAXD strides)
   double* G = acc_cta + (size_t)cta * oa.accd;
@@ -1156,7 +1172,13 @@ int adj_t(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double
   auto kern = oc->h->allpar ? k_oc_adj<R, DL, true> : k_oc_adj<R, DL, false>;
   smem_limit_once<k_oc_adj<R, DL, true>>();
   smem_limit_once<k_oc_adj<R, DL, false>>();
-  kern<<<oc->oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oc->oa, (const C*)tb.tab, (const R*)tb.coef,
+  OcArgs oa = oc->oa;
+  // bounded-wait limit and the test knob that makes one wait run out (tests only)
+  oa.wlim = 1 << 22;
+  if (const char* e = std::getenv("SG_TEST_WAIT_LIMIT")) oa.wlim = std::max(1, atoi(e));
+  const char* sk = std::getenv("SG_TEST_SKIP_BULK");
+  oa.skip_first = sk && sk[0] == '1';
+  kern<<<oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oa, (const C*)tb.tab, (const R*)tb.coef,
                                              (const C*)tb.ph, (const C*)tb.opd, (const C*)segY, pbar_img, n0, n1,
                                              dt, xa, gF_cta, acc_cta, (long long)nst * std::max(1, oc->oa.K), err,
                                              (float2*)pblo);
