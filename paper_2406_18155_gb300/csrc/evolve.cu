@@ -53,6 +53,7 @@ struct TabArgs {
   int opd_off[SG_MAXQ];
   int e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
   double J[SG_MAXEDGE];
+  int e_zpart[SG_MAXEDGE];    // real-operator rows: coupling factors both real (0) or both imaginary (1)
   int drv_of_slot_start[SG_MAXQ + 1];
   int drv_list[SG_MAXDRIVE];
   double dt;
@@ -216,6 +217,67 @@ __global__ void k_tables32(TabArgs a, float* __restrict__ coef32, float2* __rest
         const double2 O = a.opd[a.opd_off[i] + op * d * d + ab];
         const float ox = (float)O.x, oy = (float)O.y;
         row[off + ab] = make_float2(sc * (ox * P.x - oy * P.y), sc * (ox * P.y + oy * P.x));
+      }
+    }
+  }
+}
+
+// Stage rows of the real-operator tiled passes (slab_dev.cuh): per 1-body slot
+// sum_k f_k(t) O_k (+ diag E in the lab frame) and per coupling J A (x) B, each as
+// its real matrix in the truncated eigenbasis (the interaction-frame phases are
+// applied to the state instead).  A coupling whose two factors are imaginary
+// stores -J Im(A) and Im(B).  Rows are packed for the passes: FP32 duplicates each
+// element into both lanes of a float2; with zpar every operator is parity-odd and
+// row x keeps its columns c with x + c odd in its first d / 2 places.
+template <typename Z> __device__ __forceinline__ Z zpack(double v);
+template <> __device__ __forceinline__ float2 zpack<float2>(double v) { return make_float2((float)v, (float)v); }
+template <> __device__ __forceinline__ double zpack<double>(double v) { return v; }
+
+template <typename Z>
+__global__ void k_tables_z(TabArgs a, Z* __restrict__ zt, int zpar) {
+  const int q = blockIdx.x;
+  const int n = q / 3, j = q % 3;
+  const double t = (double)(2 * n + j) * a.dt * 0.5;
+  __shared__ double f[SG_MAXDRIVE];
+  for (int k = threadIdx.x; k < a.K; k += blockDim.x) {
+    const DriveDev dr = a.drives[k];
+    f[k] = envelope_dev(dr, a.amps, n, j, t) * cos(dr.omega * t + dr.phase);
+  }
+  __syncthreads();
+  Z* row = zt + (size_t)q * a.p.row;
+  for (int u = 0; u < a.p.n1; ++u) {
+    const int i = a.p.s1_mode[u], d = a.dims[i];
+    for (int el = threadIdx.x; el < d * d; el += blockDim.x) {
+      const int x = el / d, kk = el % d;
+      double v = 0.0;
+      if (!zpar || kk < d / 2) {
+        const int c = zpar ? ((x + 1) & 1) + 2 * kk : kk;
+        for (int xx = a.drv_of_slot_start[u]; xx < a.drv_of_slot_start[u + 1]; ++xx) {
+          const int k = a.drv_list[xx];
+          v += f[k] * a.opd[a.opd_off[i] + a.drives[k].op * d * d + x * d + c].x;
+        }
+        if (a.frame == SG_FRAME_LAB && x == c) v += a.E[a.eoff[i] + x];
+      }
+      row[a.p.s1_off[u] + el] = zpack<Z>(v);
+    }
+  }
+  for (int e = 0; e < a.p.ne; ++e) {
+    const bool im = a.e_zpart[e] != 0;
+    for (int side = 0; side < 2; ++side) {
+      const int i = side == 0 ? a.p.e_a[e] : a.p.e_b[e];
+      const int op = side == 0 ? a.e_opa[e] : a.e_opb[e];
+      const int d = a.dims[i];
+      const int off = side == 0 ? a.p.e_offL[e] : a.p.e_offR[e];
+      const double sc = side == 0 ? (im ? -a.J[e] : a.J[e]) : 1.0;
+      for (int el = threadIdx.x; el < d * d; el += blockDim.x) {
+        const int x = el / d, kk = el % d;
+        double v = 0.0;
+        if (!zpar || kk < d / 2) {
+          const int c = zpar ? ((x + 1) & 1) + 2 * kk : kk;
+          const double2 O = a.opd[a.opd_off[i] + op * d * d + x * d + c];
+          v = sc * (im ? O.y : O.x);
+        }
+        row[off + el] = zpack<Z>(v);
       }
     }
   }
@@ -1511,6 +1573,38 @@ int path_choice() {
   return v == "gather" ? 2 : (v == "slab" ? 1 : 0);
 }
 
+// Which part of a stored operator is its real matrix: 0 real, 1 imaginary, -1 a
+// genuinely complex operator (the truncated eigenvectors are real, so n and phi are
+// one or the other; a user's local operator may be neither).
+int op_part(const sg_system* sys, int mode, int op) {
+  const std::vector<double>& od = sys->opd_host[mode];
+  const int d = sys->modes[mode].d;
+  double mr = 0.0, mi = 0.0;
+  for (int ab = 0; ab < d * d; ++ab) {
+    const size_t k = 2 * ((size_t)op * d * d + ab);
+    if (k + 1 >= od.size()) return -1;
+    mr = std::max(mr, std::fabs(od[k]));
+    mi = std::max(mi, std::fabs(od[k + 1]));
+  }
+  if (mi <= 1e-12 * mr) return 0;
+  if (mr <= 1e-12 * mi) return 1;
+  return -1;
+}
+
+// Every term real in the eigenbasis up to the frame phases: 1-body slots of real
+// operators, couplings of two real or two imaginary factors (ta.e_zpart set).
+bool real_terms(const sg_system* sys, const Setup& s, TabArgs& ta) {
+  for (const HostDrive& hd : sys->drives)
+    if (op_part(sys, hd.mode, hd.op) != 0) return false;
+  for (int e = 0; e < s.p.ne; ++e) {
+    const HostCoupling& c = sys->couplings[e];
+    const int pa = op_part(sys, c.a, c.op_a), pb = op_part(sys, c.b, c.op_b);
+    if (pa < 0 || pa != pb) return false;
+    ta.e_zpart[e] = pa;
+  }
+  return true;
+}
+
 sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, bool grad) {
   sg_ctx* ctx = sys->ctx;
   Setup& s = sv.s;
@@ -1606,6 +1700,21 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   }
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
+  // real-operator forward passes on the tiled kernels (opt-in: SG_SLAB_REAL=1)
+  if (sv.slab && !s.q2 && slab_real_shape_ok(sv.slab) && real_terms(sys, s, ta)) {
+    const char* e = std::getenv("SG_SLAB_REAL");
+    if (e && e[0] == '1') {
+      const int zpar = slab_allpar(sv.slab) ? 1 : 0;
+      void* zt = sv.ar.get<double>(nst * (size_t)s.p.row);      // 8-byte elements in both precisions
+      if (!zt) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the stage tables failed");
+      if (sv.mixed) k_tables_z<float2><<<(unsigned)nst, 64, 0, st>>>(ta, (float2*)zt, zpar);
+      else k_tables_z<double><<<(unsigned)nst, 64, 0, st>>>(ta, (double*)zt, zpar);
+      ++sv.launches;
+      SG_CUDA_TRY(ctx, cudaGetLastError());
+      slab_bind_real(sv.slab, zt, sv.ph, s.sumd);
+      s.ta = ta;
+    }
+  }
   {
     const char* e = std::getenv("SG_KTIMING");
     sv.kt.on = e && e[0] == '1';
@@ -1805,7 +1914,7 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));     // reads only from an idle stream (see dcopy)
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
-  if (herr) return sg_fail(ctx, SG_E_CUDA, "on-chip adjoint: a bulk copy of a stage input did not complete");
+  if (herr) return sg_fail(ctx, SG_E_TIMEOUT, "on-chip adjoint: a bounded wait for a stage input's bulk copy ran out");
   return SG_OK;
 }
 

@@ -19,6 +19,10 @@
 
 namespace {
 
+// Dynamic shared memory a tiled pass may take: the 227 KB opt-in limit of a block
+// less 1 KB for the kernels' static shared variables.
+constexpr size_t kSlabSmemMax = 226 * 1024;
+
 // KIND: 0 first partial pass (kA = k), 1 middle partial (kA += k), 2 last pass after
 // partials (k += kA then the RK4 epilogue), 3 single pass (epilogue).
 template <typename R, int DL>
@@ -56,6 +60,98 @@ __global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 3 : 1) k_slab_fwd(SlabPa
         ok[j] = t < sp.T;
         g[j] = ok[j] ? base + __ldg(off + t) : base;
         const C a = ok[j] ? ks[spos<DL>(t)] : cmk<C>(0.0, 0.0);
+        k[j] = cmk<C>(a.y, -a.x);                   // -i H y
+        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? kA[g[j]] : cmk<C>(0.0, 0.0);
+        ps[j] = (KIND >= 2) && ok[j] ? psi_in[g[j]] : make_double2(0.0, 0.0);
+        dd[j] = (KIND >= 2) && ok[j] && !STORE && STAGE > 0 ? Dacc[g[j]] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        if (!ok[j]) continue;
+        C kk = k[j];
+        if (KIND == 0) { kA[g[j]] = kk; continue; }
+        if (KIND == 1) { kA[g[j]] = cmk<C>(pa[j].x + kk.x, pa[j].y + kk.y); continue; }
+        if (KIND == 2) kk = cmk<C>(pa[j].x + kk.x, pa[j].y + kk.y);
+        const C pr = to_c(ps[j], R(0));
+        const C d = dd[j];
+        if (STAGE == 0) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(h / 6 * kk.x, h / 6 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+        } else if (STAGE == 1) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(d.x + h / 3 * kk.x, d.y + h / 3 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+        } else if (STAGE == 2) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(d.x + h / 3 * kk.x, d.y + h / 3 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h * kk.x, pr.y + h * kk.y);
+        } else {
+          R incx = d.x + h / 6 * kk.x, incy = d.y + h / 6 * kk.y;
+          double2 pn = make_double2(ps[j].x + (double)incx, ps[j].y + (double)incy);
+          psi_out[g[j]] = pn;
+          Xn[g[j]] = to_c(pn, R(0));
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Forward stage pass with real operators (slab_dev.cuh): the tile is loaded and
+// rotated by the conjugate group phases, the phases apply real matrices, and the
+// epilogue rotates back before the RK4 update of k_slab_fwd (same KIND / STAGE /
+// STORE semantics).  Tile entry t = tid + 256 j has the phase lo[tid] hi[j].
+template <typename R, int DL, bool PAR>
+__global__ void __launch_bounds__(kST, 2)
+k_zslab_fwd(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename ZM<R>::T* __restrict__ zrow,
+            const double2* __restrict__ phrow, const double2* __restrict__ psi_in, double2* psi_out,
+            typename CT<R>::T* __restrict__ Xn, typename CT<R>::T* __restrict__ Dacc,
+            typename CT<R>::T* __restrict__ kA, double dt, const int STAGE, const bool STORE, const int KIND) {
+  typedef typename CT<R>::T C;
+  typedef typename ZM<R>::T Z;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* ys = reinterpret_cast<C*>(smraw);
+  C* ks = ys + spad(sp.T);
+  C* plo = ks + spad(sp.T);                       // 256
+  C* phi = plo + 256;                             // T / 256
+  Z* M = reinterpret_cast<Z*>(smraw + zrow_smem_off(sp.T, sizeof(C)));
+  const int* __restrict__ off = sp.off;
+  for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = zrow[i];
+  zphase_tables<DL>(sp, phrow, plo, phi);
+  __syncthreads();
+  const int L = sp.T < 256 ? sp.T : 256;
+  const C pl = threadIdx.x < L ? plo[threadIdx.x] : cmk<C>(1.0, 0.0);
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const R h = (R)dt;
+  constexpr int NB = 8;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long base = tile_base(sp, tile);
+    // load, rotated into the real-operator basis: y_r = conj(P) y
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * NB) {
+      C v[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + j * kST;
+        v[j] = t < sp.T ? X[base + __ldg(off + t)] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + j * kST;
+        if (t < sp.T) ys[spos<DL>(t)] = zcmulc(zcmul(pl, phi[t / 256]), v[j]);
+      }
+    }
+    __syncthreads();
+    zpass_apply<DL, PAR, R>(sp, M, ys, ks, kST);
+    constexpr int EB = 4;
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * EB) {
+      long long g[EB];
+      C k[EB], pa[EB], dd[EB];
+      double2 ps[EB];
+      bool ok[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int t = t0 + j * kST;
+        ok[j] = t < sp.T;
+        g[j] = ok[j] ? base + __ldg(off + t) : base;
+        const C a = ok[j] ? zcmul(zcmul(pl, phi[t / 256]), ks[spos<DL>(t)]) : cmk<C>(0.0, 0.0);
         k[j] = cmk<C>(a.y, -a.x);                   // -i H y
         pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? kA[g[j]] : cmk<C>(0.0, 0.0);
         ps[j] = (KIND >= 2) && ok[j] ? psi_in[g[j]] : make_double2(0.0, 0.0);
@@ -360,6 +456,11 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
         local[tm[k]] = k;
       }
     }
+    {
+      int eoff[SG_MAXQ], e = 0;                // offsets of each mode's levels in a phase row
+      for (int i = 0; i < nq; ++i) { eoff[i] = e; e += p.dims[i]; }
+      for (int k = 0; k < sp.ng; ++k) sp.tphoff[k] = eoff[tm[k]];
+    }
     sp.no = 0;
     for (int m : order)
       if (!groups[g].count(m)) { sp.odim[sp.no] = p.dims[m]; sp.ost[sp.no] = st_int[m]; ++sp.no; }
@@ -478,14 +579,16 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
     cudaMemcpyAsync(h->off_dev[g], off.data(), sp.T * sizeof(int), cudaMemcpyHostToDevice, st);
     sp.off = h->off_dev[g];
     h->sm_fwd[g] = 2 * spad(sp.T) * csz + p.row * csz;
+    h->sm_zfwd[g] = zrow_smem_off(sp.T, csz) + (size_t)p.row * 8;
     h->sm_adj[g] = std::max(3 * spad(sp.T) * csz + p.row * csz, (size_t)kMaxX * DL * DL * sizeof(double2));
-    if (h->sm_adj[g] > 200 * 1024 && !metadata_only) { slab_plan_destroy(h); return nullptr; }
+    if (h->sm_adj[g] > kSlabSmemMax && !metadata_only) { slab_plan_destroy(h); return nullptr; }
   }
   h->allpar = true;
   for (int g = 0; g < np; ++g)
     for (int q = 0; q < h->pass[g].nph; ++q) h->allpar = h->allpar && h->pass[g].ph[q].allpar;
   long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   h->grid_fwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 3 : 1));
+  h->grid_zfwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
   h->grid_adj = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
   cudaStreamSynchronize(st);
   return h;
@@ -498,6 +601,14 @@ void slab_plan_destroy(SlabPlanHost* h) {
 }
 
 int slab_passes(const SlabPlanHost* h) { return h->np; }
+
+bool slab_real_shape_ok(const SlabPlanHost* h) { return h->DL == 2 || h->DL == 4; }
+bool slab_allpar(const SlabPlanHost* h) { return h->allpar; }
+void slab_bind_real(SlabPlanHost* h, const void* ztab, const double2* ph, int sumd) {
+  h->ztab = ztab;
+  h->zph = ph;
+  h->zsumd = sumd;
+}
 
 size_t slab_partial_elems(const SlabPlanHost* h) {
   return (size_t)std::max(h->grid_adj, 1) * kMaxX * h->DL * h->DL;
@@ -520,28 +631,48 @@ namespace {
 template <typename R, int DL>
 void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, const double2* pin,
                 double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st, int stage,
-                bool store, int kind) {
+                bool store, int kind, int q) {
   typedef typename CT<R>::T C;
+  if constexpr (DL == 2 || DL == 4) {
+    if (h->ztab) {
+      typedef typename ZM<R>::T Z;
+      auto zk = h->allpar ? k_zslab_fwd<R, DL, true> : k_zslab_fwd<R, DL, false>;
+      static const bool zattr = [] {
+        cudaFuncSetAttribute(k_zslab_fwd<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+        cudaFuncSetAttribute(k_zslab_fwd<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+        return true;
+      }();
+      (void)zattr;
+      zk<<<h->grid_zfwd, kST, h->sm_zfwd[g], st>>>(h->pass[g], (const C*)X,
+                                                   (const Z*)h->ztab + (size_t)q * h->pass[g].row,
+                                                   h->zph + (size_t)q * h->zsumd, pin, pout, (C*)Xn, (C*)Dacc,
+                                                   (C*)kA, dt, stage, store, kind);
+      return;
+    }
+  }
   auto kern = k_slab_fwd<R, DL>;
   // once per kernel, thread-safe (solves on several host threads launch the same kernels)
-  static const bool attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+  static const bool attr = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax) ==
                            cudaSuccess;
   (void)attr;
   kern<<<h->grid_fwd, kST, h->sm_fwd[g], st>>>(h->pass[g], (const C*)X, (const C*)row, pin, pout,
                                                  (C*)Xn, (C*)Dacc, (C*)kA, dt, stage, store, kind);
 }
 
-// One RK4 stage: the partial passes accumulate into kA, the last one applies the epilogue.
+// One RK4 stage: the partial passes accumulate into kA, the last one applies the
+// epilogue.  q: the stage slot 3 n + j of the stage's time.
 template <typename R, int DL>
 void fwd_stage(const SlabPlanHost* h, int stage, bool store, const void* X, const void* row,
-               const double2* pin, double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st) {
+               const double2* pin, double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st,
+               int q) {
   if (h->np == 1) {
-    fwd_launch<R, DL>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 3);
+    fwd_launch<R, DL>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 3, q);
     return;
   }
-  fwd_launch<R, DL>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 0);
-  for (int g = 1; g < h->np - 1; ++g) fwd_launch<R, DL>(h, g, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 1);
-  fwd_launch<R, DL>(h, h->np - 1, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 2);
+  fwd_launch<R, DL>(h, 0, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 0, q);
+  for (int g = 1; g < h->np - 1; ++g)
+    fwd_launch<R, DL>(h, g, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 1, q);
+  fwd_launch<R, DL>(h, h->np - 1, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 2, q);
 }
 
 template <typename R, int DL>
@@ -551,8 +682,8 @@ void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, cons
   typedef typename CT<R>::T C;
   auto kern = h->allpar ? k_slab_adj<R, DL, true> : k_slab_adj<R, DL, false>;
   static const bool attr = [] {
-    cudaFuncSetAttribute(k_slab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    cudaFuncSetAttribute(k_slab_adj<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaFuncSetAttribute(k_slab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+    cudaFuncSetAttribute(k_slab_adj<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
     return true;
   }();
   (void)attr;
@@ -582,10 +713,11 @@ template <typename R, int DL>
 int fwd_step_t(const SlabPlanHost* h, const void* tab, int step, const double2* pin, double2* pout,
                void*& X, void*& Xo, void* Dacc, void* kA, double dt, cudaStream_t st) {
   const int row = h->pass[0].row;
-  fwd_stage<R, DL>(h, 0, false, X, row_of<R>(tab, row, step, 0), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
-  fwd_stage<R, DL>(h, 1, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
-  fwd_stage<R, DL>(h, 2, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
-  fwd_stage<R, DL>(h, 3, false, X, row_of<R>(tab, row, step, 2), pin, pout, Xo, Dacc, kA, dt, st); std::swap(X, Xo);
+  const int q = 3 * step;
+  fwd_stage<R, DL>(h, 0, false, X, row_of<R>(tab, row, step, 0), pin, nullptr, Xo, Dacc, kA, dt, st, q); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 1, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st, q + 1); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 2, false, X, row_of<R>(tab, row, step, 1), pin, nullptr, Xo, Dacc, kA, dt, st, q + 1); std::swap(X, Xo);
+  fwd_stage<R, DL>(h, 3, false, X, row_of<R>(tab, row, step, 2), pin, pout, Xo, Dacc, kA, dt, st, q + 2); std::swap(X, Xo);
   return 4 * h->np;
 }
 
@@ -595,10 +727,11 @@ template <typename R, int DL>
 int fwd_step_keep_t(const SlabPlanHost* h, const void* tab, int step, const double2* pin, double2* pout,
                     void* const Yk[4], void* Ynext0, void* Dacc, void* kA, double dt, cudaStream_t st) {
   const int row = h->pass[0].row;
-  fwd_stage<R, DL>(h, 0, false, Yk[0], row_of<R>(tab, row, step, 0), pin, nullptr, Yk[1], Dacc, kA, dt, st);
-  fwd_stage<R, DL>(h, 1, false, Yk[1], row_of<R>(tab, row, step, 1), pin, nullptr, Yk[2], Dacc, kA, dt, st);
-  fwd_stage<R, DL>(h, 2, false, Yk[2], row_of<R>(tab, row, step, 1), pin, nullptr, Yk[3], Dacc, kA, dt, st);
-  fwd_stage<R, DL>(h, 3, false, Yk[3], row_of<R>(tab, row, step, 2), pin, pout, Ynext0, Dacc, kA, dt, st);
+  const int q = 3 * step;
+  fwd_stage<R, DL>(h, 0, false, Yk[0], row_of<R>(tab, row, step, 0), pin, nullptr, Yk[1], Dacc, kA, dt, st, q);
+  fwd_stage<R, DL>(h, 1, false, Yk[1], row_of<R>(tab, row, step, 1), pin, nullptr, Yk[2], Dacc, kA, dt, st, q + 1);
+  fwd_stage<R, DL>(h, 2, false, Yk[2], row_of<R>(tab, row, step, 1), pin, nullptr, Yk[3], Dacc, kA, dt, st, q + 1);
+  fwd_stage<R, DL>(h, 3, false, Yk[3], row_of<R>(tab, row, step, 2), pin, pout, Ynext0, Dacc, kA, dt, st, q + 2);
   return 4 * h->np;
 }
 
@@ -606,9 +739,10 @@ template <typename R, int DL>
 int fwd_store_t(const SlabPlanHost* h, const void* tab, int step, const double2* psi, void* const Y[4],
                 void* kA, double dt, cudaStream_t st) {
   const int row = h->pass[0].row;
-  fwd_stage<R, DL>(h, 0, true, Y[0], row_of<R>(tab, row, step, 0), psi, nullptr, Y[1], nullptr, kA, dt, st);
-  fwd_stage<R, DL>(h, 1, true, Y[1], row_of<R>(tab, row, step, 1), psi, nullptr, Y[2], nullptr, kA, dt, st);
-  fwd_stage<R, DL>(h, 2, true, Y[2], row_of<R>(tab, row, step, 1), psi, nullptr, Y[3], nullptr, kA, dt, st);
+  const int q = 3 * step;
+  fwd_stage<R, DL>(h, 0, true, Y[0], row_of<R>(tab, row, step, 0), psi, nullptr, Y[1], nullptr, kA, dt, st, q);
+  fwd_stage<R, DL>(h, 1, true, Y[1], row_of<R>(tab, row, step, 1), psi, nullptr, Y[2], nullptr, kA, dt, st, q + 1);
+  fwd_stage<R, DL>(h, 2, true, Y[2], row_of<R>(tab, row, step, 1), psi, nullptr, Y[3], nullptr, kA, dt, st, q + 1);
   return 3 * h->np;
 }
 

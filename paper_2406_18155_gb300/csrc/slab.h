@@ -46,3 +46,15 @@ int slab_adj_step(const SlabPlanHost* sp, bool mixed, const void* tab, int step,
                   cudaStream_t st);
 // Size of the per-block partial buffer (double2 elements) slab_adj_step needs.
 size_t slab_partial_elems(const SlabPlanHost* sp);
+
+// Real-operator form of the forward stage passes (slab_dev.cuh): usable when every
+// term is real in the truncated eigenbasis up to the interaction-frame phases and
+// the level count is 2 or 4 (slab_real_shape_ok).  ztab: stage rows of real
+// elements (float2 {m, m} pairs in mixed precision, double in FP64) at the complex
+// row's offsets, parity-odd rows compressed when slab_allpar; ph: the stage phase
+// rows exp(i E t), FP64, sumd per stage slot (3 per step).  Once bound, the
+// forward, replay and recompute passes use it; the adjoint passes keep the complex
+// rows.
+bool slab_real_shape_ok(const SlabPlanHost* sp);
+bool slab_allpar(const SlabPlanHost* sp);
+void slab_bind_real(SlabPlanHost* sp, const void* ztab, const double2* ph, int sumd);

@@ -50,6 +50,7 @@ struct SlabPass {
   int nph;                        // register-blocked phases
   Phase ph[kMaxPhase];
   const int* off;                 // device tile offsets [T]
+  int tphoff[SG_MAXQ];            // tile digit k: offset of its mode's levels in a stage's phase row
 };
 
 // Padded shared-memory position of tile entry t: one pad element per 16 and per
@@ -405,6 +406,176 @@ inline Phase make_phase(const SlabPass& sp, int DL, int ka, int kb) {
   return P;
 }
 
+// ---------------------------------------------------------------------------
+// Real-operator phases.  In the interaction frame a local operator is
+// X(t) = P(t) X_r P(t)^dag with P = diag(exp(i E t)) on its mode; in the truncated
+// eigenbasis X_r is real, or i times a real matrix, and the two factors of a
+// coupling then multiply to a real term.  The terms of one pass act only on the
+// pass's mode group G, so their sum is P_G(t) H_r(t) P_G(t)^dag with P_G the product
+// of the group's phases (the other modes' phases cancel), and a pass computes
+//     H y = P_G (H_r (P_G^dag y))
+// with one phase rotation per tile entry on the way in and one on the way out, and
+// real matrix elements times complex amplitudes in between: half the multiply-adds
+// of the complex form, and in FP32 one packed two-lane FMA per element (the real
+// element duplicated in both lanes, the amplitude's real and imaginary parts in the
+// two lanes).
+//
+// Table layout (one stage row, the complex row's offsets): a d x d block per term,
+// row x holding the stored elements of row x; a parity-odd operator stores only its
+// columns c with x + c odd, in increasing order, in the first d/2 places of the row.
+// ---------------------------------------------------------------------------
+template <typename R> struct ZM;
+template <> struct ZM<float> { typedef float2 T; };     // {m, m}
+template <> struct ZM<double> { typedef double T; };
+
+__device__ __forceinline__ float2 zfma(float2 m, float2 y, float2 o) { return __ffma2_rn(m, y, o); }
+__device__ __forceinline__ double2 zfma(double m, double2 y, double2 o) {
+  return make_double2(fma(m, y.x, o.x), fma(m, y.y, o.y));
+}
+template <bool PAR> __host__ __device__ constexpr int zcol(int x, int k) { return PAR ? ((x + 1) & 1) + 2 * k : k; }
+template <int DL, bool PAR> __host__ __device__ constexpr int znz() { return PAR ? DL / 2 : DL; }
+
+// The stored elements of one row (NZ consecutive elements, 16-byte aligned when
+// the row offset is a multiple of the row length; FP32 loads them as float4 pairs).
+template <int NZ>
+__device__ __forceinline__ void zrow_ld(const float2* __restrict__ p, float2 (&r)[NZ]) {
+  if constexpr (NZ % 2 == 0) {
+#pragma unroll
+    for (int k = 0; k < NZ; k += 2) {
+      const float4 v = *reinterpret_cast<const float4*>(p + k);
+      r[k] = make_float2(v.x, v.y);
+      r[k + 1] = make_float2(v.z, v.w);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) r[k] = p[k];
+  }
+}
+template <int NZ>
+__device__ __forceinline__ void zrow_ld(const double* __restrict__ p, double (&r)[NZ]) {
+#pragma unroll
+  for (int k = 0; k < NZ; ++k) r[k] = p[k];
+}
+
+// One block of one phase with real matrices (the operation of phase_block):
+//   out[x][z] (+)= sum_a L[x][a] sum_c R[z][c] y[a][c] + sum_a A[x][a] y[a][z] + sum_c B[z][c] y[x][c]
+// FL: bit 0 edge L (x) R, bit 1 A on ka, bit 2 B on kb, bit 3 first phase (no running sum).
+template <int DL, bool PAR, int FL, typename R>
+__device__ __forceinline__ void zphase_block(const Phase& P, const typename ZM<R>::T* __restrict__ M,
+                                             const typename CT<R>::T* __restrict__ ys,
+                                             typename CT<R>::T* __restrict__ ks, int pb) {
+  typedef typename CT<R>::T C;
+  typedef typename ZM<R>::T Z;
+  constexpr bool HE = FL & 1, HA = (FL >> 1) & 1, HB = (FL >> 2) & 1, FIRST = (FL >> 3) & 1;
+  constexpr int NZ = znz<DL, PAR>();
+  const int psa = P.psa, psb = P.psb;
+  C y[DL][DL];
+#pragma unroll
+  for (int x = 0; x < DL; ++x)
+#pragma unroll
+    for (int z = 0; z < DL; ++z) y[x][z] = ys[pb + x * psa + z * psb];
+  Z l[DL][NZ];
+  if constexpr (HE) {
+#pragma unroll
+    for (int x = 0; x < DL; ++x) zrow_ld<NZ>(M + P.offL + x * DL, l[x]);
+  }
+#pragma unroll
+  for (int z = 0; z < DL; ++z) {
+    C o[DL];
+#pragma unroll
+    for (int x = 0; x < DL; ++x) o[x] = FIRST ? cmk<C>(0.0, 0.0) : ks[pb + x * psa + z * psb];
+    if constexpr (HE) {
+      Z r[NZ];
+      zrow_ld<NZ>(M + P.offR + z * DL, r);
+      C u[DL];
+#pragma unroll
+      for (int aa = 0; aa < DL; ++aa) {
+        C t = cmk<C>(0.0, 0.0);
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) t = zfma(r[k], y[aa][zcol<PAR>(z, k)], t);
+        u[aa] = t;
+      }
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) o[x] = zfma(l[x][k], u[zcol<PAR>(x, k)], o[x]);
+    }
+    if constexpr (HA) {
+#pragma unroll
+      for (int x = 0; x < DL; ++x) {
+        Z a[NZ];
+        zrow_ld<NZ>(M + P.offA + x * DL, a);
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) o[x] = zfma(a[k], y[zcol<PAR>(x, k)][z], o[x]);
+      }
+    }
+    if constexpr (HB) {
+      Z b[NZ];
+      zrow_ld<NZ>(M + P.offB + z * DL, b);
+#pragma unroll
+      for (int x = 0; x < DL; ++x)
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) o[x] = zfma(b[k], y[x][zcol<PAR>(z, k)], o[x]);
+    }
+#pragma unroll
+    for (int x = 0; x < DL; ++x) ks[pb + x * psa + z * psb] = o[x];
+  }
+}
+
+template <int DL, bool PAR, int FL, typename R>
+__device__ __forceinline__ void zphase_all(const Phase& P, const typename ZM<R>::T* __restrict__ M,
+                                           const typename CT<R>::T* __restrict__ ys,
+                                           typename CT<R>::T* __restrict__ ks, int nb, int nthr) {
+  for (int b = threadIdx.x; b < nb; b += nthr) zphase_block<DL, PAR, FL, R>(P, M, ys, ks, blk_pos<DL>(P, b));
+}
+
+// ks = H_r ys over every phase of the pass (threads [0, nthr)); ends with a barrier.
+template <int DL, bool PAR, typename R>
+__device__ __forceinline__ void zpass_apply(const SlabPass& sp, const typename ZM<R>::T* __restrict__ M,
+                                            const typename CT<R>::T* __restrict__ ys,
+                                            typename CT<R>::T* __restrict__ ks, int nthr) {
+  const int nb = sp.T / (DL * DL);
+  for (int q = 0; q < sp.nph; ++q) {
+    const Phase& P = sp.ph[q];
+    const int fl = (P.offL >= 0 ? 1 : 0) | (P.offA >= 0 ? 2 : 0) | (P.offB >= 0 ? 4 : 0) | (q == 0 ? 8 : 0);
+    switch (fl) {
+#define SG_ZCASE(F) case F: zphase_all<DL, PAR, F, R>(P, M, ys, ks, nb, nthr); break;
+      SG_ZCASE(1) SG_ZCASE(2) SG_ZCASE(3) SG_ZCASE(4) SG_ZCASE(5) SG_ZCASE(6) SG_ZCASE(7)
+      SG_ZCASE(9) SG_ZCASE(10) SG_ZCASE(11) SG_ZCASE(12) SG_ZCASE(13) SG_ZCASE(14) SG_ZCASE(15)
+#undef SG_ZCASE
+      default: break;
+    }
+    __syncthreads();
+  }
+}
+
+// Phase factors of the tile entries at one stage: entry t = l + L h (L = min(T, 256))
+// has P_G(t) = lo[l] hi[h], each the product of exp(i E t) over the group digits in
+// that part of t.  Computed in FP64 from the stage's phase row, stored in R.
+template <int DL, typename C>
+__device__ __forceinline__ void zphase_tables(const SlabPass& sp, const double2* __restrict__ phrow, C* lo, C* hi) {
+  const int L = sp.T < 256 ? sp.T : 256;
+  for (int i = threadIdx.x; i < L + sp.T / L; i += blockDim.x) {
+    const bool is_lo = i < L;
+    const int v = is_lo ? i : (i - L) * L;       // tile index whose part this is
+    double pr = 1.0, pi = 0.0;
+    for (int k = 0; k < sp.ng; ++k) {
+      if ((sp.tsh[k] < L) != is_lo) continue;
+      const double2 e = phrow[sp.tphoff[k] + (v / sp.tsh[k]) % DL];
+      const double nr = pr * e.x - pi * e.y, ni = pr * e.y + pi * e.x;
+      pr = nr;
+      pi = ni;
+    }
+    if (is_lo) lo[i] = cmk<C>(pr, pi); else hi[i - L] = cmk<C>(pr, pi);
+  }
+}
+template <typename C> __device__ __forceinline__ C zcmul(C a, C b) {
+  return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename C> __device__ __forceinline__ C zcmulc(C a, C b) {     // conj(a) b
+  return cmk<C>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
 struct PermArgs {
   int nq, S;
   long long D;
@@ -424,4 +595,17 @@ struct SlabPlanHost {
   PermArgs perm{};
   int grid_fwd = 0, grid_adj = 0;
   size_t sm_fwd[kMaxPass] = {0}, sm_adj[kMaxPass] = {0};
+  // real-operator forward passes (bound by slab_bind_real)
+  const void* ztab = nullptr;
+  const double2* zph = nullptr;
+  int zsumd = 0;
+  int grid_zfwd = 0;
+  size_t sm_zfwd[kMaxPass] = {0};
 };
+
+// Byte offset of the real-operator row in the shared memory of k_zslab_fwd: after
+// the two tiles and the phase parts (256 low, T / 256 high), 16-byte aligned.
+__host__ __device__ inline size_t zrow_smem_off(int T, size_t csz) {
+  const int nhi = T > 256 ? T / 256 : 1;
+  return ((2 * (size_t)spad(T) + 256 + nhi) * csz + 15) & ~(size_t)15;
+}
