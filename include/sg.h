@@ -248,7 +248,8 @@ sg_status sg_evolve(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
  * device address; make that first call before any stream capture.  All calls
  * share the one array and it keeps the last call's contents: calls that overlap
  * on the GPU (on different streams or contexts) race.  Uses the generic gather
- * kernels.  Returns SG_E_INVALID with the needed size when the evolution needs
+ * kernels.  It synchronises the context stream before it returns (its small
+ * inputs are staged from host buffers that live only for the call).  Returns SG_E_INVALID with the needed size when the evolution needs
  * more than the 32 MiB (stage tables of 3 T/dt rows plus three D x S slabs). */
 sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
 
@@ -320,15 +321,23 @@ typedef struct {
   int active_slots, max_slots;
 } sg_stats;
 
-/* A server owns one worker thread that admits requests into slots while the
- * device memory they need fits `mem_budget_bytes` and a slot is free, groups the
- * admitted requests by step shape and advances each group in shared batched
- * launches.  Requests that arrive while others run join at the next step
- * boundary of the shared launch loop. */
+/* A server owns `max_slots` slots, each a worker thread with its own CUDA stream
+ * (continuous batching): requests are admitted in arrival order while a slot is
+ * free and the device memory they need fits `mem_budget_bytes`; each admitted
+ * request runs as one independent fidelity(+gradient) solve on its slot's stream,
+ * so the kernels of all admitted requests overlap on the device, and a request
+ * that arrives while others run starts as soon as a slot and memory free up.
+ * Results do not depend on what else runs (each solve has its own buffers and
+ * fixed-order reductions).  gpu_busy_frac in sg_stats is the fraction of the
+ * server's wall time with at least one request running, not a device occupancy. */
 sg_status sg_server_create(sg_ctx* ctx, size_t mem_budget_bytes, int max_slots, sg_server** out);
 sg_status sg_server_destroy(sg_server* srv);
 /* Queue a request.  The request's system must stay alive until its result is
- * polled.  Returns SG_E_NOMEM_RETRY if the request alone exceeds the budget. */
+ * polled, and the caller makes no other call on it meanwhile (its slot runs it
+ * with the slot's context and prepares it if needed).  One system has at most one
+ * request queued or running: a second submit of the same system before the first
+ * is done (or cancelled) returns SG_E_STATE.  Returns SG_E_NOMEM_RETRY if the
+ * request alone exceeds the budget. */
 sg_status sg_server_submit(sg_server* srv, const sg_request* req, uint64_t* ticket);
 /* SG_OK and *out filled when done; SG_E_PENDING while queued or running. */
 sg_status sg_server_poll(sg_server* srv, uint64_t ticket, sg_result* out);

@@ -1,10 +1,12 @@
 // Serving: continuous batching of fidelity(+gradient) solves on one GPU.
 //
 // Requests are admitted in arrival order while a slot is free and the device
-// memory they need fits the budget.  Each slot owns a CUDA stream, so the kernels
-// of all admitted requests overlap on the device; a request that arrives while
-// others run starts as soon as a slot and memory free up, without waiting for the
-// running ones to finish.  Results are bitwise independent of what else runs: every
+// memory they need fits the budget.  Each slot owns a worker thread and a CUDA
+// stream and runs one request's solve at a time, so the kernels of all admitted
+// requests overlap on the device; a request that arrives while others run starts
+// as soon as a slot and memory free up, without waiting for the running ones to
+// finish.  A system has at most one request in the server at a time (the slot runs
+// it with its own context and may prepare it).  Results are bitwise independent of what else runs: every
 // solve uses only its own buffers and fixed-order reductions.
 #include <cstdio>
 #include "sg_internal.h"
@@ -69,6 +71,9 @@ struct sg_server {
   std::condition_variable cv, done_cv;
   std::deque<Req*> queue;
   std::map<uint64_t, std::unique_ptr<Req>> reqs;
+  // systems with a request queued or running: a slot swaps the system's context and
+  // may prepare it, so one system has at most one request in the server at a time
+  std::map<const sg_system*, int> inflight;
   uint64_t next_ticket = 1;
   size_t mem_in_use = 0;
   int active = 0;
@@ -123,6 +128,7 @@ struct sg_server {
         --active;
         if (active == 0 && busy_since >= 0) { busy_accum += r->done_s - busy_since; busy_since = -1; }
         ++completed;
+        inflight.erase(r->sys);
         latencies.push_back(r->done_s - r->submit_s);
         last_done = r->done_s;
       }
@@ -205,11 +211,15 @@ sg_status sg_server_submit(sg_server* srv, const sg_request* req, uint64_t* tick
   r->target.assign(req->target_re_im, req->target_re_im + 2 * dc * dc);
   r->mem = estimate_bytes(req->sys, r->opts, req->want_grad);
   std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->inflight.count(req->sys))
+    return sg_fail(srv->ctx, SG_E_STATE, "this system already has a request queued or running in the server; "
+                                         "give each concurrent request its own system");
   ++srv->submitted;
   if (r->mem > srv->budget) {
     ++srv->rejected;
     return sg_fail(srv->ctx, SG_E_NOMEM_RETRY, "request alone exceeds the memory budget");
   }
+  srv->inflight[req->sys] = 1;
   r->ticket = srv->next_ticket++;
   r->submit_s = now_s(srv->t0);
   *ticket = r->ticket;
@@ -267,6 +277,7 @@ sg_status sg_server_cancel(sg_server* srv, uint64_t ticket) {
   Req* r = it->second.get();
   if (r->state != 0) return r->state == 3 ? SG_OK : sg_fail(srv->ctx, SG_E_STATE, "request already started");
   srv->queue.erase(std::remove(srv->queue.begin(), srv->queue.end(), r), srv->queue.end());
+  srv->inflight.erase(r->sys);
   r->state = 3;
   ++srv->cancelled;
   srv->done_cv.notify_all();

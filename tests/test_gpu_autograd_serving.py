@@ -133,3 +133,23 @@ def test_server_admission_and_cancel(sgctx):
         assert srv.wait(x)["status"] == 0
     assert srv.stats()["cancelled"] == 1
     srv.close()
+
+
+def test_server_refuses_a_system_already_in_flight(sgctx):
+    # a slot runs a request with its own context and may prepare the system, so a
+    # system takes one request at a time; after its result it can be submitted again
+    from paper_2406_18155_gb300.api import Server
+    from paper_2406_18155_gb300.capi import SGError, SG_E_STATE
+    wl = W.fluxonium_pair_cr(seed=4, T=2.0)
+    s = _system(sgctx, wl)
+    srv = Server(sgctx, mem_budget_bytes=4 << 30, max_slots=2)
+    t0 = srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"])
+    with pytest.raises(SGError) as e:
+        srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"])
+    assert e.value.code == SG_E_STATE
+    r0 = srv.wait(t0)
+    t1 = srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"])
+    r1 = srv.wait(t1)
+    assert r0["status"] == 0 and r1["status"] == 0
+    assert r0["F"][0] == r1["F"][0] and np.array_equal(r0["grad_pulse"], r1["grad_pulse"])
+    srv.close()

@@ -1,13 +1,16 @@
 """sg_evolve_noalloc: the evolution entry point for callers that cannot allocate
 device memory during the call (their memory belongs to another allocator, or
 they cannot afford cudaMalloc's synchronisation).  It must give the same states
-as sg_evolve, on repeated calls that reuse its fixed scratch array, and refuse
-sizes beyond that array.  Kept in a file of its own that pytest collects last."""
+as sg_evolve and as the FP64 oracle, on repeated calls that reuse its fixed scratch
+array, and refuse sizes beyond that array.  Kept in a file of its own that pytest
+collects last."""
 import ctypes
 
 import numpy as np
 import pytest
 
+from oracle.evolve import frame_epilogue, initial_columns, rk4_evolve
+from oracle.system import OracleSystem
 from paper_2406_18155_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -32,9 +35,12 @@ def test_noalloc_matches_sg_evolve_on_two_calls(sgctx, prec, tol):
     s = System.from_workload(sgctx, wl)
     s.prepare()
     ref = s.evolve(wl["T"], wl["dt"], precision=prec, col_index=wl["col_index"]).cpu().numpy()
+    so = OracleSystem(wl)
+    orc = frame_epilogue(so, rk4_evolve(so, initial_columns(so, wl["col_index"])))
     for _ in range(2):
         out = _noalloc(sgctx, s, wl["T"], wl["dt"], prec, wl["col_index"])
         assert np.max(np.abs(out - ref)) < tol
+        assert np.max(np.abs(out - orc)) < tol
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(sgctx):
