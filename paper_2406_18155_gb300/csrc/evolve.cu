@@ -1700,10 +1700,11 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   }
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
-  // real-operator forward passes on the tiled kernels (opt-in: SG_SLAB_REAL=1)
+  // real-operator forward passes on the tiled kernels (SG_SLAB_REAL=0 keeps the
+  // complex rows, a test knob)
   if (sv.slab && !s.q2 && slab_real_shape_ok(sv.slab) && real_terms(sys, s, ta)) {
     const char* e = std::getenv("SG_SLAB_REAL");
-    if (e && e[0] == '1') {
+    if (!(e && e[0] == '0')) {
       const int zpar = slab_allpar(sv.slab) ? 1 : 0;
       void* zt = sv.ar.get<double>(nst * (size_t)s.p.row);      // 8-byte elements in both precisions
       if (!zt) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the stage tables failed");

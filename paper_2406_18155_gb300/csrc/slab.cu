@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 3 : 1) k_slab_fwd(SlabPa
 // epilogue rotates back before the RK4 update of k_slab_fwd (same KIND / STAGE /
 // STORE semantics).  Tile entry t = tid + 256 j has the phase lo[tid] hi[j].
 template <typename R, int DL, bool PAR>
-__global__ void __launch_bounds__(kST, 2)
+__global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 2 : 1)
 k_zslab_fwd(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename ZM<R>::T* __restrict__ zrow,
             const double2* __restrict__ phrow, const double2* __restrict__ psi_in, double2* psi_out,
             typename CT<R>::T* __restrict__ Xn, typename CT<R>::T* __restrict__ Dacc,
@@ -184,6 +184,129 @@ k_zslab_fwd(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename
       }
     }
     __syncthreads();
+  }
+}
+
+// The same forward pass, warp-specialised for FP32 tiles of >= 256 entries: 8
+// compute warps run the phases of tile i while 8 memory warps write back tile
+// i - 1 (epilogue) and load tile i + 1, two buffer pairs in shared memory.
+// Protocol (named barriers, 512 arrivals each; b = i mod 2):
+//   compute, per tile i:  sync LOADED[b] -> phases (barrier 1 among themselves)
+//                         -> arrive COMPUTED[b]
+//   memory:  load tiles 0, 1 -> arrive LOADED[0], LOADED[1]; per tile i: sync
+//            COMPUTED[b] -> epilogue of tile i -> load tile i + 2 into buffer b ->
+//            arrive LOADED[b]
+// A buffer is reloaded only after its epilogue, and recomputed only after that
+// load, so no barrier id ever has two generations pending.
+constexpr int kWST = 512;
+template <int DL, bool PAR>
+__global__ void __launch_bounds__(kWST, 1)
+k_zslab_fwd_ws(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__ zrow,
+               const double2* __restrict__ phrow, const double2* __restrict__ psi_in, double2* psi_out,
+               float2* __restrict__ Xn, float2* __restrict__ Dacc, float2* __restrict__ kA, double dt,
+               const int STAGE, const bool STORE, const int KIND) {
+  typedef float2 C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int TP = spad(sp.T);
+  C* const tiles = reinterpret_cast<C*>(smraw);
+  C* const plo = tiles + 4 * TP;                  // 256
+  C* const phi = plo + 256;                       // T / 256
+  float2* const M = reinterpret_cast<float2*>(smraw + zrow_smem_off(sp.T, sizeof(C), 4));
+  for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = zrow[i];
+  zphase_tables<DL>(sp, phrow, plo, phi);
+  __syncthreads();
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const int n = blockIdx.x < ntiles ? (int)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  if (threadIdx.x < kST) {
+    // ---- compute warps
+    for (int i = 0; i < n; ++i) {
+      const int b = i & 1;
+      nb_sync(2 + b, kWST);
+      zpass_apply<DL, PAR, float>(sp, M, tiles + b * TP, tiles + (2 + b) * TP, kST, 1);
+      __threadfence_block();
+      nb_arrive(4 + b, kWST);
+    }
+    return;
+  }
+  // ---- memory warps: thread tm owns the tile entries t = tm + 256 j
+  const int tm = threadIdx.x - kST;
+  const C pl = plo[tm];
+  const int* __restrict__ off = sp.off;
+  const float h = (float)dt;
+  auto load = [&](int i, C* ys) {
+    const long long base = tile_base(sp, (long long)blockIdx.x + (long long)i * gridDim.x);
+    constexpr int NB = 8;
+    for (int t0 = tm; t0 < sp.T; t0 += kST * NB) {
+      C v[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + j * kST;
+        v[j] = t < sp.T ? X[base + __ldg(off + t)] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + j * kST;
+        if (t < sp.T) ys[spos<DL>(t)] = zcmulc(zcmul(pl, phi[t / 256]), v[j]);
+      }
+    }
+    __threadfence_block();
+  };
+  auto epilogue = [&](int i, const C* ks) {
+    const long long base = tile_base(sp, (long long)blockIdx.x + (long long)i * gridDim.x);
+    constexpr int EB = 4;
+    for (int t0 = tm; t0 < sp.T; t0 += kST * EB) {
+      long long g[EB];
+      C k[EB], pa[EB], dd[EB];
+      double2 ps[EB];
+      bool ok[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int t = t0 + j * kST;
+        ok[j] = t < sp.T;
+        g[j] = ok[j] ? base + __ldg(off + t) : base;
+        const C a = ok[j] ? zcmul(zcmul(pl, phi[t / 256]), ks[spos<DL>(t)]) : cmk<C>(0.0, 0.0);
+        k[j] = cmk<C>(a.y, -a.x);                   // -i H y
+        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? kA[g[j]] : cmk<C>(0.0, 0.0);
+        ps[j] = (KIND >= 2) && ok[j] ? psi_in[g[j]] : make_double2(0.0, 0.0);
+        dd[j] = (KIND >= 2) && ok[j] && !STORE && STAGE > 0 ? Dacc[g[j]] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        if (!ok[j]) continue;
+        C kk = k[j];
+        if (KIND == 0) { kA[g[j]] = kk; continue; }
+        if (KIND == 1) { kA[g[j]] = cmk<C>(pa[j].x + kk.x, pa[j].y + kk.y); continue; }
+        if (KIND == 2) kk = cmk<C>(pa[j].x + kk.x, pa[j].y + kk.y);
+        const C pr = to_c(ps[j], 0.f);
+        const C d = dd[j];
+        if (STAGE == 0) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(h / 6 * kk.x, h / 6 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+        } else if (STAGE == 1) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(d.x + h / 3 * kk.x, d.y + h / 3 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+        } else if (STAGE == 2) {
+          if (!STORE) Dacc[g[j]] = cmk<C>(d.x + h / 3 * kk.x, d.y + h / 3 * kk.y);
+          Xn[g[j]] = cmk<C>(pr.x + h * kk.x, pr.y + h * kk.y);
+        } else {
+          const float incx = d.x + h / 6 * kk.x, incy = d.y + h / 6 * kk.y;
+          const double2 pn = make_double2(ps[j].x + (double)incx, ps[j].y + (double)incy);
+          psi_out[g[j]] = pn;
+          Xn[g[j]] = to_c(pn, 0.f);
+        }
+      }
+    }
+  };
+  if (n > 0) { load(0, tiles); nb_arrive(2, kWST); }
+  if (n > 1) { load(1, tiles + TP); nb_arrive(3, kWST); }
+  for (int i = 0; i < n; ++i) {
+    const int b = i & 1;
+    nb_sync(4 + b, kWST);
+    epilogue(i, tiles + (2 + b) * TP);
+    if (i + 2 < n) {
+      load(i + 2, tiles + b * TP);
+      nb_arrive(2 + b, kWST);
+    }
   }
 }
 
@@ -580,6 +703,10 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
     sp.off = h->off_dev[g];
     h->sm_fwd[g] = 2 * spad(sp.T) * csz + p.row * csz;
     h->sm_zfwd[g] = zrow_smem_off(sp.T, csz) + (size_t)p.row * 8;
+    {
+      const size_t ws = zrow_smem_off(sp.T, csz, 4) + (size_t)p.row * 8;
+      h->sm_zws[g] = (mixed && sp.T >= 256 && ws <= kSlabSmemMax) ? ws : 0;
+    }
     h->sm_adj[g] = std::max(3 * spad(sp.T) * csz + p.row * csz, (size_t)kMaxX * DL * DL * sizeof(double2));
     if (h->sm_adj[g] > kSlabSmemMax && !metadata_only) { slab_plan_destroy(h); return nullptr; }
   }
@@ -628,6 +755,14 @@ void slab_from_internal(const SlabPlanHost* h, const double2* in, double2* api, 
 // ---------------------------------------------------------------------------
 namespace {
 
+// The warp-specialised real-operator forward pass runs only with SG_SLAB_WS=1: with
+// 8 compute warps per SM its phases wait on dependencies and barriers (measured 25 %
+// slower on the 10-fluxonium ring than the one-role kernel at 16 warps per SM).
+bool zws_off() {
+  const char* e = std::getenv("SG_SLAB_WS");
+  return !(e && e[0] == '1');
+}
+
 template <typename R, int DL>
 void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, const double2* pin,
                 double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st, int stage,
@@ -643,6 +778,24 @@ void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, co
         return true;
       }();
       (void)zattr;
+      if constexpr (sizeof(R) == 4) {
+        if (h->sm_zws[g] && !zws_off()) {
+          auto wk = h->allpar ? k_zslab_fwd_ws<DL, true> : k_zslab_fwd_ws<DL, false>;
+          static const bool wattr = [] {
+            cudaFuncSetAttribute(k_zslab_fwd_ws<DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+            cudaFuncSetAttribute(k_zslab_fwd_ws<DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+            return true;
+          }();
+          (void)wattr;
+          const long long ntiles = (long long)h->pass[g].S * h->pass[g].ntpc;
+          const int grid = (int)std::min<long long>(ntiles, 152);
+          wk<<<grid, kWST, h->sm_zws[g], st>>>(h->pass[g], (const float2*)X,
+                                              (const float2*)h->ztab + (size_t)q * h->pass[g].row,
+                                              h->zph + (size_t)q * h->zsumd, pin, pout, (float2*)Xn,
+                                              (float2*)Dacc, (float2*)kA, dt, stage, store, kind);
+          return;
+        }
+      }
       zk<<<h->grid_zfwd, kST, h->sm_zfwd[g], st>>>(h->pass[g], (const C*)X,
                                                    (const Z*)h->ztab + (size_t)q * h->pass[g].row,
                                                    h->zph + (size_t)q * h->zsumd, pin, pout, (C*)Xn, (C*)Dacc,

@@ -53,8 +53,8 @@ size_t slab_partial_elems(const SlabPlanHost* sp);
 // elements (float2 {m, m} pairs in mixed precision, double in FP64) at the complex
 // row's offsets, parity-odd rows compressed when slab_allpar; ph: the stage phase
 // rows exp(i E t), FP64, sumd per stage slot (3 per step).  Once bound, the
-// forward, replay and recompute passes use it; the adjoint passes keep the complex
-// rows.
+// forward, replay and recompute passes use it (SG_SLAB_REAL=0 at the solve keeps
+// the complex rows); the adjoint passes keep the complex rows.
 bool slab_real_shape_ok(const SlabPlanHost* sp);
 bool slab_allpar(const SlabPlanHost* sp);
 void slab_bind_real(SlabPlanHost* sp, const void* ztab, const double2* ph, int sumd);

@@ -529,11 +529,22 @@ __device__ __forceinline__ void zphase_all(const Phase& P, const typename ZM<R>:
   for (int b = threadIdx.x; b < nb; b += nthr) zphase_block<DL, PAR, FL, R>(P, M, ys, ks, blk_pos<DL>(P, b));
 }
 
-// ks = H_r ys over every phase of the pass (threads [0, nthr)); ends with a barrier.
+// Named barriers: bar.sync waits for `n` threads (arrivals included), bar.arrive
+// counts this thread's warp without waiting; both order the shared-memory accesses
+// before them for the threads the barrier completes.  id 0 is __syncthreads.
+__device__ __forceinline__ void nb_sync(int id, int n) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void nb_arrive(int id, int n) {
+  asm volatile("bar.arrive %0, %1;\n" ::"r"(id), "r"(n) : "memory");
+}
+
+// ks = H_r ys over every phase of the pass (threads [0, nthr)); every phase ends
+// with a barrier among those threads (__syncthreads when bar_id is 0).
 template <int DL, bool PAR, typename R>
 __device__ __forceinline__ void zpass_apply(const SlabPass& sp, const typename ZM<R>::T* __restrict__ M,
                                             const typename CT<R>::T* __restrict__ ys,
-                                            typename CT<R>::T* __restrict__ ks, int nthr) {
+                                            typename CT<R>::T* __restrict__ ks, int nthr, int bar_id = 0) {
   const int nb = sp.T / (DL * DL);
   for (int q = 0; q < sp.nph; ++q) {
     const Phase& P = sp.ph[q];
@@ -545,7 +556,8 @@ __device__ __forceinline__ void zpass_apply(const SlabPass& sp, const typename Z
 #undef SG_ZCASE
       default: break;
     }
-    __syncthreads();
+    if (bar_id == 0) __syncthreads();
+    else nb_sync(bar_id, nthr);
   }
 }
 
@@ -601,11 +613,13 @@ struct SlabPlanHost {
   int zsumd = 0;
   int grid_zfwd = 0;
   size_t sm_zfwd[kMaxPass] = {0};
+  size_t sm_zws[kMaxPass] = {0};   // warp-specialised FP32 pass (0: not usable for this pass)
 };
 
 // Byte offset of the real-operator row in the shared memory of k_zslab_fwd: after
-// the two tiles and the phase parts (256 low, T / 256 high), 16-byte aligned.
-__host__ __device__ inline size_t zrow_smem_off(int T, size_t csz) {
+// `ntile` tiles (2, or 4 for the double-buffered kernel) and the phase parts (256
+// low, T / 256 high), 16-byte aligned.
+__host__ __device__ inline size_t zrow_smem_off(int T, size_t csz, int ntile = 2) {
   const int nhi = T > 256 ? T / 256 : 1;
-  return ((2 * (size_t)spad(T) + 256 + nhi) * csz + 15) & ~(size_t)15;
+  return (((size_t)ntile * spad(T) + 256 + nhi) * csz + 15) & ~(size_t)15;
 }
