@@ -1,7 +1,8 @@
 #!/usr/bin/env python
-"""Benchmark of the fidelity + adjoint-gradient solve on one GB300 (or N, as
-independent replicas with their own seeds: the columns of one solve are a
-partition of the path, so N GPUs run weak-scaled copies and need no collective).
+"""Benchmark of the fidelity + adjoint-gradient solve on one GB300, or on N: by
+default N independent replicas with their own seeds (weak scaling, no collective);
+with --shard one gate's columns split over the N ranks, which sum their fidelity
+terms and gradients over NCCL (strong scaling).
 
 One bench step = one pass of the whole hot path on the workload: subsystem build
 and eigensolve, stage tables, forward RK4 of every column with checkpoints,
@@ -9,7 +10,7 @@ fidelity, co-state, checkpointed discrete adjoint with fused cross-density
 reductions, and the parameter chain.  Metric: state-column RK steps per second of
 that solve (S columns x N steps per solve).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py [--gpus N [--shard]] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...     # the FP64 CPU oracle as it stands
 """
 import argparse
@@ -174,7 +175,9 @@ def bench_config(args, wl, desc, world):
             else "pulse and Hamiltonian parameters",
             "l2": "inputs larger than L2 (slab 128 MiB c64 / 256 MiB c128)"
             if D * S * 8 > 129e6 else "L2-resident working set; no flush",
-            "parallelism": f"{world} independent replica(s), one per GPU"}
+            "parallelism": (f"one gate's columns sharded over {world} GPUs (NCCL sums of the fidelity terms "
+                            "and gradients)" if world > 1 and getattr(args, "shard", False)
+                            else f"{world} independent replica(s), one per GPU")}
 
 
 def _json_num(x):
@@ -199,7 +202,8 @@ def run_ours(args):
         B.build()
     from paper_2406_18155_gb300.api import Context, System, evolve_opts
     desc, make = WORKLOADS[args.workload]
-    wl = make(1000 + rank)
+    shard = world > 1 and args.shard
+    wl = make(1000 if shard else 1000 + rank)      # one gate over all ranks, or one replica each
     if args.t_ns > 0:                     # shortened run (profiling captures)
         wl["T"] = round(args.t_ns / wl["dt"]) * wl["dt"]
         for d in wl["drives"]:
@@ -217,8 +221,18 @@ def run_ours(args):
     grad = grad_set(args)
     args.grad_set = grad
 
+    if shard:
+        # this rank's contiguous block of the gate's columns; the fidelity sums and the
+        # gradients are summed over ranks through the library's callback (NCCL)
+        from paper_2406_18155_gb300.shard import column_block, torch_allreduce
+        c0, c1 = column_block(S, rank, world)
+        red = torch_allreduce(device=f"cuda:{local}")
+
     def one_step(ham=(grad == "all")):
         sysm.prepare()
+        if shard:
+            return sysm.fidelity_grad_sharded(wl["T"], wl["dt"], wl["target"], wl["col_index"][c0:c1], red,
+                                              kind=wl["fid_kind"], precision=prec, ckpt=args.ckpt, ham=ham)
         return sysm.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
                                   kind=wl["fid_kind"], precision=prec, ckpt=args.ckpt, ham=ham)
 
@@ -262,7 +276,7 @@ def run_ours(args):
         tt = torch.tensor([t_s], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_s = float(tt.item())
-    units = S * N * args.steps * world
+    units = S * N * args.steps * (1 if shard else world)
     value = units / t_s
 
     # ---- end to end through the public call: host target in, host gradients out
@@ -281,14 +295,14 @@ def run_ours(args):
         tt = torch.tensor([t_e2e], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
-    e2e_value = S * N * max(1, args.e2e_steps) * world / t_e2e
+    e2e_value = S * N * max(1, args.e2e_steps) * (1 if shard else world) / t_e2e
 
     out = None
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                "steps": args.steps, "warmup": args.warmup,
                "ms_per_step": t_s / args.steps * 1e3, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None,
+               "scaling": "strong" if shard else "weak", "vs_baseline": None,
                "dtype": "c64 stages, c128 state/co-state, f64 reductions" if prec == "mixed" else "c128",
                "data": "synthetic (seeded, shapes and value ranges of the paper's fluxonium workloads)",
                "config": bench_config(args, wl, desc, world),
@@ -707,6 +721,9 @@ def main():
     ap.add_argument("--workload", default="fluxonium_ring10", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--ckpt", type=int, default=0)
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1 GPUs: shard one gate's columns over the ranks (strong scaling) "
+                         "instead of running one replica per GPU")
     ap.add_argument("--fp64-steps", type=int, default=64,
                     help="forward steps of the FP64-vs-mixed comparison (0: skip)")
     ap.add_argument("--fp64-grad-steps", type=int, default=64,

@@ -276,6 +276,31 @@ sg_status sg_fidelity_grad(sg_system* sys, const sg_evolve_opts* opts,
                            const double* target_re_im, int kind, double* F_out,
                            double* grad_pulse, double* grad_ham, int ckpt_interval);
 
+/* Column-sharded F and gradient: the paper distributes the unitary's columns across
+ * devices (Sec. 4.2, multi-GPU benchmark).  Each shard (a process, usually one per
+ * GPU) calls this with its own columns in opts->col_index; together the shards'
+ * columns are the columns of the unsharded sg_fidelity_grad (for SG_FID_AVG every
+ * computational state exactly once over all shards).  The columns evolve
+ * independently; the fidelity couples them only through sums over columns, so the
+ * call exchanges two small vectors through the caller's collective:
+ *   1. after the forward evolution, buf = {Re z, Im z, q, S_c} (n = 4) of this
+ *      shard, z = sum_s <target_l(s)|psi_s>, q = sum_s ||T^dag psi_s||^2 over its
+ *      computational columns, S_c their number;
+ *   2. after the adjoint, this shard's gradient {grad_pulse, grad_ham} (n = the
+ *      number of pulse parameters, plus 3 Nq + couplings when grad_ham is given).
+ * `allreduce(buf, n, user)` must replace buf by its element-wise sum over all
+ * shards (every shard calls it the same number of times, in the same order) and
+ * return 0; non-zero aborts the call with SG_E_STATE.  F (from the sums) and the
+ * gradient (the sum of the shards' gradients, linear in the co-states) then equal
+ * the unsharded call's up to summation order, on every shard.  Product basis, no
+ * compensation (else SG_E_UNSUPPORTED).  The callback runs on the calling thread
+ * between kernel launches, with the context stream idle and the context held: it
+ * must not call this library on the same context. */
+typedef int (*sg_allreduce_fn)(double* buf, int n, void* user);
+sg_status sg_fidelity_grad_sharded(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
+                                   int kind, double* F_out, double* grad_pulse, double* grad_ham,
+                                   int ckpt_interval, sg_allreduce_fn allreduce, void* user);
+
 /* Timing and memory of the last sg_fidelity / sg_fidelity_grad on this system:
  * out[0] forward ms, out[1] gradient (backward) ms, out[2] peak library device
  * bytes during the call, out[3] checkpoint interval used, out[4] number of kernel

@@ -264,6 +264,31 @@ class System:
                                          _dptr(gp), _dptr(gh) if ham else None, int(ckpt)))
         return F, gp[:npul], (gh[:nham] if ham else None)
 
+    def fidelity_grad_sharded(self, T, dt, target, col_index, allreduce, kind="avg", precision="mixed",
+                              frame="interaction", ckpt=0, ham=True, solver="rk4"):
+        """This shard's part of a column-sharded fidelity + gradient solve
+        (sg_fidelity_grad_sharded): col_index are this shard's columns, `allreduce` maps
+        a float64 numpy vector to its sum over all shards (shard.torch_allreduce).
+        Returns the F and gradient of the whole solve, the same on every shard."""
+        from .capi import SG_ALLREDUCE_FN
+        o, keep = evolve_opts(T, dt, precision, frame, col_index, solver=solver)
+        tg = _c128_pairs(target)
+        F = np.zeros(2)
+        npul, nham = self.param_counts()
+        gp, gh = np.zeros(max(npul, 1)), np.zeros(max(nham, 1))
+
+        def cb(buf, n, user):
+            try:
+                v = np.ctypeslib.as_array(buf, shape=(n,))
+                v[:] = np.asarray(allreduce(v.copy()), dtype=np.float64).reshape(n)
+                return 0
+            except Exception:                      # reported by the library as SG_E_STATE
+                return 1
+        fn = SG_ALLREDUCE_FN(cb)
+        self._chk(lib().sg_fidelity_grad_sharded(self.h, C.byref(o), _dptr(tg), _KIND[kind], _dptr(F),
+                                                 _dptr(gp), _dptr(gh) if ham else None, int(ckpt), fn, None))
+        return F, gp[:npul], (gh[:nham] if ham else None)
+
     def last_stats(self):
         out = np.zeros(5)
         self._chk(lib().sg_last_stats(self.h, _dptr(out)))

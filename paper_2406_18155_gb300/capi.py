@@ -60,6 +60,8 @@ class sg_stats(C.Structure):
 
 _P = C.c_void_p
 _I = C.c_int
+# int (*sg_allreduce_fn)(double* buf, int n, void* user)
+SG_ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.POINTER(C.c_double), C.c_int, C.c_void_p)
 _D = C.c_double
 _PD = C.POINTER(C.c_double)
 _PI = C.POINTER(C.c_int)
@@ -88,6 +90,8 @@ SIGNATURES = {
     "sg_evolve_noalloc": (_I, [_P, C.POINTER(sg_evolve_opts), _P]),
     "sg_fidelity": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _PD, _PD]),
     "sg_fidelity_grad": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I]),
+    "sg_fidelity_grad_sharded": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I,
+                                      SG_ALLREDUCE_FN, _P]),
     "sg_last_stats": (_I, [_P, _PD]),
     "sg_kernel_times": (_I, [_P, _PD, _I]),
     "sg_server_create": (_I, [_P, C.c_size_t, _I, C.POINTER(_P)]),

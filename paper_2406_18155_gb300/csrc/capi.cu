@@ -289,6 +289,17 @@ sg_status sg_fidelity_grad(sg_system* sys, const sg_evolve_opts* opts, const dou
                           ckpt_interval);
 }
 
+sg_status sg_fidelity_grad_sharded(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
+                                   int kind, double* F_out, double* grad_pulse, double* grad_ham,
+                                   int ckpt_interval, sg_allreduce_fn allreduce, void* user) {
+  if (!sys) return SG_E_INVALID;
+  if (!allreduce) return sg_fail(sys->ctx, SG_E_INVALID, "a sharded solve needs the caller's all-reduce");
+  if (ckpt_interval < 0) return sg_fail(sys->ctx, SG_E_INVALID, "ckpt_interval must be >= 0");
+  std::lock_guard<std::mutex> lk(sys->ctx->mu);
+  return sg_fidelity_impl(sys, opts, target_re_im, kind, F_out, nullptr, true, grad_pulse, grad_ham,
+                          ckpt_interval, allreduce, user);
+}
+
 sg_status sg_last_stats(const sg_system* sys, double* out5) {
   if (!sys || !out5) return SG_E_INVALID;
   for (int i = 0; i < 5; ++i) out5[i] = sys->last_stats[i];

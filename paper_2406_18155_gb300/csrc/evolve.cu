@@ -813,6 +813,76 @@ __global__ void k_fidelity(FidArgs a) {
   }
 }
 
+// Column-sharded fidelity (Sec. 4.2: the unitary's columns distributed over
+// devices).  Both fidelities depend on the columns only through sums over them:
+//   z = tr M = sum_s <t_l(s) | u_s>,  q = tr(M M^dag) = sum_s ||T^dag u_s||^2,  S_c,
+// so a shard evolves its columns, contributes its partial sums, and after the sums
+// over shards computes F and its columns' co-states exactly as the unsharded solve:
+//   F_state = |z / S_c|^2,  F_avg = (q + |z|^2) / (D_c (D_c + 1)),
+//   co-state of column s (label l):  F_state: 2 z / S_c^2 t_l,
+//                                    F_avg:   2 (T (T^dag u_s) + z t_l) / (D_c (D_c + 1)).
+// k_shard_partials writes M_loc[x][s] = (T^dag u_s)_x (D_c x S, the shard's columns)
+// and part = {Re z, Im z, q, S_c} of this shard.
+__global__ void k_shard_partials(FidArgs a, double* __restrict__ part) {
+  __shared__ double red[kT];
+  const int tid = threadIdx.x, nt = blockDim.x, Dc = a.Dc;
+  double zr = 0.0, zi = 0.0, q = 0.0, sc = 0.0;
+  for (int i = tid; i < Dc * a.S; i += nt) {
+    const int x = i / a.S, s = i % a.S, l = a.lab[s];
+    double2 acc = make_double2(0.0, 0.0);
+    if (l >= 0) {
+      for (int r = 0; r < Dc; ++r) {
+        const double2 t = a.Tg[r * Dc + x], u = a.Uc[r * a.S + s];
+        acc.x += t.x * u.x + t.y * u.y;
+        acc.y += t.x * u.y - t.y * u.x;
+      }
+      q += acc.x * acc.x + acc.y * acc.y;
+      if (x == l) { zr += acc.x; zi += acc.y; }
+      if (x == 0) sc += 1.0;
+    }
+    a.M[i] = acc;
+  }
+  const double Zr = block_sum(zr, red), Zi = block_sum(zi, red);
+  const double Q = block_sum(q, red), Sc = block_sum(sc, red);
+  if (tid == 0) { part[0] = Zr; part[1] = Zi; part[2] = Q; part[3] = Sc; }
+}
+
+// F from the sums over every shard (glob = {Re z, Im z, q, S_c}) and the co-states
+// of this shard's columns (lab frame, D_c x S).  F_avg is defined when the shards
+// together evolved every computational state once (S_c = D_c; the caller's column
+// partition guarantees they are distinct).
+__global__ void k_shard_costate(FidArgs a, const double* __restrict__ glob) {
+  const int tid = threadIdx.x, nt = blockDim.x, Dc = a.Dc;
+  const double Zr = glob[0], Zi = glob[1], Q = glob[2], Sc = glob[3];
+  const bool full = (int)llround(Sc) == Dc;
+  if (tid == 0) {
+    a.F[0] = full ? (Q + Zr * Zr + Zi * Zi) / ((double)Dc * (Dc + 1)) : nan("");
+    a.F[1] = (Zr * Zr + Zi * Zi) / (Sc * Sc);
+  }
+  if (!a.bar) return;
+  for (int i = tid; i < Dc * a.S; i += nt) {
+    const int r = i / a.S, s = i % a.S, l = a.lab[s];
+    double2 b = make_double2(0.0, 0.0);
+    if (l >= 0) {
+      const double2 t = a.Tg[r * Dc + l];
+      if (a.kind == SG_FID_STATE) {
+        const double f = 2.0 / (Sc * Sc);
+        b = make_double2(f * (Zr * t.x - Zi * t.y), f * (Zr * t.y + Zi * t.x));
+      } else {
+        double2 acc = make_double2(Zr * t.x - Zi * t.y, Zr * t.y + Zi * t.x);
+        for (int x = 0; x < Dc; ++x) {
+          const double2 tt = a.Tg[r * Dc + x], m = a.M[x * a.S + s];
+          acc.x += tt.x * m.x - tt.y * m.y;
+          acc.y += tt.x * m.y + tt.y * m.x;
+        }
+        const double f = 2.0 / ((double)Dc * (Dc + 1));
+        b = make_double2(f * acc.x, f * acc.y);
+      }
+    }
+    a.bar[i] = b;
+  }
+}
+
 // Virtual-Z compensation: phases a (rows) and b (columns) of diag(1, e^{i phase}) gates
 // on the qubits maximising |tr M|, M = T^dag Z(a) U Z(b), tr M = sum_rl W[r][l]
 // za[r] zb[l] with W = conj(T) o U and za[r] = exp(i sum_q a_q bit_q(r)).  Coordinate
@@ -2153,8 +2223,9 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
 
 sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, int kind,
                            double* F_out, double* Ucomp_out, bool grad, double* grad_pulse,
-                           double* grad_ham, int ckpt) {
+                           double* grad_ham, int ckpt, sg_allreduce_fn red, void* red_user) {
   sg_ctx* ctx = sys->ctx;
+  const bool shard = red != nullptr;    // this call evolves one shard of the columns
   if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
   if (!target) return sg_fail(ctx, SG_E_INVALID, "target is NULL");
   if (!o || !o->col_index) return sg_fail(ctx, SG_E_INVALID, "fidelity needs opts->col_index");
@@ -2195,8 +2266,17 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   bool full = true;
   for (int j = 0; j < s.Dc; ++j) if (seen[j] != 1) full = false;
   if (full && s.Dc > 256) full = false;
-  if (grad && kind == SG_FID_AVG && !full)
+  if (shard) {
+    for (int j = 0; j < s.Dc; ++j)
+      if (seen[j] > 1) return sg_fail(ctx, SG_E_INVALID, "a computational state is evolved twice in this shard");
+    if (o->compensation != SG_COMP_NONE || o->basis != SG_BASIS_PRODUCT)
+      return sg_fail(ctx, SG_E_UNSUPPORTED, "a sharded solve takes the product basis without compensation");
+    if (kind == SG_FID_AVG && s.Dc > 256)
+      return sg_fail(ctx, SG_E_INVALID, "F_avg needs Dc <= 256");
+    full = false;
+  } else if (grad && kind == SG_FID_AVG && !full) {
     return sg_fail(ctx, SG_E_INVALID, "F_avg needs every computational state evolved exactly once (Dc <= 256)");
+  }
   if (o->compensation != SG_COMP_NONE && o->compensation != SG_COMP_VZ)
     return sg_fail(ctx, SG_E_INVALID, "compensation must be SG_COMP_NONE or SG_COMP_VZ");
   const bool vz = o->compensation == SG_COMP_VZ;
@@ -2218,7 +2298,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   double2* Tg = sv.ar.get<double2>((size_t)s.Dc * s.Dc);
   double2* Uc = sv.ar.get<double2>((size_t)s.Dc * s.S);
   double2* barc = sv.ar.get<double2>((size_t)s.Dc * s.S);
-  double2* Mbuf = sv.ar.get<double2>(full ? (size_t)s.Dc * s.Dc : 1);
+  double2* Mbuf = sv.ar.get<double2>(shard ? (size_t)s.Dc * s.S : (full ? (size_t)s.Dc * s.Dc : 1));
   double* Fd = sv.ar.get<double>(2);
   const long long n = s.D * s.S;
   sv.psi = sv.ar.get<double2>(n);
@@ -2325,7 +2405,26 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   fa.Uc = Uc; fa.Tg = Tfid; fa.lab = lab_dev; fa.F = Fd; fa.bar = grad ? barc : nullptr; fa.M = Mbuf;
   fa.T = s.T;
   fa.frame = s.frame;
-  k_fidelity<<<1, kT, 0, st>>>(fa);
+  if (shard) {
+    // this shard's partial sums, summed over the shards by the caller, then F and the
+    // co-states from the totals
+    double* part = sv.ar.get<double>(4);
+    if (!part) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+    k_shard_partials<<<1, kT, 0, st>>>(fa, part);
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    double hp[4];
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));    // reads only from an idle stream (see dcopy)
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(hp, part, sizeof hp, cudaMemcpyDeviceToHost, st));
+    SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+    if (red(hp, 4, red_user) != 0) return sg_fail(ctx, SG_E_STATE, "the caller's all-reduce of the fidelity sums failed");
+    if (!(hp[3] >= 1.0)) return sg_fail(ctx, SG_E_INVALID, "no shard evolved a computational state");
+    if (grad && kind == SG_FID_AVG && (int)std::llround(hp[3]) != s.Dc)
+      return sg_fail(ctx, SG_E_INVALID, "F_avg needs the shards to evolve every computational state exactly once");
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(part, hp, sizeof hp, cudaMemcpyHostToDevice, st));
+    k_shard_costate<<<1, kT, 0, st>>>(fa, part);
+  } else {
+    k_fidelity<<<1, kT, 0, st>>>(fa);
+  }
   sv.launches += 3;
   SG_CUDA_TRY(ctx, cudaGetLastError());
   cudaEventRecord(ev1, st);
@@ -2425,6 +2524,17 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
         grad_ham[3 * i + 2] = sys->modes[i].kind == 0 ? 0.0 : gd[3 * i + 2];
       }
       for (int e = 0; e < ne; ++e) grad_ham[3 * s.nq + e] = jb[e];
+    }
+    if (shard) {
+      // the gradient is linear in the co-states: the sum of the shards' gradients
+      const int nh = grad_ham ? 3 * s.nq + ne : 0;
+      std::vector<double> g((size_t)s.n_pulse + nh + 1, 0.0);
+      if (grad_pulse) for (int k = 0; k < s.n_pulse; ++k) g[k] = grad_pulse[k];
+      for (int k = 0; k < nh; ++k) g[s.n_pulse + k] = grad_ham[k];
+      if (red(g.data(), s.n_pulse + nh, red_user) != 0)
+        return sg_fail(ctx, SG_E_STATE, "the caller's all-reduce of the gradient failed");
+      if (grad_pulse) for (int k = 0; k < s.n_pulse; ++k) grad_pulse[k] = g[k];
+      for (int k = 0; k < nh; ++k) grad_ham[k] = g[s.n_pulse + k];
     }
     peak = sv.ar.bytes;
   } else {

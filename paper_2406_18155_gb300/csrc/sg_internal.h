@@ -94,9 +94,11 @@ sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev,
 
 // evolve.cu
 sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev);
+// red (nullable): the column-sharded solve's all-reduce (sg_fidelity_grad_sharded).
 sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target,
                            int kind, double* F_out, double* Ucomp_out, bool grad,
-                           double* grad_pulse, double* grad_ham, int ckpt);
+                           double* grad_pulse, double* grad_ham, int ckpt,
+                           sg_allreduce_fn red = nullptr, void* red_user = nullptr);
 
 // Dressed computational states (the eigenbasis of the idle Hamiltonian, App. C): one
 // block builds the D x D idle Hamiltonian (D <= kMaxDressed) in global scratch,
