@@ -253,6 +253,26 @@ sg_status sg_evolve(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
  * more than the 32 MiB (stage tables of 3 T/dt rows plus three D x S slabs). */
 sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
 
+/* Batched dense evolution on the tensor cores: nsys systems of one shape (the same
+ * modes and level counts, the same number of drives; parameters, couplings and
+ * pulses may differ) evolved together from the basis columns opts->col_index over
+ * the same T and dt, leaving the lab-frame states in psi_dev (device, nsys x D x S
+ * complex128, system-major, column innermost; caller-owned).  The paper applies H
+ * densely where the matrices are small (App. B, the dense versus local cost); here
+ * each system's terms, real in the truncated eigenbasis up to the interaction-frame
+ * phases, form the constant operand [C; O_1; ...; O_K] of tcgen05 TF32 matrix
+ * products with the state z = P^dag y (P the frame phases), each product split into
+ * three TF32 products (3xTF32, about FP32 accuracy, accumulated in FP32 in tensor
+ * memory); the RK4 stage math is FP32 and the state float-float.  Requires
+ * opts->precision == SG_MIXED and the RK4 solver; S = ncols in {4, 8, 16};
+ * (1 + drives) x D, with D rounded up to a multiple of 8, at most 128 (for
+ * example D = 16 with one drive: 4 systems per CTA; D = 25: 2); D <= 64; every
+ * operator of a drive real, every coupling of two real or two imaginary factors
+ * (else SG_E_UNSUPPORTED).  All systems must be prepared and share one context.
+ * A bounded wait for the tensor-core products that runs out returns SG_E_TIMEOUT.
+ * sg_last_stats of the first system gets the device time of the launch (out[0]). */
+sg_status sg_evolve_batch(sg_system* const* systems, int nsys, const sg_evolve_opts* opts, void* psi_dev);
+
 /* Evolve the columns named by opts->col_index and reduce them to fidelities.
  * target_re_im: host, Dc x Dc complex (Dc = 2^Nq), row-major (re, im); column j is
  * the target image of computational state j.  Columns whose initial state is not

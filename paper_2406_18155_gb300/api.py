@@ -296,6 +296,19 @@ class System:
                 "ckpt_interval": int(out[3]), "launches": int(out[4])}
 
 
+def evolve_batch(systems, T, dt, col_index, frame="interaction"):
+    """Lab-frame states of prepared same-shape systems evolved together on the tensor
+    cores (sg_evolve_batch): a (B, D, S) complex128 torch tensor on the device."""
+    import torch
+    D, _ = systems[0].dims()
+    S = len(col_index)
+    psi = torch.empty((len(systems), D, S), dtype=torch.complex128, device=f"cuda:{systems[0].ctx.device}")
+    o, keep = evolve_opts(T, dt, "mixed", frame, col_index)
+    hs = (C.c_void_p * len(systems))(*[s.h for s in systems])
+    systems[0]._chk(lib().sg_evolve_batch(hs, len(systems), C.byref(o), C.c_void_p(psi.data_ptr())))
+    return psi
+
+
 def workload_fidelity(ctx, wl, precision="mixed", grad=False, ckpt=0):
     """Convenience: build, prepare and solve one workload dict."""
     s = System.from_workload(ctx, wl)

@@ -289,6 +289,12 @@ sg_status sg_fidelity_grad(sg_system* sys, const sg_evolve_opts* opts, const dou
                           ckpt_interval);
 }
 
+sg_status sg_evolve_batch(sg_system* const* systems, int nsys, const sg_evolve_opts* opts, void* psi_dev) {
+  if (!systems || nsys < 1 || !systems[0]) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(systems[0]->ctx->mu);
+  return sg_evolve_batch_impl(systems, nsys, opts, psi_dev);
+}
+
 sg_status sg_fidelity_grad_sharded(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
                                    int kind, double* F_out, double* grad_pulse, double* grad_ham,
                                    int ckpt_interval, sg_allreduce_fn allreduce, void* user) {

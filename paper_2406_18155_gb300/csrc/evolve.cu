@@ -20,6 +20,7 @@
 #include "onchip.h"
 #include "grad.cuh"
 #include "slab.h"
+#include "dense.h"
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
@@ -2688,4 +2689,170 @@ extern "C" sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opt
   if (!opts) return sg_fail(ctx, SG_E_INVALID, "null options");
   double2* psi = static_cast<double2*>(psi_dev);
   return opts->precision == SG_MIXED ? noalloc_run<float>(sys, opts, psi) : noalloc_run<double>(sys, opts, psi);
+}
+
+// ---------------------------------------------------------------------------
+// Batched dense evolution on the tensor cores (sg_evolve_batch, dense.cu)
+// ---------------------------------------------------------------------------
+namespace {
+
+// f_k at every stage slot of every system (FP64 envelope and carrier, stored FP32).
+__global__ void k_batch_coef(const DriveDev* __restrict__ drives, const double* __restrict__ amps, int B, int K,
+                             int N, double dt, float* __restrict__ coef) {
+  const long long total = (long long)B * 3 * N * K;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+       x += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(x % K);
+    const long long bq = x / K;
+    const int q = (int)(bq % (3ll * N));
+    const int b = (int)(bq / (3ll * N));
+    const int n = q / 3, j = q % 3;
+    const double t = (double)(2 * n + j) * dt * 0.5;
+    const DriveDev dr = drives[(size_t)b * K + k];
+    coef[x] = (float)(envelope_dev(dr, amps, n, j, t) * cos(dr.omega * t + dr.phase));
+  }
+}
+
+// Real part (part 0) or imaginary part (part 1) of element (x, y) of operator op of mode m.
+double op_elem(const sg_system* sys, int m, int op, int x, int y, int part) {
+  const int d = sys->modes[m].d;
+  return sys->opd_host[m][2 * ((size_t)op * d * d + x * d + y) + part];
+}
+
+}  // namespace
+
+sg_status sg_evolve_batch_impl(sg_system* const* systems, int B, const sg_evolve_opts* o, void* psi_dev) {
+  if (!systems || B < 1 || !systems[0]) return SG_E_INVALID;
+  sg_system* s0 = systems[0];
+  sg_ctx* ctx = s0->ctx;
+  if (!o || !o->col_index || !psi_dev) return sg_fail(ctx, SG_E_INVALID, "batch evolution needs col_index and psi_dev");
+  if (o->precision != SG_MIXED)
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the tensor-core batch runs 3xTF32 products (precision SG_MIXED)");
+  if (o->solver != SG_SOLVER_RK4) return sg_fail(ctx, SG_E_UNSUPPORTED, "the tensor-core batch runs RK4");
+  if (o->frame != SG_FRAME_INTERACTION && o->frame != SG_FRAME_LAB) return sg_fail(ctx, SG_E_INVALID, "bad frame");
+  const int nq = (int)s0->modes.size(), K = (int)s0->drives.size();
+  for (int b = 0; b < B; ++b) {
+    const sg_system* sy = systems[b];
+    if (!sy || !sy->prepared) return sg_fail(ctx, SG_E_STATE, "every system of a batch must be prepared");
+    if (sy->ctx != ctx) return sg_fail(ctx, SG_E_INVALID, "the systems of a batch must share a context");
+    if ((int)sy->modes.size() != nq || (int)sy->drives.size() != K)
+      return sg_fail(ctx, SG_E_INVALID, "the systems of a batch must have the same modes and drive count");
+    for (int m = 0; m < nq; ++m)
+      if (sy->modes[m].d != s0->modes[m].d) return sg_fail(ctx, SG_E_INVALID, "the systems of a batch differ in levels");
+  }
+  Setup s;
+  sg_status rc = build_setup(s0, o, s);
+  if (rc != SG_OK) return rc;
+  const int D = (int)s.D, S = s.S;
+  int Dp = 0, R = 0, G = 0, Nn = 0;
+  if (s.D > 64 || !dense_shape(D, S, K, &Dp, &R, &G, &Nn))
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the tensor-core batch takes 2 S in {8, 16, 32} and (1 + drives) x D "
+                                          "(padded) <= 128");
+  for (int c = 0; c < S; ++c)
+    if (o->col_index[c] < 0 || o->col_index[c] >= s.D) return sg_fail(ctx, SG_E_INVALID, "col_index out of range");
+  SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  keep_pool_memory(ctx->device);
+  cudaStream_t st = ctx->stream;
+  // per system: dense real [C; O_1..O_K] (R x Dp), composite energies, drives
+  std::vector<double> A((size_t)B * R * Dp, 0.0), E((size_t)B * D, 0.0), amps;
+  std::vector<DriveDev> drv((size_t)B * std::max(1, K));
+  std::vector<int> dig((size_t)D * nq);
+  for (int i = 0; i < D; ++i)
+    for (int m = 0; m < nq; ++m) dig[(size_t)i * nq + m] = (int)((i / s.p.st[m]) % s.p.dims[m]);
+  for (int b = 0; b < B; ++b) {
+    sg_system* sy = systems[b];
+    Setup sb;
+    rc = b == 0 ? SG_OK : build_setup(sy, o, sb);
+    if (rc != SG_OK) return rc;
+    const Setup& ss = b == 0 ? s : sb;
+    TabArgs ta = ss.ta;
+    if (!real_terms(sy, ss, ta))
+      return sg_fail(ctx, SG_E_UNSUPPORTED, "the tensor-core batch needs every term real in the eigenbasis up to the "
+                                            "frame phases");
+    double* Ab = A.data() + (size_t)b * R * Dp;
+    for (int i = 0; i < D; ++i) {
+      double e = 0.0;
+      for (int m = 0; m < nq; ++m) e += sy->E_host[m][dig[(size_t)i * nq + m]];
+      E[(size_t)b * D + i] = e;
+      if (ss.frame == SG_FRAME_LAB) Ab[(size_t)i * Dp + i] += e;
+    }
+    // couplings: J A (x) B on modes (a, b), the other digits equal
+    for (int e = 0; e < ss.p.ne; ++e) {
+      const HostCoupling& c = sy->couplings[e];
+      const int part = ta.e_zpart[e];
+      const double J = part ? -c.J : c.J;
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          bool same = true;
+          for (int m = 0; m < nq && same; ++m)
+            if (m != c.a && m != c.b) same = dig[(size_t)i * nq + m] == dig[(size_t)j * nq + m];
+          if (!same) continue;
+          const int ia = dig[(size_t)i * nq + c.a], ja = dig[(size_t)j * nq + c.a];
+          const int ib = dig[(size_t)i * nq + c.b], jb = dig[(size_t)j * nq + c.b];
+          Ab[(size_t)i * Dp + j] += J * op_elem(sy, c.a, c.op_a, ia, ja, part) * op_elem(sy, c.b, c.op_b, ib, jb, part);
+        }
+    }
+    // drives: O_k on its mode
+    for (int k = 0; k < K; ++k) {
+      const HostDrive& hd = sy->drives[k];
+      double* Ok = Ab + (size_t)(1 + k) * Dp * Dp;
+      for (int i = 0; i < D; ++i)
+        for (int j = 0; j < D; ++j) {
+          bool same = true;
+          for (int m = 0; m < nq && same; ++m)
+            if (m != hd.mode) same = dig[(size_t)i * nq + m] == dig[(size_t)j * nq + m];
+          if (same)
+            Ok[(size_t)i * Dp + j] = op_elem(sy, hd.mode, hd.op, dig[(size_t)i * nq + hd.mode],
+                                             dig[(size_t)j * nq + hd.mode], 0);
+        }
+      DriveDev dd = ss.drives[k];
+      dd.amps_off += (int)amps.size();
+      drv[(size_t)b * K + k] = dd;
+    }
+    for (double v : ss.amps) amps.push_back(v);
+  }
+  Arena ar;
+  ar.st = st;
+  double* A_dev = ar.get<double>(A.size());
+  double* E_dev = ar.get<double>(E.size());
+  DriveDev* drv_dev = ar.get<DriveDev>(drv.size());
+  double* amps_dev = ar.get<double>(std::max<size_t>(1, amps.size()));
+  long long* cols_dev = ar.get<long long>(S);
+  float* coef = ar.get<float>((size_t)B * 3 * s.N * std::max(1, K));
+  int* err = ar.get<int>(1);
+  if (!A_dev || !E_dev || !drv_dev || !amps_dev || !cols_dev || !coef || !err)
+    return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(A_dev, A.data(), A.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(E_dev, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(drv_dev, drv.data(), drv.size() * sizeof(DriveDev), cudaMemcpyHostToDevice, st));
+  if (!amps.empty())
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(amps_dev, amps.data(), amps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols_dev, o->col_index, S * sizeof(long long), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(err, 0, sizeof(int), st));
+  if (K) k_batch_coef<<<grid_for((long long)B * 3 * s.N * K), kT, 0, st>>>(drv_dev, amps_dev, B, K, s.N, s.dt, coef);
+  DenseArgs da{};
+  da.B = B; da.D = D; da.Dp = Dp; da.S = S; da.K = K; da.R = R; da.G = G; da.N = Nn;
+  da.nsteps = s.N; da.frame = s.frame; da.dt = s.dt;
+  da.A = A_dev; da.coef = coef; da.E = E_dev; da.cols = cols_dev;
+  da.out = static_cast<double2*>(psi_dev); da.err = err; da.wlim = 1 << 22;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0); cudaEventCreate(&e1);
+  cudaEventRecord(e0, st);
+  const cudaError_t le = dense_launch(da, st);
+  cudaEventRecord(e1, st);
+  if (le != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return sg_fail(ctx, SG_E_CUDA, cudaGetErrorString(le)); }
+  int herr = 0;
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0); cudaEventDestroy(e1);
+  s0->last_stats[0] = ms;
+  s0->last_stats[1] = 0;
+  s0->last_stats[2] = (double)ar.bytes;
+  s0->last_stats[3] = 0;
+  s0->last_stats[4] = K ? 2 : 1;
+  if (herr) return sg_fail(ctx, SG_E_TIMEOUT, "tensor-core batch: a bounded wait for the MMAs ran out");
+  return SG_OK;
 }

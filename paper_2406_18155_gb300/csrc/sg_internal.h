@@ -94,6 +94,7 @@ sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev,
 
 // evolve.cu
 sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev);
+sg_status sg_evolve_batch_impl(sg_system* const* systems, int B, const sg_evolve_opts* o, void* psi_dev);
 // red (nullable): the column-sharded solve's all-reduce (sg_fidelity_grad_sharded).
 sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target,
                            int kind, double* F_out, double* Ucomp_out, bool grad,
