@@ -429,6 +429,77 @@ def serving_bench(ctx, n_requests, slots, seed=7):
                       "serving distribution (the full stream is 10k requests), fidelity + gradient each"}
 
 
+def dense_comparison(ctx, nsys, onchip_sys, threads=32):
+    """Configs 1-2 shapes (transmon pair D = 16, 16 columns; fluxonium CR pair D = 25,
+    4 columns; full horizons, 10^4 steps) as batches of systems of different seeds:
+    the tensor-core batch (sg_evolve_batch, 3xTF32) against the on-chip kernels
+    (sg_evolve, mixed) for one system alone and for many systems at once (the on-chip
+    solves issued from `threads` host threads, each with its own context and stream).
+    Device time of the batch launch; wall time of the concurrent on-chip solves."""
+    import torch
+    from concurrent.futures import ThreadPoolExecutor
+    from paper_2406_18155_gb300.api import Context, System, evolve_batch
+    out = {}
+    for name, make in (("transmon_pair_d16", lambda sd: W.transmon_pair(seed=sd)),
+                       ("fluxonium_pair_cr_d25", lambda sd: W.fluxonium_pair_cr(seed=sd))):
+        wls = [make(sd) for sd in range(nsys)]
+        S, N = len(wls[0]["col_index"]), int(round(wls[0]["T"] / wls[0]["dt"]))
+        sys_ = []
+        for wl in wls:
+            s_ = System.from_workload(ctx, wl)
+            s_.prepare()
+            sys_.append(s_)
+        r = {"columns": S, "rk4_steps": N}
+        for B in (1, nsys):
+            evolve_batch(sys_[:B], wls[0]["T"], wls[0]["dt"], wls[0]["col_index"])      # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            evolve_batch(sys_[:B], wls[0]["T"], wls[0]["dt"], wls[0]["col_index"])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+            r[f"tensor_batch_{B}_wall_s"] = wall
+            r[f"tensor_batch_{B}_col_steps_per_s"] = B * S * N / wall
+        # on-chip, one system alone
+        sys_[0].evolve(wls[0]["T"], wls[0]["dt"], precision="mixed", col_index=wls[0]["col_index"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sys_[0].evolve(wls[0]["T"], wls[0]["dt"], precision="mixed", col_index=wls[0]["col_index"])
+        torch.cuda.synchronize()
+        r["onchip_1_wall_s"] = time.perf_counter() - t0
+        r["onchip_1_col_steps_per_s"] = S * N / r["onchip_1_wall_s"]
+        # on-chip, many systems at once from several host threads
+        M = min(onchip_sys, nsys)
+        per = [list(range(k, M, threads)) for k in range(threads)]
+        ctxs = [Context(ctx.device, stream=torch.cuda.Stream(ctx.device)) for _ in range(threads)]
+        loc = []
+        for k in range(threads):
+            row = []
+            for idx in per[k]:
+                s_ = System.from_workload(ctxs[k], wls[idx])
+                s_.prepare()
+                row.append((s_, wls[idx]))
+            loc.append(row)
+
+        def work(k):
+            for s_, wl in loc[k]:
+                s_.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"])
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(work, range(threads)))                  # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            list(ex.map(work, range(threads)))
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - t0
+        r[f"onchip_{M}_concurrent_wall_s"] = wall
+        r[f"onchip_{M}_concurrent_col_steps_per_s"] = M * S * N / wall
+        r["tensor_over_onchip_throughput"] = r[f"tensor_batch_{nsys}_col_steps_per_s"] / r[
+            f"onchip_{M}_concurrent_col_steps_per_s"]
+        for c in ctxs:
+            c.close()
+        out[name] = r
+    return out
+
+
 def slab_passes(D):
     # plans used by the tiled kernels: one pass while a column fits one tile
     # (4096 entries), two overlapping mode groups for the ring beyond that
@@ -737,6 +808,11 @@ def main():
     ap.add_argument("--serving", type=int, default=64, help="Poisson requests of the serving sample (0: skip); twice as many run saturated first")
     ap.add_argument("--serving-slots", type=int, default=32)
     ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
+    ap.add_argument("--dense", type=int, default=0,
+                    help="compare the tensor-core batch with the on-chip kernels on this many systems of the "
+                         "config-1 and config-2 shapes and exit")
+    ap.add_argument("--dense-onchip", type=int, default=512,
+                    help="systems of the concurrent on-chip comparison (with --dense)")
     ap.add_argument("--t-ns", type=float, default=0.0, help="shorten the workload to T ns (profiling)")
     ap.add_argument("--q2", action="store_true",
                     help="also time the second-order Suzuki-Trotter solver against RK4 (D <= 4096)")
@@ -756,6 +832,14 @@ def main():
         torch.cuda.set_device(0)
         for r in onchip_shapes(Context(0), args.onchip_shapes, args.shape):
             print(json.dumps(r), flush=True)
+    elif args.dense > 0:
+        import torch
+        from paper_2406_18155_gb300 import build as B
+        B.build()
+        from paper_2406_18155_gb300.api import Context
+        torch.cuda.set_device(0)
+        print(json.dumps({"dense_tensor_vs_onchip": dense_comparison(Context(0), args.dense, args.dense_onchip)}),
+              flush=True)
     elif args.only_serving:
         import torch
         from paper_2406_18155_gb300 import build as B
