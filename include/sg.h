@@ -253,6 +253,34 @@ sg_status sg_evolve(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
  * more than the 32 MiB (stage tables of 3 T/dt rows plus three D x S slabs). */
 sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opts, void* psi_dev);
 
+/* Open-system evolution (the paper's LindbladObj, Sec. 2.2; its solver carried over to
+ * the vectorised master equation, App. C last paragraph):
+ *   d rho/dt = -i [H(t), rho] + sum_c g_c (L_c rho L_c^dag - {L_c^dag L_c, rho} / 2).
+ * sg_add_collapse adds a collapse operator L (host, d x d complex row-major (re, im),
+ * in the mode's truncated eigenbasis; copied) on one mode at rate g >= 0 (1/ns); in
+ * the interaction frame L rotates with the frame like every operator.  At most 16.
+ * The evolution runs vec(rho) (row-major, ket index x D + bra index) under
+ * -i H_eff on 2 Nq modes (ket modes, then bra modes with negated energies) with
+ * the local terms of the generator: ket 1-body H_i(t) - (i/2) sum_c g_c L_c^dag L_c,
+ * bra 1-body -H_i(t)^T - (i/2) sum_c g_c (L_c^dag L_c)^T, ket couplings J A (x) B, bra
+ * couplings -J A^T (x) B^T, jumps i g_c L_c (x) L_c^*, on the same RK4 kernels (stage
+ * times of R2, complex stage rows, FP64 or mixed); at most 8 modes (16 doubled).
+ * No gradient. */
+sg_status sg_add_collapse(sg_system* sys, int mode, const double* L_re_im, double rate, int* id_out);
+/* rho(T) (host, D x D complex row-major, lab frame) from rho0 (host, same layout).
+ * opts: T, dt, precision, frame; ncols and col_index are ignored. */
+sg_status sg_evolve_open(sg_system* sys, const sg_evolve_opts* opts, const double* rho0_re_im,
+                         double* rho_out_re_im);
+/* Average gate fidelity of the open evolution against the target unitary (host,
+ * Dc x Dc complex): the channel on the computational block, S[(a,b),(j,k)] =
+ * <c_a| E(|c_j><c_k|) |c_b>, from Dc^2 density-matrix evolutions run as columns of
+ * one solve; F_out[1] = F_pro = Re sum conj(T (x) T^*) S / Dc^2 (process fidelity),
+ * F_out[0] = F_avg = (Dc^2 F_pro + P) / (Dc (Dc + 1)) with P the population kept in
+ * the computational block (Nielsen's relation written for a channel that may leak;
+ * for a closed evolution it equals sg_fidelity's F_avg).  1..6 qubit modes. */
+sg_status sg_gate_fidelity_open(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
+                                double* F_out);
+
 /* Batched dense evolution on the tensor cores: nsys systems of one shape (the same
  * modes and level counts, the same number of drives; parameters, couplings and
  * pulses may differ) evolved together from the basis columns opts->col_index over

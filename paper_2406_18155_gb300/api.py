@@ -168,8 +168,35 @@ class System:
                         sigma=d.get("sigma", 1.0), t0=d.get("t0", 0.0), length=d["length"],
                         omega_d=d.get("omega_d", 0.0), omega_mode=d.get("omega_mode"),
                         phase=d.get("phase", 0.0))
+        for c in wl.get("collapse", []):
+            s.add_collapse(c["mode"], c["L"], c["rate"])
         s.wl = wl
         return s
+
+    def add_collapse(self, mode, L, rate):
+        """Collapse operator L (d x d, truncated eigenbasis) on `mode` at rate (1/ns)."""
+        a = _c128_pairs(np.asarray(L, dtype=np.complex128))
+        self._keep.append(a)
+        out = C.c_int()
+        self._chk(lib().sg_add_collapse(self.h, int(mode), _dptr(a), float(rate), C.byref(out)))
+        return out.value
+
+    def evolve_open(self, T, dt, rho0, precision="mixed", frame="interaction"):
+        """Lab-frame rho(T) (D x D numpy) of the open evolution from rho0 (sg_evolve_open)."""
+        o, keep = evolve_opts(T, dt, precision, frame, None, ncols=1)
+        r0 = _c128_pairs(np.asarray(rho0, dtype=np.complex128))
+        out = np.zeros_like(r0)
+        self._chk(lib().sg_evolve_open(self.h, C.byref(o), _dptr(r0), _dptr(out)))
+        return out.view(np.complex128).reshape(np.asarray(rho0).shape)
+
+    def gate_fidelity_open(self, T, dt, target, precision="mixed", frame="interaction"):
+        """(F_avg, F_pro) of the open evolution on the computational block against the
+        target unitary (sg_gate_fidelity_open)."""
+        o, keep = evolve_opts(T, dt, precision, frame, None, ncols=1)
+        tg = _c128_pairs(target)
+        F = np.zeros(2)
+        self._chk(lib().sg_gate_fidelity_open(self.h, C.byref(o), _dptr(tg), _dptr(F)))
+        return F[0], F[1]
 
     def close(self):
         if self.h:

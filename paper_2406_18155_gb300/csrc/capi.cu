@@ -134,6 +134,32 @@ sg_status sg_add_local_op(sg_system* sys, int mode, const double* re_im, int* op
   return SG_OK;
 }
 
+sg_status sg_add_collapse(sg_system* sys, int mode, const double* L_re_im, double rate, int* id_out) {
+  if (!sys) return SG_E_INVALID;
+  if (mode < 0 || mode >= (int)sys->modes.size()) return sg_fail(sys->ctx, SG_E_INVALID, "mode index out of range");
+  if (!L_re_im) return sg_fail(sys->ctx, SG_E_INVALID, "collapse operator is NULL");
+  if (!isfin(rate) || rate < 0.0) return sg_fail(sys->ctx, SG_E_INVALID, "collapse rate must be finite and >= 0");
+  const int d = sys->modes[mode].d;
+  for (int k = 0; k < 2 * d * d; ++k)
+    if (!isfin(L_re_im[k])) return sg_fail(sys->ctx, SG_E_INVALID, "collapse operator entries must be finite");
+  if (sys->collapses.size() >= 16) return sg_fail(sys->ctx, SG_E_UNSUPPORTED, "at most 16 collapse operators");
+  sys->collapses.push_back(HostCollapse{mode, std::vector<double>(L_re_im, L_re_im + 2 * d * d), rate});
+  if (id_out) *id_out = (int)sys->collapses.size() - 1;
+  return SG_OK;
+}
+
+sg_status sg_evolve_open(sg_system* sys, const sg_evolve_opts* opts, const double* rho0_re_im, double* rho_out_re_im) {
+  if (!sys) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(sys->ctx->mu);
+  return sg_evolve_open_impl(sys, opts, rho0_re_im, rho_out_re_im);
+}
+
+sg_status sg_gate_fidelity_open(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im, double* F_out) {
+  if (!sys) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(sys->ctx->mu);
+  return sg_gate_fidelity_open_impl(sys, opts, target_re_im, F_out);
+}
+
 sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b, double strength,
                           int* term_out) {
   if (!sys) return SG_E_INVALID;

@@ -56,10 +56,15 @@ struct sg_ctx {
 
 struct StageTables;  // defined in evolve.cu
 
+// A collapse operator of the open-system evolution: L (d x d complex in the truncated
+// eigenbasis, 2 d^2 doubles) on one mode at rate gamma (1/ns).
+struct HostCollapse { int mode; std::vector<double> L; double rate; };
+
 struct sg_system {
   sg_ctx* ctx = nullptr;
   std::vector<HostMode> modes;
   std::vector<HostCoupling> couplings;
+  std::vector<HostCollapse> collapses;
   std::vector<HostDrive> drives;
   bool prepared = false;
   // device data
@@ -94,6 +99,8 @@ sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev,
 
 // evolve.cu
 sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev);
+sg_status sg_evolve_open_impl(sg_system* sys, const sg_evolve_opts* o, const double* rho0, double* rho_out);
+sg_status sg_gate_fidelity_open_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, double* F_out);
 sg_status sg_evolve_batch_impl(sg_system* const* systems, int B, const sg_evolve_opts* o, void* psi_dev);
 // red (nullable): the column-sharded solve's all-reduce (sg_fidelity_grad_sharded).
 sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target,
