@@ -371,13 +371,49 @@ def onchip_shapes(ctx, nsteps, only=None):
     return sorted(out, key=lambda r: (r["D"], r["shape"]))
 
 
-def serving_bench(ctx, n_requests, slots, seed=7):
+class UtilSampler:
+    """Device utilisation (nvidia-smi utilization.gpu: the fraction of time a kernel was
+    running) sampled every 200 ms while a serving stream runs."""
+
+    def __init__(self, device):
+        self.device, self.proc, self.vals = device, None, []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            try:
+                self.vals.append(float(line.strip()))
+            except ValueError:
+                pass
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        return statistics.mean(self.vals) / 100.0 if self.vals else None
+
+
+def serving_bench(ctx, n_requests, slots, seed=7, rates=(0.7,), n_saturated=None):
     """Config 4: requests of 2-5 coupled transmons or fluxoniums at 3-5 levels,
     T ~ U[20, 200] ns, random 10-segment pulses, each a fidelity + gradient solve.
-    First 2 x n_requests submitted at once: the saturated throughput is their count
-    over the wall time until the last finishes (a conservative figure: it includes
-    the drain, when only the longest requests are left).  Then n_requests with
-    Poisson arrivals at 0.7 x that rate (latency under load)."""
+    First n_saturated requests (default 2 x n_requests) submitted at once: the
+    saturated throughput is their count over the wall time until the last finishes
+    (conservative: it includes the drain, when only the longest requests are left).
+    Then, for each rate fraction, a stream of n_requests with Poisson arrivals at
+    that fraction of the saturated rate: solves/s, p50/p99 latency (submit -> result)
+    and the device utilisation sampled during the stream."""
     from paper_2406_18155_gb300.api import Server, System
     rng = np.random.Generator(np.random.PCG64(seed))
 
@@ -385,48 +421,57 @@ def serving_bench(ctx, n_requests, slots, seed=7):
         out = []
         for _ in range(nr):
             wl = W.serving_request(rng)
-            s = System.from_workload(ctx, wl)
-            out.append((wl, s))
+            s_ = System.from_workload(ctx, wl)
+            out.append((wl, s_))
         return out
 
     srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
-    sat = make(max(4, 2 * n_requests))
+    sat = make(max(4, n_saturated or 2 * n_requests))
     t0 = time.perf_counter()
-    tk = [srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg") for wl, s in sat]
+    tk = [srv.submit(s_, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg") for wl, s_ in sat]
     sat_res = [srv.wait(t) for t in tk]
     sat_rate = len(sat) / (time.perf_counter() - t0)
     srv.close()
-    srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
-    reqs = make(n_requests)
-    rate = 0.7 * sat_rate
-    gaps = rng.exponential(1.0 / rate, size=len(reqs))
-    t0 = time.perf_counter()
-    tk = []
-    next_t = 0.0
-    for (wl, s), g in zip(reqs, gaps):
-        next_t += g
-        dly = next_t - (time.perf_counter() - t0)
-        if dly > 0:
-            time.sleep(dly)
-        tk.append(srv.submit(s, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg"))
-    res = [srv.wait(t) for t in tk]
-    wall = time.perf_counter() - t0
-    lat = np.array([r["done_s"] - r["submit_s"] for r in res])
-    st = srv.stats()
-    srv.close()
-    steps = np.array([int(round(wl["T"] / wl["dt"])) for wl, _ in reqs])
-    return {"requests": len(reqs), "saturated_solves_per_s": sat_rate, "saturated_requests": len(sat),
-            "arrival_rate_per_s": rate,
+    del sat
+    out = {"saturated_solves_per_s": sat_rate, "saturated_requests": len(sat_res), "slots": slots,
+           "saturated_errors": int(sum(r["status"] != 0 for r in sat_res)), "streams": []}
+    for frac in rates:
+        srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
+        reqs = make(n_requests)
+        rate = frac * sat_rate
+        gaps = rng.exponential(1.0 / rate, size=len(reqs))
+        util = UtilSampler(ctx.device)
+        util.start()
+        t0 = time.perf_counter()
+        tk = []
+        next_t = 0.0
+        for (wl, s_), g in zip(reqs, gaps):
+            next_t += g
+            dly = next_t - (time.perf_counter() - t0)
+            if dly > 0:
+                time.sleep(dly)
+            tk.append(srv.submit(s_, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg"))
+        res = [srv.wait(t) for t in tk]
+        wall = time.perf_counter() - t0
+        u = util.stop()
+        lat = np.array([r["done_s"] - r["submit_s"] for r in res])
+        srv.close()
+        steps = np.array([int(round(wl["T"] / wl["dt"])) for wl, _ in reqs])
+        out["streams"].append({
+            "rate_fraction": frac, "arrival_rate_per_s": rate, "requests": len(reqs),
             "solves_per_s": len(reqs) / wall, "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "slots": slots,
-            "gpu_busy_frac": st["gpu_busy_frac"], "errors": int(sum(r["status"] != 0 for r in res)),
-            "saturated_errors": int(sum(r["status"] != 0 for r in sat_res)),
-            "error_kinds": sorted({f'{wl["name"]}: {r["error"]}'
-                                   for (wl, _), r in list(zip(reqs, res)) + list(zip(sat, sat_res))
-                                   if r["status"] != 0}),
-            "mean_rk4_steps": float(steps.mean()),
-            "sample": f"{len(sat)} requests submitted at once + {len(reqs)} Poisson arrivals of the "
-                      "serving distribution (the full stream is 10k requests), fidelity + gradient each"}
+            "p99_s": float(np.percentile(lat, 99)), "device_utilisation": u,
+            "errors": int(sum(r["status"] != 0 for r in res)), "mean_rk4_steps": float(steps.mean())})
+        del reqs
+    # the first stream's figures at the top level, as before
+    st0 = out["streams"][0]
+    out.update({"requests": st0["requests"], "arrival_rate_per_s": st0["arrival_rate_per_s"],
+                "solves_per_s": st0["solves_per_s"], "p50_s": st0["p50_s"], "p99_s": st0["p99_s"],
+                "errors": st0["errors"], "device_utilisation": st0["device_utilisation"],
+                "sample": f"{len(sat_res)} requests submitted at once, then {n_requests} Poisson arrivals of the "
+                          f"serving distribution at each of {list(rates)} x the saturated rate (the full stream "
+                          "is 10k requests), fidelity + gradient each"})
+    return out
 
 
 def dense_comparison(ctx, nsys, onchip_sys, threads=32):
@@ -807,6 +852,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=64, help="Poisson requests of the serving sample (0: skip); twice as many run saturated first")
     ap.add_argument("--serving-slots", type=int, default=32)
+    ap.add_argument("--serving-rates", default="0.7",
+                    help="arrival rates as fractions of the saturated rate, comma-separated")
+    ap.add_argument("--serving-saturated", type=int, default=0,
+                    help="requests of the saturated sample (default 2 x --serving)")
     ap.add_argument("--only-serving", action="store_true", help="print just the serving sample")
     ap.add_argument("--dense", type=int, default=0,
                     help="compare the tensor-core batch with the on-chip kernels on this many systems of the "
@@ -846,8 +895,9 @@ def main():
         B.build()
         from paper_2406_18155_gb300.api import Context
         torch.cuda.set_device(0)
-        print(json.dumps({"serving": serving_bench(Context(0), args.serving, args.serving_slots)}),
-              flush=True)
+        rates = tuple(float(x) for x in args.serving_rates.split(","))
+        print(json.dumps({"serving": serving_bench(Context(0), args.serving, args.serving_slots, rates=rates,
+                                                   n_saturated=args.serving_saturated or None)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:
