@@ -284,6 +284,26 @@ __global__ void k_tables_z(TabArgs a, Z* __restrict__ zt, int zpar) {
   }
 }
 
+// The drive operators themselves as real matrices in the truncated eigenbasis,
+// packed like the stage rows (one DL x DL block per drive, DL the common level
+// count): the pulse-gradient adjoint of the real-operator passes contracts drive k's
+// operator with the rotated co-state and state.  One block per drive.
+template <typename Z>
+__global__ void k_ops_z(TabArgs a, Z* __restrict__ zo, int zpar, int DL) {
+  const int k = blockIdx.x;
+  const DriveDev dr = a.drives[k];
+  const int i = dr.mode, d = a.dims[i];
+  for (int el = threadIdx.x; el < DL * DL; el += blockDim.x) {
+    const int x = el / DL, kk = el % DL;
+    double v = 0.0;
+    if (x < d && (zpar ? kk < d / 2 : kk < d)) {
+      const int c = zpar ? ((x + 1) & 1) + 2 * kk : kk;
+      v = a.opd[a.opd_off[i] + dr.op * d * d + x * d + c].x;
+    }
+    zo[(size_t)k * DL * DL + el] = zpack<Z>(v);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Suzuki-Trotter tables (Sec. 2.3, App. A), lab frame
 // ---------------------------------------------------------------------------
@@ -1782,8 +1802,17 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
       if (sv.mixed) k_tables_z<float2><<<(unsigned)nst, 64, 0, st>>>(ta, (float2*)zt, zpar);
       else k_tables_z<double><<<(unsigned)nst, 64, 0, st>>>(ta, (double*)zt, zpar);
       ++sv.launches;
+      // the drive operators for the pulse-gradient adjoint
+      void* zo = nullptr;
+      if (grad && s.K > 0) {
+        zo = sv.ar.get<double>((size_t)s.K * s.p.dl * s.p.dl);
+        if (!zo) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the stage tables failed");
+        if (sv.mixed) k_ops_z<float2><<<(unsigned)s.K, 32, 0, st>>>(ta, (float2*)zo, zpar, s.p.dl);
+        else k_ops_z<double><<<(unsigned)s.K, 32, 0, st>>>(ta, (double*)zo, zpar, s.p.dl);
+        ++sv.launches;
+      }
       SG_CUDA_TRY(ctx, cudaGetLastError());
-      slab_bind_real(sv.slab, zt, sv.ph, s.sumd);
+      slab_bind_real(sv.slab, zt, sv.ph, s.sumd, zo, ta.drv_of_slot_start, ta.drv_list);
       s.ta = ta;
     }
   }

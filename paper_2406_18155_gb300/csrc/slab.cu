@@ -19,9 +19,6 @@
 
 namespace {
 
-// Dynamic shared memory a tiled pass may take: the 227 KB opt-in limit of a block
-// less 1 KB for the kernels' static shared variables.
-constexpr size_t kSlabSmemMax = 226 * 1024;
 
 // KIND: 0 first partial pass (kA = k), 1 middle partial (kA += k), 2 last pass after
 // partials (k += kA then the RK4 epilogue), 3 single pass (epilogue).
@@ -310,143 +307,6 @@ k_zslab_fwd_ws(SlabPass sp, const float2* __restrict__ X, const float2* __restri
   }
 }
 
-// Adjoint pass: X = kbar_s tile, Y = y_s tile.  Applies A_s^dag = i H to kbar
-// (partial, or with the adjoint epilogue) with the register-blocked phases, and
-// accumulates the cross-densities of this pass's slots: warp w owns slots w and
-// w + 8, its lanes walk the blocks of the slot's phase, and the d x d partial sums
-// stay in registers across all tiles; one fixed-order reduction at the end.
-template <typename R, int DL, bool PARX>
-__global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 2 : 1)
-k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename CT<R>::T* __restrict__ Y,
-           const typename CT<R>::T* __restrict__ tabrow, double2* __restrict__ pbar,
-           typename CT<R>::T* __restrict__ Xn, typename CT<R>::T* __restrict__ Db,
-           typename CT<R>::T* __restrict__ yA, double dt, XArgs xa, const int STAGE, const int KIND) {
-  typedef typename CT<R>::T C;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  C* xs = reinterpret_cast<C*>(smraw);
-  C* ys = xs + spad(sp.T);
-  C* ks = ys + spad(sp.T);
-  C* M = ks + spad(sp.T);
-  const int* __restrict__ off = sp.off;
-  load_common(sp, tabrow, M);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr int NA = xd_n<DL, PARX>();
-  C acc[kSPW][NA];
-#pragma unroll
-  for (int s = 0; s < kSPW; ++s)
-#pragma unroll
-    for (int a = 0; a < NA; ++a) acc[s][a] = cmk<C>(0.0, 0.0);
-  const long long ntiles = (long long)sp.S * sp.ntpc;
-  const R h = (R)dt;
-  const int nb = sp.T / (DL * DL);
-  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long base = tile_base(sp, tile);
-    load_tile<DL, 8>(sp, X, base, off, xs);
-    load_tile<DL, 8>(sp, Y, base, off, ys);
-    __syncthreads();
-    pass_apply<DL>(sp, M, xs, ks);
-    constexpr int EB = 4;
-    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * EB) {
-      long long g[EB];
-      C yb[EB], pa[EB], dd[EB];
-      double2 pbv[EB];
-      bool ok[EB];
-#pragma unroll
-      for (int j = 0; j < EB; ++j) {
-        const int t = t0 + j * kST;
-        ok[j] = t < sp.T;
-        g[j] = ok[j] ? base + __ldg(off + t) : base;
-        const C a = ok[j] ? ks[spos<DL>(t)] : cmk<C>(0.0, 0.0);
-        yb[j] = cmk<C>(-a.y, a.x);                  // i H kbar
-        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? yA[g[j]] : cmk<C>(0.0, 0.0);
-        pbv[j] = (KIND >= 2) && ok[j] ? pbar[g[j]] : make_double2(0.0, 0.0);
-        dd[j] = (KIND >= 2) && ok[j] && STAGE < 3 ? Db[g[j]] : cmk<C>(0.0, 0.0);
-      }
-#pragma unroll
-      for (int j = 0; j < EB; ++j) {
-        if (!ok[j]) continue;
-        C y = yb[j];
-        if (KIND == 0) { yA[g[j]] = y; continue; }
-        if (KIND == 1) { yA[g[j]] = cmk<C>(pa[j].x + y.x, pa[j].y + y.y); continue; }
-        if (KIND == 2) y = cmk<C>(pa[j].x + y.x, pa[j].y + y.y);
-        const C pr = to_c(pbv[j], R(0));
-        const C d = dd[j];
-        if (STAGE == 3) {
-          Db[g[j]] = y;
-          Xn[g[j]] = cmk<C>(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
-        } else if (STAGE == 2) {
-          Db[g[j]] = cmk<C>(d.x + y.x, d.y + y.y);
-          Xn[g[j]] = cmk<C>(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
-        } else if (STAGE == 1) {
-          Db[g[j]] = cmk<C>(d.x + y.x, d.y + y.y);
-          Xn[g[j]] = cmk<C>(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
-        } else {
-          double2 pn = make_double2(pbv[j].x + (double)(d.x + y.x), pbv[j].y + (double)(d.y + y.y));
-          pbar[g[j]] = pn;
-          C q = to_c(pn, R(0));
-          Xn[g[j]] = cmk<C>(h / 6 * q.x, h / 6 * q.y);
-        }
-      }
-    }
-    // cross-densities of this warp's slots over the tile
-#pragma unroll
-    for (int s = 0; s < kSPW; ++s) {
-      const int slot = warp + s * (kST / 32);
-      if (slot >= sp.nx) continue;                  // warp-uniform
-      const Phase& P = sp.ph[sp.x_ph[slot]];
-      const int type = sp.x_type[slot];
-      if (type >= 2 && !xa.ham) continue;           // coupling slot, not wanted
-      for (int b = lane; b < nb; b += 32)
-        xd_slot<DL, PARX>(P, type, M, xs, ys, blk_pos<DL>(P, b), acc[s]);
-    }
-    __syncthreads();
-  }
-  // warp reductions -> block partials [block][slot][DL*DL]
-#pragma unroll
-  for (int s = 0; s < kSPW; ++s) {
-    const int slot = warp + s * (kST / 32);
-    if (slot >= sp.nx) continue;                    // warp-uniform
-    if (sp.x_type[slot] >= 2 && !xa.ham) continue;
-#pragma unroll
-    for (int a = 0; a < DL; ++a)
-#pragma unroll
-      for (int b = 0; b < DL; ++b) {
-        double vr = 0.0, vi = 0.0;
-        if (!PARX || ((a + b) & 1)) {
-          vr = acc[s][xd_i<DL, PARX>(a, b)].x;
-          vi = acc[s][xd_i<DL, PARX>(a, b)].y;
-          for (int o = 16; o > 0; o >>= 1) {
-            vr += __shfl_xor_sync(0xffffffffu, vr, o);
-            vi += __shfl_xor_sync(0xffffffffu, vi, o);
-          }
-        }
-        if (lane == 0) xa.partial[((size_t)blockIdx.x * kMaxX + slot) * DL * DL + a * DL + b] = make_double2(vr, vi);
-      }
-  }
-  __shared__ bool last;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(xa.ticket, 1u) == gridDim.x - 1);
-  __syncthreads();
-  if (!last) return;
-  double2* Wt = reinterpret_cast<double2*>(smraw);   // nx * DL * DL
-  for (int i = threadIdx.x; i < sp.nx * DL * DL; i += blockDim.x) {
-    const int slot = i / (DL * DL), ab = i % (DL * DL);
-    double sr = 0.0, si = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) {
-      double2 v = __ldcg(xa.partial + ((size_t)b * kMaxX + slot) * DL * DL + ab);
-      sr += v.x;
-      si += v.y;
-    }
-    Wt[i] = make_double2(si, -sr);                     // W = -i C
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) *xa.ticket = 0u;
-  if (threadIdx.x < sp.nx && (xa.ham || sp.x_type[threadIdx.x] < 2))
-    contract_slot(xa, sp.x_gslot[threadIdx.x], Wt + threadIdx.x * DL * DL, DL);
-}
-
-
 // api [D][S] (digits in mode order) <-> internal [S][D] (permuted digits)
 __global__ void k_perm(PermArgs a, const double2* __restrict__ src, double2* __restrict__ dst, int to_int) {
   const long long total = a.D * a.S;
@@ -731,10 +591,31 @@ int slab_passes(const SlabPlanHost* h) { return h->np; }
 
 bool slab_real_shape_ok(const SlabPlanHost* h) { return h->DL == 2 || h->DL == 4; }
 bool slab_allpar(const SlabPlanHost* h) { return h->allpar; }
-void slab_bind_real(SlabPlanHost* h, const void* ztab, const double2* ph, int sumd) {
+void slab_bind_real(SlabPlanHost* h, const void* ztab, const double2* ph, int sumd, const void* zop,
+                    const int* drv_of_slot_start, const int* drv_list) {
   h->ztab = ztab;
   h->zph = ph;
   h->zsumd = sumd;
+  h->zop = zop;
+  h->zadj = zop != nullptr;
+  const size_t csz = h->mixed ? sizeof(float2) : sizeof(double2);
+  for (int g = 0; g < h->np && h->zadj; ++g) {
+    SlabPass& sp = h->pass[g];
+    sp.nd = 0;
+    for (int x = 0; x < sp.nx && h->zadj; ++x) {
+      if (sp.x_type[x] >= 2) continue;                 // coupling slots carry no drive
+      const int u = sp.x_gslot[x];
+      for (int i = drv_of_slot_start[u]; i < drv_of_slot_start[u + 1]; ++i) {
+        if (sp.nd >= kMaxDrv) { h->zadj = false; break; }
+        sp.d_ph[sp.nd] = sp.x_ph[x];
+        sp.d_type[sp.nd] = sp.x_type[x];
+        sp.d_k[sp.nd] = drv_list[i];
+        ++sp.nd;
+      }
+    }
+    h->sm_zadj[g] = zrow_smem_off(sp.T, csz, 3) + (size_t)(((sp.row + 1) & ~1) + sp.nd * h->DL * h->DL) * 8;
+    if (h->sm_zadj[g] > kSlabSmemMax) h->zadj = false;
+  }
 }
 
 size_t slab_partial_elems(const SlabPlanHost* h) {
@@ -828,34 +709,6 @@ void fwd_stage(const SlabPlanHost* h, int stage, bool store, const void* X, cons
   fwd_launch<R, DL>(h, h->np - 1, X, row, pin, pout, Xn, Dacc, kA, dt, st, stage, store, 2, q);
 }
 
-template <typename R, int DL>
-void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, const void* row,
-                double2* pbar, void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st,
-                int stage, int kind) {
-  typedef typename CT<R>::T C;
-  auto kern = h->allpar ? k_slab_adj<R, DL, true> : k_slab_adj<R, DL, false>;
-  static const bool attr = [] {
-    cudaFuncSetAttribute(k_slab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
-    cudaFuncSetAttribute(k_slab_adj<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
-    return true;
-  }();
-  (void)attr;
-  kern<<<h->grid_adj, kST, h->sm_adj[g], st>>>(h->pass[g], (const C*)X, (const C*)Y, (const C*)row, pbar,
-                                                 (C*)Xn, (C*)Db, (C*)yA, dt, xa, stage, kind);
-}
-
-template <typename R, int DL>
-void adj_stage(const SlabPlanHost* h, int stage, const void* X, const void* Y, const void* row, double2* pbar,
-               void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st) {
-  if (h->np == 1) {
-    adj_launch<R, DL>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 3);
-    return;
-  }
-  adj_launch<R, DL>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 0);
-  for (int g = 1; g < h->np - 1; ++g) adj_launch<R, DL>(h, g, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 1);
-  adj_launch<R, DL>(h, h->np - 1, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 2);
-}
-
 template <typename R>
 const void* row_of(const void* tab, int row, int step, int j) {
   typedef typename CT<R>::T C;
@@ -899,48 +752,8 @@ int fwd_store_t(const SlabPlanHost* h, const void* tab, int step, const double2*
   return 3 * h->np;
 }
 
-template <typename R, int DL>
-int adj_step_t(const SlabPlanHost* h, const void* tab, int step, void* const Y[4], double2* pbar,
-               void*& KB, void*& KB2, void* Db, void* yA, double dt, XArgs xa, const double2* tab64,
-               const double* coef, const double2* ph, int sumd, int K, cudaStream_t st) {
-  const int row = h->pass[0].row;
-  auto set = [&](int j) {
-    xa.q = 3 * step + j;
-    xa.t = (double)(2 * step + j) * dt * 0.5;
-    xa.tabrow = tab64 + (size_t)xa.q * row;
-    xa.coef = coef + (size_t)xa.q * K;
-    xa.ph = ph + (size_t)xa.q * sumd;
-  };
-  set(2);
-  adj_stage<R, DL>(h, 3, KB, Y[3], row_of<R>(tab, row, step, 2), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
-  set(1);
-  adj_stage<R, DL>(h, 2, KB, Y[2], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
-  adj_stage<R, DL>(h, 1, KB, Y[1], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
-  set(0);
-  adj_stage<R, DL>(h, 0, KB, Y[0], row_of<R>(tab, row, step, 0), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
-  return 4 * h->np;
-}
-
 }  // namespace
 
-#define SLAB_DISPATCH(FN, ...)                                                              \
-  do {                                                                                      \
-    if (mixed) {                                                                            \
-      switch (h->DL) {                                                                      \
-        case 2: return FN<float, 2>(__VA_ARGS__);                                          \
-        case 3: return FN<float, 3>(__VA_ARGS__);                                          \
-        case 4: return FN<float, 4>(__VA_ARGS__);                                          \
-        default: return FN<float, 5>(__VA_ARGS__);                                         \
-      }                                                                                     \
-    } else {                                                                                \
-      switch (h->DL) {                                                                      \
-        case 2: return FN<double, 2>(__VA_ARGS__);                                         \
-        case 3: return FN<double, 3>(__VA_ARGS__);                                         \
-        case 4: return FN<double, 4>(__VA_ARGS__);                                         \
-        default: return FN<double, 5>(__VA_ARGS__);                                        \
-      }                                                                                     \
-    }                                                                                       \
-  } while (0)
 
 int slab_fwd_step(const SlabPlanHost* h, bool mixed, const void* tab, int step, const double2* pin,
                   double2* pout, void*& X, void*& Xo, void* Dacc, void* kA, double dt, cudaStream_t st) {
@@ -958,9 +771,3 @@ int slab_fwd_step_keep(const SlabPlanHost* h, bool mixed, const void* tab, int s
   SLAB_DISPATCH(fwd_step_keep_t, h, tab, step, pin, pout, Yk, Ynext0, Dacc, kA, dt, st);
 }
 
-int slab_adj_step(const SlabPlanHost* h, bool mixed, const void* tab, int step, void* const Y[4],
-                  double2* pbar, void*& KB, void*& KB2, void* Db, void* yA, double dt, XArgs xa,
-                  const double2* tab64, const double* coef, const double2* ph, int sumd, int K,
-                  cudaStream_t st) {
-  SLAB_DISPATCH(adj_step_t, h, tab, step, Y, pbar, KB, KB2, Db, yA, dt, xa, tab64, coef, ph, sumd, K, st);
-}

@@ -54,7 +54,12 @@ size_t slab_partial_elems(const SlabPlanHost* sp);
 // row's offsets, parity-odd rows compressed when slab_allpar; ph: the stage phase
 // rows exp(i E t), FP64, sumd per stage slot (3 per step).  Once bound, the
 // forward, replay and recompute passes use it (SG_SLAB_REAL=0 at the solve keeps
-// the complex rows); the adjoint passes keep the complex rows.
+// the complex rows).
 bool slab_real_shape_ok(const SlabPlanHost* sp);
 bool slab_allpar(const SlabPlanHost* sp);
-void slab_bind_real(SlabPlanHost* sp, const void* ztab, const double2* ph, int sumd);
+// zop: the drive operators' real matrices (K x DL x DL, packed like the rows), with
+// the drives of each 1-body slot (drv_list[drv_of_slot_start[u] .. [u + 1]]): the
+// adjoint passes of a pulse-only gradient then run in the real-operator form too
+// (nullptr keeps the complex-row adjoint).
+void slab_bind_real(SlabPlanHost* sp, const void* ztab, const double2* ph, int sumd, const void* zop,
+                    const int* drv_of_slot_start, const int* drv_list);

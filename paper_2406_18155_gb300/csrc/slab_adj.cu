@@ -1,0 +1,437 @@
+// Tiled RK4 adjoint stage kernels for HBM-resident slabs (see slab.h): the co-state
+// pull-back of one RK4 stage, one launch per pass, with the gradient's
+// cross-density terms of the pass's slots (Sec. 2.5, Eqs. 7-12).  The plan, the
+// layout and the forward passes are in slab.cu.
+#include "sg_internal.h"
+#include "kplan.h"
+#include "grad.cuh"
+#include "slab.h"
+#include "slab_dev.cuh"
+#include <cstdlib>
+#include <utility>
+
+namespace {
+
+// Adjoint pass: X = kbar_s tile, Y = y_s tile.  Applies A_s^dag = i H to kbar
+// (partial, or with the adjoint epilogue) with the register-blocked phases, and
+// accumulates the cross-densities of this pass's slots: warp w owns slots w and
+// w + 8, its lanes walk the blocks of the slot's phase, and the d x d partial sums
+// stay in registers across all tiles; one fixed-order reduction at the end.
+template <typename R, int DL, bool PARX>
+__global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 2 : 1)
+k_slab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename CT<R>::T* __restrict__ Y,
+           const typename CT<R>::T* __restrict__ tabrow, double2* __restrict__ pbar,
+           typename CT<R>::T* __restrict__ Xn, typename CT<R>::T* __restrict__ Db,
+           typename CT<R>::T* __restrict__ yA, double dt, XArgs xa, const int STAGE, const int KIND) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* xs = reinterpret_cast<C*>(smraw);
+  C* ys = xs + spad(sp.T);
+  C* ks = ys + spad(sp.T);
+  C* M = ks + spad(sp.T);
+  const int* __restrict__ off = sp.off;
+  load_common(sp, tabrow, M);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int NA = xd_n<DL, PARX>();
+  C acc[kSPW][NA];
+#pragma unroll
+  for (int s = 0; s < kSPW; ++s)
+#pragma unroll
+    for (int a = 0; a < NA; ++a) acc[s][a] = cmk<C>(0.0, 0.0);
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const R h = (R)dt;
+  const int nb = sp.T / (DL * DL);
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long base = tile_base(sp, tile);
+    load_tile<DL, 8>(sp, X, base, off, xs);
+    load_tile<DL, 8>(sp, Y, base, off, ys);
+    __syncthreads();
+    pass_apply<DL>(sp, M, xs, ks);
+    constexpr int EB = 4;
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * EB) {
+      long long g[EB];
+      C yb[EB], pa[EB], dd[EB];
+      double2 pbv[EB];
+      bool ok[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int t = t0 + j * kST;
+        ok[j] = t < sp.T;
+        g[j] = ok[j] ? base + __ldg(off + t) : base;
+        const C a = ok[j] ? ks[spos<DL>(t)] : cmk<C>(0.0, 0.0);
+        yb[j] = cmk<C>(-a.y, a.x);                  // i H kbar
+        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? yA[g[j]] : cmk<C>(0.0, 0.0);
+        pbv[j] = (KIND >= 2) && ok[j] ? pbar[g[j]] : make_double2(0.0, 0.0);
+        dd[j] = (KIND >= 2) && ok[j] && STAGE < 3 ? Db[g[j]] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        if (!ok[j]) continue;
+        C y = yb[j];
+        if (KIND == 0) { yA[g[j]] = y; continue; }
+        if (KIND == 1) { yA[g[j]] = cmk<C>(pa[j].x + y.x, pa[j].y + y.y); continue; }
+        if (KIND == 2) y = cmk<C>(pa[j].x + y.x, pa[j].y + y.y);
+        const C pr = to_c(pbv[j], R(0));
+        const C d = dd[j];
+        if (STAGE == 3) {
+          Db[g[j]] = y;
+          Xn[g[j]] = cmk<C>(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
+        } else if (STAGE == 2) {
+          Db[g[j]] = cmk<C>(d.x + y.x, d.y + y.y);
+          Xn[g[j]] = cmk<C>(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
+        } else if (STAGE == 1) {
+          Db[g[j]] = cmk<C>(d.x + y.x, d.y + y.y);
+          Xn[g[j]] = cmk<C>(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
+        } else {
+          double2 pn = make_double2(pbv[j].x + (double)(d.x + y.x), pbv[j].y + (double)(d.y + y.y));
+          pbar[g[j]] = pn;
+          C q = to_c(pn, R(0));
+          Xn[g[j]] = cmk<C>(h / 6 * q.x, h / 6 * q.y);
+        }
+      }
+    }
+    // cross-densities of this warp's slots over the tile
+#pragma unroll
+    for (int s = 0; s < kSPW; ++s) {
+      const int slot = warp + s * (kST / 32);
+      if (slot >= sp.nx) continue;                  // warp-uniform
+      const Phase& P = sp.ph[sp.x_ph[slot]];
+      const int type = sp.x_type[slot];
+      if (type >= 2 && !xa.ham) continue;           // coupling slot, not wanted
+      for (int b = lane; b < nb; b += 32)
+        xd_slot<DL, PARX>(P, type, M, xs, ys, blk_pos<DL>(P, b), acc[s]);
+    }
+    __syncthreads();
+  }
+  // warp reductions -> block partials [block][slot][DL*DL]
+#pragma unroll
+  for (int s = 0; s < kSPW; ++s) {
+    const int slot = warp + s * (kST / 32);
+    if (slot >= sp.nx) continue;                    // warp-uniform
+    if (sp.x_type[slot] >= 2 && !xa.ham) continue;
+#pragma unroll
+    for (int a = 0; a < DL; ++a)
+#pragma unroll
+      for (int b = 0; b < DL; ++b) {
+        double vr = 0.0, vi = 0.0;
+        if (!PARX || ((a + b) & 1)) {
+          vr = acc[s][xd_i<DL, PARX>(a, b)].x;
+          vi = acc[s][xd_i<DL, PARX>(a, b)].y;
+          for (int o = 16; o > 0; o >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, o);
+            vi += __shfl_xor_sync(0xffffffffu, vi, o);
+          }
+        }
+        if (lane == 0) xa.partial[((size_t)blockIdx.x * kMaxX + slot) * DL * DL + a * DL + b] = make_double2(vr, vi);
+      }
+  }
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(xa.ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  double2* Wt = reinterpret_cast<double2*>(smraw);   // nx * DL * DL
+  for (int i = threadIdx.x; i < sp.nx * DL * DL; i += blockDim.x) {
+    const int slot = i / (DL * DL), ab = i % (DL * DL);
+    double sr = 0.0, si = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+      double2 v = __ldcg(xa.partial + ((size_t)b * kMaxX + slot) * DL * DL + ab);
+      sr += v.x;
+      si += v.y;
+    }
+    Wt[i] = make_double2(si, -sr);                     // W = -i C
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *xa.ticket = 0u;
+  if (threadIdx.x < sp.nx && (xa.ham || sp.x_type[threadIdx.x] < 2))
+    contract_slot(xa, sp.x_gslot[threadIdx.x], Wt + threadIdx.x * DL * DL, DL);
+}
+
+
+
+// Drive term of one block of the real-operator pulse-gradient adjoint:
+//   sum over the block of Im( conj(k~_a) (O y~)_a ),
+// O the drive's real operator acting on the block digit of the drive's mode (the
+// first digit for type 0, the second for type 1).  Entries are streamed one line of
+// the other digit at a time.
+template <int DL, bool PAR, typename R>
+__device__ __forceinline__ R zdrive_block(const Phase& P, int type, const typename ZM<R>::T* __restrict__ O,
+                                          const typename CT<R>::T* __restrict__ xs,
+                                          const typename CT<R>::T* __restrict__ ys, int pb) {
+  typedef typename CT<R>::T C;
+  typedef typename ZM<R>::T Z;
+  constexpr int NZ = znz<DL, PAR>();
+  const int sa = type == 0 ? P.psa : P.psb;      // the drive's digit
+  const int sz = type == 0 ? P.psb : P.psa;      // the block's other digit
+  Z o[DL][NZ];
+#pragma unroll
+  for (int a = 0; a < DL; ++a) zrow_ld<NZ>(O + a * DL, o[a]);
+  R g = R(0);
+#pragma unroll
+  for (int z = 0; z < DL; ++z) {
+    C yv[DL], kv[DL];
+#pragma unroll
+    for (int a = 0; a < DL; ++a) {
+      yv[a] = ys[pb + a * sa + z * sz];
+      kv[a] = xs[pb + a * sa + z * sz];
+    }
+#pragma unroll
+    for (int a = 0; a < DL; ++a) {
+      C v = cmk<C>(0.0, 0.0);
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) v = zfma(o[a][k], yv[zcol<PAR>(a, k)], v);
+      g = fma(kv[a].x, v.y, g);
+      g = fma(-kv[a].y, v.x, g);
+    }
+  }
+  return g;
+}
+
+// Adjoint stage pass with real operators, for the pulse gradient (no Hamiltonian-
+// parameter gradient).  The kbar_s and y_s tiles are loaded rotated into the
+// real-operator basis, k~ = conj(P_G) kbar and y~ = conj(P_G) y_s; the phases apply
+// H_r to k~ and the epilogue rotates back, i H kbar = i P_G (H_r k~), before the
+// adjoint update of k_slab_adj (same KIND / STAGE semantics).  Drive k acts as
+// f_k(t) P O_k P^dag with O_k real in the truncated eigenbasis, so its term of
+// dF/df_k at this stage, Re sum_ab (-i C_ab) (O_k)_ab e^{i(E_a - E_b) t} with C the
+// cross-density of kbar and y_s on the drive's mode (Sec. 2.5), reduces to
+//   Im sum <k~, O_k y~>   (the frame phases cancel),
+// accumulated by every thread over its blocks of the slot's phase in registers; the
+// block sums go to gpart and the last block adds their fixed-order total to
+// gFq[k], the stage's row of dF/df.
+template <typename R, int DL, bool PAR>
+__global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 2 : 1)
+k_zslab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename CT<R>::T* __restrict__ Y,
+            const typename ZM<R>::T* __restrict__ zrow, const typename ZM<R>::T* __restrict__ zop,
+            const double2* __restrict__ phrow, double2* __restrict__ pbar, typename CT<R>::T* __restrict__ Xn,
+            typename CT<R>::T* __restrict__ Db, typename CT<R>::T* __restrict__ yA, double dt,
+            double* __restrict__ gpart, unsigned* __restrict__ ticket, double* __restrict__ gFq, const int STAGE,
+            const int KIND) {
+  typedef typename CT<R>::T C;
+  typedef typename ZM<R>::T Z;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ double gred[kST / 32][kMaxDrv];
+  __shared__ bool last;
+  C* xs = reinterpret_cast<C*>(smraw);
+  C* ys = xs + spad(sp.T);
+  C* ks = ys + spad(sp.T);
+  C* plo = ks + spad(sp.T);                       // 256
+  C* phi = plo + 256;                             // T / 256
+  Z* M = reinterpret_cast<Z*>(smraw + zrow_smem_off(sp.T, sizeof(C), 3));
+  Z* Op = M + ((sp.row + 1) & ~1);                // 16-byte aligned rows
+  const int* __restrict__ off = sp.off;
+  for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = zrow[i];
+  for (int i = threadIdx.x; i < sp.nd * DL * DL; i += blockDim.x)
+    Op[i] = zop[(size_t)sp.d_k[i / (DL * DL)] * DL * DL + i % (DL * DL)];
+  zphase_tables<DL>(sp, phrow, plo, phi);
+  __syncthreads();
+  const int L = sp.T < 256 ? sp.T : 256;
+  const C pl = threadIdx.x < L ? plo[threadIdx.x] : cmk<C>(1.0, 0.0);
+  R g[kMaxDrv];
+#pragma unroll
+  for (int j = 0; j < kMaxDrv; ++j) g[j] = R(0);
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const R h = (R)dt;
+  const int nb = sp.T / (DL * DL);
+  constexpr int NB = 4;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long base = tile_base(sp, tile);
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * NB) {
+      C vx[NB], vy[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + j * kST;
+        const long long o = base + (t < sp.T ? __ldg(off + t) : 0);
+        vx[j] = t < sp.T ? X[o] : cmk<C>(0.0, 0.0);
+        vy[j] = t < sp.T ? Y[o] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + j * kST;
+        if (t < sp.T) {
+          const C f = zcmul(pl, phi[t / 256]);
+          xs[spos<DL>(t)] = zcmulc(f, vx[j]);
+          ys[spos<DL>(t)] = zcmulc(f, vy[j]);
+        }
+      }
+    }
+    __syncthreads();
+    zpass_apply<DL, PAR, R>(sp, M, xs, ks, kST);
+    constexpr int EB = 4;
+    for (int t0 = threadIdx.x; t0 < sp.T; t0 += kST * EB) {
+      long long gi[EB];
+      C yb[EB], pa[EB], dd[EB];
+      double2 pbv[EB];
+      bool ok[EB];
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        const int t = t0 + j * kST;
+        ok[j] = t < sp.T;
+        gi[j] = ok[j] ? base + __ldg(off + t) : base;
+        const C a = ok[j] ? zcmul(zcmul(pl, phi[t / 256]), ks[spos<DL>(t)]) : cmk<C>(0.0, 0.0);
+        yb[j] = cmk<C>(-a.y, a.x);                  // i H kbar
+        pa[j] = (KIND == 1 || KIND == 2) && ok[j] ? yA[gi[j]] : cmk<C>(0.0, 0.0);
+        pbv[j] = (KIND >= 2) && ok[j] ? pbar[gi[j]] : make_double2(0.0, 0.0);
+        dd[j] = (KIND >= 2) && ok[j] && STAGE < 3 ? Db[gi[j]] : cmk<C>(0.0, 0.0);
+      }
+#pragma unroll
+      for (int j = 0; j < EB; ++j) {
+        if (!ok[j]) continue;
+        C y = yb[j];
+        if (KIND == 0) { yA[gi[j]] = y; continue; }
+        if (KIND == 1) { yA[gi[j]] = cmk<C>(pa[j].x + y.x, pa[j].y + y.y); continue; }
+        if (KIND == 2) y = cmk<C>(pa[j].x + y.x, pa[j].y + y.y);
+        const C pr = to_c(pbv[j], R(0));
+        const C d = dd[j];
+        if (STAGE == 3) {
+          Db[gi[j]] = y;
+          Xn[gi[j]] = cmk<C>(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
+        } else if (STAGE == 2) {
+          Db[gi[j]] = cmk<C>(d.x + y.x, d.y + y.y);
+          Xn[gi[j]] = cmk<C>(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
+        } else if (STAGE == 1) {
+          Db[gi[j]] = cmk<C>(d.x + y.x, d.y + y.y);
+          Xn[gi[j]] = cmk<C>(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
+        } else {
+          double2 pn = make_double2(pbv[j].x + (double)(d.x + y.x), pbv[j].y + (double)(d.y + y.y));
+          pbar[gi[j]] = pn;
+          C q = to_c(pn, R(0));
+          Xn[gi[j]] = cmk<C>(h / 6 * q.x, h / 6 * q.y);
+        }
+      }
+    }
+    // drive terms of this pass over the tile
+#pragma unroll
+    for (int j = 0; j < kMaxDrv; ++j) {
+      if (j < sp.nd) {
+        const Phase& P = sp.ph[sp.d_ph[j]];
+        const int type = sp.d_type[j];
+        for (int b = threadIdx.x; b < nb; b += kST)
+          g[j] += zdrive_block<DL, PAR, R>(P, type, Op + j * DL * DL, xs, ys, blk_pos<DL>(P, b));
+      }
+    }
+    __syncthreads();
+  }
+  // block sums (FP64, fixed order) -> gpart[block][j]; the last block adds the totals
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < kMaxDrv; ++j) {
+    if (j < sp.nd) {
+      double v = (double)g[j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) gred[warp][j] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < sp.nd) {
+    double v = 0.0;
+    for (int w = 0; w < kST / 32; ++w) v += gred[w][threadIdx.x];
+    gpart[(size_t)blockIdx.x * kMaxDrv + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (threadIdx.x < sp.nd) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(gpart + (size_t)b * kMaxDrv + threadIdx.x);
+    gFq[sp.d_k[threadIdx.x]] += v;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
+}
+
+}  // namespace
+
+namespace {
+
+// The real-operator pulse-gradient adjoint runs unless SG_SLAB_ZADJ=0 (a test knob
+// that keeps the complex-row pass).
+bool zadj_on() {
+  const char* e = std::getenv("SG_SLAB_ZADJ");
+  return !(e && e[0] == '0');
+}
+
+template <typename R, int DL>
+void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, const void* row,
+                double2* pbar, void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st,
+                int stage, int kind) {
+  typedef typename CT<R>::T C;
+  if constexpr (DL == 2 || DL == 4) {
+    // parity-odd plans only (every operator couples levels of opposite parity: the
+    // fluxonium and transmon n and phi at n_g = 0, phi_ext = pi)
+    if (h->ztab && h->zadj && h->allpar && !xa.ham && zadj_on()) {
+      typedef typename ZM<R>::T Z;
+      auto zk = k_zslab_adj<R, DL, true>;
+      static const bool zattr = [] {
+        cudaFuncSetAttribute(k_zslab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+        return true;
+      }();
+      (void)zattr;
+      zk<<<h->grid_adj, kST, h->sm_zadj[g], st>>>(
+          h->pass[g], (const C*)X, (const C*)Y, (const Z*)h->ztab + (size_t)xa.q * h->pass[g].row, (const Z*)h->zop,
+          h->zph + (size_t)xa.q * h->zsumd, pbar, (C*)Xn, (C*)Db, (C*)yA, dt, reinterpret_cast<double*>(xa.partial),
+          xa.ticket, xa.acc.gF + (size_t)xa.q * xa.K, stage, kind);
+      return;
+    }
+  }
+  auto kern = h->allpar ? k_slab_adj<R, DL, true> : k_slab_adj<R, DL, false>;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_slab_adj<R, DL, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+    cudaFuncSetAttribute(k_slab_adj<R, DL, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+    return true;
+  }();
+  (void)attr;
+  kern<<<h->grid_adj, kST, h->sm_adj[g], st>>>(h->pass[g], (const C*)X, (const C*)Y, (const C*)row, pbar,
+                                                 (C*)Xn, (C*)Db, (C*)yA, dt, xa, stage, kind);
+}
+
+template <typename R, int DL>
+void adj_stage(const SlabPlanHost* h, int stage, const void* X, const void* Y, const void* row, double2* pbar,
+               void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st) {
+  if (h->np == 1) {
+    adj_launch<R, DL>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 3);
+    return;
+  }
+  adj_launch<R, DL>(h, 0, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 0);
+  for (int g = 1; g < h->np - 1; ++g) adj_launch<R, DL>(h, g, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 1);
+  adj_launch<R, DL>(h, h->np - 1, X, Y, row, pbar, Xn, Db, yA, dt, xa, st, stage, 2);
+}
+
+template <typename R>
+const void* row_of(const void* tab, int row, int step, int j) {
+  typedef typename CT<R>::T C;
+  return static_cast<const C*>(tab) + ((size_t)3 * step + j) * row;
+}
+
+template <typename R, int DL>
+int adj_step_t(const SlabPlanHost* h, const void* tab, int step, void* const Y[4], double2* pbar,
+               void*& KB, void*& KB2, void* Db, void* yA, double dt, XArgs xa, const double2* tab64,
+               const double* coef, const double2* ph, int sumd, int K, cudaStream_t st) {
+  const int row = h->pass[0].row;
+  auto set = [&](int j) {
+    xa.q = 3 * step + j;
+    xa.t = (double)(2 * step + j) * dt * 0.5;
+    xa.tabrow = tab64 + (size_t)xa.q * row;
+    xa.coef = coef + (size_t)xa.q * K;
+    xa.ph = ph + (size_t)xa.q * sumd;
+  };
+  set(2);
+  adj_stage<R, DL>(h, 3, KB, Y[3], row_of<R>(tab, row, step, 2), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  set(1);
+  adj_stage<R, DL>(h, 2, KB, Y[2], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  adj_stage<R, DL>(h, 1, KB, Y[1], row_of<R>(tab, row, step, 1), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  set(0);
+  adj_stage<R, DL>(h, 0, KB, Y[0], row_of<R>(tab, row, step, 0), pbar, KB2, Db, yA, dt, xa, st); std::swap(KB, KB2);
+  return 4 * h->np;
+}
+
+}  // namespace
+
+int slab_adj_step(const SlabPlanHost* h, bool mixed, const void* tab, int step, void* const Y[4],
+                  double2* pbar, void*& KB, void*& KB2, void* Db, void* yA, double dt, XArgs xa,
+                  const double2* tab64, const double* coef, const double2* ph, int sumd, int K,
+                  cudaStream_t st) {
+  SLAB_DISPATCH(adj_step_t, h, tab, step, Y, pbar, KB, KB2, Db, yA, dt, xa, tab64, coef, ph, sumd, K, st);
+}

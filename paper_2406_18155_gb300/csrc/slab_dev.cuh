@@ -14,6 +14,10 @@ constexpr int kMaxPass = 4;
 constexpr int kSPW = 2;           // cross-density slots per warp
 constexpr int kMaxX = kSPW * (kST / 32);
 constexpr int kMaxPhase = 12;
+constexpr int kMaxDrv = 8;
+// Dynamic shared memory a tiled pass may take: the 227 KB opt-in limit of a block
+// less 1 KB for the kernels' static shared variables.
+constexpr size_t kSlabSmemMax = 226 * 1024;        // drives per pass of the real-operator pulse-gradient adjoint
 
 // One phase of a pass: every thread owns d x d blocks over two tile digits
 // (ka, kb) and applies the terms living on them in registers: the edge
@@ -51,6 +55,11 @@ struct SlabPass {
   Phase ph[kMaxPhase];
   const int* off;                 // device tile offsets [T]
   int tphoff[SG_MAXQ];            // tile digit k: offset of its mode's levels in a stage's phase row
+  // drives whose 1-body slot lies in this pass (real-operator pulse-gradient adjoint):
+  // the phase whose blocks carry the slot's digit, on its first (0) or second (1)
+  // digit, and the global drive index
+  int nd;
+  int d_ph[kMaxDrv], d_type[kMaxDrv], d_k[kMaxDrv];
 };
 
 // Padded shared-memory position of tile entry t: one pad element per 16 and per
@@ -614,6 +623,11 @@ struct SlabPlanHost {
   int grid_zfwd = 0;
   size_t sm_zfwd[kMaxPass] = {0};
   size_t sm_zws[kMaxPass] = {0};   // warp-specialised FP32 pass (0: not usable for this pass)
+  // real-operator pulse-gradient adjoint (bound by slab_bind_real when every pass has
+  // at most kMaxDrv drives): the drive operators' real matrices, K x DL x DL
+  const void* zop = nullptr;
+  bool zadj = false;
+  size_t sm_zadj[kMaxPass] = {0};
 };
 
 // Byte offset of the real-operator row in the shared memory of k_zslab_fwd: after
@@ -623,3 +637,23 @@ __host__ __device__ inline size_t zrow_smem_off(int T, size_t csz, int ntile = 2
   const int nhi = T > 256 ? T / 256 : 1;
   return (((size_t)ntile * spad(T) + 256 + nhi) * csz + 15) & ~(size_t)15;
 }
+
+// Instantiates FN<R, DL> for the plan's precision and level count.
+#define SLAB_DISPATCH(FN, ...)                                                              \
+  do {                                                                                      \
+    if (mixed) {                                                                            \
+      switch (h->DL) {                                                                      \
+        case 2: return FN<float, 2>(__VA_ARGS__);                                          \
+        case 3: return FN<float, 3>(__VA_ARGS__);                                          \
+        case 4: return FN<float, 4>(__VA_ARGS__);                                          \
+        default: return FN<float, 5>(__VA_ARGS__);                                         \
+      }                                                                                     \
+    } else {                                                                                \
+      switch (h->DL) {                                                                      \
+        case 2: return FN<double, 2>(__VA_ARGS__);                                         \
+        case 3: return FN<double, 3>(__VA_ARGS__);                                         \
+        case 4: return FN<double, 4>(__VA_ARGS__);                                         \
+        default: return FN<double, 5>(__VA_ARGS__);                                        \
+      }                                                                                     \
+    }                                                                                       \
+  } while (0)

@@ -1,7 +1,8 @@
-"""GPU parity of the tiled kernels' real-operator forward passes (every local
-operator real in the truncated eigenbasis up to the interaction-frame phases,
-which are applied once per tile entry) against the FP64 oracle and against the
-complex-row passes, through the C ABI.
+"""GPU parity of the tiled kernels' real-operator passes (every local operator real
+in the truncated eigenbasis up to the interaction-frame phases, which are applied
+once per tile entry) against the FP64 oracle and against the complex-row passes,
+through the C ABI: the forward passes, and the adjoint passes of the pulse-parameter
+gradient.
 
 Shapes: level counts 4 and 2, one-pass and multi-pass plans (a small tile budget,
 and the two-group ring of 4^7 states), parity-odd plans (compressed rows) and the
@@ -99,6 +100,41 @@ def test_real_forward_gradient_matches_oracle(sgctx, real_slab, name):
                                       precision="mixed", ckpt=4)
     assert abs(F32[k] - Fr) < 1e-5
     assert np.max(np.abs(np.concatenate([gp32, gh32]) - gr)) <= 1e-3 * np.max(np.abs(gr))
+
+
+@pytest.mark.parametrize("name", ["ring4_l4_multipass", "chain6_l2_multipass", "chain5_l4_onepass"])
+def test_real_pulse_gradient_adjoint_matches_oracle(sgctx, real_slab, name):
+    # pulse-parameter gradient only: the adjoint passes run in the real-operator form
+    # too, each drive's term contracted with the rotated co-state and state; against
+    # the oracle's adjoint and against the complex-row adjoint (SG_SLAB_ZADJ=0)
+    make, tmax = CASES[name]
+    if tmax:
+        real_slab.setenv("SG_SLAB_TMAX", str(tmax))
+    wl = make()
+    wl["fid_kind"] = "state"
+    s = _system(sgctx, wl)
+    Fr, gr, _ = adjoint_gradient(wl)
+    gr = gr[:s.param_counts()[0]]
+    scale = np.max(np.abs(gr))
+    out = {}
+    for zadj in ("1", "0"):
+        real_slab.setenv("SG_SLAB_ZADJ", zadj)
+        for prec in ("fp64", "mixed"):
+            F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                        precision=prec, ckpt=4, ham=False)
+            assert gh is None
+            out[zadj, prec] = (F, gp)
+    F, gp = out["1", "fp64"]
+    assert abs(F[1] - Fr) < 1e-10
+    assert np.max(np.abs(gp - gr)) <= 1e-8 * scale
+    F32, gp32 = out["1", "mixed"]
+    assert abs(F32[1] - Fr) < 1e-5
+    assert np.max(np.abs(gp32 - gr)) <= 1e-3 * scale
+    # the same gradient as the complex-row adjoint up to rounding (a zero difference
+    # would mean the real-operator adjoint never ran)
+    d64 = np.max(np.abs(gp - out["0", "fp64"][1]))
+    assert 0 < d64 <= 1e-12 * scale
+    assert np.max(np.abs(gp32 - out["0", "mixed"][1])) <= 1e-4 * scale
 
 
 def test_real_two_pass_ring7_against_matrix_free_oracle(sgctx, real_slab):
