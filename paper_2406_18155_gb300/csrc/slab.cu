@@ -12,6 +12,7 @@
 #include "grad.cuh"
 #include "slab.h"
 #include "slab_dev.cuh"
+#include "slab_lean.cuh"
 #include <algorithm>
 #include <cstdlib>
 #include <set>
@@ -178,6 +179,112 @@ k_zslab_fwd(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename
           psi_out[g[j]] = pn;
           Xn[g[j]] = to_c(pn, R(0));
         }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Epilogue of the lean forward pass (slab_lean.cuh) for one pass kind and stage:
+// thread tid's entries t = tid + 256 j, their H y rotated back to the frame basis,
+// then the partial sum or the RK4 update of k_slab_fwd.
+template <int KIND, int STAGE, bool STORE>
+__device__ __forceinline__ void lepi_fwd(const float2* __restrict__ ks, const float2* __restrict__ phi, float2 pl,
+                                         int s0, const int* __restrict__ ohi, long long bl,
+                                         const double2* __restrict__ psi_in, double2* __restrict__ psi_out,
+                                         float2* __restrict__ Xn, float2* __restrict__ Dacc,
+                                         float2* __restrict__ kA, float h) {
+  constexpr int EB = 4;
+#pragma unroll
+  for (int j0 = 0; j0 < lean::LJ; j0 += EB) {
+    long long g[EB];
+    float2 k[EB], pa[EB], dd[EB];
+    double2 ps[EB];
+#pragma unroll
+    for (int jj = 0; jj < EB; ++jj) {
+      const int j = j0 + jj;
+      g[jj] = bl + ohi[j];
+      const float2 a = zcmul(zcmul(pl, phi[j]), ks[s0 + 273 * j]);
+      k[jj] = make_float2(a.y, -a.x);                 // -i H y
+      if (KIND == 1 || KIND == 2) pa[jj] = kA[g[jj]];
+      if (KIND >= 2) ps[jj] = psi_in[g[jj]];
+      if (KIND >= 2 && !STORE && STAGE > 0) dd[jj] = Dacc[g[jj]];
+    }
+#pragma unroll
+    for (int jj = 0; jj < EB; ++jj) {
+      float2 kk = k[jj];
+      if (KIND == 0) { kA[g[jj]] = kk; continue; }
+      if (KIND == 1) { kA[g[jj]] = make_float2(pa[jj].x + kk.x, pa[jj].y + kk.y); continue; }
+      if (KIND == 2) kk = make_float2(pa[jj].x + kk.x, pa[jj].y + kk.y);
+      const float2 pr = make_float2((float)ps[jj].x, (float)ps[jj].y);
+      if (STAGE == 0) {
+        if (!STORE) Dacc[g[jj]] = make_float2(h / 6 * kk.x, h / 6 * kk.y);
+        Xn[g[jj]] = make_float2(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+      } else if (STAGE == 1) {
+        if (!STORE) Dacc[g[jj]] = make_float2(dd[jj].x + h / 3 * kk.x, dd[jj].y + h / 3 * kk.y);
+        Xn[g[jj]] = make_float2(pr.x + h / 2 * kk.x, pr.y + h / 2 * kk.y);
+      } else if (STAGE == 2) {
+        if (!STORE) Dacc[g[jj]] = make_float2(dd[jj].x + h / 3 * kk.x, dd[jj].y + h / 3 * kk.y);
+        Xn[g[jj]] = make_float2(pr.x + h * kk.x, pr.y + h * kk.y);
+      } else {
+        const float incx = dd[jj].x + h / 6 * kk.x, incy = dd[jj].y + h / 6 * kk.y;
+        const double2 pn = make_double2(ps[jj].x + (double)incx, ps[jj].y + (double)incy);
+        psi_out[g[jj]] = pn;
+        Xn[g[jj]] = make_float2((float)pn.x, (float)pn.y);
+      }
+    }
+  }
+}
+
+// Lean forward stage pass: the operation of k_zslab_fwd<float, 4, true> on 4096-entry
+// tiles, with the index work of slab_lean.cuh.
+__global__ void __launch_bounds__(kST, 2)
+k_lean_fwd(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__ zrow,
+           const double2* __restrict__ phrow, const double2* __restrict__ psi_in, double2* psi_out,
+           float2* __restrict__ Xn, float2* __restrict__ Dacc, float2* __restrict__ kA, double dt,
+           const int STAGE, const bool STORE, const int KIND) {
+  using namespace lean;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ float2 phi[LJ];
+  __shared__ int ohi[LJ];
+  __shared__ int lph[kMaxPhase][kLph];
+  float2* ys = reinterpret_cast<float2*>(smraw);
+  float2* ks = ys + spad(LT);
+  float2* M = reinterpret_cast<float2*>(smraw + ((2 * spad(LT) * sizeof(float2) + 15) & ~(size_t)15));
+  for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = zrow[i];
+  float2 pl;
+  int olo;
+  lsetup(sp, phrow, phi, ohi, pl, olo);
+  lphases_to_smem(sp, lph);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int s0 = tid + (tid >> 4);                  // spos(tid); spos(tid + 256 j) = s0 + 273 j
+  const int nph = sp.nph;
+  const float h = (float)dt;
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long bl = tile_base(sp, tile) + olo;
+#pragma unroll
+    for (int j0 = 0; j0 < LJ; j0 += 8) {
+      float2 v[8];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) v[jj] = X[bl + ohi[j0 + jj]];
+#pragma unroll
+      for (int jj = 0; jj < 8; ++jj) ys[s0 + 273 * (j0 + jj)] = zcmulc(zcmul(pl, phi[j0 + jj]), v[jj]);
+    }
+    __syncthreads();
+    lpass(nph, lph, M, ys, ks, tid);
+    if (KIND == 0) lepi_fwd<0, 0, false>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h);
+    else if (KIND == 1) lepi_fwd<1, 0, false>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h);
+    else {
+      switch ((KIND == 3 ? 8 : 0) + 2 * STAGE + (STORE ? 1 : 0)) {
+#define SG_LEPI(K, S, ST) case (K == 3 ? 8 : 0) + 2 * S + ST: \
+        lepi_fwd<K, S, ST>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h); break;
+        SG_LEPI(2, 0, 0) SG_LEPI(2, 0, 1) SG_LEPI(2, 1, 0) SG_LEPI(2, 1, 1) SG_LEPI(2, 2, 0) SG_LEPI(2, 2, 1)
+        SG_LEPI(2, 3, 0) SG_LEPI(3, 0, 0) SG_LEPI(3, 0, 1) SG_LEPI(3, 1, 0) SG_LEPI(3, 1, 1) SG_LEPI(3, 2, 0)
+        SG_LEPI(3, 2, 1) SG_LEPI(3, 3, 0)
+#undef SG_LEPI
+        default: break;
       }
     }
     __syncthreads();
@@ -573,6 +680,12 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
   h->allpar = true;
   for (int g = 0; g < np; ++g)
     for (int q = 0; q < h->pass[g].nph; ++q) h->allpar = h->allpar && h->pass[g].ph[q].allpar;
+  h->sm_lean = ((2 * spad(lean::LT) * sizeof(float2) + 15) & ~(size_t)15) + (size_t)p.row * sizeof(float2);
+  h->sm_lean_adj = ((3 * spad(lean::LT) * sizeof(float2) + 15) & ~(size_t)15) +
+                   (size_t)(((p.row + 1) & ~1) + kMaxDrv * 16) * sizeof(float2);
+  for (int g = 0; g < np; ++g)
+    h->lean[g] = mixed && DL == 4 && h->allpar && h->pass[g].T == lean::LT && h->pass[g].ng == 6 &&
+                 h->pass[g].nph <= kMaxPhase && h->sm_lean_adj <= kLeanSmemMax;
   long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   h->grid_fwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 3 : 1));
   h->grid_zfwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
@@ -644,11 +757,32 @@ bool zws_off() {
   return !(e && e[0] == '1');
 }
 
+// The lean FP32 passes run unless SG_SLAB_LEAN=0 (a test knob that keeps the
+// general real-operator passes).
+bool lean_on() {
+  const char* e = std::getenv("SG_SLAB_LEAN");
+  return !(e && e[0] == '0');
+}
+
 template <typename R, int DL>
 void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, const double2* pin,
                 double2* pout, void* Xn, void* Dacc, void* kA, double dt, cudaStream_t st, int stage,
                 bool store, int kind, int q) {
   typedef typename CT<R>::T C;
+  if constexpr (sizeof(R) == 4 && DL == 4) {
+    if (h->ztab && h->lean[g] && zws_off() && lean_on()) {
+      static const bool lattr = [] {
+        cudaFuncSetAttribute(k_lean_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeanSmemMax);
+        return true;
+      }();
+      (void)lattr;
+      k_lean_fwd<<<h->grid_zfwd, kST, h->sm_lean, st>>>(h->pass[g], (const float2*)X,
+                                                        (const float2*)h->ztab + (size_t)q * h->pass[g].row,
+                                                        h->zph + (size_t)q * h->zsumd, pin, pout, (float2*)Xn,
+                                                        (float2*)Dacc, (float2*)kA, dt, stage, store, kind);
+      return;
+    }
+  }
   if constexpr (DL == 2 || DL == 4) {
     if (h->ztab) {
       typedef typename ZM<R>::T Z;

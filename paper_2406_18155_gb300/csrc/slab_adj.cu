@@ -7,6 +7,7 @@
 #include "grad.cuh"
 #include "slab.h"
 #include "slab_dev.cuh"
+#include "slab_lean.cuh"
 #include <cstdlib>
 #include <utility>
 
@@ -342,12 +343,170 @@ k_zslab_adj(SlabPass sp, const typename CT<R>::T* __restrict__ X, const typename
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
+// Epilogue of the lean adjoint pass for one pass kind and stage (the update of
+// k_slab_adj on thread tid's entries t = tid + 256 j, i H kbar rotated back first).
+template <int KIND, int STAGE>
+__device__ __forceinline__ void lepi_adj(const float2* __restrict__ ks, const float2* __restrict__ phi, float2 pl,
+                                         int s0, const int* __restrict__ ohi, long long bl,
+                                         double2* __restrict__ pbar, float2* __restrict__ Xn,
+                                         float2* __restrict__ Db, float2* __restrict__ yA, float h) {
+  constexpr int EB = 4;
+#pragma unroll
+  for (int j0 = 0; j0 < lean::LJ; j0 += EB) {
+    long long g[EB];
+    float2 yb[EB], pa[EB], dd[EB];
+    double2 pbv[EB];
+#pragma unroll
+    for (int jj = 0; jj < EB; ++jj) {
+      const int j = j0 + jj;
+      g[jj] = bl + ohi[j];
+      const float2 a = zcmul(zcmul(pl, phi[j]), ks[s0 + 273 * j]);
+      yb[jj] = make_float2(-a.y, a.x);                 // i H kbar
+      if (KIND == 1 || KIND == 2) pa[jj] = yA[g[jj]];
+      if (KIND >= 2) pbv[jj] = pbar[g[jj]];
+      if (KIND >= 2 && STAGE < 3) dd[jj] = Db[g[jj]];
+    }
+#pragma unroll
+    for (int jj = 0; jj < EB; ++jj) {
+      float2 y = yb[jj];
+      if (KIND == 0) { yA[g[jj]] = y; continue; }
+      if (KIND == 1) { yA[g[jj]] = make_float2(pa[jj].x + y.x, pa[jj].y + y.y); continue; }
+      if (KIND == 2) y = make_float2(pa[jj].x + y.x, pa[jj].y + y.y);
+      const float2 pr = make_float2((float)pbv[jj].x, (float)pbv[jj].y);
+      if (STAGE == 3) {
+        Db[g[jj]] = y;
+        Xn[g[jj]] = make_float2(h / 3 * pr.x + h * y.x, h / 3 * pr.y + h * y.y);
+      } else if (STAGE == 2) {
+        Db[g[jj]] = make_float2(dd[jj].x + y.x, dd[jj].y + y.y);
+        Xn[g[jj]] = make_float2(h / 3 * pr.x + h / 2 * y.x, h / 3 * pr.y + h / 2 * y.y);
+      } else if (STAGE == 1) {
+        Db[g[jj]] = make_float2(dd[jj].x + y.x, dd[jj].y + y.y);
+        Xn[g[jj]] = make_float2(h / 6 * pr.x + h / 2 * y.x, h / 6 * pr.y + h / 2 * y.y);
+      } else {
+        const double2 pn = make_double2(pbv[jj].x + (double)(dd[jj].x + y.x), pbv[jj].y + (double)(dd[jj].y + y.y));
+        pbar[g[jj]] = pn;
+        const float2 q = make_float2((float)pn.x, (float)pn.y);
+        Xn[g[jj]] = make_float2(h / 6 * q.x, h / 6 * q.y);
+      }
+    }
+  }
+}
+
+// Lean adjoint stage pass: the operation of k_zslab_adj<float, 4, true> on 4096-entry
+// tiles, with the index work of slab_lean.cuh.
+__global__ void __launch_bounds__(kST, 2)
+k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__ Y,
+           const float2* __restrict__ zrow, const float2* __restrict__ zop, const double2* __restrict__ phrow,
+           double2* __restrict__ pbar, float2* __restrict__ Xn, float2* __restrict__ Db, float2* __restrict__ yA,
+           double dt, double* __restrict__ gpart, unsigned* __restrict__ ticket, double* __restrict__ gFq,
+           const int STAGE, const int KIND) {
+  using namespace lean;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ float2 phi[LJ];
+  __shared__ int ohi[LJ];
+  __shared__ double gred[kST / 32][kMaxDrv];
+  __shared__ bool last;
+  __shared__ int lph[kMaxPhase][kLph];
+  float2* xs = reinterpret_cast<float2*>(smraw);
+  float2* ys = xs + spad(LT);
+  float2* ks = ys + spad(LT);
+  float2* M = reinterpret_cast<float2*>(smraw + ((3 * spad(LT) * sizeof(float2) + 15) & ~(size_t)15));
+  float2* Op = M + ((sp.row + 1) & ~1);
+  for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = zrow[i];
+  for (int i = threadIdx.x; i < sp.nd * 16; i += blockDim.x) Op[i] = zop[(size_t)sp.d_k[i / 16] * 16 + i % 16];
+  float2 pl;
+  int olo;
+  lsetup(sp, phrow, phi, ohi, pl, olo);
+  lphases_to_smem(sp, lph);
+  __syncthreads();
+  const int tid = threadIdx.x;
+  const int s0 = tid + (tid >> 4);
+  const int nph = sp.nph;
+  const float h = (float)dt;
+  float g[kMaxDrv];
+#pragma unroll
+  for (int j = 0; j < kMaxDrv; ++j) g[j] = 0.f;
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long bl = tile_base(sp, tile) + olo;
+#pragma unroll
+    for (int j0 = 0; j0 < LJ; j0 += 4) {
+      float2 vx[4], vy[4];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        vx[jj] = X[bl + ohi[j0 + jj]];
+        vy[jj] = Y[bl + ohi[j0 + jj]];
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const float2 f = zcmul(pl, phi[j0 + jj]);
+        xs[s0 + 273 * (j0 + jj)] = zcmulc(f, vx[jj]);
+        ys[s0 + 273 * (j0 + jj)] = zcmulc(f, vy[jj]);
+      }
+    }
+    __syncthreads();
+    lpass(nph, lph, M, xs, ks, tid);
+    if (KIND == 0) lepi_adj<0, 0>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h);
+    else if (KIND == 1) lepi_adj<1, 0>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h);
+    else {
+      switch ((KIND == 3 ? 4 : 0) + STAGE) {
+#define SG_LEPA(K, S) case (K == 3 ? 4 : 0) + S: lepi_adj<K, S>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h); break;
+        SG_LEPA(2, 0) SG_LEPA(2, 1) SG_LEPA(2, 2) SG_LEPA(2, 3) SG_LEPA(3, 0) SG_LEPA(3, 1) SG_LEPA(3, 2) SG_LEPA(3, 3)
+#undef SG_LEPA
+        default: break;
+      }
+    }
+    // one instance of the contraction routines: the loop over the pass's drives is not
+    // unrolled, and the term goes to its register by predicated adds
+#pragma unroll 1
+    for (int j = 0; j < sp.nd; ++j) {
+      const float v = ldrive_any(lph[sp.d_ph[j]], sp.d_type[j], Op + 16 * j, xs, ys, tid);
+#pragma unroll
+      for (int i = 0; i < kMaxDrv; ++i)
+        if (i == j) g[i] += v;
+    }
+    __syncthreads();
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < kMaxDrv; ++j) {
+    if (j < sp.nd) {
+      double v = (double)g[j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) gred[warp][j] = v;
+    }
+  }
+  __syncthreads();
+  if (tid < sp.nd) {
+    double v = 0.0;
+    for (int w = 0; w < kST / 32; ++w) v += gred[w][tid];
+    gpart[(size_t)blockIdx.x * kMaxDrv + tid] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (tid < sp.nd) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(gpart + (size_t)b * kMaxDrv + tid);
+    gFq[sp.d_k[tid]] += v;
+  }
+  if (tid == 0) *ticket = 0u;
+}
+
 }  // namespace
 
 namespace {
 
 // The real-operator pulse-gradient adjoint runs unless SG_SLAB_ZADJ=0 (a test knob
 // that keeps the complex-row pass).
+// The lean FP32 adjoint runs unless SG_SLAB_LEAN=0.
+bool lean_adj_on() {
+  const char* e = std::getenv("SG_SLAB_LEAN");
+  return !(e && e[0] == '0');
+}
+
 bool zadj_on() {
   const char* e = std::getenv("SG_SLAB_ZADJ");
   return !(e && e[0] == '0');
@@ -358,6 +517,20 @@ void adj_launch(const SlabPlanHost* h, int g, const void* X, const void* Y, cons
                 double2* pbar, void* Xn, void* Db, void* yA, double dt, const XArgs& xa, cudaStream_t st,
                 int stage, int kind) {
   typedef typename CT<R>::T C;
+  if constexpr (sizeof(R) == 4 && DL == 4) {
+    if (h->ztab && h->zadj && h->allpar && h->lean[g] && !xa.ham && zadj_on() && lean_adj_on()) {
+      static const bool lattr = [] {
+        cudaFuncSetAttribute(k_lean_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeanSmemMax);
+        return true;
+      }();
+      (void)lattr;
+      k_lean_adj<<<h->grid_adj, kST, h->sm_lean_adj, st>>>(
+          h->pass[g], (const float2*)X, (const float2*)Y, (const float2*)h->ztab + (size_t)xa.q * h->pass[g].row,
+          (const float2*)h->zop, h->zph + (size_t)xa.q * h->zsumd, pbar, (float2*)Xn, (float2*)Db, (float2*)yA, dt,
+          reinterpret_cast<double*>(xa.partial), xa.ticket, xa.acc.gF + (size_t)xa.q * xa.K, stage, kind);
+      return;
+    }
+  }
   if constexpr (DL == 2 || DL == 4) {
     // parity-odd plans only (every operator couples levels of opposite parity: the
     // fluxonium and transmon n and phi at n_g = 0, phi_ext = pi)

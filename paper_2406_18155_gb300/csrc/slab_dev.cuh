@@ -17,7 +17,10 @@ constexpr int kMaxPhase = 12;
 constexpr int kMaxDrv = 8;
 // Dynamic shared memory a tiled pass may take: the 227 KB opt-in limit of a block
 // less 1 KB for the kernels' static shared variables.
-constexpr size_t kSlabSmemMax = 226 * 1024;        // drives per pass of the real-operator pulse-gradient adjoint
+constexpr size_t kSlabSmemMax = 226 * 1024;
+// The lean passes' dynamic shared-memory limit (their static shared variables take up
+// to ~1.5 KB).
+constexpr size_t kLeanSmemMax = 200 * 1024;        // drives per pass of the real-operator pulse-gradient adjoint
 
 // One phase of a pass: every thread owns d x d blocks over two tile digits
 // (ka, kb) and applies the terms living on them in registers: the edge
@@ -628,6 +631,10 @@ struct SlabPlanHost {
   const void* zop = nullptr;
   bool zadj = false;
   size_t sm_zadj[kMaxPass] = {0};
+  // lean FP32 passes (slab_lean.cuh): 4 levels, parity-odd, passes whose tiles hold
+  // 4096 entries (each pass picks its kernel on its own)
+  bool lean[kMaxPass] = {false, false, false, false};
+  size_t sm_lean = 0, sm_lean_adj = 0;
 };
 
 // Byte offset of the real-operator row in the shared memory of k_zslab_fwd: after

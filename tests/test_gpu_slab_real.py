@@ -149,6 +149,29 @@ def test_real_two_pass_ring7_against_matrix_free_oracle(sgctx, real_slab):
     assert np.max(np.abs(psi32 - ref)) < 1e-5
 
 
+def test_lean_passes_on_the_two_group_ring_plan(sgctx, real_slab):
+    # 4-level parity-odd plans whose tiles hold 4096 entries (the 2^20 ring's plan
+    # shape; here the 4^7 ring) run the lean FP32 forward and adjoint passes: the
+    # arithmetic of the general real-operator passes with compile-time block strides.
+    # Against those passes (SG_SLAB_LEAN=0) and against FP64 on the same plan.
+    wl = W.fluxonium_chain(seed=9, nq=7, levels=4, T=0.1, dt=0.01, nseg=2, ring=True, ncols=3)
+    wl["fid_kind"] = "state"
+    s = _system(sgctx, wl)
+    args = (wl["T"], wl["dt"], wl["target"], wl["col_index"])
+    out = {}
+    for lean in ("1", "0"):
+        real_slab.setenv("SG_SLAB_LEAN", lean)
+        psi = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"]).cpu().numpy()
+        F, gp, _ = s.fidelity_grad(*args, kind="state", precision="mixed", ckpt=3, ham=False)
+        out[lean] = (psi, F, gp)
+    F64, g64, _ = s.fidelity_grad(*args, kind="state", precision="fp64", ckpt=3, ham=False)
+    scale = np.max(np.abs(g64))
+    assert np.max(np.abs(out["1"][0] - out["0"][0])) < 1e-6
+    assert abs(out["1"][1][1] - F64[1]) < 1e-5
+    assert np.max(np.abs(out["1"][2] - g64)) <= 1e-3 * scale
+    assert np.max(np.abs(out["1"][2] - out["0"][2])) <= 1e-4 * scale
+
+
 def test_complex_local_operator_keeps_the_complex_rows(sgctx, real_slab):
     # a genuinely complex local operator is not real up to phases: the plan keeps the
     # complex-row passes and still matches the oracle
