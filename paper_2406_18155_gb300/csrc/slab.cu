@@ -194,7 +194,7 @@ __device__ __forceinline__ void lepi_fwd(const float2* __restrict__ ks, const fl
                                          const double2* __restrict__ psi_in, double2* __restrict__ psi_out,
                                          float2* __restrict__ Xn, float2* __restrict__ Dacc,
                                          float2* __restrict__ kA, float h) {
-  constexpr int EB = 4;
+  constexpr int EB = 8;
 #pragma unroll
   for (int j0 = 0; j0 < lean::LJ; j0 += EB) {
     long long g[EB];
@@ -237,7 +237,9 @@ __device__ __forceinline__ void lepi_fwd(const float2* __restrict__ ks, const fl
 }
 
 // Lean forward stage pass: the operation of k_zslab_fwd<float, 4, true> on 4096-entry
-// tiles, with the index work of slab_lean.cuh.
+// tiles, with the index work of slab_lean.cuh.  The next tile's entries stream into a
+// dense shared-memory buffer by cp.async while the current tile's phases run; at the
+// start of a tile they are rotated into the real-operator basis from there.
 __global__ void __launch_bounds__(kST, 2)
 k_lean_fwd(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__ zrow,
            const double2* __restrict__ phrow, const double2* __restrict__ psi_in, double2* psi_out,
@@ -247,32 +249,34 @@ k_lean_fwd(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ float2 phi[LJ];
   __shared__ int ohi[LJ];
+  __shared__ int ohi2[LJ / 2];
   __shared__ int lph[kMaxPhase][kLph];
   float2* ys = reinterpret_cast<float2*>(smraw);
   float2* ks = ys + spad(LT);
-  float2* M = reinterpret_cast<float2*>(smraw + ((2 * spad(LT) * sizeof(float2) + 15) & ~(size_t)15));
-  for (int i = threadIdx.x; i < sp.row; i += blockDim.x) M[i] = zrow[i];
+  float2* raw = reinterpret_cast<float2*>(smraw + ((2 * spad(LT) * sizeof(float2) + 15) & ~(size_t)15));
+  float2* M = raw + LT;
+  const int tid = threadIdx.x;
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const int olo2 = __ldg(sp.off + 2 * tid);
+  if (tid < LJ / 2) ohi2[tid] = __ldg(sp.off + 2 * kST * tid);
+  __syncthreads();
+  if ((long long)blockIdx.x < ntiles) lprefetch(X, tile_base(sp, blockIdx.x) + olo2, ohi2, raw, tid);
+  for (int i = tid; i < sp.row; i += blockDim.x) M[i] = zrow[i];
   float2 pl;
   int olo;
   lsetup(sp, phrow, phi, ohi, pl, olo);
   lphases_to_smem(sp, lph);
-  __syncthreads();
-  const int tid = threadIdx.x;
   const int s0 = tid + (tid >> 4);                  // spos(tid); spos(tid + 256 j) = s0 + 273 j
   const int nph = sp.nph;
   const float h = (float)dt;
-  const long long ntiles = (long long)sp.S * sp.ntpc;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long bl = tile_base(sp, tile) + olo;
+    lprefetch_wait();
+    __syncthreads();                                // every thread's copies of this tile landed
 #pragma unroll
-    for (int j0 = 0; j0 < LJ; j0 += 8) {
-      float2 v[8];
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) v[jj] = X[bl + ohi[j0 + jj]];
-#pragma unroll
-      for (int jj = 0; jj < 8; ++jj) ys[s0 + 273 * (j0 + jj)] = zcmulc(zcmul(pl, phi[j0 + jj]), v[jj]);
-    }
-    __syncthreads();
+    for (int j = 0; j < LJ; ++j) ys[s0 + 273 * j] = zcmulc(zcmul(pl, phi[j]), raw[tid + kST * j]);
+    __syncthreads();                                // raw is free again
+    if (tile + gridDim.x < ntiles) lprefetch(X, tile_base(sp, tile + gridDim.x) + olo2, ohi2, raw, tid);
     lpass(nph, lph, M, ys, ks, tid);
     if (KIND == 0) lepi_fwd<0, 0, false>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h);
     else if (KIND == 1) lepi_fwd<1, 0, false>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h);
@@ -289,6 +293,7 @@ k_lean_fwd(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
     }
     __syncthreads();
   }
+  lprefetch_wait();
 }
 
 // The same forward pass, warp-specialised for FP32 tiles of >= 256 entries: 8
@@ -525,11 +530,13 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
   h->perm.nq = nq; h->perm.S = p.S; h->perm.D = p.D;
   for (int i = 0; i < nq; ++i) { h->perm.dims[i] = p.dims[i]; h->perm.st_api[i] = p.st[i]; h->perm.st_int[i] = st_int[i]; }
   const size_t csz = mixed ? sizeof(float2) : sizeof(double2);
+  int pass_low_mode[kMaxPass] = {0, 0, 0, 0};     // each pass's lowest tile digit
   for (int g = 0; g < np; ++g) {
     SlabPass& sp = h->pass[g];
     sp = SlabPass{};
     std::vector<int> tm;                  // tile modes in internal order
     for (int m : order) if (groups[g].count(m)) tm.push_back(m);
+    pass_low_mode[g] = tm.back();
     sp.ng = (int)tm.size();
     sp.T = 1;
     for (int m : tm) sp.T *= p.dims[m];
@@ -680,12 +687,14 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
   h->allpar = true;
   for (int g = 0; g < np; ++g)
     for (int q = 0; q < h->pass[g].nph; ++q) h->allpar = h->allpar && h->pass[g].ph[q].allpar;
-  h->sm_lean = ((2 * spad(lean::LT) * sizeof(float2) + 15) & ~(size_t)15) + (size_t)p.row * sizeof(float2);
+  h->sm_lean = ((2 * spad(lean::LT) * sizeof(float2) + 15) & ~(size_t)15) +
+                (size_t)(lean::LT + p.row) * sizeof(float2);
   h->sm_lean_adj = ((3 * spad(lean::LT) * sizeof(float2) + 15) & ~(size_t)15) +
                    (size_t)(((p.row + 1) & ~1) + kMaxDrv * 16) * sizeof(float2);
   for (int g = 0; g < np; ++g)
     h->lean[g] = mixed && DL == 4 && h->allpar && h->pass[g].T == lean::LT && h->pass[g].ng == 6 &&
-                 h->pass[g].nph <= kMaxPhase && h->sm_lean_adj <= kLeanSmemMax;
+                 h->pass[g].nph <= kMaxPhase && h->sm_lean_adj <= kLeanSmemMax &&
+                 h->sm_lean <= kLeanSmemMax && st_int[pass_low_mode[g]] == 1;
   long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   h->grid_fwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 3 : 1));
   h->grid_zfwd = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
@@ -770,7 +779,7 @@ void fwd_launch(const SlabPlanHost* h, int g, const void* X, const void* row, co
                 bool store, int kind, int q) {
   typedef typename CT<R>::T C;
   if constexpr (sizeof(R) == 4 && DL == 4) {
-    if (h->ztab && h->lean[g] && zws_off() && lean_on()) {
+    if (h->ztab && h->lean[g] && zws_off() && lean_on() && ((uintptr_t)X & 15) == 0) {
       static const bool lattr = [] {
         cudaFuncSetAttribute(k_lean_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kLeanSmemMax);
         return true;

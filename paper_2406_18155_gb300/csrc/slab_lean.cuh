@@ -231,5 +231,23 @@ __device__ __forceinline__ void lsetup(const SlabPass& sp, const double2* __rest
   olo = __ldg(sp.off + tid);
 }
 
+// Asynchronous copy of one tile's entries into dense shared memory (raw[t] = X[tile
+// entry t]): thread tid copies the entry pairs (2m, 2m + 1), m = tid + 256 j (j < 8), by
+// one 16-byte cp.async each.  A pair is contiguous and 16-byte aligned in the slab:
+// the lowest tile digit has global stride 1 and every other digit a stride that is a
+// multiple of 4 (checked on the host, with the slab's alignment), and the digit map is
+// linear in the bits of t, so entry 2m sits at off(2 tid) + off(512 j).
+__device__ __forceinline__ void lprefetch(const float2* __restrict__ X, long long base2,
+                                          const int* __restrict__ ohi2, float2* raw, int tid) {
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const float2* src = X + base2 + ohi2[j];
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(raw + 2 * (tid + kST * j));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+__device__ __forceinline__ void lprefetch_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 }  // namespace lean
 }  // namespace
