@@ -265,7 +265,7 @@ sg_status sg_evolve_noalloc(sg_system* sys, const sg_evolve_opts* opts, void* ps
  * bra 1-body -H_i(t)^T - (i/2) sum_c g_c (L_c^dag L_c)^T, ket couplings J A (x) B, bra
  * couplings -J A^T (x) B^T, jumps i g_c L_c (x) L_c^*, on the same RK4 kernels (stage
  * times of R2, complex stage rows, FP64 or mixed); at most 8 modes (16 doubled).
- * No gradient. */
+ * sg_gate_fidelity_open_grad adds the pulse-parameter gradient of the gate fidelity. */
 sg_status sg_add_collapse(sg_system* sys, int mode, const double* L_re_im, double rate, int* id_out);
 /* rho(T) (host, D x D complex row-major, lab frame) from rho0 (host, same layout).
  * opts: T, dt, precision, frame; ncols and col_index are ignored. */
@@ -280,6 +280,18 @@ sg_status sg_evolve_open(sg_system* sys, const sg_evolve_opts* opts, const doubl
  * for a closed evolution it equals sg_fidelity's F_avg).  1..6 qubit modes. */
 sg_status sg_gate_fidelity_open(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
                                 double* F_out);
+/* sg_gate_fidelity_open with the gradient of one of its fidelities w.r.t. the pulse
+ * parameters (the paper's back-propagation carried over to the vectorised master
+ * equation, App. C last paragraph; Sec. 2.5): kind SG_FID_AVG differentiates F_avg,
+ * SG_FID_STATE the process fidelity F_pro.  F_out[2] as sg_gate_fidelity_open;
+ * grad_pulse (host, sg_param_counts' pulse count doubles, the order of sg_get_params)
+ * receives dF/d(pulse parameters).  Exact derivative of the discrete map: the Dc^2
+ * columns are pulled back through each RK4 step by the adjoint of the non-Hermitian
+ * generator (stage rows of H_eff^dag), from segment checkpoints every ckpt steps
+ * (0: round(sqrt(N))).  opts: T, dt, precision, frame (ncols and col_index ignored;
+ * RK4 only).  The Hamiltonian-parameter gradient of the open evolution is not built. */
+sg_status sg_gate_fidelity_open_grad(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
+                                     int kind, double* F_out, double* grad_pulse, int ckpt);
 
 /* Batched dense evolution on the tensor cores: nsys systems of one shape (the same
  * modes and level counts, the same number of drives; parameters, couplings and

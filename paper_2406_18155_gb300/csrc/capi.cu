@@ -160,6 +160,13 @@ sg_status sg_gate_fidelity_open(sg_system* sys, const sg_evolve_opts* opts, cons
   return sg_gate_fidelity_open_impl(sys, opts, target_re_im, F_out);
 }
 
+sg_status sg_gate_fidelity_open_grad(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
+                                     int kind, double* F_out, double* grad_pulse, int ckpt) {
+  if (!sys) return SG_E_INVALID;
+  std::lock_guard<std::mutex> lk(sys->ctx->mu);
+  return sg_gate_fidelity_open_grad_impl(sys, opts, target_re_im, kind, F_out, grad_pulse, ckpt);
+}
+
 sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b, double strength,
                           int* term_out) {
   if (!sys) return SG_E_INVALID;

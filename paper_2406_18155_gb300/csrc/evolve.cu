@@ -1646,6 +1646,10 @@ struct Solve {
   const void* q2rows = nullptr;   // Q2: 1-body unitaries and coupling unitaries (stage precision)
   const void* q2edges = nullptr;
   const void* q2grad = nullptr;   // Q2 pulse gradient: per step U_i(n)^dag and U_i(n)^dag L_k(n)
+  // stage rows the adjoint passes apply, when they are not the forward rows (the open
+  // evolution's non-Hermitian generator: rows of H_eff^dag); null: the forward rows
+  const double2* adj_tab = nullptr;
+  const float2* adj_tab32 = nullptr;
   ~Solve() {
     slab_plan_destroy(slab);
     onchip_plan_destroy(oc);
@@ -1848,8 +1852,8 @@ void launch_adj(const Solve& sv, cudaStream_t st, const typename CT<R>::T* X, in
   const int j = STAGE == 0 ? 0 : (STAGE == 3 ? 2 : 1);
   const size_t q = 3ull * n + j;
   const C* row;
-  if (sizeof(R) == 4) row = reinterpret_cast<const C*>(sv.tab32 + q * s.p.row);
-  else row = reinterpret_cast<const C*>(sv.tab + q * s.p.row);
+  if (sizeof(R) == 4) row = reinterpret_cast<const C*>((sv.adj_tab32 ? sv.adj_tab32 : sv.tab32) + q * s.p.row);
+  else row = reinterpret_cast<const C*>((sv.adj_tab ? sv.adj_tab : sv.tab) + q * s.p.row);
   k_adj<R, STAGE><<<grid_for(s.D * s.S), kT, s.p.row * sizeof(C), st>>>(s.p, X, row, pbar, Xn, Db, s.dt);
 }
 
@@ -1992,7 +1996,9 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
   onchip_to_image(oc, pbar, pimg, st);
   ++sv.launches;
   const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
-  OnchipTables tb{tab, sv.coef, sv.ph, sv.opd_dev};
+  const void* atab = sizeof(R) == 4 ? (sv.adj_tab32 ? (const void*)sv.adj_tab32 : tab)
+                                    : (sv.adj_tab ? (const void*)sv.adj_tab : tab);
+  OnchipTables tb{atab, sv.coef, sv.ph, sv.opd_dev};
   if (sizeof(R) == 4) {
     // FP32 tables (k_tables32) and an FP32 copy of the operators
     const long long nop = 2 * (long long)s.opdflat.size();
@@ -2000,7 +2006,7 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
     if (!op32 || !sv.coef32 || !sv.ph32) return sg_fail(ctx, SG_E_NOMEM, "FP32 tables missing");
     onchip_to_f32(reinterpret_cast<const double*>(sv.opd_dev), op32, nop, st);
     ++sv.launches;
-    tb = OnchipTables{tab, sv.coef32, sv.ph32, op32};
+    tb = OnchipTables{atab, sv.coef32, sv.ph32, op32};
   }
   const int nseg = (int)ckpts.size();
   for (int c = nseg - 1; c >= 0; --c) {
@@ -2096,6 +2102,8 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
     k_cast<R><<<grid_for(n), kT, 0, st>>>(pint, KB, n, s.dt / 6.0);
     sv.launches += 2;
     const void* tab = sizeof(R) == 4 ? (const void*)sv.tab32 : (const void*)sv.tab;
+    const void* atab = sizeof(R) == 4 ? (sv.adj_tab32 ? (const void*)sv.adj_tab32 : tab)
+                                      : (sv.adj_tab ? (const void*)sv.adj_tab : tab);
     void* KBv = KB;
     void* KB2v = KB2;
     const int nseg = (int)ckpts.size();
@@ -2119,7 +2127,7 @@ sg_status run_backward(sg_system* sys, Solve& sv, std::vector<double2*>& ckpts, 
         void* Yv[4] = {segY[4 * (step - n0)], segY[4 * (step - n0) + 1], segY[4 * (step - n0) + 2],
                        segY[4 * (step - n0) + 3]};
         sv.kt.run(1, step, [&] {
-          return slab_adj_step(sv.slab, sv.mixed, tab, step, Yv, pint, KBv, KB2v, Db, yA, s.dt, xa, sv.tab,
+          return slab_adj_step(sv.slab, sv.mixed, atab, step, Yv, pint, KBv, KB2v, Db, yA, s.dt, xa, sv.tab,
                                sv.coef, sv.ph, s.sumd, s.K, st);
         });
       }
@@ -2588,6 +2596,186 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   sv.kt.finish(sys->ktimes);
   sys->last_stats[4] = sv.launches + (double)(sv.kt.total[0] + sv.kt.total[1] + sv.kt.total[2]);
   return SG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gradient of the open-system gate fidelity (sg_gate_fidelity_open_grad)
+// ---------------------------------------------------------------------------
+// The Dc^2 inputs |c_j><c_k| evolve as columns of the doubled system (lindblad.cu);
+// the channel fidelity is linear in the evolved columns, so its co-state is fixed by
+// the target (k_open_costate).  The discrete adjoint of the non-Hermitian generator
+// A = -i H_eff pulls the co-state back with A^dag = i H_eff^dag, i.e. the adjoint passes
+// apply the stage rows of the conjugate-transposed doubled system, while the drive
+// terms of dF/df contract the forward operators (Sec. 2.5 on the vectorised equation,
+// App. C last paragraph).  A drive of the open system appears twice in the doubled
+// one, on the ket mode with its parameters and on the bra mode with their negatives,
+// so its gradient is the ket copy's minus the bra copy's.
+sg_status sg_gate_fidelity_open_grad_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, int kind,
+                                          double* F_out, double* grad_pulse, int ckpt) {
+  sg_ctx* ctx = sys->ctx;
+  if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
+  if (!o || !target || !F_out || !grad_pulse)
+    return sg_fail(ctx, SG_E_INVALID, "the open gate fidelity gradient needs opts, target, F_out and grad_pulse");
+  if (kind != SG_FID_AVG && kind != SG_FID_STATE) return sg_fail(ctx, SG_E_INVALID, "bad fidelity kind");
+  if (o->solver != SG_SOLVER_RK4) return sg_fail(ctx, SG_E_UNSUPPORTED, "the open evolution runs RK4");
+  const int nq = (int)sys->modes.size();
+  int nqb = 0;
+  for (const HostMode& m : sys->modes) nqb += m.coupler ? 0 : 1;
+  if (nqb < 1 || nqb > 6) return sg_fail(ctx, SG_E_UNSUPPORTED, "the open gate fidelity takes 1..6 qubit modes");
+  const int Dc = 1 << nqb;
+  long long D = 1;
+  std::vector<long long> stv(nq);
+  for (int i = nq - 1; i >= 0; --i) { stv[i] = D; D *= sys->modes[i].d; }
+  std::vector<long long> comp(Dc), cols((size_t)Dc * Dc);
+  for (int j = 0; j < Dc; ++j) {
+    long long r = 0;
+    for (int i = 0, b = nqb - 1; i < nq; ++i) r += (long long)(sys->modes[i].coupler ? 0 : (j >> b--) & 1) * stv[i];
+    comp[j] = r;
+  }
+  for (int j = 0; j < Dc; ++j)
+    for (int k = 0; k < Dc; ++k) cols[(size_t)j * Dc + k] = comp[j] * D + comp[k];
+  sg_system dsys, dadj;
+  sg_status rc = lindblad_doubled(sys, o->T, dsys);
+  if (rc != SG_OK) return rc;
+  lindblad_adjoint_rows(dsys, dadj);
+  sg_evolve_opts od = *o;
+  od.ncols = Dc * Dc;
+  od.col_index = cols.data();
+  od.compensation = SG_COMP_NONE;
+  od.basis = SG_BASIS_PRODUCT;
+  Solve sv, sva;
+  sv.ar.st = sva.ar.st = ctx->stream;
+  sv.want_ham = sva.want_ham = false;
+  rc = build_setup(&dsys, &od, sv.s);
+  if (rc != SG_OK) return rc;
+  rc = build_setup(&dadj, &od, sva.s);
+  if (rc != SG_OK) return rc;
+  Setup& s = sv.s;
+  if (sva.s.p.row != s.p.row || sva.s.N != s.N)
+    return sg_fail(ctx, SG_E_STATE, "adjoint rows of the open evolution do not match its plan");
+  SG_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  keep_pool_memory(ctx->device);
+  cudaStream_t st = ctx->stream;
+  const long long n = s.D * s.S;
+  long long* cols_dev = sv.ar.get<long long>(s.S);
+  long long* comp_dev = sv.ar.get<long long>(Dc);
+  double2* Tg = sv.ar.get<double2>((size_t)Dc * Dc);
+  double* Fd = sv.ar.get<double>(2);
+  int* poff = sv.ar.get<int>(std::max(1, s.K));
+  sv.psi = sv.ar.get<double2>(n);
+  if (!cols_dev || !comp_dev || !Tg || !Fd || !poff || !sv.psi) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(cols_dev, cols.data(), s.S * sizeof(long long), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(comp_dev, comp.data(), Dc * sizeof(long long), cudaMemcpyHostToDevice, st));
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(Tg, target, (size_t)Dc * Dc * sizeof(double2), cudaMemcpyHostToDevice, st));
+  if (s.K) SG_CUDA_TRY(ctx, cudaMemcpyAsync(poff, s.pulse_off.data(), s.K * sizeof(int), cudaMemcpyHostToDevice, st));
+  rc = upload_and_tables(&dsys, &od, sv, true);
+  if (rc != SG_OK) return rc;
+  rc = upload_and_tables(&dadj, &od, sva, true);
+  if (rc != SG_OK) return rc;
+  sv.adj_tab = sva.tab;
+  sv.adj_tab32 = sva.tab32;
+  if ((o->precision == SG_MIXED ? (const void*)sv.adj_tab32 : (const void*)sv.adj_tab) == nullptr)
+    return sg_fail(ctx, SG_E_STATE, "adjoint rows of the open evolution missing");
+  // checkpoints
+  int K = ckpt > 0 ? ckpt : std::max(1, (int)std::lround(std::sqrt((double)s.N)));
+  K = std::min(K, s.N);
+  const int nck = (s.N + K - 1) / K;
+  std::vector<double2*> ckpts;
+  if (sv.onchip(true)) {
+    const long long ns = onchip_state_elems(sv.oc);
+    double2* p = sv.ar.get<double2>((size_t)nck * ns);
+    if (!p) return sg_fail(ctx, SG_E_NOMEM, "device allocation of checkpoints failed");
+    for (int c = 0; c < nck; ++c) ckpts.push_back(p + (size_t)c * ns);
+  } else {
+    for (int c = 0; c < nck; ++c) {
+      double2* p = sv.ar.get<double2>(n);
+      if (!p) return sg_fail(ctx, SG_E_NOMEM, "device allocation of checkpoints failed");
+      ckpts.push_back(p);
+    }
+  }
+  cudaEvent_t ev0, ev1, ev2;
+  cudaEventCreate(&ev0); cudaEventCreate(&ev1); cudaEventCreate(&ev2);
+  auto done = [&](sg_status r) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return r; };
+  cudaEventRecord(ev0, st);
+  rc = o->precision == SG_MIXED ? run_forward<float>(&dsys, sv, cols_dev, false, K, &ckpts)
+                                : run_forward<double>(&dsys, sv, cols_dev, false, K, &ckpts);
+  if (rc != SG_OK) return done(rc);
+  if (s.frame == SG_FRAME_INTERACTION) k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
+  launch_open_fidelity(sv.psi, comp_dev, Tg, D, Dc, Fd, st);
+  sv.launches += 2;
+  cudaEventRecord(ev1, st);
+  // accumulators (the pulse gradient reads gF; the adjoint kernels also write the
+  // per-term operator and energy co-gradients of the 1-body slots)
+  const int ne = s.p.ne, n1 = s.p.n1;
+  const size_t MD2 = SG_MAXD * SG_MAXD;
+  GradAcc acc{};
+  acc.gF = sv.ar.get<double>(3ull * s.N * std::max(1, s.K));
+  acc.obD = sv.ar.get<double2>(std::max(1, s.K) * MD2);
+  acc.obL = sv.ar.get<double2>(std::max(1, ne) * MD2);
+  acc.obR = sv.ar.get<double2>(std::max(1, ne) * MD2);
+  acc.ebB = sv.ar.get<double>(std::max(1, n1) * SG_MAXD);
+  acc.ebL = sv.ar.get<double>(std::max(1, ne) * SG_MAXD);
+  acc.ebR = sv.ar.get<double>(std::max(1, ne) * SG_MAXD);
+  acc.jb = sv.ar.get<double>(std::max(1, ne));
+  double* omega_bar = sv.ar.get<double>(std::max(1, s.K));
+  double* gpulse = sv.ar.get<double>(std::max(1, s.n_pulse));
+  double2* pbar = sv.ar.get<double2>(n);
+  if (!acc.gF || !acc.obD || !acc.obL || !acc.obR || !acc.ebB || !acc.ebL || !acc.ebR || !acc.jb || !omega_bar ||
+      !gpulse || !pbar)
+    return done(sg_fail(ctx, SG_E_NOMEM, "device allocation of gradient accumulators failed"));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.gF, 0, 3ull * s.N * std::max(1, s.K) * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.obD, 0, std::max(1, s.K) * MD2 * sizeof(double2), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.obL, 0, std::max(1, ne) * MD2 * sizeof(double2), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.obR, 0, std::max(1, ne) * MD2 * sizeof(double2), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.ebB, 0, std::max(1, n1) * SG_MAXD * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.ebL, 0, std::max(1, ne) * SG_MAXD * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.ebR, 0, std::max(1, ne) * SG_MAXD * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.jb, 0, std::max(1, ne) * sizeof(double), st));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(pbar, 0, n * sizeof(double2), st));
+  launch_open_costate(comp_dev, Tg, D, Dc, kind, pbar, st);
+  if (s.frame == SG_FRAME_INTERACTION) k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, +1.0), pbar);
+  sv.launches += 2;
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  rc = o->precision == SG_MIXED ? run_backward<float>(&dsys, sv, ckpts, K, pbar, acc)
+                                : run_backward<double>(&dsys, sv, ckpts, K, pbar, acc);
+  if (rc != SG_OK) return done(rc);
+  if (s.K) {
+    int np_max = 1;
+    for (auto& d : s.drives) np_max = std::max(np_max, d.kind == SG_ENV_PWC ? d.nseg : 1);
+    const int pt = 64;
+    k_pulse_chain<<<s.K, pt, pt * (np_max + 1) * sizeof(double), st>>>(
+        sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar, 0);
+    ++sv.launches;
+  }
+  SG_CUDA_TRY(ctx, cudaGetLastError());
+  cudaEventRecord(ev2, st);
+  double Fh[2] = {0.0, 0.0};
+  std::vector<double> gd(std::max(1, s.n_pulse), 0.0);
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));    // reads only from an idle stream (see dcopy)
+  SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, sizeof Fh, cudaMemcpyDeviceToHost, st));
+  if (s.n_pulse) SG_CUDA_TRY(ctx, cudaMemcpyAsync(gd.data(), gpulse, s.n_pulse * sizeof(double), cudaMemcpyDeviceToHost, st));
+  SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  // the doubled drives 2k (ket) and 2k + 1 (bra, negated parameters) of drive k
+  int po = 0;
+  for (size_t k = 0; k < sys->drives.size(); ++k) {
+    const HostDrive& hd = sys->drives[k];
+    const int np = hd.kind == SG_ENV_PWC ? hd.nseg : 1;
+    for (int x = 0; x < np; ++x)
+      grad_pulse[po + x] = gd[s.pulse_off[2 * k] + x] - gd[s.pulse_off[2 * k + 1] + x];
+    po += np;
+  }
+  F_out[0] = Fh[0];
+  F_out[1] = Fh[1];
+  float fwd_ms = 0.f, bwd_ms = 0.f;
+  cudaEventElapsedTime(&fwd_ms, ev0, ev1);
+  cudaEventElapsedTime(&bwd_ms, ev1, ev2);
+  sys->last_stats[0] = fwd_ms;
+  sys->last_stats[1] = bwd_ms;
+  sys->last_stats[2] = (double)(sv.ar.bytes + sva.ar.bytes);
+  sys->last_stats[3] = K;
+  sv.kt.finish(sys->ktimes);
+  sys->last_stats[4] = sv.launches + (double)(sv.kt.total[0] + sv.kt.total[1] + sv.kt.total[2]);
+  return done(SG_OK);
 }
 
 // ---------------------------------------------------------------------------

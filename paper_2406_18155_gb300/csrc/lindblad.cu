@@ -18,6 +18,7 @@
 // drives of unit envelope) and evolves vec(rho) as columns of it with the ordinary
 // RK4 kernels (complex rows: the terms are not real).
 #include "sg_internal.h"
+#include <algorithm>
 #include <cmath>
 #include <complex>
 #include <vector>
@@ -150,6 +151,30 @@ sg_status lindblad_doubled(const sg_system* sys, double T, sg_system& out) {
   return SG_OK;
 }
 
+// The doubled system with every operator replaced by its conjugate transpose (drives
+// and couplings unchanged, their coefficients real): its stage rows are those of
+// H_eff^dag, so the adjoint passes, which apply i H to the co-state, apply
+// A^dag = i H_eff^dag for the forward generator A = -i H_eff (the discrete adjoint of
+// a non-Hermitian generator).
+void lindblad_adjoint_rows(const sg_system& dsys, sg_system& out) {
+  out = dsys;
+  for (size_t m = 0; m < out.modes.size(); ++m) {
+    const int d = out.modes[m].d;
+    std::vector<double>& od = out.opd_host[m];
+    const size_t nop = od.size() / (2 * (size_t)d * d);
+    for (size_t op = 0; op < nop; ++op) {
+      double* o = od.data() + 2 * op * d * d;
+      std::vector<double> t(2 * (size_t)d * d);
+      for (int x = 0; x < d; ++x)
+        for (int y = 0; y < d; ++y) {
+          t[2 * ((size_t)y * d + x)] = o[2 * ((size_t)x * d + y)];
+          t[2 * ((size_t)y * d + x) + 1] = -o[2 * ((size_t)x * d + y) + 1];
+        }
+      std::copy(t.begin(), t.end(), o);
+    }
+  }
+}
+
 namespace {
 
 // Channel on the computational block from the evolved columns |c_j><c_k| (lab frame,
@@ -192,7 +217,37 @@ __global__ void k_open_fidelity(const double2* __restrict__ psi, const long long
   }
 }
 
+// Co-state of the open gate fidelity on the evolved columns (lab frame, layout of
+// k_open_fidelity; the caller zeroes the rest): F is linear in S, F = Re sum conj(W) S,
+// so the co-state (d F / d Re s + i d F / d Im s) of entry (c_a, c_b) of column (j, k)
+// is W[(a, b), (j, k)]: S_T / (Dc (Dc + 1)) plus 1 / (Dc (Dc + 1)) where a = b, j = k
+// for F_avg (kind SG_FID_AVG), S_T / Dc^2 for F_pro (kind SG_FID_STATE).
+__global__ void k_open_costate(const long long* __restrict__ comp, const double2* __restrict__ Tg, long long D,
+                               int Dc, int kind, double2* __restrict__ bar) {
+  const int S = Dc * Dc;
+  const double sc = kind == SG_FID_AVG ? 1.0 / ((double)Dc * (Dc + 1.0)) : 1.0 / ((double)Dc * Dc);
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < S * S; x += gridDim.x * blockDim.x) {
+    const int ab = x / S, jk = x - (x / S) * S;
+    const int a = ab / Dc, b = ab - a * Dc, j = jk / Dc, k = jk - j * Dc;
+    const double2 ta = Tg[a * Dc + j], tb = Tg[b * Dc + k];
+    double re = ta.x * tb.x + ta.y * tb.y, im = ta.y * tb.x - ta.x * tb.y;
+    if (kind == SG_FID_AVG && a == b && j == k) re += 1.0;
+    bar[(comp[a] * D + comp[b]) * S + jk] = make_double2(sc * re, sc * im);
+  }
+}
+
 }  // namespace
+
+void launch_open_fidelity(const double2* psi, const long long* comp, const double2* Tg, long long D, int Dc,
+                          double* F, cudaStream_t st) {
+  k_open_fidelity<<<1, 256, 0, st>>>(psi, comp, Tg, D, Dc, F);
+}
+
+void launch_open_costate(const long long* comp, const double2* Tg, long long D, int Dc, int kind, double2* bar,
+                         cudaStream_t st) {
+  const int n = Dc * Dc * Dc * Dc;
+  k_open_costate<<<(n + 255) / 256, 256, 0, st>>>(comp, Tg, D, Dc, kind, bar);
+}
 
 sg_status sg_evolve_open_impl(sg_system* sys, const sg_evolve_opts* o, const double* rho0, double* rho_out) {
   sg_ctx* ctx = sys->ctx;
