@@ -334,7 +334,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
     if rank == 0 and args.serving > 0:
-        out["serving"] = serving_bench(ctx, args.serving, args.serving_slots)
+        out["serving"] = serving_bench(ctx, args.serving, args.serving_slots, max_batch=args.serving_batch)
     if rank == 0:
         print(json.dumps(out), flush=True)
     ctx.close()
@@ -405,7 +405,7 @@ class UtilSampler:
         return statistics.mean(self.vals) / 100.0 if self.vals else None
 
 
-def serving_bench(ctx, n_requests, slots, seed=7, rates=(0.7,), n_saturated=None):
+def serving_bench(ctx, n_requests, slots, seed=7, rates=(0.7,), n_saturated=None, max_batch=1):
     """Config 4: requests of 2-5 coupled transmons or fluxoniums at 3-5 levels,
     T ~ U[20, 200] ns, random 10-segment pulses, each a fidelity + gradient solve.
     First n_saturated requests (default 2 x n_requests) submitted at once: the
@@ -413,7 +413,8 @@ def serving_bench(ctx, n_requests, slots, seed=7, rates=(0.7,), n_saturated=None
     (conservative: it includes the drain, when only the longest requests are left).
     Then, for each rate fraction, a stream of n_requests with Poisson arrivals at
     that fraction of the saturated rate: solves/s, p50/p99 latency (submit -> result)
-    and the device utilisation sampled during the stream."""
+    and the device utilisation sampled during the stream.  max_batch > 1: each slot
+    packs queued same-shape requests into shared batched launches."""
     from paper_2406_18155_gb300.api import Server, System
     rng = np.random.Generator(np.random.PCG64(seed))
 
@@ -425,18 +426,22 @@ def serving_bench(ctx, n_requests, slots, seed=7, rates=(0.7,), n_saturated=None
             out.append((wl, s_))
         return out
 
-    srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
+    srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots, max_batch=max_batch)
     sat = make(max(4, n_saturated or 2 * n_requests))
     t0 = time.perf_counter()
     tk = [srv.submit(s_, wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg") for wl, s_ in sat]
     sat_res = [srv.wait(t) for t in tk]
     sat_rate = len(sat) / (time.perf_counter() - t0)
+    sat_st = srv.stats()
     srv.close()
     del sat
     out = {"saturated_solves_per_s": sat_rate, "saturated_requests": len(sat_res), "slots": slots,
-           "saturated_errors": int(sum(r["status"] != 0 for r in sat_res)), "streams": []}
+           "max_batch": max_batch, "saturated_errors": int(sum(r["status"] != 0 for r in sat_res)),
+           "saturated_packing": {k: sat_st[k] for k in ("batches", "batched_requests", "batched_launches",
+                                                          "batched_launch_members")},
+           "streams": []}
     for frac in rates:
-        srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots)
+        srv = Server(ctx, mem_budget_bytes=120 << 30, max_slots=slots, max_batch=max_batch)
         reqs = make(n_requests)
         rate = frac * sat_rate
         gaps = rng.exponential(1.0 / rate, size=len(reqs))
@@ -455,13 +460,16 @@ def serving_bench(ctx, n_requests, slots, seed=7, rates=(0.7,), n_saturated=None
         wall = time.perf_counter() - t0
         u = util.stop()
         lat = np.array([r["done_s"] - r["submit_s"] for r in res])
+        st_ = srv.stats()
         srv.close()
         steps = np.array([int(round(wl["T"] / wl["dt"])) for wl, _ in reqs])
         out["streams"].append({
             "rate_fraction": frac, "arrival_rate_per_s": rate, "requests": len(reqs),
             "solves_per_s": len(reqs) / wall, "p50_s": float(np.percentile(lat, 50)),
             "p99_s": float(np.percentile(lat, 99)), "device_utilisation": u,
-            "errors": int(sum(r["status"] != 0 for r in res)), "mean_rk4_steps": float(steps.mean())})
+            "errors": int(sum(r["status"] != 0 for r in res)), "mean_rk4_steps": float(steps.mean()),
+            "packing": {k: st_[k] for k in ("batches", "batched_requests", "batched_launches",
+                                            "batched_launch_members")}})
         del reqs
     # the first stream's figures at the top level, as before
     st0 = out["streams"][0]
@@ -852,6 +860,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serving", type=int, default=64, help="Poisson requests of the serving sample (0: skip); twice as many run saturated first")
     ap.add_argument("--serving-slots", type=int, default=32)
+    ap.add_argument("--serving-batch", type=int, default=1,
+                    help="per slot, pack up to this many queued same-shape requests into shared launches")
     ap.add_argument("--serving-rates", default="0.7",
                     help="arrival rates as fractions of the saturated rate, comma-separated")
     ap.add_argument("--serving-saturated", type=int, default=0,
@@ -897,7 +907,8 @@ def main():
         torch.cuda.set_device(0)
         rates = tuple(float(x) for x in args.serving_rates.split(","))
         print(json.dumps({"serving": serving_bench(Context(0), args.serving, args.serving_slots, rates=rates,
-                                                   n_saturated=args.serving_saturated or None)}), flush=True)
+                                                   n_saturated=args.serving_saturated or None,
+                                                   max_batch=args.serving_batch)}), flush=True)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -404,19 +404,34 @@ typedef struct {
   double gpu_busy_frac;
   size_t mem_in_use, mem_budget;
   int active_slots, max_slots;
+  long long batches;             /* slot runs that packed several requests (max_batch > 1)  */
+  long long batched_requests;    /* requests run in those packs                             */
+  long long batched_launches;    /* batched on-chip launches issued                        */
+  long long batched_launch_members; /* solves summed over those launches                   */
 } sg_stats;
 
 /* A server owns `max_slots` slots, each a worker thread with its own CUDA stream
  * (continuous batching): requests are admitted in arrival order while a slot is
  * free and the device memory they need fits `mem_budget_bytes`; each admitted
- * request runs as one independent fidelity(+gradient) solve on its slot's stream,
- * so the kernels of all admitted requests overlap on the device, and a request
- * that arrives while others run starts as soon as a slot and memory free up.
+ * request runs as one fidelity(+gradient) solve on its slot's stream, so the
+ * kernels of all admitted requests overlap on the device, and a request that
+ * arrives while others run starts as soon as a slot and memory free up.
  * Results do not depend on what else runs (each solve has its own buffers and
  * fixed-order reductions).  gpu_busy_frac in sg_stats is the fraction of the
  * server's wall time with at least one request running, not a device occupancy. */
 sg_status sg_server_create(sg_ctx* ctx, size_t mem_budget_bytes, int max_slots, sg_server** out);
 sg_status sg_server_destroy(sg_server* srv);
+/* Packing of same-shape requests (max_batch 1..16, default 1: none).  With
+ * max_batch > 1 a slot that admits a request also admits up to max_batch - 1 queued
+ * requests of the same step shape (modes and level counts, terms, drive kinds,
+ * columns, precision, frame and dt; parameter values and T may differ) while memory
+ * allows, and runs them together: each on a stream of its own, their on-chip
+ * launches (the forward evolution, and per checkpoint segment the recompute and
+ * the pull-back) issued as shared batched launches, one CTA range per request
+ * (pack members of different T run to the longest one's end in each shared
+ * launch).  Each request's arithmetic is that of its solve alone.  Call while no
+ * request is queued or running (SG_E_STATE otherwise). */
+sg_status sg_server_set_batch(sg_server* srv, int max_batch);
 /* Queue a request.  The request's system must stay alive until its result is
  * polled, and the caller makes no other call on it meanwhile (its slot runs it
  * with the slot's context and prepares it if needed).  One system has at most one

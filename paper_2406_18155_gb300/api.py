@@ -364,15 +364,19 @@ def workload_fidelity(ctx, wl, precision="mixed", grad=False, ckpt=0):
 
 class Server:
     """Continuous-batching server (sg_server_*): requests are admitted by device
-    memory and free slots, and run concurrently on the slots' streams."""
+    memory and free slots, and run concurrently on the slots' streams; with
+    max_batch > 1 a slot packs queued same-shape requests into shared batched
+    launches (sg_server_set_batch)."""
 
-    def __init__(self, ctx, mem_budget_bytes, max_slots):
+    def __init__(self, ctx, mem_budget_bytes, max_slots, max_batch=1):
         self.ctx = ctx
         h = C.c_void_p()
         check(lib().sg_server_create(ctx.h, C.c_size_t(int(mem_budget_bytes)), int(max_slots),
                                      C.byref(h)), ctx.h)
         self.h = h
         self._keep = {}
+        if max_batch > 1:
+            check(lib().sg_server_set_batch(self.h, int(max_batch)), ctx.h)
 
     def submit(self, system, T, dt, target, col_index=None, kind="avg", precision="mixed",
                want_grad=True):

@@ -55,7 +55,9 @@ class sg_stats(C.Structure):
                 ("cancelled", C.c_uint64), ("rejected", C.c_uint64),
                 ("solves_per_s", C.c_double), ("p50_s", C.c_double), ("p99_s", C.c_double),
                 ("gpu_busy_frac", C.c_double), ("mem_in_use", C.c_size_t),
-                ("mem_budget", C.c_size_t), ("active_slots", C.c_int), ("max_slots", C.c_int)]
+                ("mem_budget", C.c_size_t), ("active_slots", C.c_int), ("max_slots", C.c_int),
+                ("batches", C.c_longlong), ("batched_requests", C.c_longlong),
+                ("batched_launches", C.c_longlong), ("batched_launch_members", C.c_longlong)]
 
 
 _P = C.c_void_p
@@ -106,6 +108,7 @@ SIGNATURES = {
     "sg_server_wait": (_I, [_P, C.c_uint64, C.POINTER(sg_result)]),
     "sg_server_cancel": (_I, [_P, C.c_uint64]),
     "sg_server_stats": (_I, [_P, C.POINTER(sg_stats)]),
+    "sg_server_set_batch": (_I, [_P, _I]),
 }
 
 _lib = None

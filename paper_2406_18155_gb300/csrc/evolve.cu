@@ -1650,6 +1650,7 @@ struct Solve {
   // evolution's non-Hermitian generator: rows of H_eff^dag); null: the forward rows
   const double2* adj_tab = nullptr;
   const float2* adj_tab32 = nullptr;
+  double* J_dev = nullptr;        // coupling strengths (batched on-chip adjoint launches)
   ~Solve() {
     slab_plan_destroy(slab);
     onchip_plan_destroy(oc);
@@ -1737,6 +1738,9 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   if (!s.amps.empty()) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.amps_dev, s.amps.data(), s.amps.size() * sizeof(double), cudaMemcpyHostToDevice, st));
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.E_dev, s.Eflat.data(), s.sumd * sizeof(double), cudaMemcpyHostToDevice, st));
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.opd_dev, s.opdflat.data(), s.opdflat.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+  sv.J_dev = sv.ar.get<double>(std::max(1, s.p.ne));
+  if (!sv.J_dev) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
+  if (s.p.ne) SG_CUDA_TRY(ctx, cudaMemcpyAsync(sv.J_dev, s.ta.J, s.p.ne * sizeof(double), cudaMemcpyHostToDevice, st));
   TabArgs ta = s.ta;
   ta.drives = sv.drives_dev;
   ta.amps = sv.amps_dev;
@@ -1963,6 +1967,7 @@ XArgs make_xargs(const Solve& sv, GradAcc acc) {
   for (int e = 0; e < s.p.ne; ++e) { xa.e_opa[e] = s.ta.e_opa[e]; xa.e_opb[e] = s.ta.e_opb[e]; xa.J[e] = s.ta.J[e]; }
   xa.acc = acc;
   xa.ham = sv.want_ham ? 1 : 0;
+  xa.Jdev = sv.J_dev;
   return xa;
 }
 
@@ -2014,6 +2019,7 @@ sg_status run_backward_onchip(sg_system* sys, Solve& sv, std::vector<double2*>& 
     sv.launches += onchip_forward(oc, tab, nullptr, ckpts[c], nullptr, nullptr, K, n0, n1, s.dt, segY, st);
     sv.launches += onchip_adjoint(oc, tb, segY, pimg, n0, n1, s.dt, xa, (int)nst, gFc, accc, err, colow, st);
   }
+  onchip_batcher_release();                       // the solve's last on-chip launch is issued
   onchip_reduce(oc, gFc, accc, nst, s.K, s.p.n1, s.p.ne, acc, st);
   ++sv.launches;
   SG_CUDA_TRY(ctx, cudaGetLastError());
@@ -2419,6 +2425,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (s.q2) rc = run_q2(sys, sv, cols_dev, dressed);
   else rc = o->precision == SG_MIXED ? run_forward<float>(sys, sv, cols_dev, dressed, K, grad ? &ckpts : nullptr)
                                      : run_forward<double>(sys, sv, cols_dev, dressed, K, grad ? &ckpts : nullptr);
+  if (!grad || rc != SG_OK) onchip_batcher_release();    // no further on-chip launch of this solve
   if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
   if (s.frame == SG_FRAME_INTERACTION)
     k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, -1.0), sv.psi);
@@ -2513,6 +2520,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     if (s.q2) rc = run_backward_q2(sys, sv, pbar, acc);
     else rc = o->precision == SG_MIXED ? run_backward<float>(sys, sv, ckpts, K, pbar, acc)
                                        : run_backward<double>(sys, sv, ckpts, K, pbar, acc);
+    onchip_batcher_release();
     if (rc != SG_OK) { cudaEventDestroy(ev0); cudaEventDestroy(ev1); cudaEventDestroy(ev2); return rc; }
     // chains
     if (s.K) {

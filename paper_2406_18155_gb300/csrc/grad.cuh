@@ -38,6 +38,7 @@ struct XArgs {
   int drv_op[SG_MAXDRIVE];
   int e_opa[SG_MAXEDGE], e_opb[SG_MAXEDGE];
   double J[SG_MAXEDGE];
+  const double* Jdev;         // device copy of J (read by batched on-chip launches)
   double2* partial;           // gridDim x nW x DL^2
   unsigned* ticket;
   GradAcc acc;

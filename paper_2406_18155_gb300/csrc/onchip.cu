@@ -31,6 +31,10 @@
 #include "slab.h"
 #include "slab_dev.cuh"
 #include "onchip.h"
+#include <condition_variable>
+#include <cstring>
+#include <mutex>
+#include <vector>
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
@@ -176,6 +180,34 @@ struct OcArgs {
   int wlim, skip_first;
 };
 
+// One solve of a batched launch: its tables, buffers and step range (the fields of
+// the unbatched launch's arguments).  CTAs [b ncta, (b + 1) ncta) of a batched grid
+// run solve b.
+struct OcSys {
+  const void* tab;
+  const void* coef;
+  const void* ph;
+  const void* opd;
+  const double2* psi_api;
+  const double2* img_in;
+  double2* psi_out;
+  double2* ck_out;
+  void* segY;
+  double2* pbar_img;
+  double* gF_cta;
+  double* acc_cta;
+  int* err;
+  void* pblo;
+  const double* J;       // coupling strengths of the solve (Hamiltonian-gradient contraction)
+  long long nstK;
+  int n0, n1, K;
+};
+constexpr int kOcMaxBatch = 24;
+struct OcBatch {
+  int nsys;              // 0: an unbatched launch (the kernel's own arguments)
+  OcSys s[kOcMaxBatch];
+};
+
 template <int DL>
 __device__ __forceinline__ int oc_pos(const OcArgs& oa, int e) {
   const int c = e / oa.D;
@@ -217,8 +249,23 @@ template <typename R, int DL>
 __global__ void __launch_bounds__(kST, 1)
 k_oc_fwd(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, const double2* __restrict__ psi_api,
          const double2* __restrict__ img_in, double2* __restrict__ psi_out, double2* __restrict__ ck_out, int K,
-         int n0, int n1, double dt, typename CT<R>::T* __restrict__ segY) {
+         int n0, int n1, double dt, typename CT<R>::T* __restrict__ segY, const __grid_constant__ OcBatch bt) {
   typedef typename CT<R>::T C;
+  int cta = blockIdx.x;
+  if (bt.nsys > 0) {
+    const int b = blockIdx.x / oa.ncta;
+    cta = blockIdx.x - b * oa.ncta;
+    const OcSys& d = bt.s[b];
+    tab = static_cast<const C*>(d.tab);
+    psi_api = d.psi_api;
+    img_in = d.img_in;
+    psi_out = d.psi_out;
+    ck_out = d.ck_out;
+    K = d.K;
+    n0 = d.n0;
+    n1 = d.n1;
+    segY = static_cast<C*>(d.segY);
+  }
   extern __shared__ __align__(16) unsigned char sm[];
   C* ys = reinterpret_cast<C*>(sm + oa.f_ys);
   C* ks = reinterpret_cast<C*>(sm + oa.f_ks);
@@ -227,7 +274,6 @@ k_oc_fwd(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   C* dl = reinterpret_cast<C*>(sm + oa.f_dl);
   C* const M0 = reinterpret_cast<C*>(sm + oa.f_M);
   C* const M1 = M0 + oa.rowA;
-  const int cta = blockIdx.x;
   const R h = (R)dt;
   for (int e = threadIdx.x; e < oa.ent; e += blockDim.x) {
     const int c = e / oa.D, t = e - c * oa.D;
@@ -347,7 +393,8 @@ __device__ __forceinline__ void eb_rowcol(T qv, int lane, T* sq, T* eb) {
 //   lab frame, 1-body:     eb[a] += Re W_aa
 // with P_ab = exp(i (E_a - E_b) t) and X the stage's term matrix (B, L or R).
 template <int DL, typename T>
-__device__ __forceinline__ void oc_contract(const XArgs& xa, const typename CT<T>::T* __restrict__ opd, int slot,
+__device__ __forceinline__ void oc_contract(const XArgs& xa, const double* Jb, const typename CT<T>::T* __restrict__ opd,
+                                            int slot,
                                             typename CT<T>::T w, int lane, const typename CT<T>::T* tabrow,
                                             const T* cf, const typename CT<T>::T* phs, T t, int q, int s,
                                             const OcAcc<T>& A, T* sq, double* gFc) {
@@ -394,7 +441,7 @@ __device__ __forceinline__ void oc_contract(const XArgs& xa, const typename CT<T
   const int side = (slot - p.n1) / p.ne, qe = (slot - p.n1) % p.ne;
   const int i = side == 0 ? p.e_a[qe] : p.e_b[qe];
   const int op = side == 0 ? xa.e_opa[qe] : xa.e_opb[qe];
-  const T sc = side == 0 ? (T)xa.J[qe] : (T)1;
+  const T sc = side == 0 ? (T)(Jb ? Jb[qe] : xa.J[qe]) : (T)1;
   T jg = 0;
   if (on) {
     const C P = cmulT(phs[xa.eoff[i] + ia], cconjT(phs[xa.eoff[i] + ib]));
@@ -425,10 +472,32 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
          const typename CT<R>::T* __restrict__ ph, const typename CT<R>::T* __restrict__ opd,
          const typename CT<R>::T* __restrict__ segY, double2* __restrict__ pbar_img, int n0, int n1, double dt,
          XArgs xa, double* __restrict__ gF_cta, double* __restrict__ acc_cta, long long nstK,
-         int* __restrict__ err, float2* __restrict__ pblo) {
+         int* __restrict__ err, float2* __restrict__ pblo, const __grid_constant__ OcBatch bt) {
   typedef typename CT<R>::T C;
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
+  int cta = blockIdx.x;
+  const double* Jb = nullptr;                           // the solve's couplings (batched), else xa.J
+  if (bt.nsys > 0) {
+    const int b = blockIdx.x / oa.ncta;
+    cta = blockIdx.x - b * oa.ncta;
+    const OcSys& d = bt.s[b];
+    tab = static_cast<const C*>(d.tab);
+    coef = static_cast<const R*>(d.coef);
+    ph = static_cast<const C*>(d.ph);
+    opd = static_cast<const C*>(d.opd);
+    segY = static_cast<const C*>(d.segY);
+    pbar_img = d.pbar_img;
+    n0 = d.n0;
+    n1 = d.n1;
+    gF_cta = d.gF_cta;
+    acc_cta = d.acc_cta;
+    nstK = d.nstK;
+    err = d.err;
+    pblo = static_cast<float2*>(d.pblo);
+    Jb = d.J;
+  }
+  (void)pblo;
   C* xs = reinterpret_cast<C*>(sm + oa.a_xs);
   C* ks = reinterpret_cast<C*>(sm + oa.a_ks);
   C* ys = reinterpret_cast<C*>(sm + oa.a_ys);
@@ -436,7 +505,7 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   C* db = reinterpret_cast<C*>(sm + oa.a_db);
   StateArr<R> pb;
   if constexpr (sizeof(R) == 4) {
-    if (oa.pblo_g) pb.init_split(sm + oa.a_pb, pblo + (size_t)blockIdx.x * oa.ent);
+    if (oa.pblo_g) pb.init_split(sm + oa.a_pb, pblo + (size_t)cta * oa.ent);
     else pb.init(sm + oa.a_pb, oa.ent);
   } else {
     pb.init(sm + oa.a_pb, oa.ent);
@@ -460,7 +529,6 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
   const int nphase = oa.npw * 32;                      // phase threads: [0, nphase)
   const int nxw = kST / 32 - oa.npw;                   // density warps: [npw, 8)
   R* sq = reinterpret_cast<R*>(sm + oa.a_sq) + warp * 32;
-  const int cta = blockIdx.x;
   const R h = (R)dt;
   const int DD = DL * DL;
   for (int i = threadIdx.x; i < oa.K * DD; i += blockDim.x) A.obD[i] = cmk<C>(0.0, 0.0);
@@ -578,7 +646,7 @@ k_oc_adj(SlabPass sp, OcArgs oa, const typename CT<R>::T* __restrict__ tab, cons
             for (int b = 0; b < DL; ++b)
               if ((!PARX || ((a + b) & 1)) && lane == a * DL + b) mine = acc[xd_i<DL, PARX>(a, b)];
           const C w = cmk<C>(mine.y, -mine.x);             // W = -i C
-          oc_contract<DL, R>(xa, opd, sp.x_gslot[slot], w, lane, Mc, cfs, phs, tq, q, s, A, sq, gFc);
+          oc_contract<DL, R>(xa, Jb, opd, sp.x_gslot[slot], w, lane, Mc, cfs, phs, tq, q, s, A, sq, gFc);
         }
       }
       bool ok = true;
@@ -963,6 +1031,10 @@ struct OnchipPlan {
   OcArgs oa{};
   bool mixed = false, adj_ok = false, fwd_ok = false;
   size_t sm_fwd = 0, sm_adj = 0, limit = 0;
+  // everything the plan is built from (the structure of the Kronecker-sum plan,
+  // precision, drive count, energy-row length): plans with equal signatures are
+  // equal, so their solves can share batched launches
+  std::vector<long long> sig;
 };
 
 namespace {
@@ -1029,6 +1101,19 @@ void layout(OcArgs& a, int DL, size_t cs, size_t& fwd, size_t& adj) {
 
 }  // namespace
 
+namespace {
+std::vector<long long> plan_signature(const KPlan& p, bool mixed, int K, int sumd) {
+  std::vector<long long> v = {mixed ? 1 : 0, K, sumd, p.nq, p.S, p.D, p.n1, p.ne, p.row, p.dl, (long long)p.par1,
+                              (long long)p.parL, (long long)p.parR};
+  for (int i = 0; i < p.nq; ++i) { v.push_back(p.dims[i]); v.push_back(p.st[i]); }
+  for (int u = 0; u < p.n1; ++u) { v.push_back(p.s1_mode[u]); v.push_back(p.s1_off[u]); }
+  for (int e = 0; e < p.ne; ++e) {
+    v.push_back(p.e_a[e]); v.push_back(p.e_b[e]); v.push_back(p.e_offL[e]); v.push_back(p.e_offR[e]);
+  }
+  return v;
+}
+}  // namespace
+
 OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cudaStream_t st) {
   if (p.nq < 2 || p.nq > SG_MAXQ) return nullptr;
   SlabPlanHost* h = slab_plan_create(p, mixed, st, true);
@@ -1047,6 +1132,7 @@ OnchipPlan* onchip_plan_create(const KPlan& p, bool mixed, int K, int sumd, cuda
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   const size_t limit = (size_t)std::max(0, optin - 1024);
   OnchipPlan* oc = new OnchipPlan();
+  oc->sig = plan_signature(p, mixed, K, sumd);
   oc->h = h;
   oc->mixed = mixed;
   OcArgs& a = oc->oa;
@@ -1153,6 +1239,11 @@ void smem_limit_once() {
   (void)done;
 }
 
+const OcBatch& no_batch() {
+  static const OcBatch b{};
+  return b;
+}
+
 template <typename R, int DL>
 int fwd_t(const OnchipPlan* oc, const void* tab, const double2* psi_api, const double2* img_in, double2* psi_out,
           double2* ck_out, int K, int n0, int n1, double dt, void* segY, cudaStream_t st) {
@@ -1160,7 +1251,7 @@ int fwd_t(const OnchipPlan* oc, const void* tab, const double2* psi_api, const d
   auto kern = k_oc_fwd<R, DL>;
   smem_limit_once<k_oc_fwd<R, DL>>();
   kern<<<oc->oa.ncta, kST, oc->sm_fwd, st>>>(oc->h->pass[0], oc->oa, (const C*)tab, psi_api, img_in, psi_out,
-                                             ck_out, std::max(1, K), n0, n1, dt, (C*)segY);
+                                             ck_out, std::max(1, K), n0, n1, dt, (C*)segY, no_batch());
   return 1;
 }
 
@@ -1181,7 +1272,31 @@ int adj_t(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double
   kern<<<oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oa, (const C*)tb.tab, (const R*)tb.coef,
                                              (const C*)tb.ph, (const C*)tb.opd, (const C*)segY, pbar_img, n0, n1,
                                              dt, xa, gF_cta, acc_cta, (long long)nst * std::max(1, oc->oa.K), err,
-                                             (float2*)pblo);
+                                             (float2*)pblo, no_batch());
+  return 1;
+}
+
+// Batched launches: bt.nsys solves of oc's plan shape, CTAs [b ncta, (b + 1) ncta)
+// running solve b.
+template <typename R, int DL>
+int fwd_batch_t(const OnchipPlan* oc, const OcBatch& bt, double dt, cudaStream_t st) {
+  smem_limit_once<k_oc_fwd<R, DL>>();
+  k_oc_fwd<R, DL><<<bt.nsys * oc->oa.ncta, kST, oc->sm_fwd, st>>>(oc->h->pass[0], oc->oa, nullptr, nullptr, nullptr,
+                                                                  nullptr, nullptr, 1, 0, 0, dt, nullptr, bt);
+  return 1;
+}
+
+template <typename R, int DL>
+int adj_batch_t(const OnchipPlan* oc, const OcBatch& bt, double dt, const XArgs& xa, cudaStream_t st) {
+  auto kern = oc->h->allpar ? k_oc_adj<R, DL, true> : k_oc_adj<R, DL, false>;
+  smem_limit_once<k_oc_adj<R, DL, true>>();
+  smem_limit_once<k_oc_adj<R, DL, false>>();
+  OcArgs oa = oc->oa;
+  oa.wlim = 1 << 22;
+  if (const char* e = std::getenv("SG_TEST_WAIT_LIMIT")) oa.wlim = std::max(1, atoi(e));
+  oa.skip_first = 0;
+  kern<<<bt.nsys * oa.ncta, kST, oc->sm_adj, st>>>(oc->h->pass[0], oa, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                   nullptr, 0, 0, dt, xa, nullptr, nullptr, 0, nullptr, nullptr, bt);
   return 1;
 }
 
@@ -1206,15 +1321,193 @@ int adj_t(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double
     }                                                                                       \
   } while (0)
 
+// ---------------------------------------------------------------------------
+// batcher
+// ---------------------------------------------------------------------------
+namespace {
+
+struct OcPending {
+  int kind;                     // 0 forward, 1 adjoint
+  const OnchipPlan* oc;
+  OcSys d;
+  double dt;
+  const XArgs* xa;              // adjoint: the plan's structural arguments
+  cudaEvent_t ready, done;
+};
+
+thread_local OcBatcher* tl_batcher = nullptr;
+thread_local cudaEvent_t tl_ready = nullptr, tl_done = nullptr;
+
+// Two pending launches can share a batched launch: same kernel, plan shape and step.
+bool oc_compatible(const OcPending& a, const OcPending& b) {
+  if (a.kind != b.kind || a.dt != b.dt) return false;
+  const OnchipPlan* x = a.oc;
+  const OnchipPlan* y = b.oc;
+  if (x == y) return true;
+  if (a.kind == 1 && a.xa->ham != b.xa->ham) return false;
+  return x->sig == y->sig && x->sm_fwd == y->sm_fwd && x->sm_adj == y->sm_adj;
+}
+
+template <typename R, int DL>
+int batch_launch_t(const OnchipPlan* oc, int kind, const OcBatch& bt, double dt, const XArgs* xa, cudaStream_t st) {
+  return kind == 0 ? fwd_batch_t<R, DL>(oc, bt, dt, st) : adj_batch_t<R, DL>(oc, bt, dt, *xa, st);
+}
+int batch_launch(const OnchipPlan* oc, int kind, const OcBatch& bt, double dt, const XArgs* xa, cudaStream_t st) {
+  OC_DISPATCH(batch_launch_t, oc, kind, bt, dt, xa, st);
+}
+
+}  // namespace
+
+struct OcBatcher {
+  int device = 0;
+  cudaStream_t st = nullptr;
+  std::mutex mu;
+  std::condition_variable cv;
+  int participants = 0;
+  std::vector<OcPending*> subs;
+  unsigned long long gen = 0;
+  long long launches = 0, members = 0;
+
+  // Called with mu held once every participant has handed over a launch: groups
+  // them into compatible batches and issues each on st after its members' earlier
+  // work, with each member's done event after its batch.
+  void launch_round() {
+    std::vector<bool> taken(subs.size(), false);
+    for (size_t i = 0; i < subs.size(); ++i) {
+      if (taken[i]) continue;
+      std::vector<OcPending*> grp;
+      for (size_t j = i; j < subs.size() && (int)grp.size() < kOcMaxBatch; ++j)
+        if (!taken[j] && oc_compatible(*subs[i], *subs[j])) { taken[j] = true; grp.push_back(subs[j]); }
+      OcBatch bt{};
+      bt.nsys = (int)grp.size();
+      for (int b = 0; b < bt.nsys; ++b) {
+        cudaStreamWaitEvent(st, grp[b]->ready, 0);
+        bt.s[b] = grp[b]->d;
+      }
+      batch_launch(grp[0]->oc, grp[0]->kind, bt, grp[0]->dt, grp[0]->xa, st);
+      for (OcPending* m : grp) cudaEventRecord(m->done, st);
+      ++launches;
+      members += bt.nsys;
+    }
+    subs.clear();
+    ++gen;
+    cv.notify_all();
+  }
+
+  int submit(const OcPending& p0, cudaStream_t user) {
+    OcPending p = p0;
+    p.ready = tl_ready;
+    p.done = tl_done;
+    cudaEventRecord(p.ready, user);
+    std::unique_lock<std::mutex> lk(mu);
+    subs.push_back(&p);
+    const unsigned long long g = gen;
+    if ((int)subs.size() >= participants) launch_round();
+    else cv.wait(lk, [&] { return gen != g; });
+    lk.unlock();
+    cudaStreamWaitEvent(user, p.done, 0);
+    return 1;
+  }
+};
+
+OcBatcher* onchip_batcher_create(int device) {
+  OcBatcher* b = new OcBatcher();
+  b->device = device;
+  cudaSetDevice(device);
+  if (cudaStreamCreateWithFlags(&b->st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete b;
+    return nullptr;
+  }
+  return b;
+}
+
+void onchip_batcher_destroy(OcBatcher* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->st);
+  cudaStreamDestroy(b->st);
+  delete b;
+}
+
+void onchip_batcher_join(OcBatcher* b, int n) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  b->participants += n;
+}
+
+void onchip_batcher_bind(OcBatcher* b) {
+  cudaEventCreateWithFlags(&tl_ready, cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&tl_done, cudaEventDisableTiming);
+  tl_batcher = b;
+}
+
+void onchip_batcher_release() {
+  OcBatcher* b = tl_batcher;
+  if (!b) return;
+  {
+    std::lock_guard<std::mutex> lk(b->mu);
+    --b->participants;
+    if (!b->subs.empty() && (int)b->subs.size() >= b->participants) b->launch_round();
+  }
+  cudaEventDestroy(tl_ready);
+  cudaEventDestroy(tl_done);
+  tl_ready = tl_done = nullptr;
+  tl_batcher = nullptr;
+}
+
+void onchip_batcher_stats(const OcBatcher* b, long long* launches, long long* members) {
+  OcBatcher* m = const_cast<OcBatcher*>(b);
+  std::lock_guard<std::mutex> lk(m->mu);
+  if (launches) *launches = m->launches;
+  if (members) *members = m->members;
+}
+
 int onchip_forward(const OnchipPlan* oc, const void* tab, const double2* psi_api, const double2* img_in,
                    double2* psi_out, double2* ck_out, int K, int n0, int n1, double dt, void* segY,
                    cudaStream_t st) {
+  if (tl_batcher) {
+    OcPending p{};
+    p.kind = 0;
+    p.oc = oc;
+    p.dt = dt;
+    p.d.tab = tab;
+    p.d.psi_api = psi_api;
+    p.d.img_in = img_in;
+    p.d.psi_out = psi_out;
+    p.d.ck_out = ck_out;
+    p.d.segY = segY;
+    p.d.K = std::max(1, K);
+    p.d.n0 = n0;
+    p.d.n1 = n1;
+    return tl_batcher->submit(p, st);
+  }
   OC_DISPATCH(fwd_t, oc, tab, psi_api, img_in, psi_out, ck_out, K, n0, n1, dt, segY, st);
 }
 
 int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* segY, double2* pbar_img, int n0,
                    int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
                    void* colow, cudaStream_t st) {
+  if (tl_batcher) {
+    OcPending p{};
+    p.kind = 1;
+    p.oc = oc;
+    p.dt = dt;
+    p.xa = &xa;
+    p.d.tab = tb.tab;
+    p.d.coef = tb.coef;
+    p.d.ph = tb.ph;
+    p.d.opd = tb.opd;
+    p.d.segY = const_cast<void*>(segY);
+    p.d.pbar_img = pbar_img;
+    p.d.gF_cta = gF_cta;
+    p.d.acc_cta = acc_cta;
+    p.d.err = err;
+    p.d.pblo = colow;
+    p.d.J = xa.Jdev;
+    p.d.nstK = (long long)nst * std::max(1, oc->oa.K);
+    p.d.n0 = n0;
+    p.d.n1 = n1;
+    return tl_batcher->submit(p, st);
+  }
   OC_DISPATCH(adj_t, oc, tb, segY, pbar_img, n0, n1, dt, xa, nst, gF_cta, acc_cta, err, colow, st);
 }
 

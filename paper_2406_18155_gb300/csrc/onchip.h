@@ -62,6 +62,8 @@ int onchip_adjoint(const OnchipPlan* oc, const OnchipTables& tb, const void* seg
                    int n1, double dt, const XArgs& xa, int nst, double* gF_cta, double* acc_cta, int* err,
                    void* colow, cudaStream_t st);
 bool onchip_colow_global(const OnchipPlan* oc);
+
+#include "batcher.h"
 // The RK4 forward kernel fits (a plan may hold only the Q2 layout).
 bool onchip_forward_ok(const OnchipPlan* oc);
 // Element-wise FP64 -> FP32 copy (tables for the mixed-precision adjoint).

@@ -10,6 +10,7 @@
 // solve uses only its own buffers and fixed-order reductions.
 #include <cstdio>
 #include "sg_internal.h"
+#include "batcher.h"
 #include <algorithm>
 #include <cmath>
 #include <atomic>
@@ -21,6 +22,8 @@
 #include <thread>
 
 namespace {
+
+constexpr int kServerMaxBatch = 16;
 
 double now_s(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -41,7 +44,30 @@ struct Req {
   std::vector<double> gp, gh;
   double submit_s = 0, start_s = 0, done_s = 0;
   std::string error;
+  std::string shape;             // requests of one shape may share batched launches
 };
+
+// The step shape of a request: everything its on-chip launches' plan and kernels
+// depend on (modes and level counts, terms and their operators, drives and their
+// envelope kinds, columns, precision, frame, step), not the parameter values or T.
+std::string shape_key(const sg_system* sys, const sg_evolve_opts& o, const std::vector<long long>& cols, int kind,
+                      int want_grad) {
+  std::string k;
+  auto add = [&](long long v) { k += std::to_string(v); k += ','; };
+  add((long long)sys->modes.size());
+  for (const HostMode& m : sys->modes) { add(m.kind); add(m.d); add(m.coupler); add((long long)m.local.size()); }
+  add((long long)sys->couplings.size());
+  for (const HostCoupling& c : sys->couplings) { add(c.a); add(c.op_a); add(c.b); add(c.op_b); }
+  add((long long)sys->drives.size());
+  for (const HostDrive& d : sys->drives) { add(d.mode); add(d.op); add(d.kind); add(d.nseg); }
+  add((long long)sys->collapses.size());
+  for (long long c : cols) add(c);
+  add(o.precision); add(o.frame); add(o.solver); add(o.compensation); add(o.basis); add(kind); add(want_grad);
+  char dt[40];
+  std::snprintf(dt, sizeof dt, "%.17g", o.dt);
+  k += dt;
+  return k;
+}
 
 size_t estimate_bytes(const sg_system* sys, const sg_evolve_opts& o, int want_grad) {
   long long D = 1;
@@ -66,6 +92,13 @@ struct sg_server {
   sg_ctx* ctx = nullptr;
   size_t budget = 0;
   int max_slots = 1;
+  // packing: a slot takes up to max_batch queued requests of one shape and runs them
+  // together, their on-chip launches batched by the slot's batcher on its own stream;
+  // bctx[w] holds the streams of the slot's other members
+  int max_batch = 1;
+  std::vector<OcBatcher*> batchers;
+  std::vector<std::vector<sg_ctx*>> bctx;
+  long long batches = 0, batched_requests = 0;
   std::chrono::steady_clock::time_point t0;
   std::mutex mu;
   std::condition_variable cv, done_cv;
@@ -85,10 +118,30 @@ struct sg_server {
   double first_start = -1, last_done = 0;
   double busy_accum = 0, busy_since = -1;
 
+  // One request's solve on context c (its stream), through batcher bt when non-null.
+  void run_one(sg_ctx* c, Req* r, OcBatcher* bt) {
+    if (bt) onchip_batcher_bind(bt);
+    sg_ctx* saved = r->sys->ctx;
+    r->sys->ctx = c;
+    sg_status rc = SG_OK;
+    if (!r->sys->prepared) rc = sg_prepare_impl(r->sys);
+    int np = 0, nh = 0;
+    sg_param_counts(r->sys, &np, &nh);
+    r->gp.assign(std::max(1, np), 0.0);
+    r->gh.assign(std::max(1, nh), 0.0);
+    if (rc == SG_OK)
+      rc = sg_fidelity_impl(r->sys, &r->opts, r->target.data(), r->kind, r->F, nullptr,
+                            r->want_grad != 0, r->gp.data(), r->gh.data(), 0);
+    onchip_batcher_release();                   // every exit path leaves the batch
+    r->sys->ctx = saved;
+    r->status = rc;
+    if (rc != SG_OK) r->error = c->last_error;
+  }
+
   void worker(int w) {
     sg_ctx* c = wctx[w];
     for (;;) {
-      Req* r = nullptr;
+      std::vector<Req*> batch;
       {
         std::unique_lock<std::mutex> lk(mu);
         cv.wait(lk, [&] {
@@ -96,41 +149,65 @@ struct sg_server {
           return !queue.empty() && mem_in_use + queue.front()->mem <= budget;
         });
         if (stop) return;
-        r = queue.front();
+        Req* r0 = queue.front();
         queue.pop_front();
-        r->state = 1;
-        mem_in_use += r->mem;
-        if (active == 0) busy_since = now_s(t0);
-        ++active;
-        r->start_s = now_s(t0);
-        if (first_start < 0) first_start = r->start_s;
+        batch.push_back(r0);
+        mem_in_use += r0->mem;
+        // same-shape requests queued behind it join its batch while memory allows,
+        // those with the step count closest to its own first (a shared launch runs
+        // to its longest member's end)
+        if (max_batch > 1) {
+          std::vector<std::pair<double, Req*>> cand;
+          const double n0 = r0->opts.T / r0->opts.dt;
+          for (Req* r : queue)
+            if (r->shape == r0->shape) cand.push_back({std::fabs(r->opts.T / r->opts.dt - n0), r});
+          std::stable_sort(cand.begin(), cand.end(),
+                           [](const std::pair<double, Req*>& a, const std::pair<double, Req*>& b) {
+                             return a.first < b.first;
+                           });
+          for (const auto& c : cand) {
+            if ((int)batch.size() >= max_batch) break;
+            if (mem_in_use + c.second->mem > budget) continue;
+            batch.push_back(c.second);
+            mem_in_use += c.second->mem;
+            queue.erase(std::find(queue.begin(), queue.end(), c.second));
+          }
+        }
+        const double t = now_s(t0);
+        if (active == 0) busy_since = t;
+        active += (int)batch.size();
+        if (first_start < 0) first_start = t;
+        for (Req* r : batch) { r->state = 1; r->start_s = t; }
+        if (batch.size() > 1) { ++batches; batched_requests += (long long)batch.size(); }
       }
-      // run the solve on this worker's stream
-      sg_ctx* saved = r->sys->ctx;
-      r->sys->ctx = c;
-      sg_status rc = SG_OK;
-      if (!r->sys->prepared) rc = sg_prepare_impl(r->sys);
-      int np = 0, nh = 0;
-      sg_param_counts(r->sys, &np, &nh);
-      r->gp.assign(std::max(1, np), 0.0);
-      r->gh.assign(std::max(1, nh), 0.0);
-      if (rc == SG_OK)
-        rc = sg_fidelity_impl(r->sys, &r->opts, r->target.data(), r->kind, r->F, nullptr,
-                              r->want_grad != 0, r->gp.data(), r->gh.data(), 0);
-      r->sys->ctx = saved;
+      if (batch.size() == 1) {
+        run_one(c, batch[0], nullptr);
+      } else {
+        OcBatcher* bt = batchers[w];
+        onchip_batcher_join(bt, (int)batch.size());
+        std::vector<std::thread> th;
+        for (size_t i = 1; i < batch.size(); ++i)
+          th.emplace_back([this, w, i, bt, &batch] {
+            cudaSetDevice(bctx[w][i - 1]->device);
+            run_one(bctx[w][i - 1], batch[i], bt);
+          });
+        run_one(c, batch[0], bt);
+        for (auto& t : th) t.join();
+      }
       {
         std::lock_guard<std::mutex> lk(mu);
-        r->status = rc;
-        if (rc != SG_OK) r->error = c->last_error;
-        r->done_s = now_s(t0);
-        r->state = 2;
-        mem_in_use -= r->mem;
-        --active;
-        if (active == 0 && busy_since >= 0) { busy_accum += r->done_s - busy_since; busy_since = -1; }
-        ++completed;
-        inflight.erase(r->sys);
-        latencies.push_back(r->done_s - r->submit_s);
-        last_done = r->done_s;
+        const double t = now_s(t0);
+        for (Req* r : batch) {
+          r->done_s = t;
+          r->state = 2;
+          mem_in_use -= r->mem;
+          --active;
+          ++completed;
+          inflight.erase(r->sys);
+          latencies.push_back(r->done_s - r->submit_s);
+        }
+        if (active == 0 && busy_since >= 0) { busy_accum += t - busy_since; busy_since = -1; }
+        last_done = t;
       }
       cv.notify_all();
       done_cv.notify_all();
@@ -176,7 +253,39 @@ sg_status sg_server_destroy(sg_server* srv) {
   srv->cv.notify_all();
   for (auto& t : srv->workers) t.join();
   for (sg_ctx* c : srv->wctx) { cudaStreamSynchronize(c->stream); cudaStreamDestroy(c->stream); delete c; }
+  for (auto& v : srv->bctx)
+    for (sg_ctx* c : v) { cudaStreamSynchronize(c->stream); cudaStreamDestroy(c->stream); delete c; }
+  for (OcBatcher* b : srv->batchers) onchip_batcher_destroy(b);
   delete srv;
+  return SG_OK;
+}
+
+sg_status sg_server_set_batch(sg_server* srv, int max_batch) {
+  if (!srv) return SG_E_INVALID;
+  if (max_batch < 1 || max_batch > kServerMaxBatch)
+    return sg_fail(srv->ctx, SG_E_INVALID, "max_batch must be 1.." + std::to_string(kServerMaxBatch));
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->submitted > srv->completed + srv->cancelled + srv->rejected)
+    return sg_fail(srv->ctx, SG_E_STATE, "set the batch size while no request is queued or running");
+  cudaSetDevice(srv->ctx->device);
+  if (srv->batchers.empty()) srv->batchers.assign(srv->max_slots, nullptr);
+  srv->bctx.resize(srv->max_slots);
+  for (int w = 0; w < srv->max_slots; ++w) {
+    if (max_batch > 1 && !srv->batchers[w]) {
+      srv->batchers[w] = onchip_batcher_create(srv->ctx->device);
+      if (!srv->batchers[w]) return sg_fail(srv->ctx, SG_E_CUDA, "stream creation for the batched launches failed");
+    }
+    while ((int)srv->bctx[w].size() < max_batch - 1) {
+      sg_ctx* c = new sg_ctx();
+      c->device = srv->ctx->device;
+      if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return sg_fail(srv->ctx, SG_E_CUDA, "cudaStreamCreate failed");
+      }
+      srv->bctx[w].push_back(c);
+    }
+  }
+  srv->max_batch = max_batch;
   return SG_OK;
 }
 
@@ -210,6 +319,7 @@ sg_status sg_server_submit(sg_server* srv, const sg_request* req, uint64_t* tick
   const size_t dc = (size_t)1 << nqb;
   r->target.assign(req->target_re_im, req->target_re_im + 2 * dc * dc);
   r->mem = estimate_bytes(req->sys, r->opts, req->want_grad);
+  r->shape = shape_key(req->sys, r->opts, r->cols, r->kind, r->want_grad);
   std::lock_guard<std::mutex> lk(srv->mu);
   if (srv->inflight.count(req->sys))
     return sg_fail(srv->ctx, SG_E_STATE, "this system already has a request queued or running in the server; "
@@ -310,6 +420,18 @@ sg_status sg_server_stats(sg_server* srv, sg_stats* out) {
   out->mem_budget = srv->budget;
   out->active_slots = srv->active;
   out->max_slots = srv->max_slots;
+  out->batches = srv->batches;
+  out->batched_requests = srv->batched_requests;
+  long long bl = 0, bm = 0;
+  for (OcBatcher* b : srv->batchers) {
+    if (!b) continue;
+    long long l = 0, m = 0;
+    onchip_batcher_stats(b, &l, &m);
+    bl += l;
+    bm += m;
+  }
+  out->batched_launches = bl;
+  out->batched_launch_members = bm;
   return SG_OK;
 }
 

@@ -233,14 +233,18 @@ def fluxonium_ring10(seed=0, T=40.0, dt=0.01, ncols=16):
                            ring=True, ncols=ncols)
 
 
-def serving_request(rng, dt=0.01):
+def serving_request(rng, dt=0.01, nq=None, kind=None, levels=None):
     """One request of the serving stream: 2-5 coupled transmons or fluxoniums
     (one kind per request), 3-5 levels, T ~ U[20, 200] ns rounded to whole
     steps, 10-segment random drives on every qubit, all computational states,
-    Haar target, fidelity plus gradient."""
-    nq = int(rng.integers(2, 6))
-    kind = "transmon" if rng.integers(0, 2) == 0 else "fluxonium"
-    levels = int(rng.integers(3, 6))
+    Haar target, fidelity plus gradient.  nq, kind and levels fix the request's
+    shape (the same random draws are made either way)."""
+    nq_draw = int(rng.integers(2, 6))
+    kind_draw = "transmon" if rng.integers(0, 2) == 0 else "fluxonium"
+    levels_draw = int(rng.integers(3, 6))
+    nq = nq_draw if nq is None else nq
+    kind = kind_draw if kind is None else kind
+    levels = levels_draw if levels is None else levels
     nsteps = int(round(rng.uniform(20.0, 200.0) / dt))
     T = nsteps * dt
     if kind == "transmon":

@@ -82,6 +82,44 @@ def test_server_results_alone_equal_results_in_the_mix(sgctx):
     srv.close()
 
 
+def test_server_packs_same_shape_requests_into_batched_launches(sgctx):
+    # one slot packing up to 4 queued requests of one step shape (3 fluxoniums at 3
+    # levels; different parameters, pulses and durations) into shared batched
+    # on-chip launches, beside requests of other shapes: every result equals the
+    # request's solve alone
+    from paper_2406_18155_gb300.api import Server
+    rng = np.random.Generator(np.random.PCG64(7))
+    wls = []
+    for i in range(9):
+        shape = dict(nq=3, kind="fluxonium", levels=3) if i % 3 != 2 else dict(nq=2, kind="transmon", levels=4)
+        wl = W.serving_request(rng, **shape)
+        n = int(round(rng.uniform(0.2, 0.6) / wl["dt"]))
+        wl["T"] = n * wl["dt"]
+        for d in wl["drives"]:
+            d["length"] = wl["T"]
+        wls.append(wl)
+    alone = []
+    for wl in wls:
+        s = _system(sgctx, wl)
+        alone.append(s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                                     kind=wl["fid_kind"], precision="mixed"))
+    srv = Server(sgctx, mem_budget_bytes=8 << 30, max_slots=1, max_batch=4)
+    systems = [_system(sgctx, wl) for wl in wls]
+    tickets = [srv.submit(sy, wl["T"], wl["dt"], wl["target"], wl["col_index"],
+                          kind=wl["fid_kind"], precision="mixed") for sy, wl in zip(systems, wls)]
+    res = [srv.wait(t) for t in tickets]
+    for (F, gp, gh), r in zip(alone, res):
+        assert r["status"] == 0, r["error"]
+        assert abs(r["F"][1] - F[1]) <= 1e-12 and abs(r["F"][0] - F[0]) <= 1e-12
+        assert np.max(np.abs(r["grad_pulse"] - gp)) <= 1e-12 * max(1.0, np.max(np.abs(gp)))
+        assert np.max(np.abs(r["grad_ham"] - gh)) <= 1e-12 * max(1.0, np.max(np.abs(gh)))
+    st = srv.stats()
+    assert st["completed"] == len(wls)
+    assert st["batches"] >= 1 and st["batched_requests"] >= 2
+    assert st["batched_launches"] >= 1 and st["batched_launch_members"] > st["batched_launches"]
+    srv.close()
+
+
 def test_server_concurrent_shapes_sharing_kernels(sgctx):
     # every 3-level request (2..5 modes, both kinds) launches the same kernels with
     # different shared-memory sizes; many run at once, none may fail or change
