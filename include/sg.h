@@ -186,7 +186,7 @@ typedef struct {
   int ncols;                    /* S, number of evolved columns                           */
   const long long* col_index;   /* host, S flat initial basis indices, or NULL: the
                                    columns of psi are the initial states                  */
-  int solver;                   /* SG_SOLVER_RK4 (0, default), _Q2, _Q4 or _Q4J            */
+  int solver;                   /* SG_SOLVER_RK4 (0, default), _Q1, _Q2, _Q4 or _Q4J       */
   int compensation;             /* SG_COMP_NONE (0, default) or SG_COMP_VZ (fidelities)    */
   int basis;                    /* SG_BASIS_PRODUCT (0, default) or SG_BASIS_DRESSED        */
 } sg_evolve_opts;
@@ -212,7 +212,11 @@ enum { SG_BASIS_PRODUCT = 0, SG_BASIS_DRESSED = 1 };
  * gradient is that of F at the found phases (F is stationary in them). */
 enum { SG_COMP_NONE = 0, SG_COMP_VZ = 1 };
 
-/* Solvers.  SG_SOLVER_Q2: the second-order Suzuki-Trotter product of Sec. 2.3 and
+/* Solvers.  SG_SOLVER_Q1: the first-order Suzuki-Trotter product of Sec. 2.3 and App. A,
+ * Q1(dt) = prod_k exp(-i H_k dt) over the same local terms in the same order (the first
+ * acts first), the time-dependent terms at the step's midpoint; evolution and fidelity
+ * only (sg_fidelity_grad returns SG_E_UNSUPPORTED).  SG_SOLVER_Q2: the second-order
+ * Suzuki-Trotter product of Sec. 2.3 and
  * App. A, Q2(dt) = prod_k exp(-i H_k dt/2) prod_k' exp(-i H_k' dt/2) (k' reversed)
  * over the local terms H_i = diag(E^(i)) + sum_{drives on i} f(t) O (every mode, in mode
  * order) and J A (x) B (the couplings, in order), with the time-dependent terms at the
@@ -229,7 +233,7 @@ enum { SG_COMP_NONE = 0, SG_COMP_VZ = 1 };
  * checkpoints), dU/df by the Frechet derivative of the local exponential; it needs >= 2
  * modes, <= 16 drives, <= 32 couplings and four state images of a CTA's columns in
  * shared memory (mixed precision fits D = 4096, FP64 does not). */
-enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q2 = 2, SG_SOLVER_Q4 = 4, SG_SOLVER_Q4J = 5 };
+enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q1 = 1, SG_SOLVER_Q2 = 2, SG_SOLVER_Q4 = 4, SG_SOLVER_Q4J = 5 };
 
 /* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev
  * (device, D*S complex128, column innermost).  If opts->col_index is NULL psi_dev

@@ -1,7 +1,11 @@
-"""Suzuki-Trotter evolution, orders 2 and 4 (oracle; test infrastructure).
+"""Suzuki-Trotter evolution, orders 1, 2 and 4 (oracle; test infrastructure).
 
 The paper's own solver (Sec. 2.3, App. A): the evolution over one step of length
-dt is approximated by the palindromic product of local exponentials
+dt is approximated by the first-order product of local exponentials
+
+    Q1(dt) = prod_{k=1..K} exp(-i H_k dt)
+
+or by the palindromic one
 
     Q2(dt) = prod_{k=1..K} exp(-i H_k dt/2)  prod_{k=K..1} exp(-i H_k dt/2),
 
@@ -18,6 +22,8 @@ Readings taken here (the paper does not fix them):
   terms are the couplings J_e A_e (x) B_e (time independent);
 * the terms are ordered 1-body in mode order, then the couplings in term order;
   the first factor in that order acts on the state first;
+* Q1 applies the terms once each, in that order, over the full step, with the
+  time-dependent terms at the step's midpoint t_n + dt/2;
 * a time-dependent term is evaluated at the midpoint of its Q2 sub-step: for a
   sub-step c dt that starts after the fraction s of the step, at t_n + (s + c/2) dt
   (Q2: t_n + dt/2, which keeps the product second order; Q4: t_n + {p/2, 1/2,
@@ -110,13 +116,21 @@ def local_terms(sys, n, tau=0.5):
 
 
 def q2_evolve(sys, psi0, nsteps=None, scheme="q2"):
-    """Lab-frame columns after N steps of the scheme ("q2", "q4", "q4j") from the
-    columns psi0 (D x S): per step, its Q2 sub-steps in order."""
+    """Lab-frame columns after N steps of the scheme ("q1", "q2", "q4", "q4j") from the
+    columns psi0 (D x S): per step, Q1's product once, or the Q2 sub-steps in order."""
     N = sys.N if nsteps is None else nsteps
     dt = sys.dt
     S = psi0.shape[1]
     psi = np.array(psi0, dtype=np.complex128).reshape(list(sys.dims) + [S])
     _, two = local_terms(sys, 0)
+    if scheme == "q1":
+        for n in range(N):
+            one, _ = local_terms(sys, n, 0.5)
+            for i, H in enumerate(one):
+                psi = _apply_1body(psi, expm(-1j * H * dt), i)
+            for a, b, M in two:
+                psi = _apply_2body(psi, expm(-1j * M * dt), a, b, sys.dims[a], sys.dims[b])
+        return psi.reshape(sys.D, S)
     for n in range(N):
         for c, tau in SCHEMES[scheme]:
             one, _ = local_terms(sys, n, tau)

@@ -51,7 +51,8 @@ class Context:
             pass
 
 
-_SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q2": capi.SG_SOLVER_Q2, "q4": capi.SG_SOLVER_Q4, "q4j": capi.SG_SOLVER_Q4J}
+_SOLVER = {"rk4": capi.SG_SOLVER_RK4, "q1": capi.SG_SOLVER_Q1, "q2": capi.SG_SOLVER_Q2, "q4": capi.SG_SOLVER_Q4,
+           "q4j": capi.SG_SOLVER_Q4J}
 _COMP = {"none": capi.SG_COMP_NONE, "vz": capi.SG_COMP_VZ}
 _BASIS = {"product": capi.SG_BASIS_PRODUCT, "dressed": capi.SG_BASIS_DRESSED}
 
@@ -258,7 +259,7 @@ class System:
     def evolve(self, T, dt, precision="mixed", frame="interaction", col_index=None, psi=None, solver="rk4"):
         """Lab-frame columns after T, as a (D, S) complex128 torch tensor on the device.
         Starts from basis states col_index, or from the given device tensor psi.
-        solver: "rk4", or the Suzuki-Trotter "q2", "q4", "q4j" (App. A; lab frame)."""
+        solver: "rk4", or the Suzuki-Trotter "q1", "q2", "q4", "q4j" (App. A; lab frame)."""
         import torch
         D, _ = self.dims()
         if psi is None:

@@ -12,7 +12,7 @@ LIB_PATH = os.path.join(HERE, "libsupergpu.so")
 
 SG_OK = 0
 SG_E_INVALID, SG_E_NOMEM, SG_E_STATE, SG_E_CUDA, SG_E_TIMEOUT = -1, -2, -3, -4, -5
-SG_SOLVER_RK4, SG_SOLVER_Q2, SG_SOLVER_Q4, SG_SOLVER_Q4J = 0, 2, 4, 5
+SG_SOLVER_RK4, SG_SOLVER_Q1, SG_SOLVER_Q2, SG_SOLVER_Q4, SG_SOLVER_Q4J = 0, 1, 2, 4, 5
 SG_COMP_NONE, SG_COMP_VZ = 0, 1
 SG_BASIS_PRODUCT, SG_BASIS_DRESSED = 0, 1
 SG_E_PENDING, SG_E_NOMEM_RETRY, SG_E_CANCELLED, SG_E_NOTFOUND, SG_E_UNSUPPORTED = -6, -7, -8, -9, -10

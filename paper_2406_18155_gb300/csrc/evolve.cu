@@ -66,6 +66,7 @@ struct TabArgs {
   // its time-dependent terms at t_n + tau[j] dt (complex for Q4j) and its coupling
   // unitaries from set set_of[j]; set s has length setc[s] dt
   int nsub, nset;
+  int q1;                     // first-order product: full-step factors, each term once per step
   int set_of[3];
   double2 sc[3], tau[3], setc[3];
 };
@@ -386,10 +387,10 @@ __device__ void q2_onebody(const TabArgs& a, int i, int m, double2* U, double2* 
     const double2* O = a.opd + a.opd_off[i] + dr.op * d * d;
     for (int x = 0; x < d * d; ++x) A[x] = cfma(f, O[x], A[x]);
   }
-  const double h = a.dt * 0.5;
+  const double h = a.q1 ? a.dt : a.dt * 0.5;        // Q1: the full step
   for (int x = 0; x < d * d; ++x) {
     const double2 cH = cmul(a.sc[j], A[x]);
-    A[x] = make_double2(h * cH.y, -h * cH.x);                                     // -i c H dt/2
+    A[x] = make_double2(h * cH.y, -h * cH.x);                                     // -i c H dt/2 (Q1: dt)
   }
   expm_serial(A, d, U, W1, W2);
 }
@@ -407,6 +408,17 @@ __global__ void k_q2_onebody(TabArgs a, int DL, double2* __restrict__ rows) {
     if (m == M) {
       q2_onebody(a, i, 0, U0, A, W1, W2);
       for (int y = 0; y < d * d; ++y) out[y] = U0[y];
+      continue;
+    }
+    if (a.q1) {
+      // Q1: row M is step 0's 1-body factor, applied first; row m < M - 1 step m + 1's,
+      // applied after step m's couplings; row M - 1 the identity
+      if (m == M - 1) {
+        for (int y = 0; y < d * d; ++y) out[y] = make_double2(y % (d + 1) == 0 ? 1.0 : 0.0, 0.0);
+      } else {
+        q2_onebody(a, i, m + 1, U0, A, W1, W2);
+        for (int y = 0; y < d * d; ++y) out[y] = U0[y];
+      }
       continue;
     }
     q2_onebody(a, i, m, U0, A, W1, W2);
@@ -1430,6 +1442,7 @@ void set_schedule(int solver, TabArgs& ta) {
     ta.tau[0] = make_double2(0.5, 0.0);
     ta.set_of[0] = 0;
   }
+  ta.q1 = solver == SG_SOLVER_Q1 ? 1 : 0;
 }
 
 sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
@@ -1446,9 +1459,10 @@ sg_status build_setup(sg_system* sys, const sg_evolve_opts* o, Setup& s) {
     return sg_fail(ctx, SG_E_INVALID, "precision must be SG_FP64 or SG_MIXED");
   if (o->frame != SG_FRAME_INTERACTION && o->frame != SG_FRAME_LAB)
     return sg_fail(ctx, SG_E_INVALID, "frame must be SG_FRAME_INTERACTION or SG_FRAME_LAB");
-  if (o->solver != SG_SOLVER_RK4 && o->solver != SG_SOLVER_Q2 && o->solver != SG_SOLVER_Q4 &&
-      o->solver != SG_SOLVER_Q4J)
-    return sg_fail(ctx, SG_E_INVALID, "solver must be SG_SOLVER_RK4, SG_SOLVER_Q2, SG_SOLVER_Q4 or SG_SOLVER_Q4J");
+  if (o->solver != SG_SOLVER_RK4 && o->solver != SG_SOLVER_Q1 && o->solver != SG_SOLVER_Q2 &&
+      o->solver != SG_SOLVER_Q4 && o->solver != SG_SOLVER_Q4J)
+    return sg_fail(ctx, SG_E_INVALID, "solver must be SG_SOLVER_RK4, SG_SOLVER_Q1, SG_SOLVER_Q2, SG_SOLVER_Q4 or "
+                                      "SG_SOLVER_Q4J");
   s.solver = o->solver;
   s.q2 = o->solver != SG_SOLVER_RK4;
   s.frame = s.q2 ? SG_FRAME_LAB : o->frame;          // Suzuki-Trotter always runs in the lab frame
@@ -2186,7 +2200,7 @@ sg_status run_q2(sg_system* sys, Solve& sv, const long long* cols_dev, bool init
     ++sv.launches;
   }
   sg_status rc = onchip_q2_forward(sv.oc, s.p, sv.q2rows, sv.q2edges, sv.psi, sv.psi, s.N * s.ta.nsub, s.ta.nsub,
-                                   s.ta.set_of, s.ta.nset, st, &sv.launches);
+                                   s.ta.set_of, s.ta.nset, st, &sv.launches, s.ta.q1 != 0);
   if (rc != SG_OK) return sg_fail(ctx, rc, "the Suzuki-Trotter solvers support at most 16 modes and 32 couplings");
   SG_CUDA_TRY(ctx, cudaGetLastError());
   return SG_OK;
@@ -2284,6 +2298,9 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (s.q2 && grad && grad_ham)
     return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter solvers compute the pulse-parameter gradient only "
                                           "(grad_ham = NULL)");
+  if (grad && s.solver == SG_SOLVER_Q1)
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the first-order Suzuki-Trotter solver computes the evolution and the "
+                                          "fidelity only");
   for (int i = 0; i < s.nq; ++i)
     if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
       return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");

@@ -712,6 +712,7 @@ struct Q2Args {
                                   // and at the end of every step)
   int nfe;                        // coupling factors per step
   int J;                          // Q2 sub-steps per step (Q2 1, Q4 3, Q4j 2)
+  int q1;                         // first-order product: each coupling once, full step
   int setoff[3];                  // first matrix of sub-step j's coupling set: 2 ne set(j)
   Q2Factor f[kMaxQ2F];            // [0, nf0): 1-body; [nf0, nf0 + nfe): couplings in order
 };
@@ -798,11 +799,19 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
     C* const Mc = buf ? M1 : M0;
     const int so = qa.setoff[n % qa.J];
     if (n + 1 < N) issue_rows<C>(rows, rowlen, n + 1, buf ? M0 : M1, threadIdx.x, blockDim.x);
-    for (int q = 0; q < 2 * qa.nfe - 1; ++q) {
-      const int e = q < qa.nfe ? q : 2 * qa.nfe - 2 - q;             // palindrome over couplings
-      const Q2Factor& F = qa.f[qa.nf0 + e];
-      q2_apply<DL>(F, F.mat + so + (q == qa.nfe - 1 ? 1 : 0), oa, Mc, G, ys, ks);   // middle: full step
-      C* t = ys; ys = ks; ks = t;
+    if (qa.q1) {
+      for (int e = 0; e < qa.nfe; ++e) {                             // Q1: each coupling once, full step
+        const Q2Factor& F = qa.f[qa.nf0 + e];
+        q2_apply<DL>(F, F.mat + so + 1, oa, Mc, G, ys, ks);
+        C* t = ys; ys = ks; ks = t;
+      }
+    } else {
+      for (int q = 0; q < 2 * qa.nfe - 1; ++q) {
+        const int e = q < qa.nfe ? q : 2 * qa.nfe - 2 - q;           // palindrome over couplings
+        const Q2Factor& F = qa.f[qa.nf0 + e];
+        q2_apply<DL>(F, F.mat + so + (q == qa.nfe - 1 ? 1 : 0), oa, Mc, G, ys, ks);   // middle: full step
+        C* t = ys; ys = ks; ks = t;
+      }
     }
     for (int q = 0; q < qa.nf0; ++q) {
       q2_apply<DL>(qa.f[q], 0, oa, Mc, G, ys, ks);
@@ -1532,7 +1541,7 @@ int q2_t(const OnchipPlan* oc, const Q2Args& qa, const void* rows, const void* e
 
 sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
                             const double2* psi_in, double2* psi_out, int N, int J, const int* set_of, int nset,
-                            cudaStream_t st, int* launches) {
+                            cudaStream_t st, int* launches, bool q1) {
   const SlabPass& sp = oc->h->pass[0];
   const int DL = oc->h->DL;
   if (p.nq > 2 * 8 || p.ne > kMaxQ2F - 8 || J < 1 || J > 3) return SG_E_UNSUPPORTED;
@@ -1559,6 +1568,7 @@ sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* ro
     F.mat = 2 * e;                // per set and coupling: half, full
   }
   qa.J = J;
+  qa.q1 = q1 ? 1 : 0;
   for (int j = 0; j < J; ++j) qa.setoff[j] = 2 * p.ne * set_of[j];
   const int rowlen = p.nq * DL * DL;
   const int nmat = 2 * p.ne * nset;

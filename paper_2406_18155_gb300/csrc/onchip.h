@@ -78,10 +78,12 @@ void onchip_reduce(const OnchipPlan* oc, const double* gF_cta, const double* acc
 // stage precision (row N = the first half of sub-step 0; row n = the last half of
 // sub-step n followed by the first of sub-step n + 1); edges: per set s < nset and
 // coupling e the half-step and full-step d^2 x d^2 unitaries at matrix (s ne + e) 2 + {0, 1};
-// sub-step n uses set set_of[n % J].  SG_E_UNSUPPORTED beyond 16 modes or 32 couplings.
+// sub-step n uses set set_of[n % J].  q1: the first-order product instead (per step the
+// couplings once each with their full-step unitary, then the next step's full-step
+// 1-body row).  SG_E_UNSUPPORTED beyond 16 modes or 32 couplings.
 sg_status onchip_q2_forward(const OnchipPlan* oc, const KPlan& p, const void* rows, const void* edges,
                             const double2* psi_in, double2* psi_out, int N, int J, const int* set_of, int nset,
-                            cudaStream_t st, int* launches);
+                            cudaStream_t st, int* launches, bool q1 = false);
 int onchip_dl(const OnchipPlan* oc);
 // Suzuki-Trotter pulse gradient: pulls the final states psi and the co-state bar (API
 // layout, lab frame) back through every factor of the N Q2 sub-steps and adds dF/df_k

@@ -1,4 +1,4 @@
-"""GPU parity of the Suzuki-Trotter solvers (Sec. 2.3, App. A: Q2, Q4, Q4j) against
+"""GPU parity of the Suzuki-Trotter solvers (Sec. 2.3, App. A: Q1, Q2, Q4, Q4j) against
 the oracle's: lab-frame states and fidelities, FP64 within 1e-10, FP32 factors and
 state within 1e-5 on short evolutions; the pulse-parameter gradient of Q2, Q4 and
 Q4j (discrete adjoint of the product of local factors, Sec. 2.5) against the
@@ -62,6 +62,35 @@ def test_q2_matches_oracle(sgctx, default_path, name):
     assert (np.isnan(Fa) and np.isnan(Fa_r)) or abs(Fa - Fa_r) < 1e-10
     psi32 = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"], solver="q2").cpu().numpy()
     assert np.max(np.abs(psi32 - ref)) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["transmon_pair", "chain3_l3", "ring4_l3", "multipath_l4"])
+def test_q1_matches_oracle(sgctx, default_path, name):
+    # the first-order product: every term once per step over the full step
+    wl = CASES[name]()
+    s = _system(sgctx, wl)
+    so = OracleSystem(dict(wl, frame="lab"))
+    ref = q2_evolve(so, initial_columns(so, wl["col_index"]), scheme="q1")
+    psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver="q1").cpu().numpy()
+    assert np.max(np.abs(psi - ref)) < 1e-10
+    Fa_r, Fs_r, Uc_r = fidelities(so, ref)
+    Fa, Fs, Uc = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver="q1")
+    assert abs(Fs - Fs_r) < 1e-10 and np.max(np.abs(Uc - Uc_r)) < 1e-10
+    psi32 = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"], solver="q1").cpu().numpy()
+    assert np.max(np.abs(psi32 - ref)) < 1e-5
+    # Q1 and Q2 are different products of the same factors
+    q2 = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver="q2").cpu().numpy()
+    assert np.max(np.abs(q2 - psi)) > 1e-8
+
+
+def test_q1_gradient_is_refused(sgctx, default_path):
+    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
+    wl = CASES["transmon_pair"]()
+    s = _system(sgctx, wl)
+    with pytest.raises(SGError) as e:
+        s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver="q1",
+                        ham=False)
+    assert e.value.code == SG_E_UNSUPPORTED
 
 
 def test_q2_rejects_what_it_does_not_run(sgctx, default_path):

@@ -1,7 +1,8 @@
 """Pins of the oracle's Suzuki-Trotter evolutions (Sec. 2.3, App. A) against what
 the mathematics fixes: exactness when the local terms commute, the convergence
-order of Q2 (2), Q4 (4) and Q4j (3: see oracle/trotter.py), unitarity, and the
-pulse gradient against central differences."""
+order of Q1 (1), Q2 (2), Q4 (4) and Q4j (3: see oracle/trotter.py), Q2 as the
+symmetric composition of Q1 and its reverse, unitarity, and the pulse gradient
+against central differences."""
 import numpy as np
 import pytest
 from scipy.linalg import expm
@@ -154,3 +155,45 @@ def test_full_gradient_matches_central_differences_through_the_eigensolve(scheme
             vals.append(q2_fidelity(set_param_vector(wl, th), scheme=scheme))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(g[p] - fd) <= 1e-6 * max(1e-4, np.max(np.abs(g))), (prm, g[p], fd)
+
+
+def test_q1_exact_for_commuting_terms_and_first_order():
+    # uncoupled driven modes: Q1's factors commute, so a step is the exact midpoint
+    # propagator; coupled and Gaussian-driven: the error halves with dt (ratio 2)
+    wl = W.fluxonium_pair_multipath(seed=2, levels=3, nseg=4)
+    wl["couplings"] = []
+    wl = _lab(wl, 0.2, 0.01)
+    sys = OracleSystem(wl)
+    got = q2_evolve(sys, initial_columns(sys, range(sys.D)), scheme="q1")
+    U = np.eye(sys.D, dtype=complex)
+    for n in range(sys.N):
+        U = expm(-1j * sys.hamiltonian(n, 1) * sys.dt) @ U
+    assert np.max(np.abs(got - U)) < 1e-12
+    base = W.transmon_pair(seed=4)
+    base["modes"] = [dict(m, levels=3) for m in base["modes"]]
+    base["col_index"] = list(range(9))
+    ref = _converged_reference(base, 1.0)
+    e1 = _errors(base, 1.0, ref, "q1", (0.01, 0.005, 0.0025))
+    assert 1.8 < e1[0] / e1[1] < 2.2 and 1.8 < e1[1] / e1[2] < 2.2, e1
+    e2 = _errors(base, 1.0, ref, "q2", (0.01,))
+    assert e2[0] < e1[0]
+
+
+def test_q2_is_q1_then_its_reverse_at_half_steps():
+    # with time-independent terms, Q2(dt) = Q1rev(dt/2) Q1(dt/2): Q1 over half a step,
+    # then the same factors in reverse order (App. A's symmetric composition)
+    wl = W.fluxonium_pair_multipath(seed=3, levels=3, nseg=4)
+    wl["drives"] = []
+    wl = _lab(wl, 0.02, 0.01)
+    sys = OracleSystem(wl)
+    psi0 = initial_columns(sys, range(sys.D))
+    q2 = q2_evolve(sys, psi0, nsteps=1, scheme="q2")
+    half = OracleSystem(dict(wl, dt=0.005, T=0.005))
+    psi = q2_evolve(half, psi0, nsteps=1, scheme="q1").reshape(list(sys.dims) + [sys.D])
+    from oracle.trotter import local_terms, _apply_1body, _apply_2body
+    one, two = local_terms(half, 0)
+    for a, b, M in reversed(two):
+        psi = _apply_2body(psi, expm(-1j * M * 0.005), a, b, sys.dims[a], sys.dims[b])
+    for i in reversed(range(sys.nq)):
+        psi = _apply_1body(psi, expm(-1j * one[i] * 0.005), i)
+    assert np.max(np.abs(psi.reshape(sys.D, sys.D) - q2)) < 1e-12
