@@ -284,18 +284,20 @@ sg_status sg_evolve_open(sg_system* sys, const sg_evolve_opts* opts, const doubl
  * for a closed evolution it equals sg_fidelity's F_avg).  1..6 qubit modes. */
 sg_status sg_gate_fidelity_open(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
                                 double* F_out);
-/* sg_gate_fidelity_open with the gradient of one of its fidelities w.r.t. the pulse
- * parameters (the paper's back-propagation carried over to the vectorised master
- * equation, App. C last paragraph; Sec. 2.5): kind SG_FID_AVG differentiates F_avg,
- * SG_FID_STATE the process fidelity F_pro.  F_out[2] as sg_gate_fidelity_open;
- * grad_pulse (host, sg_param_counts' pulse count doubles, the order of sg_get_params)
- * receives dF/d(pulse parameters).  Exact derivative of the discrete map: the Dc^2
- * columns are pulled back through each RK4 step by the adjoint of the non-Hermitian
- * generator (stage rows of H_eff^dag), from segment checkpoints every ckpt steps
- * (0: round(sqrt(N))).  opts: T, dt, precision, frame (ncols and col_index ignored;
- * RK4 only).  The Hamiltonian-parameter gradient of the open evolution is not built. */
+/* sg_gate_fidelity_open with the gradient of one of its fidelities (the paper's
+ * back-propagation carried over to the vectorised master equation, App. C last
+ * paragraph; Sec. 2.5): kind SG_FID_AVG differentiates F_avg, SG_FID_STATE the process
+ * fidelity F_pro.  F_out[2] as sg_gate_fidelity_open; grad_pulse (host, sg_param_counts'
+ * pulse count doubles, the order of sg_get_params) receives dF/d(pulse parameters);
+ * grad_ham (host, the Hamiltonian count: E_J, E_C, E_L per mode, then J per coupling;
+ * NULL: not computed) dF/d(Hamiltonian parameters) through the subsystems'
+ * eigen-derivatives (the collapse operators are held fixed in the truncated
+ * eigenbasis).  Exact derivative of the discrete map: the Dc^2 columns are pulled back
+ * through each RK4 step by the adjoint of the non-Hermitian generator (stage rows of
+ * H_eff^dag), from segment checkpoints every ckpt steps (0: round(sqrt(N))).  opts: T,
+ * dt, precision, frame (ncols and col_index ignored; RK4 only). */
 sg_status sg_gate_fidelity_open_grad(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
-                                     int kind, double* F_out, double* grad_pulse, int ckpt);
+                                     int kind, double* F_out, double* grad_pulse, double* grad_ham, int ckpt);
 
 /* Batched dense evolution on the tensor cores: nsys systems of one shape (the same
  * modes and level counts, the same number of drives; parameters, couplings and

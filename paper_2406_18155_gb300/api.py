@@ -199,17 +199,21 @@ class System:
         self._chk(lib().sg_gate_fidelity_open(self.h, C.byref(o), _dptr(tg), _dptr(F)))
         return F[0], F[1]
 
-    def gate_fidelity_open_grad(self, T, dt, target, kind="avg", precision="mixed", frame="interaction", ckpt=0):
-        """(F_avg, F_pro) and dF/d(pulse parameters) of F_avg (kind "avg") or F_pro
-        (kind "pro") of the open evolution (sg_gate_fidelity_open_grad)."""
+    def gate_fidelity_open_grad(self, T, dt, target, kind="avg", precision="mixed", frame="interaction", ckpt=0,
+                                ham=False):
+        """(F_avg, F_pro), dF/d(pulse parameters) and (ham=True) dF/d(Hamiltonian
+        parameters, else None) of F_avg (kind "avg") or F_pro (kind "pro") of the open
+        evolution (sg_gate_fidelity_open_grad)."""
         o, keep = evolve_opts(T, dt, precision, frame, None, ncols=1)
         tg = _c128_pairs(target)
         F = np.zeros(2)
-        npul, _ = self.param_counts()
+        npul, nham = self.param_counts()
         g = np.zeros(max(npul, 1))
+        gh = np.zeros(max(nham, 1))
         k = {"avg": 0, "pro": 1}[kind]
-        self._chk(lib().sg_gate_fidelity_open_grad(self.h, C.byref(o), _dptr(tg), k, _dptr(F), _dptr(g), int(ckpt)))
-        return F, g[:npul]
+        self._chk(lib().sg_gate_fidelity_open_grad(self.h, C.byref(o), _dptr(tg), k, _dptr(F), _dptr(g),
+                                                   _dptr(gh) if ham else None, int(ckpt)))
+        return (F, g[:npul], gh[:nham]) if ham else (F, g[:npul])
 
     def close(self):
         if self.h:

@@ -94,7 +94,7 @@ SIGNATURES = {
     "sg_add_collapse": (_I, [_P, _I, _PD, _D, _PI]),
     "sg_evolve_open": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _PD]),
     "sg_gate_fidelity_open": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _PD]),
-    "sg_gate_fidelity_open_grad": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _I]),
+    "sg_gate_fidelity_open_grad": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I]),
     "sg_fidelity": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _PD, _PD]),
     "sg_fidelity_grad": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I]),
     "sg_fidelity_grad_sharded": (_I, [_P, C.POINTER(sg_evolve_opts), _PD, _I, _PD, _PD, _PD, _I,

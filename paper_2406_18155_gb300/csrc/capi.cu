@@ -161,10 +161,10 @@ sg_status sg_gate_fidelity_open(sg_system* sys, const sg_evolve_opts* opts, cons
 }
 
 sg_status sg_gate_fidelity_open_grad(sg_system* sys, const sg_evolve_opts* opts, const double* target_re_im,
-                                     int kind, double* F_out, double* grad_pulse, int ckpt) {
+                                     int kind, double* F_out, double* grad_pulse, double* grad_ham, int ckpt) {
   if (!sys) return SG_E_INVALID;
   std::lock_guard<std::mutex> lk(sys->ctx->mu);
-  return sg_gate_fidelity_open_grad_impl(sys, opts, target_re_im, kind, F_out, grad_pulse, ckpt);
+  return sg_gate_fidelity_open_grad_impl(sys, opts, target_re_im, kind, F_out, grad_pulse, grad_ham, ckpt);
 }
 
 sg_status sg_add_coupling(sg_system* sys, int mode_a, int op_a, int mode_b, int op_b, double strength,

@@ -1665,6 +1665,10 @@ struct Solve {
   const double2* adj_tab = nullptr;
   const float2* adj_tab32 = nullptr;
   double* J_dev = nullptr;        // coupling strengths (batched on-chip adjoint launches)
+  // the generic gather kernels only: their cross-densities read the forward rows
+  // (xa.tabrow) while the apply reads adj_tab; the tiled and on-chip adjoints contract
+  // the coupling cross-densities with the rows they apply
+  bool force_gather = false;
   ~Solve() {
     slab_plan_destroy(slab);
     onchip_plan_destroy(oc);
@@ -1722,7 +1726,7 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   // plans first: they upload their offset tables, and every host-to-device copy of
   // a solve goes before its first kernel (see dcopy)
   sv.mixed = o->precision == SG_MIXED;
-  const int pc = path_choice();
+  const int pc = sv.force_gather ? 2 : path_choice();
   if (pc == 0) sv.oc = onchip_plan_create(s.p, sv.mixed, s.K, s.sumd, st);
   if (pc <= 1 && !(sv.oc && onchip_adjoint_ok(sv.oc))) sv.slab = slab_plan_create(s.p, sv.mixed, st);
   // mixed precision on the on-chip kernels reads only FP32 tables
@@ -2634,9 +2638,13 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
 // terms of dF/df contract the forward operators (Sec. 2.5 on the vectorised equation,
 // App. C last paragraph).  A drive of the open system appears twice in the doubled
 // one, on the ket mode with its parameters and on the bra mode with their negatives,
-// so its gradient is the ket copy's minus the bra copy's.
+// so its gradient is the ket copy's minus the bra copy's.  The Hamiltonian-parameter
+// gradient (grad_ham) folds the doubled modes' operator and energy co-gradients onto
+// the open system's modes (a bra mode carries the operators transposed and the energies
+// negated, k_open_fold) before the eigen-derivative chain, and a coupling's gradient
+// is its ket copy's minus its bra copy's (strength -J).
 sg_status sg_gate_fidelity_open_grad_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, int kind,
-                                          double* F_out, double* grad_pulse, int ckpt) {
+                                          double* F_out, double* grad_pulse, double* grad_ham, int ckpt) {
   sg_ctx* ctx = sys->ctx;
   if (!sys->prepared) return sg_fail(ctx, SG_E_STATE, "system is not prepared (call sg_prepare)");
   if (!o || !target || !F_out || !grad_pulse)
@@ -2670,7 +2678,11 @@ sg_status sg_gate_fidelity_open_grad_impl(sg_system* sys, const sg_evolve_opts* 
   od.basis = SG_BASIS_PRODUCT;
   Solve sv, sva;
   sv.ar.st = sva.ar.st = ctx->stream;
-  sv.want_ham = sva.want_ham = false;
+  sv.want_ham = sva.want_ham = grad_ham != nullptr;
+  // the Hamiltonian gradient contracts the coupling and energy terms with the forward
+  // rows of the non-Hermitian generator: the gather kernels keep them apart from the
+  // applied (conjugate-transposed) rows
+  sv.force_gather = sva.force_gather = grad_ham != nullptr;
   rc = build_setup(&dsys, &od, sv.s);
   if (rc != SG_OK) return rc;
   rc = build_setup(&dadj, &od, sva.s);
@@ -2758,6 +2770,18 @@ sg_status sg_gate_fidelity_open_grad_impl(sg_system* sys, const sg_evolve_opts* 
   SG_CUDA_TRY(ctx, cudaMemsetAsync(acc.jb, 0, std::max(1, ne) * sizeof(double), st));
   SG_CUDA_TRY(ctx, cudaMemsetAsync(pbar, 0, n * sizeof(double2), st));
   launch_open_costate(comp_dev, Tg, D, Dc, kind, pbar, st);
+  double* ebar_frame = sv.ar.get<double>((size_t)s.nq * SG_MAXD);
+  if (!ebar_frame) return done(sg_fail(ctx, SG_E_NOMEM, "device allocation failed"));
+  SG_CUDA_TRY(ctx, cudaMemsetAsync(ebar_frame, 0, (size_t)s.nq * SG_MAXD * sizeof(double), st));
+  if (grad_ham && s.frame == SG_FRAME_INTERACTION) {
+    // energy cotangent of the frame epilogue, from the lab-frame states and co-state
+    OpenModes om{};
+    om.nq = nq;
+    om.D = D;
+    for (int i = 0; i < nq; ++i) { om.dims[i] = sys->modes[i].d; om.st[i] = stv[i]; }
+    launch_open_frame_ebar(sv.psi, pbar, comp_dev, om, Dc, s.T, ebar_frame, st);
+    ++sv.launches;
+  }
   if (s.frame == SG_FRAME_INTERACTION) k_frame<<<grid_for(n), kT, 0, st>>>(frame_args(s, sv.E_dev, +1.0), pbar);
   sv.launches += 2;
   SG_CUDA_TRY(ctx, cudaGetLastError());
@@ -2772,14 +2796,60 @@ sg_status sg_gate_fidelity_open_grad_impl(sg_system* sys, const sg_evolve_opts* 
         sv.drives_dev, sv.amps_dev, acc.gF, s.K, s.N, s.dt, poff, s.n_pulse, gpulse, omega_bar, 0);
     ++sv.launches;
   }
+  double* gdev = nullptr;
+  if (grad_ham) {
+    // the doubled modes' co-gradients, folded onto the open system's modes, then the
+    // eigen-derivative chain of the open system
+    const size_t MD2 = SG_MAXD * SG_MAXD;
+    double2* opbar_d = sv.ar.get<double2>((size_t)s.nq * 2 * MD2);
+    double* ebar_d = sv.ar.get<double>((size_t)s.nq * SG_MAXD);
+    double2* opbar = sv.ar.get<double2>((size_t)nq * 2 * MD2);
+    double* ebar = sv.ar.get<double>((size_t)nq * SG_MAXD);
+    gdev = sv.ar.get<double>(3 * nq);
+    if (!opbar_d || !ebar_d || !opbar || !ebar || !gdev)
+      return done(sg_fail(ctx, SG_E_NOMEM, "device allocation of gradient accumulators failed"));
+    AssembleArgs aa{};
+    aa.nq = s.nq; aa.n1 = n1; aa.ne = ne; aa.K = s.K;
+    for (int i = 0; i < s.nq; ++i) { aa.dims[i] = s.p.dims[i]; aa.s1_of_mode[i] = s.s1_of_mode[i]; }
+    for (int k = 0; k < s.K; ++k) {
+      aa.drv_mode[k] = dsys.drives[k].mode; aa.drv_op[k] = dsys.drives[k].op;
+      aa.drv_omode[k] = dsys.drives[k].omega_mode;
+    }
+    for (int e = 0; e < ne; ++e) {
+      aa.e_a[e] = s.p.e_a[e]; aa.e_b[e] = s.p.e_b[e]; aa.e_opa[e] = s.ta.e_opa[e]; aa.e_opb[e] = s.ta.e_opb[e];
+    }
+    aa.acc = acc; aa.omega_bar = omega_bar; aa.ebar_frame = ebar_frame; aa.opbar = opbar_d; aa.ebar = ebar_d;
+    if (!s.K) SG_CUDA_TRY(ctx, cudaMemsetAsync(omega_bar, 0, sizeof(double), st));
+    k_assemble<<<1, kT, 0, st>>>(aa);
+    launch_open_fold(nq, opbar_d, ebar_d, opbar, ebar, st);
+    sv.launches += 2;
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    sg_status rc2 = sg_chain_device_params(sys, opbar, ebar, gdev);
+    if (rc2 != SG_OK) return done(rc2);
+    ++sv.launches;
+  }
   SG_CUDA_TRY(ctx, cudaGetLastError());
   cudaEventRecord(ev2, st);
   double Fh[2] = {0.0, 0.0};
   std::vector<double> gd(std::max(1, s.n_pulse), 0.0);
+  std::vector<double> gdh(3 * (size_t)nq), jbh(std::max(1, ne));
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));    // reads only from an idle stream (see dcopy)
   SG_CUDA_TRY(ctx, cudaMemcpyAsync(Fh, Fd, sizeof Fh, cudaMemcpyDeviceToHost, st));
   if (s.n_pulse) SG_CUDA_TRY(ctx, cudaMemcpyAsync(gd.data(), gpulse, s.n_pulse * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (grad_ham) {
+    SG_CUDA_TRY(ctx, cudaMemcpyAsync(gdh.data(), gdev, 3 * nq * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (ne) SG_CUDA_TRY(ctx, cudaMemcpyAsync(jbh.data(), acc.jb, ne * sizeof(double), cudaMemcpyDeviceToHost, st));
+  }
   SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));
+  if (grad_ham) {
+    for (int i = 0; i < nq; ++i) {
+      grad_ham[3 * i + 0] = gdh[3 * i + 0];
+      grad_ham[3 * i + 1] = gdh[3 * i + 1];
+      grad_ham[3 * i + 2] = sys->modes[i].kind == 0 ? 0.0 : gdh[3 * i + 2];
+    }
+    // the doubled couplings 2e (ket, J) and 2e + 1 (bra, -J) of coupling e
+    for (size_t e = 0; e < sys->couplings.size(); ++e) grad_ham[3 * nq + e] = jbh[2 * e] - jbh[2 * e + 1];
+  }
   // the doubled drives 2k (ket) and 2k + 1 (bra, negated parameters) of drive k
   int po = 0;
   for (size_t k = 0; k < sys->drives.size(); ++k) {

@@ -114,11 +114,10 @@ sg_status lindblad_doubled(const sg_system* sys, double T, sg_system& out) {
     if (out.opd_host[m].size() / (2 * (size_t)d * d) > SG_MAXOP)
       return sg_fail(ctx, SG_E_UNSUPPORTED, "too many operators on a mode of the open evolution");
   }
-  // drives: the ket copy and the bra copy with negated amplitudes (-H^T), carrier fixed
+  // drives: the ket copy and the bra copy with negated amplitudes (-H^T); a carrier tied
+  // to a mode's 0-1 frequency stays tied to that (ket) mode in both copies
   for (const HostDrive& hd : sys->drives) {
     HostDrive k = hd;
-    k.omega_d = hd.omega_mode >= 0 ? sys->E_host[hd.omega_mode][1] : hd.omega_d;
-    k.omega_mode = -1;
     out.drives.push_back(k);
     HostDrive b = k;
     b.mode = nq + hd.mode;
@@ -247,6 +246,65 @@ void launch_open_costate(const long long* comp, const double2* Tg, long long D, 
                          cudaStream_t st) {
   const int n = Dc * Dc * Dc * Dc;
   k_open_costate<<<(n + 255) / 256, 256, 0, st>>>(comp, Tg, D, Dc, kind, bar);
+}
+
+namespace {
+
+// Energy cotangent of the lab-frame epilogue exp(-i E_tot T) of the doubled columns:
+// dF/dE_dm[l] = T sum Re(conj(bar) (-i) psi) over the entries whose doubled mode dm
+// (ket modes 0..nq-1, then bra modes) sits in level l; the co-state is non-zero on the
+// computational block only (rows comp[a] D + comp[b]).  One block per doubled mode.
+__global__ void k_open_frame_ebar(const double2* __restrict__ psi, const double2* __restrict__ bar,
+                                  const long long* __restrict__ comp, OpenModes om, int Dc, double T,
+                                  double* __restrict__ ebar) {
+  __shared__ double red[256][SG_MAXD];
+  const int dm = blockIdx.x, m = dm % om.nq;
+  const bool bra = dm >= om.nq;
+  const int S = Dc * Dc;
+  double part[SG_MAXD];
+  for (int l = 0; l < SG_MAXD; ++l) part[l] = 0.0;
+  for (int x = threadIdx.x; x < S * S; x += blockDim.x) {
+    const int ab = x / S, jk = x - (x / S) * S;
+    const int a = ab / Dc, b = ab - a * Dc;
+    const long long r = comp[a] * om.D + comp[b];
+    const int lev = (int)(((bra ? comp[b] : comp[a]) / om.st[m]) % om.dims[m]);
+    const double2 bv = bar[r * S + jk], u = psi[r * S + jk];
+    part[lev] += T * (bv.x * u.y - bv.y * u.x);
+  }
+  for (int l = 0; l < SG_MAXD; ++l) red[threadIdx.x][l] = part[l];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int l = 0; l < SG_MAXD; ++l) red[threadIdx.x][l] += red[threadIdx.x + o][l];
+    __syncthreads();
+  }
+  if (threadIdx.x < SG_MAXD) ebar[dm * SG_MAXD + threadIdx.x] += red[0][threadIdx.x];
+}
+
+// Co-gradients of the doubled modes folded onto the open system's modes: a bra mode
+// carries the operators transposed and the energies negated, so
+//   opbar[m][op] = opbar_d[m][op] + opbar_d[nq + m][op]^T,  ebar[m] = ebar_d[m] - ebar_d[nq + m].
+__global__ void k_open_fold(int nq, const double2* __restrict__ opbar_d, const double* __restrict__ ebar_d,
+                            double2* __restrict__ opbar, double* __restrict__ ebar) {
+  const int MD2 = SG_MAXD * SG_MAXD;
+  for (int x = threadIdx.x; x < nq * 2 * MD2; x += blockDim.x) {
+    const int mo = x / MD2, ab = x - mo * MD2, a = ab / SG_MAXD, b = ab - a * SG_MAXD;
+    const double2 k = opbar_d[x], br = opbar_d[(size_t)nq * 2 * MD2 + mo * MD2 + b * SG_MAXD + a];
+    opbar[x] = make_double2(k.x + br.x, k.y + br.y);
+  }
+  for (int x = threadIdx.x; x < nq * SG_MAXD; x += blockDim.x) ebar[x] = ebar_d[x] - ebar_d[nq * SG_MAXD + x];
+}
+
+}  // namespace
+
+void launch_open_frame_ebar(const double2* psi, const double2* bar, const long long* comp, const OpenModes& om, int Dc,
+                            double T, double* ebar_d, cudaStream_t st) {
+  k_open_frame_ebar<<<2 * om.nq, 256, 0, st>>>(psi, bar, comp, om, Dc, T, ebar_d);
+}
+
+void launch_open_fold(int nq, const double2* opbar_d, const double* ebar_d, double2* opbar, double* ebar,
+                      cudaStream_t st) {
+  k_open_fold<<<1, 256, 0, st>>>(nq, opbar_d, ebar_d, opbar, ebar);
 }
 
 sg_status sg_evolve_open_impl(sg_system* sys, const sg_evolve_opts* o, const double* rho0, double* rho_out) {

@@ -102,7 +102,7 @@ sg_status sg_evolve_impl(sg_system* sys, const sg_evolve_opts* o, void* psi_dev)
 sg_status sg_evolve_open_impl(sg_system* sys, const sg_evolve_opts* o, const double* rho0, double* rho_out);
 sg_status sg_gate_fidelity_open_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, double* F_out);
 sg_status sg_gate_fidelity_open_grad_impl(sg_system* sys, const sg_evolve_opts* o, const double* target, int kind,
-                                          double* F_out, double* grad_pulse, int ckpt);
+                                          double* F_out, double* grad_pulse, double* grad_ham, int ckpt);
 // lindblad.cu: the doubled (ket/bra) system of the vectorised master equation, its
 // conjugate-transposed copy (adjoint rows), and the channel fidelity and its co-state
 sg_status lindblad_doubled(const sg_system* sys, double T, sg_system& out);
@@ -111,6 +111,12 @@ void launch_open_fidelity(const double2* psi, const long long* comp, const doubl
                           double* F, cudaStream_t st);
 void launch_open_costate(const long long* comp, const double2* Tg, long long D, int Dc, int kind, double2* bar,
                          cudaStream_t st);
+// the open system's modes (level counts and row strides of its D x D index)
+struct OpenModes { int nq; long long D; int dims[SG_MAXQ]; long long st[SG_MAXQ]; };
+void launch_open_frame_ebar(const double2* psi, const double2* bar, const long long* comp, const OpenModes& om, int Dc,
+                            double T, double* ebar_d, cudaStream_t st);
+void launch_open_fold(int nq, const double2* opbar_d, const double* ebar_d, double2* opbar, double* ebar,
+                      cudaStream_t st);
 sg_status sg_evolve_batch_impl(sg_system* const* systems, int B, const sg_evolve_opts* o, void* psi_dev);
 // red (nullable): the column-sharded solve's all-reduce (sg_fidelity_grad_sharded).
 sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double* target,

@@ -8,7 +8,9 @@ the GPU too.  The pulse-parameter gradient of the gate fidelity
 (sg_gate_fidelity_open_grad) against the oracle's discrete adjoint of the
 superoperator RK4 (FP64 within 1e-8 of its largest component, mixed 1e-3) on all
 three kernel families, and its process-fidelity variant against central
-differences."""
+differences; the Hamiltonian-parameter gradient (E_J, E_C, E_L, J through the
+eigen-derivatives) against central differences of the oracle's gate fidelity and,
+without collapse operators, against the closed-system gradient."""
 import numpy as np
 import pytest
 
@@ -161,3 +163,51 @@ def test_open_process_fidelity_gradient_matches_central_differences(sgctx):
         s.set_params(pulse=p0)
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(g[k] - fd) <= 1e-6 * max(1e-3, np.max(np.abs(g))), (k, g[k], fd)
+
+
+def _ham_names(wl):
+    return [("mode", i, p) for i in range(len(wl["modes"])) for p in ("ej", "ec", "el")] + \
+           [("coupling", e, "J") for e in range(len(wl["couplings"]))]
+
+
+def test_open_hamiltonian_gradient_matches_central_differences(sgctx):
+    import copy
+    wl = _flux_cr()
+    s = _system(sgctx, wl)
+    F, gp, gh = s.gate_fidelity_open_grad(wl["T"], wl["dt"], wl["target"], kind="avg", precision="fp64",
+                                          ckpt=4, ham=True)
+    Fr, gr = gate_fidelity_pulse_gradient(wl)
+    assert abs(F[0] - Fr) < 1e-10
+    assert np.max(np.abs(gp - gr)) <= 1e-8 * np.max(np.abs(gr))
+    scale = np.max(np.abs(gh))
+    for idx, (what, k, p) in enumerate(_ham_names(wl)):
+        v = wl["modes"][k][p] if what == "mode" else wl["couplings"][k]["J"]
+        h = 1e-5 * max(abs(v), 1e-3)
+        vals = []
+        for sgn in (1, -1):
+            w2 = copy.deepcopy(wl)
+            if what == "mode":
+                w2["modes"][k][p] = v + sgn * h
+            else:
+                w2["couplings"][k]["J"] = v + sgn * h
+            vals.append(gate_fidelity(w2)[0])
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(gh[idx] - fd) <= 1e-6 * scale + 1e-9, (what, k, p, gh[idx], fd)
+    F32, gp32, gh32 = s.gate_fidelity_open_grad(wl["T"], wl["dt"], wl["target"], kind="avg",
+                                                precision="mixed", ckpt=4, ham=True)
+    assert np.max(np.abs(gh32 - gh)) <= 1e-3 * scale
+
+
+def test_open_hamiltonian_gradient_closed_limit(sgctx):
+    # without collapse operators the open F_avg and its gradient are the closed ones up
+    # to RK4 on vec(rho) against RK4 on the states (fifth order per step)
+    wl = _transmon()
+    wl["collapse"] = []
+    s = _system(sgctx, wl)
+    F, gp, gh = s.gate_fidelity_open_grad(wl["T"], wl["dt"], wl["target"], kind="avg", precision="fp64",
+                                          ham=True)
+    Fc, gpc, ghc = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg",
+                                   precision="fp64")
+    assert abs(F[0] - Fc[0]) < 1e-8
+    assert np.max(np.abs(gp - gpc)) <= 1e-6 * np.max(np.abs(gpc))
+    assert np.max(np.abs(gh - ghc)) <= 1e-6 * np.max(np.abs(ghc))
