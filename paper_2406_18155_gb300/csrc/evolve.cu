@@ -699,6 +699,13 @@ __global__ void __launch_bounds__(kT) k_adj(KPlan p, const typename CT<R>::T* __
   }
 }
 
+// complex64 -> complex128, element-wise
+__global__ void k_widen(const float2* __restrict__ src, double2* __restrict__ dst, long long n) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    dst[e] = make_double2((double)src[e].x, (double)src[e].y);
+}
+
 template <typename R>
 __global__ void k_cast(const double2* __restrict__ src, typename CT<R>::T* __restrict__ dst,
                        long long n, double scale) {
@@ -1737,9 +1744,12 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   sv.opd_dev = sv.ar.get<double2>(s.opdflat.size());
   const size_t nst = s.q2 ? 0 : 3ull * s.N;
   if (s.q2) {
-    // Q2 reads no RK4 tables; it needs the on-chip kernels
-    if (!sv.oc) return sg_fail(ctx, SG_E_UNSUPPORTED, "the Q2 solver runs on the on-chip kernels: every mode "
-                                                    "with the same level count 2..5 and D <= 4096");
+    // Q2 reads no RK4 tables; it runs on the on-chip kernels, or beyond them on the
+    // tiles of a two-pass plan (the palindromic products; Q1 on-chip only)
+    if (!sv.oc && !(sv.slab && !s.ta.q1 && slab_q2_ok(sv.slab, s.p, sv.mixed)))
+      return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter solvers run on the on-chip kernels (every mode with "
+                                            "the same level count 2..5 and D <= 4096) or on the tiles of a two-pass "
+                                            "plan whose first pass holds the first couplings (Q2, Q4, Q4j)");
   } else if (f32only) {
     sv.coef32 = sv.ar.get<float>(nst * std::max(1, s.K));
     sv.ph32 = sv.ar.get<float2>(nst * s.sumd);
@@ -1770,7 +1780,7 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   ta.tab32 = sv.tab32;
   s.ta = ta;
   if (s.q2) {
-    const int DL = onchip_dl(sv.oc);
+    const int DL = sv.oc ? onchip_dl(sv.oc) : slab_dl(sv.slab);
     const long long M = (long long)s.N * ta.nsub;                  // Q2 sub-steps
     const int nset = ta.nset, ne1 = std::max(1, s.p.ne);
     const size_t D4 = (size_t)DL * DL * DL * DL;
@@ -2203,6 +2213,26 @@ sg_status run_q2(sg_system* sys, Solve& sv, const long long* cols_dev, bool init
     k_init_cols<<<grid_for(s.D * s.S), kT, 0, st>>>(sv.psi, s.D, s.S, cols_dev);
     ++sv.launches;
   }
+  if (!sv.oc) {
+    // tiled: the internal layout in the stage precision, evolved in place
+    const long long n = s.D * s.S;
+    double2* pint = sv.ar.get<double2>(n);
+    float2* X32 = sv.mixed ? sv.ar.get<float2>(n) : nullptr;
+    if (!pint || (sv.mixed && !X32)) return sg_fail(ctx, SG_E_NOMEM, "device allocation of the state failed");
+    slab_to_internal(sv.slab, sv.psi, pint, st);
+    void* X = pint;
+    if (sv.mixed) {
+      k_cast<float><<<grid_for(n), kT, 0, st>>>(pint, X32, n, 1.0);
+      X = X32;
+    }
+    sv.launches += slab_q2_run(sv.slab, sv.mixed, sv.q2rows, sv.q2edges, X, s.N * s.ta.nsub, s.ta.nsub,
+                               s.ta.set_of, st);
+    if (sv.mixed) k_widen<<<grid_for(n), kT, 0, st>>>(X32, pint, n);
+    slab_from_internal(sv.slab, pint, sv.psi, st);
+    sv.launches += sv.mixed ? 4 : 2;
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    return SG_OK;
+  }
   sg_status rc = onchip_q2_forward(sv.oc, s.p, sv.q2rows, sv.q2edges, sv.psi, sv.psi, s.N * s.ta.nsub, s.ta.nsub,
                                    s.ta.set_of, s.ta.nset, st, &sv.launches, s.ta.q1 != 0);
   if (rc != SG_OK) return sg_fail(ctx, rc, "the Suzuki-Trotter solvers support at most 16 modes and 32 couplings");
@@ -2380,6 +2410,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   }
   rc = upload_and_tables(sys, o, sv, grad);
   if (rc != SG_OK) return rc;
+  if (grad && s.q2 && !sv.oc)
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter gradient runs on the on-chip kernels (D <= 4096)");
   double2* Vc = nullptr;
   if (dressed) {
     // dressed computational states of the idle Hamiltonian (one block, FP64 Jacobi)

@@ -717,32 +717,6 @@ struct Q2Args {
   Q2Factor f[kMaxQ2F];            // [0, nf0): 1-body; [nf0, nf0 + nfe): couplings in order
 };
 
-// o[x][z] = sum_{a,c} G[(x d + z), (a d + c)] y[a][c] over one block (digits ka, kb).
-template <int DL, typename C>
-__device__ __forceinline__ void block_dense(const C* __restrict__ G, const C* __restrict__ ys, C* __restrict__ ks,
-                                            int pb, int psa, int psb) {
-  C y[DL][DL];
-#pragma unroll
-  for (int a = 0; a < DL; ++a)
-#pragma unroll
-    for (int c = 0; c < DL; ++c) y[a][c] = ys[pb + a * psa + c * psb];
-  // one output per iteration (a runtime loop keeps the d^4 code small)
-#pragma unroll 1
-  for (int xz = 0; xz < DL * DL; ++xz) {
-    const C* g = G + xz * DL * DL;
-    C acc0 = cmk<C>(0.0, 0.0), acc1 = cmk<C>(0.0, 0.0);       // two chains for latency
-#pragma unroll
-    for (int a = 0; a < DL; ++a)
-#pragma unroll
-      for (int c = 0; c < DL; ++c) {
-        if ((a * DL + c) & 1) acc1 = cfma(g[a * DL + c], y[a][c], acc1);
-        else acc0 = cfma(g[a * DL + c], y[a][c], acc0);
-      }
-    const int x = xz / DL, z = xz - x * DL;
-    ks[pb + x * psa + z * psb] = cmk<C>(acc0.x + acc1.x, acc0.y + acc1.y);
-  }
-}
-
 template <int DL, typename C>
 __device__ __forceinline__ void q2_apply(const Q2Factor& F, int mat, const OcArgs& oa, const C* __restrict__ M,
                                          const C* __restrict__ edges, const C* __restrict__ ys, C* __restrict__ ks) {

@@ -557,6 +557,7 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
       int eoff[SG_MAXQ], e = 0;                // offsets of each mode's levels in a phase row
       for (int i = 0; i < nq; ++i) { eoff[i] = e; e += p.dims[i]; }
       for (int k = 0; k < sp.ng; ++k) sp.tphoff[k] = eoff[tm[k]];
+      for (int k = 0; k < sp.ng; ++k) sp.tmode[k] = tm[k];
     }
     sp.no = 0;
     for (int m : order)
@@ -705,6 +706,7 @@ SlabPlanHost* slab_plan_create(const KPlan& p, bool mixed, cudaStream_t st, bool
 
 void slab_plan_destroy(SlabPlanHost* h) {
   if (!h) return;
+  slab_q2_free(h);
   for (int g = 0; g < kMaxPass; ++g) if (h->off_dev[g]) cudaFreeAsync(h->off_dev[g], h->st);
   delete h;
 }

@@ -63,3 +63,21 @@ bool slab_allpar(const SlabPlanHost* sp);
 // (nullptr keeps the complex-row adjoint).
 void slab_bind_real(SlabPlanHost* sp, const void* ztab, const double2* ph, int sumd, const void* zop,
                     const int* drv_of_slot_start, const int* drv_list);
+
+// Suzuki-Trotter products (Sec. 2.3, App. A: the palindromic Q2 sub-steps of Q2, Q4 and
+// Q4j) on the tiles of a two-pass plan, for slabs too large for the on-chip kernels.
+// One sub-step is two in-place passes over the state (stage precision, internal
+// layout): the first group's tiles take the previous sub-step's reversed couplings of
+// that group, the merged 1-body factors of its modes and this sub-step's couplings of
+// that group; the second group's tiles its other modes' 1-body factors and its part of
+// the palindrome (with the middle, full-step coupling).  Needs the couplings of the
+// first pass to come before those of the second in term order (the ring's and the
+// chain's plans).  slab_q2_ok builds the factor lists (false: unsupported).
+bool slab_q2_ok(SlabPlanHost* sp, const KPlan& p, bool mixed);
+void slab_q2_free(SlabPlanHost* sp);
+int slab_dl(const SlabPlanHost* sp);
+// M = N J sub-steps from X (in place).  rows: (M + 1) x nq x DL^2 merged 1-body factors
+// (the Q2 tables of the on-chip path), edges: per set and coupling the half- and
+// full-step unitaries; sub-step m uses set set_of[m % J].  Returns launches.
+int slab_q2_run(const SlabPlanHost* sp, bool mixed, const void* rows, const void* edges, void* X, int M, int J,
+                const int* set_of, cudaStream_t st);

@@ -58,6 +58,7 @@ struct SlabPass {
   Phase ph[kMaxPhase];
   const int* off;                 // device tile offsets [T]
   int tphoff[SG_MAXQ];            // tile digit k: offset of its mode's levels in a stage's phase row
+  int tmode[SG_MAXQ];             // tile digit k: its mode
   // drives whose 1-body slot lies in this pass (real-operator pulse-gradient adjoint):
   // the phase whose blocks carry the slot's digit, on its first (0) or second (1)
   // digit, and the global drive index
@@ -172,6 +173,33 @@ __device__ __forceinline__ void blk_apply(const Phase& P, const C* __restrict__ 
   if (P.offB >= 0) {
     if (P.par & 8u) blk_right_acc<DL, true>(M + P.offB, y, out);
     else blk_right_acc<DL, false>(M + P.offB, y, out);
+  }
+}
+
+// o[x][z] = sum_{a,c} G[(x d + z), (a d + c)] y[a][c] over one block (digits ka, kb): a
+// dense two-mode factor (the Suzuki-Trotter coupling unitaries).
+template <int DL, typename C>
+__device__ __forceinline__ void block_dense(const C* __restrict__ G, const C* __restrict__ ys, C* __restrict__ ks,
+                                            int pb, int psa, int psb) {
+  C y[DL][DL];
+#pragma unroll
+  for (int a = 0; a < DL; ++a)
+#pragma unroll
+    for (int c = 0; c < DL; ++c) y[a][c] = ys[pb + a * psa + c * psb];
+  // one output per iteration (a runtime loop keeps the d^4 code small)
+#pragma unroll 1
+  for (int xz = 0; xz < DL * DL; ++xz) {
+    const C* g = G + xz * DL * DL;
+    C acc0 = cmk<C>(0.0, 0.0), acc1 = cmk<C>(0.0, 0.0);       // two chains for latency
+#pragma unroll
+    for (int a = 0; a < DL; ++a)
+#pragma unroll
+      for (int c = 0; c < DL; ++c) {
+        if ((a * DL + c) & 1) acc1 = cfma(g[a * DL + c], y[a][c], acc1);
+        else acc0 = cfma(g[a * DL + c], y[a][c], acc0);
+      }
+    const int x = xz / DL, z = xz - x * DL;
+    ks[pb + x * psa + z * psb] = cmk<C>(acc0.x + acc1.x, acc0.y + acc1.y);
   }
 }
 
@@ -631,6 +659,9 @@ struct SlabPlanHost {
   const void* zop = nullptr;
   bool zadj = false;
   size_t sm_zadj[kMaxPass] = {0};
+  // Suzuki-Trotter products on the tiles (slab_q2.cu): the factor lists of the two
+  // passes of a sub-step (nullptr: not supported for this plan)
+  struct SQPlan* q2 = nullptr;
   // lean FP32 passes (slab_lean.cuh): 4 levels, parity-odd, passes whose tiles hold
   // 4096 entries (each pass picks its kernel on its own)
   bool lean[kMaxPass] = {false, false, false, false};

@@ -93,6 +93,44 @@ def test_q1_gradient_is_refused(sgctx, default_path):
     assert e.value.code == SG_E_UNSUPPORTED
 
 
+@pytest.mark.parametrize("scheme", ["q2", "q4", "q4j"])
+def test_tiled_products_match_oracle(sgctx, monkeypatch, scheme):
+    # beyond the on-chip kernels the palindromic products run on the tiles of a two-pass
+    # plan: the 4^7 ring (a 4096-entry and a 64-entry group) and, forced by a small tile
+    # budget, a 3-level chain of 5 modes
+    monkeypatch.delenv("SG_PATH", raising=False)
+    monkeypatch.delenv("SG_SLAB_TMAX", raising=False)
+    ring = _short(W.fluxonium_chain(seed=11, nq=7, levels=4, nseg=2, ring=True, ncols=3), T=0.1)
+    chain = _short(W.fluxonium_chain(seed=12, nq=5, levels=3, nseg=3, ncols=6), T=0.2)
+    for wl, env in ((ring, {}), (chain, {"SG_PATH": "slab", "SG_SLAB_TMAX": "27"})):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        s = _system(sgctx, wl)
+        so = OracleSystem(dict(wl, frame="lab"))
+        ref = q2_evolve(so, initial_columns(so, wl["col_index"]), scheme=scheme)
+        psi = s.evolve(wl["T"], wl["dt"], precision="fp64", col_index=wl["col_index"], solver=scheme).cpu().numpy()
+        assert np.max(np.abs(psi - ref)) < 1e-10
+        psi32 = s.evolve(wl["T"], wl["dt"], precision="mixed", col_index=wl["col_index"],
+                         solver=scheme).cpu().numpy()
+        assert np.max(np.abs(psi32 - ref)) < 1e-5
+        Fa, Fs, Uc = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver=scheme)
+        _, Fs_r, Uc_r = fidelities(so, ref)
+        assert abs(Fs - Fs_r) < 1e-10 and np.max(np.abs(Uc - Uc_r)) < 1e-10
+        for k in env:
+            monkeypatch.delenv(k)
+
+
+def test_tiled_products_refuse_the_gradient(sgctx, default_path):
+    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
+    wl = _short(W.fluxonium_chain(seed=11, nq=7, levels=4, nseg=2, ring=True, ncols=3), T=0.05)
+    wl["fid_kind"] = "state"
+    s = _system(sgctx, wl)
+    with pytest.raises(SGError) as e:
+        s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state", precision="mixed",
+                        solver="q2", ham=False)
+    assert e.value.code == SG_E_UNSUPPORTED
+
+
 def test_q2_rejects_what_it_does_not_run(sgctx, default_path):
     from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
     wl = CASES["transmon_pair"]()
