@@ -331,6 +331,8 @@ def run_ours(args):
                                                    grad == "all", stream)
         if args.q2 and D <= 4096:
             out["q2_vs_rk4"] = q2_comparison(sysm, wl, stream)
+        elif args.q2:
+            out["q2_vs_rk4"] = q2_tiled_comparison(sysm, wl, stream, args.q2_steps)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample_steps)
     if rank == 0 and args.serving > 0:
@@ -675,6 +677,35 @@ def fp64_comparison(sysm, wl, nsteps, grad_steps, ham, stream):
     return out
 
 
+def q2_tiled_comparison(sysm, wl, stream, nsteps):
+    """The paper's Suzuki-Trotter products on the tiled kernels (slabs beyond the
+    on-chip kernels) against RK4, forward only, over the first nsteps steps of the
+    workload: col-steps/s (device time) of RK4 (mixed), Q2 (mixed, FP64) and Q4
+    (mixed), and the largest difference of the Q2 and Q4 states from RK4's (each
+    solver's own truncation error at the workload's dt)."""
+    import torch
+    T = nsteps * wl["dt"]
+    out = {"steps": nsteps}
+    psi = {}
+    for solver, prec in (("rk4", "mixed"), ("q2", "mixed"), ("q2", "fp64"), ("q4", "mixed")):
+        kw = dict(precision=prec, col_index=wl["col_index"], solver=solver)
+        sysm.evolve(T, wl["dt"], **kw)                                   # warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = sysm.evolve(T, wl["dt"], **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"{solver}_{prec}_forward_col_steps_per_s"] = len(wl["col_index"]) * nsteps / (e0.elapsed_time(e1) / 1e3)
+        if prec == "mixed":
+            psi[solver] = r.cpu().numpy()
+    out["q2_over_rk4_mixed"] = out["q2_mixed_forward_col_steps_per_s"] / out["rk4_mixed_forward_col_steps_per_s"]
+    out["max_abs_dpsi_q2_rk4"] = float(np.max(np.abs(psi["q2"] - psi["rk4"])))
+    out["max_abs_dpsi_q4_rk4"] = float(np.max(np.abs(psi["q4"] - psi["rk4"])))
+    return out
+
+
 def q2_comparison(sysm, wl, stream):
     """The paper's Suzuki-Trotter solvers (Q2, Q4, Q4j) against RK4 on the whole
     workload (single-tile systems only): forward and pulse-gradient col-steps/s of
@@ -874,7 +905,9 @@ def main():
                     help="systems of the concurrent on-chip comparison (with --dense)")
     ap.add_argument("--t-ns", type=float, default=0.0, help="shorten the workload to T ns (profiling)")
     ap.add_argument("--q2", action="store_true",
-                    help="also time the second-order Suzuki-Trotter solver against RK4 (D <= 4096)")
+                    help="also time the Suzuki-Trotter solvers against RK4 (beyond D = 4096: tiled, forward)")
+    ap.add_argument("--q2-steps", type=int, default=400,
+                    help="steps of the tiled Suzuki-Trotter comparison")
     ap.add_argument("--grad", default="config", choices=["config", "pulse", "all"],
                     help="gradient set: the configuration's (ring: pulse segments), pulse only, or all")
     ap.add_argument("--no-full-gradient", dest="full_gradient", action="store_false",

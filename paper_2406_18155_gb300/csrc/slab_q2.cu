@@ -31,11 +31,44 @@ struct SQFactor {
   int kind;                 // 0: two modes' 1-body factors L (x) R, 1: one mode's, 2: a coupling (dense)
   int mat;                  // kind 2: 2 e (half step) or 2 e + 1 (full step)
   int prev;                 // kind 2: from the previous sub-step's coupling set
+  int spar;                 // kind 2: both factors parity-odd, so the unitary keeps the parity of
+                            // the two levels' sum and half its entries are zero
 };
 struct SQList {
   int nf, ndense;
   SQFactor f[kMaxSQ];
 };
+
+// block_dense for a coupling unitary that keeps the parity of a + c (exp of A (x) B with
+// A and B parity-odd): output (x, z) reads only the inputs (a, c) with a + c = x + z mod 2.
+template <int DL, typename C>
+__device__ __forceinline__ void block_dense_sp(const C* __restrict__ G, const C* __restrict__ ys,
+                                               C* __restrict__ ks, int pb, int psa, int psb) {
+  C y[DL][DL];
+#pragma unroll
+  for (int a = 0; a < DL; ++a)
+#pragma unroll
+    for (int c = 0; c < DL; ++c) y[a][c] = ys[pb + a * psa + c * psb];
+#pragma unroll
+  for (int par = 0; par < 2; ++par) {
+#pragma unroll 1
+    for (int xz = 0; xz < DL * DL; ++xz) {
+      const int x = xz / DL, z = xz - x * DL;
+      if (((x + z) & 1) != par) continue;
+      const C* g = G + xz * DL * DL;
+      C acc0 = cmk<C>(0.0, 0.0), acc1 = cmk<C>(0.0, 0.0);
+#pragma unroll
+      for (int a = 0; a < DL; ++a)
+#pragma unroll
+        for (int c = 0; c < DL; ++c) {
+          if (((a + c) & 1) != par) continue;
+          if (a & 1) acc1 = cfma(g[a * DL + c], y[a][c], acc1);
+          else acc0 = cfma(g[a * DL + c], y[a][c], acc0);
+        }
+      ks[pb + x * psa + z * psb] = cmk<C>(acc0.x + acc1.x, acc0.y + acc1.y);
+    }
+  }
+}
 
 template <typename R, int DL>
 __global__ void __launch_bounds__(kST, sizeof(R) == 4 ? 2 : 1)
@@ -72,7 +105,10 @@ k_slab_q2(SlabPass sp, SQList fl, const typename CT<R>::T* __restrict__ row,
       const SQFactor& F = fl.f[q];
       for (int b = threadIdx.x; b < nb; b += kST) {
         const int pb = blk_pos<DL>(F.P, b);
-        if (F.kind == 2) block_dense<DL>(G + (size_t)g * D4, ys, ks, pb, F.P.psa, F.P.psb);
+        if (F.kind == 2) {
+          if (F.spar) block_dense_sp<DL>(G + (size_t)g * D4, ys, ks, pb, F.P.psa, F.P.psb);
+          else block_dense<DL>(G + (size_t)g * D4, ys, ks, pb, F.P.psa, F.P.psb);
+        }
         else phase_block<DL, false>(F.P, M, ys, ks, pb, true);
       }
       g += F.kind == 2 ? 1 : 0;
@@ -120,7 +156,7 @@ void add_onebody(const SlabPass& sp, int DL, const std::vector<int>& modes, SQLi
   }
 }
 
-void add_coupling(const Phase& E, int DL, int mat, int prev, SQList& L, bool& ok) {
+void add_coupling(const Phase& E, int DL, int mat, int prev, SQList& L, bool& ok, int spar) {
   if (L.nf >= kMaxSQ) { ok = false; return; }
   SQFactor& F = L.f[L.nf++];
   F = SQFactor{};
@@ -129,6 +165,7 @@ void add_coupling(const Phase& E, int DL, int mat, int prev, SQList& L, bool& ok
   F.kind = 2;
   F.mat = mat;
   F.prev = prev;
+  F.spar = spar;
   ++L.ndense;
 }
 
@@ -158,11 +195,12 @@ bool slab_q2_ok(SlabPlanHost* h, const KPlan& p, bool mixed) {
   }
   SQPlan* q = new SQPlan();
   bool ok = true;
+  auto sp_of = [&](int e) { return (int)(((p.parL >> e) & 1ull) && ((p.parR >> e) & 1ull)); };
   const SlabPass& A = h->pass[0];
   const SlabPass& B = h->pass[1];
-  auto e1_fwd = [&](SQList& L) { for (auto& e : E[0]) add_coupling(e.second, DL, 2 * e.first, 0, L, ok); };
+  auto e1_fwd = [&](SQList& L) { for (auto& e : E[0]) add_coupling(e.second, DL, 2 * e.first, 0, L, ok, sp_of(e.first)); };
   auto e1_rev = [&](SQList& L) {
-    for (auto it = E[0].rbegin(); it != E[0].rend(); ++it) add_coupling(it->second, DL, 2 * it->first, 1, L, ok);
+    for (auto it = E[0].rbegin(); it != E[0].rend(); ++it) add_coupling(it->second, DL, 2 * it->first, 1, L, ok, sp_of(it->first));
   };
   q->a_first = SQList{};
   add_onebody(A, DL, m1, q->a_first, ok);
@@ -176,10 +214,10 @@ bool slab_q2_ok(SlabPlanHost* h, const KPlan& p, bool mixed) {
   add_onebody(A, DL, m1, q->a_final, ok);
   q->b_mid = SQList{};
   add_onebody(B, DL, m2, q->b_mid, ok);
-  for (size_t j = 0; j + 1 < E[1].size(); ++j) add_coupling(E[1][j].second, DL, 2 * E[1][j].first, 0, q->b_mid, ok);
-  add_coupling(E[1].back().second, DL, 2 * E[1].back().first + 1, 0, q->b_mid, ok);
+  for (size_t j = 0; j + 1 < E[1].size(); ++j) add_coupling(E[1][j].second, DL, 2 * E[1][j].first, 0, q->b_mid, ok, sp_of(E[1][j].first));
+  add_coupling(E[1].back().second, DL, 2 * E[1].back().first + 1, 0, q->b_mid, ok, sp_of(E[1].back().first));
   for (int j = (int)E[1].size() - 2; j >= 0; --j)
-    add_coupling(E[1][j].second, DL, 2 * E[1][j].first, 0, q->b_mid, ok);
+    add_coupling(E[1][j].second, DL, 2 * E[1][j].first, 0, q->b_mid, ok, sp_of(E[1][j].first));
   q->b_final = SQList{};
   add_onebody(B, DL, m2, q->b_final, ok);
   const size_t csz = mixed ? sizeof(float2) : sizeof(double2);
