@@ -269,14 +269,26 @@ k_lean_fwd(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
   const int s0 = tid + (tid >> 4);                  // spos(tid); spos(tid + 256 j) = s0 + 273 j
   const int nph = sp.nph;
   const float h = (float)dt;
+  __shared__ LPf pf[3];
+  __shared__ int npf;
+  if (tid == 0) {
+    int n = 0;
+    if (KIND == 1 || KIND == 2) pf[n++] = LPf{reinterpret_cast<const char*>(kA), (int)sizeof(float2)};
+    if (KIND >= 2) pf[n++] = LPf{reinterpret_cast<const char*>(psi_in), (int)sizeof(double2)};
+    if (KIND >= 2 && !STORE && STAGE > 0) pf[n++] = LPf{reinterpret_cast<const char*>(Dacc), (int)sizeof(float2)};
+    npf = n;
+  }
+  const bool contig = ltile_contig(sp, tid);        // (a barrier: pf and npf are visible after it)
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long bl = tile_base(sp, tile) + olo;
+    const long long tb = tile_base(sp, tile), bl = tb + olo;
     lprefetch_wait();
     __syncthreads();                                // every thread's copies of this tile landed
 #pragma unroll
     for (int j = 0; j < LJ; ++j) ys[s0 + 273 * j] = zcmulc(zcmul(pl, phi[j]), raw[tid + kST * j]);
     __syncthreads();                                // raw is free again
     if (tile + gridDim.x < ntiles) lprefetch(X, tile_base(sp, tile + gridDim.x) + olo2, ohi2, raw, tid);
+    // the epilogue's operands of this tile stream into L2 while its phases run
+    lprefetch_l2(pf, npf, tb, bl, ohi, contig, tid);
     lpass(nph, lph, M, ys, ks, tid);
     if (KIND == 0) lepi_fwd<0, 0, false>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h);
     else if (KIND == 1) lepi_fwd<1, 0, false>(ks, phi, pl, s0, ohi, bl, psi_in, psi_out, Xn, Dacc, kA, h);

@@ -249,5 +249,43 @@ __device__ __forceinline__ void lprefetch(const float2* __restrict__ X, long lon
 }
 __device__ __forceinline__ void lprefetch_wait() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Whether every tile of the pass is one contiguous run of the slab (tile offset of
+// entry t equal to t: by the linear digit map, true when it holds for t < 256 and for
+// t = 256 j).  Call from every thread of the block.
+__device__ __forceinline__ bool ltile_contig(const SlabPass& sp, int tid) {
+  const bool ok = __ldg(sp.off + tid) == tid && (tid >= LJ || __ldg(sp.off + tid * kST) == tid * kST);
+  return __syncthreads_and(ok) != 0;
+}
+
+// L2 prefetch of one tile of up to three arrays (descriptors in shared memory: base
+// address and bytes per entry), so that the loads that follow a while later hit L2
+// instead of waiting on DRAM.  A contiguous tile (tb: its first entry) goes by 8 KB
+// bulk prefetches, one per thread, when 16-byte aligned; any other tile by one line
+// prefetch per entry t = tid + 256 j of thread tid (bl: the thread's base, as in the
+// epilogues), which a warp's lanes share by the 16-entry runs of the layout.  The
+// arrays are read at run time so that no branch on the pass kind splits the tile loop.
+struct LPf {
+  const char* p;
+  int esz;
+};
+__device__ __forceinline__ void lprefetch_l2(const LPf* __restrict__ pf, int npf, long long tb, long long bl,
+                                             const int* __restrict__ ohi, bool contig, int tid) {
+  constexpr int kChunk = 8192;
+#pragma unroll 1
+  for (int i = 0, c = tid; i < npf; ++i) {
+    const char* p = pf[i].p;
+    const int esz = pf[i].esz;
+    const char* t0 = p + tb * esz;
+    if (contig && (reinterpret_cast<unsigned long long>(t0) & 15ull) == 0) {
+      const int nc = LT * esz / kChunk;
+      if (c >= 0 && c < nc) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(t0 + (long long)c * kChunk), "r"(kChunk));
+      c -= nc;
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < LJ; ++j) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p + (bl + ohi[j]) * esz));
+    }
+  }
+}
+
 }  // namespace lean
 }  // namespace
