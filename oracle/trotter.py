@@ -162,8 +162,9 @@ def q2_pulse_gradient(wl, kind=None, scheme="q2"):
     With psi_m = X_m psi_{m-1} over the factors X_m of every step in order and the
     co-state psibar = dF/dRe psi + i dF/dIm psi of the final lab-frame columns,
     psibar_{m-1} = X_m^dag psibar_m and dF/dtheta = sum_m Re <psibar_m, dX_m/dtheta psi_{m-1}>.
-    A 1-body factor is X = exp(A), A = -i c (dt/2) H_i(t_n + tau dt), so
-    dX/df_k = L(A, -i c (dt/2) O_k), the Frechet derivative of expm (scipy's
+    A 1-body factor is X = exp(A), A = -i c h H_i(t_n + tau dt) with h = dt/2 for the
+    Q2 sub-steps and h = dt for Q1 (each term once per step, at the step's midpoint), so
+    dX/df_k = L(A, -i c h O_k), the Frechet derivative of expm (scipy's
     expm_frechet), for each drive k on mode i; f_k(t) = E_k(t) cos(omega t + phase)
     carries the pulse parameters through the envelope (sub_envelope).
     Returns (F, gradient over the pulse parameters in sg_param order)."""
@@ -173,17 +174,19 @@ def q2_pulse_gradient(wl, kind=None, scheme="q2"):
     sys = OracleSystem(dict(wl, frame="lab"))
     kind = kind or wl["fid_kind"]
     dt, N, S = sys.dt, sys.N, len(wl["col_index"])
-    subs = SCHEMES[scheme]
+    q1 = scheme == "q1"
+    subs = [(1.0, 0.5)] if q1 else SCHEMES[scheme]
+    h = dt if q1 else dt / 2
     psi = initial_columns(sys, wl["col_index"]).reshape(list(sys.dims) + [S])
     _, two = local_terms(sys, 0)
     tape = []                                   # (factor, mode/edge, A or G, state before, step, sub-step)
     for n in range(N):
         for j, (c, tau) in enumerate(subs):
             one, _ = local_terms(sys, n, tau)
-            A = [-1j * c * (dt / 2) * H for H in one]
-            G = [(a, b, expm(-1j * c * M * dt / 2)) for a, b, M in two]
+            A = [-1j * c * h * H for H in one]
+            G = [(a, b, expm(-1j * c * M * h)) for a, b, M in two]
             seq = [("1", i, A[i]) for i in range(sys.nq)] + [("2", e, G[e]) for e in range(len(G))]
-            for kind_f, idx, X in seq + seq[::-1]:
+            for kind_f, idx, X in (seq if q1 else seq + seq[::-1]):
                 tape.append((kind_f, idx, X, psi.copy(), n, j))
                 if kind_f == "1":
                     psi = _apply_1body(psi, expm(X), idx)
@@ -201,7 +204,7 @@ def q2_pulse_gradient(wl, kind=None, scheme="q2"):
             for k, dr in enumerate(sys.drives):
                 if dr["mode"] != idx:
                     continue
-                L = expm_frechet(X, -1j * c * (dt / 2) * sys.op(idx, dr["op"]), compute_expm=False)
+                L = expm_frechet(X, -1j * c * h * sys.op(idx, dr["op"]), compute_expm=False)
                 gf[k, n, j] += np.vdot(bar, _apply_1body(before, L, idx))
             bar = _apply_1body(bar, expm(X).conj().T, idx)
         else:

@@ -103,7 +103,7 @@ def test_unitary_to_round_off():
     assert 1e-12 < dev < 1e-4, dev
 
 
-@pytest.mark.parametrize("scheme", ["q2", "q4", "q4j"])
+@pytest.mark.parametrize("scheme", ["q1", "q2", "q4", "q4j"])
 def test_pulse_gradient_matches_central_differences(scheme):
     import copy
     from oracle.trotter import q2_pulse_gradient, q2_fidelity
