@@ -214,8 +214,7 @@ enum { SG_COMP_NONE = 0, SG_COMP_VZ = 1 };
 
 /* Solvers.  SG_SOLVER_Q1: the first-order Suzuki-Trotter product of Sec. 2.3 and App. A,
  * Q1(dt) = prod_k exp(-i H_k dt) over the same local terms in the same order (the first
- * acts first), the time-dependent terms at the step's midpoint; evolution and fidelity
- * only (sg_fidelity_grad returns SG_E_UNSUPPORTED).  SG_SOLVER_Q2: the second-order
+ * acts first), the time-dependent terms at the step's midpoint.  SG_SOLVER_Q2: the second-order
  * Suzuki-Trotter product of Sec. 2.3 and
  * App. A, Q2(dt) = prod_k exp(-i H_k dt/2) prod_k' exp(-i H_k' dt/2) (k' reversed)
  * over the local terms H_i = diag(E^(i)) + sum_{drives on i} f(t) O (every mode, in mode
@@ -226,7 +225,10 @@ enum { SG_COMP_NONE = 0, SG_COMP_VZ = 1 };
  * product Q2(p dt) Q2(p* dt), p = (3 - i sqrt 3)/6, the drive coefficients continued to
  * the complex sub-step midpoints; third order (the composition is not palindromic).
  * They run on the on-chip kernels (every mode with the same level count 2..5,
- * D <= 4096), else SG_E_UNSUPPORTED.  sg_fidelity_grad with a Suzuki-Trotter solver
+ * D <= 4096) and, for the evolution and the fidelity, on the HBM-tiled kernels of a
+ * two-pass plan whose first group's couplings come first in term order and whose last
+ * coupling lies in the second group; else SG_E_UNSUPPORTED.  sg_fidelity_grad with a
+ * Suzuki-Trotter solver (on-chip kernels only)
  * computes the pulse-parameter gradient only (grad_ham must be NULL, else
  * SG_E_UNSUPPORTED): the exact discrete adjoint of the product (Sec. 2.5), the states
  * pulled back through each factor's inverse and the co-state through its adjoint (no

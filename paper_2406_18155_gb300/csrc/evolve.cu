@@ -497,7 +497,8 @@ __global__ void k_q2_edges(TabArgs a, int DL, double2* __restrict__ mats, double
 // inverses when the step length is real), then per drive k on mode i,
 // M_k(m) = U_i(m)^-1 L_k(m) with L_k(m) = L(A, -i c_j (dt/2) O_k) the Frechet derivative
 // of expm at A = -i c_j (dt/2) H_i(t_n + tau_j dt), the top-right block of
-// exp([[A, E], [0, A]]) (Sec. 2.5: dU/df_k).  One thread per (m, row).
+// exp([[A, E], [0, A]]) (Sec. 2.5: dU/df_k).  Q1: the step's full-step factor, dt for
+// dt/2 throughout.  One thread per (m, row).
 constexpr int kQ2MaxD = 5;
 __global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
   const int per = 2 * a.nq + a.K, M = a.N * a.nsub;
@@ -526,7 +527,7 @@ __global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
     constexpr int MM = 4 * kQ2MaxD * kQ2MaxD;
     double2 Z[MM], RZ[MM], Z1[MM], Z2[MM];
     const double2* O = a.opd + a.opd_off[i] + dr.op * d * d;
-    const double h = a.dt * 0.5;
+    const double h = a.q1 ? a.dt : a.dt * 0.5;       // Q1: full-step factors
     const double2 c = a.sc[m % a.nsub];
     for (int p = 0; p < mm * mm; ++p) Z[p] = make_double2(0.0, 0.0);
     for (int p = 0; p < d; ++p)
@@ -534,7 +535,7 @@ __global__ void k_q2_gradtabs(TabArgs a, int DL, double2* __restrict__ rows) {
         Z[p * mm + q] = A[p * d + q];
         Z[(p + d) * mm + q + d] = A[p * d + q];
         const double2 cO = cmul(c, O[p * d + q]);
-        Z[p * mm + q + d] = make_double2(h * cO.y, -h * cO.x);                 // -i c (dt/2) O
+        Z[p * mm + q + d] = make_double2(h * cO.y, -h * cO.x);                 // -i c (dt/2) O (Q1: dt)
       }
     expm_serial(Z, mm, RZ, Z1, Z2);
     for (int p = 0; p < d * d; ++p) A[p] = make_double2(-A[p].x, -A[p].y);
@@ -2262,7 +2263,7 @@ sg_status run_backward_q2(sg_system* sys, Solve& sv, double2* pbar, GradAcc acc)
                           (size_t)2 * std::max(1, s.p.ne) * s.ta.nset * DL * DL * DL * DL * es;
   sg_status rc = onchip_q2_pulse_adjoint(sv.oc, s.p, drv_mode, s.K, sv.q2grad, adj_edges, sv.psi, pbar,
                                          s.N * s.ta.nsub, s.ta.nsub, s.ta.set_of, s.ta.nset, nst * Kd, gFc, st,
-                                         &sv.launches);
+                                         &sv.launches, s.ta.q1 != 0);
   if (rc != SG_OK)
     return sg_fail(ctx, rc, "the Q2 gradient needs 2..16 modes, <= 32 couplings, <= 16 drives and its buffers "
                             "in shared memory");
@@ -2332,9 +2333,6 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (s.q2 && grad && grad_ham)
     return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter solvers compute the pulse-parameter gradient only "
                                           "(grad_ham = NULL)");
-  if (grad && s.solver == SG_SOLVER_Q1)
-    return sg_fail(ctx, SG_E_UNSUPPORTED, "the first-order Suzuki-Trotter solver computes the evolution and the "
-                                          "fidelity only");
   for (int i = 0; i < s.nq; ++i)
     if (s.qpos[i] >= 0 && s.p.dims[i] < 2)
       return sg_fail(ctx, SG_E_INVALID, "computational states need >= 2 levels per qubit mode");

@@ -818,11 +818,14 @@ k_oc_q2(SlabPass sp, OcArgs oa, Q2Args qa, const typename CT<R>::T* __restrict__
 // the cross-density over mode i.  Each thread contracts its blocks' cross-densities
 // with M_k at once, so a sub-step reduces one scalar per drive over the CTA (warp
 // shuffles, then the warps in fixed order) into slot n (the sub-step) of the CTA's gF
-// block.  The 1-body factors are applied as Kronecker pairs like the forward.
+// block.  The 1-body factors are applied as Kronecker pairs like the forward.  The
+// first-order product Q1 takes the same route with one full-step 1-body factor per
+// step and each coupling once.
 constexpr int kQ2G = 16;          // drives of a Q2 gradient solve (per-thread partials)
 struct Q2AdjArgs {
   int nq, K, ne, n1f;             // modes, drives, couplings, 1-body factors of a half step
   int J;                          // Q2 sub-steps per step
+  int q1;                         // first-order product: per step the 1-body factors, then each coupling once
   int setoff[3];                  // first matrix of sub-step j's pull-back coupling set: 4 ne set(j)
   int row;                        // (nq + K) d^2: U_i(n)^dag then M_k(n)
   unsigned driven;                // bit i: a drive acts on mode i
@@ -875,11 +878,16 @@ k_oc_q2_adj(SlabPass sp, OcArgs oa, Q2AdjArgs qa, const typename CT<R>::T* __res
     R g[kQ2G];
 #pragma unroll
     for (int k = 0; k < kQ2G; ++k) g[k] = R(0);
-    for (int h = 0; h < 2; ++h) {
-      if (h == 1) {                                                  // couplings (palindrome)
-        for (int q = 0; q < 2 * qa.ne - 1; ++q) {
-          const int e = q < qa.ne ? q : 2 * qa.ne - 2 - q;
-          const C* Gi = G + (size_t)(so + 4 * e + (q == qa.ne - 1 ? 1 : 0)) * DL * DL * DL * DL;
+    // Q2: the second half step of the 1-body factors (h = 0), then the couplings and the
+    // first half step (h = 1).  Q1: the couplings in reverse order over the full step,
+    // then the step's full-step 1-body factors.
+    for (int h = qa.q1; h < 2; ++h) {
+      if (h == 1) {
+        const int nqe = qa.q1 ? qa.ne : 2 * qa.ne - 1;
+        for (int q = 0; q < nqe; ++q) {
+          const int e = qa.q1 ? qa.ne - 1 - q : (q < qa.ne ? q : 2 * qa.ne - 2 - q);   // Q2: the palindrome
+          const bool full = qa.q1 || q == qa.ne - 1;
+          const C* Gi = G + (size_t)(so + 4 * e + (full ? 1 : 0)) * DL * DL * DL * DL;
           const C* Gd = Gi + (size_t)2 * DL * DL * DL * DL;
           const Phase& P = qa.edge[e];
           for (int b = threadIdx.x; b < oa.nbt; b += blockDim.x) {
@@ -1588,7 +1596,7 @@ int q2adj_t(const OnchipPlan* oc, const Q2AdjArgs& qa, const void* rows, const v
 sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
                                   const void* edges, const double2* psi, const double2* bar, int N, int J,
                                   const int* set_of, int nset, long long nstK, double* gF_cta, cudaStream_t st,
-                                  int* launches) {
+                                  int* launches, bool q1) {
   const SlabPass& sp = oc->h->pass[0];
   const int DL = oc->h->DL;
   if ((size_t)oc->oa.b_G > oc->limit || p.nq < 2 || p.ne > 32 || K > kQ2G || K != oc->oa.K || J < 1 || J > 3 ||
@@ -1618,6 +1626,7 @@ sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const in
     qa.driven |= 1u << drv_mode[k];
   }
   qa.J = J;
+  qa.q1 = q1 ? 1 : 0;
   for (int j = 0; j < J; ++j) qa.setoff[j] = 4 * p.ne * set_of[j];      // per set and coupling: inverse and adjoint pairs
   int n = 0;
   if (oc->mixed) {

@@ -92,9 +92,11 @@ int onchip_dl(const OnchipPlan* oc);
 // half-step factors U_i(n)^-1 (states), their adjoints U_i(n)^dag (co-states), then
 // M_k(n) = U_i(n)^-1 L_k(n) with L_k the Frechet derivative of the local exponential
 // along drive k's operator; edges: per set and coupling the inverse (half, full) and
-// adjoint (half, full) coupling factors.  SG_E_UNSUPPORTED for one mode, more than 32
-// couplings or 16 drives, or when the layout does not fit in shared memory.
+// adjoint (half, full) coupling factors.  q1: the first-order product (N steps, rows of
+// its full-step factors; the couplings pulled back in reverse order by their full-step
+// factors).  SG_E_UNSUPPORTED for one mode, more than 32 couplings or 16 drives, or when
+// the layout does not fit in shared memory.
 sg_status onchip_q2_pulse_adjoint(const OnchipPlan* oc, const KPlan& p, const int* drv_mode, int K, const void* rows,
                                   const void* edges, const double2* psi, const double2* bar, int N, int J,
                                   const int* set_of, int nset, long long nstK, double* gF_cta, cudaStream_t st,
-                                  int* launches);
+                                  int* launches, bool q1 = false);

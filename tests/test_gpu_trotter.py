@@ -83,14 +83,25 @@ def test_q1_matches_oracle(sgctx, default_path, name):
     assert np.max(np.abs(q2 - psi)) > 1e-8
 
 
-def test_q1_gradient_is_refused(sgctx, default_path):
-    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
-    wl = CASES["transmon_pair"]()
+@pytest.mark.parametrize("name", ["transmon_pair", "ring4_l3", "pair_cr_l5", "local_ops_l3"])
+def test_q1_pulse_gradient_matches_oracle(sgctx, default_path, name):
+    """The first-order product's pulse gradient: the couplings pulled back in reverse
+    order by their full-step factors, then the step's full-step 1-body factors with the
+    Frechet derivatives along dt (not dt/2), against the oracle's adjoint."""
+    wl = CASES[name]()
     s = _system(sgctx, wl)
-    with pytest.raises(SGError) as e:
-        s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", solver="q1",
-                        ham=False)
-    assert e.value.code == SG_E_UNSUPPORTED
+    F_r, g_r = q2_pulse_gradient(wl, scheme="q1")
+    scale = max(1.0, np.max(np.abs(g_r)))
+    for prec, tol_F, tol_g in (("fp64", 1e-10, 1e-9), ("mixed", 1e-5, 2e-4)):
+        F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind=wl["fid_kind"],
+                                    precision=prec, ham=False, solver="q1")
+        assert gh is None and gp.shape == g_r.shape
+        Fk = F[0] if wl["fid_kind"] == "avg" else F[1]
+        assert abs(Fk - F_r) < tol_F, (prec, Fk, F_r)
+        assert np.max(np.abs(gp - g_r)) < tol_g * scale, (prec, np.max(np.abs(gp - g_r)), scale)
+    # not Q2's gradient: the two products differ at this step
+    _, g2 = q2_pulse_gradient(wl, scheme="q2")
+    assert np.max(np.abs(g2 - g_r)) > 1e-6 * np.max(np.abs(g_r))
 
 
 @pytest.mark.parametrize("scheme", ["q2", "q4", "q4j"])
