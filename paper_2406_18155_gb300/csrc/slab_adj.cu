@@ -427,20 +427,8 @@ k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
 #pragma unroll
   for (int j = 0; j < kMaxDrv; ++j) g[j] = 0.f;
   const long long ntiles = (long long)sp.S * sp.ntpc;
-  __shared__ LPf pf[5];                            // the next tile's X, Y; this tile's epilogue operands
-  __shared__ int npf;
-  if (tid == 0) {
-    pf[0] = LPf{reinterpret_cast<const char*>(X), (int)sizeof(float2)};
-    pf[1] = LPf{reinterpret_cast<const char*>(Y), (int)sizeof(float2)};
-    int n = 2;
-    if (KIND == 1 || KIND == 2) pf[n++] = LPf{reinterpret_cast<const char*>(yA), (int)sizeof(float2)};
-    if (KIND >= 2) pf[n++] = LPf{reinterpret_cast<const char*>(pbar), (int)sizeof(double2)};
-    if (KIND >= 2 && STAGE < 3) pf[n++] = LPf{reinterpret_cast<const char*>(Db), (int)sizeof(float2)};
-    npf = n - 2;
-  }
-  const bool contig = ltile_contig(sp, tid);        // (a barrier: pf and npf are visible after it)
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long tb = tile_base(sp, tile), bl = tb + olo;
+    const long long bl = tile_base(sp, tile) + olo;
 #pragma unroll
     for (int j0 = 0; j0 < LJ; j0 += 4) {
       float2 vx[4], vy[4];
@@ -457,13 +445,6 @@ k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
       }
     }
     __syncthreads();
-    // while the phases run: the next tile's inputs and this tile's epilogue operands
-    // stream into L2
-    if (tile + gridDim.x < ntiles) {
-      const long long tn = tile_base(sp, tile + gridDim.x);
-      lprefetch_l2(pf, 2, tn, tn + olo, ohi, contig, tid);
-    }
-    lprefetch_l2(pf + 2, npf, tb, bl, ohi, contig, tid);
     lpass(nph, lph, M, xs, ks, tid);
     if (KIND == 0) lepi_adj<0, 0>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h);
     else if (KIND == 1) lepi_adj<1, 0>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h);
