@@ -196,7 +196,7 @@ typedef struct {
  * eigenstates of the idle Hamiltonian (lab frame, no drives: level energies and
  * couplings) of largest overlap with the bare computational states, each signed so
  * that overlap is positive; the evolved columns start in them and are projected on
- * them (U -> V^dag U V restricted to the computational states).  Needs D <= 256, a real
+ * them (U -> V^dag U V restricted to the computational states).  Needs D <= 1024, a real
  * idle Hamiltonian, non-degenerate dressed computational levels and every evolved
  * column a computational state (each once), else SG_E_INVALID / SG_E_UNSUPPORTED; with
  * sg_fidelity_grad, grad_ham must be NULL (the pulse gradient only). */

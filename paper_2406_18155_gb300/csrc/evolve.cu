@@ -2379,8 +2379,8 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   if (o->basis != SG_BASIS_PRODUCT && o->basis != SG_BASIS_DRESSED)
     return sg_fail(ctx, SG_E_INVALID, "basis must be SG_BASIS_PRODUCT or SG_BASIS_DRESSED");
   const bool dressed = o->basis == SG_BASIS_DRESSED;
-  if (dressed && (s.D > kMaxDressed || !full || Sc != s.S))
-    return sg_fail(ctx, SG_E_INVALID, "the dressed basis needs D <= 256 and the evolved columns to be the "
+  if (dressed && (s.D > kMaxDressedLarge || !full || Sc != s.S))
+    return sg_fail(ctx, SG_E_INVALID, "the dressed basis needs D <= 1024 and the evolved columns to be the "
                                       "computational states, each once");
   if (dressed && grad && grad_ham)
     return sg_fail(ctx, SG_E_UNSUPPORTED, "the dressed basis computes the pulse-parameter gradient only "
@@ -2412,7 +2412,7 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter gradient runs on the on-chip kernels (D <= 4096)");
   double2* Vc = nullptr;
   if (dressed) {
-    // dressed computational states of the idle Hamiltonian (one block, FP64 Jacobi)
+    // dressed computational states of the idle Hamiltonian (FP64 Jacobi)
     DressArgs da{};
     da.D = (int)s.D; da.nq = s.nq; da.ne = s.p.ne; da.Dc = s.Dc;
     for (int i = 0; i < s.nq; ++i) {
@@ -2431,12 +2431,11 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
     long long* comp_dev = sv.ar.get<long long>(s.Dc);
     int* derr = sv.ar.get<int>(1);
     Vc = sv.ar.get<double2>((size_t)s.D * s.Dc);
-    da.work = sv.ar.get<double>(2 * (size_t)s.D * s.D);
+    da.work = sv.ar.get<double>(dressed_work_doubles((int)s.D));
     if (!comp_dev || !derr || !Vc || !da.work) return sg_fail(ctx, SG_E_NOMEM, "device allocation failed");
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(comp_dev, comp.data(), s.Dc * sizeof(long long), cudaMemcpyHostToDevice, st));
     da.E = sv.E_dev; da.opd = sv.opd_dev; da.comp = comp_dev; da.Vc = Vc; da.err = derr;
-    SG_CUDA_TRY(ctx, launch_dressed(da, st));
-    ++sv.launches;
+    SG_CUDA_TRY(ctx, launch_dressed(da, st, &sv.launches));
     int herr = 0;
     SG_CUDA_TRY(ctx, cudaStreamSynchronize(st));     // reads only from an idle stream (see dcopy)
     SG_CUDA_TRY(ctx, cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, st));

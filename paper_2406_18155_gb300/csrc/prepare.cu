@@ -14,10 +14,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
 // Parallel cyclic Jacobi eigensolver for a symmetric M x M matrix held in shared
 // memory (row-major, leading dimension M).  On return A is diagonal (eigenvalues
 // on the diagonal, unsorted) and V holds the eigenvectors in columns.  Rotations
@@ -346,11 +342,68 @@ __global__ void __launch_bounds__(kThreads) k_chain(ChainArgs a) {
   if (tid == 0) a.out[q * 3 + p] = red[0];
 }
 
-// One block: the idle Hamiltonian H[r][c] = delta_rc sum_i E_i[l_i(r)] + sum_e J_e
-// A_e[l_a(r)][l_a(c)] B_e[l_b(r)][l_b(c)] (other digits equal), real symmetric (flag 1
-// otherwise), Jacobi eigenpairs, then per label j the eigenvector k of largest
-// |V[comp_j][k]| (flag 2 if two labels share one, flag 3 if its eigenvalue is within
-// 1e-9 of another), signed so that V[comp_j][k] > 0.
+// Element (r, c) of the idle Hamiltonian H[r][c] = delta_rc sum_i E_i[l_i(r)] + sum_e J_e
+// A_e[l_a(r)][l_a(c)] B_e[l_b(r)][l_b(c)] (other digits equal); hi: its imaginary part.
+__device__ void dressed_h(const DressArgs& a, int r, int c, double& h, double& hi) {
+  h = 0.0;
+  hi = 0.0;
+  if (r == c)
+    for (int q = 0; q < a.nq; ++q) h += a.E[a.eoff[q] + (int)((r / a.st[q]) % a.dims[q])];
+  for (int e = 0; e < a.ne; ++e) {
+    const int qa = a.e_a[e], qb = a.e_b[e];
+    bool same = true;
+    for (int q = 0; q < a.nq; ++q)
+      if (q != qa && q != qb && (r / a.st[q]) % a.dims[q] != (c / a.st[q]) % a.dims[q]) same = false;
+    if (!same) continue;
+    const int da = a.dims[qa], db = a.dims[qb];
+    const int ra = (int)((r / a.st[qa]) % da), ca = (int)((c / a.st[qa]) % da);
+    const int rb = (int)((r / a.st[qb]) % db), cb = (int)((c / a.st[qb]) % db);
+    const double2 x = a.opd[a.opd_off[qa] + a.e_opa[e] * da * da + ra * da + ca];
+    const double2 y = a.opd[a.opd_off[qb] + a.e_opb[e] * db * db + rb * db + cb];
+    h += a.J[e] * (x.x * y.x - x.y * y.y);
+    hi += a.J[e] * (x.x * y.y + x.y * y.x);
+  }
+}
+
+// One block, after the eigensolve (eigenvalues on the diagonal of A, eigenvectors in
+// the columns of V): per label j the eigenvector k of largest |V[comp_j][k]| (flag 2 if
+// two labels share one, flag 3 if its eigenvalue is within 1e-9 of another), signed so
+// that V[comp_j][k] > 0, into Vc; *err from the flags in bad (bit 0: complex H).
+__device__ void dressed_pick(const DressArgs& a, const double* A, const double* V, int* kk, int* bad) {
+  const int D = a.D, tid = threadIdx.x, nt = blockDim.x;
+  for (int j = tid; j < a.Dc; j += nt) {
+    const int r = (int)a.comp[j];
+    int best = 0;
+    double bv = -1.0;
+    for (int k = 0; k < D; ++k) {
+      const double v = fabs(V[(size_t)r * D + k]);
+      if (v > bv) { bv = v; best = k; }
+    }
+    kk[j] = best;
+  }
+  __syncthreads();
+  double scale = 0.0;
+  for (int k = 0; k < D; ++k) scale = fmax(scale, fabs(A[(size_t)k * D + k]));
+  for (int j = tid; j < a.Dc; j += nt) {
+    for (int m = 0; m < j; ++m)
+      if (kk[m] == kk[j]) atomicOr(bad, 2);
+    const double lk = A[(size_t)kk[j] * D + kk[j]];
+    for (int k = 0; k < D; ++k)
+      if (k != kk[j] && fabs(A[(size_t)k * D + k] - lk) <= 1e-9 * fmax(1.0, scale)) atomicOr(bad, 4);
+  }
+  __syncthreads();
+  for (int i = tid; i < D * a.Dc; i += nt) {
+    const int r = i / a.Dc, j = i - r * a.Dc;
+    const int k = kk[j];
+    const double sg = V[(size_t)a.comp[j] * D + k] < 0.0 ? -1.0 : 1.0;
+    a.Vc[i] = make_double2(sg * V[(size_t)r * D + k], 0.0);
+  }
+  __syncthreads();
+  if (tid == 0) *a.err = *bad & 1 ? 1 : (*bad & 2 ? 2 : (*bad & 4 ? 3 : 0));
+}
+
+// One block (D <= kMaxDressed): the idle Hamiltonian in global scratch, real
+// symmetric (flag 1 otherwise), Jacobi eigenpairs in the block, then dressed_pick.
 __global__ void __launch_bounds__(kThreads) k_dressed(DressArgs a) {
   const int D = a.D, tid = threadIdx.x, nt = blockDim.x;
   double* A = a.work;                                        // D x D, then V (global: D <= 256)
@@ -363,56 +416,139 @@ __global__ void __launch_bounds__(kThreads) k_dressed(DressArgs a) {
   __syncthreads();
   for (int i = tid; i < D * D; i += nt) {
     const int r = i / D, c = i - r * D;
-    double h = 0.0, hi = 0.0;
-    if (r == c)
-      for (int q = 0; q < a.nq; ++q) h += a.E[a.eoff[q] + (int)((r / a.st[q]) % a.dims[q])];
-    for (int e = 0; e < a.ne; ++e) {
-      const int qa = a.e_a[e], qb = a.e_b[e];
-      bool same = true;
-      for (int q = 0; q < a.nq; ++q)
-        if (q != qa && q != qb && (r / a.st[q]) % a.dims[q] != (c / a.st[q]) % a.dims[q]) same = false;
-      if (!same) continue;
-      const int da = a.dims[qa], db = a.dims[qb];
-      const int ra = (int)((r / a.st[qa]) % da), ca = (int)((c / a.st[qa]) % da);
-      const int rb = (int)((r / a.st[qb]) % db), cb = (int)((c / a.st[qb]) % db);
-      const double2 x = a.opd[a.opd_off[qa] + a.e_opa[e] * da * da + ra * da + ca];
-      const double2 y = a.opd[a.opd_off[qb] + a.e_opb[e] * db * db + rb * db + cb];
-      h += a.J[e] * (x.x * y.x - x.y * y.y);
-      hi += a.J[e] * (x.x * y.y + x.y * y.x);
-    }
+    double h, hi;
+    dressed_h(a, r, c, h, hi);
     if (fabs(hi) > 1e-12 * (fabs(h) + 1.0)) atomicOr(&bad, 1);
     A[i] = h;
   }
   __syncthreads();
   jacobi_eigen(A, V, D, cs, pairs);
-  for (int j = tid; j < a.Dc; j += nt) {
-    const int r = (int)a.comp[j];
-    int best = 0;
-    double bv = -1.0;
-    for (int k = 0; k < D; ++k) {
-      const double v = fabs(V[r * D + k]);
-      if (v > bv) { bv = v; best = k; }
+  dressed_pick(a, A, V, kk, &bad);
+}
+
+// ---- the same for kMaxDressed < D <= kMaxDressedLarge, over the whole GPU ----------
+// The matrix lives in global memory (L2-resident at these sizes) and every round of the
+// round-robin Jacobi ordering is one launch: for rows i and index pairs (p', q'),
+//   A_new[i][{p', q'}] = (R_k A_old)[i][{p', q'}] J_k'
+// with k the pair of i and R_k, J_k' the row and column rotations of pairs k and k'
+// (the same 2 x 2 Schur rotations as jacobi_eigen, from A_old's diagonal blocks), and
+// V[i][{p', q'}] <- V[i][{p', q'}] J_k'.  Every thread reads only A_old, so the
+// rotations of one round need no barrier; A_old and A_new swap per round.
+
+// The pairs of round r (circle method over Mp players; index M is a dummy when M is odd):
+// position 0 holds player 0, position pos >= 1 holds 1 + (pos - 1 + r) mod (Mp - 1), and
+// positions k and Mp - 1 - k play each other.
+__device__ __forceinline__ int jac_player(int pos, int r, int Mp) {
+  return pos == 0 ? 0 : 1 + (pos - 1 + r) % (Mp - 1);
+}
+__device__ __forceinline__ int jac_pos(int i, int r, int Mp) {
+  return i == 0 ? 0 : 1 + ((i - 1 - r) % (Mp - 1) + (Mp - 1)) % (Mp - 1);
+}
+// Rotation (c, s) of the pair (p, q), p < q, from A's diagonal block; (1, 0) for the dummy.
+__device__ __forceinline__ void jac_cs(const double* A, int M, int p, int q, double& c, double& s) {
+  c = 1.0;
+  s = 0.0;
+  if (q >= M) return;
+  const double apq = A[(size_t)p * M + q];
+  if (apq == 0.0) return;
+  const double app = A[(size_t)p * M + p], aqq = A[(size_t)q * M + q];
+  const double tau = (aqq - app) / (2.0 * apq);
+  const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
+__global__ void k_dressed_build(DressArgs a, double* __restrict__ A, double* __restrict__ V) {
+  const long long D = a.D, n = D * D;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / D), c = (int)(i - r * D);
+    double h, hi;
+    dressed_h(a, r, c, h, hi);
+    if (fabs(hi) > 1e-12 * (fabs(h) + 1.0)) atomicOr(a.err, 1);
+    A[i] = h;
+    V[i] = r == c ? 1.0 : 0.0;
+  }
+}
+
+__global__ void k_jac_round(const double* __restrict__ Ao, double* __restrict__ An, double* __restrict__ V, int M,
+                            int Mp, int r) {
+  const int npair = Mp / 2;
+  const long long n = (long long)M * npair;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(x / npair), k2 = (int)(x - (long long)i * npair);
+    // the pair (p, q) of row i and its rotation
+    const int pos = jac_pos(i, r, Mp), k = pos < npair ? pos : Mp - 1 - pos;
+    const int a0 = jac_player(k, r, Mp), b0 = jac_player(Mp - 1 - k, r, Mp);
+    const int p = min(a0, b0), q = max(a0, b0);
+    double c, s;
+    jac_cs(Ao, M, p, q, c, s);
+    // the column pair (p2, q2) and its rotation
+    const int a2 = jac_player(k2, r, Mp), b2 = jac_player(Mp - 1 - k2, r, Mp);
+    const int p2 = min(a2, b2), q2 = max(a2, b2);
+    double c2, s2;
+    jac_cs(Ao, M, p2, q2, c2, s2);
+    // row rotation: row p <- c row p - s row q, row q <- s row p + c row q
+    const double* rp = Ao + (size_t)p * M;
+    const double* rq = q < M ? Ao + (size_t)q * M : rp;
+    const bool hq2 = q2 < M;
+    const double bp = rp[p2], bq = q < M ? rq[p2] : 0.0;
+    const double cp = hq2 ? rp[q2] : 0.0, cq = q < M && hq2 ? rq[q2] : 0.0;
+    double u, w;                                           // (R A)[i][p2], (R A)[i][q2]
+    if (i == p) { u = c * bp - s * bq; w = c * cp - s * cq; }
+    else        { u = s * bp + c * bq; w = s * cp + c * cq; }
+    // column rotation: col p2 <- c2 col p2 - s2 col q2, col q2 <- s2 col p2 + c2 col q2
+    double np2 = c2 * u - s2 * w, nq2 = s2 * u + c2 * w;
+    if (k2 == k && s != 0.0) {                             // the annihilated pair is exactly zero
+      if (i == p) nq2 = 0.0;
+      else np2 = 0.0;
     }
-    kk[j] = best;
+    double* out = An + (size_t)i * M;
+    out[p2] = np2;
+    if (hq2) out[q2] = nq2;
+    double* v = V + (size_t)i * M;
+    if (hq2) {
+      const double vp = v[p2], vq = v[q2];
+      v[p2] = c2 * vp - s2 * vq;
+      v[q2] = s2 * vp + c2 * vq;
+    }
   }
+}
+
+// Off-diagonal and diagonal squared mass of A: per block partial sums (each thread a
+// fixed stride of the entries, then the block in a fixed tree), summed in block order.
+__global__ void k_jac_mass(const double* __restrict__ A, int M, double* __restrict__ part) {
+  __shared__ double ro[kThreads], rd[kThreads];
+  const long long n = (long long)M * M;
+  double off = 0.0, dia = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(i / M), c = (int)(i - (long long)r * M);
+    if (r != c) off += A[i] * A[i]; else dia += A[i] * A[i];
+  }
+  ro[threadIdx.x] = off;
+  rd[threadIdx.x] = dia;
   __syncthreads();
-  double scale = 0.0;
-  for (int k = 0; k < D; ++k) scale = fmax(scale, fabs(A[k * D + k]));
-  for (int j = tid; j < a.Dc; j += nt) {
-    for (int m = 0; m < j; ++m)
-      if (kk[m] == kk[j]) atomicOr(&bad, 2);
-    const double lk = A[kk[j] * D + kk[j]];
-    for (int k = 0; k < D; ++k)
-      if (k != kk[j] && fabs(A[k * D + k] - lk) <= 1e-9 * fmax(1.0, scale)) atomicOr(&bad, 4);
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) { ro[threadIdx.x] += ro[threadIdx.x + s]; rd[threadIdx.x] += rd[threadIdx.x + s]; }
+    __syncthreads();
   }
+  if (threadIdx.x == 0) { part[2 * blockIdx.x] = ro[0]; part[2 * blockIdx.x + 1] = rd[0]; }
+}
+__global__ void k_jac_mass_sum(const double* __restrict__ part, int nb, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double o = 0.0, d = 0.0;
+    for (int b = 0; b < nb; ++b) { o += part[2 * b]; d += part[2 * b + 1]; }
+    out[0] = o;
+    out[1] = d;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_dressed_pick(DressArgs a, const double* __restrict__ A,
+                                                           const double* __restrict__ V) {
+  __shared__ int kk[kMaxDressed];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = *a.err;                        // bit 0 from the build
   __syncthreads();
-  for (int i = tid; i < D * a.Dc; i += nt) {
-    const int r = i / a.Dc, j = i - r * a.Dc;
-    const int k = kk[j];
-    const double sg = V[(int)a.comp[j] * D + k] < 0.0 ? -1.0 : 1.0;
-    a.Vc[i] = make_double2(sg * V[r * D + k], 0.0);
-  }
-  if (tid == 0) *a.err = bad & 1 ? 1 : (bad & 2 ? 2 : (bad & 4 ? 3 : 0));
+  dressed_pick(a, A, V, kk, &bad);
 }
 
 }  // namespace
@@ -542,8 +678,48 @@ sg_status sg_chain_device_params(sg_system* sys, const double2* opbar_dev, const
   return SG_OK;
 }
 
-cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st) {
-  if (a.D < 2 || a.D > kMaxDressed || a.Dc > a.D) return cudaErrorInvalidValue;
-  k_dressed<<<1, kThreads, 0, st>>>(a);
+size_t dressed_work_doubles(int D) {
+  const size_t D2 = (size_t)D * D;
+  return D <= kMaxDressed ? 2 * D2 : 3 * D2 + 2 * (size_t)kJacMassBlocks + 2;
+}
+
+cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st, int* launches) {
+  if (a.D < 2 || a.D > kMaxDressedLarge || a.Dc > a.D || a.Dc > kMaxDressed) return cudaErrorInvalidValue;
+  if (a.D <= kMaxDressed) {
+    k_dressed<<<1, kThreads, 0, st>>>(a);
+    if (launches) ++*launches;
+    return cudaGetLastError();
+  }
+  const int M = a.D, Mp = (M + 1) & ~1, npair = Mp / 2;
+  const size_t D2 = (size_t)M * M;
+  double* A = a.work;
+  double* B = A + D2;
+  double* V = B + D2;
+  double* part = V + D2;
+  double* mass = part + 2 * kJacMassBlocks;
+  cudaError_t e = cudaMemsetAsync(a.err, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int gb = (int)std::min<long long>(4096, ((long long)D2 + kThreads - 1) / kThreads);
+  k_dressed_build<<<gb, kThreads, 0, st>>>(a, A, V);
+  int n = 1;
+  const int gr = (int)(((long long)M * npair + kThreads - 1) / kThreads);
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    k_jac_mass<<<kJacMassBlocks, kThreads, 0, st>>>(A, M, part);
+    k_jac_mass_sum<<<1, 32, 0, st>>>(part, kJacMassBlocks, mass);
+    n += 2;
+    double hm[2] = {0.0, 0.0};
+    if ((e = cudaMemcpyAsync(hm, mass, sizeof(hm), cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if (hm[0] <= 1e-32 * hm[1] || hm[0] == 0.0) break;       // the criterion of jacobi_eigen
+    for (int r = 0; r < Mp - 1; ++r) {
+      k_jac_round<<<gr, kThreads, 0, st>>>(A, B, V, M, Mp, r);
+      std::swap(A, B);
+    }
+    n += Mp - 1;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  k_dressed_pick<<<1, kThreads, 0, st>>>(a, A, V);
+  ++n;
+  if (launches) *launches += n;
   return cudaGetLastError();
 }

@@ -124,12 +124,15 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
                            double* grad_pulse, double* grad_ham, int ckpt,
                            sg_allreduce_fn red = nullptr, void* red_user = nullptr);
 
-// Dressed computational states (the eigenbasis of the idle Hamiltonian, App. C): one
-// block builds the D x D idle Hamiltonian (D <= kMaxDressed) in global scratch,
-// diagonalises it with the parallel Jacobi solver, assigns every computational label
-// the eigenvector of largest overlap on its bare state, and fixes the sign so that
-// overlap is positive.
+// Dressed computational states (the eigenbasis of the idle Hamiltonian, App. C): the
+// D x D idle Hamiltonian is built in global scratch and diagonalised by the parallel
+// (round-robin) Jacobi solver, in one block for D <= kMaxDressed and over the whole GPU
+// for D <= kMaxDressedLarge (one launch per round, convergence read by the host after
+// every sweep); every computational label (Dc <= kMaxDressed) takes the eigenvector of
+// largest overlap on its bare state, signed so that this overlap is positive.
 constexpr int kMaxDressed = 256;
+constexpr int kMaxDressedLarge = 1024;
+constexpr int kJacMassBlocks = 152;
 struct DressArgs {
   int D, nq, ne, Dc;
   int dims[SG_MAXQ];
@@ -141,9 +144,12 @@ struct DressArgs {
   const double2* opd;           // flat truncated operators
   const long long* comp;        // Dc flat rows of the bare computational states
   double2* Vc;                  // out: D x Dc (row-major)
-  double* work;                 // scratch: 2 D^2 doubles (the matrix, then its eigenvectors)
+  double* work;                 // scratch of dressed_work_doubles(D) doubles
   int* err;                     // out: 0, 1 complex idle Hamiltonian, 2 shared dressed
                                 // state, 3 degenerate dressed level
 };
-// Launches the dressed-state kernel on stream st (no synchronisation).
-cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st);
+// Runs the dressed-state solve on stream st: one launch for D <= kMaxDressed (no
+// synchronisation), else the launches of the GPU-wide Jacobi with one stream
+// synchronisation per sweep.  launches (nullable): incremented by the launch count.
+cudaError_t launch_dressed(const DressArgs& a, cudaStream_t st, int* launches);
+size_t dressed_work_doubles(int D);

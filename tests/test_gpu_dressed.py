@@ -81,11 +81,42 @@ def test_dressed_requests_that_are_refused(sgctx):
         s.fidelity(wl["T"], wl["dt"], wl["target"], list(wl["col_index"]) + [2], precision="fp64",
                    basis="dressed")
     assert e.value.code == SG_E_INVALID
-    big = W.fluxonium_chain(seed=8, nq=4, levels=5, T=0.2, dt=0.01, nseg=2)          # D = 625 > 256
+    big = W.fluxonium_chain(seed=8, nq=5, levels=5, T=0.2, dt=0.01, nseg=2)          # D = 3125 > 1024
     s2 = _system(sgctx, big)
     with pytest.raises(SGError) as e:
         s2.fidelity(big["T"], big["dt"], big["target"], big["col_index"], precision="fp64", basis="dressed")
     assert e.value.code == SG_E_INVALID
+
+
+def _large(nq, levels, T):
+    wl = W.fluxonium_chain(seed=8, nq=nq, levels=levels, T=T, dt=0.01, nseg=2)
+    wl["fid_kind"] = "avg"                   # F_state of this target is ~1e-12
+    return wl
+
+
+@pytest.mark.parametrize("nq,levels,T", [(4, 5, 0.1), (5, 4, 0.06)])
+def test_dressed_beyond_one_block(sgctx, nq, levels, T):
+    """D = 625 and D = 1024 (the largest): the idle Hamiltonian is diagonalised by the
+    Jacobi rounds over the whole GPU instead of one block."""
+    wl = _large(nq, levels, T)
+    s = _system(sgctx, wl)
+    Fa_r, Fs_r, Uc_r = dressed_fidelities(wl)
+    Fa, Fs, Uc = s.fidelity(wl["T"], wl["dt"], wl["target"], wl["col_index"], precision="fp64", basis="dressed")
+    assert abs(Fa - Fa_r) < 1e-10 and abs(Fs - Fs_r) < 1e-10
+    assert np.max(np.abs(Uc - Uc_r)) < 1e-10
+
+
+def test_dressed_gradient_beyond_one_block(sgctx):
+    wl = _large(4, 5, 0.1)
+    s = _system(sgctx, wl)
+    F_r, g_r = dressed_pulse_gradient(wl, "avg")
+    scale = np.max(np.abs(g_r))
+    for prec, tol_F, tol_g in (("fp64", 1e-10, 1e-8), ("mixed", 1e-5, 1e-3)):
+        F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="avg", precision=prec,
+                                    ham=False, ckpt=7, basis="dressed")
+        assert gh is None
+        assert abs(F[0] - F_r) < tol_F
+        assert np.max(np.abs(gp - g_r)) <= tol_g * scale, (prec, np.max(np.abs(gp - g_r)), scale)
 
 
 def test_dressed_basis_with_the_q2_solver(sgctx):
