@@ -394,6 +394,9 @@ __device__ __forceinline__ void lepi_adj(const float2* __restrict__ ks, const fl
 
 // Lean adjoint stage pass: the operation of k_zslab_adj<float, 4, true> on 4096-entry
 // tiles, with the index work of slab_lean.cuh.
+// entries of the two input tiles a thread loads before it stores any (all 16: 32 loads in
+// flight per thread, one DRAM round trip per tile instead of four)
+constexpr int kLB = 16;
 __global__ void __launch_bounds__(kST, 2)
 k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__ Y,
            const float2* __restrict__ zrow, const float2* __restrict__ zop, const double2* __restrict__ phrow,
@@ -430,15 +433,15 @@ k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long bl = tile_base(sp, tile) + olo;
 #pragma unroll
-    for (int j0 = 0; j0 < LJ; j0 += 4) {
-      float2 vx[4], vy[4];
+    for (int j0 = 0; j0 < LJ; j0 += kLB) {
+      float2 vx[kLB], vy[kLB];
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
+      for (int jj = 0; jj < kLB; ++jj) {
         vx[jj] = X[bl + ohi[j0 + jj]];
         vy[jj] = Y[bl + ohi[j0 + jj]];
       }
 #pragma unroll
-      for (int jj = 0; jj < 4; ++jj) {
+      for (int jj = 0; jj < kLB; ++jj) {
         const float2 f = zcmul(pl, phi[j0 + jj]);
         xs[s0 + 273 * (j0 + jj)] = zcmulc(f, vx[jj]);
         ys[s0 + 273 * (j0 + jj)] = zcmulc(f, vy[jj]);
