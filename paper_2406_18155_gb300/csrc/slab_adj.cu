@@ -430,8 +430,18 @@ k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
 #pragma unroll
   for (int j = 0; j < kMaxDrv; ++j) g[j] = 0.f;
   const long long ntiles = (long long)sp.S * sp.ntpc;
+  __shared__ LPf pf[3];                            // this tile's epilogue operands
+  __shared__ int npf;
+  if (tid == 0) {
+    int n = 0;
+    if (KIND == 1 || KIND == 2) pf[n++] = LPf{reinterpret_cast<const char*>(yA), (int)sizeof(float2)};
+    if (KIND >= 2) pf[n++] = LPf{reinterpret_cast<const char*>(pbar), (int)sizeof(double2)};
+    if (KIND >= 2 && STAGE < 3) pf[n++] = LPf{reinterpret_cast<const char*>(Db), (int)sizeof(float2)};
+    npf = n;
+  }
+  const bool contig = ltile_contig(sp, tid);        // (a barrier: pf and npf are visible after it)
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long bl = tile_base(sp, tile) + olo;
+    const long long tb = tile_base(sp, tile), bl = tb + olo;
 #pragma unroll
     for (int j0 = 0; j0 < LJ; j0 += kLB) {
       float2 vx[kLB], vy[kLB];
@@ -448,6 +458,8 @@ k_lean_adj(SlabPass sp, const float2* __restrict__ X, const float2* __restrict__
       }
     }
     __syncthreads();
+    // the epilogue's operands of this tile stream into L2 while its phases run
+    lprefetch_l2(pf, npf, tb, bl, ohi, contig, tid);
     lpass(nph, lph, M, xs, ks, tid);
     if (KIND == 0) lepi_adj<0, 0>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h);
     else if (KIND == 1) lepi_adj<1, 0>(ks, phi, pl, s0, ohi, bl, pbar, Xn, Db, yA, h);
