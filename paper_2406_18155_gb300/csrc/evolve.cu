@@ -1746,11 +1746,11 @@ sg_status upload_and_tables(sg_system* sys, const sg_evolve_opts* o, Solve& sv, 
   const size_t nst = s.q2 ? 0 : 3ull * s.N;
   if (s.q2) {
     // Q2 reads no RK4 tables; it runs on the on-chip kernels, or beyond them on the
-    // tiles of a two-pass plan (the palindromic products; Q1 on-chip only)
-    if (!sv.oc && !(sv.slab && !s.ta.q1 && slab_q2_ok(sv.slab, s.p, sv.mixed)))
+    // tiles of a two-pass plan
+    if (!sv.oc && !(sv.slab && slab_q2_ok(sv.slab, s.p, sv.mixed)))
       return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter solvers run on the on-chip kernels (every mode with "
                                             "the same level count 2..5 and D <= 4096) or on the tiles of a two-pass "
-                                            "plan whose first pass holds the first couplings (Q2, Q4, Q4j)");
+                                            "plan whose first pass holds the first couplings");
   } else if (f32only) {
     sv.coef32 = sv.ar.get<float>(nst * std::max(1, s.K));
     sv.ph32 = sv.ar.get<float2>(nst * s.sumd);
@@ -2227,7 +2227,7 @@ sg_status run_q2(sg_system* sys, Solve& sv, const long long* cols_dev, bool init
       X = X32;
     }
     sv.launches += slab_q2_run(sv.slab, sv.mixed, sv.q2rows, sv.q2edges, X, s.N * s.ta.nsub, s.ta.nsub,
-                               s.ta.set_of, st);
+                               s.ta.set_of, s.ta.q1 != 0, st);
     if (sv.mixed) k_widen<<<grid_for(n), kT, 0, st>>>(X32, pint, n);
     slab_from_internal(sv.slab, pint, sv.psi, st);
     sv.launches += sv.mixed ? 4 : 2;

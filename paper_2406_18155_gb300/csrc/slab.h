@@ -78,6 +78,8 @@ void slab_q2_free(SlabPlanHost* sp);
 int slab_dl(const SlabPlanHost* sp);
 // M = N J sub-steps from X (in place).  rows: (M + 1) x nq x DL^2 merged 1-body factors
 // (the Q2 tables of the on-chip path), edges: per set and coupling the half- and
-// full-step unitaries; sub-step m uses set set_of[m % J].  Returns launches.
+// full-step unitaries; sub-step m uses set set_of[m % J].  q1: the first-order product
+// (M steps; rows of its full-step factors, each coupling once per step by its full-step
+// unitary).  Returns launches.
 int slab_q2_run(const SlabPlanHost* sp, bool mixed, const void* rows, const void* edges, void* X, int M, int J,
-                const int* set_of, cudaStream_t st);
+                const int* set_of, bool q1, cudaStream_t st);

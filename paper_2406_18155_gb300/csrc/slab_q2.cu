@@ -12,6 +12,11 @@
 //   pass B (tiles of G2):  merged row of the modes of G2 outside G1, E2 forward (half),
 //                          coupling ne-1 (full), E2 reversed (half)
 // and after the last sub-step pass A without E1 forward and pass B with the row alone.
+// The first-order product Q1 (each term once per step, full-step factors; the tables'
+// row m holds step m + 1's 1-body factors) is one pass of each kind per step:
+//   pass A:  row of G1's modes, E1 (full step, term order)
+//   pass B:  row of the modes of G2 outside G1, E2 (full step, term order)
+// (G2's other modes' factors commute with E1, so this is the step's term order).
 // Each pass loads a tile, applies its factors in shared memory (one block of d x d
 // entries per thread and factor) and writes the tile back in place.
 #include "sg_internal.h"
@@ -124,6 +129,7 @@ k_slab_q2(SlabPass sp, SQList fl, const typename CT<R>::T* __restrict__ row,
 
 struct SQPlan {
   SQList a_first, a_mid, a_final, b_mid, b_final;
+  SQList a_q1, b_q1;                              // the first-order product's step
   size_t sm_a = 0, sm_b = 0;
   int grid = 0;
 };
@@ -220,14 +226,20 @@ bool slab_q2_ok(SlabPlanHost* h, const KPlan& p, bool mixed) {
     add_coupling(E[1][j].second, DL, 2 * E[1][j].first, 0, q->b_mid, ok, sp_of(E[1][j].first));
   q->b_final = SQList{};
   add_onebody(B, DL, m2, q->b_final, ok);
+  q->a_q1 = SQList{};
+  add_onebody(A, DL, m1, q->a_q1, ok);
+  for (auto& e : E[0]) add_coupling(e.second, DL, 2 * e.first + 1, 0, q->a_q1, ok, sp_of(e.first));
+  q->b_q1 = SQList{};
+  add_onebody(B, DL, m2, q->b_q1, ok);
+  for (auto& e : E[1]) add_coupling(e.second, DL, 2 * e.first + 1, 0, q->b_q1, ok, sp_of(e.first));
   const size_t csz = mixed ? sizeof(float2) : sizeof(double2);
   const size_t D4 = (size_t)DL * DL * DL * DL;
   const size_t nrow = (size_t)p.nq * DL * DL;
   auto need = [&](const SlabPass& sp, const SQList& L) {
     return (2 * (size_t)spad(sp.T) + nrow + (size_t)L.ndense * D4) * csz;
   };
-  q->sm_a = std::max({need(A, q->a_first), need(A, q->a_mid), need(A, q->a_final)});
-  q->sm_b = std::max(need(B, q->b_mid), need(B, q->b_final));
+  q->sm_a = std::max({need(A, q->a_first), need(A, q->a_mid), need(A, q->a_final), need(A, q->a_q1)});
+  q->sm_b = std::max({need(B, q->b_mid), need(B, q->b_final), need(B, q->b_q1)});
   const long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   q->grid = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
   if (!ok || q->sm_a > kSlabSmemMax || q->sm_b > kSlabSmemMax) {
@@ -249,7 +261,7 @@ namespace {
 
 template <typename R, int DL>
 int q2_run_t(const SlabPlanHost* h, const void* rows, const void* edges, void* X, int M, int J, const int* set_of,
-             cudaStream_t st) {
+             bool q1, cudaStream_t st) {
   typedef typename CT<R>::T C;
   static const bool attr = [] {
     cudaFuncSetAttribute(k_slab_q2<R, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
@@ -274,6 +286,15 @@ int q2_run_t(const SlabPlanHost* h, const void* rows, const void* edges, void* X
     return 1;
   };
   int n = 0;
+  if (q1) {
+    for (int m = 0; m < M; ++m) {
+      const int so = 2 * ne * set_of[m % J];
+      const int rowidx = m == 0 ? M : m - 1;        // step m's full-step 1-body factors
+      n += launch(0, q.a_q1, rowidx, so, so);
+      n += launch(1, q.b_q1, rowidx, so, so);
+    }
+    return n;
+  }
   for (int m = 0; m < M; ++m) {
     const int so_cur = 2 * ne * set_of[m % J];
     const int so_prev = m > 0 ? 2 * ne * set_of[(m - 1) % J] : 0;
@@ -292,6 +313,6 @@ int q2_run_t(const SlabPlanHost* h, const void* rows, const void* edges, void* X
 }  // namespace
 
 int slab_q2_run(const SlabPlanHost* h, bool mixed, const void* rows, const void* edges, void* X, int M, int J,
-                const int* set_of, cudaStream_t st) {
-  SLAB_DISPATCH(q2_run_t, h, rows, edges, X, M, J, set_of, st);
+                const int* set_of, bool q1, cudaStream_t st) {
+  SLAB_DISPATCH(q2_run_t, h, rows, edges, X, M, J, set_of, q1, st);
 }

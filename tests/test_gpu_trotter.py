@@ -104,11 +104,11 @@ def test_q1_pulse_gradient_matches_oracle(sgctx, default_path, name):
     assert np.max(np.abs(g2 - g_r)) > 1e-6 * np.max(np.abs(g_r))
 
 
-@pytest.mark.parametrize("scheme", ["q2", "q4", "q4j"])
+@pytest.mark.parametrize("scheme", ["q1", "q2", "q4", "q4j"])
 def test_tiled_products_match_oracle(sgctx, monkeypatch, scheme):
-    # beyond the on-chip kernels the palindromic products run on the tiles of a two-pass
-    # plan: the 4^7 ring (a 4096-entry and a 64-entry group) and, forced by a small tile
-    # budget, a 3-level chain of 5 modes
+    # beyond the on-chip kernels the products run on the tiles of a two-pass plan: the
+    # 4^7 ring (a 4096-entry and a 64-entry group) and, forced by a small tile budget, a
+    # 3-level chain of 5 modes
     monkeypatch.delenv("SG_PATH", raising=False)
     monkeypatch.delenv("SG_SLAB_TMAX", raising=False)
     ring = _short(W.fluxonium_chain(seed=11, nq=7, levels=4, nseg=2, ring=True, ncols=3), T=0.1)
