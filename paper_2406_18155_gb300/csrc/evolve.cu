@@ -2248,6 +2248,44 @@ sg_status run_backward_q2(sg_system* sys, Solve& sv, double2* pbar, GradAcc acc)
   sg_ctx* ctx = sys->ctx;
   cudaStream_t st = ctx->stream;
   Setup& s = sv.s;
+  if (!sv.oc) {
+    // tiled: the final states and co-states in the internal layout and stage precision,
+    // pulled back pass by pass
+    const long long n = s.D * s.S;
+    double2* pi = sv.ar.get<double2>(n);
+    double2* li = sv.ar.get<double2>(n);
+    float2* X32 = sv.mixed ? sv.ar.get<float2>(n) : nullptr;
+    float2* L32 = sv.mixed ? sv.ar.get<float2>(n) : nullptr;
+    double* gpart = sv.ar.get<double>(slab_q2_grad_part(sv.slab));
+    unsigned* ticket = sv.ar.get<unsigned>(1);
+    if (!pi || !li || (sv.mixed && (!X32 || !L32)) || !gpart || !ticket)
+      return sg_fail(ctx, SG_E_NOMEM, "device allocation of the Q2 adjoint buffers failed");
+    SG_CUDA_TRY(ctx, cudaMemsetAsync(ticket, 0, sizeof(unsigned), st));
+    slab_to_internal(sv.slab, sv.psi, pi, st);
+    slab_to_internal(sv.slab, pbar, li, st);
+    sv.launches += 2;
+    void* X = pi;
+    void* L = li;
+    if (sv.mixed) {
+      k_cast<float><<<grid_for(n), kT, 0, st>>>(pi, X32, n, 1.0);
+      k_cast<float><<<grid_for(n), kT, 0, st>>>(li, L32, n, 1.0);
+      sv.launches += 2;
+      X = X32;
+      L = L32;
+    }
+    int drv_mode[SG_MAXDRIVE];
+    for (int k = 0; k < s.K; ++k) drv_mode[k] = s.drives[k].mode;
+    const size_t es = sv.mixed ? sizeof(float2) : sizeof(double2);
+    const int DL = slab_dl(sv.slab);
+    const void* edges_pb = static_cast<const char*>(sv.q2edges) +
+                           (size_t)2 * std::max(1, s.p.ne) * s.ta.nset * DL * DL * DL * DL * es;
+    const int nl = slab_q2_grad_run(sv.slab, sv.mixed, sv.q2grad, edges_pb, X, L, s.N * s.ta.nsub, s.ta.nsub,
+                                    s.ta.set_of, s.ta.q1 != 0, s.K, drv_mode, acc.gF, gpart, ticket, st);
+    if (nl < 0) return sg_fail(ctx, SG_E_UNSUPPORTED, "a drive's mode has no 1-body factor in the tiled plan");
+    sv.launches += nl;
+    SG_CUDA_TRY(ctx, cudaGetLastError());
+    return SG_OK;
+  }
   const int ncta = onchip_ctas(sv.oc);
   const long long nst = 3ll * s.N;
   const int Kd = std::max(1, s.K);
@@ -2408,8 +2446,9 @@ sg_status sg_fidelity_impl(sg_system* sys, const sg_evolve_opts* o, const double
   }
   rc = upload_and_tables(sys, o, sv, grad);
   if (rc != SG_OK) return rc;
-  if (grad && s.q2 && !sv.oc)
-    return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter gradient runs on the on-chip kernels (D <= 4096)");
+  if (grad && s.q2 && !sv.oc && (!slab_q2_grad_ok(sv.slab) || s.K > 16))
+    return sg_fail(ctx, SG_E_UNSUPPORTED, "the Suzuki-Trotter gradient on the tiled kernels needs <= 16 drives "
+                                          "and its pull-back lists in shared memory");
   double2* Vc = nullptr;
   if (dressed) {
     // dressed computational states of the idle Hamiltonian (FP64 Jacobi)

@@ -83,3 +83,17 @@ int slab_dl(const SlabPlanHost* sp);
 // unitary).  Returns launches.
 int slab_q2_run(const SlabPlanHost* sp, bool mixed, const void* rows, const void* edges, void* X, int M, int J,
                 const int* set_of, bool q1, cudaStream_t st);
+// Pulse gradient of the tiled product (the discrete adjoint of Sec. 2.5): the final
+// states X and co-states Lb (internal layout, stage precision) are pulled back through
+// every factor in reverse order, X by the inverse factors and Lb by the adjoints, and at
+// each 1-body half step every drive k of the pass's modes adds Re <Lb, M_k(s) X> to
+// gF[s K + k].  gtab: per sub-step s the gradient tables [2 nq + K][DL^2] (U^-1, U^dag,
+// M_k); edges_pb: the pull-back coupling table (per set and coupling the inverse half,
+// inverse full, adjoint half and adjoint full factor); gpart: slab_q2_grad_part(sp)
+// doubles; ticket: one zeroed counter (left zeroed).  slab_q2_grad_ok: the backward lists
+// fit.  Returns launches, or -1 when a drive's mode has no 1-body factor in the plan.
+bool slab_q2_grad_ok(const SlabPlanHost* sp);
+size_t slab_q2_grad_part(const SlabPlanHost* sp);
+int slab_q2_grad_run(const SlabPlanHost* sp, bool mixed, const void* gtab, const void* edges_pb, void* X, void* Lb,
+                     int M, int J, const int* set_of, bool q1, int K, const int* drv_mode, double* gF,
+                     double* gpart, unsigned* ticket, cudaStream_t st);

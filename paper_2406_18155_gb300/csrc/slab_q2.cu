@@ -125,11 +125,112 @@ k_slab_q2(SlabPass sp, SQList fl, const typename CT<R>::T* __restrict__ row,
   }
 }
 
+// Pulse gradient on the tiles (Sec. 2.5 on the product): at a point of the backward
+// sequence where the 1-body factors U_i(s) of a group's modes have just been undone
+// (states psi <- U^-1 psi, co-states lambda <- U^dag lambda), every drive k on such a mode i
+// adds Re <lambda, M_k(s) psi> = Re sum_ab M_k[a][b] sum conj(lambda[a, ..]) psi[b, ..] to
+// dF/df_k(s), M_k(s) = U_i(s)^-1 L_k(s) from the gradient tables.  Each thread contracts
+// its blocks' cross-densities at once; per drive the block sums in fixed order, the CTAs'
+// partials in CTA order by the last CTA to finish (ticket), into gF[s K + k].
+constexpr int kSQDrv = 16;
+// dynamic shared memory of the contraction kernel: below the tiled kernels' cap by its
+// static reduction buffer, so that the two together stay within a CTA's shared memory
+constexpr size_t kXdSmemMax = kSlabSmemMax - 4096;
+struct SQDList {
+  int nd;
+  int k[kSQDrv];                  // drive index
+  Phase P[kSQDrv];                // block layout of the drive's mode: its digit first
+};
+
+template <typename R, int DL>
+__global__ void __launch_bounds__(kST, 1)
+k_slab_q2_xd(SlabPass sp, SQDList dl, const typename CT<R>::T* __restrict__ X,
+             const typename CT<R>::T* __restrict__ Lb, const typename CT<R>::T* __restrict__ Mk, int nq,
+             double* __restrict__ gpart, unsigned* __restrict__ ticket, double* __restrict__ gFs) {
+  typedef typename CT<R>::T C;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  C* xs = reinterpret_cast<C*>(smraw);            // psi
+  C* xb = xs + spad(sp.T);                        // lambda
+  C* Ms = xb + spad(sp.T);                        // the drives' M_k, in list order
+  __shared__ double red[kST / 32][kSQDrv];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < dl.nd * DL * DL; i += blockDim.x)
+    Ms[i] = Mk[(size_t)(2 * nq + dl.k[i / (DL * DL)]) * DL * DL + i % (DL * DL)];
+  R g[kSQDrv];
+#pragma unroll
+  for (int j = 0; j < kSQDrv; ++j) g[j] = R(0);
+  __syncthreads();
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const int nb = sp.T / (DL * DL);
+  const int* __restrict__ off = sp.off;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long base = tile_base(sp, tile);
+    load_tile<DL, 8>(sp, X, base, off, xs);
+    load_tile<DL, 8>(sp, Lb, base, off, xb);
+    __syncthreads();
+    for (int j = 0; j < dl.nd; ++j) {
+      const Phase& P = dl.P[j];
+      const C* M = Ms + j * DL * DL;
+      R v = R(0);
+      for (int b = tid; b < nb; b += kST) {
+        C acc[DL * DL];
+#pragma unroll
+        for (int a = 0; a < DL * DL; ++a) acc[a] = cmk<C>(0.0, 0.0);
+        xd_slot<DL, false>(P, 0, M, xb, xs, blk_pos<DL>(P, b), acc);
+#pragma unroll
+        for (int ab = 0; ab < DL * DL; ++ab) v += M[ab].x * acc[ab].x - M[ab].y * acc[ab].y;
+      }
+#pragma unroll
+      for (int i = 0; i < kSQDrv; ++i)
+        if (i == j) g[i] += v;
+    }
+    __syncthreads();
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int j = 0; j < kSQDrv; ++j) {
+    if (j < dl.nd) {
+      double v = (double)g[j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][j] = v;
+    }
+  }
+  __syncthreads();
+  if (tid < dl.nd) {
+    double v = 0.0;
+    for (int w = 0; w < kST / 32; ++w) v += red[w][tid];
+    gpart[(size_t)blockIdx.x * kSQDrv + tid] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (tid < dl.nd) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(gpart + (size_t)b * kSQDrv + tid);
+    gFs[dl.k[tid]] += v;
+  }
+  __syncthreads();
+  if (tid == 0) *ticket = 0u;                     // ready for the next launch on the stream
+}
+
 }  // namespace
 
 struct SQPlan {
   SQList a_first, a_mid, a_final, b_mid, b_final;
   SQList a_q1, b_q1;                              // the first-order product's step
+  // backward (pull-back) lists of the gradient, couplings by their table index 4 e +
+  // (0 half, 1 full) in the pull-back set (+2: the adjoint):
+  //   b1: E2's palindrome, then G2's other modes;  b2: those modes alone
+  //   a1: E1 in reverse term order, then G1's modes;  a2: G1's modes;  a3: E1 in term order
+  //   a1q / b1q: Q1's couplings (full step) in reverse term order, then the modes
+  SQList b1, b2, a1, a2, a3, a1q, b1q;
+  int mgroup[SG_MAXQ];                            // pass of mode i's 1-body factors (0, 1)
+  Phase mphase[SG_MAXQ];                          // its block layout in that pass, its digit first
+  size_t sm_ga = 0, sm_gb = 0, sm_xa = 0, sm_xb = 0;
+  bool grad_ok = false;
   size_t sm_a = 0, sm_b = 0;
   int grid = 0;
 };
@@ -232,6 +333,42 @@ bool slab_q2_ok(SlabPlanHost* h, const KPlan& p, bool mixed) {
   q->b_q1 = SQList{};
   add_onebody(B, DL, m2, q->b_q1, ok);
   for (auto& e : E[1]) add_coupling(e.second, DL, 2 * e.first + 1, 0, q->b_q1, ok, sp_of(e.first));
+  // the gradient's pull-back lists (gok: they fit; the evolution does not need them)
+  bool gok = true;
+  auto pb = [&](const std::pair<int, Phase>& e, bool full, SQList& L) {
+    add_coupling(e.second, DL, 4 * e.first + (full ? 1 : 0), 0, L, gok, sp_of(e.first));
+  };
+  q->b1 = SQList{};
+  for (size_t j = 0; j + 1 < E[1].size(); ++j) pb(E[1][j], false, q->b1);
+  pb(E[1].back(), true, q->b1);
+  for (int j = (int)E[1].size() - 2; j >= 0; --j) pb(E[1][j], false, q->b1);
+  add_onebody(B, DL, m2, q->b1, gok);
+  q->b2 = SQList{};
+  add_onebody(B, DL, m2, q->b2, gok);
+  q->a1 = SQList{};
+  for (auto it = E[0].rbegin(); it != E[0].rend(); ++it) pb(*it, false, q->a1);
+  add_onebody(A, DL, m1, q->a1, gok);
+  q->a2 = SQList{};
+  add_onebody(A, DL, m1, q->a2, gok);
+  q->a3 = SQList{};
+  for (auto& e : E[0]) pb(e, false, q->a3);
+  q->b1q = SQList{};
+  for (auto it = E[1].rbegin(); it != E[1].rend(); ++it) pb(*it, true, q->b1q);
+  add_onebody(B, DL, m2, q->b1q, gok);
+  q->a1q = SQList{};
+  for (auto it = E[0].rbegin(); it != E[0].rend(); ++it) pb(*it, true, q->a1q);
+  add_onebody(A, DL, m1, q->a1q, gok);
+  for (int i = 0; i < SG_MAXQ; ++i) q->mgroup[i] = -1;
+  for (int g = 0; g < 2; ++g) {
+    const SlabPass& sp = h->pass[g];
+    for (int m : (g == 0 ? m1 : m2)) {
+      int ka = -1;
+      for (int k = 0; k < sp.ng; ++k) if (sp.tmode[k] == m) ka = k;
+      if (ka < 0) { gok = false; continue; }
+      q->mgroup[m] = g;
+      q->mphase[m] = make_phase(sp, DL, ka, ka == sp.ng - 1 ? sp.ng - 2 : sp.ng - 1);
+    }
+  }
   const size_t csz = mixed ? sizeof(float2) : sizeof(double2);
   const size_t D4 = (size_t)DL * DL * DL * DL;
   const size_t nrow = (size_t)p.nq * DL * DL;
@@ -240,6 +377,11 @@ bool slab_q2_ok(SlabPlanHost* h, const KPlan& p, bool mixed) {
   };
   q->sm_a = std::max({need(A, q->a_first), need(A, q->a_mid), need(A, q->a_final), need(A, q->a_q1)});
   q->sm_b = std::max({need(B, q->b_mid), need(B, q->b_final), need(B, q->b_q1)});
+  q->sm_ga = std::max({need(A, q->a1), need(A, q->a2), need(A, q->a3), need(A, q->a1q)});
+  q->sm_gb = std::max({need(B, q->b1), need(B, q->b2), need(B, q->b1q)});
+  q->sm_xa = (2 * (size_t)spad(A.T) + (size_t)kSQDrv * DL * DL) * csz;
+  q->sm_xb = (2 * (size_t)spad(B.T) + (size_t)kSQDrv * DL * DL) * csz;
+  q->grad_ok = gok && std::max(q->sm_ga, q->sm_gb) <= kSlabSmemMax && std::max(q->sm_xa, q->sm_xb) <= kXdSmemMax;
   const long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   q->grid = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
   if (!ok || q->sm_a > kSlabSmemMax || q->sm_b > kSlabSmemMax) {
@@ -310,7 +452,110 @@ int q2_run_t(const SlabPlanHost* h, const void* rows, const void* edges, void* X
   return n;
 }
 
+// Backward of the tiled product for the pulse gradient: the reverse of the forward's
+// factor sequence (per sub-step m, forward pass A: E1 reversed (m - 1), U_G1(m - 1) second
+// half, U_G1(m) first half, E1 (m); pass B: U_G2'(m - 1) second half, U_G2'(m) first half,
+// E2's palindrome (m); after the last sub-step E1 reversed and U_G1 second half, then
+// U_G2' second half), each factor undone on the states by its inverse and on the
+// co-states by its adjoint, a contribution point after every 1-body half step.  Q1: per
+// step pass A U_G1(m), E1; pass B U_G2'(m), E2.
+template <typename R, int DL>
+int q2_grad_t(const SlabPlanHost* h, const void* gtab, const void* edges_pb, void* X, void* Lb, int M, int J,
+              const int* set_of, bool q1, int K, const int* drv_mode, double* gF, double* gpart, unsigned* ticket,
+              cudaStream_t st) {
+  typedef typename CT<R>::T C;
+  static const bool attr = [] {
+    cudaFuncSetAttribute(k_slab_q2<R, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
+    cudaFuncSetAttribute(k_slab_q2_xd<R, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXdSmemMax);
+    return true;
+  }();
+  (void)attr;
+  const SQPlan& q = *h->q2;
+  const int nq = h->perm.nq;
+  const int nrow = nq * DL * DL;
+  const size_t rowblk = (size_t)(2 * nq + K) * DL * DL;
+  const size_t D4 = (size_t)DL * DL * DL * DL;
+  const int ne = [&] {
+    int n = 0;
+    for (int g = 0; g < h->np; ++g) n += h->pass[g].ne;
+    return n;
+  }();
+  const C* G = static_cast<const C*>(gtab);
+  const C* Ep = static_cast<const C*>(edges_pb);
+  C* Xc = static_cast<C*>(X);
+  C* Lc = static_cast<C*>(Lb);
+  SQDList dl[2] = {};
+  for (int k = 0; k < K; ++k) {
+    const int g = q.mgroup[drv_mode[k]];
+    if (g < 0 || dl[g].nd >= kSQDrv) return -1;
+    dl[g].k[dl[g].nd] = k;
+    dl[g].P[dl[g].nd++] = q.mphase[drv_mode[k]];
+  }
+  auto app = [&](int g, const SQList& L, int srow, int sigma) {
+    if (L.nf == 0) return 0;
+    const C* rows = G + (size_t)srow * rowblk;
+    const int so = 4 * ne * sigma;
+    const size_t sm = g == 0 ? q.sm_ga : q.sm_gb;
+    k_slab_q2<R, DL><<<q.grid, kST, sm, st>>>(h->pass[g], L, rows, Ep, 0, so, nrow, Xc);           // U^-1
+    k_slab_q2<R, DL><<<q.grid, kST, sm, st>>>(h->pass[g], L, rows + nrow, Ep + 2 * D4, 0, so, nrow, Lc);   // U^dag
+    return 2;
+  };
+  auto xd = [&](int g, int srow) {
+    if (dl[g].nd == 0) return 0;
+    k_slab_q2_xd<R, DL><<<q.grid, kST, g == 0 ? q.sm_xa : q.sm_xb, st>>>(
+        h->pass[g], dl[g], Xc, Lc, G + (size_t)srow * rowblk, nq, gpart, ticket, gF + (size_t)srow * K);
+    return 1;
+  };
+  int n = 0;
+  if (q1) {
+    for (int m = M - 1; m >= 0; --m) {
+      const int sg = set_of[m % J];
+      n += app(1, q.b1q, m, sg);
+      n += xd(1, m);
+      n += app(0, q.a1q, m, sg);
+      n += xd(0, m);
+    }
+    return n;
+  }
+  if (M > 0) {
+    const int s = M - 1, sg = set_of[s % J];
+    n += app(1, q.b2, s, sg);                       // U_G2'(M - 1), second half
+    n += xd(1, s);
+    n += app(0, q.a2, s, sg);                       // U_G1(M - 1), second half
+    n += xd(0, s);
+    n += app(0, q.a3, s, sg);                       // E1 reversed (M - 1)
+  }
+  for (int m = M - 1; m >= 0; --m) {
+    const int sg = set_of[m % J];
+    n += app(1, q.b1, m, sg);                       // E2's palindrome, U_G2'(m) first half
+    n += xd(1, m);
+    if (m > 0) {
+      n += app(1, q.b2, m - 1, set_of[(m - 1) % J]);   // U_G2'(m - 1) second half
+      n += xd(1, m - 1);
+    }
+    n += app(0, q.a1, m, sg);                       // E1 (m), U_G1(m) first half
+    n += xd(0, m);
+    if (m > 0) {
+      const int sp = set_of[(m - 1) % J];
+      n += app(0, q.a2, m - 1, sp);                 // U_G1(m - 1) second half
+      n += xd(0, m - 1);
+      n += app(0, q.a3, m - 1, sp);                 // E1 reversed (m - 1)
+    }
+  }
+  return n;
+}
+
 }  // namespace
+
+bool slab_q2_grad_ok(const SlabPlanHost* h) { return h->q2 && h->q2->grad_ok; }
+
+size_t slab_q2_grad_part(const SlabPlanHost* h) { return (size_t)std::max(1, h->q2 ? h->q2->grid : 1) * kSQDrv; }
+
+int slab_q2_grad_run(const SlabPlanHost* h, bool mixed, const void* gtab, const void* edges_pb, void* X, void* Lb,
+                     int M, int J, const int* set_of, bool q1, int K, const int* drv_mode, double* gF,
+                     double* gpart, unsigned* ticket, cudaStream_t st) {
+  SLAB_DISPATCH(q2_grad_t, h, gtab, edges_pb, X, Lb, M, J, set_of, q1, K, drv_mode, gF, gpart, ticket, st);
+}
 
 int slab_q2_run(const SlabPlanHost* h, bool mixed, const void* rows, const void* edges, void* X, int M, int J,
                 const int* set_of, bool q1, cudaStream_t st) {

@@ -131,15 +131,48 @@ def test_tiled_products_match_oracle(sgctx, monkeypatch, scheme):
             monkeypatch.delenv(k)
 
 
-def test_tiled_products_refuse_the_gradient(sgctx, default_path):
-    from paper_2406_18155_gb300.capi import SGError, SG_E_UNSUPPORTED
-    wl = _short(W.fluxonium_chain(seed=11, nq=7, levels=4, nseg=2, ring=True, ncols=3), T=0.05)
-    wl["fid_kind"] = "state"
-    s = _system(sgctx, wl)
-    with pytest.raises(SGError) as e:
-        s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state", precision="mixed",
-                        solver="q2", ham=False)
-    assert e.value.code == SG_E_UNSUPPORTED
+def _phase_target(wl):
+    """A diagonal target carrying the phases of the evolved columns' diagonal entries, so
+    that F_state is near 1 and its gradient is not negligible."""
+    from oracle.evolve import comp_map
+    so = OracleSystem(dict(wl, frame="lab"))
+    psi = q2_evolve(so, initial_columns(so, wl["col_index"]), scheme="q2")
+    comp, cols = comp_map(so)
+    T = np.eye(len(comp), dtype=complex)
+    for s_, j in enumerate(cols):
+        if j >= 0:
+            u = psi[comp[j], s_]
+            T[j, j] = u / abs(u)
+    wl = dict(wl, target=T.tolist(), fid_kind="state")
+    return wl
+
+
+@pytest.mark.parametrize("scheme", ["q1", "q2", "q4", "q4j"])
+def test_tiled_pulse_gradient_matches_oracle(sgctx, monkeypatch, scheme):
+    """The pulse gradient on the tiles of a two-pass plan: the final states and co-states
+    pulled back pass by pass through the inverse and adjoint factors, a cross-density
+    contraction after every 1-body half step, against the oracle's adjoint (the 4^7 ring
+    and the forced two-pass 3-level chain)."""
+    monkeypatch.delenv("SG_PATH", raising=False)
+    monkeypatch.delenv("SG_SLAB_TMAX", raising=False)
+    ring = _short(W.fluxonium_chain(seed=11, nq=7, levels=4, nseg=2, ring=True, ncols=3), T=0.05)
+    chain = _short(W.fluxonium_chain(seed=12, nq=5, levels=3, nseg=3, ncols=6), T=0.1)
+    for wl, env in ((ring, {}), (chain, {"SG_PATH": "slab", "SG_SLAB_TMAX": "27"})):
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        wl = _phase_target(wl)
+        s = _system(sgctx, wl)
+        F_r, g_r = q2_pulse_gradient(wl, kind="state", scheme=scheme)
+        assert F_r > 0.5
+        scale = np.max(np.abs(g_r))
+        for prec, tol_F, tol_g in (("fp64", 1e-10, 1e-9), ("mixed", 1e-5, 2e-4)):
+            F, gp, gh = s.fidelity_grad(wl["T"], wl["dt"], wl["target"], wl["col_index"], kind="state",
+                                        precision=prec, ham=False, solver=scheme)
+            assert gh is None and gp.shape == g_r.shape
+            assert abs(F[1] - F_r) < tol_F, (prec, F[1], F_r)
+            assert np.max(np.abs(gp - g_r)) < tol_g * scale, (prec, np.max(np.abs(gp - g_r)), scale)
+        for k in env:
+            monkeypatch.delenv(k)
 
 
 def test_q2_rejects_what_it_does_not_run(sgctx, default_path):
