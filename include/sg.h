@@ -225,16 +225,16 @@ enum { SG_COMP_NONE = 0, SG_COMP_VZ = 1 };
  * product Q2(p dt) Q2(p* dt), p = (3 - i sqrt 3)/6, the drive coefficients continued to
  * the complex sub-step midpoints; third order (the composition is not palindromic).
  * They run on the on-chip kernels (every mode with the same level count 2..5,
- * D <= 4096) and, for the evolution and the fidelity, on the HBM-tiled kernels of a
- * two-pass plan whose first group's couplings come first in term order and whose last
- * coupling lies in the second group; else SG_E_UNSUPPORTED.  sg_fidelity_grad with a
- * Suzuki-Trotter solver (on-chip kernels only)
+ * D <= 4096) and on the HBM-tiled kernels of a two-pass plan whose first group's
+ * couplings come first in term order and whose last coupling lies in the second group;
+ * else SG_E_UNSUPPORTED.  sg_fidelity_grad with a Suzuki-Trotter solver
  * computes the pulse-parameter gradient only (grad_ham must be NULL, else
  * SG_E_UNSUPPORTED): the exact discrete adjoint of the product (Sec. 2.5), the states
  * pulled back through each factor's inverse and the co-state through its adjoint (no
  * checkpoints), dU/df by the Frechet derivative of the local exponential; it needs >= 2
- * modes, <= 16 drives, <= 32 couplings and four state images of a CTA's columns in
- * shared memory (mixed precision fits D = 4096, FP64 does not). */
+ * modes, <= 16 drives, <= 32 couplings and, on-chip, four state images of a CTA's
+ * columns in shared memory (mixed precision fits D = 4096, FP64 does not; the tiled
+ * kernels hold two tiles of states and two of co-states). */
 enum { SG_SOLVER_RK4 = 0, SG_SOLVER_Q1 = 1, SG_SOLVER_Q2 = 2, SG_SOLVER_Q4 = 4, SG_SOLVER_Q4J = 5 };
 
 /* Evolve S columns from t = 0 to T and leave the lab-frame states in psi_dev
