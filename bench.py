@@ -679,10 +679,11 @@ def fp64_comparison(sysm, wl, nsteps, grad_steps, ham, stream):
 
 def q2_tiled_comparison(sysm, wl, stream, nsteps):
     """The paper's Suzuki-Trotter products on the tiled kernels (slabs beyond the
-    on-chip kernels) against RK4, forward only, over the first nsteps steps of the
-    workload: col-steps/s (device time) of RK4 (mixed), Q2 (mixed, FP64) and Q4
-    (mixed), and the largest difference of the Q2 and Q4 states from RK4's (each
-    solver's own truncation error at the workload's dt)."""
+    on-chip kernels) against RK4 over the first nsteps steps of the workload:
+    forward col-steps/s (device time) of RK4 (mixed), Q2 (mixed, FP64) and Q4 (mixed),
+    the largest difference of the Q2 and Q4 states from RK4's (each solver's own
+    truncation error at the workload's dt), and the pulse-gradient solves of RK4 and
+    Q2 (mixed)."""
     import torch
     T = nsteps * wl["dt"]
     out = {"steps": nsteps}
@@ -703,6 +704,19 @@ def q2_tiled_comparison(sysm, wl, stream, nsteps):
     out["q2_over_rk4_mixed"] = out["q2_mixed_forward_col_steps_per_s"] / out["rk4_mixed_forward_col_steps_per_s"]
     out["max_abs_dpsi_q2_rk4"] = float(np.max(np.abs(psi["q2"] - psi["rk4"])))
     out["max_abs_dpsi_q4_rk4"] = float(np.max(np.abs(psi["q4"] - psi["rk4"])))
+    # pulse-gradient solves (fidelity + adjoint) over the same steps: RK4's checkpointed
+    # adjoint against Q2's pull-back through inverse factors on the tiles
+    for solver in ("rk4", "q2"):
+        kw = dict(kind=wl["fid_kind"], precision="mixed", ham=False, solver=solver)
+        sysm.fidelity_grad(T, wl["dt"], wl["target"], wl["col_index"], **kw)          # warm
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sysm.fidelity_grad(T, wl["dt"], wl["target"], wl["col_index"], **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[f"{solver}_mixed_pulse_gradient_col_steps_per_s"] = len(wl["col_index"]) * nsteps / (e0.elapsed_time(e1) / 1e3)
     return out
 
 
