@@ -25,6 +25,7 @@
 #include "slab.h"
 #include "slab_dev.cuh"
 #include <algorithm>
+#include <cstdlib>
 #include <utility>
 #include <vector>
 
@@ -216,6 +217,158 @@ k_slab_q2_xd(SlabPass sp, SQDList dl, const typename CT<R>::T* __restrict__ X,
   if (tid == 0) *ticket = 0u;                     // ready for the next launch on the stream
 }
 
+// The backward of one pass of one sub-step in one launch: states and co-states tiled
+// side by side, the pass's pull-back factors applied to both in shared memory (kind 0/1:
+// 1-body rows of sub-step s0, or s1 when prev; kind 2: the pull-back set so0, or so1 when
+// prev; states by the inverse, co-states by the adjoint) and at each contraction point
+// (kind 3, mat = point 0 or 1) the drives' U^-1 L_k of sub-step s0 or s1 contracted with
+// the cross-densities, so a pass reads and writes the two slabs once.  Reduction as in
+// k_slab_q2_xd, into gF0 and gF1.
+template <typename R, int DL>
+__global__ void __launch_bounds__(kST, 1)
+k_slab_q2_bwd(SlabPass sp, SQList fl, SQDList dl, const typename CT<R>::T* __restrict__ rows0,
+              const typename CT<R>::T* __restrict__ rows1, const typename CT<R>::T* __restrict__ Ep, int so0,
+              int so1, int nq, typename CT<R>::T* __restrict__ X, typename CT<R>::T* __restrict__ Lb,
+              double* __restrict__ gpart, unsigned* __restrict__ ticket, double* __restrict__ gF0,
+              double* __restrict__ gF1) {
+  typedef typename CT<R>::T C;
+  constexpr int D4 = DL * DL * DL * DL;
+  constexpr int D2 = DL * DL;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const int TP = spad(sp.T), nrow = nq * D2;
+  C* ys = reinterpret_cast<C*>(smraw);            // states
+  C* ks = ys + TP;
+  C* yb = ks + TP;                                // co-states
+  C* kb = yb + TP;
+  C* Mr = kb + TP;                                // rows: s0 U^-1, s0 U^dag, s1 U^-1, s1 U^dag
+  C* Mk = Mr + 4 * nrow;                          // M_k of the pass's drives: s0, then s1
+  C* G = Mk + 2 * kSQDrv * D2;                    // per coupling factor: inverse, adjoint
+  __shared__ double red[kST / 32][2 * kSQDrv];
+  __shared__ bool last;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < 2 * nrow; i += blockDim.x) {
+    Mr[i] = rows0[i];
+    Mr[2 * nrow + i] = rows1[i];
+  }
+  for (int i = tid; i < dl.nd * D2; i += blockDim.x) {
+    const size_t o = (size_t)(2 * nq + dl.k[i / D2]) * D2 + i % D2;
+    Mk[i] = rows0[o];
+    Mk[kSQDrv * D2 + i] = rows1[o];
+  }
+  {
+    int g = 0;
+    for (int q = 0; q < fl.nf; ++q) {
+      if (fl.f[q].kind != 2) continue;
+      const C* src = Ep + (size_t)(fl.f[q].mat + (fl.f[q].prev ? so1 : so0)) * D4;
+      for (int i = tid; i < D4; i += blockDim.x) {
+        G[(size_t)(2 * g) * D4 + i] = src[i];
+        G[(size_t)(2 * g + 1) * D4 + i] = src[2 * D4 + i];
+      }
+      ++g;
+    }
+  }
+  R gv[2][kSQDrv];
+#pragma unroll
+  for (int pt = 0; pt < 2; ++pt)
+#pragma unroll
+    for (int j = 0; j < kSQDrv; ++j) gv[pt][j] = R(0);
+  __syncthreads();
+  const long long ntiles = (long long)sp.S * sp.ntpc;
+  const int nb = sp.T / D2;
+  const int* __restrict__ off = sp.off;
+  for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const long long base = tile_base(sp, tile);
+    load_tile<DL, 8>(sp, X, base, off, ys);
+    load_tile<DL, 8>(sp, Lb, base, off, yb);
+    __syncthreads();
+    int g = 0;
+    for (int q = 0; q < fl.nf; ++q) {
+      const SQFactor& F = fl.f[q];
+      if (F.kind == 3) {
+        const int pt = F.mat;
+        for (int j = 0; j < dl.nd; ++j) {
+          const Phase& P = dl.P[j];
+          const C* M = Mk + (pt * kSQDrv + j) * D2;
+          R v = R(0);
+          for (int b = tid; b < nb; b += kST) {
+            C acc[D2];
+#pragma unroll
+            for (int a = 0; a < D2; ++a) acc[a] = cmk<C>(0.0, 0.0);
+            xd_slot<DL, false>(P, 0, M, yb, ys, blk_pos<DL>(P, b), acc);
+#pragma unroll
+            for (int ab = 0; ab < D2; ++ab) v += M[ab].x * acc[ab].x - M[ab].y * acc[ab].y;
+          }
+#pragma unroll
+          for (int i = 0; i < kSQDrv; ++i) {
+            if (i == j) {
+              if (pt == 0) gv[0][i] += v;
+              else gv[1][i] += v;
+            }
+          }
+        }
+        continue;                                 // read-only: the next factor's barrier orders it
+      }
+      const C* Mi = Mr + (F.prev ? 2 * nrow : 0);
+      for (int b = tid; b < nb; b += kST) {
+        const int pb = blk_pos<DL>(F.P, b);
+        if (F.kind == 2) {
+          const C* Gi = G + (size_t)(2 * g) * D4;
+          if (F.spar) {
+            block_dense_sp<DL>(Gi, ys, ks, pb, F.P.psa, F.P.psb);
+            block_dense_sp<DL>(Gi + D4, yb, kb, pb, F.P.psa, F.P.psb);
+          } else {
+            block_dense<DL>(Gi, ys, ks, pb, F.P.psa, F.P.psb);
+            block_dense<DL>(Gi + D4, yb, kb, pb, F.P.psa, F.P.psb);
+          }
+        } else {
+          phase_block<DL, false>(F.P, Mi, ys, ks, pb, true);
+          phase_block<DL, false>(F.P, Mi + nrow, yb, kb, pb, true);
+        }
+      }
+      g += F.kind == 2 ? 1 : 0;
+      __syncthreads();
+      C* t = ys; ys = ks; ks = t;
+      t = yb; yb = kb; kb = t;
+    }
+    for (int t = tid; t < sp.T; t += kST) {
+      const long long o = base + __ldg(off + t);
+      X[o] = ys[spos<DL>(t)];
+      Lb[o] = yb[spos<DL>(t)];
+    }
+    __syncthreads();
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int pt = 0; pt < 2; ++pt)
+#pragma unroll
+    for (int j = 0; j < kSQDrv; ++j) {
+      if (j < dl.nd) {
+        double v = (double)gv[pt][j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][pt * kSQDrv + j] = v;
+      }
+    }
+  __syncthreads();
+  if (tid < 2 * kSQDrv && (tid % kSQDrv) < dl.nd) {
+    double v = 0.0;
+    for (int w = 0; w < kST / 32; ++w) v += red[w][tid];
+    gpart[(size_t)blockIdx.x * 2 * kSQDrv + tid] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  if (tid < 2 * kSQDrv && (tid % kSQDrv) < dl.nd) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(gpart + (size_t)b * 2 * kSQDrv + tid);
+    if (tid < kSQDrv) gF0[dl.k[tid]] += v;
+    else if (gF1) gF1[dl.k[tid - kSQDrv]] += v;
+  }
+  __syncthreads();
+  if (tid == 0) *ticket = 0u;
+}
+
 }  // namespace
 
 struct SQPlan {
@@ -231,6 +384,11 @@ struct SQPlan {
   Phase mphase[SG_MAXQ];                          // its block layout in that pass, its digit first
   size_t sm_ga = 0, sm_gb = 0, sm_xa = 0, sm_xb = 0;
   bool grad_ok = false;
+  // the same backward fused to one launch per pass and sub-step (k_slab_q2_bwd): factor
+  // lists with contraction points (kind 3), prev = the earlier sub-step's rows and set
+  SQList fb_mid, fb_0, fb_fin, fa_mid, fa_0, fa_fin, fbq, faq;
+  size_t sm_fa = 0, sm_fb = 0;
+  bool fused_ok = false;
   size_t sm_a = 0, sm_b = 0;
   int grid = 0;
 };
@@ -382,6 +540,38 @@ bool slab_q2_ok(SlabPlanHost* h, const KPlan& p, bool mixed) {
   q->sm_xa = (2 * (size_t)spad(A.T) + (size_t)kSQDrv * DL * DL) * csz;
   q->sm_xb = (2 * (size_t)spad(B.T) + (size_t)kSQDrv * DL * DL) * csz;
   q->grad_ok = gok && std::max(q->sm_ga, q->sm_gb) <= kSlabSmemMax && std::max(q->sm_xa, q->sm_xb) <= kXdSmemMax;
+  bool fok = q->grad_ok;
+  auto cat = [&](SQList& dst, const SQList& src, int prev) {
+    for (int i = 0; i < src.nf; ++i) {
+      if (dst.nf >= kMaxSQ) { fok = false; return; }
+      dst.f[dst.nf] = src.f[i];
+      dst.f[dst.nf].prev = prev;
+      dst.ndense += src.f[i].kind == 2 ? 1 : 0;
+      ++dst.nf;
+    }
+  };
+  auto point = [&](SQList& dst, int pt) {
+    if (dst.nf >= kMaxSQ) { fok = false; return; }
+    SQFactor& F = dst.f[dst.nf++];
+    F = SQFactor{};
+    F.kind = 3;
+    F.mat = pt;
+  };
+  q->fb_mid = SQList{}; cat(q->fb_mid, q->b1, 0); point(q->fb_mid, 0); cat(q->fb_mid, q->b2, 1); point(q->fb_mid, 1);
+  q->fb_0 = SQList{};   cat(q->fb_0, q->b1, 0);   point(q->fb_0, 0);
+  q->fb_fin = SQList{}; cat(q->fb_fin, q->b2, 0); point(q->fb_fin, 0);
+  q->fa_mid = SQList{}; cat(q->fa_mid, q->a1, 0); point(q->fa_mid, 0); cat(q->fa_mid, q->a2, 1); point(q->fa_mid, 1);
+  cat(q->fa_mid, q->a3, 1);
+  q->fa_0 = SQList{};   cat(q->fa_0, q->a1, 0);   point(q->fa_0, 0);
+  q->fa_fin = SQList{}; cat(q->fa_fin, q->a2, 0); point(q->fa_fin, 0); cat(q->fa_fin, q->a3, 0);
+  q->fbq = SQList{};    cat(q->fbq, q->b1q, 0);   point(q->fbq, 0);
+  q->faq = SQList{};    cat(q->faq, q->a1q, 0);   point(q->faq, 0);
+  auto fneed = [&](const SlabPass& sp, const SQList& L) {
+    return (4 * (size_t)spad(sp.T) + 4 * nrow + 2 * (size_t)kSQDrv * DL * DL + 2 * (size_t)L.ndense * D4) * csz;
+  };
+  q->sm_fa = std::max({fneed(A, q->fa_mid), fneed(A, q->fa_0), fneed(A, q->fa_fin), fneed(A, q->faq)});
+  q->sm_fb = std::max({fneed(B, q->fb_mid), fneed(B, q->fb_0), fneed(B, q->fb_fin), fneed(B, q->fbq)});
+  q->fused_ok = fok && std::max(q->sm_fa, q->sm_fb) <= kXdSmemMax;
   const long long ntiles = (long long)p.S * (p.D / h->pass[0].T);
   q->grid = (int)std::min<long long>(ntiles, 152ll * (mixed ? 2 : 1));
   if (!ok || q->sm_a > kSlabSmemMax || q->sm_b > kSlabSmemMax) {
@@ -459,6 +649,12 @@ int q2_run_t(const SlabPlanHost* h, const void* rows, const void* edges, void* X
 // U_G2' second half), each factor undone on the states by its inverse and on the
 // co-states by its adjoint, a contribution point after every 1-body half step.  Q1: per
 // step pass A U_G1(m), E1; pass B U_G2'(m), E2.
+// SG_Q2_FUSE=0: the segmented backward (pull-back and contraction launches apart)
+bool q2_fuse_on() {
+  const char* e = std::getenv("SG_Q2_FUSE");
+  return !(e && e[0] == '0');
+}
+
 template <typename R, int DL>
 int q2_grad_t(const SlabPlanHost* h, const void* gtab, const void* edges_pb, void* X, void* Lb, int M, int J,
               const int* set_of, bool q1, int K, const int* drv_mode, double* gF, double* gpart, unsigned* ticket,
@@ -467,6 +663,7 @@ int q2_grad_t(const SlabPlanHost* h, const void* gtab, const void* edges_pb, voi
   static const bool attr = [] {
     cudaFuncSetAttribute(k_slab_q2<R, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSlabSmemMax);
     cudaFuncSetAttribute(k_slab_q2_xd<R, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXdSmemMax);
+    cudaFuncSetAttribute(k_slab_q2_bwd<R, DL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kXdSmemMax);
     return true;
   }();
   (void)attr;
@@ -507,6 +704,34 @@ int q2_grad_t(const SlabPlanHost* h, const void* gtab, const void* edges_pb, voi
     return 1;
   };
   int n = 0;
+  if (q.fused_ok && q2_fuse_on()) {
+    auto fz = [&](int g, const SQList& L, int s0, int s1, int sg0, int sg1) {
+      k_slab_q2_bwd<R, DL><<<q.grid, kST, g == 0 ? q.sm_fa : q.sm_fb, st>>>(
+          h->pass[g], L, dl[g], G + (size_t)s0 * rowblk, G + (size_t)(s1 >= 0 ? s1 : s0) * rowblk, Ep,
+          4 * ne * sg0, 4 * ne * sg1, nq, Xc, Lc, gpart, ticket, gF + (size_t)s0 * K,
+          s1 >= 0 ? gF + (size_t)s1 * K : nullptr);
+      return 1;
+    };
+    if (q1) {
+      for (int m = M - 1; m >= 0; --m) {
+        const int sg = set_of[m % J];
+        n += fz(1, q.fbq, m, -1, sg, sg);
+        n += fz(0, q.faq, m, -1, sg, sg);
+      }
+      return n;
+    }
+    if (M > 0) {
+      const int sg = set_of[(M - 1) % J];
+      n += fz(1, q.fb_fin, M - 1, -1, sg, sg);
+      n += fz(0, q.fa_fin, M - 1, -1, sg, sg);
+    }
+    for (int m = M - 1; m >= 0; --m) {
+      const int sg = set_of[m % J], sp = m > 0 ? set_of[(m - 1) % J] : sg;
+      n += fz(1, m > 0 ? q.fb_mid : q.fb_0, m, m > 0 ? m - 1 : -1, sg, sp);
+      n += fz(0, m > 0 ? q.fa_mid : q.fa_0, m, m > 0 ? m - 1 : -1, sg, sp);
+    }
+    return n;
+  }
   if (q1) {
     for (int m = M - 1; m >= 0; --m) {
       const int sg = set_of[m % J];
@@ -549,7 +774,7 @@ int q2_grad_t(const SlabPlanHost* h, const void* gtab, const void* edges_pb, voi
 
 bool slab_q2_grad_ok(const SlabPlanHost* h) { return h->q2 && h->q2->grad_ok; }
 
-size_t slab_q2_grad_part(const SlabPlanHost* h) { return (size_t)std::max(1, h->q2 ? h->q2->grid : 1) * kSQDrv; }
+size_t slab_q2_grad_part(const SlabPlanHost* h) { return (size_t)std::max(1, h->q2 ? h->q2->grid : 1) * 2 * kSQDrv; }
 
 int slab_q2_grad_run(const SlabPlanHost* h, bool mixed, const void* gtab, const void* edges_pb, void* X, void* Lb,
                      int M, int J, const int* set_of, bool q1, int K, const int* drv_mode, double* gF,

@@ -147,14 +147,17 @@ def _phase_target(wl):
     return wl
 
 
-@pytest.mark.parametrize("scheme", ["q1", "q2", "q4", "q4j"])
-def test_tiled_pulse_gradient_matches_oracle(sgctx, monkeypatch, scheme):
+@pytest.mark.parametrize("scheme,fuse", [("q1", "1"), ("q2", "1"), ("q4", "1"), ("q4j", "1"), ("q2", "0"),
+                                         ("q4j", "0")])
+def test_tiled_pulse_gradient_matches_oracle(sgctx, monkeypatch, scheme, fuse):
     """The pulse gradient on the tiles of a two-pass plan: the final states and co-states
     pulled back pass by pass through the inverse and adjoint factors, a cross-density
     contraction after every 1-body half step, against the oracle's adjoint (the 4^7 ring
-    and the forced two-pass 3-level chain)."""
+    and the forced two-pass 3-level chain); one fused launch per pass and sub-step, and
+    (SG_Q2_FUSE=0) the segmented pull-back and contraction launches."""
     monkeypatch.delenv("SG_PATH", raising=False)
     monkeypatch.delenv("SG_SLAB_TMAX", raising=False)
+    monkeypatch.setenv("SG_Q2_FUSE", fuse)
     ring = _short(W.fluxonium_chain(seed=11, nq=7, levels=4, nseg=2, ring=True, ncols=3), T=0.05)
     chain = _short(W.fluxonium_chain(seed=12, nq=5, levels=3, nseg=3, ncols=6), T=0.1)
     for wl, env in ((ring, {}), (chain, {"SG_PATH": "slab", "SG_SLAB_TMAX": "27"})):
