@@ -17,7 +17,12 @@ Readings taken here (the paper fixes the idea, not these details):
 * the evolved columns are exactly the dressed computational states, each once.
 
 The pulse gradient needs no derivative of V (V does not depend on the pulses): the
-co-state of the final states is V_c times the co-state of the projected block.
+co-state of the final states is V_c times the co-state of the projected block.  The
+Hamiltonian-parameter gradient adds V's derivative: each dressed vector moves by the
+first-order perturbation formula dv_k = sum_{m != k} v_m <v_m|dH0|v_k> / (lam_k - lam_m)
+of the idle Hamiltonian H0 (real symmetric, non-degenerate levels), contracted with the
+co-vector of V_c from the initial columns (the co-state pulled back to t = 0) and from
+the projection (psi(T) times the block's co-state).
 """
 import numpy as np
 
@@ -86,3 +91,64 @@ def dressed_pulse_gradient(wl, kind=None):
     grad, _ = adjoint_from_costate(sys, hist, psi_lab, Vc @ barc, sys.N)
     npul = sum(n_pulse_params(dr) for dr in wl["drives"])
     return F, grad[:npul]
+
+
+def idle_hamiltonian_derivative(sys, prm):
+    """dH0/dtheta of the idle Hamiltonian for one parameter of sys.param_list(): zero for
+    pulse parameters; A (x) B for a coupling's J; for a device parameter of mode i its
+    energies' derivative on the diagonal and J times the derivative of its coupling
+    operators (eigen-derivatives of the subsystem, as in the evolution's dH)."""
+    kind, a, b = prm
+    D = sys.D
+    if kind == "pulse":
+        return np.zeros((D, D), dtype=np.complex128)
+    if kind == "J":
+        c = sys.couplings[a]
+        return sys.embed({c["a"]: sys.op(c["a"], c["op_a"]), c["b"]: sys.op(c["b"], c["op_b"])})
+    i, p = a, b
+    _, dops = sys.mode_derivs(i, p)
+    out = np.diag(sys.dHd_diag(prm)).astype(np.complex128)
+    for c in sys.couplings:
+        if c["a"] == i:
+            out += c["J"] * sys.embed({i: sys.dop(dops, i, c["op_a"]), c["b"]: sys.op(c["b"], c["op_b"])})
+        elif c["b"] == i:
+            out += c["J"] * sys.embed({c["a"]: sys.op(c["a"], c["op_a"]), i: sys.dop(dops, i, c["op_b"])})
+    return out
+
+
+def dressed_full_gradient(wl, kind=None):
+    """F and dF/dtheta for every parameter (pulse, then E_J, E_C, E_L per mode, then J
+    per coupling) in the dressed basis: the evolution's discrete RK4 adjoint with the
+    co-state V_c barc, plus V_c's derivative contracted with
+    W = psi(T) barc^dag (projection) + lambda(0) on the labels' columns (initial states)."""
+    kind = kind or wl["fid_kind"]
+    sys, Vc, cols, psi_lab, hist = dressed_evolve(wl)
+    T = np.asarray(wl["target"], dtype=np.complex128)
+    F, barc = block_fidelity_and_costate(T, Vc.conj().T @ psi_lab, cols, kind)
+    grad, prms, bar0 = adjoint_from_costate(sys, hist, psi_lab, Vc @ barc, sys.N, with_bar=True)
+    H0 = idle_hamiltonian(sys)
+    if np.max(np.abs(H0.imag)) > 1e-12 * max(1.0, np.max(np.abs(H0.real))):
+        raise ValueError("the dressed gradient needs a real idle Hamiltonian")
+    w, V = np.linalg.eigh(H0.real)
+    comp, _ = comp_map(sys)
+    Dc = len(comp)
+    W = psi_lab @ barc.conj().T                     # D x Dc, from U_c = V_c^dag psi(T)
+    for s_, j in enumerate(cols):
+        W[:, j] += bar0[:, s_]                      # from the initial columns V_c[:, j]
+    ks, sg = [], []
+    for j, r in enumerate(comp):
+        k = int(np.argmax(np.abs(V[r, :])))
+        ks.append(k)
+        sg.append(1.0 if V[r, k] > 0 else -1.0)
+    for p_, prm in enumerate(prms):
+        if prm[0] == "pulse":
+            continue
+        dH = idle_hamiltonian_derivative(sys, prm)
+        M = V.T @ dH @ V                            # <v_m|dH0|v_k>
+        for j in range(Dc):
+            k = ks[j]
+            den = w[k] - w
+            den[k] = np.inf
+            dv = V @ (M[:, k] / den)
+            grad[p_] += np.real(np.vdot(W[:, j], sg[j] * dv))
+    return F, grad

@@ -225,9 +225,11 @@ def adjoint_gradient(wl, kind=None, nsteps=None):
     return F, grad, prms
 
 
-def adjoint_from_costate(sys, hist, psi_lab, bar_lab, N):
+def adjoint_from_costate(sys, hist, psi_lab, bar_lab, N, with_bar=False):
     """Pull a lab-frame co-state back through the frame epilogue and N RK4 steps:
-    returns (sum over stages of Re <kbar_s, dA_s/dtheta y_s> + the frame term, params)."""
+    returns (sum over stages of Re <kbar_s, dA_s/dtheta y_s> + the frame term, params),
+    and with with_bar the co-state of the initial columns as a third item (the frame is
+    the identity at t = 0)."""
     dt = sys.dt
     prms = sys.param_list()
     grad = np.zeros(len(prms))
@@ -270,6 +272,8 @@ def adjoint_from_costate(sys, hist, psi_lab, bar_lab, N):
             grad[p] += np.real(np.vdot(kb1, dA1 @ y1) + np.vdot(kb2, dA2 @ y2)
                                + np.vdot(kb3, dA2 @ y3) + np.vdot(kb4, dA4 @ y4))
         bar = bar + yb2 + yb3 + yb4 + A1.conj().T @ kb1
+    if with_bar:
+        return grad, prms, bar
     return grad, prms
 
 

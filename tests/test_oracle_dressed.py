@@ -79,6 +79,41 @@ def test_dressed_pulse_gradient_matches_central_differences():
     assert np.max(np.abs(g - fd)) <= 1e-6 * max(1e-6, np.max(np.abs(fd))), (g, fd)
 
 
+def test_dressed_full_gradient_matches_central_differences_through_the_eigensolves():
+    """The Hamiltonian-parameter gradient in the dressed basis (E_J, E_C, E_L per mode, J
+    per coupling) against central differences of F through both eigensolves (each
+    subsystem's and the idle Hamiltonian's).  The derivative of the dressed vectors is
+    about 1 % of the gradient here, far above the tolerance, so dropping it (or a sign
+    slip in it) fails."""
+    from oracle.dressed import dressed_evolve, dressed_full_gradient
+    from oracle.evolve import adjoint_from_costate, block_fidelity_and_costate, param_vector, set_param_vector
+    wl = W.fluxonium_chain(seed=7, nq=3, levels=3, T=0.3, dt=0.01, nseg=2)
+    theta = np.asarray(param_vector(wl), dtype=float)
+    for kind in ("avg", "state"):
+        F, g = dressed_full_gradient(wl, kind)
+        _, gp = dressed_pulse_gradient(wl, kind)
+        npul = len(gp)
+        assert np.array_equal(g[:npul], gp)
+        fd = []
+        for i in range(npul, len(theta)):
+            h = 1e-6 * max(1.0, abs(theta[i]))
+            vals = []
+            for sgn in (1, -1):
+                t2 = theta.copy()
+                t2[i] += sgn * h
+                Fa, Fs, _ = dressed_fidelities(set_param_vector(wl, t2))
+                vals.append(Fa if kind == "avg" else Fs)
+            fd.append((vals[0] - vals[1]) / (2 * h))
+        fd = np.array(fd)
+        assert np.max(np.abs(g[npul:] - fd)) <= 1e-5 * np.max(np.abs(fd)), (kind, g[npul:], fd)
+        if kind == "avg":
+            sys_, Vc, cols, psi_lab, hist = dressed_evolve(wl)
+            T = np.asarray(wl["target"], dtype=complex)
+            _, barc = block_fidelity_and_costate(T, Vc.conj().T @ psi_lab, cols, kind)
+            g_evo, _ = adjoint_from_costate(sys_, hist, psi_lab, Vc @ barc, sys_.N)
+            assert np.max(np.abs(g_evo[npul:] - fd)) > 100 * 1e-5 * np.max(np.abs(fd))
+
+
 def test_paper_multipath_chain_dressed_frequencies_and_zero_zz_coupling():
     # Sec. 3.1's 3-qubit multipath chain: the printed dressed 0-1 frequencies, and the
     # capacitive coupling at which the static ZZ rate of the left pair vanishes
